@@ -1,0 +1,260 @@
+"""ctypes loader for the FP64 CPU oracle (``oracle/karl_oracle.cpp``).
+
+TEST INFRASTRUCTURE ONLY.  The oracle is the correctness reference for the
+CUDA path: only the tests, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU
+baseline may import this module.  The product package never does.
+
+``build()`` compiles the oracle in-tree with g++ (FP contraction off so the
+x86 and Arm builds round the same way).  ``run()`` marshals a problem from
+``paper_2503_10263_gb300.inputs`` into the oracle's own C structs and returns
+the tallies as numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from typing import Dict, Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "karl_oracle.cpp")
+_HDR = os.path.join(_HERE, "karl_oracle.h")
+_LIB = os.path.join(_HERE, "libkarl_oracle.so")
+
+N_SPECIES = 3
+N_REASONS = 8
+LEDGER_LEN = 64
+# ledger slots (mirrors karl_oracle.h)
+E_IN_PRIMARY, E_IN_THERMAL, E_EXIT0, E_EXIT1, E_CUTOFF, E_CAP, E_RECOMB, E_CLUSTER, \
+    E_LOSS_IONIZ, E_LOSS_EXCIT, E_LOSS_RECOIL, E_STALLED = range(12)
+BIRTHS = 12
+DEATHS = 15
+N_COLLISIONS, N_FLIGHTS, N_SPAWN_E, N_SPAWN_ION = 39, 40, 41, 42
+REASONS = ("exit0", "exit1", "cutoff", "cap_coll", "cap_time", "recomb", "cluster", "stalled")
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library next to its source."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+               "-shared", "-pthread", "-o", tmp, _SRC]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Problem(C.Structure):
+    _fields_ = [
+        ("length_m", C.c_double), ("n_zbins", C.c_int32), ("n_seg_m3", C.POINTER(C.c_double)),
+        ("area_m2", C.c_double), ("activity_bq", C.c_double), ("e_cut_ev", C.c_double),
+        ("max_collisions", C.c_uint32), ("max_lifetime_s", C.c_double),
+        ("gas_temperature_k", C.c_double), ("n_tebins", C.c_int32), ("n_spec_bins", C.c_int32),
+        ("spec_bin_ev", C.c_double), ("species_mass_ev", C.c_double * 3),
+        ("target_mass_ev", C.c_double), ("n_energy", C.c_int32), ("e_min_ev", C.c_double),
+        ("e_max_ev", C.c_double), ("n_channels", C.c_int32), ("kind", C.POINTER(C.c_int32)),
+        ("species_in", C.POINTER(C.c_int32)), ("species_out", C.POINTER(C.c_int32)),
+        ("loss_ev", C.POINTER(C.c_double)), ("sigma_m2", C.POINTER(C.c_double)),
+        ("ioniz_eps_ev", C.c_double),
+    ]
+
+
+class _Prims(C.Structure):
+    _fields_ = [("n", C.c_int64), ("z_m", C.POINTER(C.c_double)), ("e_ev", C.POINTER(C.c_double)),
+                ("mu", C.POINTER(C.c_double)), ("species", C.POINTER(C.c_uint8)),
+                ("n_decays", C.c_int64), ("pid_offset", C.c_int64)]
+
+
+class _Tallies(C.Structure):
+    _fields_ = [("spectrum", C.POINTER(C.c_uint64)), ("time_fx", C.POINTER(C.c_uint64)),
+                ("cross_pos", C.POINTER(C.c_uint64)), ("cross_neg", C.POINTER(C.c_uint64)),
+                ("recomb", C.POINTER(C.c_uint64)), ("ledger", C.POINTER(C.c_int64)),
+                ("chan_count", C.POINTER(C.c_uint64)), ("per_primary", C.POINTER(C.c_uint64)),
+                ("density", C.POINTER(C.c_double)), ("current", C.POINTER(C.c_double)),
+                ("field", C.POINTER(C.c_double))]
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = C.CDLL(build())
+        lib.orc_run.argtypes = [C.POINTER(_Problem), C.POINTER(_Prims), C.c_uint64, C.c_int,
+                                C.c_int, C.c_int, C.POINTER(_Tallies)]
+        lib.orc_run.restype = C.c_int
+        lib.orc_run_pass.argtypes = [C.POINTER(_Problem), C.POINTER(_Prims), C.c_uint64, C.c_int,
+                                     C.POINTER(C.c_uint64), C.c_int, C.c_int, C.POINTER(_Tallies)]
+        lib.orc_run_pass.restype = C.c_int
+        lib.orc_philox4x64.argtypes = [C.POINTER(C.c_uint64)] * 3
+        lib.orc_philox4x64.restype = None
+        lib.orc_sigma.argtypes = [C.POINTER(_Problem), C.c_int, C.c_double]
+        lib.orc_sigma.restype = C.c_double
+        lib.orc_collide.argtypes = [C.POINTER(_Problem), C.c_int, C.c_int, C.c_double, C.c_double,
+                                    C.POINTER(C.c_uint64), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double), C.POINTER(C.c_int)]
+        lib.orc_collide.restype = C.c_int
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+class _Marshal:
+    """Keeps the numpy buffers behind a _Problem alive."""
+
+    def __init__(self, prob):
+        self.n_seg = np.ascontiguousarray(prob.n_seg_m3, np.float64)
+        self.kind = np.array([c.kind for c in prob.channels], np.int32)
+        self.sin = np.array([c.species_in for c in prob.channels], np.int32)
+        self.sout = np.array([c.species_out for c in prob.channels], np.int32)
+        self.loss = np.array([c.loss_ev for c in prob.channels], np.float64)
+        self.sigma = (prob.sigma_matrix() if prob.channels
+                      else np.zeros((0, prob.n_energy))).astype(np.float64)
+        self.sigma = np.ascontiguousarray(self.sigma)
+        s = _Problem()
+        s.length_m = prob.length_m
+        s.n_zbins = prob.n_zbins
+        s.n_seg_m3 = _ptr(self.n_seg, C.c_double)
+        s.area_m2 = prob.area_m2
+        s.activity_bq = prob.activity_bq
+        s.e_cut_ev = prob.e_cut_ev
+        s.max_collisions = min(int(prob.max_collisions), 0xFFFFFFFF)
+        s.max_lifetime_s = prob.max_lifetime_s
+        s.gas_temperature_k = prob.gas_temperature_k
+        s.n_tebins = prob.n_tebins
+        s.n_spec_bins = prob.n_spec_bins
+        s.spec_bin_ev = prob.spec_bin_ev
+        for i in range(3):
+            s.species_mass_ev[i] = float(prob.species_mass_ev[i])
+        s.target_mass_ev = prob.target_mass_ev
+        s.n_energy = prob.n_energy
+        s.e_min_ev = prob.e_min_ev
+        s.e_max_ev = prob.e_max_ev
+        s.n_channels = prob.n_channels
+        s.kind = _ptr(self.kind, C.c_int32)
+        s.species_in = _ptr(self.sin, C.c_int32)
+        s.species_out = _ptr(self.sout, C.c_int32)
+        s.loss_ev = _ptr(self.loss, C.c_double)
+        s.sigma_m2 = _ptr(self.sigma, C.c_double)
+        s.ioniz_eps_ev = prob.ioniz_eps_ev
+        self.s = s
+
+
+def _prims(pr, pid_offset: int = 0, n_decays: Optional[int] = None):
+    z = np.ascontiguousarray(pr.z_m, np.float64)
+    e = np.ascontiguousarray(pr.e_ev, np.float64)
+    mu = np.ascontiguousarray(pr.mu, np.float64)
+    sp = np.ascontiguousarray(pr.species, np.uint8)
+    s = _Prims(pr.n, _ptr(z, C.c_double), _ptr(e, C.c_double), _ptr(mu, C.c_double),
+               _ptr(sp, C.c_uint8), int(pr.n_decays if n_decays is None else n_decays),
+               int(pid_offset))
+    return s, (z, e, mu, sp)
+
+
+def empty_tallies(prob, n_primaries: int) -> Dict[str, np.ndarray]:
+    nz, ntb = prob.n_zbins, prob.n_tebins
+    return {
+        "spectrum": np.zeros((2, N_SPECIES, prob.n_spec_bins + 1), np.uint64),
+        "time_fx": np.zeros((N_SPECIES, nz + 2, ntb), np.uint64),
+        "cross_pos": np.zeros((N_SPECIES, nz + 1), np.uint64),
+        "cross_neg": np.zeros((N_SPECIES, nz + 1), np.uint64),
+        "recomb": np.zeros((N_SPECIES, nz), np.uint64),
+        "ledger": np.zeros(LEDGER_LEN, np.int64),
+        "chan_count": np.zeros(max(prob.n_channels, 1), np.uint64),
+        "per_primary": np.zeros(max(n_primaries, 1), np.uint64),
+        "density": np.zeros((N_SPECIES, nz), np.float64),
+        "current": np.zeros((N_SPECIES, nz + 1), np.float64),
+        "field": np.zeros((N_SPECIES, nz, ntb), np.float64),
+    }
+
+
+def _tallies_struct(t: Dict[str, np.ndarray], with_norm: bool = True) -> _Tallies:
+    s = _Tallies()
+    s.spectrum = _ptr(t["spectrum"], C.c_uint64)
+    s.time_fx = _ptr(t["time_fx"], C.c_uint64)
+    s.cross_pos = _ptr(t["cross_pos"], C.c_uint64)
+    s.cross_neg = _ptr(t["cross_neg"], C.c_uint64)
+    s.recomb = _ptr(t["recomb"], C.c_uint64)
+    s.ledger = _ptr(t["ledger"], C.c_int64)
+    s.chan_count = _ptr(t["chan_count"], C.c_uint64)
+    s.per_primary = _ptr(t["per_primary"], C.c_uint64)
+    if with_norm:
+        s.density = _ptr(t["density"], C.c_double)
+        s.current = _ptr(t["current"], C.c_double)
+        s.field = _ptr(t["field"], C.c_double)
+    return s
+
+
+def run(prob, prims, seed: int = 1, n_passes: Optional[int] = None, mode: int = 0,
+        n_threads: int = 1) -> Dict[str, np.ndarray]:
+    """Whole run (one or two passes).  mode 0: optical-depth flights;
+    mode 1: paper-literal segment stop and redraw."""
+    lib = _load()
+    m = _Marshal(prob)
+    ps, keep = _prims(prims)
+    t = empty_tallies(prob, prims.n)
+    ts = _tallies_struct(t)
+    npass = prob.n_passes if n_passes is None else n_passes
+    rc = lib.orc_run(C.byref(m.s), C.byref(ps), C.c_uint64(seed), npass, mode, n_threads,
+                     C.byref(ts))
+    if rc != 0:
+        raise RuntimeError(f"oracle run failed: {rc}")
+    t["per_primary"] = t["per_primary"][:prims.n]
+    t["chan_count"] = t["chan_count"][:prob.n_channels]
+    return t
+
+
+def run_pass(prob, prims, seed: int, pass_index: int, field_time_in: Optional[np.ndarray] = None,
+             pid_offset: int = 0, n_decays: Optional[int] = None, mode: int = 0,
+             n_threads: int = 1) -> Dict[str, np.ndarray]:
+    """One pass over a primary-id range, raw tallies only (for sharding)."""
+    lib = _load()
+    m = _Marshal(prob)
+    ps, keep = _prims(prims, pid_offset, n_decays)
+    t = empty_tallies(prob, prims.n)
+    ts = _tallies_struct(t, with_norm=False)
+    fin = None
+    if field_time_in is not None:
+        fin = np.ascontiguousarray(field_time_in, np.uint64)
+    rc = lib.orc_run_pass(C.byref(m.s), C.byref(ps), C.c_uint64(seed), pass_index,
+                          _ptr(fin, C.c_uint64) if fin is not None else None, mode, n_threads,
+                          C.byref(ts))
+    if rc != 0:
+        raise RuntimeError(f"oracle pass failed: {rc}")
+    t["per_primary"] = t["per_primary"][:prims.n]
+    t["chan_count"] = t["chan_count"][:prob.n_channels]
+    return t
+
+
+def philox4x64(ctr, key) -> np.ndarray:
+    lib = _load()
+    c = np.array(ctr, np.uint64)
+    k = np.array(key, np.uint64)
+    o = np.zeros(4, np.uint64)
+    lib.orc_philox4x64(_ptr(c, C.c_uint64), _ptr(k, C.c_uint64), _ptr(o, C.c_uint64))
+    return o
+
+
+def sigma(prob, channel: int, e_ev: float) -> float:
+    lib = _load()
+    m = _Marshal(prob)
+    return float(lib.orc_sigma(C.byref(m.s), channel, e_ev))
+
+
+def collide(prob, channel: int, species: int, e_ev: float, mu: float, words):
+    """Single collision with given raw Philox words; returns [(E, mu, species)]."""
+    lib = _load()
+    m = _Marshal(prob)
+    w = np.array(words, np.uint64)
+    oe = np.zeros(2)
+    om = np.zeros(2)
+    osp = np.zeros(2, np.int32)
+    n = lib.orc_collide(C.byref(m.s), channel, species, e_ev, mu, _ptr(w, C.c_uint64),
+                        _ptr(oe, C.c_double), _ptr(om, C.c_double), _ptr(osp, C.c_int))
+    return [(float(oe[i]), float(om[i]), int(osp[i])) for i in range(n)]

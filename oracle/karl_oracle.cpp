@@ -1,0 +1,731 @@
+/*
+ * karl_oracle.cpp - plain FP64 CPU oracle of the KARL transport step.
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, by __graft_entry__.smoke()
+ * and by bench.py's CPU-baseline leg, never by the product path.
+ *
+ * Each primary is followed event by event, with its products on a stack, the
+ * way the paper's main cycle does (Sec. 2.1, Fig. 1): draw a free path from the
+ * mean free path (Eqs. mean_free_path and distance_from_mfp), move, tally the
+ * time spent per segment and the face crossings (Secs. 2.2-2.3), check the
+ * terminator (Sec. 3.2), pick a channel with probability sigma_i n_i over the
+ * total (Sec. 2.1), and perform it (Sec. 3.3).  Written for reading, not speed:
+ * linear walks over segments, no tables beyond the inputs, FP64 throughout.
+ *
+ * Readings where the paper is silent (the same ones the GPU path follows):
+ *  - gas density is piecewise constant per z segment; the magnetic field is
+ *    uniform along z, so only z and the pitch cosine mu matter (drift mover,
+ *    Sec. 3.1, exact for uniform B and no E field);
+ *  - sigma(E): linear interpolation in ln E on the input nodes, zero for
+ *    E <= loss of the channel, clamped to the end nodes outside the grid;
+ *  - lab kinetic energy with the target at rest; relativistic speed;
+ *  - elastic: isotropic in the centre-of-mass frame;
+ *  - ionization: secondary energy W in [0, (E-I)/2] with pdf ~ 1/(1+(W/eps)^2),
+ *    the fast electron is the incident one, binary-encounter polar angles,
+ *    secondary azimuth = primary azimuth - pi (Sec. 3.3, Ionization); the ion
+ *    gets a thermal target velocity (no recoil);
+ *  - clustering: the product takes a thermal target's direction and the speed
+ *    that keeps the target's kinetic energy with the product mass;
+ *  - recombination: the impactor is deleted, the partner's field logs one
+ *    deletion in the segment (Sec. 3.3, Recombination);
+ *  - two passes: pass 1 without recombination builds the target fields,
+ *    pass 2 uses them frozen;
+ *  - random numbers: Philox4x64-10 (Salmon et al., SC'11) keyed by
+ *    (seed, primary id), counter (event index, lineage id, pass/domain, sub).
+ */
+#include "karl_oracle.h"
+
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+namespace {
+
+const double C_LIGHT = 299792458.0;
+const double KB_EV = 8.617333262e-5;
+const double TWO_PI = 6.283185307179586476925286766559;
+const double Q_ENERGY = 16777216.0;             /* 2^24 units per eV */
+const double Q_TIME = 1125899906842624.0;       /* 2^50 units per s */
+
+enum { ELASTIC = 0, IONIZATION = 1, EXCITATION = 2, CLUSTERING = 3, RECOMBINATION = 4 };
+enum { SP_E = 0, SP_T2P = 1, SP_T3P = 2 };
+enum { R_EXIT0 = 0, R_EXIT1 = 1, R_CUTOFF = 2, R_CAP_COLL = 3, R_CAP_TIME = 4,
+       R_RECOMB = 5, R_CLUSTER = 6, R_STALLED = 7 };
+enum { DOM_EVENT = 0, DOM_ION_BIRTH = 1, DOM_CLUSTER = 2, DOM_REDRAW = 3 };
+
+/* ---------------- Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11) -------- */
+void mulhilo64(uint64_t a, uint64_t b, uint64_t* hi, uint64_t* lo) {
+  unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
+  *lo = (uint64_t)p;
+  *hi = (uint64_t)(p >> 64);
+}
+
+void philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+  uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+  uint64_t k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; ++r) {
+    uint64_t hi0, lo0, hi1, lo1;
+    mulhilo64(M0, x0, &hi0, &lo0);
+    mulhilo64(M1, x2, &hi1, &lo1);
+    uint64_t y0 = hi1 ^ x1 ^ k0;
+    uint64_t y1 = lo1;
+    uint64_t y2 = hi0 ^ x3 ^ k1;
+    uint64_t y3 = lo0;
+    x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    k0 += W0; k1 += W1;
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* uniform in [0,1) and in (0,1] from the top 53 bits of a word */
+double u01(uint64_t w) { return (double)(w >> 11) * (1.0 / 9007199254740992.0); }
+double eta01(uint64_t w) { return (double)((w >> 11) + 1) * (1.0 / 9007199254740992.0); }
+
+/* SplitMix64 output function (Steele, Lea, Flood 2014) for lineage ids */
+uint64_t mix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+uint64_t child_node(uint64_t parent, uint32_t ev, uint32_t slot) {
+  return mix64(mix64(parent) ^ (((uint64_t)ev << 2) | slot));
+}
+
+int64_t quant_e(double e_ev) { return (int64_t)std::floor(e_ev * Q_ENERGY); }
+
+struct Particle {
+  double z;
+  int64_t eq;        /* kinetic energy, 2^-24 eV */
+  double mu;         /* cos(pitch) w.r.t. +z */
+  uint64_t node;     /* lineage id */
+  double t_alive;
+  uint32_t ev;       /* collisions so far = index of the next flight */
+  int species;
+};
+
+/* Raw tallies of one worker. */
+struct Tally {
+  std::vector<uint64_t> spectrum, time_fx, cross_pos, cross_neg, recomb, chan_count;
+  std::vector<int64_t> ledger;
+  void init(const orc_problem* p) {
+    int nz = p->n_zbins;
+    spectrum.assign((size_t)2 * ORC_N_SPECIES * (p->n_spec_bins + 1), 0);
+    time_fx.assign((size_t)ORC_N_SPECIES * (nz + 2) * p->n_tebins, 0);
+    cross_pos.assign((size_t)ORC_N_SPECIES * (nz + 1), 0);
+    cross_neg.assign((size_t)ORC_N_SPECIES * (nz + 1), 0);
+    recomb.assign((size_t)ORC_N_SPECIES * nz, 0);
+    chan_count.assign((size_t)p->n_channels, 0);
+    ledger.assign(ORC_LEDGER_LEN, 0);
+  }
+};
+
+struct Run {
+  const orc_problem* p;
+  uint64_t seed;
+  int pass;          /* 1 or 2 */
+  int mode;          /* 0 optical depth, 1 segment stop */
+  double dz;
+  /* per recombination channel: rate density of the partner field per segment
+   * (pass 2 only); electrons use sigma_k(E) * f, ions use f / v. */
+  std::vector<std::vector<double>> field;   /* [n_channels][n_zbins] (empty if unused) */
+};
+
+double face(const Run& R, int k) {
+  return k >= R.p->n_zbins ? R.p->length_m : (double)k * R.dz;
+}
+int segment_of(const Run& R, double z) {
+  int j = (int)std::floor(z / R.dz);
+  if (j < 0) j = 0;
+  if (j > R.p->n_zbins - 1) j = R.p->n_zbins - 1;
+  return j;
+}
+
+/* relativistic speed from kinetic energy (Sec. 3.1 remark on gamma) */
+double speed(double e_ev, double m_ev) {
+  double x = e_ev / m_ev;
+  return C_LIGHT * std::sqrt(x * (2.0 + x)) / (1.0 + x);
+}
+
+/* cross section of channel k at lab energy E: linear in ln E between nodes */
+double sigma_at(const orc_problem* p, int k, double e) {
+  if (!(e > p->loss_ev[k])) return 0.0;
+  int n = p->n_energy;
+  double h = std::log(p->e_max_ev / p->e_min_ev) / (double)(n - 1);
+  double x = std::log(e / p->e_min_ev) / h;
+  int i = (int)std::floor(x);
+  double f;
+  if (i < 0) { i = 0; f = 0.0; }
+  else if (i > n - 2) { i = n - 2; f = 1.0; }
+  else { f = x - (double)i; }
+  const double* s = p->sigma_m2 + (size_t)k * n;
+  return (1.0 - f) * s[i] + f * s[i + 1];
+}
+
+bool channel_active(const Run& R, int k, int species) {
+  const orc_problem* p = R.p;
+  if (p->species_in[k] != species) return false;
+  if (p->kind[k] == RECOMBINATION) return R.pass == 2 && !R.field[k].empty();
+  return true;
+}
+
+/* Per-flight coefficient of channel k: sigma_k(E) for gas channels and for an
+ * electron recombining with an ion field; 1/v for an ion recombining with the
+ * electron field (whose per-segment value already carries sigma v).  E is
+ * constant along a flight, so these are evaluated once per flight. */
+void flight_coefficients(const Run& R, int species, double e, double v, double* c) {
+  const orc_problem* p = R.p;
+  for (int k = 0; k < p->n_channels; ++k) {
+    if (!channel_active(R, k, species)) { c[k] = 0.0; continue; }
+    if (p->kind[k] == RECOMBINATION && species != SP_E) c[k] = 1.0 / v;
+    else c[k] = sigma_at(p, k, e);
+  }
+}
+
+/* macroscopic rate per unit path length of channel k in segment j
+ * (the inverse mean free path of Eq. mean_free_path, one term) */
+double channel_rate(const Run& R, int k, const double* c, int j) {
+  if (R.p->kind[k] == RECOMBINATION) return R.field[k].empty() ? 0.0 : c[k] * R.field[k][j];
+  return c[k] * R.p->n_seg_m3[j];
+}
+
+double total_rate(const Run& R, const double* c, int j) {
+  double r = 0.0;
+  for (int k = 0; k < R.p->n_channels; ++k) r += channel_rate(R, k, c, j);
+  return r;
+}
+
+int tebin(const orc_problem* p, double e) {
+  if (p->n_tebins <= 1) return 0;
+  double x = std::log(e / p->e_min_ev) / std::log(p->e_max_ev / p->e_min_ev) * p->n_tebins;
+  int b = (int)std::floor(x);
+  if (b < 0) b = 0;
+  if (b > p->n_tebins - 1) b = p->n_tebins - 1;
+  return b;
+}
+
+uint64_t quant_t(double len, double inv_speed_z) {
+  double t = len * inv_speed_z;
+  return (uint64_t)(t * Q_TIME + 0.5);
+}
+
+struct Worker {
+  const Run* R;
+  Tally T;
+  uint64_t pid;
+  uint64_t tree_collisions;
+
+  void add_time(int s, int j, int b, uint64_t q) {
+    const orc_problem* p = R->p;
+    T.time_fx[((size_t)s * (p->n_zbins + 2) + (j + 1)) * p->n_tebins + b] += q;
+  }
+  void die(const Particle& P, int reason, int ledger_slot) {
+    T.ledger[ORC_DEATHS + P.species * ORC_N_REASONS + reason] += 1;
+    T.ledger[ledger_slot] += P.eq;
+  }
+  void block(uint32_t ev, uint64_t node, int domain, uint64_t sub, uint64_t w[4]) {
+    uint64_t ctr[4] = {(uint64_t)ev, node, ((uint64_t)R->pass << 8) | (uint64_t)domain, sub};
+    uint64_t key[2] = {R->seed, pid};
+    philox4x64_10(ctr, key, w);
+  }
+  /* thermal target: Gamma(3/2, kT) energy = Exp(1) + Z^2/2 (Box-Muller), isotropic */
+  void thermal(const uint64_t w[4], double* e, double* mu) {
+    double kt = KB_EV * R->p->gas_temperature_k;
+    double c = std::cos(TWO_PI * u01(w[2]));
+    *e = kt * (-std::log(eta01(w[0])) - std::log(eta01(w[1])) * c * c);
+    *mu = 2.0 * u01(w[3]) - 1.0;
+  }
+
+  /* Tally the straight flight z0 -> z1 (both inside [0,L]), direction sign dir. */
+  void tally_flight(const Particle& P, double z0, double z1, int dir, double inv_speed_z,
+                    int b, bool exits, int jc) {
+    const orc_problem* p = R->p;
+    int s = P.species;
+    int nz = p->n_zbins;
+    int j0 = segment_of(*R, z0);
+    if (dir > 0) {
+      int j1 = exits ? nz - 1 : jc;
+      if (j1 < j0) j1 = j0;
+      for (int j = j0; j <= j1; ++j) {
+        double lo = (j == j0) ? z0 : face(*R, j);
+        double hi = (j == j1) ? z1 : face(*R, j + 1);
+        bool full = (j != j0) && (j != j1 || exits);
+        double len = full ? R->dz : std::fmax(hi - lo, 0.0);
+        add_time(s, j, b, quant_t(len, inv_speed_z));
+        if (j != j1 || exits) T.cross_pos[(size_t)s * (nz + 1) + j + 1] += 1;
+      }
+    } else {
+      int j1 = exits ? 0 : jc;
+      if (j1 > j0) j1 = j0;
+      for (int j = j0; j >= j1; --j) {
+        double hi = (j == j0) ? z0 : face(*R, j + 1);
+        double lo = (j == j1) ? z1 : face(*R, j);
+        bool full = (j != j0) && (j != j1 || exits);
+        double len = full ? R->dz : std::fmax(hi - lo, 0.0);
+        add_time(s, j, b, quant_t(len, inv_speed_z));
+        if (j != j1 || exits) T.cross_neg[(size_t)s * (nz + 1) + j] += 1;
+      }
+    }
+  }
+
+  /* Free flight, optical-depth form: walk the segments along the path,
+   * accumulating the optical depth until it reaches tau. Returns the end
+   * position; *exit_end = 0/1 if the particle left through z=0 / z=L. */
+  double flight_optical_depth(const Particle& P, double tau, const double* c, int* exit_end,
+                              int* jc) {
+    const orc_problem* p = R->p;
+    int nz = p->n_zbins;
+    double amu = std::fabs(P.mu);
+    int dir = P.mu > 0 ? 1 : -1;
+    double pos = P.z;
+    int j = segment_of(*R, pos);
+    double rem = tau;
+    for (;;) {
+      double r = total_rate(*R, c, j);
+      double bound = dir > 0 ? face(*R, j + 1) : face(*R, j);
+      double len = dir > 0 ? std::fmax(bound - pos, 0.0) : std::fmax(pos - bound, 0.0);
+      double depth = r * len / amu;
+      if (r > 0.0 && depth >= rem) {
+        double dzc = rem / r * amu;
+        double zc = dir > 0 ? pos + dzc : pos - dzc;
+        if (dir > 0 && zc > bound) zc = bound;
+        if (dir < 0 && zc < bound) zc = bound;
+        *exit_end = -1;
+        *jc = j;
+        return zc;
+      }
+      rem -= depth;
+      if (dir > 0 && j == nz - 1) { *exit_end = 1; return p->length_m; }
+      if (dir < 0 && j == 0) { *exit_end = 0; return 0.0; }
+      pos = bound;
+      j += dir;
+    }
+  }
+
+  /* Free flight, paper-literal form (Sec. 3.1): in each segment draw a
+   * distance from the local mean free path; if it reaches the segment face,
+   * stop there without interaction and draw a new distance. */
+  double flight_segment_stop(const Particle& P, double eta0, const double* c, int* exit_end,
+                             int* jc) {
+    const orc_problem* p = R->p;
+    int nz = p->n_zbins;
+    double amu = std::fabs(P.mu);
+    int dir = P.mu > 0 ? 1 : -1;
+    double pos = P.z;
+    int j = segment_of(*R, pos);
+    double eta = eta0;
+    uint64_t redraw = 0;
+    for (;;) {
+      double r = total_rate(*R, c, j);
+      double path = r > 0.0 ? -std::log(eta) / r : INFINITY;     /* Eq. distance_from_mfp */
+      double bound = dir > 0 ? face(*R, j + 1) : face(*R, j);
+      double len = dir > 0 ? std::fmax(bound - pos, 0.0) : std::fmax(pos - bound, 0.0);
+      if (path * amu < len) {
+        *exit_end = -1;
+        *jc = j;
+        double zc = dir > 0 ? pos + path * amu : pos - path * amu;
+        return zc;
+      }
+      if (dir > 0 && j == nz - 1) { *exit_end = 1; return p->length_m; }
+      if (dir < 0 && j == 0) { *exit_end = 0; return 0.0; }
+      pos = bound;
+      j += dir;
+      uint64_t w[4];
+      block(P.ev, P.node, DOM_REDRAW, ++redraw, w);
+      eta = eta01(w[0]);
+    }
+  }
+
+  void spectrum_add(int end, const Particle& P) {
+    const orc_problem* p = R->p;
+    int64_t binq = (int64_t)std::llround(p->spec_bin_ev * Q_ENERGY);
+    int64_t bin = P.eq / binq;
+    if (bin > p->n_spec_bins) bin = p->n_spec_bins;
+    T.spectrum[((size_t)end * ORC_N_SPECIES + P.species) * (p->n_spec_bins + 1) + bin] += 1;
+  }
+
+  /* Follow one particle to termination; products go on the stack. */
+  void transport(Particle P, std::vector<Particle>& stack) {
+    const orc_problem* p = R->p;
+    const int64_t ecut_q = quant_e(p->e_cut_ev);
+    std::vector<double> coef((size_t)p->n_channels + 1, 0.0);
+    for (;;) {
+      int s = P.species;
+      double m = p->species_mass_ev[s];
+      double e = (double)P.eq / Q_ENERGY;
+      double v = speed(e, m);
+      uint64_t w[4];
+      block(P.ev, P.node, DOM_EVENT, 0, w);
+      double eta = eta01(w[0]);
+      double tau = -std::log(eta);                 /* Eq. distance_from_mfp, in optical depth */
+      T.ledger[ORC_N_FLIGHTS] += 1;
+      flight_coefficients(*R, s, e, v, coef.data());
+      int b = tebin(p, e);
+      double amu = std::fabs(P.mu);
+      double zc;
+      int exit_end = -1;
+      int j = -1;
+      double tflight;
+      if (P.mu == 0.0) {
+        /* no motion along z: collide in place after path tau / rate */
+        j = segment_of(*R, P.z);
+        double r = total_rate(*R, coef.data(), j);
+        if (!(r > 0.0)) { die(P, R_STALLED, ORC_E_STALLED); return; }
+        double path = tau / r;
+        tflight = path / v;
+        add_time(s, j, b, (uint64_t)(tflight * Q_TIME + 0.5));
+        zc = P.z;
+      } else {
+        if (R->mode == 1) zc = flight_segment_stop(P, eta, coef.data(), &exit_end, &j);
+        else zc = flight_optical_depth(P, tau, coef.data(), &exit_end, &j);
+        double inv_speed_z = 1.0 / (amu * v);
+        tally_flight(P, P.z, zc, P.mu > 0 ? 1 : -1, inv_speed_z, b, exit_end >= 0, j);
+        tflight = std::fabs(zc - P.z) * inv_speed_z;
+      }
+      P.t_alive += tflight;
+      if (exit_end >= 0) {                                  /* left the geometry */
+        spectrum_add(exit_end, P);
+        die(P, exit_end == 0 ? R_EXIT0 : R_EXIT1, exit_end == 0 ? ORC_E_EXIT0 : ORC_E_EXIT1);
+        return;
+      }
+      P.z = zc;
+      /* ---- collision in segment j: channel with probability rate_k / rate_tot ---- */
+      P.ev += 1;
+      tree_collisions += 1;
+      T.ledger[ORC_N_COLLISIONS] += 1;
+      double rtot = total_rate(*R, coef.data(), j);
+      double target = u01(w[1]) * rtot;
+      int ch = -1, last = -1;
+      double cum = 0.0;
+      for (int k = 0; k < p->n_channels; ++k) {
+        double rk = channel_rate(*R, k, coef.data(), j);
+        if (!(rk > 0.0)) continue;
+        last = k;
+        cum += rk;
+        if (target < cum) { ch = k; break; }
+      }
+      if (ch < 0) ch = last;                                 /* rounding at the top end */
+      T.chan_count[ch] += 1;
+      int kind = p->kind[ch];
+      if (kind == ELASTIC) {
+        /* isotropic in CM; lab energy and polar angle for a target at rest */
+        double g = m / p->target_mass_ev;
+        double cchi = 2.0 * u01(w[2]) - 1.0;
+        double a = 1.0 + 2.0 * g * cchi + g * g;
+        double e1 = e * a / ((1.0 + g) * (1.0 + g));
+        double ct = (cchi + g) / std::sqrt(a);
+        int64_t eq1 = quant_e(e1);
+        if (eq1 > P.eq) eq1 = P.eq;
+        T.ledger[ORC_E_LOSS_RECOIL] += P.eq - eq1;
+        P.eq = eq1;
+        double st = std::sqrt(std::fmax(0.0, 1.0 - ct * ct));
+        double cphi = std::cos(TWO_PI * u01(w[3]));
+        double smu = std::sqrt(std::fmax(0.0, 1.0 - P.mu * P.mu));
+        P.mu = std::fmax(-1.0, std::fmin(1.0, P.mu * ct + smu * st * cphi));
+      } else if (kind == EXCITATION) {
+        int64_t lq = quant_e(p->loss_ev[ch]);
+        P.eq -= lq;
+        T.ledger[ORC_E_LOSS_EXCIT] += lq;
+      } else if (kind == IONIZATION) {
+        int64_t iq = quant_e(p->loss_ev[ch]);
+        int64_t avail = P.eq - iq;
+        double eps = p->ioniz_eps_ev;
+        double wmax = (e - p->loss_ev[ch]) * 0.5;
+        double wsec = eps * std::tan(u01(w[2]) * std::atan(wmax / eps));
+        int64_t wq = quant_e(wsec);
+        if (wq > avail / 2) wq = avail / 2;
+        if (wq < 0) wq = 0;
+        int64_t eq1 = avail - wq;
+        T.ledger[ORC_E_LOSS_IONIZ] += iq;
+        double c2p = avail > 0 ? (double)eq1 / (double)avail : 1.0;   /* cos^2 primary */
+        double c2s = avail > 0 ? (double)wq / (double)avail : 0.0;    /* cos^2 secondary */
+        double cp = std::sqrt(c2p), sp = std::sqrt(c2s);              /* sin_p = cos_s */
+        double cphi = std::cos(TWO_PI * u01(w[3]));
+        double smu = std::sqrt(std::fmax(0.0, 1.0 - P.mu * P.mu));
+        double mu_p = std::fmax(-1.0, std::fmin(1.0, P.mu * cp + smu * sp * cphi));
+        double mu_s = std::fmax(-1.0, std::fmin(1.0, P.mu * sp - smu * cp * cphi));
+        uint32_t ev_coll = P.ev - 1;
+        /* secondary electron */
+        Particle S;
+        S.z = P.z; S.eq = wq; S.mu = mu_s; S.node = child_node(P.node, ev_coll, 0);
+        S.t_alive = 0.0; S.ev = 0; S.species = SP_E;
+        T.ledger[ORC_BIRTHS + SP_E] += 1;
+        T.ledger[ORC_N_SPAWN_E] += 1;
+        if (S.eq < ecut_q) die(S, R_CUTOFF, ORC_E_CUTOFF);
+        else stack.push_back(S);
+        /* ion with the target's (thermal) velocity */
+        int ion = p->species_out[ch];
+        if (ion >= 0) {
+          Particle I;
+          I.z = P.z; I.node = child_node(P.node, ev_coll, 1);
+          I.t_alive = 0.0; I.ev = 0; I.species = ion;
+          uint64_t wi[4];
+          block(0, I.node, DOM_ION_BIRTH, 0, wi);
+          double ei, mui;
+          thermal(wi, &ei, &mui);
+          I.eq = quant_e(ei); I.mu = mui;
+          T.ledger[ORC_E_IN_THERMAL] += I.eq;
+          T.ledger[ORC_BIRTHS + ion] += 1;
+          T.ledger[ORC_N_SPAWN_ION] += 1;
+          stack.push_back(I);
+        }
+        P.eq = eq1;
+        P.mu = mu_p;
+      } else if (kind == CLUSTERING) {
+        /* incident ion consumed; product with a thermal target's energy */
+        die(P, R_CLUSTER, ORC_E_CLUSTER);
+        uint64_t wc[4];
+        block(P.ev - 1, P.node, DOM_CLUSTER, 0, wc);
+        double ec, muc;
+        thermal(wc, &ec, &muc);
+        Particle C;
+        C.z = P.z; C.eq = quant_e(ec); C.mu = muc;
+        C.node = child_node(P.node, P.ev - 1, 2);
+        C.t_alive = 0.0; C.ev = 0; C.species = p->species_out[ch];
+        T.ledger[ORC_E_IN_THERMAL] += C.eq;
+        T.ledger[ORC_BIRTHS + C.species] += 1;
+        P = C;
+        continue;
+      } else if (kind == RECOMBINATION) {
+        int partner = p->species_out[ch];
+        T.recomb[(size_t)partner * p->n_zbins + j] += 1;
+        die(P, R_RECOMB, ORC_E_RECOMB);
+        return;
+      }
+      /* ---- terminator (Sec. 3.2) ---- */
+      if (P.species == SP_E && P.eq < ecut_q) { die(P, R_CUTOFF, ORC_E_CUTOFF); return; }
+      if (P.ev >= p->max_collisions) { die(P, R_CAP_COLL, ORC_E_CAP); return; }
+      if (P.t_alive >= p->max_lifetime_s) { die(P, R_CAP_TIME, ORC_E_CAP); return; }
+    }
+  }
+
+  void run_range(const orc_primaries* pr, int64_t lo, int64_t hi, uint64_t* per_primary) {
+    const orc_problem* p = R->p;
+    const int64_t ecut_q = quant_e(p->e_cut_ev);
+    std::vector<Particle> stack;
+    for (int64_t i = lo; i < hi; ++i) {
+      pid = (uint64_t)(pr->pid_offset + i);
+      tree_collisions = 0;
+      Particle P;
+      P.z = pr->z_m[i]; P.eq = quant_e(pr->e_ev[i]); P.mu = pr->mu[i];
+      P.node = 0; P.t_alive = 0.0; P.ev = 0; P.species = pr->species[i];
+      T.ledger[ORC_E_IN_PRIMARY] += P.eq;
+      T.ledger[ORC_BIRTHS + P.species] += 1;
+      if (P.species == SP_E && P.eq < ecut_q) die(P, R_CUTOFF, ORC_E_CUTOFF);
+      else stack.push_back(P);
+      while (!stack.empty()) {
+        Particle Q = stack.back();
+        stack.pop_back();
+        transport(Q, stack);
+      }
+      if (per_primary) per_primary[i] += tree_collisions;
+    }
+  }
+};
+
+/* Target fields for pass 2 from raw pass-1 time tallies (Eq. target_field_density
+ * with N_gamma = 0 in pass 1; t_sim from Eq. simulated_time). */
+void build_fields(Run& R, const uint64_t* time_in, int64_t n_decays) {
+  const orc_problem* p = R.p;
+  int nz = p->n_zbins, ntb = p->n_tebins;
+  double tsim = (double)n_decays / p->activity_bq;
+  double vol = R.dz * p->area_m2;
+  R.field.assign(p->n_channels, std::vector<double>());
+  for (int k = 0; k < p->n_channels; ++k) {
+    if (p->kind[k] != RECOMBINATION) continue;
+    int partner = p->species_out[k];
+    std::vector<double> f(nz, 0.0);
+    for (int j = 0; j < nz; ++j) {
+      double acc = 0.0;
+      for (int b = 0; b < ntb; ++b) {
+        uint64_t t = time_in[((size_t)partner * (nz + 2) + (j + 1)) * ntb + b];
+        double n = (double)t / Q_TIME / (tsim * vol);
+        if (p->species_in[k] == SP_E) {
+          acc += n;                                  /* ion density */
+        } else {
+          /* ion impactor: electron field weighted by sigma(E_b) v(E_b) */
+          double eb = p->e_min_ev * std::pow(p->e_max_ev / p->e_min_ev, (b + 0.5) / ntb);
+          acc += n * sigma_at(p, k, eb) * speed(eb, p->species_mass_ev[SP_E]);
+        }
+      }
+      f[j] = acc;
+    }
+    R.field[k] = f;
+  }
+}
+
+void add_into(orc_tallies* out, const Tally& T, const orc_problem* p) {
+  for (size_t i = 0; i < T.spectrum.size(); ++i) out->spectrum[i] += T.spectrum[i];
+  for (size_t i = 0; i < T.time_fx.size(); ++i) out->time_fx[i] += T.time_fx[i];
+  for (size_t i = 0; i < T.cross_pos.size(); ++i) out->cross_pos[i] += T.cross_pos[i];
+  for (size_t i = 0; i < T.cross_neg.size(); ++i) out->cross_neg[i] += T.cross_neg[i];
+  for (size_t i = 0; i < T.recomb.size(); ++i) out->recomb[i] += T.recomb[i];
+  for (int i = 0; i < ORC_LEDGER_LEN; ++i) out->ledger[i] += T.ledger[i];
+  for (int i = 0; i < p->n_channels; ++i) out->chan_count[i] += T.chan_count[i];
+}
+
+int check_problem(const orc_problem* p) {
+  if (!p || p->n_zbins <= 0 || !(p->length_m > 0) || p->n_energy < 2 || p->n_channels < 0 ||
+      p->n_tebins < 1 || p->n_spec_bins < 1 || !(p->spec_bin_ev > 0) || !p->n_seg_m3)
+    return 1;
+  return 0;
+}
+
+int do_pass(const orc_problem* p, const orc_primaries* pr, uint64_t seed, int pass,
+            const uint64_t* field_time_in, int mode, int n_threads, orc_tallies* out) {
+  Run R;
+  R.p = p; R.seed = seed; R.pass = pass; R.mode = mode;
+  R.dz = p->length_m / p->n_zbins;
+  R.field.assign(p->n_channels, std::vector<double>());
+  if (pass == 2 && field_time_in) build_fields(R, field_time_in, pr->n_decays);
+  if (n_threads < 1) n_threads = 1;
+  if ((int64_t)n_threads > pr->n) n_threads = (int)(pr->n > 0 ? pr->n : 1);
+  std::vector<Worker> W(n_threads);
+  std::vector<std::thread> th;
+  for (int t = 0; t < n_threads; ++t) {
+    W[t].R = &R;
+    W[t].T.init(p);
+    int64_t lo = pr->n * t / n_threads, hi = pr->n * (t + 1) / n_threads;
+    if (n_threads == 1) W[t].run_range(pr, lo, hi, out->per_primary);
+    else th.emplace_back([&W, t, pr, lo, hi, out] { W[t].run_range(pr, lo, hi, out->per_primary); });
+  }
+  for (auto& x : th) x.join();
+  for (int t = 0; t < n_threads; ++t) add_into(out, W[t].T, p);
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+void orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+  philox4x64_10(ctr, key, out);
+}
+
+double orc_sigma(const orc_problem* p, int channel, double e_ev) { return sigma_at(p, channel, e_ev); }
+
+int orc_collide(const orc_problem* p, int ch, int species, double e_ev, double mu,
+                const uint64_t w[4], double* out_e, double* out_mu, int* out_species) {
+  /* same kinematics as Worker::transport, for single-collision enumeration */
+  double m = p->species_mass_ev[species];
+  int64_t eq = quant_e(e_ev);
+  double e = (double)eq / Q_ENERGY;
+  int kind = p->kind[ch];
+  if (kind == ELASTIC) {
+    double g = m / p->target_mass_ev;
+    double cchi = 2.0 * u01(w[2]) - 1.0;
+    double a = 1.0 + 2.0 * g * cchi + g * g;
+    double e1 = e * a / ((1.0 + g) * (1.0 + g));
+    double ct = (cchi + g) / std::sqrt(a);
+    int64_t eq1 = quant_e(e1);
+    if (eq1 > eq) eq1 = eq;
+    double st = std::sqrt(std::fmax(0.0, 1.0 - ct * ct));
+    double cphi = std::cos(TWO_PI * u01(w[3]));
+    double smu = std::sqrt(std::fmax(0.0, 1.0 - mu * mu));
+    out_e[0] = (double)eq1 / Q_ENERGY;
+    out_mu[0] = std::fmax(-1.0, std::fmin(1.0, mu * ct + smu * st * cphi));
+    out_species[0] = species;
+    return 1;
+  }
+  if (kind == EXCITATION) {
+    out_e[0] = (double)(eq - quant_e(p->loss_ev[ch])) / Q_ENERGY;
+    out_mu[0] = mu; out_species[0] = species;
+    return 1;
+  }
+  if (kind == IONIZATION) {
+    int64_t iq = quant_e(p->loss_ev[ch]);
+    int64_t avail = eq - iq;
+    double eps = p->ioniz_eps_ev;
+    double wmax = (e - p->loss_ev[ch]) * 0.5;
+    double wsec = eps * std::tan(u01(w[2]) * std::atan(wmax / eps));
+    int64_t wq = quant_e(wsec);
+    if (wq > avail / 2) wq = avail / 2;
+    if (wq < 0) wq = 0;
+    int64_t eq1 = avail - wq;
+    double c2p = avail > 0 ? (double)eq1 / (double)avail : 1.0;
+    double c2s = avail > 0 ? (double)wq / (double)avail : 0.0;
+    double cp = std::sqrt(c2p), sp = std::sqrt(c2s);
+    double cphi = std::cos(TWO_PI * u01(w[3]));
+    double smu = std::sqrt(std::fmax(0.0, 1.0 - mu * mu));
+    out_e[0] = (double)eq1 / Q_ENERGY;
+    out_mu[0] = std::fmax(-1.0, std::fmin(1.0, mu * cp + smu * sp * cphi));
+    out_species[0] = species;
+    out_e[1] = (double)wq / Q_ENERGY;
+    out_mu[1] = std::fmax(-1.0, std::fmin(1.0, mu * sp - smu * cp * cphi));
+    out_species[1] = SP_E;
+    return 2;
+  }
+  if (kind == CLUSTERING) {
+    double kt = KB_EV * p->gas_temperature_k;
+    double c = std::cos(TWO_PI * u01(w[2]));
+    double ec = kt * (-std::log(eta01(w[0])) - std::log(eta01(w[1])) * c * c);
+    out_e[0] = (double)quant_e(ec) / Q_ENERGY;
+    out_mu[0] = 2.0 * u01(w[3]) - 1.0;
+    out_species[0] = p->species_out[ch];
+    return 1;
+  }
+  return 0;   /* recombination: no products */
+}
+
+int orc_run_pass(const orc_problem* p, const orc_primaries* pr, uint64_t seed, int pass,
+                 const uint64_t* field_time_in, int mode, int n_threads, orc_tallies* out) {
+  if (check_problem(p) || !pr || !out || (pass != 1 && pass != 2)) return 1;
+  return do_pass(p, pr, seed, pass, field_time_in, mode, n_threads, out);
+}
+
+int orc_run(const orc_problem* p, const orc_primaries* pr, uint64_t seed, int n_passes,
+            int mode, int n_threads, orc_tallies* out) {
+  if (check_problem(p) || !pr || !out || n_passes < 1 || n_passes > 2) return 1;
+  int nz = p->n_zbins, ntb = p->n_tebins;
+  size_t ntime = (size_t)ORC_N_SPECIES * (nz + 2) * ntb;
+  /* pass 1 into out; if two passes, keep its time tally and rerun */
+  int rc = do_pass(p, pr, seed, 1, nullptr, mode, n_threads, out);
+  if (rc) return rc;
+  std::vector<uint64_t> time1(out->time_fx, out->time_fx + ntime);
+  if (n_passes == 2) {
+    std::memset(out->spectrum, 0, sizeof(uint64_t) * 2 * ORC_N_SPECIES * (p->n_spec_bins + 1));
+    std::memset(out->time_fx, 0, sizeof(uint64_t) * ntime);
+    std::memset(out->cross_pos, 0, sizeof(uint64_t) * ORC_N_SPECIES * (nz + 1));
+    std::memset(out->cross_neg, 0, sizeof(uint64_t) * ORC_N_SPECIES * (nz + 1));
+    std::memset(out->recomb, 0, sizeof(uint64_t) * ORC_N_SPECIES * nz);
+    std::memset(out->ledger, 0, sizeof(int64_t) * ORC_LEDGER_LEN);
+    std::memset(out->chan_count, 0, sizeof(uint64_t) * p->n_channels);
+    if (out->per_primary) std::memset(out->per_primary, 0, sizeof(uint64_t) * pr->n);
+    rc = do_pass(p, pr, seed, 2, time1.data(), mode, n_threads, out);
+    if (rc) return rc;
+  }
+  /* normalisation: Eq. target_field_density, current j = (N+ - N-)/(A t_sim) */
+  double dz = p->length_m / nz;
+  double tsim = (double)pr->n_decays / p->activity_bq;
+  double vol = dz * p->area_m2;
+  for (int s = 0; s < ORC_N_SPECIES; ++s) {
+    for (int j = 0; j < nz; ++j) {
+      double tsum = 0.0, t1 = 0.0;
+      for (int b = 0; b < ntb; ++b) {
+        size_t idx = ((size_t)s * (nz + 2) + (j + 1)) * ntb + b;
+        tsum += (double)out->time_fx[idx] / Q_TIME;
+        double nb = (double)time1[idx] / Q_TIME / (tsim * vol);
+        t1 += nb;
+        if (out->field) out->field[((size_t)s * nz + j) * ntb + b] = nb;
+      }
+      if (out->density)
+        out->density[(size_t)s * nz + j] =
+            tsum / (tsim * vol) - (double)out->recomb[(size_t)s * nz + j] / vol;
+      (void)t1;
+    }
+    if (out->current)
+      for (int k = 0; k <= nz; ++k) {
+        size_t idx = (size_t)s * (nz + 1) + k;
+        out->current[idx] =
+            ((double)out->cross_pos[idx] - (double)out->cross_neg[idx]) / (p->area_m2 * tsim);
+      }
+  }
+  return 0;
+}
+
+}  /* extern "C" */

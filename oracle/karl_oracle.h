@@ -1,0 +1,108 @@
+/*
+ * karl_oracle.h - plain FP64 CPU oracle of the KARL transport step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library is the correctness reference for the
+ * CUDA path.  Only the tests, __graft_entry__.smoke() and bench.py's CPU
+ * baseline may load it; the product path never calls it.
+ *
+ * It follows the paper event by event (Sec. 2.1 main cycle and Fig. 1, the
+ * free-path law Eqs. mean_free_path / distance_from_mfp, the segment-stop
+ * mover rule of Sec. 3.1, the interactions of Sec. 3.3, the density-field and
+ * current estimators of Secs. 2.2-2.3 and Eq. target_field_density) in FP64.
+ * It shares no code with the GPU path.
+ */
+#ifndef KARL_ORACLE_H
+#define KARL_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_N_SPECIES = 3, ORC_N_REASONS = 8, ORC_LEDGER_LEN = 64 };
+
+/* ledger layout (int64): energies in units of 2^-24 eV, then counters */
+enum {
+  ORC_E_IN_PRIMARY = 0, ORC_E_IN_THERMAL = 1, ORC_E_EXIT0 = 2, ORC_E_EXIT1 = 3,
+  ORC_E_CUTOFF = 4, ORC_E_CAP = 5, ORC_E_RECOMB = 6, ORC_E_CLUSTER = 7,
+  ORC_E_LOSS_IONIZ = 8, ORC_E_LOSS_EXCIT = 9, ORC_E_LOSS_RECOIL = 10, ORC_E_STALLED = 11,
+  ORC_BIRTHS = 12,              /* [3] */
+  ORC_DEATHS = 15,              /* [3][8] */
+  ORC_N_COLLISIONS = 39, ORC_N_FLIGHTS = 40, ORC_N_SPAWN_E = 41, ORC_N_SPAWN_ION = 42
+};
+
+typedef struct {
+  double length_m;
+  int32_t n_zbins;
+  const double* n_seg_m3;      /* [n_zbins] */
+  double area_m2;
+  double activity_bq;
+  double e_cut_ev;
+  uint32_t max_collisions;
+  double max_lifetime_s;       /* +inf: no cap */
+  double gas_temperature_k;
+  int32_t n_tebins;
+  int32_t n_spec_bins;
+  double spec_bin_ev;
+  double species_mass_ev[ORC_N_SPECIES];
+  double target_mass_ev;
+  int32_t n_energy;
+  double e_min_ev, e_max_ev;
+  int32_t n_channels;
+  const int32_t* kind;         /* 0 elastic 1 ionization 2 excitation 3 clustering 4 recombination */
+  const int32_t* species_in;
+  const int32_t* species_out;
+  const double* loss_ev;
+  const double* sigma_m2;      /* [n_channels][n_energy] */
+  double ioniz_eps_ev;
+} orc_problem;
+
+typedef struct {
+  int64_t n;
+  const double* z_m;
+  const double* e_ev;
+  const double* mu;
+  const uint8_t* species;
+  int64_t n_decays;            /* decays of the whole run, for t_sim = N/a */
+  int64_t pid_offset;          /* primary id of element 0 */
+} orc_primaries;
+
+typedef struct {
+  uint64_t* spectrum;          /* [2][3][n_spec_bins+1] */
+  uint64_t* time_fx;           /* [3][n_zbins+2][n_tebins], LSB 2^-50 s */
+  uint64_t* cross_pos;         /* [3][n_zbins+1] */
+  uint64_t* cross_neg;         /* [3][n_zbins+1] */
+  uint64_t* recomb;            /* [3][n_zbins] */
+  int64_t* ledger;             /* [ORC_LEDGER_LEN] */
+  uint64_t* chan_count;        /* [n_channels] */
+  uint64_t* per_primary;       /* [n] collisions in each primary's tree, may be NULL */
+  double* density;             /* [3][n_zbins], may be NULL */
+  double* current;             /* [3][n_zbins+1], may be NULL */
+  double* field;               /* [3][n_zbins][n_tebins] pass-1 densities, may be NULL */
+} orc_tallies;
+
+/* mode 0: free flight by optical depth (one draw per flight);
+ * mode 1: paper-literal segment stop and redraw (Sec. 3.1). */
+int orc_run(const orc_problem* p, const orc_primaries* pr, uint64_t seed, int n_passes,
+            int mode, int n_threads, orc_tallies* out);
+
+/* One pass only.  pass = 1: no recombination.  pass = 2: recombination with
+ * the target fields built from field_time_in (raw pass-1 time tallies of the
+ * whole run, [3][n_zbins+2][n_tebins]).  Output tallies are raw and
+ * accumulated (+=) into out; density/current/field are not written. */
+int orc_run_pass(const orc_problem* p, const orc_primaries* pr, uint64_t seed, int pass,
+                 const uint64_t* field_time_in, int mode, int n_threads, orc_tallies* out);
+
+/* Test hooks. */
+void orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
+double orc_sigma(const orc_problem* p, int channel, double e_ev);
+/* One collision of channel `channel` for a particle (species, e_ev, mu) with
+ * the four uniforms u[0..3] as raw 64-bit words.  Returns the number of
+ * products written to out_* (the incident particle first, if it survives). */
+int orc_collide(const orc_problem* p, int channel, int species, double e_ev, double mu,
+                const uint64_t words[4], double* out_e, double* out_mu, int* out_species);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

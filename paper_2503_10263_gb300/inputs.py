@@ -1,0 +1,386 @@
+"""Seeded synthetic inputs for the KARL transport step.
+
+This module builds the problem descriptions that both the CUDA path and the
+CPU oracle consume: geometry and gas profile, cross-section tables, species
+masses and the primary particles of each decay.  It holds none of the
+transport arithmetic (flights, channel choice, kinematics, tallies); it only
+writes down inputs, so both sides can be fed identical data.
+
+Every quantity is synthetic.  The paper's cross-section data (Yoon, Janev,
+Rudd, Kim, Elsepa), its gas-flow profile and its KATRIN parameter file are not
+available, so analytic Born-Bethe-form tables stand in for the data behind the
+cross-section figures of Sec. 3.3, and a parabolic profile stands in for the
+measured gas column (Sec. 5 example run: L = 16.57 m, B = 2.5 T).
+
+Configurations (sizes follow the hot-path workloads):
+
+* ``config1``: 1e4 beta electrons, uniform 1e19 m^-3 gas in a 10 m column,
+  4 electron channels, FP64.
+* ``config2``: 1e7 decays (one beta electron and one thermal T2+ each),
+  parabolic profile with 5e21 m^-2 column, 7 electron channels, T2+ -> T3+
+  clustering and electron-ion recombination (two passes).
+* ``config3``: ``config1`` inputs, run in the FP32 precision form.
+* ``config4_batch``: 256 source configurations of uneven size.
+* ``config5_requests``: Poisson arrivals of config-4-style requests.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional
+
+import numpy as np
+
+# ---------------------------------------------------------------------------
+# physical constants (CODATA 2018) used to describe the inputs
+AMU_EV = 931.49410242e6          # atomic mass unit, eV/c^2
+ME_EV = 510998.95000             # electron rest energy, eV
+M_T_ATOM_U = 3.01604928          # tritium atom mass, u
+M_T2_EV = 2.0 * M_T_ATOM_U * AMU_EV          # neutral T2 (binding neglected)
+M_T2P_EV = M_T2_EV - ME_EV                   # T2+
+M_T3P_EV = 3.0 * M_T_ATOM_U * AMU_EV - ME_EV  # T3+
+KB_EV_PER_K = 8.617333262e-5
+ALPHA_FS = 7.2973525693e-3
+PI_A0_SQ_M2 = math.pi * (5.29177210903e-11) ** 2   # 8.797e-21 m^2
+RYDBERG_EV = 13.605693122994
+T_HALF_S = 12.32 * 365.25 * 86400.0          # tritium half-life
+
+# species and channel kinds (numeric values are part of the C ABI)
+E, T2P, T3P = 0, 1, 2
+N_SPECIES = 3
+SPECIES_MASS_EV = np.array([ME_EV, M_T2P_EV, M_T3P_EV], dtype=np.float64)
+SPECIES_NAMES = ("e-", "T2+", "T3+")
+
+ELASTIC, IONIZATION, EXCITATION, CLUSTERING, RECOMBINATION = 0, 1, 2, 3, 4
+KIND_NAMES = ("elastic", "ionization", "excitation", "clustering", "recombination")
+
+
+@dataclasses.dataclass
+class Channel:
+    name: str
+    kind: int
+    species_in: int
+    species_out: int      # ionization: ion species produced (-1 none);
+                          # clustering: product; recombination: partner field
+    loss_ev: float
+    sigma_m2: np.ndarray  # [n_energy] values at the table nodes
+
+
+@dataclasses.dataclass
+class Problem:
+    """One source configuration: geometry, gas, tables and run options."""
+    name: str
+    length_m: float
+    n_zbins: int
+    n_seg_m3: np.ndarray           # [n_zbins] piecewise-constant gas density
+    area_m2: float
+    activity_bq: float
+    e_cut_ev: float
+    max_collisions: int
+    max_lifetime_s: float          # inf = no lifetime cap
+    b_tesla: float
+    gas_temperature_k: float
+    n_tebins: int                  # energy bins of the time (density) tally
+    n_spec_bins: int               # end-spectrum bins (+1 overflow)
+    spec_bin_ev: float
+    species_mass_ev: np.ndarray    # [3]
+    target_mass_ev: float          # background gas molecule (T2)
+    n_energy: int
+    e_min_ev: float
+    e_max_ev: float
+    ioniz_eps_ev: float
+    channels: List[Channel]
+    n_passes: int = 1
+
+    @property
+    def n_channels(self) -> int:
+        return len(self.channels)
+
+    def energy_nodes(self) -> np.ndarray:
+        return energy_nodes(self.n_energy, self.e_min_ev, self.e_max_ev)
+
+    def sigma_matrix(self) -> np.ndarray:
+        return np.ascontiguousarray(
+            np.stack([c.sigma_m2 for c in self.channels]).astype(np.float64))
+
+    def column_m2(self) -> float:
+        return float(np.sum(self.n_seg_m3) * self.length_m / self.n_zbins)
+
+
+@dataclasses.dataclass
+class Primaries:
+    z_m: np.ndarray
+    e_ev: np.ndarray
+    mu: np.ndarray
+    species: np.ndarray            # uint8
+    n_decays: int
+
+    @property
+    def n(self) -> int:
+        return int(self.z_m.shape[0])
+
+    def slice(self, first: int, count: int) -> "Primaries":
+        s = slice(first, first + count)
+        return Primaries(self.z_m[s].copy(), self.e_ev[s].copy(), self.mu[s].copy(),
+                         self.species[s].copy(), self.n_decays)
+
+
+# ---------------------------------------------------------------------------
+# cross-section tables (synthetic Born-Bethe form)
+
+def energy_nodes(n: int, e_min: float, e_max: float) -> np.ndarray:
+    i = np.arange(n, dtype=np.float64)
+    return e_min * (e_max / e_min) ** (i / (n - 1))
+
+
+def born_bethe(e: np.ndarray, e_k: float, m_k: float) -> np.ndarray:
+    """pi a0^2 M (R/E) ln(E/E_k) above threshold, 0 at and below it."""
+    out = np.zeros_like(e)
+    on = e > e_k
+    out[on] = PI_A0_SQ_M2 * m_k * (RYDBERG_EV / e[on]) * np.log(e[on] / e_k)
+    return out
+
+
+def elastic_sigma(e: np.ndarray, s0: float = 1e-19, e_s: float = 10.0) -> np.ndarray:
+    return s0 / (1.0 + e / e_s)
+
+
+def recomb_sigma(e: np.ndarray, s_r: float = 1e-20) -> np.ndarray:
+    return s_r * (1.0 / e)
+
+
+def electron_channels(nodes: np.ndarray, full: bool) -> List[Channel]:
+    """Electron-T2 channels in table (selection) order."""
+    ch = [Channel("elastic", ELASTIC, E, -1, 0.0, elastic_sigma(nodes)),
+          Channel("ionization", IONIZATION, E, T2P if full else -1, 15.4,
+                  born_bethe(nodes, 15.4, 4.2))]
+    if full:
+        for ek, m in ((8.9, 0.3), (11.4, 0.9), (12.6, 0.7)):
+            ch.append(Channel(f"excitation_{ek}", EXCITATION, E, -1, ek,
+                              born_bethe(nodes, ek, m)))
+        ch.append(Channel("vibration", EXCITATION, E, -1, 0.5, born_bethe(nodes, 0.5, 0.05)))
+        ch.append(Channel("rotation", EXCITATION, E, -1, 0.044, born_bethe(nodes, 0.044, 0.02)))
+    else:
+        ch.append(Channel("excitation", EXCITATION, E, -1, 12.6, born_bethe(nodes, 12.6, 1.6)))
+        ch.append(Channel("vibration", EXCITATION, E, -1, 0.5, born_bethe(nodes, 0.5, 0.05)))
+    return ch
+
+
+def ion_channels(nodes: np.ndarray) -> List[Channel]:
+    """Recombination (both directions) and T2+ + T2 -> T3+ clustering."""
+    rec = recomb_sigma(nodes)
+    return [
+        Channel("recomb_e_T2+", RECOMBINATION, E, T2P, 0.0, rec.copy()),
+        Channel("recomb_e_T3+", RECOMBINATION, E, T3P, 0.0, rec.copy()),
+        Channel("clustering_T2+", CLUSTERING, T2P, T3P, 0.0, np.full_like(nodes, 1.91e-18)),
+        Channel("recomb_T2+_e", RECOMBINATION, T2P, E, 0.0, rec.copy()),
+        Channel("recomb_T3+_e", RECOMBINATION, T3P, E, 0.0, rec.copy()),
+    ]
+
+
+# ---------------------------------------------------------------------------
+# gas profiles
+
+def parabolic_segment_means(n0: float, length: float, nz: int) -> np.ndarray:
+    """Exact mean of n0[1-(2z/L-1)^2] + 0.05 n0 over each of nz segments."""
+    edges = np.linspace(0.0, length, nz + 1)
+    u = 2.0 * edges / length - 1.0
+    prim = u - u ** 3 / 3.0                    # antiderivative in u
+    mean_par = (prim[1:] - prim[:-1]) / (u[1:] - u[:-1])
+    return n0 * (mean_par + 0.05)
+
+
+def parabolic_n0(column_m2: float, length: float) -> float:
+    return column_m2 / ((2.0 / 3.0 + 0.05) * length)
+
+
+def activity_for(column_m2: float, area_m2: float) -> float:
+    """Decays/s of the T2 column: two tritium nuclei per molecule."""
+    lam = math.log(2.0) / T_HALF_S
+    return 2.0 * lam * column_m2 * area_m2
+
+
+# ---------------------------------------------------------------------------
+# primary generators
+
+def beta_pdf(e_ev: np.ndarray, e0: float = 18600.0, z_daughter: int = 2) -> np.ndarray:
+    """Allowed beta spectrum F(Z,E) p W (E0-E)^2 with the nonrelativistic
+    Fermi function F = 2 pi eta / (1 - exp(-2 pi eta)), eta = Z alpha / beta."""
+    e = np.asarray(e_ev, dtype=np.float64)
+    w = e + ME_EV
+    p = np.sqrt(np.maximum(w * w - ME_EV * ME_EV, 0.0))
+    beta = np.where(w > 0, p / w, 0.0)
+    out = np.zeros_like(e)
+    ok = (e > 0) & (e < e0)
+    eta = z_daughter * ALPHA_FS / beta[ok]
+    fermi = 2.0 * math.pi * eta / (-np.expm1(-2.0 * math.pi * eta))
+    out[ok] = fermi * p[ok] * w[ok] * (e0 - e[ok]) ** 2
+    return out
+
+
+def sample_beta(rng: np.random.Generator, n: int, e0: float = 18600.0) -> np.ndarray:
+    """Rejection sampling of the allowed spectrum (the injector's method)."""
+    grid = np.linspace(1e-6, e0, 200001)
+    fmax = float(beta_pdf(grid, e0).max()) * 1.02
+    out = np.empty(n, dtype=np.float64)
+    filled = 0
+    while filled < n:
+        m = int((n - filled) * 2.2) + 64
+        e = rng.uniform(0.0, e0, m)
+        keep = e[rng.uniform(0.0, fmax, m) < beta_pdf(e, e0)]
+        k = min(keep.size, n - filled)
+        out[filled:filled + k] = keep[:k]
+        filled += k
+    return out
+
+
+def sample_thermal_energy(rng: np.random.Generator, n: int, t_k: float) -> np.ndarray:
+    """Maxwell-Boltzmann kinetic energies: Gamma(3/2, kT)."""
+    return rng.gamma(1.5, KB_EV_PER_K * t_k, n)
+
+
+def isotropic_mu(rng: np.random.Generator, n: int) -> np.ndarray:
+    return rng.uniform(-1.0, 1.0, n)
+
+
+def positions_by_density(rng: np.random.Generator, n: int, n_seg: np.ndarray,
+                         length: float) -> np.ndarray:
+    """Birth positions with probability proportional to the gas density."""
+    nz = n_seg.shape[0]
+    p = n_seg / n_seg.sum()
+    seg = rng.choice(nz, size=n, p=p)
+    dz = length / nz
+    return np.minimum((seg + rng.uniform(0.0, 1.0, n)) * dz, length)
+
+
+# ---------------------------------------------------------------------------
+# configurations
+
+def _problem(name: str, length: float, nz: int, n_seg: np.ndarray, full: bool,
+             n_energy: int = 2048, n_tebins: Optional[int] = None) -> Problem:
+    nodes = energy_nodes(n_energy, 1.0, 2.0e4)
+    chans = electron_channels(nodes, full)
+    if full:
+        chans += ion_channels(nodes)
+    area = 1.0
+    column = float(np.sum(n_seg) * length / nz)
+    return Problem(
+        name=name, length_m=length, n_zbins=nz, n_seg_m3=np.ascontiguousarray(n_seg, np.float64),
+        area_m2=area, activity_bq=activity_for(column, area), e_cut_ev=1.0,
+        max_collisions=1_000_000, max_lifetime_s=math.inf, b_tesla=2.5,
+        gas_temperature_k=80.0, n_tebins=(64 if full else 1) if n_tebins is None else n_tebins,
+        n_spec_bins=20000, spec_bin_ev=1.0, species_mass_ev=SPECIES_MASS_EV.copy(),
+        target_mass_ev=M_T2_EV, n_energy=n_energy, e_min_ev=1.0, e_max_ev=2.0e4,
+        ioniz_eps_ev=8.0, channels=chans, n_passes=2 if full else 1)
+
+
+def config1(n_primaries: int = 10_000, seed: int = 1, density_m3: float = 1e19,
+            length: float = 10.0, nz: int = 1000):
+    """Plain method: uniform gas, four electron channels, beta electrons
+    born uniformly along z with isotropic pitch."""
+    prob = _problem("config1", length, nz, np.full(nz, density_m3), full=False)
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 1]))
+    z = rng.uniform(0.0, length, n_primaries)
+    e = sample_beta(rng, n_primaries)
+    mu = isotropic_mu(rng, n_primaries)
+    prims = Primaries(z, e, mu, np.zeros(n_primaries, np.uint8), n_primaries)
+    return prob, prims
+
+
+def config2(n_decays: int = 10_000_000, seed: int = 1, column_m2: float = 5e21,
+            length: float = 10.0, nz: int = 1000):
+    """Full-size plain method: parabolic profile, full channel set, one beta
+    electron and one thermal T2+ per decay, both born where the gas is."""
+    n0 = parabolic_n0(column_m2, length)
+    prob = _problem("config2", length, nz, parabolic_segment_means(n0, length, nz), full=True)
+    return prob, decay_primaries(prob, n_decays, seed)
+
+
+def decay_primaries(prob: Problem, n_decays: int, seed: int) -> Primaries:
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 2]))
+    z = positions_by_density(rng, n_decays, prob.n_seg_m3, prob.length_m)
+    e_beta = sample_beta(rng, n_decays)
+    mu_e = isotropic_mu(rng, n_decays)
+    e_ion = sample_thermal_energy(rng, n_decays, prob.gas_temperature_k)
+    mu_i = isotropic_mu(rng, n_decays)
+    # interleave: decay d -> particle 2d (electron), 2d+1 (T2+)
+    zz = np.repeat(z, 2)
+    ee = np.empty(2 * n_decays); ee[0::2] = e_beta; ee[1::2] = e_ion
+    mm = np.empty(2 * n_decays); mm[0::2] = mu_e; mm[1::2] = mu_i
+    sp = np.empty(2 * n_decays, np.uint8); sp[0::2] = E; sp[1::2] = T2P
+    return Primaries(zz, ee, mm, sp, n_decays)
+
+
+def config3(n_primaries: int = 10_000, seed: int = 1):
+    """Config 1 inputs; the precision form is a run option."""
+    prob, prims = config1(n_primaries, seed)
+    prob.name = "config3"
+    return prob, prims
+
+
+def config4_batch(n_configs: int = 256, meta_seed: int = 1, np_lo: float = 1e3,
+                  np_hi: float = 1e6, nz: int = 1000):
+    """Uneven batch of source configurations: column 0.1-1.0 x 5e21 m^-2,
+    length 2-10 m, decays log-uniform in [np_lo, np_hi]."""
+    rng = np.random.default_rng(np.random.SeedSequence([meta_seed, 4]))
+    out = []
+    for i in range(n_configs):
+        col = rng.uniform(0.1, 1.0) * 5e21
+        length = rng.uniform(2.0, 10.0)
+        nd = int(round(math.exp(rng.uniform(math.log(np_lo), math.log(np_hi)))))
+        n0 = parabolic_n0(col, length)
+        prob = _problem(f"config4_{i}", length, nz, parabolic_segment_means(n0, length, nz),
+                        full=True)
+        seed = (meta_seed << 32) + i
+        out.append((prob, decay_primaries(prob, nd, seed), seed))
+    return out
+
+
+def config5_requests(duration_s: float = 60.0, rate_hz: float = 50.0, arrival_seed: int = 1,
+                     np_lo: float = 1e3, np_hi: float = 1e6, nz: int = 1000,
+                     max_requests: Optional[int] = None):
+    """Poisson arrivals of config-4-style requests: (t_arrival, problem,
+    primaries, seed)."""
+    rng = np.random.default_rng(np.random.SeedSequence([arrival_seed, 5]))
+    t = 0.0
+    out = []
+    i = 0
+    while True:
+        t += rng.exponential(1.0 / rate_hz)
+        if t > duration_s or (max_requests is not None and i >= max_requests):
+            break
+        col = rng.uniform(0.1, 1.0) * 5e21
+        length = rng.uniform(2.0, 10.0)
+        nd = int(round(math.exp(rng.uniform(math.log(np_lo), math.log(np_hi)))))
+        n0 = parabolic_n0(col, length)
+        prob = _problem(f"req_{i}", length, nz, parabolic_segment_means(n0, length, nz),
+                        full=True)
+        seed = (arrival_seed << 32) + i
+        out.append((t, prob, decay_primaries(prob, nd, seed), seed))
+        i += 1
+    return out
+
+
+# ---------------------------------------------------------------------------
+# small test problems
+
+def uniform_problem(n_seg_m3: float, length: float, nz: int, channels: List[Channel],
+                    n_energy: int = 2048, e_min: float = 1.0, e_max: float = 2.0e4,
+                    e_cut: float = 1.0, n_tebins: int = 1, n_passes: int = 1,
+                    n_spec_bins: int = 20000, spec_bin_ev: float = 1.0,
+                    max_collisions: int = 1_000_000, max_lifetime_s: float = math.inf) -> Problem:
+    n_seg = np.full(nz, float(n_seg_m3))
+    column = float(np.sum(n_seg) * length / nz)
+    return Problem(
+        name="test", length_m=length, n_zbins=nz, n_seg_m3=n_seg, area_m2=1.0,
+        activity_bq=activity_for(column, 1.0) if column > 0 else 1.0, e_cut_ev=e_cut,
+        max_collisions=max_collisions, max_lifetime_s=max_lifetime_s, b_tesla=2.5,
+        gas_temperature_k=80.0, n_tebins=n_tebins, n_spec_bins=n_spec_bins,
+        spec_bin_ev=spec_bin_ev, species_mass_ev=SPECIES_MASS_EV.copy(),
+        target_mass_ev=M_T2_EV, n_energy=n_energy, e_min_ev=e_min, e_max_ev=e_max,
+        ioniz_eps_ev=8.0, channels=channels, n_passes=n_passes)
+
+
+def beam(n: int, z0: float, e_ev: float, mu: float, species: int = E) -> Primaries:
+    return Primaries(np.full(n, z0), np.full(n, e_ev), np.full(n, mu),
+                     np.full(n, species, np.uint8), n)
