@@ -1,0 +1,337 @@
+"""Benchmark of the KARL transport hot path on GB300.
+
+One step = one whole run of the full-size plain method (1e7 decays, each a
+beta electron and a thermal T2+, parabolic 5e21 m^-2 column over 10 m, 1000
+segments, seven electron channels, T2+ -> T3+ clustering and electron-ion
+recombination, two passes) through the C ABI.  The metric is collision
+events per second (performed interactions of all channels in both passes);
+primaries/s and flights/s are reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Rank 0 prints one JSON line.  With N > 1 (torchrun) every rank runs its own
+replica of the workload with its own primary ids (weak scaling, no
+collective on the data path); value = all ranks' collisions / max time.
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+BYTES_PER_EVENT_FP64 = 104     # event-based state model: 52 B read + 52 B written per event
+BYTES_PER_EVENT_FP32 = 80
+WORKLOAD = ("config2: 1e7 decays (1e7 beta e- + 1e7 thermal T2+), parabolic profile with "
+            "5e21 m^-2 column, L = 10 m, 1000 z segments, 7 e- channels + T2+ clustering + "
+            "e-/ion recombination, two passes")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _oracle_sample(n_decays_total: int, seconds: float, threads: int):
+    """Time the oracle as it stands on a bounded sample of the same workload."""
+    import oracle
+    from paper_2503_10263_gb300 import inputs
+    oracle.build()
+
+    def run(nd):
+        prob, prims = inputs.config2(n_decays=nd, seed=1)
+        t0 = time.perf_counter()
+        r = oracle.run(prob, prims, seed=1, n_threads=threads)
+        dt = time.perf_counter() - t0
+        return int(r["ledger"][39]), dt
+
+    c0, t0 = run(500)
+    rate = c0 / max(t0, 1e-6)
+    per_decay = c0 / 500
+    nd = int(min(n_decays_total, max(500, seconds * rate / max(per_decay, 1))))
+    c, dt = run(nd)
+    return c, dt, nd
+
+
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    coll = secs = 0.0
+    nd = 0
+    for i in range(args.warmup + args.steps):
+        c, dt, nd = _oracle_sample(args.decays, args.ref_step_s, threads)
+        if i >= args.warmup:
+            coll += c
+            secs += dt
+    value = coll / secs
+    sample = (f"first {nd} decays of the workload (both passes) per step, "
+              f"{args.steps} timed steps after {args.warmup} warm-up")
+    line = {
+        "metric": "collision events/s", "value": value, "unit": "collision events/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD, "sample_decays": nd, "parallelism": "host threads"},
+        "cpu_baseline": {"value": value, "unit": "collision events/s", "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "collision events/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2503_10263_gb300 import inputs, karl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2503_10263_gb300 import build as kbuild
+    kbuild.build()
+
+    prob, prims = inputs.config2(n_decays=args.decays, seed=1)
+    n = prims.n
+    pid_offset = rank * n                           # each replica has its own primaries
+    ctx = karl.Context(prob)
+    prec = karl.FP32 if args.precision == "fp32" else karl.FP64
+    stream = torch.cuda.current_stream(dev)
+    pt = {"z_m": torch.from_numpy(prims.z_m).to(dev), "e_ev": torch.from_numpy(prims.e_ev).to(dev),
+          "mu": torch.from_numpy(prims.mu).to(dev),
+          "species": torch.from_numpy(prims.species).to(dev)}
+    tmpl = ctx.empty_tallies(0)
+    dt = {k: torch.zeros(v.shape, dtype=torch.float64 if v.dtype == np.float64 else torch.int64,
+                         device=dev) for k, v in tmpl.items() if k != "per_primary"}
+    pptr = {k: v.data_ptr() for k, v in pt.items()}
+    optr = {k: v.data_ptr() for k, v in dt.items()}
+
+    def step(i):
+        ctx.run_device(pptr, n, prims.n_decays, optr, seed=1000 + i, precision=prec,
+                       stream=stream.cuda_stream, pid_offset=pid_offset, timeout_s=args.timeout)
+        st = ctx.stats()
+        return st
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    coll = flights = parts = launches = 0
+    kms = []
+    ev0.record(stream)
+    for i in range(args.steps):
+        st = step(args.warmup + i)
+        coll += st.collisions[0] + st.collisions[1]
+        flights += st.flights[0] + st.flights[1]
+        parts += st.particles[0] + st.particles[1]
+        launches += st.kernel_launches
+        kms += [st.kernel_ms[0], st.kernel_ms[1]]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1000.0
+    led = dt["ledger"].cpu().numpy()
+    ok_balance = int(led[0]) + int(led[1]) == int(led[2:12].sum())
+
+    # whole-job aggregation: collisions summed, time = max over ranks
+    tot = torch.tensor([float(coll), float(flights), float(prims.n_decays * args.steps)],
+                       dtype=torch.float64, device=dev)
+    tmax = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    coll_all, flights_all, decays_all = tot.tolist()
+    tm = float(tmax.item())
+    value = coll_all / tm
+
+    # e2e: the same metric through the public API with host buffers (pinned
+    # primaries copied in, tallies read back, every step)
+    e2e = None
+    if args.e2e_steps > 0:
+        hp = {k: torch.from_numpy(getattr(prims, k) if k != "species" else prims.species)
+              .pin_memory() for k in ("z_m", "e_ev", "mu")}
+        hp["species"] = torch.from_numpy(prims.species).pin_memory()
+        hprims = karl.Primaries(n, hp["z_m"].data_ptr(), hp["e_ev"].data_ptr(),
+                                hp["mu"].data_ptr(), hp["species"].data_ptr(), prims.n_decays,
+                                pid_offset, 0)
+        host_t = ctx.empty_tallies(0)
+        del host_t["per_primary"]
+        ts = karl.Tallies()
+        for k, v in host_t.items():
+            setattr(ts, k, v.ctypes.data)
+        ts.on_device = 0
+        h2d = sum(int(v.numel() * v.element_size()) for v in hp.values())
+        d2h = sum(int(v.nbytes) for v in host_t.values())
+        ecoll = 0
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for i in range(args.e2e_steps):
+            o = ctx.opts(seed=5000 + i, precision=prec, stream=stream.cuda_stream,
+                         timeout_s=args.timeout)
+            stt = karl.karl_run(ctx.ctx, hprims, o, ts)
+            if stt != karl.OK:
+                raise RuntimeError(karl.karl_last_error(ctx.ctx))
+            s2 = ctx.stats()
+            ecoll += s2.collisions[0] + s2.collisions[1]
+        e_el = time.perf_counter() - t0
+        et = torch.tensor([float(ecoll)], dtype=torch.float64, device=dev)
+        emax = torch.tensor([e_el], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(et, op=dist.ReduceOp.SUM)
+            dist.all_reduce(emax, op=dist.ReduceOp.MAX)
+        e2e = {"value": float(et.item()) / float(emax.item()), "unit": "collision events/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    hbm, peak_kind = _peaks()
+    bpe = BYTES_PER_EVENT_FP32 if prec == karl.FP32 else BYTES_PER_EVENT_FP64
+    per_launch_events = coll / max(len(kms), 1)
+    avg_ms = sum(kms) / max(len(kms), 1)
+    achieved = bpe * per_launch_events / (avg_ms / 1000.0) / 1e9
+    line = {
+        "metric": "collision events/s", "value": value, "unit": "collision events/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * tm / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == karl.FP32 else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "decays": args.decays, "primaries_per_decay": 2,
+                   "precision": args.precision, "l2": "inputs larger than L2 (primaries 500 MB)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "primaries_per_s": decays_all / tm, "flights_per_s": flights_all / tm,
+        "collisions_per_step": coll / args.steps,
+        "transport_kernel_ms": kms,
+        "ledger_balanced": ok_balance,
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "model": f"{bpe} B per collision event (state read+write), {peak_kind} peak",
+                     "kernel": "karl::transport_kernel"},
+        "e2e": e2e,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        c, secs, nd = _oracle_sample(args.decays, args.cpu_seconds, threads)
+        line["cpu_baseline"] = {"value": c / secs, "unit": "collision events/s", "cores": threads,
+                                "kind": "oracle",
+                                "sample": f"first {nd} decays of the workload, both passes, "
+                                          f"{secs:.1f} s on {threads} threads"}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--decays", type=int, default=10_000_000)
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--timeout", type=float, default=600.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-step-s", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

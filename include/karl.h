@@ -1,0 +1,220 @@
+/*
+ * karl.h - C ABI of the GB300 (sm_103a) KARL transport hot path.
+ *
+ * KARL follows beta-decay electrons and their secondary electrons and ions
+ * through the tritium source along the magnetic-field axis (Sec. 2.1 main
+ * cycle, Fig. 1).  Each step samples a free path from the local gas density
+ * and the total cross section (Eqs. mean_free_path and distance_from_mfp),
+ * picks a channel with probability sigma_i n_i / sum_j sigma_j n_j, performs
+ * it (Sec. 3.3: elastic, ionization, excitation, clustering, recombination),
+ * spawns products, and adds to the end-spectrum, density (Sec. 2.2, Eq.
+ * target_field_density) and current (Sec. 2.3) tallies and to the
+ * recombination target fields.  All of it runs in CUDA kernels on one GPU.
+ *
+ * Conventions for every entry point:
+ *  - units are SI (m, m^-3, m^2, s, T) except energies in eV;
+ *  - the caller owns every buffer it passes; create() copies what it needs;
+ *  - no exception crosses the ABI: every error is a karl_status, and the
+ *    context stays usable after KARL_EINVAL, KARL_ETIMEOUT, KARL_ECAPACITY and
+ *    KARL_ECANCELLED;
+ *  - a context is used by one host thread at a time;
+ *  - pointers marked "host or device" are device pointers when the struct's
+ *    on_device field is 1, host pointers otherwise.
+ */
+#ifndef KARL_H
+#define KARL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct karl_ctx karl_ctx;
+
+typedef enum karl_status {
+  KARL_OK = 0,
+  KARL_EINVAL = 1,      /* invalid argument or inconsistent tables */
+  KARL_ENOMEM = 2,      /* device or pinned allocation failed */
+  KARL_ECUDA = 3,       /* CUDA runtime error (the message has the detail) */
+  KARL_ETIMEOUT = 4,    /* the transport kernel hit its time limit and stopped */
+  KARL_EOVERFLOW = 5,   /* a 64-bit tally would overflow */
+  KARL_ECAPACITY = 6,   /* particle queue too small even after regrowth */
+  KARL_ECANCELLED = 7,  /* karl_cancel() was called during the run */
+  KARL_EBUSY = 8,       /* server queue full */
+  KARL_ENOTFOUND = 9    /* unknown request id */
+} karl_status;
+
+enum { KARL_N_SPECIES = 3, KARL_N_REASONS = 8, KARL_LEDGER_LEN = 64, KARL_MAX_CHANNELS = 16 };
+
+/* tracked species (Sec. 3.8, Species: electron, T2+, T3+) */
+enum { KARL_ELECTRON = 0, KARL_T2P = 1, KARL_T3P = 2 };
+
+/* interaction kinds (Sec. 3.3) */
+enum {
+  KARL_ELASTIC = 0,        /* energy conserved in the CM frame, isotropic CM angle */
+  KARL_IONIZATION = 1,     /* E -> E - I - W, secondary electron W, ion species_out */
+  KARL_EXCITATION = 2,     /* E -> E - loss, direction unchanged */
+  KARL_CLUSTERING = 3,     /* ion -> species_out with a thermal target's energy */
+  KARL_RECOMBINATION = 4   /* impactor deleted; species_out = partner field */
+};
+
+/* termination reasons (Sec. 3.2 terminator and deletion logger) */
+enum {
+  KARL_R_EXIT0 = 0, KARL_R_EXIT1 = 1, KARL_R_CUTOFF = 2, KARL_R_CAP_COLL = 3,
+  KARL_R_CAP_TIME = 4, KARL_R_RECOMB = 5, KARL_R_CLUSTER = 6, KARL_R_STALLED = 7
+};
+
+/* ledger slots (int64).  Energies in units of 2^-24 eV; per history and in
+ * total  IN_PRIMARY + IN_THERMAL == sum(EXIT0 .. STALLED)  holds exactly, and
+ * births[s] == sum_r deaths[s][r]. */
+enum {
+  KARL_L_E_IN_PRIMARY = 0, KARL_L_E_IN_THERMAL = 1, KARL_L_E_EXIT0 = 2, KARL_L_E_EXIT1 = 3,
+  KARL_L_E_CUTOFF = 4, KARL_L_E_CAP = 5, KARL_L_E_RECOMB = 6, KARL_L_E_CLUSTER = 7,
+  KARL_L_E_LOSS_IONIZ = 8, KARL_L_E_LOSS_EXCIT = 9, KARL_L_E_LOSS_RECOIL = 10,
+  KARL_L_E_STALLED = 11,
+  KARL_L_BIRTHS = 12,        /* [3] */
+  KARL_L_DEATHS = 15,        /* [3][8] */
+  KARL_L_N_COLLISIONS = 39, KARL_L_N_FLIGHTS = 40, KARL_L_N_SPAWN_E = 41, KARL_L_N_SPAWN_ION = 42
+};
+
+/* Geometry, gas and terminator settings (copied at create).
+ * The source is a column [0, length_m] cut into n_zbins equal segments (the
+ * density-field segmentation of Sec. 2.2); the gas density is constant in
+ * each segment.  B is uniform along z, so the guiding-centre motion is
+ * exact (Sec. 3.1, drift mover) and only z and the pitch cosine are tracked. */
+typedef struct karl_geometry {
+  double length_m;             /* > 0 */
+  int32_t n_zbins;             /* 1 .. 1<<20 */
+  const double* n_seg_m3;      /* host, [n_zbins], >= 0 */
+  double area_m2;              /* face area A and segment volume A*dz, > 0 */
+  double activity_bq;          /* a of Eq. simulated_time, > 0 */
+  double e_cut_ev;             /* electrons below this energy are terminated */
+  uint32_t max_collisions;     /* terminator cap on interactions per particle */
+  double max_lifetime_s;       /* terminator cap on time alive (INFINITY = none) */
+  double gas_temperature_k;    /* thermal target for ion products */
+  int32_t n_tebins;            /* log-E bins of the time (density) tally, >= 1 */
+  int32_t n_spec_bins;         /* end-spectrum bins (one overflow bin added) */
+  double spec_bin_ev;          /* end-spectrum bin width, > 0 */
+  double species_mass_ev[KARL_N_SPECIES];   /* rest energies */
+  double target_mass_ev;       /* background gas molecule */
+} karl_geometry;
+
+/* Cross-section tables (copied at create).  sigma of channel k at energy E is
+ * linear in ln E between the log-spaced nodes e_min * (e_max/e_min)^(i/(n-1)),
+ * clamped outside, and zero for E <= loss_ev[k] (Sec. 3.3: the cross section
+ * is a one-dimensional functional of the energy). */
+typedef struct karl_xs {
+  int32_t n_energy;            /* >= 2 */
+  double e_min_ev, e_max_ev;   /* 0 < e_min < e_max */
+  int32_t n_channels;          /* 0 .. KARL_MAX_CHANNELS, selection order */
+  const int32_t* kind;         /* host, [n_channels] */
+  const int32_t* species_in;   /* host, impactor species */
+  const int32_t* species_out;  /* host, see the kinds above; -1 = none */
+  const double* loss_ev;       /* host, threshold / energy loss (>= 0) */
+  const double* sigma_m2;      /* host, [n_channels][n_energy], >= 0 */
+  double ioniz_eps_ev;         /* eps of the secondary-energy pdf 1/(1+(W/eps)^2) */
+} karl_xs;
+
+/* Primary particles (one beta electron and, with ions, one T2+ per decay,
+ * Sec. 3.5).  Primary id = pid_offset + index keys the random streams, so a
+ * run split into id ranges sums to the same tallies bit for bit. */
+typedef struct karl_primaries {
+  int64_t n;                   /* >= 0 */
+  const double* z_m;           /* host or device, [n], 0 <= z <= length */
+  const double* e_ev;          /* host or device, [n], > 0 */
+  const double* mu;            /* host or device, [n], -1 <= mu <= 1 */
+  const uint8_t* species;      /* host or device, [n] */
+  int64_t n_decays;            /* decays of the whole run: t_sim = n_decays / activity */
+  int64_t pid_offset;
+  int32_t on_device;
+} karl_primaries;
+
+/* Output tallies (caller-owned, zeroed by the run).  Layouts are row-major. */
+typedef struct karl_tallies {
+  uint64_t* spectrum;          /* [2][3][n_spec_bins+1] particles leaving at z=0 / z=L */
+  uint64_t* time_fx;           /* [3][n_zbins+2][n_tebins] time in segment, LSB 2^-50 s;
+                                  rows 0 and n_zbins+1 are the under/overflow bins */
+  uint64_t* cross_pos;         /* [3][n_zbins+1] face crossings towards +z */
+  uint64_t* cross_neg;         /* [3][n_zbins+1] face crossings towards -z */
+  uint64_t* recomb;            /* [3][n_zbins] deletions logged in each species' field */
+  int64_t* ledger;             /* [KARL_LEDGER_LEN] */
+  uint64_t* chan_count;        /* [n_channels] collisions per channel */
+  uint64_t* per_primary;       /* [n] collisions in each primary's tree, or NULL */
+  double* density;             /* [3][n_zbins] Eq. target_field_density, or NULL */
+  double* current;             /* [3][n_zbins+1] (N+ - N-)/(A t_sim), or NULL */
+  double* field;               /* [3][n_zbins][n_tebins] pass-1 densities, or NULL */
+  int32_t on_device;
+} karl_tallies;
+
+enum { KARL_FP64 = 0, KARL_FP32 = 1 };
+
+typedef struct karl_run_opts {
+  uint64_t seed;
+  int32_t n_passes;            /* 1, or 2 when recombination channels exist */
+  int32_t precision;           /* KARL_FP64 (plain) or KARL_FP32 (precision form) */
+  int32_t block_size;          /* 0 = default */
+  int32_t blocks_per_sm;       /* 0 = occupancy maximum */
+  double timeout_s;            /* kernel time limit; <= 0 = 600 s */
+  void* stream;                /* cudaStream_t, NULL = the context's own stream */
+} karl_run_opts;
+
+/* Validate and copy geometry and tables to the current CUDA device.
+ * Errors: KARL_EINVAL (any field out of range, NULL table), KARL_ENOMEM,
+ * KARL_ECUDA.  *out is NULL on error. */
+karl_status karl_create(const karl_geometry* geom, const karl_xs* xs, karl_ctx** out);
+
+/* Whole run: pass 1 (no recombination) and, if n_passes == 2, pass 2 with
+ * the target fields frozen from pass 1 (Eq. target_field_density, Sec. 3.6
+ * additive fields).  Tallies of the last pass are returned, normalised
+ * density/current from them, and the pass-1 densities as `field`.
+ * Blocks until done (the work is ordered on opts->stream).
+ * Errors: KARL_EINVAL, KARL_ENOMEM, KARL_ECUDA, KARL_ETIMEOUT, KARL_ECAPACITY,
+ * KARL_ECANCELLED; on error the tallies are unspecified. */
+karl_status karl_run(karl_ctx* ctx, const karl_primaries* prim, const karl_run_opts* opts,
+                     karl_tallies* out);
+
+/* One pass over a primary-id range, raw integer tallies only, ADDED to out
+ * (density/current/field untouched).  pass = 2 builds the target fields from
+ * field_time_in (host, [3][n_zbins+2][n_tebins], the pass-1 time tallies
+ * summed over every shard) and prim->n_decays.  This is the host-side
+ * exchange step of a run split over ranks (Sec. 3.6: additive sync). */
+karl_status karl_run_pass(karl_ctx* ctx, const karl_primaries* prim, const karl_run_opts* opts,
+                          int32_t pass, const uint64_t* field_time_in, karl_tallies* out);
+
+/* Request that a running karl_run on this context stop (thread-safe).  The
+ * kernel polls the flag; the run returns KARL_ECANCELLED. */
+void karl_cancel(karl_ctx* ctx);
+
+/* Sizes of the tally arrays (elements) for buffer allocation. */
+typedef struct karl_layout {
+  int64_t spectrum, time_fx, cross, recomb, ledger, chan_count, density, current, field;
+} karl_layout;
+karl_status karl_tally_layout(const karl_ctx* ctx, karl_layout* out);
+
+/* Statistics of the last run on this context. */
+typedef struct karl_run_stats {
+  double kernel_ms[2];         /* transport kernel time per pass (CUDA events) */
+  int64_t collisions[2];
+  int64_t flights[2];
+  int64_t particles[2];        /* particles processed (primaries + products) */
+  int32_t grid_blocks, block_size;
+  int32_t queue_capacity;
+  int64_t kernel_launches;
+} karl_run_stats;
+karl_status karl_last_stats(const karl_ctx* ctx, karl_run_stats* out);
+
+/* Free everything the context owns.  NULL is ignored. */
+void karl_destroy(karl_ctx* ctx);
+
+/* Static description of a status code. */
+const char* karl_status_string(karl_status s);
+
+/* Detail of the last error on this context (empty if none). */
+const char* karl_last_error(const karl_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KARL_H */

@@ -355,6 +355,8 @@ struct Worker {
     const int64_t ecut_q = quant_e(p->e_cut_ev);
     std::vector<double> coef((size_t)p->n_channels + 1, 0.0);
     for (;;) {
+      /* a particle without kinetic energy never moves: stalled */
+      if (P.eq <= 0) { die(P, R_STALLED, ORC_E_STALLED); return; }
       int s = P.species;
       double m = p->species_mass_ev[s];
       double e = (double)P.eq / Q_ENERGY;

@@ -1,0 +1,837 @@
+// karl_abi.cu - C ABI of the KARL transport path (declared in include/karl.h).
+//
+// Host orchestration only: argument checks, device tables, the pass sequence
+// (pass 1 without recombination, target fields, pass 2), queue regrowth, and
+// small kernels for the prefix sums of the range-add tallies and the
+// normalisation of Eq. target_field_density and the current of Sec. 2.3.
+// Every step of the transport itself runs in transport.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/karl.h"
+#include "karl_device.cuh"
+
+namespace karl {
+cudaError_t launch_transport(bool f32, const Params& P, const Ring& R, Control* ctl,
+                             const volatile int* cancel, unsigned long long timeout_ns, int grid,
+                             int block, cudaStream_t st);
+cudaError_t transport_occupancy(bool f32, int block, int* blocks_per_sm);
+}  // namespace karl
+
+using namespace karl;
+
+namespace {
+
+const double Q_TIME = 1125899906842624.0;
+const double Q_ENERGY = 16777216.0;
+const double C_LIGHT = 299792458.0;
+const double KB_EV = 8.617333262e-5;
+
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  cudaError_t ensure(size_t count) {
+    if (count <= n && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+    if (e == cudaSuccess) n = std::max<size_t>(count, 1);
+    else p = nullptr;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+}  // namespace
+
+struct karl_ctx {
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t own_stream = nullptr;
+  // copies of the inputs
+  double L = 0, dz = 0, area = 1, activity = 1, e_cut = 0, max_life = 0, kT = 0;
+  unsigned max_coll = 0;
+  int nz = 0, ntb = 1, nspec = 1;
+  double spec_bin = 1;
+  double mass[NSP] = {0, 0, 0};
+  double target_mass = 1;
+  int n_energy = 0, nch = 0;
+  double e_min = 1, e_max = 2;
+  double eps_ion = 8;
+  std::vector<double> nseg, sigma;
+  std::vector<int> kind, sin, sout;
+  std::vector<double> loss;
+  // device tables
+  DevBuf<double> d_nseg, d_colgas, d_sig, d_frate, d_fcol, d_time1;
+  DevBuf<float> d_sigf;
+  // device work buffers
+  DevBuf<double> d_pz, d_pe, d_pmu;
+  DevBuf<uint8_t> d_psp;
+  DevBuf<unsigned long long> d_spec, d_tpt, d_trg, d_xpos, d_xneg, d_recomb, d_ledger, d_chan,
+      d_pp, d_time, d_cpos, d_cneg;
+  DevBuf<double> d_density, d_current, d_field;
+  DevBuf<int> d_bad;
+  // ring
+  DevBuf<double> r_z, r_mu, r_tal;
+  DevBuf<long long> r_eq;
+  DevBuf<unsigned long long> r_node, r_pid, r_seq;
+  DevBuf<unsigned> r_ev;
+  DevBuf<uint8_t> r_sp;
+  unsigned long long ring_cap = 0;
+  Control* d_ctl = nullptr;
+  int* h_cancel = nullptr;      // pinned, mapped
+  int* d_cancel = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  karl_run_stats stats;
+  std::string err;
+};
+
+namespace {
+
+karl_status fail(karl_ctx* c, karl_status s, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return s;
+}
+
+karl_status cuda_fail(karl_ctx* c, cudaError_t e, const char* where) {
+  karl_status s = (e == cudaErrorMemoryAllocation) ? KARL_ENOMEM : KARL_ECUDA;
+  return fail(c, s, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);  \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// small kernels
+
+__global__ void k_ring_init(unsigned long long* seq, unsigned long long cap) {
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < cap;
+       i += (unsigned long long)gridDim.x * blockDim.x)
+    seq[i] = i;
+}
+
+__global__ void k_check_primaries(const double* z, const double* e, const double* mu,
+                                  const uint8_t* sp, long long n, double L, int* bad) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    bool ok = z[i] >= 0.0 && z[i] <= L && e[i] > 0.0 && e[i] < 1e12 && mu[i] >= -1.0 &&
+              mu[i] <= 1.0 && sp[i] < NSP;
+    if (!ok) atomicAdd(bad, 1);
+  }
+}
+
+// time = point adds + prefix of range adds, per (species, energy bin)
+__global__ void k_finalize_time(const unsigned long long* pt, const unsigned long long* rg,
+                                unsigned long long* out, int nz, int ntb) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= NSP * ntb) return;
+  int s = t / ntb, b = t % ntb;
+  unsigned long long acc = 0;
+  for (int row = 0; row < nz + 2; ++row) {
+    size_t i = ((size_t)s * (nz + 2) + row) * ntb + b;
+    acc += rg[i];
+    out[i] = pt[i] + acc;
+  }
+}
+
+__global__ void k_finalize_cross(const unsigned long long* rg, unsigned long long* out, int nz) {
+  int s = threadIdx.x;
+  if (s >= NSP) return;
+  unsigned long long acc = 0;
+  for (int k = 0; k <= nz; ++k) {
+    acc += rg[(size_t)s * (nz + 2) + k];
+    out[(size_t)s * (nz + 1) + k] = acc;
+  }
+}
+
+__device__ double sigma_interp(const double* sig, int n, double e_min, double e_max, double loss,
+                               double e) {
+  if (!(e > loss)) return 0.0;
+  double h = log(e_max / e_min) / (double)(n - 1);
+  double x = log(e / e_min) / h;
+  int i = (int)floor(x);
+  double f;
+  if (i < 0) { i = 0; f = 0.0; }
+  else if (i > n - 2) { i = n - 2; f = 1.0; }
+  else f = x - (double)i;
+  return (1.0 - f) * sig[i] + f * sig[i + 1];
+}
+
+struct FieldArgs {
+  int nz, ntb, n_energy, nch;
+  double tsim, vol, dz, e_min, e_max, me;
+  int kind[MAXCH], sin[MAXCH], sout[MAXCH];
+  double loss[MAXCH];
+};
+
+// Target fields of pass 2 from the pass-1 time tally (Eq. target_field_density
+// with t_sim of Eq. simulated_time).  Electron impactor: ion density.  Ion
+// impactor: sum over electron energy bins of n_e(E_b) sigma(E_b) v(E_b).
+__global__ void k_build_fields(FieldArgs A, const unsigned long long* time1, const double* sig,
+                               double* frate, double* fcol) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= A.nch * A.nz) return;
+  int k = t / A.nz, j = t % A.nz;
+  if (A.kind[k] != RECOMBINATION) return;
+  int partner = A.sout[k];
+  double acc = 0.0;
+  for (int b = 0; b < A.ntb; ++b) {
+    unsigned long long tt = time1[((size_t)partner * (A.nz + 2) + (j + 1)) * A.ntb + b];
+    double n = (double)tt / Q_TIME / (A.tsim * A.vol);
+    if (A.sin[k] == SP_E) {
+      acc += n;
+    } else {
+      double eb = A.e_min * pow(A.e_max / A.e_min, (b + 0.5) / A.ntb);
+      double x = eb / A.me;
+      double v = C_LIGHT * sqrt(x * (2.0 + x)) / (1.0 + x);
+      acc += n * sigma_interp(sig + (size_t)k * A.n_energy, A.n_energy, A.e_min, A.e_max,
+                              A.loss[k], eb) * v;
+    }
+  }
+  frate[(size_t)k * A.nz + j] = acc;
+}
+
+__global__ void k_field_columns(const double* frate, double* fcol, int nch, int nz, double dz) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nch) return;
+  double c = 0.0;
+  fcol[(size_t)k * (nz + 1)] = 0.0;
+  for (int j = 0; j < nz; ++j) {
+    c += frate[(size_t)k * nz + j] * dz;
+    fcol[(size_t)k * (nz + 1) + j + 1] = c;
+  }
+}
+
+__global__ void k_normalize(const unsigned long long* time, const unsigned long long* time1,
+                            const unsigned long long* recomb, const unsigned long long* cpos,
+                            const unsigned long long* cneg, double* density, double* current,
+                            double* field, int nz, int ntb, double tsim, double vol, double area) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < NSP * nz) {
+    int s = t / nz, j = t % nz;
+    double tsum = 0.0;
+    for (int b = 0; b < ntb; ++b) {
+      size_t idx = ((size_t)s * (nz + 2) + (j + 1)) * ntb + b;
+      tsum += (double)time[idx] / Q_TIME;
+      if (field) field[((size_t)s * nz + j) * ntb + b] = (double)time1[idx] / Q_TIME / (tsim * vol);
+    }
+    if (density) density[(size_t)s * nz + j] =
+        tsum / (tsim * vol) - (double)recomb[(size_t)s * nz + j] / vol;
+  }
+  if (t < NSP * (nz + 1) && current) {
+    current[t] = ((double)cpos[t] - (double)cneg[t]) / (area * tsim);
+  }
+}
+
+__global__ void k_accumulate(unsigned long long* dst, const unsigned long long* src, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    dst[i] += src[i];
+}
+
+int grid_for(size_t n, int block) {
+  size_t g = (n + block - 1) / block;
+  return (int)std::min<size_t>(std::max<size_t>(g, 1), 4096);
+}
+
+// ---------------------------------------------------------------------------
+// helpers
+
+bool is_fin(double x) { return std::isfinite(x); }
+
+karl_status stage_primaries(karl_ctx* ctx, const karl_primaries* pr, cudaStream_t st,
+                            const double** z, const double** e, const double** mu,
+                            const uint8_t** sp) {
+  if (pr->n == 0) {
+    *z = *e = *mu = nullptr;
+    *sp = nullptr;
+    return KARL_OK;
+  }
+  if (!pr->z_m || !pr->e_ev || !pr->mu || !pr->species)
+    return fail(ctx, KARL_EINVAL, "primaries: NULL array");
+  size_t n = (size_t)pr->n;
+  if (pr->on_device) {
+    *z = pr->z_m; *e = pr->e_ev; *mu = pr->mu; *sp = pr->species;
+  } else {
+    for (size_t i = 0; i < n; ++i) {
+      double zi = pr->z_m[i], ei = pr->e_ev[i], mi = pr->mu[i];
+      if (!(zi >= 0.0 && zi <= ctx->L) || !(ei > 0.0 && ei < 1e12) || !(mi >= -1.0 && mi <= 1.0) ||
+          pr->species[i] >= NSP)
+        return fail(ctx, KARL_EINVAL, "primary %zu out of range (z=%g e=%g mu=%g species=%d)", i,
+                    zi, ei, mi, (int)pr->species[i]);
+    }
+    CK(ctx->d_pz.ensure(n));
+    CK(ctx->d_pe.ensure(n));
+    CK(ctx->d_pmu.ensure(n));
+    CK(ctx->d_psp.ensure(n));
+    CK(cudaMemcpyAsync(ctx->d_pz.p, pr->z_m, n * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->d_pe.p, pr->e_ev, n * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->d_pmu.p, pr->mu, n * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->d_psp.p, pr->species, n, cudaMemcpyHostToDevice, st));
+    *z = ctx->d_pz.p; *e = ctx->d_pe.p; *mu = ctx->d_pmu.p; *sp = ctx->d_psp.p;
+    return KARL_OK;
+  }
+  // device primaries: check on the device
+  CK(ctx->d_bad.ensure(1));
+  CK(cudaMemsetAsync(ctx->d_bad.p, 0, sizeof(int), st));
+  k_check_primaries<<<grid_for(n, 256), 256, 0, st>>>(*z, *e, *mu, *sp, (long long)n, ctx->L,
+                                                      ctx->d_bad.p);
+  CK(cudaGetLastError());
+  ctx->stats.kernel_launches += 1;
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, ctx->d_bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (bad) return fail(ctx, KARL_EINVAL, "%d primaries out of range", bad);
+  return KARL_OK;
+}
+
+size_t n_time(const karl_ctx* c) { return (size_t)NSP * (c->nz + 2) * c->ntb; }
+size_t n_spec(const karl_ctx* c) { return (size_t)2 * NSP * (c->nspec + 1); }
+size_t n_cross_rg(const karl_ctx* c) { return (size_t)NSP * (c->nz + 2); }
+size_t n_cross(const karl_ctx* c) { return (size_t)NSP * (c->nz + 1); }
+size_t n_recomb(const karl_ctx* c) { return (size_t)NSP * c->nz; }
+
+karl_status ensure_ring(karl_ctx* ctx, unsigned long long cap) {
+  if (ctx->ring_cap >= cap) return KARL_OK;
+  size_t n = (size_t)cap;
+  CK(ctx->r_z.ensure(n));
+  CK(ctx->r_mu.ensure(n));
+  CK(ctx->r_tal.ensure(n));
+  CK(ctx->r_eq.ensure(n));
+  CK(ctx->r_node.ensure(n));
+  CK(ctx->r_pid.ensure(n));
+  CK(ctx->r_seq.ensure(n));
+  CK(ctx->r_ev.ensure(n));
+  CK(ctx->r_sp.ensure(n));
+  ctx->ring_cap = cap;
+  return KARL_OK;
+}
+
+// Fill the pass-independent part of the kernel parameters.
+void base_params(const karl_ctx* c, Params& P, const karl_run_opts* o, int pass) {
+  std::memset(&P, 0, sizeof P);
+  P.nz = c->nz;
+  P.L = c->L;
+  P.dz = c->dz;
+  P.nseg = c->d_nseg.p;
+  P.colgas = c->d_colgas.p;
+  P.n_energy = c->n_energy;
+  P.e_min = c->e_min;
+  P.log_ratio_h = std::log(c->e_max / c->e_min) / (double)(c->n_energy - 1);
+  P.sig = c->d_sig.p;
+  P.sigf = c->d_sigf.p;
+  P.nch = c->nch;
+  for (int k = 0; k < c->nch; ++k) {
+    P.ch[k].kind = c->kind[k];
+    P.ch[k].sin = c->sin[k];
+    P.ch[k].sout = c->sout[k];
+    P.ch[k].loss_q = (long long)std::floor(c->loss[k] * Q_ENERGY);
+    P.ch[k].thr_q = (long long)std::floor(c->loss[k] * Q_ENERGY);
+    P.ch[k].loss_ev = c->loss[k];
+  }
+  for (int s = 0; s < NSP; ++s) {
+    int n = 0;
+    for (int k = 0; k < c->nch; ++k) {
+      if (c->sin[k] != s) continue;
+      if (c->kind[k] == RECOMBINATION && pass != 2) continue;
+      if (n < MAXSPCH) P.sc[s][n++] = (int8_t)k;
+    }
+    P.nsc[s] = n;
+    P.mass[s] = c->mass[s];
+  }
+  P.target_mass = c->target_mass;
+  P.eps_ion = c->eps_ion;
+  P.kT = c->kT;
+  P.ecut_q = (long long)std::floor(c->e_cut * Q_ENERGY);
+  P.max_coll = c->max_coll;
+  P.max_life = c->max_life;
+  P.ntb = c->ntb;
+  P.tb_scale = c->ntb / std::log(c->e_max / c->e_min);
+  P.nspec = c->nspec;
+  P.spec_bin_q = (long long)std::llround(c->spec_bin * Q_ENERGY);
+  P.seed = o->seed;
+  P.pass = pass;
+}
+
+// One pass into the context's raw tally buffers (which are zeroed first).
+karl_status run_one_pass(karl_ctx* ctx, const karl_primaries* pr, const karl_run_opts* o,
+                         int pass, const double* pz, const double* pe, const double* pmu,
+                         const uint8_t* psp, bool per_primary, cudaStream_t st) {
+  size_t nt = n_time(ctx);
+  CK(ctx->d_spec.ensure(n_spec(ctx)));
+  CK(ctx->d_tpt.ensure(nt));
+  CK(ctx->d_trg.ensure(nt));
+  CK(ctx->d_xpos.ensure(n_cross_rg(ctx)));
+  CK(ctx->d_xneg.ensure(n_cross_rg(ctx)));
+  CK(ctx->d_recomb.ensure(n_recomb(ctx)));
+  CK(ctx->d_ledger.ensure(LEDGER));
+  CK(ctx->d_chan.ensure(MAXCH));
+  if (per_primary) CK(ctx->d_pp.ensure((size_t)std::max<int64_t>(pr->n, 1)));
+  bool f32 = o->precision == KARL_FP32;
+  int block = o->block_size > 0 ? o->block_size : 256;
+  int bps = 0;
+  CK(transport_occupancy(f32, block, &bps));
+  if (o->blocks_per_sm > 0) bps = std::min(bps, (int)o->blocks_per_sm);
+  if (bps < 1) bps = 1;
+  int grid = ctx->num_sms * bps;
+  unsigned long long cap = ctx->ring_cap ? ctx->ring_cap : (1ULL << 22);
+  double timeout = o->timeout_s > 0 ? o->timeout_s : 600.0;
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    karl_status rs = ensure_ring(ctx, cap);
+    if (rs != KARL_OK) return rs;
+    CK(cudaMemsetAsync(ctx->d_spec.p, 0, n_spec(ctx) * 8, st));
+    CK(cudaMemsetAsync(ctx->d_tpt.p, 0, nt * 8, st));
+    CK(cudaMemsetAsync(ctx->d_trg.p, 0, nt * 8, st));
+    CK(cudaMemsetAsync(ctx->d_xpos.p, 0, n_cross_rg(ctx) * 8, st));
+    CK(cudaMemsetAsync(ctx->d_xneg.p, 0, n_cross_rg(ctx) * 8, st));
+    CK(cudaMemsetAsync(ctx->d_recomb.p, 0, n_recomb(ctx) * 8, st));
+    CK(cudaMemsetAsync(ctx->d_ledger.p, 0, LEDGER * 8, st));
+    CK(cudaMemsetAsync(ctx->d_chan.p, 0, MAXCH * 8, st));
+    if (per_primary) CK(cudaMemsetAsync(ctx->d_pp.p, 0, (size_t)std::max<int64_t>(pr->n, 1) * 8, st));
+    CK(cudaMemsetAsync(ctx->d_ctl, 0, sizeof(Control), st));
+    k_ring_init<<<grid_for((size_t)ctx->ring_cap, 256), 256, 0, st>>>(ctx->r_seq.p, ctx->ring_cap);
+    CK(cudaGetLastError());
+    ctx->stats.kernel_launches += 1;
+
+    Params P;
+    base_params(ctx, P, o, pass);
+    if (pass == 2) {
+      for (int k = 0; k < ctx->nch; ++k) {
+        if (ctx->kind[k] != RECOMBINATION) continue;
+        P.frate[k] = ctx->d_frate.p + (size_t)k * ctx->nz;
+        P.fcol[k] = ctx->d_fcol.p + (size_t)k * (ctx->nz + 1);
+      }
+    }
+    P.pid_offset = pr->pid_offset;
+    P.n_prim = pr->n;
+    P.pz = pz; P.pe = pe; P.pmu = pmu; P.psp = psp;
+    P.spectrum = ctx->d_spec.p;
+    P.time_pt = ctx->d_tpt.p;
+    P.time_rg = ctx->d_trg.p;
+    P.xpos_rg = ctx->d_xpos.p;
+    P.xneg_rg = ctx->d_xneg.p;
+    P.recomb = ctx->d_recomb.p;
+    P.ledger = ctx->d_ledger.p;
+    P.chan_count = ctx->d_chan.p;
+    P.per_primary = per_primary ? ctx->d_pp.p : nullptr;
+
+    Ring R;
+    R.z = ctx->r_z.p; R.eq = ctx->r_eq.p; R.mu = ctx->r_mu.p; R.node = ctx->r_node.p;
+    R.tal = ctx->r_tal.p; R.pid = ctx->r_pid.p; R.ev = ctx->r_ev.p; R.sp = ctx->r_sp.p;
+    R.seq = ctx->r_seq.p; R.cap = ctx->ring_cap; R.mask = ctx->ring_cap - 1;
+
+    *ctx->h_cancel = 0;
+    CK(cudaEventRecord(ctx->ev0, st));
+    CK(launch_transport(f32, P, R, ctx->d_ctl, ctx->d_cancel,
+                        (unsigned long long)(timeout * 1e9), grid, block, st));
+    CK(cudaEventRecord(ctx->ev1, st));
+    Control hc;
+    CK(cudaMemcpyAsync(&hc, ctx->d_ctl, sizeof hc, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    int pi = pass - 1;
+    ctx->stats.kernel_ms[pi] = ms;
+    ctx->stats.particles[pi] = (int64_t)hc.particles;
+    ctx->stats.grid_blocks = grid;
+    ctx->stats.block_size = block;
+    ctx->stats.queue_capacity = (int32_t)std::min<unsigned long long>(ctx->ring_cap, 0x7fffffff);
+    ctx->stats.kernel_launches += 1;
+    if (hc.error == ERR_CAPACITY) {       // ring too small: grow and rerun the pass
+      cap = ctx->ring_cap * 4;
+      continue;
+    }
+    if (hc.error == ERR_TIMEOUT) return fail(ctx, KARL_ETIMEOUT, "transport kernel timed out");
+    if (hc.error == ERR_CANCELLED) return fail(ctx, KARL_ECANCELLED, "run cancelled");
+    if (hc.error != 0) return fail(ctx, KARL_ECUDA, "transport kernel error %d", hc.error);
+    long long led[LEDGER];
+    CK(cudaMemcpy(led, ctx->d_ledger.p, sizeof led, cudaMemcpyDeviceToHost));
+    ctx->stats.collisions[pi] = led[L_N_COLL];
+    ctx->stats.flights[pi] = led[L_N_FLIGHT];
+    // finalize range adds
+    CK(ctx->d_time.ensure(nt));
+    CK(ctx->d_cpos.ensure(n_cross(ctx)));
+    CK(ctx->d_cneg.ensure(n_cross(ctx)));
+    k_finalize_time<<<grid_for((size_t)NSP * ctx->ntb, 64), 64, 0, st>>>(
+        ctx->d_tpt.p, ctx->d_trg.p, ctx->d_time.p, ctx->nz, ctx->ntb);
+    k_finalize_cross<<<1, 32, 0, st>>>(ctx->d_xpos.p, ctx->d_cpos.p, ctx->nz);
+    k_finalize_cross<<<1, 32, 0, st>>>(ctx->d_xneg.p, ctx->d_cneg.p, ctx->nz);
+    CK(cudaGetLastError());
+    ctx->stats.kernel_launches += 3;
+    return KARL_OK;
+  }
+  return fail(ctx, KARL_ECAPACITY, "particle ring overflow at capacity %llu",
+              (unsigned long long)ctx->ring_cap);
+}
+
+karl_status build_fields(karl_ctx* ctx, const unsigned long long* d_time1, int64_t n_decays,
+                         cudaStream_t st) {
+  FieldArgs A;
+  std::memset(&A, 0, sizeof A);
+  A.nz = ctx->nz;
+  A.ntb = ctx->ntb;
+  A.n_energy = ctx->n_energy;
+  A.nch = ctx->nch;
+  A.tsim = (double)n_decays / ctx->activity;
+  A.vol = ctx->dz * ctx->area;
+  A.dz = ctx->dz;
+  A.e_min = ctx->e_min;
+  A.e_max = ctx->e_max;
+  A.me = ctx->mass[SP_E];
+  for (int k = 0; k < ctx->nch; ++k) {
+    A.kind[k] = ctx->kind[k];
+    A.sin[k] = ctx->sin[k];
+    A.sout[k] = ctx->sout[k];
+    A.loss[k] = ctx->loss[k];
+  }
+  size_t nk = (size_t)std::max(ctx->nch, 1);
+  CK(ctx->d_frate.ensure(nk * ctx->nz));
+  CK(ctx->d_fcol.ensure(nk * (ctx->nz + 1)));
+  CK(cudaMemsetAsync(ctx->d_frate.p, 0, nk * ctx->nz * 8, st));
+  k_build_fields<<<grid_for((size_t)ctx->nch * ctx->nz, 256), 256, 0, st>>>(
+      A, d_time1, ctx->d_sig.p, ctx->d_frate.p, ctx->d_fcol.p);
+  k_field_columns<<<1, 32, 0, st>>>(ctx->d_frate.p, ctx->d_fcol.p, ctx->nch, ctx->nz, ctx->dz);
+  CK(cudaGetLastError());
+  ctx->stats.kernel_launches += 2;
+  return KARL_OK;
+}
+
+bool has_recombination(const karl_ctx* c) {
+  for (int k = 0; k < c->nch; ++k)
+    if (c->kind[k] == RECOMBINATION) return true;
+  return false;
+}
+
+karl_status copy_out(karl_ctx* ctx, void* dst, const void* src, size_t bytes, bool dst_dev,
+                     cudaStream_t st) {
+  if (!dst || bytes == 0) return KARL_OK;
+  CK(cudaMemcpyAsync(dst, src, bytes, dst_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     st));
+  return KARL_OK;
+}
+
+karl_status check_opts(karl_ctx* ctx, const karl_run_opts* o) {
+  if (!o) return fail(ctx, KARL_EINVAL, "opts is NULL");
+  if (o->precision != KARL_FP64 && o->precision != KARL_FP32)
+    return fail(ctx, KARL_EINVAL, "precision must be KARL_FP64 or KARL_FP32");
+  if (o->block_size != 0 && (o->block_size < 32 || o->block_size > 256 || o->block_size % 32))
+    return fail(ctx, KARL_EINVAL, "block_size must be a multiple of 32 in [32, 256]");
+  return KARL_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+
+extern "C" {
+
+const char* karl_status_string(karl_status s) {
+  switch (s) {
+    case KARL_OK: return "ok";
+    case KARL_EINVAL: return "invalid argument";
+    case KARL_ENOMEM: return "out of memory";
+    case KARL_ECUDA: return "CUDA error";
+    case KARL_ETIMEOUT: return "timed out";
+    case KARL_EOVERFLOW: return "tally overflow";
+    case KARL_ECAPACITY: return "particle queue capacity exceeded";
+    case KARL_ECANCELLED: return "cancelled";
+    case KARL_EBUSY: return "busy";
+    case KARL_ENOTFOUND: return "not found";
+  }
+  return "unknown status";
+}
+
+const char* karl_last_error(const karl_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+karl_status karl_create(const karl_geometry* g, const karl_xs* x, karl_ctx** out) {
+  if (!out) return KARL_EINVAL;
+  *out = nullptr;
+  if (!g || !x) return KARL_EINVAL;
+  if (!(g->length_m > 0) || !is_fin(g->length_m) || g->n_zbins < 1 || g->n_zbins > (1 << 20) ||
+      !g->n_seg_m3 || !(g->area_m2 > 0) || !(g->activity_bq > 0) || !(g->e_cut_ev >= 0) ||
+      !(g->max_lifetime_s > 0) || !(g->gas_temperature_k >= 0) || g->n_tebins < 1 ||
+      g->n_tebins > 4096 || g->n_spec_bins < 1 || g->n_spec_bins > (1 << 24) ||
+      !(g->spec_bin_ev > 0) || !(g->target_mass_ev > 0))
+    return KARL_EINVAL;
+  for (int s = 0; s < NSP; ++s)
+    if (!(g->species_mass_ev[s] > 0)) return KARL_EINVAL;
+  for (int j = 0; j < g->n_zbins; ++j)
+    if (!(g->n_seg_m3[j] >= 0) || !is_fin(g->n_seg_m3[j])) return KARL_EINVAL;
+  if (x->n_energy < 2 || !(x->e_min_ev > 0) || !(x->e_max_ev > x->e_min_ev) ||
+      x->n_channels < 0 || x->n_channels > KARL_MAX_CHANNELS || !(x->ioniz_eps_ev > 0))
+    return KARL_EINVAL;
+  if (x->n_channels > 0 &&
+      (!x->kind || !x->species_in || !x->species_out || !x->loss_ev || !x->sigma_m2))
+    return KARL_EINVAL;
+  int per_sp[NSP] = {0, 0, 0}, rec_sp[NSP] = {0, 0, 0};
+  for (int k = 0; k < x->n_channels; ++k) {
+    int kd = x->kind[k], si = x->species_in[k], so = x->species_out[k];
+    if (kd < 0 || kd > RECOMBINATION || si < 0 || si >= NSP || so < -1 || so >= NSP ||
+        !(x->loss_ev[k] >= 0) || !is_fin(x->loss_ev[k]))
+      return KARL_EINVAL;
+    if ((kd == CLUSTERING || kd == RECOMBINATION) && so < 0) return KARL_EINVAL;
+    if (kd == RECOMBINATION && si != SP_E && so != SP_E) return KARL_EINVAL;
+    if (kd == RECOMBINATION && si == SP_E && so == SP_E) return KARL_EINVAL;
+    per_sp[si]++;
+    if (kd == RECOMBINATION) rec_sp[si]++;
+    for (int i = 0; i < x->n_energy; ++i) {
+      double v = x->sigma_m2[(size_t)k * x->n_energy + i];
+      if (!(v >= 0) || !is_fin(v)) return KARL_EINVAL;
+    }
+  }
+  for (int s = 0; s < NSP; ++s)
+    if (per_sp[s] > MAXSPCH || rec_sp[s] > 2) return KARL_EINVAL;
+
+  karl_ctx* ctx = new (std::nothrow) karl_ctx();
+  if (!ctx) return KARL_ENOMEM;
+  std::memset(&ctx->stats, 0, sizeof ctx->stats);
+  auto bail = [&](karl_status s) {
+    karl_destroy(ctx);
+    return s;
+  };
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(KARL_ECUDA);
+  if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device) !=
+      cudaSuccess)
+    return bail(KARL_ECUDA);
+  ctx->L = g->length_m;
+  ctx->nz = g->n_zbins;
+  ctx->dz = g->length_m / g->n_zbins;
+  ctx->area = g->area_m2;
+  ctx->activity = g->activity_bq;
+  ctx->e_cut = g->e_cut_ev;
+  ctx->max_coll = g->max_collisions;
+  ctx->max_life = g->max_lifetime_s;
+  ctx->kT = KB_EV * g->gas_temperature_k;
+  ctx->ntb = g->n_tebins;
+  ctx->nspec = g->n_spec_bins;
+  ctx->spec_bin = g->spec_bin_ev;
+  for (int s = 0; s < NSP; ++s) ctx->mass[s] = g->species_mass_ev[s];
+  ctx->target_mass = g->target_mass_ev;
+  ctx->n_energy = x->n_energy;
+  ctx->e_min = x->e_min_ev;
+  ctx->e_max = x->e_max_ev;
+  ctx->nch = x->n_channels;
+  ctx->eps_ion = x->ioniz_eps_ev;
+  try {
+    ctx->nseg.assign(g->n_seg_m3, g->n_seg_m3 + g->n_zbins);
+    for (int k = 0; k < x->n_channels; ++k) {
+      ctx->kind.push_back(x->kind[k]);
+      ctx->sin.push_back(x->species_in[k]);
+      ctx->sout.push_back(x->species_out[k]);
+      ctx->loss.push_back(x->loss_ev[k]);
+    }
+    ctx->sigma.assign(x->sigma_m2, x->sigma_m2 + (size_t)x->n_channels * x->n_energy);
+  } catch (...) {
+    return bail(KARL_ENOMEM);
+  }
+  // gas column to each face
+  std::vector<double> col(ctx->nz + 1, 0.0);
+  for (int j = 0; j < ctx->nz; ++j) col[j + 1] = col[j] + ctx->nseg[j] * ctx->dz;
+  std::vector<float> sigf(ctx->sigma.begin(), ctx->sigma.end());
+  size_t nsig = std::max<size_t>(ctx->sigma.size(), 1);
+  if (ctx->d_nseg.ensure(ctx->nz) || ctx->d_colgas.ensure(ctx->nz + 1) ||
+      ctx->d_sig.ensure(nsig) || ctx->d_sigf.ensure(nsig) || ctx->d_ledger.ensure(LEDGER))
+    return bail(KARL_ENOMEM);
+  if (cudaMemcpy(ctx->d_nseg.p, ctx->nseg.data(), ctx->nz * 8, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(ctx->d_colgas.p, col.data(), (ctx->nz + 1) * 8, cudaMemcpyHostToDevice) ||
+      (ctx->sigma.size() &&
+       (cudaMemcpy(ctx->d_sig.p, ctx->sigma.data(), ctx->sigma.size() * 8, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(ctx->d_sigf.p, sigf.data(), sigf.size() * 4, cudaMemcpyHostToDevice))))
+    return bail(KARL_ECUDA);
+  if (cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) ||
+      cudaMalloc(&ctx->d_ctl, sizeof(Control)) ||
+      cudaHostAlloc(&ctx->h_cancel, sizeof(int), cudaHostAllocMapped) ||
+      cudaHostGetDevicePointer(&ctx->d_cancel, ctx->h_cancel, 0) ||
+      cudaEventCreate(&ctx->ev0) || cudaEventCreate(&ctx->ev1))
+    return bail(KARL_ECUDA);
+  *ctx->h_cancel = 0;
+  *out = ctx;
+  return KARL_OK;
+}
+
+void karl_cancel(karl_ctx* ctx) {
+  if (ctx && ctx->h_cancel) *(volatile int*)ctx->h_cancel = 1;
+}
+
+karl_status karl_tally_layout(const karl_ctx* c, karl_layout* o) {
+  if (!c || !o) return KARL_EINVAL;
+  o->spectrum = (int64_t)n_spec(c);
+  o->time_fx = (int64_t)n_time(c);
+  o->cross = (int64_t)n_cross(c);
+  o->recomb = (int64_t)n_recomb(c);
+  o->ledger = LEDGER;
+  o->chan_count = c->nch;
+  o->density = (int64_t)NSP * c->nz;
+  o->current = (int64_t)n_cross(c);
+  o->field = (int64_t)NSP * c->nz * c->ntb;
+  return KARL_OK;
+}
+
+karl_status karl_last_stats(const karl_ctx* c, karl_run_stats* o) {
+  if (!c || !o) return KARL_EINVAL;
+  *o = c->stats;
+  return KARL_OK;
+}
+
+karl_status karl_run_pass(karl_ctx* ctx, const karl_primaries* pr, const karl_run_opts* o,
+                          int32_t pass, const uint64_t* field_time_in, karl_tallies* out) {
+  if (!ctx) return KARL_EINVAL;
+  ctx->err.clear();
+  if (!pr || !out || pr->n < 0) return fail(ctx, KARL_EINVAL, "NULL argument or n < 0");
+  karl_status s = check_opts(ctx, o);
+  if (s) return s;
+  if (pass != 1 && pass != 2) return fail(ctx, KARL_EINVAL, "pass must be 1 or 2");
+  if (pass == 2 && !field_time_in) return fail(ctx, KARL_EINVAL, "pass 2 needs field_time_in");
+  if (pass == 2 && !(pr->n_decays > 0)) return fail(ctx, KARL_EINVAL, "n_decays must be > 0");
+  if (!out->spectrum || !out->time_fx || !out->cross_pos || !out->cross_neg || !out->recomb ||
+      !out->ledger || (ctx->nch > 0 && !out->chan_count))
+    return fail(ctx, KARL_EINVAL, "tally buffer is NULL");
+  cudaStream_t st = o->stream ? (cudaStream_t)o->stream : ctx->own_stream;
+  const double *pz, *pe, *pmu;
+  const uint8_t* psp;
+  ctx->stats.kernel_launches = 0;
+  s = stage_primaries(ctx, pr, st, &pz, &pe, &pmu, &psp);
+  if (s) return s;
+  if (pass == 2) {
+    CK(ctx->d_time1.ensure(n_time(ctx)));
+    CK(cudaMemcpyAsync(ctx->d_time1.p, field_time_in, n_time(ctx) * 8, cudaMemcpyHostToDevice, st));
+    s = build_fields(ctx, (const unsigned long long*)ctx->d_time1.p, pr->n_decays, st);
+    if (s) return s;
+  }
+  bool pp = out->per_primary != nullptr && pr->n > 0;
+  s = run_one_pass(ctx, pr, o, pass, pz, pe, pmu, psp, pp, st);
+  if (s) return s;
+  // add raw tallies into the caller's buffers
+  struct Item { void* dst; const void* src; size_t n; };
+  Item items[] = {
+      {out->spectrum, ctx->d_spec.p, n_spec(ctx)}, {out->time_fx, ctx->d_time.p, n_time(ctx)},
+      {out->cross_pos, ctx->d_cpos.p, n_cross(ctx)}, {out->cross_neg, ctx->d_cneg.p, n_cross(ctx)},
+      {out->recomb, ctx->d_recomb.p, n_recomb(ctx)}, {out->ledger, ctx->d_ledger.p, (size_t)LEDGER},
+      {out->chan_count, ctx->d_chan.p, (size_t)ctx->nch},
+      {pp ? out->per_primary : nullptr, ctx->d_pp.p, (size_t)pr->n}};
+  for (const Item& it : items) {
+    if (!it.dst || it.n == 0) continue;
+    if (out->on_device) {
+      k_accumulate<<<grid_for(it.n, 256), 256, 0, st>>>((unsigned long long*)it.dst,
+                                                         (const unsigned long long*)it.src, it.n);
+      CK(cudaGetLastError());
+      ctx->stats.kernel_launches += 1;
+    } else {
+      std::vector<unsigned long long> tmp(it.n);
+      CK(cudaMemcpyAsync(tmp.data(), it.src, it.n * 8, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      unsigned long long* d = (unsigned long long*)it.dst;
+      for (size_t i = 0; i < it.n; ++i) d[i] += tmp[i];
+    }
+  }
+  CK(cudaStreamSynchronize(st));
+  return KARL_OK;
+}
+
+karl_status karl_run(karl_ctx* ctx, const karl_primaries* pr, const karl_run_opts* o,
+                     karl_tallies* out) {
+  if (!ctx) return KARL_EINVAL;
+  ctx->err.clear();
+  if (!pr || !out || pr->n < 0) return fail(ctx, KARL_EINVAL, "NULL argument or n < 0");
+  karl_status s = check_opts(ctx, o);
+  if (s) return s;
+  if (o->n_passes != 1 && o->n_passes != 2) return fail(ctx, KARL_EINVAL, "n_passes must be 1 or 2");
+  if (!(pr->n_decays > 0)) return fail(ctx, KARL_EINVAL, "n_decays must be > 0");
+  if (!out->spectrum || !out->time_fx || !out->cross_pos || !out->cross_neg || !out->recomb ||
+      !out->ledger || (ctx->nch > 0 && !out->chan_count))
+    return fail(ctx, KARL_EINVAL, "tally buffer is NULL");
+  cudaStream_t st = o->stream ? (cudaStream_t)o->stream : ctx->own_stream;
+  const double *pz, *pe, *pmu;
+  const uint8_t* psp;
+  std::memset(ctx->stats.kernel_ms, 0, sizeof ctx->stats.kernel_ms);
+  ctx->stats.kernel_launches = 0;
+  s = stage_primaries(ctx, pr, st, &pz, &pe, &pmu, &psp);
+  if (s) return s;
+  bool pp = out->per_primary != nullptr && pr->n > 0;
+  s = run_one_pass(ctx, pr, o, 1, pz, pe, pmu, psp, pp, st);
+  if (s) return s;
+  size_t nt = n_time(ctx);
+  CK(ctx->d_time1.ensure(nt));
+  CK(cudaMemcpyAsync(ctx->d_time1.p, ctx->d_time.p, nt * 8, cudaMemcpyDeviceToDevice, st));
+  if (o->n_passes == 2 && has_recombination(ctx)) {
+    s = build_fields(ctx, (const unsigned long long*)ctx->d_time1.p, pr->n_decays, st);
+    if (s) return s;
+    s = run_one_pass(ctx, pr, o, 2, pz, pe, pmu, psp, pp, st);
+    if (s) return s;
+  }
+  // normalisation (Eq. target_field_density, Eq. simulated_time, Sec. 2.3)
+  double tsim = (double)pr->n_decays / ctx->activity;
+  double vol = ctx->dz * ctx->area;
+  CK(ctx->d_density.ensure((size_t)NSP * ctx->nz));
+  CK(ctx->d_current.ensure(n_cross(ctx)));
+  CK(ctx->d_field.ensure((size_t)NSP * ctx->nz * ctx->ntb));
+  k_normalize<<<grid_for(n_cross(ctx), 256), 256, 0, st>>>(
+      ctx->d_time.p, (const unsigned long long*)ctx->d_time1.p, ctx->d_recomb.p, ctx->d_cpos.p,
+      ctx->d_cneg.p, ctx->d_density.p, ctx->d_current.p, ctx->d_field.p, ctx->nz, ctx->ntb, tsim,
+      vol, ctx->area);
+  CK(cudaGetLastError());
+  ctx->stats.kernel_launches += 1;
+  bool dev = out->on_device != 0;
+  if ((s = copy_out(ctx, out->spectrum, ctx->d_spec.p, n_spec(ctx) * 8, dev, st)) ||
+      (s = copy_out(ctx, out->time_fx, ctx->d_time.p, nt * 8, dev, st)) ||
+      (s = copy_out(ctx, out->cross_pos, ctx->d_cpos.p, n_cross(ctx) * 8, dev, st)) ||
+      (s = copy_out(ctx, out->cross_neg, ctx->d_cneg.p, n_cross(ctx) * 8, dev, st)) ||
+      (s = copy_out(ctx, out->recomb, ctx->d_recomb.p, n_recomb(ctx) * 8, dev, st)) ||
+      (s = copy_out(ctx, out->ledger, ctx->d_ledger.p, LEDGER * 8, dev, st)) ||
+      (s = copy_out(ctx, out->chan_count, ctx->d_chan.p, (size_t)ctx->nch * 8, dev, st)) ||
+      (s = copy_out(ctx, pp ? out->per_primary : nullptr, ctx->d_pp.p, (size_t)pr->n * 8, dev, st)) ||
+      (s = copy_out(ctx, out->density, ctx->d_density.p, (size_t)NSP * ctx->nz * 8, dev, st)) ||
+      (s = copy_out(ctx, out->current, ctx->d_current.p, n_cross(ctx) * 8, dev, st)) ||
+      (s = copy_out(ctx, out->field, ctx->d_field.p, (size_t)NSP * ctx->nz * ctx->ntb * 8, dev, st)))
+    return s;
+  CK(cudaStreamSynchronize(st));
+  return KARL_OK;
+}
+
+void karl_destroy(karl_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->own_stream) cudaStreamSynchronize(ctx->own_stream);
+  ctx->d_nseg.release(); ctx->d_colgas.release(); ctx->d_sig.release(); ctx->d_sigf.release();
+  ctx->d_frate.release(); ctx->d_fcol.release(); ctx->d_time1.release();
+  ctx->d_pz.release(); ctx->d_pe.release(); ctx->d_pmu.release(); ctx->d_psp.release();
+  ctx->d_spec.release(); ctx->d_tpt.release(); ctx->d_trg.release(); ctx->d_xpos.release();
+  ctx->d_xneg.release(); ctx->d_recomb.release(); ctx->d_ledger.release(); ctx->d_chan.release();
+  ctx->d_pp.release(); ctx->d_time.release(); ctx->d_cpos.release(); ctx->d_cneg.release();
+  ctx->d_density.release(); ctx->d_current.release(); ctx->d_field.release(); ctx->d_bad.release();
+  ctx->r_z.release(); ctx->r_mu.release(); ctx->r_tal.release(); ctx->r_eq.release();
+  ctx->r_node.release(); ctx->r_pid.release(); ctx->r_seq.release(); ctx->r_ev.release();
+  ctx->r_sp.release();
+  if (ctx->d_ctl) cudaFree(ctx->d_ctl);
+  if (ctx->h_cancel) cudaFreeHost(ctx->h_cancel);
+  if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+  if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+  delete ctx;
+}
+
+}  // extern "C"

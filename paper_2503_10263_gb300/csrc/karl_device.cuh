@@ -1,0 +1,192 @@
+// karl_device.cuh - device-side types and helpers of the KARL transport path.
+//
+// Random numbers: Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
+// numbers: as easy as 1, 2, 3", SC'11), keyed by (seed, primary id) with the
+// counter (event index, lineage id, pass << 8 | domain, sub-index).  Streams
+// are therefore independent of scheduling order, batch mix and grid shape.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace karl {
+
+constexpr int NSP = 3;            // e-, T2+, T3+
+constexpr int MAXCH = 16;         // channels in the tables
+constexpr int MAXSPCH = 10;       // active channels of one species
+constexpr int LEDGER = 64;
+constexpr int NREASON = 8;
+
+enum { ELASTIC = 0, IONIZATION = 1, EXCITATION = 2, CLUSTERING = 3, RECOMBINATION = 4 };
+enum { SP_E = 0 };
+enum { R_EXIT0 = 0, R_EXIT1 = 1, R_CUTOFF = 2, R_CAP_COLL = 3, R_CAP_TIME = 4,
+       R_RECOMB = 5, R_CLUSTER = 6, R_STALLED = 7 };
+enum { L_E_IN_PRIMARY = 0, L_E_IN_THERMAL = 1, L_E_EXIT0 = 2, L_E_EXIT1 = 3, L_E_CUTOFF = 4,
+       L_E_CAP = 5, L_E_RECOMB = 6, L_E_CLUSTER = 7, L_LOSS_IONIZ = 8, L_LOSS_EXCIT = 9,
+       L_LOSS_RECOIL = 10, L_E_STALLED = 11, L_BIRTHS = 12, L_DEATHS = 15, L_N_COLL = 39,
+       L_N_FLIGHT = 40, L_N_SPAWN_E = 41, L_N_SPAWN_ION = 42 };
+enum { DOM_EVENT = 0, DOM_ION_BIRTH = 1, DOM_CLUSTER = 2 };
+enum { ERR_NONE = 0, ERR_TIMEOUT = 4, ERR_CAPACITY = 6, ERR_CANCELLED = 7 };
+
+struct ChanDev {
+  int32_t kind, sin, sout, pad;
+  long long loss_q;        // loss in 2^-24 eV units (floor)
+  long long thr_q;         // channel open iff eq > thr_q  (E > loss_ev exactly)
+  double loss_ev;
+};
+
+// Everything one pass of the transport kernel reads.  Passed by value.
+struct Params {
+  // geometry and gas (Sec. 2.2 segmentation)
+  int nz;
+  double L, dz;
+  const double* nseg;      // [nz] gas density per segment
+  const double* colgas;    // [nz+1] column to each face, sum_{i<k} n_i dz
+  // recombination target fields of pass 2, per channel (NULL if unused)
+  const double* frate[MAXCH];   // [nz] partner field per segment
+  const double* fcol[MAXCH];    // [nz+1] its column to each face
+  // cross sections
+  int n_energy;
+  double e_min, log_ratio_h;    // h = ln(e_max/e_min)/(n-1)
+  const double* sig;            // [nch][n_energy]
+  const float* sigf;            // same, FP32
+  int nch;
+  ChanDev ch[MAXCH];
+  int nsc[NSP];
+  int8_t sc[NSP][MAXSPCH];      // active channels per species, in selection order
+  // species and targets
+  double mass[NSP];
+  double target_mass, eps_ion, kT;
+  long long ecut_q;
+  unsigned max_coll;
+  double max_life;
+  int ntb;
+  double tb_scale;              // ntb / ln(e_max/e_min)
+  int nspec;
+  long long spec_bin_q;
+  // random streams
+  unsigned long long seed;
+  int pass;
+  long long pid_offset;
+  // primaries (device)
+  long long n_prim;
+  const double* pz;
+  const double* pe;
+  const double* pmu;
+  const uint8_t* psp;
+  // raw tallies (device)
+  unsigned long long* spectrum;   // [2][3][nspec+1]
+  unsigned long long* time_pt;    // [3][nz+2][ntb] point adds
+  unsigned long long* time_rg;    // [3][nz+2][ntb] range adds (difference form)
+  unsigned long long* xpos_rg;    // [3][nz+2] face crossings +z (difference form)
+  unsigned long long* xneg_rg;    // [3][nz+2] face crossings -z (difference form)
+  unsigned long long* recomb;     // [3][nz]
+  unsigned long long* ledger;     // [64]
+  unsigned long long* chan_count; // [nch]
+  unsigned long long* per_primary;// [n_prim] or NULL
+};
+
+// Particle ring (structure of arrays) shared by all warps of a pass.
+struct Ring {
+  double* z;
+  long long* eq;
+  double* mu;
+  unsigned long long* node;
+  double* tal;
+  unsigned long long* pid;
+  unsigned* ev;
+  uint8_t* sp;
+  unsigned long long* seq;      // per-cell sequence number (bounded MPMC ring)
+  unsigned long long cap, mask;
+};
+
+struct Control {
+  unsigned long long head;      // next ring position to consume
+  unsigned long long tail;      // next ring position to produce
+  unsigned long long prim_next; // next primary index
+  long long active;             // particles held by lanes (speculative +)
+  int error;
+  int abort;
+  unsigned long long particles; // particles started (primaries + products)
+  unsigned long long max_occupancy;
+};
+
+// ------------------------------------------------------------------------
+// Philox4x64-10
+
+__device__ __forceinline__ void philox4x64_10(unsigned long long c0, unsigned long long c1,
+                                              unsigned long long c2, unsigned long long c3,
+                                              unsigned long long k0, unsigned long long k1,
+                                              unsigned long long out[4]) {
+  const unsigned long long M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+  const unsigned long long W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    unsigned long long hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+    unsigned long long hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+    unsigned long long n0 = hi1 ^ c1 ^ k0;
+    unsigned long long n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += W0; k1 += W1;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// SplitMix64 output function (Steele, Lea, Flood 2014): lineage ids of products
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+  unsigned long long z = x + 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ unsigned long long child_node(unsigned long long parent, unsigned ev,
+                                                         unsigned slot) {
+  return mix64(mix64(parent) ^ (((unsigned long long)ev << 2) | slot));
+}
+
+// uniforms from the top bits of a 64-bit word
+__device__ __forceinline__ double u01d(unsigned long long w) {
+  return (double)(w >> 11) * (1.0 / 9007199254740992.0);
+}
+__device__ __forceinline__ double eta01d(unsigned long long w) {
+  return (double)((w >> 11) + 1) * (1.0 / 9007199254740992.0);
+}
+__device__ __forceinline__ float u01f(unsigned long long w) {
+  return (float)(unsigned)(w >> 40) * (1.0f / 16777216.0f);
+}
+__device__ __forceinline__ float eta01f(unsigned long long w) {
+  return (float)((unsigned)(w >> 40) + 1u) * (1.0f / 16777216.0f);
+}
+
+// ------------------------------------------------------------------------
+// memory-model helpers
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ long long ld_relaxed_s(const long long* p) {
+  long long v;
+  asm volatile("ld.relaxed.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_relaxed_i(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+}  // namespace karl

@@ -1,0 +1,709 @@
+// transport.cu - persistent Monte Carlo transport kernel of the KARL hot path.
+//
+// One launch runs one pass over all primaries of a run (Sec. 2.1 main cycle,
+// Fig. 1).  Every lane holds one particle in registers and performs one event
+// per loop iteration: a free flight by optical depth (Eqs. mean_free_path and
+// distance_from_mfp over the piecewise-constant column, equal in law to the
+// segment-stop mover of Sec. 3.1), the time/density and current tallies of
+// Secs. 2.2-2.3 as range adds, the terminator of Sec. 3.2, a channel chosen
+// with probability sigma_i n_i / sum_j sigma_j n_j, and its kinematics
+// (Sec. 3.3).  Products go to a device-wide ring; lanes whose particle ended
+// take the next one from the ring (products first) or from the primaries.
+// All waits are bounded by iteration counts and a wall-clock deadline, after
+// which the kernel records an error and returns.
+#include "karl_device.cuh"
+
+namespace karl {
+
+constexpr double Q_E = 16777216.0;             // 2^24 energy units per eV
+constexpr double INV_Q_E = 1.0 / 16777216.0;
+constexpr double Q_T = 1125899906842624.0;     // 2^50 time units per s
+constexpr double C_LIGHT = 299792458.0;
+constexpr unsigned FULL = 0xffffffffu;
+constexpr long long SPIN_LIMIT = 1LL << 26;    // bounded waits on ring cells
+
+template <bool F32> struct RT;
+template <> struct RT<false> {
+  using R = double;
+  static __device__ __forceinline__ R u(unsigned long long w) { return u01d(w); }
+  static __device__ __forceinline__ R eta(unsigned long long w) { return eta01d(w); }
+  static __device__ __forceinline__ R lg(R x) { return log(x); }
+  static __device__ __forceinline__ R sq(R x) { return sqrt(x); }
+  static __device__ __forceinline__ R tn(R x) { return tan(x); }
+  static __device__ __forceinline__ R atn(R x) { return atan(x); }
+  static __device__ __forceinline__ R cpi(R x) { return cospi(x); }
+  static __device__ __forceinline__ R tab(const Params& P, int k, int i) {
+    return __ldg(P.sig + (size_t)k * P.n_energy + i);
+  }
+};
+template <> struct RT<true> {
+  using R = float;
+  static __device__ __forceinline__ R u(unsigned long long w) { return u01f(w); }
+  static __device__ __forceinline__ R eta(unsigned long long w) { return eta01f(w); }
+  static __device__ __forceinline__ R lg(R x) { return logf(x); }
+  static __device__ __forceinline__ R sq(R x) { return sqrtf(x); }
+  static __device__ __forceinline__ R tn(R x) { return tanf(x); }
+  static __device__ __forceinline__ R atn(R x) { return atanf(x); }
+  static __device__ __forceinline__ R cpi(R x) { return cospif(x); }
+  static __device__ __forceinline__ R tab(const Params& P, int k, int i) {
+    return __ldg(P.sigf + (size_t)k * P.n_energy + i);
+  }
+};
+
+struct Lane {
+  double z;
+  long long eq;
+  double mu;
+  unsigned long long node;
+  double tal;
+  unsigned long long pid;
+  unsigned ev;
+  int sp;
+};
+
+__device__ __forceinline__ double face(const Params& P, int k) {
+  return k >= P.nz ? P.L : (double)k * P.dz;
+}
+__device__ __forceinline__ int segment_of(const Params& P, double z) {
+  int j = (int)floor(z / P.dz);
+  return j < 0 ? 0 : (j > P.nz - 1 ? P.nz - 1 : j);
+}
+__device__ __forceinline__ unsigned long long quant_t(double len, double inv_sz) {
+  double t = len * inv_sz;
+  return (unsigned long long)(t * Q_T + 0.5);
+}
+__device__ __forceinline__ long long quant_e(double e) { return (long long)floor(e * Q_E); }
+
+template <class R>
+__device__ __forceinline__ R speed(R e, R m) {
+  R x = e / m;
+  return (R)C_LIGHT * sqrt(x * ((R)2 + x)) / ((R)1 + x);
+}
+
+struct Shared {
+  unsigned long long ledger[LEDGER];
+  unsigned long long chan[MAXCH];
+};
+
+__device__ __forceinline__ void sadd(unsigned long long* p, long long v) {
+  atomicAdd(p, (unsigned long long)v);
+}
+
+// Range add of q over rows [a, b] (inclusive) of a difference array with row
+// stride `stride`; rows are then recovered by a prefix sum.
+__device__ __forceinline__ void range_add(unsigned long long* d, int a, int b, size_t stride,
+                                          unsigned long long q) {
+  if (a > b) return;
+  atomicAdd(d + (size_t)a * stride, q);
+  atomicAdd(d + (size_t)(b + 1) * stride, (unsigned long long)0 - q);
+}
+
+// ---------------------------------------------------------------------------
+// ring cells
+
+__device__ bool ring_put(const Ring& R, Control* ctl, unsigned long long pos, const Lane& p,
+                         unsigned long long deadline) {
+  unsigned long long* cell = R.seq + (pos & R.mask);
+  long long spins = 0;
+  while (ld_acquire(cell) != pos) {           // previous occupant not consumed yet
+    if (++spins > SPIN_LIMIT || ((spins & 1023) == 0 && globaltimer_ns() > deadline)) {
+      atomicCAS(&ctl->error, 0, ERR_CAPACITY);
+      atomicExch(&ctl->abort, 1);
+      return false;
+    }
+    __nanosleep(64);
+  }
+  size_t i = pos & R.mask;
+  R.z[i] = p.z; R.eq[i] = p.eq; R.mu[i] = p.mu; R.node[i] = p.node; R.tal[i] = p.tal;
+  R.pid[i] = p.pid; R.ev[i] = p.ev; R.sp[i] = (uint8_t)p.sp;
+  st_release(cell, pos + 1);
+  return true;
+}
+
+__device__ bool ring_get(const Ring& R, Control* ctl, unsigned long long pos, Lane& p,
+                         unsigned long long deadline) {
+  unsigned long long* cell = R.seq + (pos & R.mask);
+  long long spins = 0;
+  while (ld_acquire(cell) != pos + 1) {        // producer still writing
+    if (++spins > SPIN_LIMIT || ((spins & 1023) == 0 && globaltimer_ns() > deadline)) {
+      atomicCAS(&ctl->error, 0, ERR_TIMEOUT);
+      atomicExch(&ctl->abort, 1);
+      return false;
+    }
+    __nanosleep(32);
+  }
+  size_t i = pos & R.mask;
+  p.z = R.z[i]; p.eq = R.eq[i]; p.mu = R.mu[i]; p.node = R.node[i]; p.tal = R.tal[i];
+  p.pid = R.pid[i]; p.ev = R.ev[i]; p.sp = R.sp[i];
+  st_release(cell, pos + R.cap);
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// one event of one particle
+
+struct EventOut {
+  bool alive;
+  bool child_e, child_i;
+  Lane ce, ci;
+  unsigned long long flights, colls;
+};
+
+template <bool F32>
+__device__ __forceinline__ void die(const Params& P, Shared& S, Lane& L, int reason, int slot) {
+  sadd(&S.ledger[L_DEATHS + L.sp * NREASON + reason], 1);
+  sadd(&S.ledger[slot], L.eq);
+  if (P.per_primary) atomicAdd(P.per_primary + (L.pid - (unsigned long long)P.pid_offset),
+                               (unsigned long long)L.ev);
+}
+
+template <bool F32>
+__device__ __forceinline__ void thermal(const Params& P, const unsigned long long w[4],
+                                        long long& eq, double& mu) {
+  // Maxwell-Boltzmann target: Gamma(3/2, kT) = Exp(1) + Z^2/2 (Box-Muller), isotropic
+  double c = cospi(2.0 * u01d(w[2]));
+  double e = P.kT * (-log(eta01d(w[0])) - log(eta01d(w[1])) * c * c);
+  eq = quant_e(e);
+  mu = 2.0 * u01d(w[3]) - 1.0;
+}
+
+template <bool F32>
+__device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o) {
+  using T = RT<F32>;
+  using R = typename T::R;
+  o.child_e = o.child_i = false;
+  o.alive = true;
+  if (L.eq <= 0) {                 // no kinetic energy: the particle never moves
+    die<F32>(P, S, L, R_STALLED, L_E_STALLED);
+    o.alive = false;
+    return;
+  }
+  const int s = L.sp;
+  const R m = (R)P.mass[s];
+  const R e = (R)((double)L.eq * INV_Q_E);
+  const R v = speed<R>(e, m);
+
+  unsigned long long w[4];
+  philox4x64_10((unsigned long long)L.ev, L.node,
+                ((unsigned long long)P.pass << 8) | DOM_EVENT, 0ULL, P.seed, L.pid, w);
+  const R tau = -T::lg(T::eta(w[0]));
+  o.flights += 1;
+
+  // per-flight coefficients: sigma_k(E) (gas, electron recombination) or 1/v
+  // (ion recombining with the electron field, whose rate already has sigma v)
+  const int nsc = P.nsc[s];
+  R coef[MAXSPCH];
+  R lx = T::lg(e / (R)P.e_min) / (R)P.log_ratio_h;
+  int ti = (int)floor(lx);
+  R tf;
+  if (ti < 0) { ti = 0; tf = (R)0; }
+  else if (ti > P.n_energy - 2) { ti = P.n_energy - 2; tf = (R)1; }
+  else { tf = lx - (R)ti; }
+  R gas = (R)0;
+#pragma unroll
+  for (int c = 0; c < MAXSPCH; ++c) {
+    if (c >= nsc) break;
+    const int k = P.sc[s][c];
+    const ChanDev& ch = P.ch[k];
+    R cv;
+    if (ch.kind == RECOMBINATION && s != SP_E) {
+      cv = (R)1 / v;
+    } else if (L.eq > ch.thr_q) {
+      cv = ((R)1 - tf) * T::tab(P, k, ti) + tf * T::tab(P, k, ti + 1);
+    } else {
+      cv = (R)0;
+    }
+    coef[c] = cv;
+    if (ch.kind != RECOMBINATION) gas += cv;
+  }
+  // recombination terms of this flight (at most two): coefficient and field
+  int nrec = 0;
+  double rc[2] = {0.0, 0.0};
+  const double* rcol[2] = {P.colgas, P.colgas};
+  const double* rrate[2] = {P.nseg, P.nseg};
+#pragma unroll
+  for (int c = 0; c < MAXSPCH; ++c) {
+    if (c >= nsc) break;
+    const int kk = P.sc[s][c];
+    if (P.ch[kk].kind == RECOMBINATION && nrec < 2) {
+      rc[nrec] = (double)coef[c];
+      rcol[nrec] = P.fcol[kk];
+      rrate[nrec] = P.frate[kk];
+      ++nrec;
+    }
+  }
+  // energy bin of the time tally
+  int b = 0;
+  if (P.ntb > 1) {
+    b = (int)floor(T::lg(e / (R)P.e_min) * (R)P.tb_scale);
+    b = b < 0 ? 0 : (b > P.ntb - 1 ? P.ntb - 1 : b);
+  }
+  const size_t trow = (size_t)P.ntb;                         // stride between z rows
+  const size_t tbase = (size_t)s * (P.nz + 2) * P.ntb + b;   // (s, row 0, b)
+  const size_t xbase = (size_t)s * (P.nz + 2);
+  const double gasd = (double)gas;
+
+  // G(k) = optical-depth column of the whole rate to face k
+  auto colsum = [&](int k) -> double {
+    double g = gasd * __ldg(P.colgas + k);
+    if (nrec > 0) g += rc[0] * __ldg(rcol[0] + k);
+    if (nrec > 1) g += rc[1] * __ldg(rcol[1] + k);
+    return g;
+  };
+  auto segrate = [&](int j) -> double {
+    double r = gasd * __ldg(P.nseg + j);
+    if (nrec > 0) r += rc[0] * __ldg(rrate[0] + j);
+    if (nrec > 1) r += rc[1] * __ldg(rrate[1] + j);
+    return r;
+  };
+
+  double zc;
+  int jc;
+  int exit_end = -1;
+  double tflight;
+  if (L.mu == 0.0) {
+    // no motion along z: collide in place after path tau / rate
+    jc = segment_of(P, L.z);
+    double r = 0.0;
+#pragma unroll
+    for (int c = 0; c < MAXSPCH; ++c) {
+      if (c >= nsc) break;
+      const int kk = P.sc[s][c];
+      r += (double)coef[c] * (P.ch[kk].kind == RECOMBINATION ? __ldg(P.frate[kk] + jc)
+                                                               : __ldg(P.nseg + jc));
+    }
+    if (!(r > 0.0)) {
+      die<F32>(P, S, L, R_STALLED, L_E_STALLED);
+      o.alive = false;
+      return;
+    }
+    double path = (double)tau / r;
+    tflight = path / (double)v;
+    atomicAdd(P.time_pt + tbase + (size_t)(jc + 1) * trow,
+              (unsigned long long)(tflight * Q_T + 0.5));
+    zc = L.z;
+  } else {
+    const double amu = fabs(L.mu);
+    const int j0 = segment_of(P, L.z);
+    const double f0 = face(P, j0);
+    const double dz0 = L.z - f0;
+    const double g0 = colsum(j0) + segrate(j0) * dz0;
+    const double delta = (double)tau * amu;
+    const int nz = P.nz;
+    if (L.mu > 0.0) {
+      const double target = g0 + delta;
+      if (target >= colsum(nz)) {
+        exit_end = 1;
+        zc = P.L;
+        jc = nz - 1;
+      } else {
+        int lo = j0, hi = nz;                  // G(lo) <= target < G(hi)
+        while (hi - lo > 1) {
+          int mid = (lo + hi) >> 1;
+          if (colsum(mid) <= target) lo = mid; else hi = mid;
+        }
+        jc = lo;
+        double r = segrate(jc);
+        double fj = face(P, jc);
+        zc = fj + (target - colsum(jc)) / r;
+        double fj1 = face(P, jc + 1);
+        if (zc > fj1) zc = fj1;
+        if (zc < L.z) zc = L.z;
+      }
+    } else {
+      const double target = g0 - delta;
+      if (target <= 0.0) {
+        exit_end = 0;
+        zc = 0.0;
+        jc = 0;
+      } else {
+        int lo = 0, hi = j0 + 1;               // G(lo) < target <= G(hi)
+        while (hi - lo > 1) {
+          int mid = (lo + hi) >> 1;
+          if (colsum(mid) >= target) hi = mid; else lo = mid;
+        }
+        jc = lo;
+        double r = segrate(jc);
+        double fj = face(P, jc);
+        zc = fj + (target - colsum(jc)) / r;
+        if (zc < fj) zc = fj;
+        double fj1 = face(P, jc + 1);
+        if (zc > fj1) zc = fj1;
+        if (zc > L.z) zc = L.z;
+      }
+    }
+    // time in each segment crossed (range add of the full-segment time) and
+    // the face crossings (Secs. 2.2, 2.3)
+    const double inv_sz = 1.0 / (amu * (double)v);
+    const bool ex = exit_end >= 0;
+    if (L.mu > 0.0) {
+      const int j1 = jc;
+      if (j1 == j0) {
+        atomicAdd(P.time_pt + tbase + (size_t)(j0 + 1) * trow, quant_t(fmax(zc - L.z, 0.0), inv_sz));
+      } else {
+        atomicAdd(P.time_pt + tbase + (size_t)(j0 + 1) * trow,
+                  quant_t(fmax(face(P, j0 + 1) - L.z, 0.0), inv_sz));
+        const unsigned long long qf = quant_t(P.dz, inv_sz);
+        range_add(P.time_rg + tbase, j0 + 2, j1, trow, qf);     // rows j0+1 .. j1-1 (+1 offset)
+        atomicAdd(P.time_pt + tbase + (size_t)(j1 + 1) * trow,
+                  ex ? qf : quant_t(fmax(zc - face(P, j1), 0.0), inv_sz));
+      }
+      range_add(P.xpos_rg + xbase, j0 + 1, ex ? nz : j1, 1, 1ULL);
+    } else {
+      const int j1 = jc;
+      if (j1 == j0) {
+        atomicAdd(P.time_pt + tbase + (size_t)(j0 + 1) * trow, quant_t(fmax(L.z - zc, 0.0), inv_sz));
+      } else {
+        atomicAdd(P.time_pt + tbase + (size_t)(j0 + 1) * trow,
+                  quant_t(fmax(L.z - face(P, j0), 0.0), inv_sz));
+        const unsigned long long qf = quant_t(P.dz, inv_sz);
+        range_add(P.time_rg + tbase, j1 + 2, j0, trow, qf);     // rows j1+1 .. j0-1 (+1 offset)
+        atomicAdd(P.time_pt + tbase + (size_t)(j1 + 1) * trow,
+                  ex ? qf : quant_t(fmax(face(P, j1 + 1) - zc, 0.0), inv_sz));
+      }
+      range_add(P.xneg_rg + xbase, ex ? 0 : j1 + 1, j0, 1, 1ULL);
+    }
+    tflight = fabs(zc - L.z) * inv_sz;
+  }
+  L.tal += tflight;
+  if (exit_end >= 0) {
+    long long bin = L.eq / P.spec_bin_q;
+    if (bin > P.nspec) bin = P.nspec;
+    atomicAdd(P.spectrum + ((size_t)exit_end * NSP + s) * (P.nspec + 1) + bin, 1ULL);
+    die<F32>(P, S, L, exit_end == 0 ? R_EXIT0 : R_EXIT1, exit_end == 0 ? L_E_EXIT0 : L_E_EXIT1);
+    o.alive = false;
+    return;
+  }
+  L.z = zc;
+
+  // ---- collision in segment jc ----
+  L.ev += 1;
+  o.colls += 1;
+  double rk[MAXSPCH];
+  double rtot = 0.0;
+#pragma unroll
+  for (int c = 0; c < MAXSPCH; ++c) {
+    if (c >= nsc) break;
+    const int kk = P.sc[s][c];
+    rk[c] = (double)coef[c] * (P.ch[kk].kind == RECOMBINATION ? __ldg(P.frate[kk] + jc)
+                                                                : __ldg(P.nseg + jc));
+    rtot += rk[c];
+  }
+  const double target = u01d(w[1]) * rtot;
+  int chs = -1, last = -1;
+  double cum = 0.0;
+#pragma unroll
+  for (int c = 0; c < MAXSPCH; ++c) {
+    if (c >= nsc) break;
+    if (!(rk[c] > 0.0)) continue;
+    last = c;
+    cum += rk[c];
+    if (target < cum) { chs = c; break; }
+  }
+  if (chs < 0) chs = last;
+  const int k = P.sc[s][chs];
+  sadd(&S.chan[k], 1);
+  const ChanDev ch = P.ch[k];
+  if (ch.kind == ELASTIC) {
+    // isotropic in CM, target at rest: lab energy and polar angle
+    const R g = m / (R)P.target_mass;
+    const R cchi = (R)2 * T::u(w[2]) - (R)1;
+    const R a = (R)1 + (R)2 * g * cchi + g * g;
+    const R e1 = e * a / (((R)1 + g) * ((R)1 + g));
+    const R ct = (cchi + g) / T::sq(a);
+    long long eq1 = quant_e((double)e1);
+    if (eq1 > L.eq) eq1 = L.eq;
+    sadd(&S.ledger[L_LOSS_RECOIL], L.eq - eq1);
+    L.eq = eq1;
+    const R st = T::sq(fmax((R)0, (R)1 - ct * ct));
+    const R cphi = T::cpi((R)2 * T::u(w[3]));
+    const R mu = (R)L.mu;
+    const R smu = T::sq(fmax((R)0, (R)1 - mu * mu));
+    L.mu = (double)fmin((R)1, fmax((R)-1, mu * ct + smu * st * cphi));
+  } else if (ch.kind == EXCITATION) {
+    L.eq -= ch.loss_q;
+    sadd(&S.ledger[L_LOSS_EXCIT], ch.loss_q);
+  } else if (ch.kind == IONIZATION) {
+    const long long avail = L.eq - ch.loss_q;
+    const R eps = (R)P.eps_ion;
+    const R wmax = (e - (R)ch.loss_ev) * (R)0.5;
+    const R wsec = eps * T::tn(T::u(w[2]) * T::atn(wmax / eps));
+    long long wq = quant_e((double)wsec);
+    if (wq > avail / 2) wq = avail / 2;
+    if (wq < 0) wq = 0;
+    const long long eq1 = avail - wq;
+    sadd(&S.ledger[L_LOSS_IONIZ], ch.loss_q);
+    // binary encounter: cos^2 of the polar angles are the energy fractions
+    const R c2p = avail > 0 ? (R)((double)eq1 / (double)avail) : (R)1;
+    const R c2s = avail > 0 ? (R)((double)wq / (double)avail) : (R)0;
+    const R cp = T::sq(c2p), sp = T::sq(c2s);
+    const R cphi = T::cpi((R)2 * T::u(w[3]));
+    const R mu = (R)L.mu;
+    const R smu = T::sq(fmax((R)0, (R)1 - mu * mu));
+    const R mu_p = fmin((R)1, fmax((R)-1, mu * cp + smu * sp * cphi));
+    const R mu_s = fmin((R)1, fmax((R)-1, mu * sp - smu * cp * cphi));
+    const unsigned evc = L.ev - 1;
+    // slow electron (azimuth opposite to the fast one)
+    sadd(&S.ledger[L_BIRTHS + SP_E], 1);
+    sadd(&S.ledger[L_N_SPAWN_E], 1);
+    Lane c;
+    c.z = L.z; c.eq = wq; c.mu = (double)mu_s; c.node = child_node(L.node, evc, 0);
+    c.tal = 0.0; c.pid = L.pid; c.ev = 0; c.sp = SP_E;
+    if (wq < P.ecut_q) {
+      die<F32>(P, S, c, R_CUTOFF, L_E_CUTOFF);
+    } else {
+      o.child_e = true;
+      o.ce = c;
+    }
+    // ion with a thermal target's velocity (no recoil)
+    if (ch.sout >= 0) {
+      Lane ion;
+      ion.z = L.z; ion.node = child_node(L.node, evc, 1); ion.tal = 0.0; ion.pid = L.pid;
+      ion.ev = 0; ion.sp = ch.sout;
+      unsigned long long wi[4];
+      philox4x64_10(0ULL, ion.node, ((unsigned long long)P.pass << 8) | DOM_ION_BIRTH, 0ULL,
+                    P.seed, L.pid, wi);
+      thermal<F32>(P, wi, ion.eq, ion.mu);
+      sadd(&S.ledger[L_E_IN_THERMAL], ion.eq);
+      sadd(&S.ledger[L_BIRTHS + ch.sout], 1);
+      sadd(&S.ledger[L_N_SPAWN_ION], 1);
+      o.child_i = true;
+      o.ci = ion;
+    }
+    L.eq = eq1;
+    L.mu = (double)mu_p;
+  } else if (ch.kind == CLUSTERING) {
+    die<F32>(P, S, L, R_CLUSTER, L_E_CLUSTER);
+    unsigned long long wc[4];
+    const unsigned evc = L.ev - 1;
+    philox4x64_10((unsigned long long)evc, L.node,
+                  ((unsigned long long)P.pass << 8) | DOM_CLUSTER, 0ULL, P.seed, L.pid, wc);
+    long long eqc;
+    double muc;
+    thermal<F32>(P, wc, eqc, muc);
+    L.node = child_node(L.node, evc, 2);
+    L.eq = eqc;
+    L.mu = muc;
+    L.tal = 0.0;
+    L.ev = 0;
+    L.sp = ch.sout;
+    sadd(&S.ledger[L_E_IN_THERMAL], eqc);
+    sadd(&S.ledger[L_BIRTHS + ch.sout], 1);
+    return;
+  } else {  // RECOMBINATION
+    atomicAdd(P.recomb + (size_t)ch.sout * P.nz + jc, 1ULL);
+    die<F32>(P, S, L, R_RECOMB, L_E_RECOMB);
+    o.alive = false;
+    return;
+  }
+  // ---- terminator (Sec. 3.2) ----
+  if (L.sp == SP_E && L.eq < P.ecut_q) {
+    die<F32>(P, S, L, R_CUTOFF, L_E_CUTOFF);
+    o.alive = false;
+  } else if (L.ev >= P.max_coll) {
+    die<F32>(P, S, L, R_CAP_COLL, L_E_CAP);
+    o.alive = false;
+  } else if (L.tal >= P.max_life) {
+    die<F32>(P, S, L, R_CAP_TIME, L_E_CAP);
+    o.alive = false;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// persistent kernel
+
+template <bool F32>
+__global__ void __launch_bounds__(256) transport_kernel(const Params Pk, Ring R, Control* ctl,
+                                                        const volatile int* cancel,
+                                                        unsigned long long timeout_ns) {
+  const unsigned long long deadline = globaltimer_ns() + timeout_ns;
+  __shared__ Shared S;
+  __shared__ Params SP;
+  if (threadIdx.x == 0) SP = Pk;
+  for (int i = threadIdx.x; i < LEDGER; i += blockDim.x) S.ledger[i] = 0;
+  for (int i = threadIdx.x; i < MAXCH; i += blockDim.x) S.chan[i] = 0;
+  __syncthreads();
+  const Params& P = SP;
+
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  bool has = false;
+  Lane L;
+  EventOut o;
+  o.flights = 0;
+  o.colls = 0;
+  unsigned long long started = 0;
+
+  for (long long iter = 0;; ++iter) {
+    if ((iter & 31) == 0) {
+      int stop = 0;
+      if (lane == 0) {
+        if (ld_relaxed_i(&ctl->abort)) stop = 1;
+        else if (cancel && *cancel) {
+          atomicCAS(&ctl->error, 0, ERR_CANCELLED);
+          atomicExch(&ctl->abort, 1);
+          stop = 1;
+        } else if (globaltimer_ns() > deadline) {
+          atomicCAS(&ctl->error, 0, ERR_TIMEOUT);
+          atomicExch(&ctl->abort, 1);
+          stop = 1;
+        }
+      }
+      if (__shfl_sync(FULL, stop, 0)) break;
+    }
+
+    // ---- idle lanes take work: products from the ring first, then primaries ----
+    const unsigned need = __ballot_sync(FULL, !has);
+    if (need) {
+      const int k = __popc(need);
+      unsigned long long base = 0;
+      int got = 0, src = 0;
+      if (lane == 0) {
+        atomicAdd((unsigned long long*)&ctl->active, (unsigned long long)k);
+        __threadfence();
+        unsigned long long h = ld_relaxed(&ctl->head), t = ld_relaxed(&ctl->tail);
+        for (int tries = 0; tries < 16 && h < t; ++tries) {
+          unsigned long long take = t - h < (unsigned long long)k ? t - h : (unsigned long long)k;
+          unsigned long long old = atomicCAS(&ctl->head, h, h + take);
+          if (old == h) { base = h; got = (int)take; src = 1; break; }
+          h = old;
+          t = ld_relaxed(&ctl->tail);
+        }
+        if (got == 0 && ld_relaxed(&ctl->prim_next) < (unsigned long long)P.n_prim &&
+            t - h < R.cap / 4) {
+          unsigned long long pn = atomicAdd(&ctl->prim_next, (unsigned long long)k);
+          if (pn < (unsigned long long)P.n_prim) {
+            unsigned long long left = (unsigned long long)P.n_prim - pn;
+            base = pn;
+            got = left < (unsigned long long)k ? (int)left : k;
+            src = 2;
+          }
+        }
+        if (got < k) atomicAdd((unsigned long long*)&ctl->active, (unsigned long long)(got - k));
+      }
+      base = __shfl_sync(FULL, base, 0);
+      got = __shfl_sync(FULL, got, 0);
+      src = __shfl_sync(FULL, src, 0);
+      bool born_dead = false;
+      if (!has && got > 0) {
+        const int rank = __popc(need & lt);
+        if (rank < got) {
+          const unsigned long long idx = base + rank;
+          if (src == 1) {
+            has = ring_get(R, ctl, idx, L, deadline);
+          } else {
+            L.z = P.pz[idx];
+            L.eq = quant_e(P.pe[idx]);
+            L.mu = P.pmu[idx];
+            L.sp = P.psp[idx];
+            L.node = 0;
+            L.tal = 0.0;
+            L.ev = 0;
+            L.pid = (unsigned long long)P.pid_offset + idx;
+            sadd(&S.ledger[L_E_IN_PRIMARY], L.eq);
+            sadd(&S.ledger[L_BIRTHS + L.sp], 1);
+            if (L.sp == SP_E && L.eq < P.ecut_q) {
+              die<F32>(P, S, L, R_CUTOFF, L_E_CUTOFF);
+              born_dead = true;
+            } else {
+              has = true;
+            }
+          }
+          started += 1;
+        }
+      }
+      const unsigned md = __ballot_sync(FULL, born_dead);
+      if (md && lane == 0) {
+        __threadfence();
+        atomicAdd((unsigned long long*)&ctl->active, (unsigned long long)(-(long long)__popc(md)));
+      }
+    }
+
+    const unsigned busy = __ballot_sync(FULL, has);
+    if (!busy) {
+      int done = 0;
+      if (lane == 0) {
+        long long a = ld_relaxed_s(&ctl->active);
+        __threadfence();
+        unsigned long long h = ld_relaxed(&ctl->head), t = ld_relaxed(&ctl->tail);
+        unsigned long long pn = ld_relaxed(&ctl->prim_next);
+        done = (a <= 0 && h >= t && pn >= (unsigned long long)P.n_prim);
+      }
+      if (__shfl_sync(FULL, done, 0)) break;
+      __nanosleep(256);
+      continue;
+    }
+
+    // ---- one event ----
+    o.child_e = o.child_i = false;
+    bool died = false;
+    if (has) {
+      event<F32>(P, S, L, o);
+      if (!o.alive) { has = false; died = true; }
+    }
+
+    // ---- products to the ring (one reservation per warp) ----
+    const unsigned me = __ballot_sync(FULL, o.child_e);
+    const unsigned mi = __ballot_sync(FULL, o.child_i);
+    if (me | mi) {
+      const int ne = __popc(me), ni = __popc(mi);
+      unsigned long long pos = 0;
+      if (lane == 0) {
+        pos = atomicAdd(&ctl->tail, (unsigned long long)(ne + ni));
+        unsigned long long occ = pos + ne + ni - ld_relaxed(&ctl->head);
+        atomicMax(&ctl->max_occupancy, occ);
+      }
+      pos = __shfl_sync(FULL, pos, 0);
+      if (o.child_e) ring_put(R, ctl, pos + __popc(me & lt), o.ce, deadline);
+      if (o.child_i) ring_put(R, ctl, pos + ne + __popc(mi & lt), o.ci, deadline);
+    }
+    const unsigned md = __ballot_sync(FULL, died);
+    if (md) {
+      __threadfence();
+      if (lane == 0)
+        atomicAdd((unsigned long long*)&ctl->active, (unsigned long long)(-(long long)__popc(md)));
+    }
+  }
+
+  // ---- flush per-lane and per-block counters ----
+  unsigned long long f = o.flights, c = o.colls, st = started;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    f += __shfl_down_sync(FULL, f, off);
+    c += __shfl_down_sync(FULL, c, off);
+    st += __shfl_down_sync(FULL, st, off);
+  }
+  if (lane == 0) {
+    atomicAdd(&S.ledger[L_N_FLIGHT], f);
+    atomicAdd(&S.ledger[L_N_COLL], c);
+    atomicAdd(&ctl->particles, st);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < LEDGER; i += blockDim.x)
+    if (S.ledger[i]) atomicAdd(P.ledger + i, S.ledger[i]);
+  for (int i = threadIdx.x; i < P.nch; i += blockDim.x)
+    if (S.chan[i]) atomicAdd(P.chan_count + i, S.chan[i]);
+}
+
+// ---------------------------------------------------------------------------
+// host-callable launchers (used by the C ABI in karl_abi.cu)
+
+cudaError_t launch_transport(bool f32, const Params& P, const Ring& R, Control* ctl,
+                             const volatile int* cancel, unsigned long long timeout_ns, int grid,
+                             int block, cudaStream_t st) {
+  if (f32)
+    transport_kernel<true><<<grid, block, 0, st>>>(P, R, ctl, cancel, timeout_ns);
+  else
+    transport_kernel<false><<<grid, block, 0, st>>>(P, R, ctl, cancel, timeout_ns);
+  return cudaGetLastError();
+}
+
+cudaError_t transport_occupancy(bool f32, int block, int* blocks_per_sm) {
+  if (f32)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, transport_kernel<true>,
+                                                         block, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, transport_kernel<false>,
+                                                       block, 0);
+}
+
+}  // namespace karl

@@ -1,0 +1,342 @@
+"""Thin ctypes binding of ``libkarl.so`` (C ABI in ``include/karl.h``).
+
+Argument marshalling only: every step of the transport runs in the CUDA
+library.  The module raises on import of the library if ``libkarl.so`` has
+not been built (``paper_2503_10263_gb300.build.build()``); there is no CPU
+fallback.
+
+Module-level functions carry the C names (``karl_create``, ``karl_run``,
+``karl_run_pass``, ``karl_destroy``, ...).  ``Context`` wraps them for
+problems from ``paper_2503_10263_gb300.inputs``; tallies come back as numpy
+arrays (host buffers) or are written to caller-provided device pointers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from typing import Dict, Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkarl.so")
+
+N_SPECIES = 3
+N_REASONS = 8
+LEDGER_LEN = 64
+MAX_CHANNELS = 16
+FP64, FP32 = 0, 1
+
+# status codes
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW, ECAPACITY, ECANCELLED, EBUSY, ENOTFOUND = range(10)
+
+# ledger slots
+E_IN_PRIMARY, E_IN_THERMAL, E_EXIT0, E_EXIT1, E_CUTOFF, E_CAP, E_RECOMB, E_CLUSTER, \
+    E_LOSS_IONIZ, E_LOSS_EXCIT, E_LOSS_RECOIL, E_STALLED = range(12)
+BIRTHS, DEATHS = 12, 15
+N_COLLISIONS, N_FLIGHTS, N_SPAWN_E, N_SPAWN_ION = 39, 40, 41, 42
+
+
+class KarlError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"karl status {status} ({msg})")
+        self.status = status
+
+
+class Geometry(C.Structure):
+    _fields_ = [("length_m", C.c_double), ("n_zbins", C.c_int32),
+                ("n_seg_m3", C.POINTER(C.c_double)), ("area_m2", C.c_double),
+                ("activity_bq", C.c_double), ("e_cut_ev", C.c_double),
+                ("max_collisions", C.c_uint32), ("max_lifetime_s", C.c_double),
+                ("gas_temperature_k", C.c_double), ("n_tebins", C.c_int32),
+                ("n_spec_bins", C.c_int32), ("spec_bin_ev", C.c_double),
+                ("species_mass_ev", C.c_double * 3), ("target_mass_ev", C.c_double)]
+
+
+class XS(C.Structure):
+    _fields_ = [("n_energy", C.c_int32), ("e_min_ev", C.c_double), ("e_max_ev", C.c_double),
+                ("n_channels", C.c_int32), ("kind", C.POINTER(C.c_int32)),
+                ("species_in", C.POINTER(C.c_int32)), ("species_out", C.POINTER(C.c_int32)),
+                ("loss_ev", C.POINTER(C.c_double)), ("sigma_m2", C.POINTER(C.c_double)),
+                ("ioniz_eps_ev", C.c_double)]
+
+
+class Primaries(C.Structure):
+    _fields_ = [("n", C.c_int64), ("z_m", C.c_void_p), ("e_ev", C.c_void_p), ("mu", C.c_void_p),
+                ("species", C.c_void_p), ("n_decays", C.c_int64), ("pid_offset", C.c_int64),
+                ("on_device", C.c_int32)]
+
+
+class Tallies(C.Structure):
+    _fields_ = [("spectrum", C.c_void_p), ("time_fx", C.c_void_p), ("cross_pos", C.c_void_p),
+                ("cross_neg", C.c_void_p), ("recomb", C.c_void_p), ("ledger", C.c_void_p),
+                ("chan_count", C.c_void_p), ("per_primary", C.c_void_p), ("density", C.c_void_p),
+                ("current", C.c_void_p), ("field", C.c_void_p), ("on_device", C.c_int32)]
+
+
+class RunOpts(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("n_passes", C.c_int32), ("precision", C.c_int32),
+                ("block_size", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("timeout_s", C.c_double), ("stream", C.c_void_p)]
+
+
+class Layout(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("spectrum", "time_fx", "cross", "recomb", "ledger",
+                                           "chan_count", "density", "current", "field")]
+
+
+class RunStats(C.Structure):
+    _fields_ = [("kernel_ms", C.c_double * 2), ("collisions", C.c_int64 * 2),
+                ("flights", C.c_int64 * 2), ("particles", C.c_int64 * 2),
+                ("grid_blocks", C.c_int32), ("block_size", C.c_int32),
+                ("queue_capacity", C.c_int32), ("kernel_launches", C.c_int64)]
+
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load libkarl.so; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "paper_2503_10263_gb300.build.build() (there is no CPU fallback)")
+    lib = C.CDLL(LIB_PATH)
+    P = C.POINTER
+    lib.karl_create.argtypes = [P(Geometry), P(XS), P(C.c_void_p)]
+    lib.karl_run.argtypes = [C.c_void_p, P(Primaries), P(RunOpts), P(Tallies)]
+    lib.karl_run_pass.argtypes = [C.c_void_p, P(Primaries), P(RunOpts), C.c_int32,
+                                  C.c_void_p, P(Tallies)]
+    lib.karl_destroy.argtypes = [C.c_void_p]
+    lib.karl_destroy.restype = None
+    lib.karl_cancel.argtypes = [C.c_void_p]
+    lib.karl_cancel.restype = None
+    lib.karl_status_string.argtypes = [C.c_int]
+    lib.karl_status_string.restype = C.c_char_p
+    lib.karl_last_error.argtypes = [C.c_void_p]
+    lib.karl_last_error.restype = C.c_char_p
+    lib.karl_tally_layout.argtypes = [C.c_void_p, P(Layout)]
+    lib.karl_last_stats.argtypes = [C.c_void_p, P(RunStats)]
+    for f in ("karl_create", "karl_run", "karl_run_pass", "karl_tally_layout", "karl_last_stats"):
+        getattr(lib, f).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+# ---- C-named wrappers -------------------------------------------------------
+
+def karl_status_string(status: int) -> str:
+    return load().karl_status_string(status).decode()
+
+
+def karl_create(geom: Geometry, xs: XS) -> C.c_void_p:
+    out = C.c_void_p()
+    st = load().karl_create(C.byref(geom), C.byref(xs), C.byref(out))
+    if st != OK:
+        raise KarlError(st, karl_status_string(st))
+    return out
+
+
+def karl_run(ctx, prim: Primaries, opts: RunOpts, tallies: Tallies) -> int:
+    return load().karl_run(ctx, C.byref(prim), C.byref(opts), C.byref(tallies))
+
+
+def karl_run_pass(ctx, prim: Primaries, opts: RunOpts, pass_index: int, field_time_in,
+                  tallies: Tallies) -> int:
+    return load().karl_run_pass(ctx, C.byref(prim), C.byref(opts), pass_index, field_time_in,
+                                C.byref(tallies))
+
+
+def karl_destroy(ctx) -> None:
+    load().karl_destroy(ctx)
+
+
+def karl_cancel(ctx) -> None:
+    load().karl_cancel(ctx)
+
+
+def karl_last_error(ctx) -> str:
+    return load().karl_last_error(ctx).decode()
+
+
+def karl_tally_layout(ctx) -> Layout:
+    lay = Layout()
+    st = load().karl_tally_layout(ctx, C.byref(lay))
+    if st != OK:
+        raise KarlError(st, karl_status_string(st))
+    return lay
+
+
+def karl_last_stats(ctx) -> RunStats:
+    s = RunStats()
+    load().karl_last_stats(ctx, C.byref(s))
+    return s
+
+
+# ---- problem marshalling ----------------------------------------------------
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _iptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+class Context:
+    """One problem's device context (tables on the GPU) and its runs."""
+
+    def __init__(self, prob):
+        self.prob = prob
+        self._keep = []
+        g = Geometry()
+        nseg = np.ascontiguousarray(prob.n_seg_m3, np.float64)
+        self._keep.append(nseg)
+        g.length_m = prob.length_m
+        g.n_zbins = prob.n_zbins
+        g.n_seg_m3 = _dptr(nseg)
+        g.area_m2 = prob.area_m2
+        g.activity_bq = prob.activity_bq
+        g.e_cut_ev = prob.e_cut_ev
+        g.max_collisions = min(int(prob.max_collisions), 0xFFFFFFFF)
+        g.max_lifetime_s = prob.max_lifetime_s if math.isfinite(prob.max_lifetime_s) else math.inf
+        g.gas_temperature_k = prob.gas_temperature_k
+        g.n_tebins = prob.n_tebins
+        g.n_spec_bins = prob.n_spec_bins
+        g.spec_bin_ev = prob.spec_bin_ev
+        for i in range(3):
+            g.species_mass_ev[i] = float(prob.species_mass_ev[i])
+        g.target_mass_ev = prob.target_mass_ev
+        x = XS()
+        kind = np.array([c.kind for c in prob.channels], np.int32)
+        sin = np.array([c.species_in for c in prob.channels], np.int32)
+        sout = np.array([c.species_out for c in prob.channels], np.int32)
+        loss = np.array([c.loss_ev for c in prob.channels], np.float64)
+        sig = np.ascontiguousarray(prob.sigma_matrix() if prob.channels
+                                   else np.zeros((0, prob.n_energy)), np.float64)
+        self._keep += [kind, sin, sout, loss, sig]
+        x.n_energy = prob.n_energy
+        x.e_min_ev = prob.e_min_ev
+        x.e_max_ev = prob.e_max_ev
+        x.n_channels = prob.n_channels
+        x.kind, x.species_in, x.species_out = _iptr(kind), _iptr(sin), _iptr(sout)
+        x.loss_ev, x.sigma_m2 = _dptr(loss), _dptr(sig)
+        x.ioniz_eps_ev = prob.ioniz_eps_ev
+        self.ctx = karl_create(g, x)
+        self.layout = karl_tally_layout(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            karl_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != OK:
+            raise KarlError(st, f"{karl_status_string(st)}: {karl_last_error(self.ctx)}")
+
+    def empty_tallies(self, n_primaries: int) -> Dict[str, np.ndarray]:
+        p = self.prob
+        nz, ntb = p.n_zbins, p.n_tebins
+        return {
+            "spectrum": np.zeros((2, N_SPECIES, p.n_spec_bins + 1), np.uint64),
+            "time_fx": np.zeros((N_SPECIES, nz + 2, ntb), np.uint64),
+            "cross_pos": np.zeros((N_SPECIES, nz + 1), np.uint64),
+            "cross_neg": np.zeros((N_SPECIES, nz + 1), np.uint64),
+            "recomb": np.zeros((N_SPECIES, nz), np.uint64),
+            "ledger": np.zeros(LEDGER_LEN, np.int64),
+            "chan_count": np.zeros(max(p.n_channels, 1), np.uint64),
+            "per_primary": np.zeros(max(n_primaries, 1), np.uint64),
+            "density": np.zeros((N_SPECIES, nz), np.float64),
+            "current": np.zeros((N_SPECIES, nz + 1), np.float64),
+            "field": np.zeros((N_SPECIES, nz, ntb), np.float64),
+        }
+
+    @staticmethod
+    def host_primaries(prims, pid_offset: int = 0, n_decays: Optional[int] = None):
+        z = np.ascontiguousarray(prims.z_m, np.float64)
+        e = np.ascontiguousarray(prims.e_ev, np.float64)
+        mu = np.ascontiguousarray(prims.mu, np.float64)
+        sp = np.ascontiguousarray(prims.species, np.uint8)
+        s = Primaries(prims.n, z.ctypes.data, e.ctypes.data, mu.ctypes.data, sp.ctypes.data,
+                      int(prims.n_decays if n_decays is None else n_decays), int(pid_offset), 0)
+        return s, (z, e, mu, sp)
+
+    @staticmethod
+    def host_tallies(t: Dict[str, np.ndarray], per_primary: bool = True,
+                     with_norm: bool = True) -> Tallies:
+        s = Tallies()
+        for k in ("spectrum", "time_fx", "cross_pos", "cross_neg", "recomb", "ledger",
+                  "chan_count"):
+            setattr(s, k, t[k].ctypes.data)
+        s.per_primary = t["per_primary"].ctypes.data if per_primary else None
+        if with_norm:
+            s.density = t["density"].ctypes.data
+            s.current = t["current"].ctypes.data
+            s.field = t["field"].ctypes.data
+        s.on_device = 0
+        return s
+
+    def opts(self, seed: int, n_passes: Optional[int] = None, precision: int = FP64,
+             block_size: int = 0, blocks_per_sm: int = 0, timeout_s: float = 120.0,
+             stream: Optional[int] = None) -> RunOpts:
+        npass = self.prob.n_passes if n_passes is None else n_passes
+        return RunOpts(seed, npass, precision, block_size, blocks_per_sm, timeout_s, stream)
+
+    def run(self, prims, seed: int = 1, n_passes: Optional[int] = None, precision: int = FP64,
+            per_primary: bool = True, **kw) -> Dict[str, np.ndarray]:
+        """Whole run with host buffers in and out (karl_run)."""
+        ps, keep = self.host_primaries(prims)
+        t = self.empty_tallies(prims.n)
+        ts = self.host_tallies(t, per_primary)
+        o = self.opts(seed, n_passes, precision, **kw)
+        self._check(karl_run(self.ctx, ps, o, ts))
+        t["per_primary"] = t["per_primary"][:prims.n]
+        t["chan_count"] = t["chan_count"][:self.prob.n_channels]
+        return t
+
+    def run_pass(self, prims, seed: int, pass_index: int, field_time_in=None,
+                 pid_offset: int = 0, n_decays: Optional[int] = None, precision: int = FP64,
+                 **kw) -> Dict[str, np.ndarray]:
+        """One pass over a primary-id range, raw tallies (karl_run_pass)."""
+        ps, keep = self.host_primaries(prims, pid_offset, n_decays)
+        t = self.empty_tallies(prims.n)
+        ts = self.host_tallies(t, True, with_norm=False)
+        o = self.opts(seed, pass_index, precision, **kw)
+        fin = None
+        if field_time_in is not None:
+            fin = np.ascontiguousarray(field_time_in, np.uint64)
+        self._check(karl_run_pass(self.ctx, ps, o, pass_index,
+                                  fin.ctypes.data if fin is not None else None, ts))
+        t["per_primary"] = t["per_primary"][:prims.n]
+        t["chan_count"] = t["chan_count"][:self.prob.n_channels]
+        return t
+
+    def run_device(self, prim_ptrs: Dict[str, int], n: int, n_decays: int,
+                   out_ptrs: Dict[str, int], seed: int = 1, n_passes: Optional[int] = None,
+                   precision: int = FP64, stream: Optional[int] = None, pid_offset: int = 0,
+                   **kw) -> None:
+        """karl_run with device pointers for the primaries and the tallies."""
+        ps = Primaries(n, prim_ptrs["z_m"], prim_ptrs["e_ev"], prim_ptrs["mu"],
+                       prim_ptrs["species"], n_decays, pid_offset, 1)
+        ts = Tallies()
+        for k in ("spectrum", "time_fx", "cross_pos", "cross_neg", "recomb", "ledger",
+                  "chan_count", "per_primary", "density", "current", "field"):
+            setattr(ts, k, out_ptrs.get(k))
+        ts.on_device = 1
+        o = self.opts(seed, n_passes, precision, stream=stream, **kw)
+        self._check(karl_run(self.ctx, ps, o, ts))
+
+    def stats(self) -> RunStats:
+        return karl_last_stats(self.ctx)
+
+    def cancel(self):
+        karl_cancel(self.ctx)

@@ -1,0 +1,74 @@
+"""Comparison helpers between the CUDA path and the oracle.
+
+Acceptance (statistical, independent or matched random streams):
+* every tally bin within 3 sigma, allowing the number of 3-sigma excursions
+  expected by chance over many bins: count <= N p + 3 sqrt(N p (1-p)),
+  p = 0.0027;
+* chi^2 over bins with enough counts has p > 0.01.
+Sigma comes from Poisson counts or, for correlated tallies, from the spread of
+per-batch results (primary-id batches).
+"""
+import math
+
+import numpy as np
+
+P3 = 0.0027
+
+
+def excursions_ok(z: np.ndarray) -> bool:
+    n = z.size
+    if n == 0:
+        return True
+    bad = int(np.sum(np.abs(z) > 3.0))
+    return bad <= n * P3 + 3.0 * math.sqrt(n * P3 * (1 - P3)) + 1
+
+
+def poisson_two_sample(a: np.ndarray, b: np.ndarray, min_count: int = 10):
+    """z-scores and chi^2 p-value for two Poisson histograms of equal expectation."""
+    from scipy import stats
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    tot = a + b
+    m = tot > 0
+    z = (a[m] - b[m]) / np.sqrt(tot[m])
+    big = tot >= min_count
+    chi2 = float(np.sum((a[big] - b[big]) ** 2 / tot[big]))
+    dof = int(np.sum(big))
+    p = float(stats.chi2.sf(chi2, dof)) if dof > 0 else 1.0
+    return z, p
+
+
+def batch_means(batches: np.ndarray):
+    """Mean and standard error over the first axis (batches)."""
+    b = np.asarray(batches, np.float64)
+    k = b.shape[0]
+    return b.mean(axis=0), b.std(axis=0, ddof=1) / math.sqrt(k)
+
+
+def batch_two_sample(ga: np.ndarray, ob: np.ndarray, min_se_frac: float = 0.0):
+    """z-scores of two batched tallies [k, ...] and chi^2 p over bins with spread."""
+    from scipy import stats
+    ma, sa = batch_means(ga)
+    mb, sb = batch_means(ob)
+    se = np.sqrt(sa ** 2 + sb ** 2)
+    m = se > 0
+    z = (ma[m] - mb[m]) / se[m]
+    chi2 = float(np.sum(z ** 2))
+    dof = int(z.size)
+    p = float(stats.chi2.sf(chi2, dof)) if dof > 0 else 1.0
+    return z, p
+
+
+def ledger_balances(L) -> bool:
+    e_in = int(L[0]) + int(L[1])
+    e_out = int(np.sum(L[2:12]))
+    births = np.asarray(L[12:15])
+    deaths = np.asarray(L[15:39]).reshape(3, 8).sum(axis=1)
+    return e_in == e_out and np.array_equal(births, deaths)
+
+
+def rel_l2(a, b) -> float:
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    d = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / d) if d > 0 else float(np.linalg.norm(a))

@@ -1,0 +1,77 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds, loads,
+exports every entry point include/karl.h declares, and rejects invalid
+arguments before any CUDA call."""
+import ctypes as C
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2503_10263_gb300 import build as kbuild
+from paper_2503_10263_gb300 import inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def karl():
+    kbuild.build()
+    from paper_2503_10263_gb300 import karl as k
+    k.load()
+    return k
+
+
+def _declared(header):
+    txt = open(os.path.join(ROOT, "include", header)).read()
+    return sorted(set(re.findall(r"\b(karl_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol(karl):
+    lib = C.CDLL(karl.LIB_PATH)
+    names = _declared("karl.h")
+    assert "karl_create" in names and "karl_run" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_status_strings(karl):
+    for s in range(10):
+        assert karl.karl_status_string(s)
+    assert karl.karl_status_string(0) == "ok"
+    assert "unknown" in karl.karl_status_string(99)
+
+
+def test_create_rejects_invalid_arguments_without_gpu(karl):
+    prob, _ = inputs.config1(n_primaries=10)
+    bad = [("length_m", -1.0), ("n_zbins", 0), ("area_m2", 0.0), ("activity_bq", 0.0),
+           ("n_tebins", 0), ("spec_bin_ev", 0.0)]
+    for field, val in bad:
+        p, _ = inputs.config1(n_primaries=10)
+        setattr(p, field, val)
+        with pytest.raises(karl.KarlError) as ei:
+            karl.Context(p)
+        assert ei.value.status == karl.EINVAL, field
+    p, _ = inputs.config1(n_primaries=10)
+    p.n_seg_m3 = p.n_seg_m3.copy()
+    p.n_seg_m3[3] = -1.0
+    with pytest.raises(karl.KarlError):
+        karl.Context(p)
+    p, _ = inputs.config1(n_primaries=10)
+    p.channels[0].sigma_m2 = p.channels[0].sigma_m2.copy()
+    p.channels[0].sigma_m2[5] = math.nan
+    with pytest.raises(karl.KarlError):
+        karl.Context(p)
+    p, _ = inputs.config1(n_primaries=10)
+    p.channels[1].species_in = 7
+    with pytest.raises(karl.KarlError):
+        karl.Context(p)
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    from paper_2503_10263_gb300 import karl as k
+    monkeypatch.setattr(k, "_lib", None)
+    monkeypatch.setattr(k, "LIB_PATH", "/nonexistent/libkarl.so")
+    with pytest.raises(ImportError):
+        k.load()
