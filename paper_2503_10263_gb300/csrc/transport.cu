@@ -559,27 +559,33 @@ __global__ void __launch_bounds__(256) transport_kernel(const Params Pk, Ring R,
       unsigned long long base = 0;
       int got = 0, src = 0;
       if (lane == 0) {
-        atomicAdd((unsigned long long*)&ctl->active, (unsigned long long)k);
-        __threadfence();
+        // Count the lanes as active only when work is visible, then claim it:
+        // idle warps that find nothing leave the counter alone.
         unsigned long long h = ld_relaxed(&ctl->head), t = ld_relaxed(&ctl->tail);
-        for (int tries = 0; tries < 16 && h < t; ++tries) {
-          unsigned long long take = t - h < (unsigned long long)k ? t - h : (unsigned long long)k;
-          unsigned long long old = atomicCAS(&ctl->head, h, h + take);
-          if (old == h) { base = h; got = (int)take; src = 1; break; }
-          h = old;
-          t = ld_relaxed(&ctl->tail);
-        }
-        if (got == 0 && ld_relaxed(&ctl->prim_next) < (unsigned long long)P.n_prim &&
-            t - h < R.cap / 4) {
-          unsigned long long pn = atomicAdd(&ctl->prim_next, (unsigned long long)k);
-          if (pn < (unsigned long long)P.n_prim) {
-            unsigned long long left = (unsigned long long)P.n_prim - pn;
-            base = pn;
-            got = left < (unsigned long long)k ? (int)left : k;
-            src = 2;
+        const unsigned long long pn = ld_relaxed(&ctl->prim_next);
+        const bool ring_work = h < t;
+        const bool prim_work = pn < (unsigned long long)P.n_prim && t - h < R.cap / 4;
+        if (ring_work || prim_work) {
+          atomicAdd((unsigned long long*)&ctl->active, (unsigned long long)k);
+          __threadfence();
+          for (int tries = 0; tries < 16 && h < t; ++tries) {
+            unsigned long long take = t - h < (unsigned long long)k ? t - h : (unsigned long long)k;
+            unsigned long long old = atomicCAS(&ctl->head, h, h + take);
+            if (old == h) { base = h; got = (int)take; src = 1; break; }
+            h = old;
+            t = ld_relaxed(&ctl->tail);
           }
+          if (got == 0 && prim_work) {
+            unsigned long long p0 = atomicAdd(&ctl->prim_next, (unsigned long long)k);
+            if (p0 < (unsigned long long)P.n_prim) {
+              unsigned long long left = (unsigned long long)P.n_prim - p0;
+              base = p0;
+              got = left < (unsigned long long)k ? (int)left : k;
+              src = 2;
+            }
+          }
+          if (got < k) atomicAdd((unsigned long long*)&ctl->active, (unsigned long long)(got - k));
         }
-        if (got < k) atomicAdd((unsigned long long*)&ctl->active, (unsigned long long)(got - k));
       }
       base = __shfl_sync(FULL, base, 0);
       got = __shfl_sync(FULL, got, 0);
@@ -623,11 +629,20 @@ __global__ void __launch_bounds__(256) transport_kernel(const Params Pk, Ring R,
     if (!busy) {
       int done = 0;
       if (lane == 0) {
-        long long a = ld_relaxed_s(&ctl->active);
+        // Done when no work is queued, none will come (no particle is held),
+        // and nothing moved between two snapshots taken around the read of
+        // the active count.  A claim visible in the first snapshot makes its
+        // active increment visible; a product reserved by a particle whose
+        // death is visible shows up in the second snapshot.
+        const unsigned long long h1 = ld_relaxed(&ctl->head), t1 = ld_relaxed(&ctl->tail);
+        const unsigned long long p1 = ld_relaxed(&ctl->prim_next);
         __threadfence();
-        unsigned long long h = ld_relaxed(&ctl->head), t = ld_relaxed(&ctl->tail);
-        unsigned long long pn = ld_relaxed(&ctl->prim_next);
-        done = (a <= 0 && h >= t && pn >= (unsigned long long)P.n_prim);
+        const long long a = ld_relaxed_s(&ctl->active);
+        __threadfence();
+        const unsigned long long h2 = ld_relaxed(&ctl->head), t2 = ld_relaxed(&ctl->tail);
+        const unsigned long long p2 = ld_relaxed(&ctl->prim_next);
+        done = (a <= 0 && h1 == h2 && t1 == t2 && p1 == p2 && h1 >= t1 &&
+                p1 >= (unsigned long long)P.n_prim);
       }
       if (__shfl_sync(FULL, done, 0)) break;
       __nanosleep(256);
