@@ -341,7 +341,9 @@ void base_params(const karl_ctx* c, Params& P, const karl_run_opts* o, int pass)
   P.colgas = c->d_colgas.p;
   P.n_energy = c->n_energy;
   P.e_min = c->e_min;
+  P.inv_e_min = 1.0 / c->e_min;
   P.log_ratio_h = std::log(c->e_max / c->e_min) / (double)(c->n_energy - 1);
+  P.inv_h = 1.0 / P.log_ratio_h;
   P.sig = c->d_sig.p;
   P.sigf = c->d_sigf.p;
   P.nch = c->nch;
@@ -362,9 +364,13 @@ void base_params(const karl_ctx* c, Params& P, const karl_run_opts* o, int pass)
     }
     P.nsc[s] = n;
     P.mass[s] = c->mass[s];
+    P.inv_mass[s] = 1.0 / c->mass[s];
+    P.gam[s] = c->mass[s] / c->target_mass;
+    P.inv_1pg2[s] = 1.0 / ((1.0 + P.gam[s]) * (1.0 + P.gam[s]));
   }
   P.target_mass = c->target_mass;
   P.eps_ion = c->eps_ion;
+  P.inv_eps_ion = 1.0 / c->eps_ion;
   P.kT = c->kT;
   P.ecut_q = (long long)std::floor(c->e_cut * Q_ENERGY);
   P.max_coll = c->max_coll;

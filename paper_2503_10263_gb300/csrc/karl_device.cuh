@@ -46,7 +46,7 @@ struct Params {
   const double* fcol[MAXCH];    // [nz+1] its column to each face
   // cross sections
   int n_energy;
-  double e_min, log_ratio_h;    // h = ln(e_max/e_min)/(n-1)
+  double e_min, inv_e_min, log_ratio_h, inv_h;   // h = ln(e_max/e_min)/(n-1)
   const double* sig;            // [nch][n_energy]
   const float* sigf;            // same, FP32
   int nch;
@@ -55,7 +55,10 @@ struct Params {
   int8_t sc[NSP][MAXSPCH];      // active channels per species, in selection order
   // species and targets
   double mass[NSP];
-  double target_mass, eps_ion, kT;
+  double inv_mass[NSP];
+  double gam[NSP];              // m / M_target
+  double inv_1pg2[NSP];         // 1 / (1 + m/M)^2
+  double target_mass, eps_ion, inv_eps_ion, kT;
   long long ecut_q;
   unsigned max_coll;
   double max_life;

@@ -29,6 +29,7 @@ template <> struct RT<false> {
   static __device__ __forceinline__ R eta(unsigned long long w) { return eta01d(w); }
   static __device__ __forceinline__ R lg(R x) { return log(x); }
   static __device__ __forceinline__ R sq(R x) { return sqrt(x); }
+  static __device__ __forceinline__ R rsq(R x) { return rsqrt(x); }
   static __device__ __forceinline__ R tn(R x) { return tan(x); }
   static __device__ __forceinline__ R atn(R x) { return atan(x); }
   static __device__ __forceinline__ R cpi(R x) { return cospi(x); }
@@ -42,6 +43,7 @@ template <> struct RT<true> {
   static __device__ __forceinline__ R eta(unsigned long long w) { return eta01f(w); }
   static __device__ __forceinline__ R lg(R x) { return logf(x); }
   static __device__ __forceinline__ R sq(R x) { return sqrtf(x); }
+  static __device__ __forceinline__ R rsq(R x) { return rsqrtf(x); }
   static __device__ __forceinline__ R tn(R x) { return tanf(x); }
   static __device__ __forceinline__ R atn(R x) { return atanf(x); }
   static __device__ __forceinline__ R cpi(R x) { return cospif(x); }
@@ -75,8 +77,8 @@ __device__ __forceinline__ unsigned long long quant_t(double len, double inv_sz)
 __device__ __forceinline__ long long quant_e(double e) { return (long long)floor(e * Q_E); }
 
 template <class R>
-__device__ __forceinline__ R speed(R e, R m) {
-  R x = e / m;
+__device__ __forceinline__ R speed(R e, R inv_m) {
+  R x = e * inv_m;
   return (R)C_LIGHT * sqrt(x * ((R)2 + x)) / ((R)1 + x);
 }
 
@@ -144,9 +146,17 @@ __device__ bool ring_get(const Ring& R, Control* ctl, unsigned long long pos, La
 
 struct EventOut {
   bool alive;
-  bool child_e, child_i;
-  Lane ce, ci;
-  unsigned long long flights, colls;
+  int chan;                               // channel of this event's collision, -1 if none
+  unsigned long long flights, colls;      // per-lane counters, flushed at the end
+  unsigned long long recoil, excit;       // per-lane energy sums (2^-24 eV)
+};
+
+// Ring access for products, made where they are created (products are rare:
+// one reservation per ionization).
+struct RingPort {
+  const Ring* R;
+  Control* ctl;
+  unsigned long long deadline;
 };
 
 template <bool F32>
@@ -168,20 +178,19 @@ __device__ __forceinline__ void thermal(const Params& P, const unsigned long lon
 }
 
 template <bool F32>
-__device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o) {
+__device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o, const RingPort& port) {
   using T = RT<F32>;
   using R = typename T::R;
-  o.child_e = o.child_i = false;
   o.alive = true;
+  o.chan = -1;
   if (L.eq <= 0) {                 // no kinetic energy: the particle never moves
     die<F32>(P, S, L, R_STALLED, L_E_STALLED);
     o.alive = false;
     return;
   }
   const int s = L.sp;
-  const R m = (R)P.mass[s];
   const R e = (R)((double)L.eq * INV_Q_E);
-  const R v = speed<R>(e, m);
+  const R v = speed<R>(e, (R)P.inv_mass[s]);
 
   unsigned long long w[4];
   philox4x64_10((unsigned long long)L.ev, L.node,
@@ -193,7 +202,8 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o) {
   // (ion recombining with the electron field, whose rate already has sigma v)
   const int nsc = P.nsc[s];
   R coef[MAXSPCH];
-  R lx = T::lg(e / (R)P.e_min) / (R)P.log_ratio_h;
+  const R le = T::lg(e * (R)P.inv_e_min);       // ln(E / e_min), shared by both lookups
+  R lx = le * (R)P.inv_h;
   int ti = (int)floor(lx);
   R tf;
   if (ti < 0) { ti = 0; tf = (R)0; }
@@ -218,24 +228,25 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o) {
   }
   // recombination terms of this flight (at most two): coefficient and field
   int nrec = 0;
-  double rc[2] = {0.0, 0.0};
-  const double* rcol[2] = {P.colgas, P.colgas};
-  const double* rrate[2] = {P.nseg, P.nseg};
+  double rc0 = 0.0, rc1 = 0.0;
+  const double* rcol0 = P.colgas;
+  const double* rcol1 = P.colgas;
+  const double* rrate0 = P.nseg;
+  const double* rrate1 = P.nseg;
 #pragma unroll
   for (int c = 0; c < MAXSPCH; ++c) {
     if (c >= nsc) break;
     const int kk = P.sc[s][c];
-    if (P.ch[kk].kind == RECOMBINATION && nrec < 2) {
-      rc[nrec] = (double)coef[c];
-      rcol[nrec] = P.fcol[kk];
-      rrate[nrec] = P.frate[kk];
+    if (P.ch[kk].kind == RECOMBINATION) {
+      if (nrec == 0) { rc0 = (double)coef[c]; rcol0 = P.fcol[kk]; rrate0 = P.frate[kk]; }
+      else { rc1 = (double)coef[c]; rcol1 = P.fcol[kk]; rrate1 = P.frate[kk]; }
       ++nrec;
     }
   }
   // energy bin of the time tally
   int b = 0;
   if (P.ntb > 1) {
-    b = (int)floor(T::lg(e / (R)P.e_min) * (R)P.tb_scale);
+    b = (int)floor(le * (R)P.tb_scale);
     b = b < 0 ? 0 : (b > P.ntb - 1 ? P.ntb - 1 : b);
   }
   const size_t trow = (size_t)P.ntb;                         // stride between z rows
@@ -246,14 +257,14 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o) {
   // G(k) = optical-depth column of the whole rate to face k
   auto colsum = [&](int k) -> double {
     double g = gasd * __ldg(P.colgas + k);
-    if (nrec > 0) g += rc[0] * __ldg(rcol[0] + k);
-    if (nrec > 1) g += rc[1] * __ldg(rcol[1] + k);
+    if (nrec > 0) g += rc0 * __ldg(rcol0 + k);
+    if (nrec > 1) g += rc1 * __ldg(rcol1 + k);
     return g;
   };
   auto segrate = [&](int j) -> double {
     double r = gasd * __ldg(P.nseg + j);
-    if (nrec > 0) r += rc[0] * __ldg(rrate[0] + j);
-    if (nrec > 1) r += rc[1] * __ldg(rrate[1] + j);
+    if (nrec > 0) r += rc0 * __ldg(rrate0 + j);
+    if (nrec > 1) r += rc1 * __ldg(rrate1 + j);
     return r;
   };
 
@@ -379,15 +390,16 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o) {
   // ---- collision in segment jc ----
   L.ev += 1;
   o.colls += 1;
-  double rk[MAXSPCH];
+  auto chan_rate = [&](int c) -> double {
+    const int kk = P.sc[s][c];
+    return (double)coef[c] * (P.ch[kk].kind == RECOMBINATION ? __ldg(P.frate[kk] + jc)
+                                                               : __ldg(P.nseg + jc));
+  };
   double rtot = 0.0;
 #pragma unroll
   for (int c = 0; c < MAXSPCH; ++c) {
     if (c >= nsc) break;
-    const int kk = P.sc[s][c];
-    rk[c] = (double)coef[c] * (P.ch[kk].kind == RECOMBINATION ? __ldg(P.frate[kk] + jc)
-                                                                : __ldg(P.nseg + jc));
-    rtot += rk[c];
+    rtot += chan_rate(c);
   }
   const double target = u01d(w[1]) * rtot;
   int chs = -1, last = -1;
@@ -395,25 +407,26 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o) {
 #pragma unroll
   for (int c = 0; c < MAXSPCH; ++c) {
     if (c >= nsc) break;
-    if (!(rk[c] > 0.0)) continue;
+    const double rkc = chan_rate(c);
+    if (!(rkc > 0.0)) continue;
     last = c;
-    cum += rk[c];
+    cum += rkc;
     if (target < cum) { chs = c; break; }
   }
   if (chs < 0) chs = last;
   const int k = P.sc[s][chs];
-  sadd(&S.chan[k], 1);
+  o.chan = k;
   const ChanDev ch = P.ch[k];
   if (ch.kind == ELASTIC) {
     // isotropic in CM, target at rest: lab energy and polar angle
-    const R g = m / (R)P.target_mass;
+    const R g = (R)P.gam[s];
     const R cchi = (R)2 * T::u(w[2]) - (R)1;
     const R a = (R)1 + (R)2 * g * cchi + g * g;
-    const R e1 = e * a / (((R)1 + g) * ((R)1 + g));
-    const R ct = (cchi + g) / T::sq(a);
+    const R e1 = e * a * (R)P.inv_1pg2[s];
+    const R ct = (cchi + g) * T::rsq(a);
     long long eq1 = quant_e((double)e1);
     if (eq1 > L.eq) eq1 = L.eq;
-    sadd(&S.ledger[L_LOSS_RECOIL], L.eq - eq1);
+    o.recoil += (unsigned long long)(L.eq - eq1);
     L.eq = eq1;
     const R st = T::sq(fmax((R)0, (R)1 - ct * ct));
     const R cphi = T::cpi((R)2 * T::u(w[3]));
@@ -422,20 +435,21 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o) {
     L.mu = (double)fmin((R)1, fmax((R)-1, mu * ct + smu * st * cphi));
   } else if (ch.kind == EXCITATION) {
     L.eq -= ch.loss_q;
-    sadd(&S.ledger[L_LOSS_EXCIT], ch.loss_q);
+    o.excit += (unsigned long long)ch.loss_q;
   } else if (ch.kind == IONIZATION) {
     const long long avail = L.eq - ch.loss_q;
     const R eps = (R)P.eps_ion;
     const R wmax = (e - (R)ch.loss_ev) * (R)0.5;
-    const R wsec = eps * T::tn(T::u(w[2]) * T::atn(wmax / eps));
+    const R wsec = eps * T::tn(T::u(w[2]) * T::atn(wmax * (R)P.inv_eps_ion));
     long long wq = quant_e((double)wsec);
     if (wq > avail / 2) wq = avail / 2;
     if (wq < 0) wq = 0;
     const long long eq1 = avail - wq;
     sadd(&S.ledger[L_LOSS_IONIZ], ch.loss_q);
     // binary encounter: cos^2 of the polar angles are the energy fractions
-    const R c2p = avail > 0 ? (R)((double)eq1 / (double)avail) : (R)1;
-    const R c2s = avail > 0 ? (R)((double)wq / (double)avail) : (R)0;
+    const double inv_avail = avail > 0 ? 1.0 / (double)avail : 0.0;
+    const R c2p = avail > 0 ? (R)((double)eq1 * inv_avail) : (R)1;
+    const R c2s = (R)((double)wq * inv_avail);
     const R cp = T::sq(c2p), sp = T::sq(c2s);
     const R cphi = T::cpi((R)2 * T::u(w[3]));
     const R mu = (R)L.mu;
@@ -449,12 +463,12 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o) {
     Lane c;
     c.z = L.z; c.eq = wq; c.mu = (double)mu_s; c.node = child_node(L.node, evc, 0);
     c.tal = 0.0; c.pid = L.pid; c.ev = 0; c.sp = SP_E;
-    if (wq < P.ecut_q) {
-      die<F32>(P, S, c, R_CUTOFF, L_E_CUTOFF);
-    } else {
-      o.child_e = true;
-      o.ce = c;
-    }
+    const bool keep_e = wq >= P.ecut_q;
+    if (!keep_e) die<F32>(P, S, c, R_CUTOFF, L_E_CUTOFF);
+    const int nprod = (keep_e ? 1 : 0) + (ch.sout >= 0 ? 1 : 0);
+    unsigned long long pos = 0;
+    if (nprod) pos = atomicAdd(&port.ctl->tail, (unsigned long long)nprod);
+    if (keep_e) ring_put(*port.R, port.ctl, pos++, c, port.deadline);
     // ion with a thermal target's velocity (no recoil)
     if (ch.sout >= 0) {
       Lane ion;
@@ -467,8 +481,7 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o) {
       sadd(&S.ledger[L_E_IN_THERMAL], ion.eq);
       sadd(&S.ledger[L_BIRTHS + ch.sout], 1);
       sadd(&S.ledger[L_N_SPAWN_ION], 1);
-      o.child_i = true;
-      o.ci = ion;
+      ring_put(*port.R, port.ctl, pos, ion, port.deadline);
     }
     L.eq = eq1;
     L.mu = (double)mu_p;
@@ -532,7 +545,14 @@ __global__ void __launch_bounds__(256) transport_kernel(const Params Pk, Ring R,
   EventOut o;
   o.flights = 0;
   o.colls = 0;
+  o.recoil = 0;
+  o.excit = 0;
+  o.chan = -1;
   unsigned long long started = 0;
+  RingPort port;
+  port.R = &R;
+  port.ctl = ctl;
+  port.deadline = deadline;
 
   for (long long iter = 0;; ++iter) {
     if ((iter & 31) == 0) {
@@ -650,28 +670,20 @@ __global__ void __launch_bounds__(256) transport_kernel(const Params Pk, Ring R,
     }
 
     // ---- one event ----
-    o.child_e = o.child_i = false;
     bool died = false;
     if (has) {
-      event<F32>(P, S, L, o);
+      event<F32>(P, S, L, o, port);
       if (!o.alive) { has = false; died = true; }
     }
 
-    // ---- products to the ring (one reservation per warp) ----
-    const unsigned me = __ballot_sync(FULL, o.child_e);
-    const unsigned mi = __ballot_sync(FULL, o.child_i);
-    if (me | mi) {
-      const int ne = __popc(me), ni = __popc(mi);
-      unsigned long long pos = 0;
-      if (lane == 0) {
-        pos = atomicAdd(&ctl->tail, (unsigned long long)(ne + ni));
-        unsigned long long occ = pos + ne + ni - ld_relaxed(&ctl->head);
-        atomicMax(&ctl->max_occupancy, occ);
-      }
-      pos = __shfl_sync(FULL, pos, 0);
-      if (o.child_e) ring_put(R, ctl, pos + __popc(me & lt), o.ce, deadline);
-      if (o.child_i) ring_put(R, ctl, pos + ne + __popc(mi & lt), o.ci, deadline);
+    // ---- channel counts, one shared-memory add per distinct channel per warp ----
+    const unsigned mc = __ballot_sync(FULL, o.chan >= 0);
+    if (o.chan >= 0) {
+      const unsigned grp = __match_any_sync(mc, o.chan);
+      if (lane == __ffs(grp) - 1) atomicAdd(&S.chan[o.chan], (unsigned long long)__popc(grp));
     }
+    o.chan = -1;
+
     const unsigned md = __ballot_sync(FULL, died);
     if (md) {
       __threadfence();
@@ -681,16 +693,20 @@ __global__ void __launch_bounds__(256) transport_kernel(const Params Pk, Ring R,
   }
 
   // ---- flush per-lane and per-block counters ----
-  unsigned long long f = o.flights, c = o.colls, st = started;
+  unsigned long long f = o.flights, c = o.colls, st = started, rc = o.recoil, ex = o.excit;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     f += __shfl_down_sync(FULL, f, off);
     c += __shfl_down_sync(FULL, c, off);
     st += __shfl_down_sync(FULL, st, off);
+    rc += __shfl_down_sync(FULL, rc, off);
+    ex += __shfl_down_sync(FULL, ex, off);
   }
   if (lane == 0) {
     atomicAdd(&S.ledger[L_N_FLIGHT], f);
     atomicAdd(&S.ledger[L_N_COLL], c);
+    atomicAdd(&S.ledger[L_LOSS_RECOIL], rc);
+    atomicAdd(&S.ledger[L_LOSS_EXCIT], ex);
     atomicAdd(&ctl->particles, st);
   }
   __syncthreads();

@@ -72,3 +72,26 @@ def rel_l2(a, b) -> float:
     b = np.asarray(b, np.float64).ravel()
     d = np.linalg.norm(b)
     return float(np.linalg.norm(a - b) / d) if d > 0 else float(np.linalg.norm(a))
+
+
+def hotelling_two_sample(a: np.ndarray, b: np.ndarray) -> float:
+    """p-value of Hotelling's two-sample T^2 test on batch vectors a [k1, d],
+    b [k2, d]: equal means, correlated components, common covariance."""
+    from scipy import stats
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    n1, d = a.shape
+    n2 = b.shape[0]
+    diff = a.mean(0) - b.mean(0)
+    s = ((n1 - 1) * np.cov(a, rowvar=False) + (n2 - 1) * np.cov(b, rowvar=False)) / (n1 + n2 - 2)
+    s = np.atleast_2d(s)
+    t2 = n1 * n2 / (n1 + n2) * float(diff @ np.linalg.solve(s, diff))
+    f = (n1 + n2 - d - 1) / (d * (n1 + n2 - 2)) * t2
+    return float(stats.f.sf(f, d, n1 + n2 - d - 1))
+
+
+def coarse_groups(x: np.ndarray, groups: int) -> np.ndarray:
+    """Sum the last axis of [k, n] into `groups` contiguous groups."""
+    k, n = x.shape
+    edges = np.linspace(0, n, groups + 1).astype(int)
+    return np.stack([x[:, a:b].sum(1) for a, b in zip(edges[:-1], edges[1:])], axis=1)
