@@ -199,6 +199,7 @@ typedef struct karl_run_stats {
   int64_t collisions[2];
   int64_t flights[2];
   int64_t particles[2];        /* particles processed (primaries + products) */
+  double lane_occupancy[2];    /* mean fraction of lanes holding a particle */
   int32_t grid_blocks, block_size;
   int32_t queue_capacity;
   int64_t kernel_launches;

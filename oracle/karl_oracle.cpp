@@ -98,6 +98,8 @@ uint64_t child_node(uint64_t parent, uint32_t ev, uint32_t slot) {
 }
 
 int64_t quant_e(double e_ev) { return (int64_t)std::floor(e_ev * Q_ENERGY); }
+/* an energy transfer, rounded to the nearest 2^-24 eV unit */
+int64_t quant_recoil(double de_ev) { return (int64_t)std::floor(de_ev * Q_ENERGY + 0.5); }
 
 struct Particle {
   double z;
@@ -419,12 +421,12 @@ struct Worker {
         double g = m / p->target_mass_ev;
         double cchi = 2.0 * u01(w[2]) - 1.0;
         double a = 1.0 + 2.0 * g * cchi + g * g;
-        double e1 = e * a / ((1.0 + g) * (1.0 + g));
         double ct = (cchi + g) / std::sqrt(a);
-        int64_t eq1 = quant_e(e1);
-        if (eq1 > P.eq) eq1 = P.eq;
-        T.ledger[ORC_E_LOSS_RECOIL] += P.eq - eq1;
-        P.eq = eq1;
+        /* energy given to the target, E - E' = E 2g(1 - cos chi)/(1+g)^2 */
+        int64_t rq = quant_recoil(e * 2.0 * g * (1.0 - cchi) / ((1.0 + g) * (1.0 + g)));
+        if (rq > P.eq) rq = P.eq;
+        T.ledger[ORC_E_LOSS_RECOIL] += rq;
+        P.eq -= rq;
         double st = std::sqrt(std::fmax(0.0, 1.0 - ct * ct));
         double cphi = std::cos(TWO_PI * u01(w[3]));
         double smu = std::sqrt(std::fmax(0.0, 1.0 - P.mu * P.mu));
@@ -622,10 +624,10 @@ int orc_collide(const orc_problem* p, int ch, int species, double e_ev, double m
     double g = m / p->target_mass_ev;
     double cchi = 2.0 * u01(w[2]) - 1.0;
     double a = 1.0 + 2.0 * g * cchi + g * g;
-    double e1 = e * a / ((1.0 + g) * (1.0 + g));
     double ct = (cchi + g) / std::sqrt(a);
-    int64_t eq1 = quant_e(e1);
-    if (eq1 > eq) eq1 = eq;
+    int64_t rq = quant_recoil(e * 2.0 * g * (1.0 - cchi) / ((1.0 + g) * (1.0 + g)));
+    if (rq > eq) rq = eq;
+    int64_t eq1 = eq - rq;
     double st = std::sqrt(std::fmax(0.0, 1.0 - ct * ct));
     double cphi = std::cos(TWO_PI * u01(w[3]));
     double smu = std::sqrt(std::fmax(0.0, 1.0 - mu * mu));

@@ -76,8 +76,9 @@ struct karl_ctx {
   std::vector<int> kind, sin, sout;
   std::vector<double> loss;
   // device tables
-  DevBuf<double> d_nseg, d_colgas, d_sig, d_frate, d_fcol, d_time1;
+  DevBuf<double> d_nseg, d_colgas, d_sig, d_sig_t, d_frate, d_fcol, d_time1;
   DevBuf<float> d_sigf;
+  cudaStream_t cancel_stream = nullptr;
   // device work buffers
   DevBuf<double> d_pz, d_pe, d_pmu;
   DevBuf<uint8_t> d_psp;
@@ -93,8 +94,8 @@ struct karl_ctx {
   DevBuf<uint8_t> r_sp;
   unsigned long long ring_cap = 0;
   Control* d_ctl = nullptr;
-  int* h_cancel = nullptr;      // pinned, mapped
-  int* d_cancel = nullptr;
+  int* h_cancel = nullptr;      // pinned host word, source of the copy that cancels
+  int* d_cancel = nullptr;      // device word polled by the kernel
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   karl_run_stats stats;
   std::string err;
@@ -344,7 +345,7 @@ void base_params(const karl_ctx* c, Params& P, const karl_run_opts* o, int pass)
   P.inv_e_min = 1.0 / c->e_min;
   P.log_ratio_h = std::log(c->e_max / c->e_min) / (double)(c->n_energy - 1);
   P.inv_h = 1.0 / P.log_ratio_h;
-  P.sig = c->d_sig.p;
+  P.sig = c->d_sig_t.p;
   P.sigf = c->d_sigf.p;
   P.nch = c->nch;
   for (int k = 0; k < c->nch; ++k) {
@@ -450,7 +451,7 @@ karl_status run_one_pass(karl_ctx* ctx, const karl_primaries* pr, const karl_run
     R.tal = ctx->r_tal.p; R.pid = ctx->r_pid.p; R.ev = ctx->r_ev.p; R.sp = ctx->r_sp.p;
     R.seq = ctx->r_seq.p; R.cap = ctx->ring_cap; R.mask = ctx->ring_cap - 1;
 
-    *ctx->h_cancel = 0;
+    CK(cudaMemsetAsync(ctx->d_cancel, 0, sizeof(int), st));
     CK(cudaEventRecord(ctx->ev0, st));
     CK(launch_transport(f32, P, R, ctx->d_ctl, ctx->d_cancel,
                         (unsigned long long)(timeout * 1e9), grid, block, st));
@@ -463,6 +464,10 @@ karl_status run_one_pass(karl_ctx* ctx, const karl_primaries* pr, const karl_run
     int pi = pass - 1;
     ctx->stats.kernel_ms[pi] = ms;
     ctx->stats.particles[pi] = (int64_t)hc.particles;
+    ctx->stats.lane_occupancy[pi] =
+        hc.busy_iters + hc.idle_iters
+            ? (double)hc.busy_lane_iters / (32.0 * (double)(hc.busy_iters + hc.idle_iters))
+            : 0.0;
     ctx->stats.grid_blocks = grid;
     ctx->stats.block_size = block;
     ctx->stats.queue_capacity = (int32_t)std::min<unsigned long long>(ctx->ring_cap, 0x7fffffff);
@@ -658,30 +663,47 @@ karl_status karl_create(const karl_geometry* g, const karl_xs* x, karl_ctx** out
   // gas column to each face
   std::vector<double> col(ctx->nz + 1, 0.0);
   for (int j = 0; j < ctx->nz; ++j) col[j + 1] = col[j] + ctx->nseg[j] * ctx->dz;
-  std::vector<float> sigf(ctx->sigma.begin(), ctx->sigma.end());
+  // [node][channel] copies for the transport kernel (all channels of one node
+  // in adjacent words), channel-major copy for the field builder
+  std::vector<double> sig_t(ctx->sigma.size());
+  std::vector<float> sigf(ctx->sigma.size());
+  for (int k = 0; k < ctx->nch; ++k)
+    for (int i = 0; i < ctx->n_energy; ++i) {
+      double v = ctx->sigma[(size_t)k * ctx->n_energy + i];
+      sig_t[(size_t)i * ctx->nch + k] = v;
+      sigf[(size_t)i * ctx->nch + k] = (float)v;
+    }
   size_t nsig = std::max<size_t>(ctx->sigma.size(), 1);
   if (ctx->d_nseg.ensure(ctx->nz) || ctx->d_colgas.ensure(ctx->nz + 1) ||
-      ctx->d_sig.ensure(nsig) || ctx->d_sigf.ensure(nsig) || ctx->d_ledger.ensure(LEDGER))
+      ctx->d_sig.ensure(nsig) || ctx->d_sig_t.ensure(nsig) || ctx->d_sigf.ensure(nsig) ||
+      ctx->d_ledger.ensure(LEDGER))
     return bail(KARL_ENOMEM);
   if (cudaMemcpy(ctx->d_nseg.p, ctx->nseg.data(), ctx->nz * 8, cudaMemcpyHostToDevice) ||
       cudaMemcpy(ctx->d_colgas.p, col.data(), (ctx->nz + 1) * 8, cudaMemcpyHostToDevice) ||
       (ctx->sigma.size() &&
        (cudaMemcpy(ctx->d_sig.p, ctx->sigma.data(), ctx->sigma.size() * 8, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(ctx->d_sig_t.p, sig_t.data(), sig_t.size() * 8, cudaMemcpyHostToDevice) ||
         cudaMemcpy(ctx->d_sigf.p, sigf.data(), sigf.size() * 4, cudaMemcpyHostToDevice))))
     return bail(KARL_ECUDA);
   if (cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) ||
-      cudaMalloc(&ctx->d_ctl, sizeof(Control)) ||
-      cudaHostAlloc(&ctx->h_cancel, sizeof(int), cudaHostAllocMapped) ||
-      cudaHostGetDevicePointer(&ctx->d_cancel, ctx->h_cancel, 0) ||
+      cudaStreamCreateWithFlags(&ctx->cancel_stream, cudaStreamNonBlocking) ||
+      cudaMalloc(&ctx->d_ctl, sizeof(Control)) || cudaMalloc(&ctx->d_cancel, sizeof(int)) ||
+      cudaHostAlloc(&ctx->h_cancel, sizeof(int), cudaHostAllocDefault) ||
+      cudaMemset(ctx->d_cancel, 0, sizeof(int)) ||
       cudaEventCreate(&ctx->ev0) || cudaEventCreate(&ctx->ev1))
     return bail(KARL_ECUDA);
-  *ctx->h_cancel = 0;
+  *ctx->h_cancel = 1;
   *out = ctx;
   return KARL_OK;
 }
 
 void karl_cancel(karl_ctx* ctx) {
-  if (ctx && ctx->h_cancel) *(volatile int*)ctx->h_cancel = 1;
+  // a copy on a stream of its own runs while the transport kernel is running
+  if (ctx && ctx->d_cancel && ctx->cancel_stream) {
+    cudaMemcpyAsync(ctx->d_cancel, ctx->h_cancel, sizeof(int), cudaMemcpyHostToDevice,
+                    ctx->cancel_stream);
+    cudaStreamSynchronize(ctx->cancel_stream);
+  }
 }
 
 karl_status karl_tally_layout(const karl_ctx* c, karl_layout* o) {
@@ -834,6 +856,9 @@ void karl_destroy(karl_ctx* ctx) {
   ctx->r_sp.release();
   if (ctx->d_ctl) cudaFree(ctx->d_ctl);
   if (ctx->h_cancel) cudaFreeHost(ctx->h_cancel);
+  if (ctx->d_cancel) cudaFree(ctx->d_cancel);
+  if (ctx->cancel_stream) cudaStreamDestroy(ctx->cancel_stream);
+  ctx->d_sig_t.release();
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);

@@ -47,7 +47,7 @@ struct Params {
   // cross sections
   int n_energy;
   double e_min, inv_e_min, log_ratio_h, inv_h;   // h = ln(e_max/e_min)/(n-1)
-  const double* sig;            // [nch][n_energy]
+  const double* sig;            // [n_energy][nch], the channels of one node together
   const float* sigf;            // same, FP32
   int nch;
   ChanDev ch[MAXCH];
@@ -110,7 +110,9 @@ struct Control {
   int error;
   int abort;
   unsigned long long particles; // particles started (primaries + products)
-  unsigned long long max_occupancy;
+  unsigned long long idle_iters;      // warp iterations without a particle
+  unsigned long long busy_iters;      // warp iterations with at least one
+  unsigned long long busy_lane_iters; // lanes holding a particle, summed over busy iterations
 };
 
 // ------------------------------------------------------------------------

@@ -34,7 +34,7 @@ template <> struct RT<false> {
   static __device__ __forceinline__ R atn(R x) { return atan(x); }
   static __device__ __forceinline__ R cpi(R x) { return cospi(x); }
   static __device__ __forceinline__ R tab(const Params& P, int k, int i) {
-    return __ldg(P.sig + (size_t)k * P.n_energy + i);
+    return __ldg(P.sig + (size_t)i * P.nch + k);      // [node][channel]
   }
 };
 template <> struct RT<true> {
@@ -48,7 +48,7 @@ template <> struct RT<true> {
   static __device__ __forceinline__ R atn(R x) { return atanf(x); }
   static __device__ __forceinline__ R cpi(R x) { return cospif(x); }
   static __device__ __forceinline__ R tab(const Params& P, int k, int i) {
-    return __ldg(P.sigf + (size_t)k * P.n_energy + i);
+    return __ldg(P.sigf + (size_t)i * P.nch + k);     // [node][channel]
   }
 };
 
@@ -422,12 +422,13 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o, const Ri
     const R g = (R)P.gam[s];
     const R cchi = (R)2 * T::u(w[2]) - (R)1;
     const R a = (R)1 + (R)2 * g * cchi + g * g;
-    const R e1 = e * a * (R)P.inv_1pg2[s];
     const R ct = (cchi + g) * T::rsq(a);
-    long long eq1 = quant_e((double)e1);
-    if (eq1 > L.eq) eq1 = L.eq;
-    o.recoil += (unsigned long long)(L.eq - eq1);
-    L.eq = eq1;
+    // energy given to the target, E - E' = E 2g(1 - cos chi)/(1+g)^2
+    const R de = e * ((R)2 * g) * ((R)1 - cchi) * (R)P.inv_1pg2[s];
+    long long rq = (long long)floor((double)de * Q_E + 0.5);
+    if (rq > L.eq) rq = L.eq;
+    o.recoil += (unsigned long long)rq;
+    L.eq -= rq;
     const R st = T::sq(fmax((R)0, (R)1 - ct * ct));
     const R cphi = T::cpi((R)2 * T::u(w[3]));
     const R mu = (R)L.mu;
@@ -549,17 +550,19 @@ __global__ void __launch_bounds__(256) transport_kernel(const Params Pk, Ring R,
   o.excit = 0;
   o.chan = -1;
   unsigned long long started = 0;
+  unsigned long long idle_iters = 0, busy_iters = 0, busy_lane_iters = 0;
+  unsigned idle_ns = 128;
   RingPort port;
   port.R = &R;
   port.ctl = ctl;
   port.deadline = deadline;
 
   for (long long iter = 0;; ++iter) {
-    if ((iter & 31) == 0) {
+    if ((iter & 63) == 0) {
       int stop = 0;
       if (lane == 0) {
         if (ld_relaxed_i(&ctl->abort)) stop = 1;
-        else if (cancel && *cancel) {
+        else if (cancel && ld_relaxed_i((const int*)cancel)) {
           atomicCAS(&ctl->error, 0, ERR_CANCELLED);
           atomicExch(&ctl->abort, 1);
           stop = 1;
@@ -665,9 +668,14 @@ __global__ void __launch_bounds__(256) transport_kernel(const Params Pk, Ring R,
                 p1 >= (unsigned long long)P.n_prim);
       }
       if (__shfl_sync(FULL, done, 0)) break;
-      __nanosleep(256);
+      __nanosleep(idle_ns);
+      if (idle_ns < 4096) idle_ns <<= 1;
+      ++idle_iters;
       continue;
     }
+    idle_ns = 128;
+    busy_lane_iters += __popc(busy);
+    ++busy_iters;
 
     // ---- one event ----
     bool died = false;
@@ -703,6 +711,9 @@ __global__ void __launch_bounds__(256) transport_kernel(const Params Pk, Ring R,
     ex += __shfl_down_sync(FULL, ex, off);
   }
   if (lane == 0) {
+    atomicAdd(&ctl->idle_iters, idle_iters);
+    atomicAdd(&ctl->busy_iters, busy_iters);
+    atomicAdd(&ctl->busy_lane_iters, busy_lane_iters);
     atomicAdd(&S.ledger[L_N_FLIGHT], f);
     atomicAdd(&S.ledger[L_N_COLL], c);
     atomicAdd(&S.ledger[L_LOSS_RECOIL], rc);

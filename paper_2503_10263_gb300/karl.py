@@ -89,6 +89,7 @@ class Layout(C.Structure):
 class RunStats(C.Structure):
     _fields_ = [("kernel_ms", C.c_double * 2), ("collisions", C.c_int64 * 2),
                 ("flights", C.c_int64 * 2), ("particles", C.c_int64 * 2),
+                ("lane_occupancy", C.c_double * 2),
                 ("grid_blocks", C.c_int32), ("block_size", C.c_int32),
                 ("queue_capacity", C.c_int32), ("kernel_launches", C.c_int64)]
 
