@@ -102,17 +102,24 @@ struct Ring {
   unsigned long long cap, mask;
 };
 
+// Work counters of one pass.  The four hot counters sit on separate 128-byte
+// lines so their atomics do not serialise on one L2 line.
 struct Control {
   unsigned long long head;      // next ring position to consume
+  char pad0[120];
   unsigned long long tail;      // next ring position to produce
+  char pad1[120];
   unsigned long long prim_next; // next primary index
-  long long active;             // particles held by lanes (speculative +)
+  char pad2[120];
+  long long active;             // particles held by lanes (current + lane stacks)
+  char pad3[120];
   int error;
   int abort;
   unsigned long long particles; // particles started (primaries + products)
   unsigned long long idle_iters;      // warp iterations without a particle
   unsigned long long busy_iters;      // warp iterations with at least one
   unsigned long long busy_lane_iters; // lanes holding a particle, summed over busy iterations
+  unsigned long long spilled;         // products sent to the shared ring
 };
 
 // ------------------------------------------------------------------------

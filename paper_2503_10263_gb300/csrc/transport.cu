@@ -151,13 +151,35 @@ struct EventOut {
   unsigned long long recoil, excit;       // per-lane energy sums (2^-24 eV)
 };
 
-// Ring access for products, made where they are created (products are rare:
-// one reservation per ionization).
+// Products of a lane's own events stay on a short stack in the lane's local
+// memory and are followed depth first after the current particle, as in the
+// paper's particle list; only when the stack is full, or once the primaries
+// are used up (so idle lanes can share the remaining work), do they go to the
+// shared ring.
+constexpr int STK = 4;
+struct LaneStack {
+  Lane s[STK];
+  int n;
+};
+
 struct RingPort {
   const Ring* R;
   Control* ctl;
   unsigned long long deadline;
+  bool local;              // primaries remain: keep products on the lane stack
+  unsigned long long spilled;
 };
+
+__device__ __forceinline__ void emit(RingPort& port, LaneStack& stk, const Lane& p) {
+  if (port.local && stk.n < STK) {
+    stk.s[stk.n++] = p;
+    atomicAdd((unsigned long long*)&port.ctl->active, 1ULL);   // held by this lane
+  } else {
+    unsigned long long pos = atomicAdd(&port.ctl->tail, 1ULL);
+    ring_put(*port.R, port.ctl, pos, p, port.deadline);
+    port.spilled += 1;
+  }
+}
 
 template <bool F32>
 __device__ __forceinline__ void die(const Params& P, Shared& S, Lane& L, int reason, int slot) {
@@ -178,7 +200,8 @@ __device__ __forceinline__ void thermal(const Params& P, const unsigned long lon
 }
 
 template <bool F32>
-__device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o, const RingPort& port) {
+__device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o, RingPort& port,
+                      LaneStack& stk) {
   using T = RT<F32>;
   using R = typename T::R;
   o.alive = true;
@@ -466,10 +489,7 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o, const Ri
     c.tal = 0.0; c.pid = L.pid; c.ev = 0; c.sp = SP_E;
     const bool keep_e = wq >= P.ecut_q;
     if (!keep_e) die<F32>(P, S, c, R_CUTOFF, L_E_CUTOFF);
-    const int nprod = (keep_e ? 1 : 0) + (ch.sout >= 0 ? 1 : 0);
-    unsigned long long pos = 0;
-    if (nprod) pos = atomicAdd(&port.ctl->tail, (unsigned long long)nprod);
-    if (keep_e) ring_put(*port.R, port.ctl, pos++, c, port.deadline);
+    else emit(port, stk, c);
     // ion with a thermal target's velocity (no recoil)
     if (ch.sout >= 0) {
       Lane ion;
@@ -482,7 +502,7 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o, const Ri
       sadd(&S.ledger[L_E_IN_THERMAL], ion.eq);
       sadd(&S.ledger[L_BIRTHS + ch.sout], 1);
       sadd(&S.ledger[L_N_SPAWN_ION], 1);
-      ring_put(*port.R, port.ctl, pos, ion, port.deadline);
+      emit(port, stk, ion);
     }
     L.eq = eq1;
     L.mu = (double)mu_p;
@@ -556,6 +576,10 @@ __global__ void __launch_bounds__(256) transport_kernel(const Params Pk, Ring R,
   port.R = &R;
   port.ctl = ctl;
   port.deadline = deadline;
+  port.local = true;
+  port.spilled = 0;
+  LaneStack stk;
+  stk.n = 0;
 
   for (long long iter = 0;; ++iter) {
     if ((iter & 63) == 0) {
@@ -573,6 +597,25 @@ __global__ void __launch_bounds__(256) transport_kernel(const Params Pk, Ring R,
         }
       }
       if (__shfl_sync(FULL, stop, 0)) break;
+      port.local = ld_relaxed(&ctl->prim_next) < (unsigned long long)P.n_prim;
+    }
+
+    // ---- a lane whose particle ended continues with its own products ----
+    if (!has && stk.n > 0) {
+      L = stk.s[--stk.n];
+      has = true;
+      started += 1;
+      // once the primaries are used up, hand the rest of the stack to the
+      // shared ring so idle lanes can take it (counted there, not here)
+      if (!port.local && stk.n > 0) {
+        const int m = stk.n;
+        unsigned long long pos = atomicAdd(&ctl->tail, (unsigned long long)m);
+        for (int i = 0; i < m; ++i) ring_put(R, ctl, pos + i, stk.s[i], deadline);
+        stk.n = 0;
+        port.spilled += m;
+        __threadfence();
+        atomicAdd((unsigned long long*)&ctl->active, (unsigned long long)(-(long long)m));
+      }
     }
 
     // ---- idle lanes take work: products from the ring first, then primaries ----
@@ -680,7 +723,7 @@ __global__ void __launch_bounds__(256) transport_kernel(const Params Pk, Ring R,
     // ---- one event ----
     bool died = false;
     if (has) {
-      event<F32>(P, S, L, o, port);
+      event<F32>(P, S, L, o, port, stk);
       if (!o.alive) { has = false; died = true; }
     }
 
@@ -702,8 +745,10 @@ __global__ void __launch_bounds__(256) transport_kernel(const Params Pk, Ring R,
 
   // ---- flush per-lane and per-block counters ----
   unsigned long long f = o.flights, c = o.colls, st = started, rc = o.recoil, ex = o.excit;
+  unsigned long long sp = port.spilled;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
+    sp += __shfl_down_sync(FULL, sp, off);
     f += __shfl_down_sync(FULL, f, off);
     c += __shfl_down_sync(FULL, c, off);
     st += __shfl_down_sync(FULL, st, off);
@@ -712,6 +757,7 @@ __global__ void __launch_bounds__(256) transport_kernel(const Params Pk, Ring R,
   }
   if (lane == 0) {
     atomicAdd(&ctl->idle_iters, idle_iters);
+    atomicAdd(&ctl->spilled, sp);
     atomicAdd(&ctl->busy_iters, busy_iters);
     atomicAdd(&ctl->busy_lane_iters, busy_lane_iters);
     atomicAdd(&S.ledger[L_N_FLIGHT], f);
