@@ -23,7 +23,8 @@ namespace karl {
 cudaError_t launch_transport(bool f32, const Params& P, const Ring& R, Control* ctl,
                              const volatile int* cancel, unsigned long long timeout_ns, int grid,
                              int block, cudaStream_t st);
-cudaError_t transport_occupancy(bool f32, int block, int* blocks_per_sm);
+cudaError_t transport_occupancy(bool f32, const Params& P, int block, int* blocks_per_sm);
+cudaError_t transport_setup();
 }  // namespace karl
 
 using namespace karl;
@@ -77,6 +78,9 @@ struct karl_ctx {
   std::vector<double> loss;
   // device tables
   DevBuf<double> d_nseg, d_colgas, d_sig, d_sig_t, d_frate, d_fcol, d_time1;
+  DevBuf<int> d_ginv;
+  int nq = 0;
+  double colmax = 0;
   DevBuf<float> d_sigf;
   cudaStream_t cancel_stream = nullptr;
   // device work buffers
@@ -340,6 +344,9 @@ void base_params(const karl_ctx* c, Params& P, const karl_run_opts* o, int pass)
   P.dz = c->dz;
   P.nseg = c->d_nseg.p;
   P.colgas = c->d_colgas.p;
+  P.ginv = c->nq > 0 ? c->d_ginv.p : nullptr;
+  P.nq = c->nq;
+  P.nq_over_colmax = c->colmax > 0 ? (double)c->nq / c->colmax : 0.0;
   P.n_energy = c->n_energy;
   P.e_min = c->e_min;
   P.inv_e_min = 1.0 / c->e_min;
@@ -400,11 +407,7 @@ karl_status run_one_pass(karl_ctx* ctx, const karl_primaries* pr, const karl_run
   if (per_primary) CK(ctx->d_pp.ensure((size_t)std::max<int64_t>(pr->n, 1)));
   bool f32 = o->precision == KARL_FP32;
   int block = o->block_size > 0 ? o->block_size : 256;
-  int bps = 0;
-  CK(transport_occupancy(f32, block, &bps));
-  if (o->blocks_per_sm > 0) bps = std::min(bps, (int)o->blocks_per_sm);
-  if (bps < 1) bps = 1;
-  int grid = ctx->num_sms * bps;
+  int grid = 0;
   unsigned long long cap = ctx->ring_cap ? ctx->ring_cap : (1ULL << 22);
   double timeout = o->timeout_s > 0 ? o->timeout_s : 600.0;
   for (int attempt = 0; attempt < 4; ++attempt) {
@@ -445,6 +448,13 @@ karl_status run_one_pass(karl_ctx* ctx, const karl_primaries* pr, const karl_run
     P.ledger = ctx->d_ledger.p;
     P.chan_count = ctx->d_chan.p;
     P.per_primary = per_primary ? ctx->d_pp.p : nullptr;
+    if (grid == 0) {
+      int bps = 0;
+      CK(transport_occupancy(f32, P, block, &bps));
+      if (o->blocks_per_sm > 0) bps = std::min(bps, (int)o->blocks_per_sm);
+      if (bps < 1) bps = 1;
+      grid = ctx->num_sms * bps;
+    }
 
     Ring R;
     R.z = ctx->r_z.p; R.eq = ctx->r_eq.p; R.mu = ctx->r_mu.p; R.node = ctx->r_node.p;
@@ -660,9 +670,18 @@ karl_status karl_create(const karl_geometry* g, const karl_xs* x, karl_ctx** out
   } catch (...) {
     return bail(KARL_ENOMEM);
   }
-  // gas column to each face
+  // gas column to each face, and its inverse on nq even steps: ginv[q] is the
+  // largest face k with col[k] <= q * colmax / nq (a search bracket)
   std::vector<double> col(ctx->nz + 1, 0.0);
   for (int j = 0; j < ctx->nz; ++j) col[j + 1] = col[j] + ctx->nseg[j] * ctx->dz;
+  ctx->colmax = col[ctx->nz];
+  ctx->nq = ctx->colmax > 0 ? std::min(8192, std::max(1024, 2 * ctx->nz)) : 0;
+  std::vector<int> ginv(ctx->nq + 1, 0);
+  for (int q = 0, k = 0; q <= ctx->nq; ++q) {
+    double c = (double)q * ctx->colmax / ctx->nq;
+    while (k < ctx->nz && col[k + 1] <= c) ++k;
+    ginv[q] = k;
+  }
   // [node][channel] copies for the transport kernel (all channels of one node
   // in adjacent words), channel-major copy for the field builder
   std::vector<double> sig_t(ctx->sigma.size());
@@ -676,16 +695,18 @@ karl_status karl_create(const karl_geometry* g, const karl_xs* x, karl_ctx** out
   size_t nsig = std::max<size_t>(ctx->sigma.size(), 1);
   if (ctx->d_nseg.ensure(ctx->nz) || ctx->d_colgas.ensure(ctx->nz + 1) ||
       ctx->d_sig.ensure(nsig) || ctx->d_sig_t.ensure(nsig) || ctx->d_sigf.ensure(nsig) ||
-      ctx->d_ledger.ensure(LEDGER))
+      ctx->d_ledger.ensure(LEDGER) || ctx->d_ginv.ensure(ctx->nq + 1))
     return bail(KARL_ENOMEM);
   if (cudaMemcpy(ctx->d_nseg.p, ctx->nseg.data(), ctx->nz * 8, cudaMemcpyHostToDevice) ||
       cudaMemcpy(ctx->d_colgas.p, col.data(), (ctx->nz + 1) * 8, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(ctx->d_ginv.p, ginv.data(), (ctx->nq + 1) * sizeof(int), cudaMemcpyHostToDevice) ||
       (ctx->sigma.size() &&
        (cudaMemcpy(ctx->d_sig.p, ctx->sigma.data(), ctx->sigma.size() * 8, cudaMemcpyHostToDevice) ||
         cudaMemcpy(ctx->d_sig_t.p, sig_t.data(), sig_t.size() * 8, cudaMemcpyHostToDevice) ||
         cudaMemcpy(ctx->d_sigf.p, sigf.data(), sigf.size() * 4, cudaMemcpyHostToDevice))))
     return bail(KARL_ECUDA);
-  if (cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) ||
+  if (transport_setup() != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) ||
       cudaStreamCreateWithFlags(&ctx->cancel_stream, cudaStreamNonBlocking) ||
       cudaMalloc(&ctx->d_ctl, sizeof(Control)) || cudaMalloc(&ctx->d_cancel, sizeof(int)) ||
       cudaHostAlloc(&ctx->h_cancel, sizeof(int), cudaHostAllocDefault) ||
@@ -859,6 +880,7 @@ void karl_destroy(karl_ctx* ctx) {
   if (ctx->d_cancel) cudaFree(ctx->d_cancel);
   if (ctx->cancel_stream) cudaStreamDestroy(ctx->cancel_stream);
   ctx->d_sig_t.release();
+  ctx->d_ginv.release();
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);

@@ -41,6 +41,9 @@ struct Params {
   double L, dz;
   const double* nseg;      // [nz] gas density per segment
   const double* colgas;    // [nz+1] column to each face, sum_{i<k} n_i dz
+  const int* ginv;         // [nq+1] largest face k with colgas[k] <= q * colmax / nq
+  int nq;
+  double nq_over_colmax;   // nq / colgas[nz] (0 if the column is empty)
   // recombination target fields of pass 2, per channel (NULL if unused)
   const double* frate[MAXCH];   // [nz] partner field per segment
   const double* fcol[MAXCH];    // [nz+1] its column to each face

@@ -151,34 +151,39 @@ struct EventOut {
   unsigned long long recoil, excit;       // per-lane energy sums (2^-24 eV)
 };
 
-// Products of a lane's own events stay on a short stack in the lane's local
-// memory and are followed depth first after the current particle, as in the
-// paper's particle list; only when the stack is full, or once the primaries
-// are used up (so idle lanes can share the remaining work), do they go to the
-// shared ring.
-constexpr int STK = 4;
-struct LaneStack {
-  Lane s[STK];
-  int n;
+// Products of a warp's events go to a short last-in-first-out queue in the
+// warp's shared memory and are taken by the warp's idle lanes, so a primary's
+// products are followed close to depth first (the paper follows a particle
+// list).  The queue spills to the shared ring when full, and once the
+// primaries are used up, so idle warps elsewhere can share the last work.
+constexpr int WQ = 32;
+constexpr int WARPS = 8;                  // 256-thread blocks
+struct WarpQueue {
+  Lane s[WQ];
+  int top;
 };
 
 struct RingPort {
   const Ring* R;
   Control* ctl;
   unsigned long long deadline;
-  bool local;              // primaries remain: keep products on the lane stack
+  WarpQueue* q;
+  bool local;              // primaries remain: keep products in the warp queue
   unsigned long long spilled;
 };
 
-__device__ __forceinline__ void emit(RingPort& port, LaneStack& stk, const Lane& p) {
-  if (port.local && stk.n < STK) {
-    stk.s[stk.n++] = p;
-    atomicAdd((unsigned long long*)&port.ctl->active, 1ULL);   // held by this lane
-  } else {
-    unsigned long long pos = atomicAdd(&port.ctl->tail, 1ULL);
-    ring_put(*port.R, port.ctl, pos, p, port.deadline);
-    port.spilled += 1;
+__device__ __forceinline__ void emit(RingPort& port, const Lane& p) {
+  if (port.local) {
+    const int i = atomicAdd(&port.q->top, 1);
+    if (i < WQ) {
+      port.q->s[i] = p;
+      atomicAdd((unsigned long long*)&port.ctl->active, 1ULL);   // held by this warp
+      return;
+    }
   }
+  unsigned long long pos = atomicAdd(&port.ctl->tail, 1ULL);
+  ring_put(*port.R, port.ctl, pos, p, port.deadline);
+  port.spilled += 1;
 }
 
 template <bool F32>
@@ -200,8 +205,7 @@ __device__ __forceinline__ void thermal(const Params& P, const unsigned long lon
 }
 
 template <bool F32>
-__device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o, RingPort& port,
-                      LaneStack& stk) {
+__device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o, RingPort& port) {
   using T = RT<F32>;
   using R = typename T::R;
   o.alive = true;
@@ -278,17 +282,34 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o, RingPort
   const double gasd = (double)gas;
 
   // G(k) = optical-depth column of the whole rate to face k
+  // (the column tables may have been staged into shared memory: plain loads)
   auto colsum = [&](int k) -> double {
-    double g = gasd * __ldg(P.colgas + k);
-    if (nrec > 0) g += rc0 * __ldg(rcol0 + k);
-    if (nrec > 1) g += rc1 * __ldg(rcol1 + k);
+    double g = gasd * P.colgas[k];
+    if (nrec > 0) g += rc0 * rcol0[k];
+    if (nrec > 1) g += rc1 * rcol1[k];
     return g;
   };
   auto segrate = [&](int j) -> double {
-    double r = gasd * __ldg(P.nseg + j);
-    if (nrec > 0) r += rc0 * __ldg(rrate0 + j);
-    if (nrec > 1) r += rc1 * __ldg(rrate1 + j);
+    double r = gasd * P.nseg[j];
+    if (nrec > 0) r += rc0 * rrate0[j];
+    if (nrec > 1) r += rc1 * rrate1[j];
     return r;
+  };
+  // Search bracket from the inverse gas-column table: exact when only the gas
+  // contributes (pass 1), otherwise widened to the whole admissible range.
+  auto bracket = [&](double target, int lo_min, int hi_max, int& lo, int& hi) {
+    lo = lo_min;
+    hi = hi_max;
+    if (nrec == 0 && gasd > 0.0 && P.nq > 0) {
+      const double q = target / gasd * P.nq_over_colmax;
+      if (q >= 0.0 && q < (double)P.nq) {
+        const int qi = (int)q;
+        const int a = P.ginv[qi] - 1, b = P.ginv[qi + 1] + 1;
+        if (a > lo) lo = a;
+        if (b < hi) hi = b;
+        if (lo >= hi) { lo = lo_min; hi = hi_max; }
+      }
+    }
   };
 
   double zc;
@@ -303,8 +324,7 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o, RingPort
     for (int c = 0; c < MAXSPCH; ++c) {
       if (c >= nsc) break;
       const int kk = P.sc[s][c];
-      r += (double)coef[c] * (P.ch[kk].kind == RECOMBINATION ? __ldg(P.frate[kk] + jc)
-                                                               : __ldg(P.nseg + jc));
+      r += (double)coef[c] * (P.ch[kk].kind == RECOMBINATION ? P.frate[kk][jc] : P.nseg[jc]);
     }
     if (!(r > 0.0)) {
       die<F32>(P, S, L, R_STALLED, L_E_STALLED);
@@ -331,7 +351,9 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o, RingPort
         zc = P.L;
         jc = nz - 1;
       } else {
-        int lo = j0, hi = nz;                  // G(lo) <= target < G(hi)
+        int lo, hi;                            // G(lo) <= target < G(hi)
+        bracket(target, j0, nz, lo, hi);
+        if (!(colsum(lo) <= target) || !(target < colsum(hi))) { lo = j0; hi = nz; }
         while (hi - lo > 1) {
           int mid = (lo + hi) >> 1;
           if (colsum(mid) <= target) lo = mid; else hi = mid;
@@ -351,7 +373,9 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o, RingPort
         zc = 0.0;
         jc = 0;
       } else {
-        int lo = 0, hi = j0 + 1;               // G(lo) < target <= G(hi)
+        int lo, hi;                            // G(lo) < target <= G(hi)
+        bracket(target, 0, j0 + 1, lo, hi);
+        if (!(colsum(lo) < target) || !(target <= colsum(hi))) { lo = 0; hi = j0 + 1; }
         while (hi - lo > 1) {
           int mid = (lo + hi) >> 1;
           if (colsum(mid) >= target) hi = mid; else lo = mid;
@@ -415,8 +439,7 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o, RingPort
   o.colls += 1;
   auto chan_rate = [&](int c) -> double {
     const int kk = P.sc[s][c];
-    return (double)coef[c] * (P.ch[kk].kind == RECOMBINATION ? __ldg(P.frate[kk] + jc)
-                                                               : __ldg(P.nseg + jc));
+    return (double)coef[c] * (P.ch[kk].kind == RECOMBINATION ? P.frate[kk][jc] : P.nseg[jc]);
   };
   double rtot = 0.0;
 #pragma unroll
@@ -489,7 +512,7 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o, RingPort
     c.tal = 0.0; c.pid = L.pid; c.ev = 0; c.sp = SP_E;
     const bool keep_e = wq >= P.ecut_q;
     if (!keep_e) die<F32>(P, S, c, R_CUTOFF, L_E_CUTOFF);
-    else emit(port, stk, c);
+    else emit(port, c);
     // ion with a thermal target's velocity (no recoil)
     if (ch.sout >= 0) {
       Lane ion;
@@ -502,7 +525,7 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o, RingPort
       sadd(&S.ledger[L_E_IN_THERMAL], ion.eq);
       sadd(&S.ledger[L_BIRTHS + ch.sout], 1);
       sadd(&S.ledger[L_N_SPAWN_ION], 1);
-      emit(port, stk, ion);
+      emit(port, ion);
     }
     L.eq = eq1;
     L.mu = (double)mu_p;
@@ -546,21 +569,61 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o, RingPort
 // ---------------------------------------------------------------------------
 // persistent kernel
 
+// Copy the column tables (and the pass-2 recombination fields) into dynamic
+// shared memory when they fit; the event code reads them through P's pointers.
+__device__ void stage_tables(Params& SP, const Params& Pk, double* dyn, int dyn_doubles) {
+  const int nz = Pk.nz;
+  int need = (2 * nz + 1) + (Pk.nq + 1 + 1) / 2 + 1;
+  int nrecf = 0;
+  for (int k = 0; k < Pk.nch; ++k)
+    if (Pk.fcol[k]) { need += 2 * nz + 1; ++nrecf; }
+  if (need > dyn_doubles) return;                   // stay in global memory
+  double* col = dyn;
+  double* nseg = col + (nz + 1);
+  int* ginv = (int*)(nseg + nz);
+  double* next = (double*)(ginv + ((Pk.nq + 2) & ~1));
+  for (int i = threadIdx.x; i <= nz; i += blockDim.x) col[i] = Pk.colgas[i];
+  for (int i = threadIdx.x; i < nz; i += blockDim.x) nseg[i] = Pk.nseg[i];
+  if (Pk.ginv)
+    for (int i = threadIdx.x; i <= Pk.nq; i += blockDim.x) ginv[i] = Pk.ginv[i];
+  if (threadIdx.x == 0) {
+    SP.colgas = col;
+    SP.nseg = nseg;
+    if (Pk.ginv) SP.ginv = ginv;
+  }
+  for (int k = 0; k < Pk.nch; ++k) {
+    if (!Pk.fcol[k]) continue;
+    double* fc = next;
+    double* fr = next + (nz + 1);
+    next += 2 * nz + 1;
+    for (int i = threadIdx.x; i <= nz; i += blockDim.x) fc[i] = Pk.fcol[k][i];
+    for (int i = threadIdx.x; i < nz; i += blockDim.x) fr[i] = Pk.frate[k][i];
+    if (threadIdx.x == 0) { SP.fcol[k] = fc; SP.frate[k] = fr; }
+  }
+}
+
 template <bool F32>
 __global__ void __launch_bounds__(256) transport_kernel(const Params Pk, Ring R, Control* ctl,
                                                         const volatile int* cancel,
-                                                        unsigned long long timeout_ns) {
+                                                        unsigned long long timeout_ns,
+                                                        int dyn_doubles) {
   const unsigned long long deadline = globaltimer_ns() + timeout_ns;
+  extern __shared__ double dyn[];
   __shared__ Shared S;
   __shared__ Params SP;
+  __shared__ WarpQueue wq[WARPS];
   if (threadIdx.x == 0) SP = Pk;
   for (int i = threadIdx.x; i < LEDGER; i += blockDim.x) S.ledger[i] = 0;
   for (int i = threadIdx.x; i < MAXCH; i += blockDim.x) S.chan[i] = 0;
+  if (threadIdx.x < WARPS) wq[threadIdx.x].top = 0;
+  __syncthreads();
+  stage_tables(SP, Pk, dyn, dyn_doubles);
   __syncthreads();
   const Params& P = SP;
 
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
+  WarpQueue& Q = wq[threadIdx.x >> 5];
   bool has = false;
   Lane L;
   EventOut o;
@@ -576,10 +639,9 @@ __global__ void __launch_bounds__(256) transport_kernel(const Params Pk, Ring R,
   port.R = &R;
   port.ctl = ctl;
   port.deadline = deadline;
+  port.q = &Q;
   port.local = true;
   port.spilled = 0;
-  LaneStack stk;
-  stk.n = 0;
 
   for (long long iter = 0;; ++iter) {
     if ((iter & 63) == 0) {
@@ -600,25 +662,43 @@ __global__ void __launch_bounds__(256) transport_kernel(const Params Pk, Ring R,
       port.local = ld_relaxed(&ctl->prim_next) < (unsigned long long)P.n_prim;
     }
 
-    // ---- a lane whose particle ended continues with its own products ----
-    if (!has && stk.n > 0) {
-      L = stk.s[--stk.n];
-      has = true;
-      started += 1;
-      // once the primaries are used up, hand the rest of the stack to the
-      // shared ring so idle lanes can take it (counted there, not here)
-      if (!port.local && stk.n > 0) {
-        const int m = stk.n;
-        unsigned long long pos = atomicAdd(&ctl->tail, (unsigned long long)m);
-        for (int i = 0; i < m; ++i) ring_put(R, ctl, pos + i, stk.s[i], deadline);
-        stk.n = 0;
-        port.spilled += m;
-        __threadfence();
-        atomicAdd((unsigned long long*)&ctl->active, (unsigned long long)(-(long long)m));
+    // ---- idle lanes take the warp's own products first (newest first) ----
+    __syncwarp();
+    {
+      const unsigned need0 = __ballot_sync(FULL, !has);
+      int top = Q.top;
+      if (top > WQ) top = WQ;
+      const int take = min(__popc(need0), top);
+      if (!has) {
+        const int rank = __popc(need0 & lt);
+        if (rank < take) {
+          L = Q.s[top - 1 - rank];
+          has = true;
+          started += 1;
+        }
       }
+      int left = top - take;
+      // once the primaries are used up, move what is left to the shared ring
+      // where idle warps can take it (counted there instead of here)
+      if (!port.local && left > 0) {
+        unsigned long long pos = 0;
+        if (lane == 0) pos = atomicAdd(&ctl->tail, (unsigned long long)left);
+        pos = __shfl_sync(FULL, pos, 0);
+        if (lane < left) ring_put(R, ctl, pos + lane, Q.s[lane], deadline);
+        __syncwarp();
+        if (lane == 0) {
+          __threadfence();
+          atomicAdd((unsigned long long*)&ctl->active, (unsigned long long)(-(long long)left));
+          port.spilled += left;
+        }
+        left = 0;
+      }
+      __syncwarp();
+      if (lane == 0) Q.top = left;
+      __syncwarp();
     }
 
-    // ---- idle lanes take work: products from the ring first, then primaries ----
+    // ---- other idle lanes take work: products from the ring, then primaries ----
     const unsigned need = __ballot_sync(FULL, !has);
     if (need) {
       const int k = __popc(need);
@@ -723,9 +803,11 @@ __global__ void __launch_bounds__(256) transport_kernel(const Params Pk, Ring R,
     // ---- one event ----
     bool died = false;
     if (has) {
-      event<F32>(P, S, L, o, port, stk);
+      event<F32>(P, S, L, o, port);
       if (!o.alive) { has = false; died = true; }
     }
+    __syncwarp();
+    if (lane == 0 && Q.top > WQ) Q.top = WQ;          // pushes past the end went to the ring
 
     // ---- channel counts, one shared-memory add per distinct channel per warp ----
     const unsigned mc = __ballot_sync(FULL, o.chan >= 0);
@@ -776,22 +858,45 @@ __global__ void __launch_bounds__(256) transport_kernel(const Params Pk, Ring R,
 // ---------------------------------------------------------------------------
 // host-callable launchers (used by the C ABI in karl_abi.cu)
 
+// dynamic shared memory for the staged tables: at most this much per block
+constexpr int DYN_MAX_BYTES = 120 * 1024;
+
+// Doubles of dynamic shared memory the staged tables of P need (0: too big,
+// read them from global memory).
+int transport_dyn_doubles(const Params& P) {
+  int need = (2 * P.nz + 1) + (P.nq + 1 + 1) / 2 + 1;
+  for (int k = 0; k < P.nch; ++k)
+    if (P.fcol[k]) need += 2 * P.nz + 1;
+  return need * 8 <= DYN_MAX_BYTES ? need : 0;
+}
+
 cudaError_t launch_transport(bool f32, const Params& P, const Ring& R, Control* ctl,
                              const volatile int* cancel, unsigned long long timeout_ns, int grid,
                              int block, cudaStream_t st) {
+  const int dd = transport_dyn_doubles(P);
+  const size_t bytes = (size_t)dd * 8;
   if (f32)
-    transport_kernel<true><<<grid, block, 0, st>>>(P, R, ctl, cancel, timeout_ns);
+    transport_kernel<true><<<grid, block, bytes, st>>>(P, R, ctl, cancel, timeout_ns, dd);
   else
-    transport_kernel<false><<<grid, block, 0, st>>>(P, R, ctl, cancel, timeout_ns);
+    transport_kernel<false><<<grid, block, bytes, st>>>(P, R, ctl, cancel, timeout_ns, dd);
   return cudaGetLastError();
 }
 
-cudaError_t transport_occupancy(bool f32, int block, int* blocks_per_sm) {
+cudaError_t transport_setup() {
+  cudaError_t e = cudaFuncSetAttribute(transport_kernel<true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, DYN_MAX_BYTES);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(transport_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              DYN_MAX_BYTES);
+}
+
+cudaError_t transport_occupancy(bool f32, const Params& P, int block, int* blocks_per_sm) {
+  const size_t bytes = (size_t)transport_dyn_doubles(P) * 8;
   if (f32)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, transport_kernel<true>,
-                                                         block, 0);
+                                                         block, bytes);
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, transport_kernel<false>,
-                                                       block, 0);
+                                                       block, bytes);
 }
 
 }  // namespace karl
