@@ -77,7 +77,7 @@ struct karl_ctx {
   std::vector<int> kind, sin, sout;
   std::vector<double> loss;
   // device tables
-  DevBuf<double> d_nseg, d_colgas, d_sig, d_sig_t, d_frate, d_fcol, d_time1;
+  DevBuf<double> d_nseg, d_colgas, d_faces, d_sig, d_sig_t, d_frate, d_fcol, d_time1;
   DevBuf<int> d_ginv;
   int nq = 0;
   double colmax = 0;
@@ -94,8 +94,7 @@ struct karl_ctx {
   DevBuf<double> r_z, r_mu, r_tal;
   DevBuf<long long> r_eq;
   DevBuf<unsigned long long> r_node, r_pid, r_seq;
-  DevBuf<unsigned> r_ev;
-  DevBuf<uint8_t> r_sp;
+  DevBuf<unsigned> r_ev, r_sj;
   unsigned long long ring_cap = 0;
   Control* d_ctl = nullptr;
   int* h_cancel = nullptr;      // pinned host word, source of the copy that cancels
@@ -331,7 +330,7 @@ karl_status ensure_ring(karl_ctx* ctx, unsigned long long cap) {
   CK(ctx->r_pid.ensure(n));
   CK(ctx->r_seq.ensure(n));
   CK(ctx->r_ev.ensure(n));
-  CK(ctx->r_sp.ensure(n));
+  CK(ctx->r_sj.ensure(n));
   ctx->ring_cap = cap;
   return KARL_OK;
 }
@@ -344,6 +343,7 @@ void base_params(const karl_ctx* c, Params& P, const karl_run_opts* o, int pass)
   P.dz = c->dz;
   P.nseg = c->d_nseg.p;
   P.colgas = c->d_colgas.p;
+  P.faces = c->d_faces.p;
   P.ginv = c->nq > 0 ? c->d_ginv.p : nullptr;
   P.nq = c->nq;
   P.nq_over_colmax = c->colmax > 0 ? (double)c->nq / c->colmax : 0.0;
@@ -383,6 +383,7 @@ void base_params(const karl_ctx* c, Params& P, const karl_run_opts* o, int pass)
   P.ecut_q = (long long)std::floor(c->e_cut * Q_ENERGY);
   P.max_coll = c->max_coll;
   P.max_life = c->max_life;
+  P.track_time = std::isfinite(c->max_life) ? 1 : 0;
   P.ntb = c->ntb;
   P.tb_scale = c->ntb / std::log(c->e_max / c->e_min);
   P.nspec = c->nspec;
@@ -458,7 +459,7 @@ karl_status run_one_pass(karl_ctx* ctx, const karl_primaries* pr, const karl_run
 
     Ring R;
     R.z = ctx->r_z.p; R.eq = ctx->r_eq.p; R.mu = ctx->r_mu.p; R.node = ctx->r_node.p;
-    R.tal = ctx->r_tal.p; R.pid = ctx->r_pid.p; R.ev = ctx->r_ev.p; R.sp = ctx->r_sp.p;
+    R.tal = ctx->r_tal.p; R.pid = ctx->r_pid.p; R.ev = ctx->r_ev.p; R.sj = ctx->r_sj.p;
     R.seq = ctx->r_seq.p; R.cap = ctx->ring_cap; R.mask = ctx->ring_cap - 1;
 
     CK(cudaMemsetAsync(ctx->d_cancel, 0, sizeof(int), st));
@@ -677,6 +678,9 @@ karl_status karl_create(const karl_geometry* g, const karl_xs* x, karl_ctx** out
   ctx->colmax = col[ctx->nz];
   ctx->nq = ctx->colmax > 0 ? std::min(8192, std::max(1024, 2 * ctx->nz)) : 0;
   std::vector<int> ginv(ctx->nq + 1, 0);
+  std::vector<double> faces(ctx->nz + 1);
+  for (int k = 0; k < ctx->nz; ++k) faces[k] = (double)k * ctx->dz;
+  faces[ctx->nz] = ctx->L;
   for (int q = 0, k = 0; q <= ctx->nq; ++q) {
     double c = (double)q * ctx->colmax / ctx->nq;
     while (k < ctx->nz && col[k + 1] <= c) ++k;
@@ -694,11 +698,13 @@ karl_status karl_create(const karl_geometry* g, const karl_xs* x, karl_ctx** out
     }
   size_t nsig = std::max<size_t>(ctx->sigma.size(), 1);
   if (ctx->d_nseg.ensure(ctx->nz) || ctx->d_colgas.ensure(ctx->nz + 1) ||
+      ctx->d_faces.ensure(ctx->nz + 1) ||
       ctx->d_sig.ensure(nsig) || ctx->d_sig_t.ensure(nsig) || ctx->d_sigf.ensure(nsig) ||
       ctx->d_ledger.ensure(LEDGER) || ctx->d_ginv.ensure(ctx->nq + 1))
     return bail(KARL_ENOMEM);
   if (cudaMemcpy(ctx->d_nseg.p, ctx->nseg.data(), ctx->nz * 8, cudaMemcpyHostToDevice) ||
       cudaMemcpy(ctx->d_colgas.p, col.data(), (ctx->nz + 1) * 8, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(ctx->d_faces.p, faces.data(), (ctx->nz + 1) * 8, cudaMemcpyHostToDevice) ||
       cudaMemcpy(ctx->d_ginv.p, ginv.data(), (ctx->nq + 1) * sizeof(int), cudaMemcpyHostToDevice) ||
       (ctx->sigma.size() &&
        (cudaMemcpy(ctx->d_sig.p, ctx->sigma.data(), ctx->sigma.size() * 8, cudaMemcpyHostToDevice) ||
@@ -874,13 +880,14 @@ void karl_destroy(karl_ctx* ctx) {
   ctx->d_density.release(); ctx->d_current.release(); ctx->d_field.release(); ctx->d_bad.release();
   ctx->r_z.release(); ctx->r_mu.release(); ctx->r_tal.release(); ctx->r_eq.release();
   ctx->r_node.release(); ctx->r_pid.release(); ctx->r_seq.release(); ctx->r_ev.release();
-  ctx->r_sp.release();
+  ctx->r_sj.release();
   if (ctx->d_ctl) cudaFree(ctx->d_ctl);
   if (ctx->h_cancel) cudaFreeHost(ctx->h_cancel);
   if (ctx->d_cancel) cudaFree(ctx->d_cancel);
   if (ctx->cancel_stream) cudaStreamDestroy(ctx->cancel_stream);
   ctx->d_sig_t.release();
   ctx->d_ginv.release();
+  ctx->d_faces.release();
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);

@@ -41,6 +41,7 @@ struct Params {
   double L, dz;
   const double* nseg;      // [nz] gas density per segment
   const double* colgas;    // [nz+1] column to each face, sum_{i<k} n_i dz
+  const double* faces;     // [nz+1] face positions k*dz (face nz = L exactly)
   const int* ginv;         // [nq+1] largest face k with colgas[k] <= q * colmax / nq
   int nq;
   double nq_over_colmax;   // nq / colgas[nz] (0 if the column is empty)
@@ -65,6 +66,7 @@ struct Params {
   long long ecut_q;
   unsigned max_coll;
   double max_life;
+  int track_time;               // a lifetime cap is set: accumulate time alive
   int ntb;
   double tb_scale;              // ntb / ln(e_max/e_min)
   int nspec;
@@ -100,7 +102,7 @@ struct Ring {
   double* tal;
   unsigned long long* pid;
   unsigned* ev;
-  uint8_t* sp;
+  unsigned* sj;                 // segment index << 8 | species
   unsigned long long* seq;      // per-cell sequence number (bounded MPMC ring)
   unsigned long long cap, mask;
 };

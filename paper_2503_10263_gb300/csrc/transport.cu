@@ -36,6 +36,10 @@ template <> struct RT<false> {
   static __device__ __forceinline__ R tab(const Params& P, int k, int i) {
     return __ldg(P.sig + (size_t)i * P.nch + k);      // [node][channel]
   }
+  static __device__ __forceinline__ R energy(long long eq) { return (double)eq * (1.0 / 16777216.0); }
+  static __device__ __forceinline__ long long quant_de(R de) {
+    return (long long)floor(de * 16777216.0 + 0.5);
+  }
 };
 template <> struct RT<true> {
   using R = float;
@@ -50,17 +54,27 @@ template <> struct RT<true> {
   static __device__ __forceinline__ R tab(const Params& P, int k, int i) {
     return __ldg(P.sigf + (size_t)i * P.nch + k);     // [node][channel]
   }
+  // energy from 2^-24 eV units with 32-bit conversions (below 65 keV)
+  static __device__ __forceinline__ R energy(long long eq) {
+    return eq < (1LL << 40) ? (float)(unsigned)(eq >> 8) * (1.0f / 65536.0f)
+                            : (float)eq * (1.0f / 16777216.0f);
+  }
+  static __device__ __forceinline__ long long quant_de(R de) {
+    const float x = de * 16777216.0f + 0.5f;
+    return x < 2.0e9f ? (long long)__float2int_rz(x) : (long long)x;
+  }
 };
 
 struct Lane {
   double z;
-  long long eq;
-  double mu;
-  unsigned long long node;
-  double tal;
-  unsigned long long pid;
-  unsigned ev;
-  int sp;
+  long long eq;                 // kinetic energy, 2^-24 eV
+  double mu;                    // pitch cosine
+  unsigned long long node;      // lineage id
+  double tal;                   // time alive (tracked only under a lifetime cap)
+  unsigned long long pid;       // primary id
+  unsigned ev;                  // collisions so far = index of the next flight
+  int sp;                       // species
+  int j;                        // segment holding z (carried from the last flight)
 };
 
 __device__ __forceinline__ double face(const Params& P, int k) {
@@ -117,7 +131,7 @@ __device__ bool ring_put(const Ring& R, Control* ctl, unsigned long long pos, co
   }
   size_t i = pos & R.mask;
   R.z[i] = p.z; R.eq[i] = p.eq; R.mu[i] = p.mu; R.node[i] = p.node; R.tal[i] = p.tal;
-  R.pid[i] = p.pid; R.ev[i] = p.ev; R.sp[i] = (uint8_t)p.sp;
+  R.pid[i] = p.pid; R.ev[i] = p.ev; R.sj[i] = ((unsigned)p.j << 8) | (unsigned)p.sp;
   st_release(cell, pos + 1);
   return true;
 }
@@ -136,7 +150,10 @@ __device__ bool ring_get(const Ring& R, Control* ctl, unsigned long long pos, La
   }
   size_t i = pos & R.mask;
   p.z = R.z[i]; p.eq = R.eq[i]; p.mu = R.mu[i]; p.node = R.node[i]; p.tal = R.tal[i];
-  p.pid = R.pid[i]; p.ev = R.ev[i]; p.sp = R.sp[i];
+  p.pid = R.pid[i]; p.ev = R.ev[i];
+  const unsigned sj = R.sj[i];
+  p.sp = (int)(sj & 0xffu);
+  p.j = (int)(sj >> 8);
   st_release(cell, pos + R.cap);
   return true;
 }
@@ -216,7 +233,7 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o, RingPort
     return;
   }
   const int s = L.sp;
-  const R e = (R)((double)L.eq * INV_Q_E);
+  const R e = T::energy(L.eq);
   const R v = speed<R>(e, (R)P.inv_mass[s]);
 
   unsigned long long w[4];
@@ -230,30 +247,13 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o, RingPort
   const int nsc = P.nsc[s];
   R coef[MAXSPCH];
   const R le = T::lg(e * (R)P.inv_e_min);       // ln(E / e_min), shared by both lookups
-  R lx = le * (R)P.inv_h;
+  const R lx = le * (R)P.inv_h;
   int ti = (int)floor(lx);
   R tf;
   if (ti < 0) { ti = 0; tf = (R)0; }
   else if (ti > P.n_energy - 2) { ti = P.n_energy - 2; tf = (R)1; }
   else { tf = lx - (R)ti; }
   R gas = (R)0;
-#pragma unroll
-  for (int c = 0; c < MAXSPCH; ++c) {
-    if (c >= nsc) break;
-    const int k = P.sc[s][c];
-    const ChanDev& ch = P.ch[k];
-    R cv;
-    if (ch.kind == RECOMBINATION && s != SP_E) {
-      cv = (R)1 / v;
-    } else if (L.eq > ch.thr_q) {
-      cv = ((R)1 - tf) * T::tab(P, k, ti) + tf * T::tab(P, k, ti + 1);
-    } else {
-      cv = (R)0;
-    }
-    coef[c] = cv;
-    if (ch.kind != RECOMBINATION) gas += cv;
-  }
-  // recombination terms of this flight (at most two): coefficient and field
   int nrec = 0;
   double rc0 = 0.0, rc1 = 0.0;
   const double* rcol0 = P.colgas;
@@ -263,10 +263,23 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o, RingPort
 #pragma unroll
   for (int c = 0; c < MAXSPCH; ++c) {
     if (c >= nsc) break;
-    const int kk = P.sc[s][c];
-    if (P.ch[kk].kind == RECOMBINATION) {
-      if (nrec == 0) { rc0 = (double)coef[c]; rcol0 = P.fcol[kk]; rrate0 = P.frate[kk]; }
-      else { rc1 = (double)coef[c]; rcol1 = P.fcol[kk]; rrate1 = P.frate[kk]; }
+    const int k = P.sc[s][c];
+    const ChanDev& ch = P.ch[k];
+    R cv;
+    if (ch.kind == RECOMBINATION && s != SP_E) {
+      cv = (R)1 / v;
+    } else if (L.eq > ch.thr_q) {
+      const R a0 = T::tab(P, k, ti);
+      cv = a0 + tf * (T::tab(P, k, ti + 1) - a0);
+    } else {
+      cv = (R)0;
+    }
+    coef[c] = cv;
+    if (ch.kind != RECOMBINATION) {
+      gas += cv;
+    } else {
+      if (nrec == 0) { rc0 = (double)cv; rcol0 = P.fcol[k]; rrate0 = P.frate[k]; }
+      else { rc1 = (double)cv; rcol1 = P.fcol[k]; rrate1 = P.frate[k]; }
       ++nrec;
     }
   }
@@ -281,8 +294,8 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o, RingPort
   const size_t xbase = (size_t)s * (P.nz + 2);
   const double gasd = (double)gas;
 
-  // G(k) = optical-depth column of the whole rate to face k
-  // (the column tables may have been staged into shared memory: plain loads)
+  // G(k) = optical-depth column of the whole rate to face k, and the rate in
+  // segment j (the column tables may live in shared memory: plain loads)
   auto colsum = [&](int k) -> double {
     double g = gasd * P.colgas[k];
     if (nrec > 0) g += rc0 * rcol0[k];
@@ -295,135 +308,84 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o, RingPort
     if (nrec > 1) r += rc1 * rrate1[j];
     return r;
   };
-  // Search bracket from the inverse gas-column table: exact when only the gas
-  // contributes (pass 1), otherwise widened to the whole admissible range.
-  auto bracket = [&](double target, int lo_min, int hi_max, int& lo, int& hi) {
-    lo = lo_min;
-    hi = hi_max;
-    if (nrec == 0 && gasd > 0.0 && P.nq > 0) {
-      const double q = target / gasd * P.nq_over_colmax;
-      if (q >= 0.0 && q < (double)P.nq) {
-        const int qi = (int)q;
-        const int a = P.ginv[qi] - 1, b = P.ginv[qi + 1] + 1;
-        if (a > lo) lo = a;
-        if (b < hi) hi = b;
-        if (lo >= hi) { lo = lo_min; hi = hi_max; }
-      }
-    }
-  };
 
+  const int j0 = L.j;
   double zc;
   int jc;
   int exit_end = -1;
-  double tflight;
+  double inv_sz = 0.0;
   if (L.mu == 0.0) {
     // no motion along z: collide in place after path tau / rate
-    jc = segment_of(P, L.z);
-    double r = 0.0;
-#pragma unroll
-    for (int c = 0; c < MAXSPCH; ++c) {
-      if (c >= nsc) break;
-      const int kk = P.sc[s][c];
-      r += (double)coef[c] * (P.ch[kk].kind == RECOMBINATION ? P.frate[kk][jc] : P.nseg[jc]);
-    }
+    jc = j0;
+    const double r = segrate(jc);
     if (!(r > 0.0)) {
       die<F32>(P, S, L, R_STALLED, L_E_STALLED);
       o.alive = false;
       return;
     }
-    double path = (double)tau / r;
-    tflight = path / (double)v;
-    atomicAdd(P.time_pt + tbase + (size_t)(jc + 1) * trow,
-              (unsigned long long)(tflight * Q_T + 0.5));
+    const double tfl = (double)tau / r / (double)v;
+    atomicAdd(P.time_pt + tbase + (size_t)(jc + 1) * trow, (unsigned long long)(tfl * Q_T + 0.5));
+    if (P.track_time) L.tal += tfl;
     zc = L.z;
   } else {
+    // One code path for both directions: the flight ends where the column of
+    // the rate, G, reaches G(z0) +- tau |mu| (optical depth along the path).
+    const bool up = L.mu > 0.0;
     const double amu = fabs(L.mu);
-    const int j0 = segment_of(P, L.z);
-    const double f0 = face(P, j0);
-    const double dz0 = L.z - f0;
-    const double g0 = colsum(j0) + segrate(j0) * dz0;
-    const double delta = (double)tau * amu;
     const int nz = P.nz;
-    if (L.mu > 0.0) {
-      const double target = g0 + delta;
-      if (target >= colsum(nz)) {
-        exit_end = 1;
-        zc = P.L;
-        jc = nz - 1;
-      } else {
-        int lo, hi;                            // G(lo) <= target < G(hi)
-        bracket(target, j0, nz, lo, hi);
-        if (!(colsum(lo) <= target) || !(target < colsum(hi))) { lo = j0; hi = nz; }
-        while (hi - lo > 1) {
-          int mid = (lo + hi) >> 1;
-          if (colsum(mid) <= target) lo = mid; else hi = mid;
-        }
-        jc = lo;
-        double r = segrate(jc);
-        double fj = face(P, jc);
-        zc = fj + (target - colsum(jc)) / r;
-        double fj1 = face(P, jc + 1);
-        if (zc > fj1) zc = fj1;
-        if (zc < L.z) zc = L.z;
-      }
+    const double g0 = colsum(j0) + segrate(j0) * (L.z - P.faces[j0]);
+    const double delta = (double)tau * amu;
+    const double target = up ? g0 + delta : g0 - delta;
+    const bool ex = up ? !(target < colsum(nz)) : !(target > 0.0);
+    if (ex) {
+      exit_end = up ? 1 : 0;
+      zc = up ? P.L : 0.0;
+      jc = up ? nz - 1 : 0;
     } else {
-      const double target = g0 - delta;
-      if (target <= 0.0) {
-        exit_end = 0;
-        zc = 0.0;
-        jc = 0;
-      } else {
-        int lo, hi;                            // G(lo) < target <= G(hi)
-        bracket(target, 0, j0 + 1, lo, hi);
-        if (!(colsum(lo) < target) || !(target <= colsum(hi))) { lo = 0; hi = j0 + 1; }
-        while (hi - lo > 1) {
-          int mid = (lo + hi) >> 1;
-          if (colsum(mid) >= target) hi = mid; else lo = mid;
+      // largest k with G(k) <= target, in [j0, nz) going up, [0, j0] going down
+      int lo = up ? j0 : 0, hi = up ? nz : j0 + 1;
+      if (nrec == 0 && gasd > 0.0 && P.nq > 0) {
+        // bracket from the inverse gas-column table (exact with gas only)
+        const double q = target / gasd * P.nq_over_colmax;
+        if (q >= 0.0 && q < (double)P.nq) {
+          const int qi = (int)q;
+          const int a = max(lo, P.ginv[qi] - 1), bb = min(hi, P.ginv[qi + 1] + 1);
+          if (a < bb && colsum(a) <= target && target < colsum(bb)) { lo = a; hi = bb; }
         }
-        jc = lo;
-        double r = segrate(jc);
-        double fj = face(P, jc);
-        zc = fj + (target - colsum(jc)) / r;
-        if (zc < fj) zc = fj;
-        double fj1 = face(P, jc + 1);
-        if (zc > fj1) zc = fj1;
-        if (zc > L.z) zc = L.z;
       }
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (colsum(mid) <= target) lo = mid; else hi = mid;
+      }
+      jc = lo;
+      const double fj = P.faces[jc], fj1 = P.faces[jc + 1];
+      const double gap = target - colsum(jc);
+      const double r = segrate(jc);
+      if (F32) zc = fj + (double)((float)gap / (float)r);
+      else zc = fj + gap / r;
+      zc = fmin(fmax(zc, fj), fj1);
+      zc = up ? fmax(zc, L.z) : fmin(zc, L.z);
     }
-    // time in each segment crossed (range add of the full-segment time) and
-    // the face crossings (Secs. 2.2, 2.3)
-    const double inv_sz = 1.0 / (amu * (double)v);
-    const bool ex = exit_end >= 0;
-    if (L.mu > 0.0) {
-      const int j1 = jc;
-      if (j1 == j0) {
-        atomicAdd(P.time_pt + tbase + (size_t)(j0 + 1) * trow, quant_t(fmax(zc - L.z, 0.0), inv_sz));
-      } else {
-        atomicAdd(P.time_pt + tbase + (size_t)(j0 + 1) * trow,
-                  quant_t(fmax(face(P, j0 + 1) - L.z, 0.0), inv_sz));
-        const unsigned long long qf = quant_t(P.dz, inv_sz);
-        range_add(P.time_rg + tbase, j0 + 2, j1, trow, qf);     // rows j0+1 .. j1-1 (+1 offset)
-        atomicAdd(P.time_pt + tbase + (size_t)(j1 + 1) * trow,
-                  ex ? qf : quant_t(fmax(zc - face(P, j1), 0.0), inv_sz));
-      }
-      range_add(P.xpos_rg + xbase, j0 + 1, ex ? nz : j1, 1, 1ULL);
+    // time in each segment crossed (Sec. 2.2) as point adds at both ends and
+    // one range add of the full-segment time, and the face crossings (Sec. 2.3)
+    inv_sz = 1.0 / (amu * (double)v);
+    const size_t row0 = tbase + (size_t)(j0 + 1) * trow;
+    if (jc == j0) {
+      atomicAdd(P.time_pt + row0, quant_t(fabs(zc - L.z), inv_sz));
     } else {
-      const int j1 = jc;
-      if (j1 == j0) {
-        atomicAdd(P.time_pt + tbase + (size_t)(j0 + 1) * trow, quant_t(fmax(L.z - zc, 0.0), inv_sz));
-      } else {
-        atomicAdd(P.time_pt + tbase + (size_t)(j0 + 1) * trow,
-                  quant_t(fmax(L.z - face(P, j0), 0.0), inv_sz));
-        const unsigned long long qf = quant_t(P.dz, inv_sz);
-        range_add(P.time_rg + tbase, j1 + 2, j0, trow, qf);     // rows j1+1 .. j0-1 (+1 offset)
-        atomicAdd(P.time_pt + tbase + (size_t)(j1 + 1) * trow,
-                  ex ? qf : quant_t(fmax(face(P, j1 + 1) - zc, 0.0), inv_sz));
-      }
-      range_add(P.xneg_rg + xbase, ex ? 0 : j1 + 1, j0, 1, 1ULL);
+      const double fs = P.faces[up ? j0 + 1 : j0];
+      atomicAdd(P.time_pt + row0, quant_t(fabs(fs - L.z), inv_sz));
+      const unsigned long long qf = quant_t(P.dz, inv_sz);
+      const double fe = P.faces[up ? jc : jc + 1];
+      atomicAdd(P.time_pt + tbase + (size_t)(jc + 1) * trow, ex ? qf : quant_t(fabs(zc - fe), inv_sz));
+      const int lo_seg = min(j0, jc), hi_seg = max(j0, jc);
+      range_add(P.time_rg + tbase, lo_seg + 2, hi_seg, trow, qf);   // full segments
     }
-    tflight = fabs(zc - L.z) * inv_sz;
+    const int fa = up ? j0 + 1 : (ex ? 0 : jc + 1);
+    const int fb = up ? (ex ? nz : jc) : j0;
+    range_add((up ? P.xpos_rg : P.xneg_rg) + xbase, fa, fb, 1, 1ULL);
+    if (P.track_time) L.tal += fabs(zc - L.z) * inv_sz;
   }
-  L.tal += tflight;
   if (exit_end >= 0) {
     long long bin = L.eq / P.spec_bin_q;
     if (bin > P.nspec) bin = P.nspec;
@@ -433,45 +395,52 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o, RingPort
     return;
   }
   L.z = zc;
+  L.j = jc;
 
-  // ---- collision in segment jc ----
+  // ---- collision in segment jc: channel with probability rate_k / rate_tot ----
   L.ev += 1;
   o.colls += 1;
-  auto chan_rate = [&](int c) -> double {
-    const int kk = P.sc[s][c];
-    return (double)coef[c] * (P.ch[kk].kind == RECOMBINATION ? P.frate[kk][jc] : P.nseg[jc]);
-  };
-  double rtot = 0.0;
-#pragma unroll
-  for (int c = 0; c < MAXSPCH; ++c) {
-    if (c >= nsc) break;
-    rtot += chan_rate(c);
-  }
-  const double target = u01d(w[1]) * rtot;
   int chs = -1, last = -1;
-  double cum = 0.0;
+  if (nrec == 0) {
+    // gas channels only: the density of segment jc factors out
+    const R target = T::u(w[1]) * gas;
+    R cum = (R)0;
 #pragma unroll
-  for (int c = 0; c < MAXSPCH; ++c) {
-    if (c >= nsc) break;
-    const double rkc = chan_rate(c);
-    if (!(rkc > 0.0)) continue;
-    last = c;
-    cum += rkc;
-    if (target < cum) { chs = c; break; }
+    for (int c = 0; c < MAXSPCH; ++c) {
+      if (c >= nsc) break;
+      if (!(coef[c] > (R)0)) continue;
+      last = c;
+      cum += coef[c];
+      if (target < cum) { chs = c; break; }
+    }
+  } else {
+    const double nj = P.nseg[jc];
+    const double target = u01d(w[1]) * segrate(jc);
+    double cum = 0.0;
+#pragma unroll
+    for (int c = 0; c < MAXSPCH; ++c) {
+      if (c >= nsc) break;
+      const int kk = P.sc[s][c];
+      const double rk = (double)coef[c] * (P.ch[kk].kind == RECOMBINATION ? P.frate[kk][jc] : nj);
+      if (!(rk > 0.0)) continue;
+      last = c;
+      cum += rk;
+      if (target < cum) { chs = c; break; }
+    }
   }
   if (chs < 0) chs = last;
   const int k = P.sc[s][chs];
   o.chan = k;
   const ChanDev ch = P.ch[k];
   if (ch.kind == ELASTIC) {
-    // isotropic in CM, target at rest: lab energy and polar angle
+    // isotropic in CM, target at rest: lab polar angle and energy transfer
     const R g = (R)P.gam[s];
     const R cchi = (R)2 * T::u(w[2]) - (R)1;
     const R a = (R)1 + (R)2 * g * cchi + g * g;
     const R ct = (cchi + g) * T::rsq(a);
     // energy given to the target, E - E' = E 2g(1 - cos chi)/(1+g)^2
     const R de = e * ((R)2 * g) * ((R)1 - cchi) * (R)P.inv_1pg2[s];
-    long long rq = (long long)floor((double)de * Q_E + 0.5);
+    long long rq = T::quant_de(de);
     if (rq > L.eq) rq = L.eq;
     o.recoil += (unsigned long long)rq;
     L.eq -= rq;
@@ -509,15 +478,14 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o, RingPort
     sadd(&S.ledger[L_N_SPAWN_E], 1);
     Lane c;
     c.z = L.z; c.eq = wq; c.mu = (double)mu_s; c.node = child_node(L.node, evc, 0);
-    c.tal = 0.0; c.pid = L.pid; c.ev = 0; c.sp = SP_E;
-    const bool keep_e = wq >= P.ecut_q;
-    if (!keep_e) die<F32>(P, S, c, R_CUTOFF, L_E_CUTOFF);
+    c.tal = 0.0; c.pid = L.pid; c.ev = 0; c.sp = SP_E; c.j = L.j;
+    if (wq < P.ecut_q) die<F32>(P, S, c, R_CUTOFF, L_E_CUTOFF);
     else emit(port, c);
     // ion with a thermal target's velocity (no recoil)
     if (ch.sout >= 0) {
       Lane ion;
       ion.z = L.z; ion.node = child_node(L.node, evc, 1); ion.tal = 0.0; ion.pid = L.pid;
-      ion.ev = 0; ion.sp = ch.sout;
+      ion.ev = 0; ion.sp = ch.sout; ion.j = L.j;
       unsigned long long wi[4];
       philox4x64_10(0ULL, ion.node, ((unsigned long long)P.pass << 8) | DOM_ION_BIRTH, 0ULL,
                     P.seed, L.pid, wi);
@@ -560,7 +528,7 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o, RingPort
   } else if (L.ev >= P.max_coll) {
     die<F32>(P, S, L, R_CAP_COLL, L_E_CAP);
     o.alive = false;
-  } else if (L.tal >= P.max_life) {
+  } else if (P.track_time && L.tal >= P.max_life) {
     die<F32>(P, S, L, R_CAP_TIME, L_E_CAP);
     o.alive = false;
   }
@@ -573,21 +541,23 @@ __device__ void event(const Params& P, Shared& S, Lane& L, EventOut& o, RingPort
 // shared memory when they fit; the event code reads them through P's pointers.
 __device__ void stage_tables(Params& SP, const Params& Pk, double* dyn, int dyn_doubles) {
   const int nz = Pk.nz;
-  int need = (2 * nz + 1) + (Pk.nq + 1 + 1) / 2 + 1;
-  int nrecf = 0;
+  int need = (3 * nz + 2) + (Pk.nq + 1 + 1) / 2 + 1;
   for (int k = 0; k < Pk.nch; ++k)
-    if (Pk.fcol[k]) { need += 2 * nz + 1; ++nrecf; }
+    if (Pk.fcol[k]) need += 2 * nz + 1;
   if (need > dyn_doubles) return;                   // stay in global memory
   double* col = dyn;
-  double* nseg = col + (nz + 1);
+  double* fac = col + (nz + 1);
+  double* nseg = fac + (nz + 1);
   int* ginv = (int*)(nseg + nz);
   double* next = (double*)(ginv + ((Pk.nq + 2) & ~1));
   for (int i = threadIdx.x; i <= nz; i += blockDim.x) col[i] = Pk.colgas[i];
+  for (int i = threadIdx.x; i <= nz; i += blockDim.x) fac[i] = Pk.faces[i];
   for (int i = threadIdx.x; i < nz; i += blockDim.x) nseg[i] = Pk.nseg[i];
   if (Pk.ginv)
     for (int i = threadIdx.x; i <= Pk.nq; i += blockDim.x) ginv[i] = Pk.ginv[i];
   if (threadIdx.x == 0) {
     SP.colgas = col;
+    SP.faces = fac;
     SP.nseg = nseg;
     if (Pk.ginv) SP.ginv = ginv;
   }
@@ -752,6 +722,7 @@ __global__ void __launch_bounds__(256) transport_kernel(const Params Pk, Ring R,
             L.tal = 0.0;
             L.ev = 0;
             L.pid = (unsigned long long)P.pid_offset + idx;
+            L.j = segment_of(P, L.z);
             sadd(&S.ledger[L_E_IN_PRIMARY], L.eq);
             sadd(&S.ledger[L_BIRTHS + L.sp], 1);
             if (L.sp == SP_E && L.eq < P.ecut_q) {
@@ -864,7 +835,7 @@ constexpr int DYN_MAX_BYTES = 120 * 1024;
 // Doubles of dynamic shared memory the staged tables of P need (0: too big,
 // read them from global memory).
 int transport_dyn_doubles(const Params& P) {
-  int need = (2 * P.nz + 1) + (P.nq + 1 + 1) / 2 + 1;
+  int need = (3 * P.nz + 2) + (P.nq + 1 + 1) / 2 + 1;
   for (int k = 0; k < P.nch; ++k)
     if (P.fcol[k]) need += 2 * P.nz + 1;
   return need * 8 <= DYN_MAX_BYTES ? need : 0;
