@@ -1,0 +1,550 @@
+// event.cuh - one transport event of one particle, shared by the single-run
+// and the multi-request (batched / served) kernels.
+//
+// A free flight by optical depth (Eqs. mean_free_path and distance_from_mfp
+// over the piecewise-constant column, equal in law to the segment-stop mover
+// of Sec. 3.1), the time/density and current tallies of Secs. 2.2-2.3 as
+// range adds, the terminator of Sec. 3.2, a channel chosen with probability
+// sigma_i n_i / sum_j sigma_j n_j, and its kinematics (Sec. 3.3).
+#pragma once
+#include "karl_device.cuh"
+
+namespace karl {
+
+
+constexpr double Q_E = 16777216.0;             // 2^24 energy units per eV
+constexpr double INV_Q_E = 1.0 / 16777216.0;
+constexpr double Q_T = 1125899906842624.0;     // 2^50 time units per s
+constexpr double C_LIGHT = 299792458.0;
+constexpr unsigned FULL = 0xffffffffu;
+constexpr long long SPIN_LIMIT = 1LL << 26;    // bounded waits on ring cells
+
+template <bool F32> struct RT;
+template <> struct RT<false> {
+  using R = double;
+  static __device__ __forceinline__ R u(unsigned long long w) { return u01d(w); }
+  static __device__ __forceinline__ R eta(unsigned long long w) { return eta01d(w); }
+  static __device__ __forceinline__ R lg(R x) { return log(x); }
+  static __device__ __forceinline__ R sq(R x) { return sqrt(x); }
+  static __device__ __forceinline__ R rsq(R x) { return rsqrt(x); }
+  static __device__ __forceinline__ R tn(R x) { return tan(x); }
+  static __device__ __forceinline__ R atn(R x) { return atan(x); }
+  static __device__ __forceinline__ R cpi(R x) { return cospi(x); }
+  static __device__ __forceinline__ R tab(const Params& P, int k, int i) {
+    return __ldg(P.sig + (size_t)i * P.nch + k);      // [node][channel]
+  }
+  static __device__ __forceinline__ R energy(long long eq) { return (double)eq * (1.0 / 16777216.0); }
+  static __device__ __forceinline__ long long quant_de(R de) {
+    return (long long)floor(de * 16777216.0 + 0.5);
+  }
+};
+template <> struct RT<true> {
+  using R = float;
+  static __device__ __forceinline__ R u(unsigned long long w) { return u01f(w); }
+  static __device__ __forceinline__ R eta(unsigned long long w) { return eta01f(w); }
+  static __device__ __forceinline__ R lg(R x) { return logf(x); }
+  static __device__ __forceinline__ R sq(R x) { return sqrtf(x); }
+  static __device__ __forceinline__ R rsq(R x) { return rsqrtf(x); }
+  static __device__ __forceinline__ R tn(R x) { return tanf(x); }
+  static __device__ __forceinline__ R atn(R x) { return atanf(x); }
+  static __device__ __forceinline__ R cpi(R x) { return cospif(x); }
+  static __device__ __forceinline__ R tab(const Params& P, int k, int i) {
+    return __ldg(P.sigf + (size_t)i * P.nch + k);     // [node][channel]
+  }
+  // energy from 2^-24 eV units with 32-bit conversions (below 65 keV)
+  static __device__ __forceinline__ R energy(long long eq) {
+    return eq < (1LL << 40) ? (float)(unsigned)(eq >> 8) * (1.0f / 65536.0f)
+                            : (float)eq * (1.0f / 16777216.0f);
+  }
+  static __device__ __forceinline__ long long quant_de(R de) {
+    const float x = de * 16777216.0f + 0.5f;
+    return x < 2.0e9f ? (long long)__float2int_rz(x) : (long long)x;
+  }
+};
+
+struct Lane {
+  double z;
+  long long eq;                 // kinetic energy, 2^-24 eV
+  double mu;                    // pitch cosine
+  unsigned long long node;      // lineage id
+  double tal;                   // time alive (tracked only under a lifetime cap)
+  unsigned long long pid;       // primary id
+  unsigned ev;                  // collisions so far = index of the next flight
+  int sp;                       // species
+  int j;                        // segment holding z (carried from the last flight)
+  int slot;                     // request slot (multi-request kernel; 0 otherwise)
+};
+
+// segment (20 bits) | species (2 bits) | request slot (10 bits) in one ring word
+__device__ __forceinline__ unsigned pack_sj(const Lane& p) {
+  return (unsigned)p.j | ((unsigned)p.sp << 20) | ((unsigned)p.slot << 22);
+}
+__device__ __forceinline__ void unpack_sj(unsigned w, Lane& p) {
+  p.j = (int)(w & 0xfffffu);
+  p.sp = (int)((w >> 20) & 3u);
+  p.slot = (int)(w >> 22);
+}
+
+__device__ __forceinline__ double face(const Params& P, int k) {
+  return k >= P.nz ? P.L : (double)k * P.dz;
+}
+__device__ __forceinline__ int segment_of(const Params& P, double z) {
+  int j = (int)floor(z / P.dz);
+  return j < 0 ? 0 : (j > P.nz - 1 ? P.nz - 1 : j);
+}
+__device__ __forceinline__ unsigned long long quant_t(double len, double inv_sz) {
+  double t = len * inv_sz;
+  return (unsigned long long)(t * Q_T + 0.5);
+}
+__device__ __forceinline__ long long quant_e(double e) { return (long long)floor(e * Q_E); }
+
+template <class R>
+__device__ __forceinline__ R speed(R e, R inv_m) {
+  R x = e * inv_m;
+  return (R)C_LIGHT * sqrt(x * ((R)2 + x)) / ((R)1 + x);
+}
+
+struct Shared {
+  unsigned long long ledger[LEDGER];
+  unsigned long long chan[MAXCH];
+};
+
+__device__ __forceinline__ void sadd(unsigned long long* p, long long v) {
+  atomicAdd(p, (unsigned long long)v);
+}
+
+// Range add of q over rows [a, b] (inclusive) of a difference array with row
+// stride `stride`; rows are then recovered by a prefix sum.
+__device__ __forceinline__ void range_add(unsigned long long* d, int a, int b, size_t stride,
+                                          unsigned long long q) {
+  if (a > b) return;
+  atomicAdd(d + (size_t)a * stride, q);
+  atomicAdd(d + (size_t)(b + 1) * stride, (unsigned long long)0 - q);
+}
+
+// ---------------------------------------------------------------------------
+// ring cells
+
+__device__ bool ring_put(const Ring& R, Control* ctl, unsigned long long pos, const Lane& p,
+                         unsigned long long deadline) {
+  unsigned long long* cell = R.seq + (pos & R.mask);
+  long long spins = 0;
+  while (ld_acquire(cell) != pos) {           // previous occupant not consumed yet
+    if (++spins > SPIN_LIMIT || ((spins & 1023) == 0 && globaltimer_ns() > deadline)) {
+      atomicCAS(&ctl->error, 0, ERR_CAPACITY);
+      atomicExch(&ctl->abort, 1);
+      return false;
+    }
+    __nanosleep(64);
+  }
+  size_t i = pos & R.mask;
+  R.z[i] = p.z; R.eq[i] = p.eq; R.mu[i] = p.mu; R.node[i] = p.node; R.tal[i] = p.tal;
+  R.pid[i] = p.pid; R.ev[i] = p.ev; R.sj[i] = pack_sj(p);
+  st_release(cell, pos + 1);
+  return true;
+}
+
+__device__ bool ring_get(const Ring& R, Control* ctl, unsigned long long pos, Lane& p,
+                         unsigned long long deadline) {
+  unsigned long long* cell = R.seq + (pos & R.mask);
+  long long spins = 0;
+  while (ld_acquire(cell) != pos + 1) {        // producer still writing
+    if (++spins > SPIN_LIMIT || ((spins & 1023) == 0 && globaltimer_ns() > deadline)) {
+      atomicCAS(&ctl->error, 0, ERR_TIMEOUT);
+      atomicExch(&ctl->abort, 1);
+      return false;
+    }
+    __nanosleep(32);
+  }
+  size_t i = pos & R.mask;
+  p.z = R.z[i]; p.eq = R.eq[i]; p.mu = R.mu[i]; p.node = R.node[i]; p.tal = R.tal[i];
+  p.pid = R.pid[i]; p.ev = R.ev[i];
+  unpack_sj(R.sj[i], p);
+  st_release(cell, pos + R.cap);
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// one event of one particle
+
+struct EventOut {
+  bool alive;
+  int chan;                               // channel of this event's collision, -1 if none
+  unsigned long long flights, colls;      // per-lane counters, flushed at the end
+  unsigned long long recoil, excit;       // per-lane energy sums (2^-24 eV)
+};
+
+// Products of a warp's events go to a short last-in-first-out queue in the
+// warp's shared memory and are taken by the warp's idle lanes, so a primary's
+// products are followed close to depth first (the paper follows a particle
+// list).  The queue spills to the shared ring when full, and once the
+// primaries are used up, so idle warps elsewhere can share the last work.
+constexpr int WQ = 32;
+constexpr int WARPS = 8;                  // 256-thread blocks
+struct WarpQueue {
+  Lane s[WQ];
+  int top;
+};
+
+struct RingPort {
+  const Ring* R;
+  Control* ctl;
+  unsigned long long deadline;
+  WarpQueue* q;
+  bool local;              // primaries remain: keep products in the warp queue
+  unsigned long long spilled;
+  // multi-request kernel: every existing particle counts in its slot's live
+  // word (low 32 bits); NULL in the single-run kernel
+  unsigned long long* slot_live;
+};
+
+__device__ __forceinline__ void emit(RingPort& port, const Lane& p) {
+  if (port.slot_live) atomicAdd(port.slot_live, 1ULL);
+  if (port.local) {
+    const int i = atomicAdd(&port.q->top, 1);
+    if (i < WQ) {
+      port.q->s[i] = p;
+      if (!port.slot_live)
+        atomicAdd((unsigned long long*)&port.ctl->active, 1ULL);   // held by this warp
+      return;
+    }
+  }
+  unsigned long long pos = atomicAdd(&port.ctl->tail, 1ULL);
+  ring_put(*port.R, port.ctl, pos, p, port.deadline);
+  port.spilled += 1;
+}
+
+template <bool F32>
+__device__ __forceinline__ void die(const Params& P, unsigned long long* led, Lane& L, int reason,
+                                    int slot) {
+  sadd(led + L_DEATHS + L.sp * NREASON + reason, 1);
+  sadd(led + slot, L.eq);
+  if (P.per_primary) atomicAdd(P.per_primary + (L.pid - (unsigned long long)P.pid_offset),
+                               (unsigned long long)L.ev);
+}
+
+template <bool F32>
+__device__ __forceinline__ void thermal(const Params& P, const unsigned long long w[4],
+                                        long long& eq, double& mu) {
+  // Maxwell-Boltzmann target: Gamma(3/2, kT) = Exp(1) + Z^2/2 (Box-Muller), isotropic
+  double c = cospi(2.0 * u01d(w[2]));
+  double e = P.kT * (-log(eta01d(w[0])) - log(eta01d(w[1])) * c * c);
+  eq = quant_e(e);
+  mu = 2.0 * u01d(w[3]) - 1.0;
+}
+
+template <bool F32>
+__device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOut& o,
+                      RingPort& port) {
+  using T = RT<F32>;
+  using R = typename T::R;
+  o.alive = true;
+  o.chan = -1;
+  if (L.eq <= 0) {                 // no kinetic energy: the particle never moves
+    die<F32>(P, led, L, R_STALLED, L_E_STALLED);
+    o.alive = false;
+    return;
+  }
+  const int s = L.sp;
+  const R e = T::energy(L.eq);
+  const R v = speed<R>(e, (R)P.inv_mass[s]);
+
+  unsigned long long w[4];
+  philox4x64_10((unsigned long long)L.ev, L.node,
+                ((unsigned long long)P.pass << 8) | DOM_EVENT, 0ULL, P.seed, L.pid, w);
+  const R tau = -T::lg(T::eta(w[0]));
+  o.flights += 1;
+
+  // per-flight coefficients: sigma_k(E) (gas, electron recombination) or 1/v
+  // (ion recombining with the electron field, whose rate already has sigma v)
+  const int nsc = P.nsc[s];
+  R coef[MAXSPCH];
+  const R le = T::lg(e * (R)P.inv_e_min);       // ln(E / e_min), shared by both lookups
+  const R lx = le * (R)P.inv_h;
+  int ti = (int)floor(lx);
+  R tf;
+  if (ti < 0) { ti = 0; tf = (R)0; }
+  else if (ti > P.n_energy - 2) { ti = P.n_energy - 2; tf = (R)1; }
+  else { tf = lx - (R)ti; }
+  R gas = (R)0;
+  int nrec = 0;
+  double rc0 = 0.0, rc1 = 0.0;
+  const double* rcol0 = P.colgas;
+  const double* rcol1 = P.colgas;
+  const double* rrate0 = P.nseg;
+  const double* rrate1 = P.nseg;
+#pragma unroll
+  for (int c = 0; c < MAXSPCH; ++c) {
+    if (c >= nsc) break;
+    const int k = P.sc[s][c];
+    const ChanDev& ch = P.ch[k];
+    R cv;
+    if (ch.kind == RECOMBINATION && s != SP_E) {
+      cv = (R)1 / v;
+    } else if (L.eq > ch.thr_q) {
+      const R a0 = T::tab(P, k, ti);
+      cv = a0 + tf * (T::tab(P, k, ti + 1) - a0);
+    } else {
+      cv = (R)0;
+    }
+    coef[c] = cv;
+    if (ch.kind != RECOMBINATION) {
+      gas += cv;
+    } else {
+      if (nrec == 0) { rc0 = (double)cv; rcol0 = P.fcol[k]; rrate0 = P.frate[k]; }
+      else { rc1 = (double)cv; rcol1 = P.fcol[k]; rrate1 = P.frate[k]; }
+      ++nrec;
+    }
+  }
+  // energy bin of the time tally
+  int b = 0;
+  if (P.ntb > 1) {
+    b = (int)floor(le * (R)P.tb_scale);
+    b = b < 0 ? 0 : (b > P.ntb - 1 ? P.ntb - 1 : b);
+  }
+  const size_t trow = (size_t)P.ntb;                         // stride between z rows
+  const size_t tbase = (size_t)s * (P.nz + 2) * P.ntb + b;   // (s, row 0, b)
+  const size_t xbase = (size_t)s * (P.nz + 2);
+  const double gasd = (double)gas;
+
+  // G(k) = optical-depth column of the whole rate to face k, and the rate in
+  // segment j (the column tables may live in shared memory: plain loads)
+  auto colsum = [&](int k) -> double {
+    double g = gasd * P.colgas[k];
+    if (nrec > 0) g += rc0 * rcol0[k];
+    if (nrec > 1) g += rc1 * rcol1[k];
+    return g;
+  };
+  auto segrate = [&](int j) -> double {
+    double r = gasd * P.nseg[j];
+    if (nrec > 0) r += rc0 * rrate0[j];
+    if (nrec > 1) r += rc1 * rrate1[j];
+    return r;
+  };
+
+  const int j0 = L.j;
+  double zc;
+  int jc;
+  int exit_end = -1;
+  double inv_sz = 0.0;
+  if (L.mu == 0.0) {
+    // no motion along z: collide in place after path tau / rate
+    jc = j0;
+    const double r = segrate(jc);
+    if (!(r > 0.0)) {
+      die<F32>(P, led, L, R_STALLED, L_E_STALLED);
+      o.alive = false;
+      return;
+    }
+    const double tfl = (double)tau / r / (double)v;
+    atomicAdd(P.time_pt + tbase + (size_t)(jc + 1) * trow, (unsigned long long)(tfl * Q_T + 0.5));
+    if (P.track_time) L.tal += tfl;
+    zc = L.z;
+  } else {
+    // One code path for both directions: the flight ends where the column of
+    // the rate, G, reaches G(z0) +- tau |mu| (optical depth along the path).
+    const bool up = L.mu > 0.0;
+    const double amu = fabs(L.mu);
+    const int nz = P.nz;
+    const double g0 = colsum(j0) + segrate(j0) * (L.z - P.faces[j0]);
+    const double delta = (double)tau * amu;
+    const double target = up ? g0 + delta : g0 - delta;
+    const bool ex = up ? !(target < colsum(nz)) : !(target > 0.0);
+    if (ex) {
+      exit_end = up ? 1 : 0;
+      zc = up ? P.L : 0.0;
+      jc = up ? nz - 1 : 0;
+    } else {
+      // largest k with G(k) <= target, in [j0, nz) going up, [0, j0] going down
+      int lo = up ? j0 : 0, hi = up ? nz : j0 + 1;
+      if (nrec == 0 && gasd > 0.0 && P.nq > 0) {
+        // bracket from the inverse gas-column table (exact with gas only)
+        const double q = target / gasd * P.nq_over_colmax;
+        if (q >= 0.0 && q < (double)P.nq) {
+          const int qi = (int)q;
+          const int a = max(lo, P.ginv[qi] - 1), bb = min(hi, P.ginv[qi + 1] + 1);
+          if (a < bb && colsum(a) <= target && target < colsum(bb)) { lo = a; hi = bb; }
+        }
+      }
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (colsum(mid) <= target) lo = mid; else hi = mid;
+      }
+      jc = lo;
+      const double fj = P.faces[jc], fj1 = P.faces[jc + 1];
+      const double gap = target - colsum(jc);
+      const double r = segrate(jc);
+      if (F32) zc = fj + (double)((float)gap / (float)r);
+      else zc = fj + gap / r;
+      zc = fmin(fmax(zc, fj), fj1);
+      zc = up ? fmax(zc, L.z) : fmin(zc, L.z);
+    }
+    // time in each segment crossed (Sec. 2.2) as point adds at both ends and
+    // one range add of the full-segment time, and the face crossings (Sec. 2.3)
+    inv_sz = 1.0 / (amu * (double)v);
+    const size_t row0 = tbase + (size_t)(j0 + 1) * trow;
+    if (jc == j0) {
+      atomicAdd(P.time_pt + row0, quant_t(fabs(zc - L.z), inv_sz));
+    } else {
+      const double fs = P.faces[up ? j0 + 1 : j0];
+      atomicAdd(P.time_pt + row0, quant_t(fabs(fs - L.z), inv_sz));
+      const unsigned long long qf = quant_t(P.dz, inv_sz);
+      const double fe = P.faces[up ? jc : jc + 1];
+      atomicAdd(P.time_pt + tbase + (size_t)(jc + 1) * trow, ex ? qf : quant_t(fabs(zc - fe), inv_sz));
+      const int lo_seg = min(j0, jc), hi_seg = max(j0, jc);
+      range_add(P.time_rg + tbase, lo_seg + 2, hi_seg, trow, qf);   // full segments
+    }
+    const int fa = up ? j0 + 1 : (ex ? 0 : jc + 1);
+    const int fb = up ? (ex ? nz : jc) : j0;
+    range_add((up ? P.xpos_rg : P.xneg_rg) + xbase, fa, fb, 1, 1ULL);
+    if (P.track_time) L.tal += fabs(zc - L.z) * inv_sz;
+  }
+  if (exit_end >= 0) {
+    long long bin = L.eq / P.spec_bin_q;
+    if (bin > P.nspec) bin = P.nspec;
+    atomicAdd(P.spectrum + ((size_t)exit_end * NSP + s) * (P.nspec + 1) + bin, 1ULL);
+    die<F32>(P, led, L, exit_end == 0 ? R_EXIT0 : R_EXIT1, exit_end == 0 ? L_E_EXIT0 : L_E_EXIT1);
+    o.alive = false;
+    return;
+  }
+  L.z = zc;
+  L.j = jc;
+
+  // ---- collision in segment jc: channel with probability rate_k / rate_tot ----
+  L.ev += 1;
+  o.colls += 1;
+  int chs = -1, last = -1;
+  if (nrec == 0) {
+    // gas channels only: the density of segment jc factors out
+    const R target = T::u(w[1]) * gas;
+    R cum = (R)0;
+#pragma unroll
+    for (int c = 0; c < MAXSPCH; ++c) {
+      if (c >= nsc) break;
+      if (!(coef[c] > (R)0)) continue;
+      last = c;
+      cum += coef[c];
+      if (target < cum) { chs = c; break; }
+    }
+  } else {
+    const double nj = P.nseg[jc];
+    const double target = u01d(w[1]) * segrate(jc);
+    double cum = 0.0;
+#pragma unroll
+    for (int c = 0; c < MAXSPCH; ++c) {
+      if (c >= nsc) break;
+      const int kk = P.sc[s][c];
+      const double rk = (double)coef[c] * (P.ch[kk].kind == RECOMBINATION ? P.frate[kk][jc] : nj);
+      if (!(rk > 0.0)) continue;
+      last = c;
+      cum += rk;
+      if (target < cum) { chs = c; break; }
+    }
+  }
+  if (chs < 0) chs = last;
+  const int k = P.sc[s][chs];
+  o.chan = k;
+  const ChanDev ch = P.ch[k];
+  if (ch.kind == ELASTIC) {
+    // isotropic in CM, target at rest: lab polar angle and energy transfer
+    const R g = (R)P.gam[s];
+    const R cchi = (R)2 * T::u(w[2]) - (R)1;
+    const R a = (R)1 + (R)2 * g * cchi + g * g;
+    const R ct = (cchi + g) * T::rsq(a);
+    // energy given to the target, E - E' = E 2g(1 - cos chi)/(1+g)^2
+    const R de = e * ((R)2 * g) * ((R)1 - cchi) * (R)P.inv_1pg2[s];
+    long long rq = T::quant_de(de);
+    if (rq > L.eq) rq = L.eq;
+    o.recoil += (unsigned long long)rq;
+    L.eq -= rq;
+    const R st = T::sq(fmax((R)0, (R)1 - ct * ct));
+    const R cphi = T::cpi((R)2 * T::u(w[3]));
+    const R mu = (R)L.mu;
+    const R smu = T::sq(fmax((R)0, (R)1 - mu * mu));
+    L.mu = (double)fmin((R)1, fmax((R)-1, mu * ct + smu * st * cphi));
+  } else if (ch.kind == EXCITATION) {
+    L.eq -= ch.loss_q;
+    o.excit += (unsigned long long)ch.loss_q;
+  } else if (ch.kind == IONIZATION) {
+    const long long avail = L.eq - ch.loss_q;
+    const R eps = (R)P.eps_ion;
+    const R wmax = (e - (R)ch.loss_ev) * (R)0.5;
+    const R wsec = eps * T::tn(T::u(w[2]) * T::atn(wmax * (R)P.inv_eps_ion));
+    long long wq = quant_e((double)wsec);
+    if (wq > avail / 2) wq = avail / 2;
+    if (wq < 0) wq = 0;
+    const long long eq1 = avail - wq;
+    sadd(led + (L_LOSS_IONIZ), ch.loss_q);
+    // binary encounter: cos^2 of the polar angles are the energy fractions
+    const double inv_avail = avail > 0 ? 1.0 / (double)avail : 0.0;
+    const R c2p = avail > 0 ? (R)((double)eq1 * inv_avail) : (R)1;
+    const R c2s = (R)((double)wq * inv_avail);
+    const R cp = T::sq(c2p), sp = T::sq(c2s);
+    const R cphi = T::cpi((R)2 * T::u(w[3]));
+    const R mu = (R)L.mu;
+    const R smu = T::sq(fmax((R)0, (R)1 - mu * mu));
+    const R mu_p = fmin((R)1, fmax((R)-1, mu * cp + smu * sp * cphi));
+    const R mu_s = fmin((R)1, fmax((R)-1, mu * sp - smu * cp * cphi));
+    const unsigned evc = L.ev - 1;
+    // slow electron (azimuth opposite to the fast one)
+    sadd(led + (L_BIRTHS + SP_E), 1);
+    sadd(led + (L_N_SPAWN_E), 1);
+    Lane c;
+    c.z = L.z; c.eq = wq; c.mu = (double)mu_s; c.node = child_node(L.node, evc, 0);
+    c.tal = 0.0; c.pid = L.pid; c.ev = 0; c.sp = SP_E; c.j = L.j; c.slot = L.slot;
+    if (wq < P.ecut_q) die<F32>(P, led, c, R_CUTOFF, L_E_CUTOFF);
+    else emit(port, c);
+    // ion with a thermal target's velocity (no recoil)
+    if (ch.sout >= 0) {
+      Lane ion;
+      ion.z = L.z; ion.node = child_node(L.node, evc, 1); ion.tal = 0.0; ion.pid = L.pid;
+      ion.ev = 0; ion.sp = ch.sout; ion.j = L.j; ion.slot = L.slot;
+      unsigned long long wi[4];
+      philox4x64_10(0ULL, ion.node, ((unsigned long long)P.pass << 8) | DOM_ION_BIRTH, 0ULL,
+                    P.seed, L.pid, wi);
+      thermal<F32>(P, wi, ion.eq, ion.mu);
+      sadd(led + (L_E_IN_THERMAL), ion.eq);
+      sadd(led + (L_BIRTHS + ch.sout), 1);
+      sadd(led + (L_N_SPAWN_ION), 1);
+      emit(port, ion);
+    }
+    L.eq = eq1;
+    L.mu = (double)mu_p;
+  } else if (ch.kind == CLUSTERING) {
+    die<F32>(P, led, L, R_CLUSTER, L_E_CLUSTER);
+    unsigned long long wc[4];
+    const unsigned evc = L.ev - 1;
+    philox4x64_10((unsigned long long)evc, L.node,
+                  ((unsigned long long)P.pass << 8) | DOM_CLUSTER, 0ULL, P.seed, L.pid, wc);
+    long long eqc;
+    double muc;
+    thermal<F32>(P, wc, eqc, muc);
+    L.node = child_node(L.node, evc, 2);
+    L.eq = eqc;
+    L.mu = muc;
+    L.tal = 0.0;
+    L.ev = 0;
+    L.sp = ch.sout;
+    sadd(led + (L_E_IN_THERMAL), eqc);
+    sadd(led + (L_BIRTHS + ch.sout), 1);
+    return;
+  } else {  // RECOMBINATION
+    atomicAdd(P.recomb + (size_t)ch.sout * P.nz + jc, 1ULL);
+    die<F32>(P, led, L, R_RECOMB, L_E_RECOMB);
+    o.alive = false;
+    return;
+  }
+  // ---- terminator (Sec. 3.2) ----
+  if (L.sp == SP_E && L.eq < P.ecut_q) {
+    die<F32>(P, led, L, R_CUTOFF, L_E_CUTOFF);
+    o.alive = false;
+  } else if (L.ev >= P.max_coll) {
+    die<F32>(P, led, L, R_CAP_COLL, L_E_CAP);
+    o.alive = false;
+  } else if (P.track_time && L.tal >= P.max_life) {
+    die<F32>(P, led, L, R_CAP_TIME, L_E_CAP);
+    o.alive = false;
+  }
+}
+
+}  // namespace karl

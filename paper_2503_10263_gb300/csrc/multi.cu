@@ -1,0 +1,453 @@
+// multi.cu - persistent transport kernel over many requests (batched and
+// served forms of the transport step).
+//
+// The event itself is the same as in the single-run kernel (event.cuh).  What
+// differs is where work comes from and where it goes: every particle carries
+// its request slot; idle lanes take their warp's products, then products from
+// the shared ring, then primaries of any request whose current pass still has
+// unclaimed primaries (a bitmap of slots); each request moves pass 1 ->
+// target fields -> pass 2 -> final tallies inside the kernel, driven by the
+// warp whose atomic decrement emptied the request's pass.  A batch is a launch
+// with every request published before it starts; a server keeps the launch
+// running while the host publishes requests into free slots.
+#include "event.cuh"
+#include "multi.cuh"
+
+namespace karl {
+
+__device__ __forceinline__ int ld_acquire_i(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_i(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// cross section from the channel-major table (target-field builder)
+__device__ double sigma_cm(const double* sig, int n, double e_min, double log_ratio_h, double loss,
+                           double e) {
+  if (!(e > loss)) return 0.0;
+  double x = log(e / e_min) / log_ratio_h;
+  int i = (int)floor(x);
+  double f;
+  if (i < 0) { i = 0; f = 0.0; }
+  else if (i > n - 2) { i = n - 2; f = 1.0; }
+  else f = x - (double)i;
+  return (1.0 - f) * sig[i] + f * sig[i + 1];
+}
+
+// Warp-cooperative end of pass p of request s (Eq. target_field_density for
+// the fields; Sec. 2.3 for the current).
+__device__ void complete_pass(SlotDesc* D, SlotCtl* C, MultiCtl* M, int s, int p, int lane) {
+  const int from = p == 1 ? SLOT_PASS1 : SLOT_PASS2;
+  int ok = 0;
+  if (lane == 0) ok = atomicCAS(&C[s].state, from, SLOT_TRANS) == from;
+  if (!__shfl_sync(FULL, ok, 0)) return;                 // someone else already did it
+  SlotDesc& d = D[s];
+  const Params& P = d.P[p - 1];
+  const int nz = P.nz, ntb = P.ntb;
+  const double inv_qt = 1.0 / Q_T;
+  if (p == 1 && d.n_passes == 2) {
+    // pass-1 time: point adds plus the prefix of the range adds
+    for (int col = lane; col < NSP * ntb; col += 32) {
+      const int sp = col / ntb, b = col % ntb;
+      unsigned long long acc = 0;
+      for (int row = 0; row < nz + 2; ++row) {
+        const size_t i = ((size_t)sp * (nz + 2) + row) * ntb + b;
+        acc += P.time_rg[i];
+        d.time1[i] = P.time_pt[i] + acc;
+      }
+    }
+    __syncwarp();
+    __threadfence();
+    // target fields of the recombination channels
+    for (int t = lane; t < P.nch * nz; t += 32) {
+      const int k = t / nz, j = t % nz;
+      const ChanDev& ch = P.ch[k];
+      if (ch.kind != RECOMBINATION) continue;
+      double acc = 0.0;
+      for (int b = 0; b < ntb; ++b) {
+        const unsigned long long tt = d.time1[((size_t)ch.sout * (nz + 2) + (j + 1)) * ntb + b];
+        const double n = (double)tt * inv_qt / (d.tsim * d.vol);
+        if (ch.sin == SP_E) {
+          acc += n;
+        } else {
+          const double eb = P.e_min * exp(P.log_ratio_h * (P.n_energy - 1) * (b + 0.5) / ntb);
+          const double x = eb * P.inv_mass[SP_E];
+          const double v = C_LIGHT * sqrt(x * (2.0 + x)) / (1.0 + x);
+          acc += n * sigma_cm(d.sig_cm + (size_t)k * P.n_energy, P.n_energy, P.e_min,
+                              P.log_ratio_h, ch.loss_ev, eb) * v;
+        }
+      }
+      d.frate[(size_t)k * nz + j] = acc;
+    }
+    __syncwarp();
+    __threadfence();
+    for (int k = lane; k < P.nch; k += 32) {
+      if (P.ch[k].kind != RECOMBINATION) continue;
+      double c = 0.0;
+      d.fcol[(size_t)k * (nz + 1)] = 0.0;
+      for (int j = 0; j < nz; ++j) {
+        c += d.frate[(size_t)k * nz + j] * P.dz;
+        d.fcol[(size_t)k * (nz + 1) + j + 1] = c;
+      }
+    }
+    __syncwarp();
+    __threadfence();
+    if (lane == 0) {
+      *(volatile int*)&C[s].pass = 2;
+      __threadfence();
+      st_release_i(&C[s].state, SLOT_PASS2);
+      if (d.n_prim > 0) atomicOr(&M->bitmap[s >> 5], 1u << (s & 31));
+    }
+    return;
+  }
+  // last pass: prefix sums into the outputs, then normalise
+  for (int col = lane; col < NSP * ntb; col += 32) {
+    const int sp = col / ntb, b = col % ntb;
+    unsigned long long acc = 0;
+    for (int row = 0; row < nz + 2; ++row) {
+      const size_t i = ((size_t)sp * (nz + 2) + row) * ntb + b;
+      acc += P.time_rg[i];
+      d.time_out[i] = P.time_pt[i] + acc;
+    }
+  }
+  for (int sp = lane; sp < 2 * NSP; sp += 32) {
+    const unsigned long long* rg = sp < NSP ? P.xpos_rg : P.xneg_rg;
+    unsigned long long* out = sp < NSP ? d.cpos_out : d.cneg_out;
+    const int ss = sp % NSP;
+    unsigned long long acc = 0;
+    for (int k = 0; k <= nz; ++k) {
+      acc += rg[(size_t)ss * (nz + 2) + k];
+      out[(size_t)ss * (nz + 1) + k] = acc;
+    }
+  }
+  __syncwarp();
+  __threadfence();
+  const unsigned long long* t1 = d.n_passes == 2 ? d.time1 : d.time_out;
+  for (int t = lane; t < NSP * nz; t += 32) {
+    const int sp = t / nz, j = t % nz;
+    double tsum = 0.0;
+    for (int b = 0; b < ntb; ++b) {
+      const size_t idx = ((size_t)sp * (nz + 2) + (j + 1)) * ntb + b;
+      tsum += (double)d.time_out[idx] * inv_qt;
+      d.field[((size_t)sp * nz + j) * ntb + b] = (double)t1[idx] * inv_qt / (d.tsim * d.vol);
+    }
+    d.density[(size_t)sp * nz + j] =
+        tsum / (d.tsim * d.vol) - (double)P.recomb[(size_t)sp * nz + j] / d.vol;
+  }
+  for (int t = lane; t < NSP * (nz + 1); t += 32)
+    d.current[t] = ((double)d.cpos_out[t] - (double)d.cneg_out[t]) / (d.area * d.tsim);
+  __syncwarp();
+  __threadfence_system();
+  if (lane == 0) {
+    st_release_i(&C[s].state, SLOT_DONE);
+    atomicAdd(&M->done_count, 1ULL);
+    *(volatile int*)d.done_flag = 1;
+    __threadfence_system();
+  }
+}
+
+// A pass of request s empties when a decrement of its word leaves no live
+// particle and every primary claimed.
+__device__ __forceinline__ bool pass_emptied(unsigned long long old, unsigned long long dec,
+                                             long long n_prim) {
+  return (old & 0xffffffffULL) == dec && (long long)(old >> 32) >= n_prim;
+}
+
+template <bool F32>
+__global__ void __launch_bounds__(256) multi_kernel(SlotDesc* D, SlotCtl* C, MultiCtl* M, Ring R,
+                                                    const volatile int* cancel,
+                                                    unsigned long long timeout_ns) {
+  const unsigned long long deadline = globaltimer_ns() + timeout_ns;
+  __shared__ WarpQueue wq[WARPS];
+  if (threadIdx.x < WARPS) wq[threadIdx.x].top = 0;
+  __syncthreads();
+  Control* ctl = &M->c;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  WarpQueue& Q = wq[threadIdx.x >> 5];
+  bool has = false;
+  Lane L;
+  L.slot = 0;
+  int lpass = 1;
+  const Params* Pl = &D[0].P[0];
+  EventOut o;
+  o.flights = o.colls = o.recoil = o.excit = 0;
+  o.chan = -1;
+  unsigned long long idle_iters = 0, busy_iters = 0, busy_lane_iters = 0, started = 0;
+  unsigned idle_ns = 128;
+  RingPort port;
+  port.R = &R;
+  port.ctl = ctl;
+  port.deadline = deadline;
+  port.q = &Q;
+  port.local = true;
+  port.spilled = 0;
+  port.slot_live = nullptr;
+
+  // the lane's particle belongs to the current pass of its request
+  auto bind = [&](int s) {
+    lpass = ld_acquire_i(&C[s].pass);
+    lpass = lpass == 2 ? 2 : 1;
+    Pl = &D[s].P[lpass - 1];
+  };
+  // passes this lane saw empty: one from a claim (lane 0), one from a death
+  int trigA = 0, tslotA = 0, tpassA = 1, trigB = 0, tslotB = 0, tpassB = 1;
+
+  for (long long iter = 0;; ++iter) {
+    if ((iter & 63) == 0) {
+      int stop = 0, local = 0;
+      if (lane == 0) {
+        if (ld_relaxed_i(&ctl->abort)) stop = 1;
+        else if (cancel && ld_relaxed_i((const int*)cancel)) {
+          atomicCAS(&ctl->error, 0, ERR_CANCELLED);
+          atomicExch(&ctl->abort, 1);
+          stop = 1;
+        } else if (globaltimer_ns() > deadline) {
+          atomicCAS(&ctl->error, 0, ERR_TIMEOUT);
+          atomicExch(&ctl->abort, 1);
+          stop = 1;
+        }
+        // adopt requests the host has published since the last look
+        unsigned long long pub = ld_acquire(&M->published);
+        unsigned long long ad = ld_relaxed(&M->adopted);
+        while (ad < pub) {
+          const unsigned long long old = atomicCAS(&M->adopted, ad, ad + 1);
+          if (old == ad) {
+            const int s = (int)ld_acquire_i((const int*)&M->pubq[ad % MAX_SLOTS]);
+            // (requests without primaries are finished by the host, never published)
+            if (ld_acquire_i(&C[s].state) == SLOT_PASS1)
+              atomicOr(&M->bitmap[s >> 5], 1u << (s & 31));
+            ++ad;
+          } else {
+            ad = old;
+          }
+        }
+        for (int i = 0; i < MAX_SLOTS / 32 && !local; ++i)
+          local = ld_relaxed_i((const int*)&M->bitmap[i]) != 0;
+      }
+      if (__shfl_sync(FULL, stop, 0)) break;
+      port.local = __shfl_sync(FULL, local, 0) != 0;
+    }
+
+    // ---- idle lanes take the warp's own products first (newest first) ----
+    __syncwarp();
+    {
+      const unsigned need0 = __ballot_sync(FULL, !has);
+      int top = Q.top;
+      if (top > WQ) top = WQ;
+      const int take = min(__popc(need0), top);
+      if (!has) {
+        const int rank = __popc(need0 & lt);
+        if (rank < take) {
+          L = Q.s[top - 1 - rank];
+          has = true;
+          started += 1;
+          bind(L.slot);
+        }
+      }
+      int left = top - take;
+      if (!port.local && left > 0) {
+        unsigned long long pos = 0;
+        if (lane == 0) pos = atomicAdd(&ctl->tail, (unsigned long long)left);
+        pos = __shfl_sync(FULL, pos, 0);
+        if (lane < left) ring_put(R, ctl, pos + lane, Q.s[lane], deadline);
+        if (lane == 0) port.spilled += left;
+        left = 0;
+      }
+      __syncwarp();
+      if (lane == 0) Q.top = left;
+      __syncwarp();
+    }
+
+    // ---- other idle lanes: products from the ring, then primaries of a request ----
+    const unsigned need = __ballot_sync(FULL, !has);
+    if (need) {
+      const int k = __popc(need);
+      unsigned long long base = 0;
+      int got = 0, src = 0, gslot = 0, gpass = 1;
+      if (lane == 0) {
+        unsigned long long h = ld_relaxed(&ctl->head), t = ld_relaxed(&ctl->tail);
+        for (int tries = 0; tries < 16 && h < t; ++tries) {
+          unsigned long long take = t - h < (unsigned long long)k ? t - h : (unsigned long long)k;
+          unsigned long long old = atomicCAS(&ctl->head, h, h + take);
+          if (old == h) { base = h; got = (int)take; src = 1; break; }
+          h = old;
+          t = ld_relaxed(&ctl->tail);
+        }
+        if (got == 0) {
+          // a request with unclaimed primaries, searched from a per-warp start
+          const int w0 = (gwarp + (int)(iter >> 6)) & (MAX_SLOTS / 32 - 1);
+          for (int i = 0; i < MAX_SLOTS / 32 && got == 0; ++i) {
+            const int wi = (w0 + i) & (MAX_SLOTS / 32 - 1);
+            unsigned bits = (unsigned)ld_relaxed_i((const int*)&M->bitmap[wi]);
+            while (bits && got == 0) {
+              const int bit = __ffs(bits) - 1;
+              bits &= bits - 1;
+              const int s = wi * 32 + bit;
+              const int st = ld_acquire_i(&C[s].state);
+              if (st != SLOT_PASS1 && st != SLOT_PASS2) continue;
+              const int p = st == SLOT_PASS2 ? 2 : 1;
+              const long long n = D[s].n_prim;
+              unsigned long long* word = &C[s].word[p - 1];
+              const unsigned long long old =
+                  atomicAdd(word, ((unsigned long long)k << 32) + (unsigned long long)k);
+              const long long next = (long long)(old >> 32);
+              if (next + k >= n) atomicAnd(&M->bitmap[wi], ~(1u << bit));
+              const long long left = n - next;
+              const int g = left <= 0 ? 0 : (left < k ? (int)left : k);
+              if (g < k) {
+                const unsigned long long dec = (unsigned long long)(k - g);
+                const unsigned long long o2 = atomicAdd(word, (unsigned long long)0 - dec);
+                if (pass_emptied(o2, dec, n)) { trigA = 1; tslotA = s; tpassA = p; }
+              }
+              if (g > 0) { got = g; base = (unsigned long long)next; src = 2; gslot = s; gpass = p; }
+            }
+          }
+        }
+      }
+      base = __shfl_sync(FULL, base, 0);
+      got = __shfl_sync(FULL, got, 0);
+      src = __shfl_sync(FULL, src, 0);
+      gslot = __shfl_sync(FULL, gslot, 0);
+      gpass = __shfl_sync(FULL, gpass, 0);
+      if (!has && got > 0) {
+        const int rank = __popc(need & lt);
+        if (rank < got) {
+          const unsigned long long idx = base + rank;
+          if (src == 1) {
+            has = ring_get(R, ctl, idx, L, deadline);
+            if (has) bind(L.slot);
+          } else {
+            lpass = gpass;
+            Pl = &D[gslot].P[gpass - 1];
+            const Params& P = *Pl;
+            L.z = P.pz[idx];
+            L.eq = quant_e(P.pe[idx]);
+            L.mu = P.pmu[idx];
+            L.sp = P.psp[idx];
+            L.node = 0;
+            L.tal = 0.0;
+            L.ev = 0;
+            L.pid = (unsigned long long)P.pid_offset + idx;
+            L.j = segment_of(P, L.z);
+            L.slot = gslot;
+            sadd(P.ledger + L_E_IN_PRIMARY, L.eq);
+            sadd(P.ledger + L_BIRTHS + L.sp, 1);
+            if (L.sp == SP_E && L.eq < P.ecut_q) {
+              die<F32>(P, P.ledger, L, R_CUTOFF, L_E_CUTOFF);
+              const unsigned long long o2 =
+                  atomicAdd(&C[gslot].word[gpass - 1], (unsigned long long)0 - 1ULL);
+              if (pass_emptied(o2, 1ULL, D[gslot].n_prim)) { trigB = 1; tslotB = gslot; tpassB = gpass; }
+            } else {
+              has = true;
+            }
+          }
+          started += 1;
+        }
+      }
+    }
+
+    // ---- one event ----
+    bool died = false;
+    const unsigned busy = __ballot_sync(FULL, has);
+    if (busy) {
+      idle_ns = 128;
+      busy_lane_iters += __popc(busy);
+      ++busy_iters;
+      if (has) {
+        port.slot_live = &C[L.slot].word[lpass - 1];
+        event<F32>(*Pl, Pl->ledger, L, o, port);
+        if (!o.alive) { has = false; died = true; }
+      }
+      __syncwarp();
+      if (lane == 0 && Q.top > WQ) Q.top = WQ;
+      // channel counts, one add per distinct (request, channel) per warp
+      const unsigned mc = __ballot_sync(FULL, o.chan >= 0);
+      if (o.chan >= 0) {
+        const unsigned key = ((unsigned)L.slot << 5) | (unsigned)o.chan;
+        const unsigned grp = __match_any_sync(mc, key);
+        if (lane == __ffs(grp) - 1)
+          atomicAdd(Pl->chan_count + o.chan, (unsigned long long)__popc(grp));
+      }
+      o.chan = -1;
+      if (died) {
+        // per-lane sums go to the request's ledger with the particle's death
+        unsigned long long* led = Pl->ledger;
+        atomicAdd(led + L_N_FLIGHT, o.flights);
+        atomicAdd(led + L_N_COLL, o.colls);
+        if (o.recoil) atomicAdd(led + L_LOSS_RECOIL, o.recoil);
+        if (o.excit) atomicAdd(led + L_LOSS_EXCIT, o.excit);
+        o.flights = o.colls = o.recoil = o.excit = 0;
+        const unsigned long long o2 =
+            atomicAdd(&C[L.slot].word[lpass - 1], (unsigned long long)0 - 1ULL);
+        if (pass_emptied(o2, 1ULL, D[L.slot].n_prim)) { trigB = 1; tslotB = L.slot; tpassB = lpass; }
+      }
+    }
+
+    // ---- passes that just emptied: the whole warp finishes them ----
+    for (int round = 0; round < 2; ++round) {
+      const int tr = round == 0 ? trigA : trigB;
+      const int ts = round == 0 ? tslotA : tslotB;
+      const int tp = round == 0 ? tpassA : tpassB;
+      unsigned mt = __ballot_sync(FULL, tr);
+      while (mt) {
+        const int srcl = __ffs(mt) - 1;
+        const int s = __shfl_sync(FULL, ts, srcl);
+        const int p = __shfl_sync(FULL, tp, srcl);
+        complete_pass(D, C, M, s, p, lane);
+        mt &= mt - 1;
+      }
+    }
+    trigA = trigB = 0;
+
+    if (!busy) {
+      // leave when the host has closed the session and every published
+      // request is done
+      int done = 0;
+      if (lane == 0) {
+        done = ld_relaxed_i(&M->shutdown) &&
+               ld_relaxed(&M->done_count) >= ld_acquire(&M->published);
+      }
+      if (__shfl_sync(FULL, done, 0)) break;
+      __nanosleep(idle_ns);
+      if (idle_ns < 8192) idle_ns <<= 1;
+      ++idle_iters;
+    }
+  }
+
+  unsigned long long sp = port.spilled, st = started;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    sp += __shfl_down_sync(FULL, sp, off);
+    st += __shfl_down_sync(FULL, st, off);
+  }
+  if (lane == 0) {
+    atomicAdd(&ctl->idle_iters, idle_iters);
+    atomicAdd(&ctl->busy_iters, busy_iters);
+    atomicAdd(&ctl->busy_lane_iters, busy_lane_iters);
+    atomicAdd(&ctl->spilled, sp);
+    atomicAdd(&ctl->particles, st);
+  }
+}
+
+cudaError_t launch_multi(bool f32, SlotDesc* D, SlotCtl* C, MultiCtl* M, const Ring& R,
+                         const volatile int* cancel, unsigned long long timeout_ns, int grid,
+                         int block, cudaStream_t st) {
+  if (f32)
+    multi_kernel<true><<<grid, block, 0, st>>>(D, C, M, R, cancel, timeout_ns);
+  else
+    multi_kernel<false><<<grid, block, 0, st>>>(D, C, M, R, cancel, timeout_ns);
+  return cudaGetLastError();
+}
+
+cudaError_t multi_occupancy(bool f32, int block, int* blocks_per_sm) {
+  if (f32)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, multi_kernel<true>, block, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, multi_kernel<false>, block, 0);
+}
+
+}  // namespace karl
