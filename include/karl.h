@@ -215,6 +215,87 @@ const char* karl_status_string(karl_status s);
 /* Detail of the last error on this context (empty if none). */
 const char* karl_last_error(const karl_ctx* ctx);
 
+
+/* ------------------------------------------------------------------------
+ * Many requests in one persistent launch (batched and served forms).
+ *
+ * A server holds one physics model (the cross-section tables and species of
+ * karl_xs) and runs requests, each with its own geometry, gas profile,
+ * primaries and seed, as independent source configurations of the same
+ * transport step (Sec. 2.1).  Requests are admitted while their device
+ * footprint fits the server's HBM budget and a slot is free; admitted
+ * requests join the running kernel (continuous batching) and move through
+ * pass 1, target fields and pass 2 on the device.  Each request's result is
+ * the same alone or in any mix: its random streams are keyed by its seed and
+ * primary ids only.
+ *
+ * A batch is a server whose requests are all submitted before
+ * karl_server_run_all(), which publishes them, runs them in one persistent
+ * launch and collects every result.  The server API is not thread-safe:
+ * serialise calls on one server.
+ */
+typedef struct karl_server karl_server;
+
+typedef struct karl_server_opts {
+  int32_t precision;           /* KARL_FP64 or KARL_FP32 */
+  int32_t max_slots;           /* requests on the device at once, 1 .. 1024 (0 = 256) */
+  int64_t hbm_budget_bytes;    /* device arena for request state (0 = 16 GiB) */
+  double timeout_s;            /* limit on one persistent launch (<= 0: 3600 s) */
+  int32_t block_size;          /* 0 = 256 */
+  int32_t blocks_per_sm;       /* 0 = occupancy maximum */
+} karl_server_opts;
+
+/* Create a server for the model in xs (tables copied).  Species masses,
+ * target mass, and the energy grid of the time tally come from each request's
+ * geometry.  Errors: KARL_EINVAL, KARL_ENOMEM, KARL_ECUDA. */
+karl_status karl_server_create(const karl_xs* xs, const karl_server_opts* opts,
+                               karl_server** out);
+
+/* Queue one request (geometry and primaries copied; host pointers only).
+ * Its results will be written into out: host buffers (on_device = 0) sized
+ * as karl_tally_layout gives for this geometry, owned by the caller and kept
+ * valid until karl_server_poll reports the request done; per_primary is not
+ * used.  n_passes as in karl_run_opts.  The request is admitted at once if a
+ * slot and arena space are free, else as earlier requests finish.
+ * Errors: KARL_EINVAL (bad geometry, primaries, buffers, or a footprint
+ * larger than the whole budget), KARL_ENOMEM. */
+karl_status karl_server_submit(karl_server* srv, const karl_geometry* geom,
+                               const karl_primaries* prim, uint64_t seed, int32_t n_passes,
+                               karl_tallies* out, uint64_t* req_id);
+
+/* Non-blocking: collects every finished request (copies its tallies into the
+ * caller's buffers, releases its device state), admits waiting requests, and
+ * sets *done = 1 if req_id has finished.  A finished id stays known until
+ * polled once with done = 1.  Errors: KARL_ENOTFOUND (unknown id),
+ * KARL_ETIMEOUT / KARL_ECANCELLED (the launch stopped before it finished),
+ * KARL_ECUDA. */
+karl_status karl_server_poll(karl_server* srv, uint64_t req_id, int* done);
+
+/* Size of each output array of a request with this geometry (elements). */
+karl_status karl_server_layout(const karl_server* srv, const karl_geometry* geom,
+                               karl_layout* out);
+
+/* Batch: admit, run and finish every submitted request in as few persistent
+ * launches as the HBM budget allows (one when everything fits), blocking
+ * until the last result is in the caller's buffers. */
+karl_status karl_server_run_all(karl_server* srv);
+
+typedef struct karl_server_stats {
+  int64_t submitted, admitted, completed, collected, waiting;
+  int64_t collisions;          /* summed over collected requests (both passes' last-pass ledgers) */
+  int64_t kernel_launches;
+  int64_t arena_bytes_in_use, arena_bytes_peak;
+  double lane_occupancy;       /* of the last finished launch */
+} karl_server_stats;
+karl_status karl_server_get_stats(const karl_server* srv, karl_server_stats* out);
+
+/* Stop the running launch after the published requests finish, free all
+ * device state.  NULL is ignored. */
+void karl_server_destroy(karl_server* srv);
+
+/* Detail of the last server error (empty if none). */
+const char* karl_server_last_error(const karl_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

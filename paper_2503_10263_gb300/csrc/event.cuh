@@ -125,7 +125,7 @@ __device__ __forceinline__ void range_add(unsigned long long* d, int a, int b, s
 // ---------------------------------------------------------------------------
 // ring cells
 
-__device__ bool ring_put(const Ring& R, Control* ctl, unsigned long long pos, const Lane& p,
+static __device__ bool ring_put(const Ring& R, Control* ctl, unsigned long long pos, const Lane& p,
                          unsigned long long deadline) {
   unsigned long long* cell = R.seq + (pos & R.mask);
   long long spins = 0;
@@ -144,7 +144,7 @@ __device__ bool ring_put(const Ring& R, Control* ctl, unsigned long long pos, co
   return true;
 }
 
-__device__ bool ring_get(const Ring& R, Control* ctl, unsigned long long pos, Lane& p,
+static __device__ bool ring_get(const Ring& R, Control* ctl, unsigned long long pos, Lane& p,
                          unsigned long long deadline) {
   unsigned long long* cell = R.seq + (pos & R.mask);
   long long spins = 0;

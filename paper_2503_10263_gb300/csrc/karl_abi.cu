@@ -17,7 +17,7 @@
 #include <vector>
 
 #include "../../include/karl.h"
-#include "karl_device.cuh"
+#include "host_common.h"
 
 namespace karl {
 cudaError_t launch_transport(bool f32, const Params& P, const Ring& R, Control* ctl,
@@ -32,9 +32,7 @@ using namespace karl;
 namespace {
 
 const double Q_TIME = 1125899906842624.0;
-const double Q_ENERGY = 16777216.0;
 const double C_LIGHT = 299792458.0;
-const double KB_EV = 8.617333262e-5;
 
 template <class T>
 struct DevBuf {
@@ -62,6 +60,8 @@ struct DevBuf {
 struct karl_ctx {
   int device = 0;
   int num_sms = 0;
+  karl_geometry geom;          // copy (n_seg_m3 points at nseg below)
+  ModelInfo model;
   cudaStream_t own_stream = nullptr;
   // copies of the inputs
   double L = 0, dz = 0, area = 1, activity = 1, e_cut = 0, max_life = 0, kT = 0;
@@ -265,8 +265,6 @@ int grid_for(size_t n, int block) {
 // ---------------------------------------------------------------------------
 // helpers
 
-bool is_fin(double x) { return std::isfinite(x); }
-
 karl_status stage_primaries(karl_ctx* ctx, const karl_primaries* pr, cudaStream_t st,
                             const double** z, const double** e, const double** mu,
                             const uint8_t** sp) {
@@ -335,61 +333,15 @@ karl_status ensure_ring(karl_ctx* ctx, unsigned long long cap) {
   return KARL_OK;
 }
 
-// Fill the pass-independent part of the kernel parameters.
+// Kernel parameters of one pass of this context (device buffers set by the caller).
 void base_params(const karl_ctx* c, Params& P, const karl_run_opts* o, int pass) {
-  std::memset(&P, 0, sizeof P);
-  P.nz = c->nz;
-  P.L = c->L;
-  P.dz = c->dz;
+  fill_params(P, c->geom, c->model, pass, o->seed, c->nq, c->colmax);
   P.nseg = c->d_nseg.p;
   P.colgas = c->d_colgas.p;
   P.faces = c->d_faces.p;
   P.ginv = c->nq > 0 ? c->d_ginv.p : nullptr;
-  P.nq = c->nq;
-  P.nq_over_colmax = c->colmax > 0 ? (double)c->nq / c->colmax : 0.0;
-  P.n_energy = c->n_energy;
-  P.e_min = c->e_min;
-  P.inv_e_min = 1.0 / c->e_min;
-  P.log_ratio_h = std::log(c->e_max / c->e_min) / (double)(c->n_energy - 1);
-  P.inv_h = 1.0 / P.log_ratio_h;
   P.sig = c->d_sig_t.p;
   P.sigf = c->d_sigf.p;
-  P.nch = c->nch;
-  for (int k = 0; k < c->nch; ++k) {
-    P.ch[k].kind = c->kind[k];
-    P.ch[k].sin = c->sin[k];
-    P.ch[k].sout = c->sout[k];
-    P.ch[k].loss_q = (long long)std::floor(c->loss[k] * Q_ENERGY);
-    P.ch[k].thr_q = (long long)std::floor(c->loss[k] * Q_ENERGY);
-    P.ch[k].loss_ev = c->loss[k];
-  }
-  for (int s = 0; s < NSP; ++s) {
-    int n = 0;
-    for (int k = 0; k < c->nch; ++k) {
-      if (c->sin[k] != s) continue;
-      if (c->kind[k] == RECOMBINATION && pass != 2) continue;
-      if (n < MAXSPCH) P.sc[s][n++] = (int8_t)k;
-    }
-    P.nsc[s] = n;
-    P.mass[s] = c->mass[s];
-    P.inv_mass[s] = 1.0 / c->mass[s];
-    P.gam[s] = c->mass[s] / c->target_mass;
-    P.inv_1pg2[s] = 1.0 / ((1.0 + P.gam[s]) * (1.0 + P.gam[s]));
-  }
-  P.target_mass = c->target_mass;
-  P.eps_ion = c->eps_ion;
-  P.inv_eps_ion = 1.0 / c->eps_ion;
-  P.kT = c->kT;
-  P.ecut_q = (long long)std::floor(c->e_cut * Q_ENERGY);
-  P.max_coll = c->max_coll;
-  P.max_life = c->max_life;
-  P.track_time = std::isfinite(c->max_life) ? 1 : 0;
-  P.ntb = c->ntb;
-  P.tb_scale = c->ntb / std::log(c->e_max / c->e_min);
-  P.nspec = c->nspec;
-  P.spec_bin_q = (long long)std::llround(c->spec_bin * Q_ENERGY);
-  P.seed = o->seed;
-  P.pass = pass;
 }
 
 // One pass into the context's raw tally buffers (which are zeroed first).
@@ -542,12 +494,6 @@ karl_status build_fields(karl_ctx* ctx, const unsigned long long* d_time1, int64
   return KARL_OK;
 }
 
-bool has_recombination(const karl_ctx* c) {
-  for (int k = 0; k < c->nch; ++k)
-    if (c->kind[k] == RECOMBINATION) return true;
-  return false;
-}
-
 karl_status copy_out(karl_ctx* ctx, void* dst, const void* src, size_t bytes, bool dst_dev,
                      cudaStream_t st) {
   if (!dst || bytes == 0) return KARL_OK;
@@ -593,42 +539,7 @@ const char* karl_last_error(const karl_ctx* ctx) { return ctx ? ctx->err.c_str()
 karl_status karl_create(const karl_geometry* g, const karl_xs* x, karl_ctx** out) {
   if (!out) return KARL_EINVAL;
   *out = nullptr;
-  if (!g || !x) return KARL_EINVAL;
-  if (!(g->length_m > 0) || !is_fin(g->length_m) || g->n_zbins < 1 || g->n_zbins > (1 << 20) ||
-      !g->n_seg_m3 || !(g->area_m2 > 0) || !(g->activity_bq > 0) || !(g->e_cut_ev >= 0) ||
-      !(g->max_lifetime_s > 0) || !(g->gas_temperature_k >= 0) || g->n_tebins < 1 ||
-      g->n_tebins > 4096 || g->n_spec_bins < 1 || g->n_spec_bins > (1 << 24) ||
-      !(g->spec_bin_ev > 0) || !(g->target_mass_ev > 0))
-    return KARL_EINVAL;
-  for (int s = 0; s < NSP; ++s)
-    if (!(g->species_mass_ev[s] > 0)) return KARL_EINVAL;
-  for (int j = 0; j < g->n_zbins; ++j)
-    if (!(g->n_seg_m3[j] >= 0) || !is_fin(g->n_seg_m3[j])) return KARL_EINVAL;
-  if (x->n_energy < 2 || !(x->e_min_ev > 0) || !(x->e_max_ev > x->e_min_ev) ||
-      x->n_channels < 0 || x->n_channels > KARL_MAX_CHANNELS || !(x->ioniz_eps_ev > 0))
-    return KARL_EINVAL;
-  if (x->n_channels > 0 &&
-      (!x->kind || !x->species_in || !x->species_out || !x->loss_ev || !x->sigma_m2))
-    return KARL_EINVAL;
-  int per_sp[NSP] = {0, 0, 0}, rec_sp[NSP] = {0, 0, 0};
-  for (int k = 0; k < x->n_channels; ++k) {
-    int kd = x->kind[k], si = x->species_in[k], so = x->species_out[k];
-    if (kd < 0 || kd > RECOMBINATION || si < 0 || si >= NSP || so < -1 || so >= NSP ||
-        !(x->loss_ev[k] >= 0) || !is_fin(x->loss_ev[k]))
-      return KARL_EINVAL;
-    if ((kd == CLUSTERING || kd == RECOMBINATION) && so < 0) return KARL_EINVAL;
-    if (kd == RECOMBINATION && si != SP_E && so != SP_E) return KARL_EINVAL;
-    if (kd == RECOMBINATION && si == SP_E && so == SP_E) return KARL_EINVAL;
-    per_sp[si]++;
-    if (kd == RECOMBINATION) rec_sp[si]++;
-    for (int i = 0; i < x->n_energy; ++i) {
-      double v = x->sigma_m2[(size_t)k * x->n_energy + i];
-      if (!(v >= 0) || !is_fin(v)) return KARL_EINVAL;
-    }
-  }
-  for (int s = 0; s < NSP; ++s)
-    if (per_sp[s] > MAXSPCH || rec_sp[s] > 2) return KARL_EINVAL;
-
+  if (!geometry_ok(g) || !xs_ok(x)) return KARL_EINVAL;
   karl_ctx* ctx = new (std::nothrow) karl_ctx();
   if (!ctx) return KARL_ENOMEM;
   std::memset(&ctx->stats, 0, sizeof ctx->stats);
@@ -648,7 +559,7 @@ karl_status karl_create(const karl_geometry* g, const karl_xs* x, karl_ctx** out
   ctx->e_cut = g->e_cut_ev;
   ctx->max_coll = g->max_collisions;
   ctx->max_life = g->max_lifetime_s;
-  ctx->kT = KB_EV * g->gas_temperature_k;
+  ctx->kT = HOST_KB_EV * g->gas_temperature_k;
   ctx->ntb = g->n_tebins;
   ctx->nspec = g->n_spec_bins;
   ctx->spec_bin = g->spec_bin_ev;
@@ -671,31 +582,15 @@ karl_status karl_create(const karl_geometry* g, const karl_xs* x, karl_ctx** out
   } catch (...) {
     return bail(KARL_ENOMEM);
   }
-  // gas column to each face, and its inverse on nq even steps: ginv[q] is the
-  // largest face k with col[k] <= q * colmax / nq (a search bracket)
-  std::vector<double> col(ctx->nz + 1, 0.0);
-  for (int j = 0; j < ctx->nz; ++j) col[j + 1] = col[j] + ctx->nseg[j] * ctx->dz;
-  ctx->colmax = col[ctx->nz];
-  ctx->nq = ctx->colmax > 0 ? std::min(8192, std::max(1024, 2 * ctx->nz)) : 0;
-  std::vector<int> ginv(ctx->nq + 1, 0);
-  std::vector<double> faces(ctx->nz + 1);
-  for (int k = 0; k < ctx->nz; ++k) faces[k] = (double)k * ctx->dz;
-  faces[ctx->nz] = ctx->L;
-  for (int q = 0, k = 0; q <= ctx->nq; ++q) {
-    double c = (double)q * ctx->colmax / ctx->nq;
-    while (k < ctx->nz && col[k + 1] <= c) ++k;
-    ginv[q] = k;
-  }
-  // [node][channel] copies for the transport kernel (all channels of one node
-  // in adjacent words), channel-major copy for the field builder
-  std::vector<double> sig_t(ctx->sigma.size());
-  std::vector<float> sigf(ctx->sigma.size());
-  for (int k = 0; k < ctx->nch; ++k)
-    for (int i = 0; i < ctx->n_energy; ++i) {
-      double v = ctx->sigma[(size_t)k * ctx->n_energy + i];
-      sig_t[(size_t)i * ctx->nch + k] = v;
-      sigf[(size_t)i * ctx->nch + k] = (float)v;
-    }
+  ctx->geom = *g;
+  ctx->geom.n_seg_m3 = ctx->nseg.data();
+  ctx->model = model_info(x);
+  const ColumnTables tabs = column_tables(ctx->nseg.data(), ctx->nz, ctx->L);
+  ctx->nq = tabs.nq;
+  ctx->colmax = tabs.colmax;
+  std::vector<double> sig_t;
+  std::vector<float> sigf;
+  node_major_tables(x, sig_t, sigf);
   size_t nsig = std::max<size_t>(ctx->sigma.size(), 1);
   if (ctx->d_nseg.ensure(ctx->nz) || ctx->d_colgas.ensure(ctx->nz + 1) ||
       ctx->d_faces.ensure(ctx->nz + 1) ||
@@ -703,9 +598,10 @@ karl_status karl_create(const karl_geometry* g, const karl_xs* x, karl_ctx** out
       ctx->d_ledger.ensure(LEDGER) || ctx->d_ginv.ensure(ctx->nq + 1))
     return bail(KARL_ENOMEM);
   if (cudaMemcpy(ctx->d_nseg.p, ctx->nseg.data(), ctx->nz * 8, cudaMemcpyHostToDevice) ||
-      cudaMemcpy(ctx->d_colgas.p, col.data(), (ctx->nz + 1) * 8, cudaMemcpyHostToDevice) ||
-      cudaMemcpy(ctx->d_faces.p, faces.data(), (ctx->nz + 1) * 8, cudaMemcpyHostToDevice) ||
-      cudaMemcpy(ctx->d_ginv.p, ginv.data(), (ctx->nq + 1) * sizeof(int), cudaMemcpyHostToDevice) ||
+      cudaMemcpy(ctx->d_colgas.p, tabs.col.data(), (ctx->nz + 1) * 8, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(ctx->d_faces.p, tabs.faces.data(), (ctx->nz + 1) * 8, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(ctx->d_ginv.p, tabs.ginv.data(), (ctx->nq + 1) * sizeof(int),
+                 cudaMemcpyHostToDevice) ||
       (ctx->sigma.size() &&
        (cudaMemcpy(ctx->d_sig.p, ctx->sigma.data(), ctx->sigma.size() * 8, cudaMemcpyHostToDevice) ||
         cudaMemcpy(ctx->d_sig_t.p, sig_t.data(), sig_t.size() * 8, cudaMemcpyHostToDevice) ||
@@ -833,7 +729,7 @@ karl_status karl_run(karl_ctx* ctx, const karl_primaries* pr, const karl_run_opt
   size_t nt = n_time(ctx);
   CK(ctx->d_time1.ensure(nt));
   CK(cudaMemcpyAsync(ctx->d_time1.p, ctx->d_time.p, nt * 8, cudaMemcpyDeviceToDevice, st));
-  if (o->n_passes == 2 && has_recombination(ctx)) {
+  if (o->n_passes == 2 && has_recombination(ctx->model)) {
     s = build_fields(ctx, (const unsigned long long*)ctx->d_time1.p, pr->n_decays, st);
     if (s) return s;
     s = run_one_pass(ctx, pr, o, 2, pz, pe, pmu, psp, pp, st);

@@ -157,7 +157,7 @@ __device__ __forceinline__ bool pass_emptied(unsigned long long old, unsigned lo
 }
 
 template <bool F32>
-__global__ void __launch_bounds__(256) multi_kernel(SlotDesc* D, SlotCtl* C, MultiCtl* M, Ring R,
+__global__ void __launch_bounds__(256, 2) multi_kernel(SlotDesc* D, SlotCtl* C, MultiCtl* M, Ring R,
                                                     const volatile int* cancel,
                                                     unsigned long long timeout_ns) {
   const unsigned long long deadline = globaltimer_ns() + timeout_ns;

@@ -54,7 +54,7 @@ __device__ void stage_tables(Params& SP, const Params& Pk, double* dyn, int dyn_
 }
 
 template <bool F32>
-__global__ void __launch_bounds__(256) transport_kernel(const Params Pk, Ring R, Control* ctl,
+__global__ void __launch_bounds__(256, 2) transport_kernel(const Params Pk, Ring R, Control* ctl,
                                                         const volatile int* cancel,
                                                         unsigned long long timeout_ns,
                                                         int dyn_doubles) {

@@ -341,3 +341,176 @@ class Context:
 
     def cancel(self):
         karl_cancel(self.ctx)
+
+
+# ---- batched / served form --------------------------------------------------
+
+class ServerOpts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("max_slots", C.c_int32),
+                ("hbm_budget_bytes", C.c_int64), ("timeout_s", C.c_double),
+                ("block_size", C.c_int32), ("blocks_per_sm", C.c_int32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
+                ("collected", C.c_int64), ("waiting", C.c_int64), ("collisions", C.c_int64),
+                ("kernel_launches", C.c_int64), ("arena_bytes_in_use", C.c_int64),
+                ("arena_bytes_peak", C.c_int64), ("lane_occupancy", C.c_double)]
+
+
+_server_bound = False
+
+
+def _bind_server(lib):
+    global _server_bound
+    if _server_bound:
+        return
+    P = C.POINTER
+    lib.karl_server_create.argtypes = [P(XS), P(ServerOpts), P(C.c_void_p)]
+    lib.karl_server_submit.argtypes = [C.c_void_p, P(Geometry), P(Primaries), C.c_uint64,
+                                       C.c_int32, P(Tallies), P(C.c_uint64)]
+    lib.karl_server_poll.argtypes = [C.c_void_p, C.c_uint64, P(C.c_int)]
+    lib.karl_server_layout.argtypes = [C.c_void_p, P(Geometry), P(Layout)]
+    lib.karl_server_run_all.argtypes = [C.c_void_p]
+    lib.karl_server_get_stats.argtypes = [C.c_void_p, P(ServerStats)]
+    lib.karl_server_destroy.argtypes = [C.c_void_p]
+    lib.karl_server_destroy.restype = None
+    lib.karl_server_last_error.argtypes = [C.c_void_p]
+    lib.karl_server_last_error.restype = C.c_char_p
+    for f in ("karl_server_create", "karl_server_submit", "karl_server_poll", "karl_server_layout",
+              "karl_server_run_all", "karl_server_get_stats"):
+        getattr(lib, f).restype = C.c_int
+    _server_bound = True
+
+
+def _geometry(prob, keep):
+    g = Geometry()
+    nseg = np.ascontiguousarray(prob.n_seg_m3, np.float64)
+    keep.append(nseg)
+    g.length_m = prob.length_m
+    g.n_zbins = prob.n_zbins
+    g.n_seg_m3 = _dptr(nseg)
+    g.area_m2 = prob.area_m2
+    g.activity_bq = prob.activity_bq
+    g.e_cut_ev = prob.e_cut_ev
+    g.max_collisions = min(int(prob.max_collisions), 0xFFFFFFFF)
+    g.max_lifetime_s = prob.max_lifetime_s if math.isfinite(prob.max_lifetime_s) else math.inf
+    g.gas_temperature_k = prob.gas_temperature_k
+    g.n_tebins = prob.n_tebins
+    g.n_spec_bins = prob.n_spec_bins
+    g.spec_bin_ev = prob.spec_bin_ev
+    for i in range(3):
+        g.species_mass_ev[i] = float(prob.species_mass_ev[i])
+    g.target_mass_ev = prob.target_mass_ev
+    return g
+
+
+def _xs(prob, keep):
+    x = XS()
+    kind = np.array([c.kind for c in prob.channels], np.int32)
+    sin = np.array([c.species_in for c in prob.channels], np.int32)
+    sout = np.array([c.species_out for c in prob.channels], np.int32)
+    loss = np.array([c.loss_ev for c in prob.channels], np.float64)
+    sig = np.ascontiguousarray(prob.sigma_matrix() if prob.channels
+                               else np.zeros((0, prob.n_energy)), np.float64)
+    keep += [kind, sin, sout, loss, sig]
+    x.n_energy = prob.n_energy
+    x.e_min_ev = prob.e_min_ev
+    x.e_max_ev = prob.e_max_ev
+    x.n_channels = prob.n_channels
+    x.kind, x.species_in, x.species_out = _iptr(kind), _iptr(sin), _iptr(sout)
+    x.loss_ev, x.sigma_m2 = _dptr(loss), _dptr(sig)
+    x.ioniz_eps_ev = prob.ioniz_eps_ev
+    return x
+
+
+class Server:
+    """Many requests in one persistent launch (karl_server_*).  The model
+    (channels and cross-section tables) is taken from `model_prob`; every
+    request brings its own geometry, gas profile, primaries and seed."""
+
+    def __init__(self, model_prob, precision: int = FP64, max_slots: int = 256,
+                 hbm_budget_bytes: int = 0, timeout_s: float = 3600.0, block_size: int = 0,
+                 blocks_per_sm: int = 0):
+        lib = load()
+        _bind_server(lib)
+        self.lib = lib
+        self.model = model_prob
+        keep = []
+        x = _xs(model_prob, keep)
+        o = ServerOpts(precision, max_slots, hbm_budget_bytes, timeout_s, block_size, blocks_per_sm)
+        h = C.c_void_p()
+        st = lib.karl_server_create(C.byref(x), C.byref(o), C.byref(h))
+        if st != OK:
+            raise KarlError(st, karl_status_string(st))
+        self.h = h
+        self._pending = {}             # req id -> (tallies dict, keep-alive objects)
+
+    def _check(self, st):
+        if st != OK:
+            raise KarlError(st, f"{karl_status_string(st)}: "
+                                f"{self.lib.karl_server_last_error(self.h).decode()}")
+
+    def _empty_tallies(self, prob):
+        nz, ntb = prob.n_zbins, prob.n_tebins
+        return {
+            "spectrum": np.zeros((2, N_SPECIES, prob.n_spec_bins + 1), np.uint64),
+            "time_fx": np.zeros((N_SPECIES, nz + 2, ntb), np.uint64),
+            "cross_pos": np.zeros((N_SPECIES, nz + 1), np.uint64),
+            "cross_neg": np.zeros((N_SPECIES, nz + 1), np.uint64),
+            "recomb": np.zeros((N_SPECIES, nz), np.uint64),
+            "ledger": np.zeros(LEDGER_LEN, np.int64),
+            "chan_count": np.zeros(max(self.model.n_channels, 1), np.uint64),
+            "density": np.zeros((N_SPECIES, nz), np.float64),
+            "current": np.zeros((N_SPECIES, nz + 1), np.float64),
+            "field": np.zeros((N_SPECIES, nz, ntb), np.float64),
+        }
+
+    def submit(self, prob, prims, seed: int, n_passes: Optional[int] = None,
+               pid_offset: int = 0) -> int:
+        keep = []
+        g = _geometry(prob, keep)
+        ps, pk = Context.host_primaries(prims, pid_offset)
+        keep.append(pk)
+        t = self._empty_tallies(prob)
+        ts = Tallies()
+        for k in ("spectrum", "time_fx", "cross_pos", "cross_neg", "recomb", "ledger",
+                  "chan_count", "density", "current", "field"):
+            setattr(ts, k, t[k].ctypes.data)
+        ts.per_primary = None
+        ts.on_device = 0
+        rid = C.c_uint64()
+        npass = prob.n_passes if n_passes is None else n_passes
+        self._check(self.lib.karl_server_submit(self.h, C.byref(g), C.byref(ps), seed, npass,
+                                                C.byref(ts), C.byref(rid)))
+        self._pending[rid.value] = (t, keep)
+        return rid.value
+
+    def poll(self, req_id: int):
+        """(done, tallies or None)."""
+        d = C.c_int()
+        self._check(self.lib.karl_server_poll(self.h, req_id, C.byref(d)))
+        if d.value:
+            t, _ = self._pending.pop(req_id)
+            t["chan_count"] = t["chan_count"][:self.model.n_channels]
+            return True, t
+        return False, None
+
+    def run_all(self):
+        self._check(self.lib.karl_server_run_all(self.h))
+
+    def stats(self) -> ServerStats:
+        s = ServerStats()
+        self._check(self.lib.karl_server_get_stats(self.h, C.byref(s)))
+        return s
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.karl_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
