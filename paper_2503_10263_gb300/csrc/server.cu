@@ -142,6 +142,7 @@ struct karl_server {
   int* h_done = nullptr;                       // mapped: written by the kernel
   int* d_done = nullptr;
   int* h_flag = nullptr;                       // pinned 1 (shutdown / cancel source)
+  char* h_zero = nullptr;                      // pinned zeros: clears device memory by copy
   cudaStream_t kstream = nullptr, cstream = nullptr;
   bool running = false;
   unsigned long long seq = 0;                  // requests published so far
@@ -172,6 +173,23 @@ karl_status sfail(karl_server* s, karl_status st, const char* fmt, ...) {
       return sfail(srv, e_ == cudaErrorMemoryAllocation ? KARL_ENOMEM : KARL_ECUDA, "%s: %s", \
                    #call, cudaGetErrorString(e_));                              \
   } while (0)
+
+// The persistent launch holds every SM, so nothing may launch a kernel while
+// it runs (a memset is a kernel): device memory of a request is cleared by
+// copies from pinned zeros, which the copy engines do beside the launch.
+constexpr size_t ZERO_CHUNK = 16u << 20;
+
+cudaError_t zero_by_copy(const karl_server* srv, void* dst, size_t bytes, cudaStream_t st) {
+  char* d = (char*)dst;
+  while (bytes) {
+    const size_t n = std::min(bytes, ZERO_CHUNK);
+    cudaError_t e = cudaMemcpyAsync(d, srv->h_zero, n, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    d += n;
+    bytes -= n;
+  }
+  return cudaSuccess;
+}
 
 size_t footprint(const Sizes& z) {
   size_t b = 0;
@@ -280,7 +298,7 @@ karl_status admit(karl_server* srv, Request& r) {
   SCK(cudaMemcpyAsync(col, r.tabs.col.data(), (z.nz + 1) * 8, cudaMemcpyHostToDevice, cs));
   SCK(cudaMemcpyAsync(faces, r.tabs.faces.data(), (z.nz + 1) * 8, cudaMemcpyHostToDevice, cs));
   SCK(cudaMemcpyAsync(ginv, r.tabs.ginv.data(), (z.nq + 1) * 4, cudaMemcpyHostToDevice, cs));
-  SCK(cudaMemsetAsync(tally0, 0, tally_bytes, cs));
+  SCK(zero_by_copy(srv, tally0, tally_bytes, cs));
   // descriptor
   const int final_pass = (r.n_passes == 2 && has_recombination(srv->model)) ? 2 : 1;
   SlotDesc& d = srv->h_desc[slot];
@@ -345,7 +363,7 @@ karl_status admit(karl_server* srv, Request& r) {
   if (z.n == 0) {
     // nothing to transport: zero outputs, finished at once
     const size_t out_bytes = (size_t)((char*)(r.density + (size_t)NSP * z.nz) - (char*)time1);
-    SCK(cudaMemsetAsync(time1, 0, out_bytes, cs));
+    SCK(zero_by_copy(srv, time1, out_bytes, cs));
     SCK(cudaStreamSynchronize(cs));
     srv->h_done[slot] = 1;
     r.state = REQ_ADMITTED;
@@ -500,6 +518,16 @@ karl_status progress(karl_server* srv) {
     if (a) return a;
     srv->waiting.pop_front();
   }
+  if (!srv->running) {
+    // published work whose launch has already left (it saw shutdown before
+    // the request was published): start another launch for it
+    for (auto& kv : srv->reqs)
+      if (kv.second.state == REQ_ADMITTED && !srv->h_done[kv.second.slot]) {
+        karl_status l = launch(srv);
+        if (l) return l;
+        break;
+      }
+  }
   srv->stats.waiting = (int64_t)srv->waiting.size();
   srv->stats.arena_bytes_in_use = (int64_t)srv->arena.in_use;
   srv->stats.arena_bytes_peak = (int64_t)srv->arena.peak;
@@ -567,8 +595,10 @@ karl_status karl_server_create(const karl_xs* xs, const karl_server_opts* opts,
       cudaHostAlloc(&srv->h_pubval, sizeof(unsigned long long) * MAX_SLOTS, cudaHostAllocDefault) ||
       cudaHostAlloc(&srv->h_done, sizeof(int) * MAX_SLOTS, cudaHostAllocMapped) ||
       cudaHostGetDevicePointer(&srv->d_done, srv->h_done, 0) ||
-      cudaHostAlloc(&srv->h_flag, sizeof(int), cudaHostAllocDefault))
+      cudaHostAlloc(&srv->h_flag, sizeof(int), cudaHostAllocDefault) ||
+      cudaHostAlloc(&srv->h_zero, ZERO_CHUNK, cudaHostAllocDefault))
     return bail(KARL_ENOMEM);
+  std::memset(srv->h_zero, 0, ZERO_CHUNK);
   std::memset(srv->h_done, 0, sizeof(int) * MAX_SLOTS);
   srv->arena.init((size_t)o.hbm_budget_bytes);
   if (sig_t.size() &&
@@ -741,6 +771,7 @@ void karl_server_destroy(karl_server* srv) {
   if (srv->h_pubval) cudaFreeHost(srv->h_pubval);
   if (srv->h_done) cudaFreeHost(srv->h_done);
   if (srv->h_flag) cudaFreeHost(srv->h_flag);
+  if (srv->h_zero) cudaFreeHost(srv->h_zero);
   if (srv->kstream) cudaStreamDestroy(srv->kstream);
   if (srv->cstream) cudaStreamDestroy(srv->cstream);
   delete srv;
