@@ -38,9 +38,9 @@ BYTES_PER_EVENT_FP32 = 80
 # FP64 pipe of one SM for this many cycles (ncu sm__pipe_fp64_cycles_active x
 # elapsed cycles x SMs / collisions, transport kernel, 2e5-decay case of this
 # workload); None: not measured for this form of the kernel.
-FP64_PIPE_CYCLES_PER_COLLISION = {"fp64": 191.0, "fp32": None}
-# DRAM bytes per collision of the same capture (read + write)
-DRAM_BYTES_PER_COLLISION = {"fp64": 23.49e6 / 331927149, "fp32": None}
+FP64_PIPE_CYCLES_PER_COLLISION = {"fp64": 193.0, "fp32": 84.0}
+# DRAM bytes per collision of the same captures (read + write)
+DRAM_BYTES_PER_COLLISION = {"fp64": 22.31e6 / 331927149, "fp32": 25.82e6 / 331928948}
 WORKLOAD = ("config2: 1e7 decays (1e7 beta e- + 1e7 thermal T2+), parabolic profile with "
             "5e21 m^-2 column, L = 10 m, 1000 z segments, 7 e- channels + T2+ clustering + "
             "e-/ion recombination, two passes")
