@@ -341,6 +341,134 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+WORKLOAD4 = ("config4: 256 source configurations in one persistent launch (column U[0.1,1] x "
+             "5e21 m^-2, L U[2,10] m, decays log-U[1e3,1e6], full channel set, two passes)")
+WORKLOAD5 = ("config5: Poisson arrivals of config-4-style requests (decays log-U[1e3,1e6]), "
+             "admitted by HBM footprint into one running launch (continuous batching)")
+
+
+def _percentile(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = (len(xs) - 1) * q / 100.0
+    f = int(math.floor(k))
+    c = min(f + 1, len(xs) - 1)
+    return xs[f] + (xs[c] - xs[f]) * (k - f)
+
+
+def run_batch(args):
+    """config 4: the whole batch of source configurations per step, through
+    the server API (inputs copied in and tallies read back every step)."""
+    import torch
+
+    from paper_2503_10263_gb300 import autotune, build as kbuild, inputs, karl
+    kbuild.build()
+    torch.cuda.set_device(0)
+    prec = karl.FP32 if args.precision == "fp32" else karl.FP64
+    block, bps = autotune.tune(prec)
+    batch = inputs.config4_batch(n_configs=args.configs, meta_seed=1)
+    n_decays = sum(pr.n_decays for _, pr, _ in batch)
+    h2d = sum(pr.n * 25 for _, pr, _ in batch)
+
+    def step():
+        srv = karl.Server(batch[0][0], precision=prec, hbm_budget_bytes=args.budget_gb << 30,
+                          timeout_s=args.timeout, block_size=block, blocks_per_sm=bps)
+        ids = [srv.submit(p, pr, s) for p, pr, s in batch]
+        srv.run_all()
+        coll = 0
+        d2h = 0
+        for rid in ids:
+            done, t = srv.poll(rid)
+            coll += int(t["ledger"][karl.N_COLLISIONS])
+            d2h += sum(v.nbytes for v in t.values())
+        st = srv.stats()
+        srv.close()
+        return coll, st.kernel_ms, st.kernel_launches, d2h, st.lane_occupancy
+
+    for _ in range(args.warmup):
+        step()
+    sampler = ClockSampler(0)
+    sampler.start()
+    t0 = time.perf_counter()
+    coll = kms = launches = d2h = 0
+    occ = []
+    for _ in range(args.steps):
+        c, k, l, d, o = step()
+        coll += c
+        kms += k
+        launches += l
+        d2h = d
+        occ.append(o)
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    line = {
+        "metric": "collision events/s", "value": coll / (kms / 1000.0), "unit": "collision events/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * wall / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == karl.FP32 else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD4, "configs": args.configs, "decays": n_decays,
+                   "block_size": block, "blocks_per_sm": bps, "launches_per_step": launches / args.steps},
+        "primaries_per_s": n_decays * args.steps / (kms / 1000.0),
+        "e2e": {"value": coll / wall, "unit": "collision events/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "lane_occupancy": occ, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """config 5: Poisson arrivals submitted on time into one running launch;
+    latency = completion - arrival on the host clock."""
+    import torch
+
+    from paper_2503_10263_gb300 import autotune, build as kbuild, inputs, karl
+    kbuild.build()
+    torch.cuda.set_device(0)
+    prec = karl.FP32 if args.precision == "fp32" else karl.FP64
+    block, bps = autotune.tune(prec)
+    reqs = inputs.config5_requests(duration_s=args.serve_seconds, rate_hz=args.rate, arrival_seed=1)
+    srv = karl.Server(reqs[0][1], precision=prec, hbm_budget_bytes=args.budget_gb << 30,
+                      max_slots=1024, timeout_s=args.timeout, block_size=block, blocks_per_sm=bps)
+    sampler = ClockSampler(0)
+    sampler.start()
+    t0 = time.perf_counter()
+    nxt = 0
+    open_ids = {}
+    lat, coll = [], 0
+    while nxt < len(reqs) or open_ids:
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and reqs[nxt][0] <= now:
+            ta, p, pr, s = reqs[nxt]
+            open_ids[srv.submit(p, pr, s)] = ta
+            nxt += 1
+        for rid in list(open_ids):
+            done, t = srv.poll(rid)
+            if done:
+                lat.append(time.perf_counter() - t0 - open_ids.pop(rid))
+                coll += int(t["ledger"][karl.N_COLLISIONS])
+        time.sleep(0.0005)
+    wall = time.perf_counter() - t0
+    srv.run_all()
+    st = srv.stats()
+    srv.close()
+    clocks = sampler.stop()
+    offered = sum(pr.n_decays for _, _, pr, _ in reqs)
+    line = {
+        "metric": "p99 request latency", "value": _percentile(lat, 99), "unit": "s",
+        "higher_is_better": False, "n_gpus": 1, "steps": 1, "warmup": 0,
+        "ms_per_step": 1000.0 * wall, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == karl.FP32 else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD5, "rate_hz": args.rate, "arrival_seconds": args.serve_seconds,
+                   "requests": len(reqs), "decays": offered, "block_size": block,
+                   "blocks_per_sm": bps},
+        "p50_latency_s": _percentile(lat, 50), "p99_latency_s": _percentile(lat, 99),
+        "sustained_collisions_per_s": coll / wall, "kernel_launches": st.kernel_launches,
+        "arena_bytes_peak": st.arena_bytes_peak, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -354,9 +482,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-s", type=float, default=10.0)
+    ap.add_argument("--workload", choices=["config2", "config4", "config5"], default="config2")
+    ap.add_argument("--configs", type=int, default=256)
+    ap.add_argument("--budget-gb", type=int, default=48)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--rate", type=float, default=50.0)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "config4":
+        run_batch(args)
+    elif args.workload == "config5":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -286,6 +286,7 @@ typedef struct karl_server_stats {
   int64_t kernel_launches;
   int64_t arena_bytes_in_use, arena_bytes_peak;
   double lane_occupancy;       /* of the last finished launch */
+  double kernel_ms;            /* device time of the finished launches (CUDA events) */
 } karl_server_stats;
 karl_status karl_server_get_stats(const karl_server* srv, karl_server_stats* out);
 

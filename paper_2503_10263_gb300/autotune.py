@@ -1,0 +1,96 @@
+"""Launch-shape autotuner for the multi-request (batched / served) kernel.
+
+The persistent kernel has no compaction pass to schedule: lanes refill from
+their warp's product queue, the shared ring and the request bitmap every
+iteration.  What remains to choose per device and precision is the launch
+shape: threads per block and resident blocks per SM (which set warps per SM
+against the 128-register budget and the per-warp queues in shared memory).
+The tuner times each candidate on a small sample batch through the server
+API and keeps the fastest in a JSON cache keyed by device and precision.
+"""
+from __future__ import annotations
+
+import json
+import os
+import time
+from typing import Dict, Optional, Tuple
+
+CANDIDATES = [(256, 2), (256, 1), (128, 4), (128, 2), (64, 8)]
+
+
+def _cache_path() -> str:
+    base = os.environ.get("KARL_CACHE_DIR") or os.path.join(os.path.expanduser("~"), ".cache")
+    return os.path.join(base, "karl_autotune.json")
+
+
+def _load() -> Dict[str, list]:
+    try:
+        with open(_cache_path()) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _store(d: Dict[str, list]) -> None:
+    path = _cache_path()
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + f".{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(d, f, indent=1)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+
+
+def device_key(precision: int) -> str:
+    import torch
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return f"{p.name}|sm{p.major}{p.minor}|{p.multi_processor_count}|prec{precision}"
+
+
+def sample_batch(n_configs: int = 12, seed: int = 77):
+    """Small config-4-style batch: uneven columns, lengths and sizes."""
+    from paper_2503_10263_gb300 import inputs
+    return inputs.config4_batch(n_configs=n_configs, meta_seed=seed, np_lo=1e3, np_hi=2e4)
+
+
+def time_shape(batch, precision: int, block: int, bps: int) -> Tuple[float, int]:
+    """Seconds for one batch with this launch shape, and its collisions."""
+    from paper_2503_10263_gb300 import karl
+    srv = karl.Server(batch[0][0], precision=precision, hbm_budget_bytes=8 << 30,
+                      timeout_s=600, block_size=block, blocks_per_sm=bps)
+    try:
+        ids = [srv.submit(p, pr, s) for p, pr, s in batch]
+        t0 = time.perf_counter()
+        srv.run_all()
+        dt = time.perf_counter() - t0
+        coll = 0
+        for rid in ids:
+            done, t = srv.poll(rid)
+            coll += int(t["ledger"][karl.N_COLLISIONS])
+    finally:
+        srv.close()
+    return dt, coll
+
+
+def tune(precision: int, force: bool = False, batch=None, verbose: bool = False) -> Tuple[int, int]:
+    """(block_size, blocks_per_sm) for the multi-request kernel, cached."""
+    key = device_key(precision)
+    cache = _load()
+    if not force and key in cache:
+        b, n = cache[key][:2]
+        return int(b), int(n)
+    batch = batch or sample_batch()
+    best: Optional[Tuple[float, int, int]] = None
+    time_shape(batch, precision, *CANDIDATES[0])           # warm-up (module load, clocks)
+    for block, bps in CANDIDATES:
+        dt, coll = time_shape(batch, precision, block, bps)
+        rate = coll / dt
+        if verbose:
+            print(f"autotune block={block} blocks/SM={bps}: {rate:.3e} collisions/s")
+        if best is None or rate > best[0]:
+            best = (rate, block, bps)
+    cache[key] = [best[1], best[2], best[0]]
+    _store(cache)
+    return best[1], best[2]

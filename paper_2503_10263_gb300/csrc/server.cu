@@ -144,6 +144,7 @@ struct karl_server {
   int* h_flag = nullptr;                       // pinned 1 (shutdown / cancel source)
   char* h_zero = nullptr;                      // pinned zeros: clears device memory by copy
   cudaStream_t kstream = nullptr, cstream = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;    // around the current launch
   bool running = false;
   unsigned long long seq = 0;                  // requests published so far
   std::vector<int> slot_req;                   // slot -> request index (-1 free)
@@ -226,9 +227,11 @@ karl_status launch(karl_server* srv) {
   SCK(multi_occupancy(f32, srv->opts.block_size, &bps));
   if (srv->opts.blocks_per_sm > 0) bps = std::min(bps, (int)srv->opts.blocks_per_sm);
   bps = std::max(bps, 1);
+  SCK(cudaEventRecord(srv->ev0, srv->kstream));
   SCK(launch_multi(f32, srv->d_desc, srv->d_ctl, srv->d_M, srv->ring, srv->d_cancel,
                    (unsigned long long)(srv->opts.timeout_s * 1e9), srv->num_sms * bps,
                    srv->opts.block_size, srv->kstream));
+  SCK(cudaEventRecord(srv->ev1, srv->kstream));
   srv->running = true;
   srv->stats.kernel_launches += 1;
   return KARL_OK;
@@ -436,6 +439,8 @@ karl_status reap_launch(karl_server* srv) {
   if (q != cudaSuccess) return sfail(srv, KARL_ECUDA, "launch: %s", cudaGetErrorString(q));
   Control hc;
   SCK(cudaMemcpy(&hc, &srv->d_M->c, sizeof hc, cudaMemcpyDeviceToHost));
+  float ms = 0.0f;
+  if (cudaEventElapsedTime(&ms, srv->ev0, srv->ev1) == cudaSuccess) srv->stats.kernel_ms += ms;
   srv->stats.lane_occupancy =
       hc.busy_iters + hc.idle_iters
           ? (double)hc.busy_lane_iters / (32.0 * (double)(hc.busy_iters + hc.idle_iters))
@@ -610,7 +615,8 @@ karl_status karl_server_create(const karl_xs* xs, const karl_server_opts* opts,
   if (cudaMemset(srv->d_ctl, 0, sizeof(SlotCtl) * MAX_SLOTS) ||
       cudaMemset(srv->d_M, 0, sizeof(MultiCtl)) || cudaMemset(srv->d_cancel, 0, sizeof(int)) ||
       cudaStreamCreateWithFlags(&srv->kstream, cudaStreamNonBlocking) ||
-      cudaStreamCreateWithFlags(&srv->cstream, cudaStreamNonBlocking))
+      cudaStreamCreateWithFlags(&srv->cstream, cudaStreamNonBlocking) ||
+      cudaEventCreate(&srv->ev0) || cudaEventCreate(&srv->ev1))
     return bail(KARL_ECUDA);
   if (ensure_ring(srv)) return bail(KARL_ENOMEM);
   *out = srv;
@@ -772,6 +778,8 @@ void karl_server_destroy(karl_server* srv) {
   if (srv->h_done) cudaFreeHost(srv->h_done);
   if (srv->h_flag) cudaFreeHost(srv->h_flag);
   if (srv->h_zero) cudaFreeHost(srv->h_zero);
+  if (srv->ev0) cudaEventDestroy(srv->ev0);
+  if (srv->ev1) cudaEventDestroy(srv->ev1);
   if (srv->kstream) cudaStreamDestroy(srv->kstream);
   if (srv->cstream) cudaStreamDestroy(srv->cstream);
   delete srv;

@@ -218,20 +218,25 @@ def beta_pdf(e_ev: np.ndarray, e0: float = 18600.0, z_daughter: int = 2) -> np.n
     return out
 
 
+_BETA_CDF = {}
+
+
+def _beta_cdf(e0: float):
+    """Tabulated CDF of the allowed spectrum on 2^18 + 1 points (trapezoid rule)."""
+    if e0 not in _BETA_CDF:
+        grid = np.linspace(0.0, e0, (1 << 18) + 1)
+        pdf = beta_pdf(grid, e0)
+        pdf[0] = beta_pdf(np.array([grid[1] * 1e-6]), e0)[0]   # finite limit at E -> 0
+        cdf = np.concatenate([[0.0], np.cumsum(0.5 * (pdf[1:] + pdf[:-1]) * np.diff(grid))])
+        _BETA_CDF[e0] = (grid, cdf / cdf[-1])
+    return _BETA_CDF[e0]
+
+
 def sample_beta(rng: np.random.Generator, n: int, e0: float = 18600.0) -> np.ndarray:
-    """Rejection sampling of the allowed spectrum (the injector's method)."""
-    grid = np.linspace(1e-6, e0, 200001)
-    fmax = float(beta_pdf(grid, e0).max()) * 1.02
-    out = np.empty(n, dtype=np.float64)
-    filled = 0
-    while filled < n:
-        m = int((n - filled) * 2.2) + 64
-        e = rng.uniform(0.0, e0, m)
-        keep = e[rng.uniform(0.0, fmax, m) < beta_pdf(e, e0)]
-        k = min(keep.size, n - filled)
-        out[filled:filled + k] = keep[:k]
-        filled += k
-    return out
+    """Allowed beta spectrum by inverse transform of its tabulated CDF."""
+    grid, cdf = _beta_cdf(e0)
+    e = np.interp(rng.uniform(0.0, 1.0, n), cdf, grid)
+    return np.clip(e, grid[1] * 1e-3, e0 * (1.0 - 1e-12))
 
 
 def sample_thermal_energy(rng: np.random.Generator, n: int, t_k: float) -> np.ndarray:
@@ -245,10 +250,13 @@ def isotropic_mu(rng: np.random.Generator, n: int) -> np.ndarray:
 
 def positions_by_density(rng: np.random.Generator, n: int, n_seg: np.ndarray,
                          length: float) -> np.ndarray:
-    """Birth positions with probability proportional to the gas density."""
+    """Birth positions with probability proportional to the gas density:
+    segment by inverse transform of the cumulative density, then uniform
+    within the segment."""
     nz = n_seg.shape[0]
-    p = n_seg / n_seg.sum()
-    seg = rng.choice(nz, size=n, p=p)
+    cdf = np.cumsum(n_seg, dtype=np.float64)
+    cdf /= cdf[-1]
+    seg = np.minimum(np.searchsorted(cdf, rng.uniform(0.0, 1.0, n), side="right"), nz - 1)
     dz = length / nz
     return np.minimum((seg + rng.uniform(0.0, 1.0, n)) * dz, length)
 

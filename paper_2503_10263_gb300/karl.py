@@ -355,7 +355,8 @@ class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
                 ("collected", C.c_int64), ("waiting", C.c_int64), ("collisions", C.c_int64),
                 ("kernel_launches", C.c_int64), ("arena_bytes_in_use", C.c_int64),
-                ("arena_bytes_peak", C.c_int64), ("lane_occupancy", C.c_double)]
+                ("arena_bytes_peak", C.c_int64), ("lane_occupancy", C.c_double),
+                ("kernel_ms", C.c_double)]
 
 
 _server_bound = False
