@@ -358,9 +358,11 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
       // largest k with G(k) <= target, in [j0, nz) going up, [0, j0] going down
       int lo = up ? j0 : 0, hi = up ? nz : j0 + 1;
       if (nrec == 0 && gasd > 0.0 && P.nq > 0) {
-        // bracket from the inverse gas-column table (exact with gas only)
-        const double q = target / gasd * P.nq_over_colmax;
-        if (q >= 0.0 && q < (double)P.nq) {
+        // bracket from the inverse gas-column table (exact with gas only).
+        // Only a hint: it is checked against the exact columns below, so it
+        // is computed in FP32 (a double divide costs the FP64 pipe ~10 ops).
+        const float q = (float)target * P.nq_over_colmax_f * __frcp_rn((float)gas);
+        if (q >= 0.0f && q < (float)P.nq) {
           const int qi = (int)q;
           const int a = max(lo, P.ginv[qi] - 1), bb = min(hi, P.ginv[qi + 1] + 1);
           if (a < bb && colsum(a) <= target && target < colsum(bb)) { lo = a; hi = bb; }

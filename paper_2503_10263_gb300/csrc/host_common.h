@@ -125,6 +125,7 @@ inline void fill_params(Params& P, const karl_geometry& g, const ModelInfo& m, i
   P.dz = g.length_m / g.n_zbins;
   P.nq = nq;
   P.nq_over_colmax = colmax > 0 ? (double)nq / colmax : 0.0;
+  P.nq_over_colmax_f = (float)P.nq_over_colmax;
   P.n_energy = m.n_energy;
   P.e_min = m.e_min;
   P.inv_e_min = 1.0 / m.e_min;

@@ -45,6 +45,7 @@ struct Params {
   const int* ginv;         // [nq+1] largest face k with colgas[k] <= q * colmax / nq
   int nq;
   double nq_over_colmax;   // nq / colgas[nz] (0 if the column is empty)
+  float nq_over_colmax_f;  // same in FP32 (search hints only)
   // recombination target fields of pass 2, per channel (NULL if unused)
   const double* frate[MAXCH];   // [nz] partner field per segment
   const double* fcol[MAXCH];    // [nz+1] its column to each face

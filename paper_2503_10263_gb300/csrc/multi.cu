@@ -167,7 +167,6 @@ __global__ void __launch_bounds__(256, 2) multi_kernel(SlotDesc* D, SlotCtl* C, 
   Control* ctl = &M->c;
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
-  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   WarpQueue& Q = wq[threadIdx.x >> 5];
   bool has = false;
   Lane L;
@@ -279,11 +278,18 @@ __global__ void __launch_bounds__(256, 2) multi_kernel(SlotDesc* D, SlotCtl* C, 
           t = ld_relaxed(&ctl->tail);
         }
         if (got == 0) {
-          // a request with unclaimed primaries, searched from a per-warp start
-          const int w0 = (gwarp + (int)(iter >> 6)) & (MAX_SLOTS / 32 - 1);
-          for (int i = 0; i < MAX_SLOTS / 32 && got == 0; ++i) {
-            const int wi = (w0 + i) & (MAX_SLOTS / 32 - 1);
+          // A request with unclaimed primaries.  The search starts at a slot
+          // chosen by the block, so the warps of a block keep to one request
+          // while it lasts and its parameters and column tables stay in L1.
+          const unsigned long long pub = ld_relaxed(&M->published);
+          const unsigned long long dn = ld_relaxed(&M->done_count);
+          const unsigned long long act = pub > dn ? pub - dn : 1ULL;
+          const int s0 = (int)((unsigned long long)blockIdx.x % (act < MAX_SLOTS ? act : MAX_SLOTS));
+          for (int i = 0; i <= MAX_SLOTS / 32 && got == 0; ++i) {
+            const int wi = ((s0 >> 5) + i) & (MAX_SLOTS / 32 - 1);
             unsigned bits = (unsigned)ld_relaxed_i((const int*)&M->bitmap[wi]);
+            if (i == 0) bits &= ~0u << (s0 & 31);                       // from s0 on
+            else if (i == MAX_SLOTS / 32) bits &= ~(~0u << (s0 & 31));  // wrapped: below s0
             while (bits && got == 0) {
               const int bit = __ffs(bits) - 1;
               bits &= bits - 1;

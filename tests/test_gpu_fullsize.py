@@ -1,0 +1,108 @@
+"""Parity at the full size of the two-pass plain method: 1e7 tritium decays
+(2e7 primaries) on the 10 m, 1000-segment parabolic column, FP64, in the
+launch configuration the benchmark times (default launch shape, host buffers
+through karl_run / karl_run_pass).
+
+The oracle cannot run 3e10 collisions in a test, so:
+  * pass 1 (gas only) histories are independent of one another: a sample of
+    primary-id ranges is re-run one by one through the oracle with the same
+    seed and ids, and the per-primary collision counts must coincide;
+  * every whole-run tally is checked through properties that hold at any
+    size: energy and particle ledger balance, spectrum counts equal exit
+    deaths, end-face crossings equal exit deaths, channel counts sum to the
+    collisions, recombination-partner deletions equal recombination deaths;
+  * integer tallies are bit-reproducible run to run (integer atomics commute).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2503_10263_gb300 import inputs
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+SEED = 1000
+RAW = ("spectrum", "time_fx", "cross_pos", "cross_neg", "recomb", "ledger", "chan_count",
+       "per_primary")
+
+
+@pytest.fixture(scope="module")
+def karl():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2503_10263_gb300 import karl as k
+    return k
+
+
+@pytest.fixture(scope="module")
+def full():
+    return inputs.config2()
+
+
+@pytest.fixture(scope="module")
+def pass1(karl, full):
+    prob, prims = full
+    ctx = karl.Context(prob)
+    a = ctx.run_pass(prims, SEED, 1, n_decays=prims.n_decays)
+    b = ctx.run_pass(prims, SEED, 1, n_decays=prims.n_decays)
+    return a, b
+
+
+def _deaths(L):
+    return np.asarray(L[15:39], np.int64).reshape(3, 8)
+
+
+def _check_properties(karl, t, nz, raw):
+    L = t["ledger"]
+    assert parity.ledger_balances(L)
+    d = _deaths(L)
+    spec = np.asarray(t["spectrum"], np.int64).reshape(2, 3, -1).sum(-1)
+    np.testing.assert_array_equal(spec[0], d[:, 0])      # exits at z = 0
+    np.testing.assert_array_equal(spec[1], d[:, 1])      # exits at z = L
+    assert int(np.sum(t["chan_count"])) == int(L[karl.N_COLLISIONS])
+    assert int(np.sum(t["recomb"])) == int(d[:, 5].sum())
+    if raw:
+        cp = np.asarray(t["cross_pos"], np.int64).reshape(3, nz + 1)
+        cn = np.asarray(t["cross_neg"], np.int64).reshape(3, nz + 1)
+        np.testing.assert_array_equal(cn[:, 0], d[:, 0])
+        np.testing.assert_array_equal(cp[:, nz], d[:, 1])
+        assert not cp[:, 0].any() and not cn[:, nz].any()
+
+
+def test_full_pass1_sampled_histories_match_oracle(karl, full, pass1):
+    prob, prims = full
+    g = pass1[0]
+    assert g["per_primary"].shape == (prims.n,)
+    rng = np.random.default_rng(20250313)
+    width, n_ranges = 256, 64
+    starts = np.sort(rng.choice(prims.n // width, n_ranges, replace=False)) * width
+    same = total = 0
+    for a in starts:
+        sub = prims.slice(int(a), width)
+        o = oracle.run_pass(prob, sub, SEED, 1, pid_offset=int(a), n_decays=prims.n_decays,
+                            n_threads=16)
+        same += int(np.sum(g["per_primary"][a:a + width] == o["per_primary"]))
+        total += width
+    assert same / total >= 0.99, same / total
+
+
+def test_full_pass1_properties_and_reproducibility(karl, full, pass1):
+    prob, prims = full
+    a, b = pass1
+    _check_properties(karl, a, prob.n_zbins, raw=True)
+    assert int(a["ledger"][karl.N_COLLISIONS]) > 10 * prims.n
+    for k in RAW:
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+
+
+def test_full_two_pass_run_properties(karl, full):
+    prob, prims = full
+    ctx = karl.Context(prob)
+    t = ctx.run(prims, seed=SEED)
+    _check_properties(karl, t, prob.n_zbins, raw=False)
+    assert int(t["ledger"][karl.BIRTHS + inputs.T3P]) > 0          # clustering ran
+    for k in ("density", "current", "field"):
+        assert np.all(np.isfinite(t[k])), k
+    assert np.all(t["field"] >= 0)
+    assert t["field"].any()
