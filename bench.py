@@ -414,7 +414,33 @@ def run_batch(args):
                 "d2h_bytes_per_step": d2h},
         "lane_occupancy": occ, "clocks": clocks,
     }
+    if args.compare_plain:
+        line["plain_one_at_a_time"] = plain_sequential(batch, prec, args.timeout)
     print(json.dumps(line), flush=True)
+
+
+def plain_sequential(batch, prec, timeout):
+    """The same requests through the plain single-request path (karl_run),
+    one after another: the comparison for the batched and served forms."""
+    import torch
+
+    from paper_2503_10263_gb300 import karl
+    coll = 0
+    kms = 0.0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for p, pr, s in batch:
+        ctx = karl.Context(p)
+        t = ctx.run(pr, seed=s, precision=prec, per_primary=False, timeout_s=timeout)
+        st = ctx.stats()
+        coll += int(t["ledger"][karl.N_COLLISIONS])
+        kms += float(st.kernel_ms[0]) + float(st.kernel_ms[1])
+        ctx.close()
+    wall = time.perf_counter() - t0
+    return {"value": coll / wall, "kernel_value": coll / (kms / 1000.0),
+            "unit": "collision events/s", "requests": len(batch),
+            "note": "karl_run per request, host buffers, two passes each; value = wall clock, "
+                    "kernel_value = transport kernel time only"}
 
 
 def run_serve(args):
@@ -466,7 +492,33 @@ def run_serve(args):
         "sustained_collisions_per_s": coll / wall, "kernel_launches": st.kernel_launches,
         "arena_bytes_peak": st.arena_bytes_peak, "clocks": clocks,
     }
+    if args.compare_plain:
+        line["plain_one_at_a_time"] = plain_serve(reqs, prec, args.timeout)
     print(json.dumps(line), flush=True)
+
+
+def plain_serve(reqs, prec, timeout):
+    """The same arrivals served first-come first-served by the plain path:
+    one karl_run at a time, each request waiting for the one before it."""
+    import torch
+
+    from paper_2503_10263_gb300 import karl
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat, coll = [], 0
+    for ta, p, pr, s in reqs:
+        now = time.perf_counter() - t0
+        if now < ta:
+            time.sleep(ta - now)
+        ctx = karl.Context(p)
+        t = ctx.run(pr, seed=s, precision=prec, per_primary=False, timeout_s=timeout)
+        ctx.close()
+        lat.append(time.perf_counter() - t0 - ta)
+        coll += int(t["ledger"][karl.N_COLLISIONS])
+    wall = time.perf_counter() - t0
+    return {"p50_latency_s": _percentile(lat, 50), "p99_latency_s": _percentile(lat, 99),
+            "sustained_collisions_per_s": coll / wall, "requests": len(reqs),
+            "note": "first-come first-served, one karl_run (two passes) per request"}
 
 
 def main():
@@ -487,6 +539,8 @@ def main():
     ap.add_argument("--budget-gb", type=int, default=48)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--rate", type=float, default=50.0)
+    ap.add_argument("--compare-plain", action="store_true",
+                    help="config4/config5: also run the requests one at a time through karl_run")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
