@@ -183,6 +183,48 @@ karl_status karl_run(karl_ctx* ctx, const karl_primaries* prim, const karl_run_o
 karl_status karl_run_pass(karl_ctx* ctx, const karl_primaries* prim, const karl_run_opts* opts,
                           int32_t pass, const uint64_t* field_time_in, karl_tallies* out);
 
+/* ---------------------------------------------------------------------------
+ * One pass that allocates nothing.  The paper has no counterpart: this is a
+ * deployment form of karl_run_pass, with the same kernel and results.
+ *
+ * Who needs it: callers that may not allocate device memory while they run --
+ * a host framework whose caching allocator or fixed budget has reserved the
+ * GPU's memory up front, or a request path that keeps cudaMalloc/cudaFree (and
+ * the device-wide synchronisation they can cause) out.  karl_run_pass grows
+ * work buffers on demand (tally staging, the particle ring, regrown on
+ * overflow); this call places all of its scratch in one static device array
+ * of KARL_STATIC_SCRATCH_BYTES per device that the library image carries, and
+ * reads and writes only caller-owned device memory.  It calls no allocating
+ * routine (no cudaMalloc, cudaFree, or library routine that allocates).
+ *
+ * Arguments as karl_run_pass, except:
+ *  - prim->on_device and out->on_device must be 1 (device pointers only), and
+ *    for pass 2 field_time_in is a DEVICE array [3][n_zbins+2][n_tebins];
+ *  - the pass's raw integer tallies OVERWRITE out's buffers (the call zeroes
+ *    them first) where karl_run_pass adds to them; per_primary may be NULL;
+ *    density, current and field are not touched.
+ * Scratch: control block, time and crossing difference arrays, pass-2 field
+ * tables, and a particle ring that gets the rest (a power of two, 2^16 to
+ * 2^22 particles).  The difference arrays, 2 * 3 * (n_zbins + 2) * n_tebins
+ * * 8 bytes plus the pass-2 tables, must fit beside the smallest ring (4 MiB):
+ * a geometry that does not fit is rejected with KARL_ECAPACITY before any
+ * launch, and so is a run whose particles overflow the ring, which cannot
+ * grow here.
+ * Set-up: the first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture on the device.
+ * Concurrency: one scratch array per device is shared by every context of the
+ * process.  Calls on the same device that overlap in time (two threads, or two
+ * streams without an order between them) race on it and corrupt each other's
+ * results: serialise them.
+ * Blocks until the pass is done.  Errors: those of karl_run_pass, plus
+ * KARL_EINVAL for host buffers and KARL_ECAPACITY as above; karl_cancel
+ * applies.  On error the tallies are unspecified. */
+#define KARL_STATIC_SCRATCH_BYTES (64u << 20)
+karl_status karl_run_pass_static(karl_ctx* ctx, const karl_primaries* prim,
+                                 const karl_run_opts* opts, int32_t pass,
+                                 const uint64_t* field_time_in, karl_tallies* out);
+
 /* Request that a running karl_run on this context stop (thread-safe).  The
  * kernel polls the flag; the run returns KARL_ECANCELLED. */
 void karl_cancel(karl_ctx* ctx);

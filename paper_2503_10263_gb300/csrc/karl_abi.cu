@@ -12,6 +12,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -791,3 +792,253 @@ void karl_destroy(karl_ctx* ctx) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// One pass with no allocation: all scratch in one static device array.
+//
+// For callers that must not allocate device memory while they run (a caching
+// allocator or a fixed memory budget that reserves the GPU up front, or a
+// request path that keeps allocation out).  The transport kernel is the same
+// as karl_run_pass's; only where its scratch lives differs.  The array is
+// carried by the library image: the CUDA runtime maps it when the module is
+// loaded on a device, before any call, and this code only looks up its
+// address.
+
+// KARL_STATIC_SCRATCH_BYTES of scratch per device, 256-byte aligned so every
+// region carved from it keeps the alignment of its element type.
+static __device__ __align__(256) unsigned char karl_static_scratch[KARL_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int SCRATCH_MAX_DEVICES = 64;
+constexpr unsigned long long SCRATCH_RING_MIN = 1ULL << 16;   // particles
+constexpr unsigned long long SCRATCH_RING_MAX = 1ULL << 22;
+
+std::mutex g_scratch_mu;
+unsigned char* g_scratch_addr[SCRATCH_MAX_DEVICES];           // zero-initialised
+bool g_scratch_ready[SCRATCH_MAX_DEVICES];
+
+// Device address of the static scratch on ctx->device, looked up the first
+// time with that device current.  Later calls reuse it.
+karl_status static_scratch(karl_ctx* ctx, unsigned char** out) {
+  if (ctx->device < 0 || ctx->device >= SCRATCH_MAX_DEVICES)
+    return fail(ctx, KARL_EINVAL, "device %d beyond the static scratch table", ctx->device);
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_ready[ctx->device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, karl_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGetSymbolAddress(karl_static_scratch)");
+    if (!p) return fail(ctx, KARL_ECUDA, "static scratch has no device address");
+    g_scratch_addr[ctx->device] = (unsigned char*)p;
+    g_scratch_ready[ctx->device] = true;
+  }
+  *out = g_scratch_addr[ctx->device];
+  return KARL_OK;
+}
+
+// Bump allocator over the static array (256-byte regions, no device call).
+struct Carve {
+  unsigned char* base;
+  size_t used = 0;
+  template <class T>
+  T* take(size_t count) {
+    T* p = (T*)(base + used);
+    used += (count * sizeof(T) + 255) & ~(size_t)255;
+    return p;
+  }
+};
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// z eq mu node tal pid seq (8 bytes each), ev sj (4 bytes each) per ring cell
+size_t ring_bytes(unsigned long long cap) {
+  return 7 * round256((size_t)cap * 8) + 2 * round256((size_t)cap * 4);
+}
+
+}  // namespace
+
+extern "C" karl_status karl_run_pass_static(karl_ctx* ctx, const karl_primaries* pr,
+                                            const karl_run_opts* o, int32_t pass,
+                                            const uint64_t* field_time_in, karl_tallies* out) {
+  if (!ctx) return KARL_EINVAL;
+  ctx->err.clear();
+  if (!pr || !out || pr->n < 0) return fail(ctx, KARL_EINVAL, "NULL argument or n < 0");
+  karl_status s = check_opts(ctx, o);
+  if (s) return s;
+  if (pass != 1 && pass != 2) return fail(ctx, KARL_EINVAL, "pass must be 1 or 2");
+  if (pass == 2 && !field_time_in) return fail(ctx, KARL_EINVAL, "pass 2 needs field_time_in");
+  if (pass == 2 && !(pr->n_decays > 0)) return fail(ctx, KARL_EINVAL, "n_decays must be > 0");
+  if (!pr->on_device || !out->on_device)
+    return fail(ctx, KARL_EINVAL, "karl_run_pass_static takes device primaries and tallies only");
+  if (pr->n > 0 && (!pr->z_m || !pr->e_ev || !pr->mu || !pr->species))
+    return fail(ctx, KARL_EINVAL, "primaries: NULL array");
+  if (!out->spectrum || !out->time_fx || !out->cross_pos || !out->cross_neg || !out->recomb ||
+      !out->ledger || (ctx->nch > 0 && !out->chan_count))
+    return fail(ctx, KARL_EINVAL, "tally buffer is NULL");
+
+  // the scratch plan, checked before any device call
+  const size_t nt = n_time(ctx), nx = n_cross_rg(ctx);
+  const size_t nk = (size_t)std::max(ctx->nch, 1);
+  size_t fixed = round256(sizeof(Control)) + round256(sizeof(int)) + 2 * round256(nt * 8) +
+                 2 * round256(nx * 8);
+  if (pass == 2) fixed += round256(nk * ctx->nz * 8) + round256(nk * (ctx->nz + 1) * 8);
+  const size_t total = KARL_STATIC_SCRATCH_BYTES;
+  if (fixed + ring_bytes(SCRATCH_RING_MIN) > total)
+    return fail(ctx, KARL_ECAPACITY,
+                "problem needs %zu bytes of scratch (tallies %zu + particle ring %zu); the "
+                "static scratch holds %zu",
+                fixed + ring_bytes(SCRATCH_RING_MIN), fixed, ring_bytes(SCRATCH_RING_MIN), total);
+  unsigned long long cap = SCRATCH_RING_MIN;
+  while (cap < SCRATCH_RING_MAX && fixed + ring_bytes(cap * 2) <= total) cap *= 2;
+
+  int prev_dev = -1;
+  if (cudaGetDevice(&prev_dev) != cudaSuccess) return fail(ctx, KARL_ECUDA, "cudaGetDevice failed");
+  if (prev_dev != ctx->device) CK(cudaSetDevice(ctx->device));
+  struct Restore {
+    int d, want;
+    ~Restore() { if (d >= 0 && d != want) cudaSetDevice(d); }
+  } restore{prev_dev, ctx->device};
+
+  unsigned char* base = nullptr;
+  s = static_scratch(ctx, &base);
+  if (s) return s;
+  Carve cv{base};
+  Control* ctl = cv.take<Control>(1);
+  int* bad = cv.take<int>(1);
+  unsigned long long* tpt = cv.take<unsigned long long>(nt);
+  unsigned long long* trg = cv.take<unsigned long long>(nt);
+  unsigned long long* xpos = cv.take<unsigned long long>(nx);
+  unsigned long long* xneg = cv.take<unsigned long long>(nx);
+  double* frate = pass == 2 ? cv.take<double>(nk * ctx->nz) : nullptr;
+  double* fcol = pass == 2 ? cv.take<double>(nk * (ctx->nz + 1)) : nullptr;
+  Ring R;
+  R.z = cv.take<double>(cap); R.eq = cv.take<long long>(cap); R.mu = cv.take<double>(cap);
+  R.node = cv.take<unsigned long long>(cap); R.tal = cv.take<double>(cap);
+  R.pid = cv.take<unsigned long long>(cap); R.seq = cv.take<unsigned long long>(cap);
+  R.ev = cv.take<unsigned>(cap); R.sj = cv.take<unsigned>(cap);
+  R.cap = cap; R.mask = cap - 1;
+  if (cv.used > total) return fail(ctx, KARL_ECAPACITY, "static scratch plan overran");
+
+  cudaStream_t st = o->stream ? (cudaStream_t)o->stream : ctx->own_stream;
+  ctx->stats.kernel_launches = 0;
+  const size_t n = (size_t)pr->n;
+
+  // what must start at zero: the control block, the primary check counter,
+  // the difference arrays, and every caller tally the kernel adds into
+  CK(cudaMemsetAsync(ctl, 0, sizeof(Control), st));
+  CK(cudaMemsetAsync(bad, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(tpt, 0, nt * 8, st));
+  CK(cudaMemsetAsync(trg, 0, nt * 8, st));
+  CK(cudaMemsetAsync(xpos, 0, nx * 8, st));
+  CK(cudaMemsetAsync(xneg, 0, nx * 8, st));
+  CK(cudaMemsetAsync(out->spectrum, 0, n_spec(ctx) * 8, st));
+  CK(cudaMemsetAsync(out->recomb, 0, n_recomb(ctx) * 8, st));
+  CK(cudaMemsetAsync(out->ledger, 0, LEDGER * 8, st));
+  if (ctx->nch > 0) CK(cudaMemsetAsync(out->chan_count, 0, (size_t)ctx->nch * 8, st));
+  const bool pp = out->per_primary != nullptr && n > 0;
+  if (pp) CK(cudaMemsetAsync(out->per_primary, 0, n * 8, st));
+  k_ring_init<<<grid_for((size_t)cap, 256), 256, 0, st>>>(R.seq, cap);
+  CK(cudaGetLastError());
+  ctx->stats.kernel_launches += 1;
+
+  if (n > 0) {
+    k_check_primaries<<<grid_for(n, 256), 256, 0, st>>>(pr->z_m, pr->e_ev, pr->mu, pr->species,
+                                                        (long long)n, ctx->L, bad);
+    CK(cudaGetLastError());
+    ctx->stats.kernel_launches += 1;
+    int hbad = 0;
+    CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (hbad) return fail(ctx, KARL_EINVAL, "%d primaries out of range", hbad);
+  }
+
+  Params P;
+  base_params(ctx, P, o, pass);
+  if (pass == 2) {
+    FieldArgs A;
+    std::memset(&A, 0, sizeof A);
+    A.nz = ctx->nz; A.ntb = ctx->ntb; A.n_energy = ctx->n_energy; A.nch = ctx->nch;
+    A.tsim = (double)pr->n_decays / ctx->activity;
+    A.vol = ctx->dz * ctx->area;
+    A.dz = ctx->dz; A.e_min = ctx->e_min; A.e_max = ctx->e_max; A.me = ctx->mass[SP_E];
+    for (int k = 0; k < ctx->nch; ++k) {
+      A.kind[k] = ctx->kind[k]; A.sin[k] = ctx->sin[k];
+      A.sout[k] = ctx->sout[k]; A.loss[k] = ctx->loss[k];
+    }
+    CK(cudaMemsetAsync(frate, 0, nk * ctx->nz * 8, st));
+    k_build_fields<<<grid_for((size_t)ctx->nch * ctx->nz, 256), 256, 0, st>>>(
+        A, (const unsigned long long*)field_time_in, ctx->d_sig.p, frate, fcol);
+    k_field_columns<<<1, 32, 0, st>>>(frate, fcol, ctx->nch, ctx->nz, ctx->dz);
+    CK(cudaGetLastError());
+    ctx->stats.kernel_launches += 2;
+    for (int k = 0; k < ctx->nch; ++k) {
+      if (ctx->kind[k] != RECOMBINATION) continue;
+      P.frate[k] = frate + (size_t)k * ctx->nz;
+      P.fcol[k] = fcol + (size_t)k * (ctx->nz + 1);
+    }
+  }
+  P.pid_offset = pr->pid_offset;
+  P.n_prim = pr->n;
+  P.pz = pr->z_m; P.pe = pr->e_ev; P.pmu = pr->mu; P.psp = pr->species;
+  P.spectrum = (unsigned long long*)out->spectrum;
+  P.time_pt = tpt;
+  P.time_rg = trg;
+  P.xpos_rg = xpos;
+  P.xneg_rg = xneg;
+  P.recomb = (unsigned long long*)out->recomb;
+  P.ledger = (unsigned long long*)out->ledger;
+  P.chan_count = (unsigned long long*)out->chan_count;
+  P.per_primary = pp ? (unsigned long long*)out->per_primary : nullptr;
+
+  const bool f32 = o->precision == KARL_FP32;
+  const int block = o->block_size > 0 ? o->block_size : 256;
+  int bps = 0;
+  CK(transport_occupancy(f32, P, block, &bps));
+  if (o->blocks_per_sm > 0) bps = std::min(bps, (int)o->blocks_per_sm);
+  if (bps < 1) bps = 1;
+  const int grid = ctx->num_sms * bps;
+  const double timeout = o->timeout_s > 0 ? o->timeout_s : 600.0;
+
+  CK(cudaMemsetAsync(ctx->d_cancel, 0, sizeof(int), st));
+  CK(cudaEventRecord(ctx->ev0, st));
+  CK(launch_transport(f32, P, R, ctl, ctx->d_cancel, (unsigned long long)(timeout * 1e9), grid,
+                      block, st));
+  CK(cudaEventRecord(ctx->ev1, st));
+  ctx->stats.kernel_launches += 1;
+  k_finalize_time<<<grid_for((size_t)NSP * ctx->ntb, 64), 64, 0, st>>>(
+      tpt, trg, (unsigned long long*)out->time_fx, ctx->nz, ctx->ntb);
+  k_finalize_cross<<<1, 32, 0, st>>>(xpos, (unsigned long long*)out->cross_pos, ctx->nz);
+  k_finalize_cross<<<1, 32, 0, st>>>(xneg, (unsigned long long*)out->cross_neg, ctx->nz);
+  CK(cudaGetLastError());
+  ctx->stats.kernel_launches += 3;
+  Control hc;
+  CK(cudaMemcpyAsync(&hc, ctl, sizeof hc, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+
+  float ms = 0;
+  cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+  const int pi = pass - 1;
+  ctx->stats.kernel_ms[pi] = ms;
+  ctx->stats.particles[pi] = (int64_t)hc.particles;
+  ctx->stats.lane_occupancy[pi] =
+      hc.busy_iters + hc.idle_iters
+          ? (double)hc.busy_lane_iters / (32.0 * (double)(hc.busy_iters + hc.idle_iters))
+          : 0.0;
+  ctx->stats.grid_blocks = grid;
+  ctx->stats.block_size = block;
+  ctx->stats.queue_capacity = (int32_t)cap;
+  if (hc.error == ERR_CAPACITY)
+    return fail(ctx, KARL_ECAPACITY,
+                "particle ring overflow at its static capacity %llu (the ring cannot grow; use "
+                "karl_run_pass, or fewer primaries per call)",
+                (unsigned long long)cap);
+  if (hc.error == ERR_TIMEOUT) return fail(ctx, KARL_ETIMEOUT, "transport kernel timed out");
+  if (hc.error == ERR_CANCELLED) return fail(ctx, KARL_ECANCELLED, "run cancelled");
+  if (hc.error != 0) return fail(ctx, KARL_ECUDA, "transport kernel error %d", hc.error);
+  long long led[LEDGER];
+  CK(cudaMemcpyAsync(led, out->ledger, sizeof led, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  ctx->stats.collisions[pi] = led[L_N_COLL];
+  ctx->stats.flights[pi] = led[L_N_FLIGHT];
+  return KARL_OK;
+}

@@ -26,6 +26,7 @@ N_SPECIES = 3
 N_REASONS = 8
 LEDGER_LEN = 64
 MAX_CHANNELS = 16
+STATIC_SCRATCH_BYTES = 64 << 20     # KARL_STATIC_SCRATCH_BYTES of karl_run_pass_static
 FP64, FP32 = 0, 1
 
 # status codes
@@ -111,6 +112,8 @@ def load() -> C.CDLL:
     lib.karl_run.argtypes = [C.c_void_p, P(Primaries), P(RunOpts), P(Tallies)]
     lib.karl_run_pass.argtypes = [C.c_void_p, P(Primaries), P(RunOpts), C.c_int32,
                                   C.c_void_p, P(Tallies)]
+    lib.karl_run_pass_static.argtypes = [C.c_void_p, P(Primaries), P(RunOpts), C.c_int32,
+                                         C.c_void_p, P(Tallies)]
     lib.karl_destroy.argtypes = [C.c_void_p]
     lib.karl_destroy.restype = None
     lib.karl_cancel.argtypes = [C.c_void_p]
@@ -121,7 +124,8 @@ def load() -> C.CDLL:
     lib.karl_last_error.restype = C.c_char_p
     lib.karl_tally_layout.argtypes = [C.c_void_p, P(Layout)]
     lib.karl_last_stats.argtypes = [C.c_void_p, P(RunStats)]
-    for f in ("karl_create", "karl_run", "karl_run_pass", "karl_tally_layout", "karl_last_stats"):
+    for f in ("karl_create", "karl_run", "karl_run_pass", "karl_run_pass_static",
+              "karl_tally_layout", "karl_last_stats"):
         getattr(lib, f).restype = C.c_int
     _lib = lib
     return lib
@@ -149,6 +153,14 @@ def karl_run_pass(ctx, prim: Primaries, opts: RunOpts, pass_index: int, field_ti
                   tallies: Tallies) -> int:
     return load().karl_run_pass(ctx, C.byref(prim), C.byref(opts), pass_index, field_time_in,
                                 C.byref(tallies))
+
+
+def karl_run_pass_static(ctx, prim: Primaries, opts: RunOpts, pass_index: int, field_time_in,
+                         tallies: Tallies) -> int:
+    """karl_run_pass with scratch in the library's static device array: device
+    buffers only, tallies overwritten, nothing allocated by the call."""
+    return load().karl_run_pass_static(ctx, C.byref(prim), C.byref(opts), pass_index,
+                                       field_time_in, C.byref(tallies))
 
 
 def karl_destroy(ctx) -> None:
@@ -335,6 +347,23 @@ class Context:
         ts.on_device = 1
         o = self.opts(seed, n_passes, precision, stream=stream, **kw)
         self._check(karl_run(self.ctx, ps, o, ts))
+
+    def run_pass_static_device(self, prim_ptrs: Dict[str, int], n: int, n_decays: int,
+                               out_ptrs: Dict[str, int], seed: int, pass_index: int,
+                               field_time_in: Optional[int] = None, pid_offset: int = 0,
+                               precision: int = FP64, stream: Optional[int] = None,
+                               **kw) -> None:
+        """karl_run_pass_static: device pointers in and out, raw tallies of
+        one pass written over out_ptrs, no allocation inside the call."""
+        ps = Primaries(n, prim_ptrs["z_m"], prim_ptrs["e_ev"], prim_ptrs["mu"],
+                       prim_ptrs["species"], n_decays, pid_offset, 1)
+        ts = Tallies()
+        for k in ("spectrum", "time_fx", "cross_pos", "cross_neg", "recomb", "ledger",
+                  "chan_count", "per_primary"):
+            setattr(ts, k, out_ptrs.get(k))
+        ts.on_device = 1
+        o = self.opts(seed, pass_index, precision, stream=stream, **kw)
+        self._check(karl_run_pass_static(self.ctx, ps, o, pass_index, field_time_in, ts))
 
     def stats(self) -> RunStats:
         return karl_last_stats(self.ctx)
