@@ -34,13 +34,19 @@ import numpy as np  # noqa: E402
 BYTES_PER_EVENT_FP64 = 104     # event-based state model: 52 B read + 52 B written per event
 BYTES_PER_EVENT_FP32 = 80
 # The transport kernel keeps particle state in registers and is bound by the
-# FP64 pipe (GB300 runs FP64 at 1/64 of FP32).  Per collision it occupies the
-# FP64 pipe of one SM for this many cycles (ncu sm__pipe_fp64_cycles_active x
-# elapsed cycles x SMs / collisions, transport kernel, 2e5-decay case of this
-# workload); None: not measured for this form of the kernel.
-FP64_PIPE_CYCLES_PER_COLLISION = {"fp64": 193.0, "fp32": 84.0}
-# DRAM bytes per collision of the same captures (read + write)
-DRAM_BYTES_PER_COLLISION = {"fp64": 22.31e6 / 331927149, "fp32": 25.82e6 / 331928948}
+# FP64 pipe (GB300 runs FP64 at 1/64 of FP32: 2 FP64 thread-instructions per
+# SM per cycle).  Work per collision, from one ncu capture of the transport
+# kernel on the 2e5-decay case of this workload (pass 1):
+#   FP64_OPS: FP64 add, multiply and fma thread-instructions executed with the
+#     predicate on (smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on);
+#   FP64_PIPE_CYCLES: SM-cycles the FP64 pipe was busy (sm__pipe_fp64_cycles_active),
+#     which also counts the lanes a divergent warp leaves idle;
+#   DRAM_BYTES: dram__bytes_read.sum + dram__bytes_write.sum.
+# None: not measured for the kernel as it stands.
+FP64_OPS_PER_COLLISION = {"fp64": 192.8, "fp32": 29.8}
+FP64_PIPE_CYCLES_PER_COLLISION = {"fp64": 179.9, "fp32": 76.5}
+DRAM_BYTES_PER_COLLISION = {"fp64": 38.73e6 / 333.3e6, "fp32": 60.25e6 / 333.3e6}
+FP64_OPS_PER_SM_CYCLE = 2
 WORKLOAD = ("config2: 1e7 decays (1e7 beta e- + 1e7 thermal T2+), parabolic profile with "
             "5e21 m^-2 column, L = 10 m, 1000 z segments, 7 e- channels + T2+ clustering + "
             "e-/ion recombination, two passes")
@@ -211,6 +217,8 @@ def run_ours(args):
     ev1 = torch.cuda.Event(enable_timing=True)
     coll = flights = parts = launches = 0
     kms = []
+    occ = []
+    per_pass = []
     ev0.record(stream)
     for i in range(args.steps):
         st = step(args.warmup + i)
@@ -219,6 +227,8 @@ def run_ours(args):
         parts += st.particles[0] + st.particles[1]
         launches += st.kernel_launches
         kms += [st.kernel_ms[0], st.kernel_ms[1]]
+        occ += [st.lane_occupancy[0], st.lane_occupancy[1]]
+        per_pass += [int(st.collisions[0]), int(st.collisions[1])]
     ev1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -292,14 +302,17 @@ def run_ours(args):
     hbm_achieved = bpe * launch_rate / 1e9
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     clk_ghz = (clocks["sm_mhz"] if clocks else 2070.0) / 1000.0
+    ops = FP64_OPS_PER_COLLISION[args.precision]
     cyc = FP64_PIPE_CYCLES_PER_COLLISION[args.precision]
     dram = DRAM_BYTES_PER_COLLISION[args.precision]
     traffic = dram * per_launch_events if dram else None
-    if cyc:
-        roofline = {"bound": "alu", "achieved": cyc * launch_rate / 1e9, "peak": n_sm * clk_ghz,
-                    "unit": "G FP64-pipe cycles/s", "frac": cyc * launch_rate / 1e9 / (n_sm * clk_ghz),
+    if ops:
+        peak = FP64_OPS_PER_SM_CYCLE * n_sm * clk_ghz
+        roofline = {"bound": "alu", "achieved": ops * launch_rate / 1e9, "peak": peak,
+                    "unit": "G FP64 thread-ops/s", "frac": ops * launch_rate / 1e9 / peak,
                     "traffic": traffic,
-                    "model": f"{cyc:.0f} FP64-pipe SM-cycles per collision (ncu), peak = {n_sm} SMs x "
+                    "model": f"{ops:.0f} FP64 add/mul/fma thread-instructions per collision (ncu); "
+                             f"peak = {FP64_OPS_PER_SM_CYCLE} per SM per cycle x {n_sm} SMs x "
                              f"median SM clock under load",
                     "kernel": "karl::transport_kernel"}
     else:
@@ -307,6 +320,13 @@ def run_ours(args):
                     "frac": hbm_achieved / hbm, "traffic": traffic,
                     "model": f"{bpe} B per collision event (state read+write), {peak_kind} peak",
                     "kernel": "karl::transport_kernel"}
+    fp64_pipe = None
+    if cyc:
+        fp64_pipe = {"busy_frac": cyc * launch_rate / 1e9 / (n_sm * clk_ghz),
+                     "cycles_per_collision": cyc,
+                     "note": "FP64 pipe busy cycles over SM cycles; the gap to roofline.frac is "
+                             "FP64 issue slots spent on idle or divergent lanes and on FP64 "
+                             "instructions other than add/mul/fma (compares, conversions)"}
     hbm_model = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm, "unit": "GB/s",
                  "frac": hbm_achieved / hbm,
                  "model": f"{bpe} B per collision event (event-based state read+write), "
@@ -322,9 +342,12 @@ def run_ours(args):
         "primaries_per_s": decays_all / tm, "flights_per_s": flights_all / tm,
         "collisions_per_step": coll / args.steps,
         "transport_kernel_ms": kms,
+        "collisions_per_launch": per_pass,
+        "lane_occupancy": [round(x, 4) for x in occ],
         "ledger_balanced": ok_balance,
         "gpu_launches": launches,
         "roofline": roofline,
+        "fp64_pipe": fp64_pipe,
         "hbm_model": hbm_model,
         "e2e": e2e,
         "clocks": clocks,

@@ -169,6 +169,7 @@ static __device__ bool ring_get(const Ring& R, Control* ctl, unsigned long long 
 
 struct EventOut {
   bool alive;
+  bool parked;                            // handed to the warp's batch of rare collisions
   int chan;                               // channel of this event's collision, -1 if none
   unsigned long long flights, colls;      // per-lane counters, flushed at the end
   unsigned long long recoil, excit;       // per-lane energy sums (2^-24 eV)
@@ -186,11 +187,29 @@ struct WarpQueue {
   int top;
 };
 
+// Collisions in the rare channels (ionization with its products, clustering)
+// cost as much FP64 work as a whole ordinary event, and a warp pays that cost
+// in full for a single lane.  A lane that selects one parks its particle here
+// (state after the flight, channel chosen) and takes other work; when enough
+// have gathered the whole warp performs them together.  The kinematics draw
+// from the same counter-based stream either way, so results do not change.
+// The same slots also hold, from the top down, the particles busy lanes hand
+// back to make room for a batch; free lanes resume those before other work.
+constexpr int RB = 32;                    // parked collisions per warp
+constexpr int RB_TRIGGER = 24;            // batch size that starts a batch
+struct RareBuf {
+  Lane s[RB];
+  int8_t ch[RB];
+  int n;                                  // parked: slots [0, n)
+  int r;                                  // handed back: slots [RB - r, RB)
+};
+
 struct RingPort {
   const Ring* R;
   Control* ctl;
   unsigned long long deadline;
   WarpQueue* q;
+  RareBuf* rare;           // NULL: perform rare collisions in line
   bool local;              // primaries remain: keep products in the warp queue
   unsigned long long spilled;
   // multi-request kernel: every existing particle counts in its slot's live
@@ -233,12 +252,117 @@ __device__ __forceinline__ void thermal(const Params& P, const unsigned long lon
   mu = 2.0 * u01d(w[3]) - 1.0;
 }
 
+// Terminator of Sec. 3.2 after a collision.
+template <bool F32>
+__device__ __forceinline__ void terminate(const Params& P, unsigned long long* led, Lane& L,
+                                          EventOut& o) {
+  if (L.sp == SP_E && L.eq < P.ecut_q) {
+    die<F32>(P, led, L, R_CUTOFF, L_E_CUTOFF);
+    o.alive = false;
+  } else if (L.ev >= P.max_coll) {
+    die<F32>(P, led, L, R_CAP_COLL, L_E_CAP);
+    o.alive = false;
+  } else if (P.track_time && L.tal >= P.max_life) {
+    die<F32>(P, led, L, R_CAP_TIME, L_E_CAP);
+    o.alive = false;
+  }
+}
+
+// Kinematics of an ionization (Sec. 3.3 Ionization: energy sharing, binary-
+// encounter angles, the slow electron and the ion as products) or a clustering
+// (Sec. 3.3 Clustering: the impactor becomes the product ion with a thermal
+// target's motion) of the particle L, whose flight and channel choice are done
+// (L.ev already counts this collision; w is the event's random block).
+template <bool F32>
+__device__ __forceinline__ void rare_kinematics(const Params& P, unsigned long long* led, Lane& L,
+                                                EventOut& o, RingPort& port, int k,
+                                                const unsigned long long w[4]) {
+  using T = RT<F32>;
+  using R = typename T::R;
+  const ChanDev ch = P.ch[k];
+  const R e = T::energy(L.eq);
+  if (ch.kind == IONIZATION) {
+    const long long avail = L.eq - ch.loss_q;
+    const R eps = (R)P.eps_ion;
+    const R wmax = (e - (R)ch.loss_ev) * (R)0.5;
+    const R wsec = eps * T::tn(T::u(w[2]) * T::atn(wmax * (R)P.inv_eps_ion));
+    long long wq = quant_e((double)wsec);
+    if (wq > avail / 2) wq = avail / 2;
+    if (wq < 0) wq = 0;
+    const long long eq1 = avail - wq;
+    sadd(led + (L_LOSS_IONIZ), ch.loss_q);
+    // binary encounter: cos^2 of the polar angles are the energy fractions
+    const double inv_avail = avail > 0 ? 1.0 / (double)avail : 0.0;
+    const R c2p = avail > 0 ? (R)((double)eq1 * inv_avail) : (R)1;
+    const R c2s = (R)((double)wq * inv_avail);
+    const R cp = T::sq(c2p), sp = T::sq(c2s);
+    const R cphi = T::cpi((R)2 * T::u(w[3]));
+    const R mu = (R)L.mu;
+    const R smu = T::sq(fmax((R)0, (R)1 - mu * mu));
+    const R mu_p = fmin((R)1, fmax((R)-1, mu * cp + smu * sp * cphi));
+    const R mu_s = fmin((R)1, fmax((R)-1, mu * sp - smu * cp * cphi));
+    const unsigned evc = L.ev - 1;
+    // slow electron (azimuth opposite to the fast one)
+    sadd(led + (L_BIRTHS + SP_E), 1);
+    sadd(led + (L_N_SPAWN_E), 1);
+    Lane c;
+    c.z = L.z; c.eq = wq; c.mu = (double)mu_s; c.node = child_node(L.node, evc, 0);
+    c.tal = 0.0; c.pid = L.pid; c.ev = 0; c.sp = SP_E; c.j = L.j; c.slot = L.slot;
+    if (wq < P.ecut_q) die<F32>(P, led, c, R_CUTOFF, L_E_CUTOFF);
+    else emit(port, c);
+    // ion with a thermal target's velocity (no recoil)
+    if (ch.sout >= 0) {
+      Lane ion;
+      ion.z = L.z; ion.node = child_node(L.node, evc, 1); ion.tal = 0.0; ion.pid = L.pid;
+      ion.ev = 0; ion.sp = ch.sout; ion.j = L.j; ion.slot = L.slot;
+      unsigned long long wi[4];
+      philox4x64_10(0ULL, ion.node, ((unsigned long long)P.pass << 8) | DOM_ION_BIRTH, 0ULL,
+                    P.seed, L.pid, wi);
+      thermal<F32>(P, wi, ion.eq, ion.mu);
+      sadd(led + (L_E_IN_THERMAL), ion.eq);
+      sadd(led + (L_BIRTHS + ch.sout), 1);
+      sadd(led + (L_N_SPAWN_ION), 1);
+      emit(port, ion);
+    }
+    L.eq = eq1;
+    L.mu = (double)mu_p;
+  } else {  // CLUSTERING
+    die<F32>(P, led, L, R_CLUSTER, L_E_CLUSTER);
+    unsigned long long wc[4];
+    const unsigned evc = L.ev - 1;
+    philox4x64_10((unsigned long long)evc, L.node,
+                  ((unsigned long long)P.pass << 8) | DOM_CLUSTER, 0ULL, P.seed, L.pid, wc);
+    long long eqc;
+    double muc;
+    thermal<F32>(P, wc, eqc, muc);
+    L.node = child_node(L.node, evc, 2);
+    L.eq = eqc;
+    L.mu = muc;
+    L.tal = 0.0;
+    L.ev = 0;
+    L.sp = ch.sout;
+    sadd(led + (L_E_IN_THERMAL), eqc);
+    sadd(led + (L_BIRTHS + ch.sout), 1);
+    return;
+  }
+  if (ch.kind == IONIZATION) terminate<F32>(P, led, L, o);
+}
+
+// The random block of the collision a parked particle chose (the event index
+// before this collision was counted).
+__device__ __forceinline__ void parked_block(const Params& P, const Lane& L,
+                                             unsigned long long w[4]) {
+  philox4x64_10((unsigned long long)(L.ev - 1), L.node,
+                ((unsigned long long)P.pass << 8) | DOM_EVENT, 0ULL, P.seed, L.pid, w);
+}
+
 template <bool F32>
 __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOut& o,
                       RingPort& port) {
   using T = RT<F32>;
   using R = typename T::R;
   o.alive = true;
+  o.parked = false;
   o.chan = -1;
   if (L.eq <= 0) {                 // no kinetic energy: the particle never moves
     die<F32>(P, led, L, R_STALLED, L_E_STALLED);
@@ -467,68 +591,19 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
   } else if (ch.kind == EXCITATION) {
     L.eq -= ch.loss_q;
     o.excit += (unsigned long long)ch.loss_q;
-  } else if (ch.kind == IONIZATION) {
-    const long long avail = L.eq - ch.loss_q;
-    const R eps = (R)P.eps_ion;
-    const R wmax = (e - (R)ch.loss_ev) * (R)0.5;
-    const R wsec = eps * T::tn(T::u(w[2]) * T::atn(wmax * (R)P.inv_eps_ion));
-    long long wq = quant_e((double)wsec);
-    if (wq > avail / 2) wq = avail / 2;
-    if (wq < 0) wq = 0;
-    const long long eq1 = avail - wq;
-    sadd(led + (L_LOSS_IONIZ), ch.loss_q);
-    // binary encounter: cos^2 of the polar angles are the energy fractions
-    const double inv_avail = avail > 0 ? 1.0 / (double)avail : 0.0;
-    const R c2p = avail > 0 ? (R)((double)eq1 * inv_avail) : (R)1;
-    const R c2s = (R)((double)wq * inv_avail);
-    const R cp = T::sq(c2p), sp = T::sq(c2s);
-    const R cphi = T::cpi((R)2 * T::u(w[3]));
-    const R mu = (R)L.mu;
-    const R smu = T::sq(fmax((R)0, (R)1 - mu * mu));
-    const R mu_p = fmin((R)1, fmax((R)-1, mu * cp + smu * sp * cphi));
-    const R mu_s = fmin((R)1, fmax((R)-1, mu * sp - smu * cp * cphi));
-    const unsigned evc = L.ev - 1;
-    // slow electron (azimuth opposite to the fast one)
-    sadd(led + (L_BIRTHS + SP_E), 1);
-    sadd(led + (L_N_SPAWN_E), 1);
-    Lane c;
-    c.z = L.z; c.eq = wq; c.mu = (double)mu_s; c.node = child_node(L.node, evc, 0);
-    c.tal = 0.0; c.pid = L.pid; c.ev = 0; c.sp = SP_E; c.j = L.j; c.slot = L.slot;
-    if (wq < P.ecut_q) die<F32>(P, led, c, R_CUTOFF, L_E_CUTOFF);
-    else emit(port, c);
-    // ion with a thermal target's velocity (no recoil)
-    if (ch.sout >= 0) {
-      Lane ion;
-      ion.z = L.z; ion.node = child_node(L.node, evc, 1); ion.tal = 0.0; ion.pid = L.pid;
-      ion.ev = 0; ion.sp = ch.sout; ion.j = L.j; ion.slot = L.slot;
-      unsigned long long wi[4];
-      philox4x64_10(0ULL, ion.node, ((unsigned long long)P.pass << 8) | DOM_ION_BIRTH, 0ULL,
-                    P.seed, L.pid, wi);
-      thermal<F32>(P, wi, ion.eq, ion.mu);
-      sadd(led + (L_E_IN_THERMAL), ion.eq);
-      sadd(led + (L_BIRTHS + ch.sout), 1);
-      sadd(led + (L_N_SPAWN_ION), 1);
-      emit(port, ion);
+  } else if (ch.kind == IONIZATION || ch.kind == CLUSTERING) {
+    if (port.rare) {
+      RareBuf* rb = port.rare;
+      const int i = atomicAdd(&rb->n, 1);
+      if (i < RB - rb->r) {
+        rb->s[i] = L;
+        rb->ch[i] = (int8_t)k;
+        o.alive = false;
+        o.parked = true;
+        return;
+      }
     }
-    L.eq = eq1;
-    L.mu = (double)mu_p;
-  } else if (ch.kind == CLUSTERING) {
-    die<F32>(P, led, L, R_CLUSTER, L_E_CLUSTER);
-    unsigned long long wc[4];
-    const unsigned evc = L.ev - 1;
-    philox4x64_10((unsigned long long)evc, L.node,
-                  ((unsigned long long)P.pass << 8) | DOM_CLUSTER, 0ULL, P.seed, L.pid, wc);
-    long long eqc;
-    double muc;
-    thermal<F32>(P, wc, eqc, muc);
-    L.node = child_node(L.node, evc, 2);
-    L.eq = eqc;
-    L.mu = muc;
-    L.tal = 0.0;
-    L.ev = 0;
-    L.sp = ch.sout;
-    sadd(led + (L_E_IN_THERMAL), eqc);
-    sadd(led + (L_BIRTHS + ch.sout), 1);
+    rare_kinematics<F32>(P, led, L, o, port, k, w);
     return;
   } else {  // RECOMBINATION
     atomicAdd(P.recomb + (size_t)ch.sout * P.nz + jc, 1ULL);
@@ -536,17 +611,7 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
     o.alive = false;
     return;
   }
-  // ---- terminator (Sec. 3.2) ----
-  if (L.sp == SP_E && L.eq < P.ecut_q) {
-    die<F32>(P, led, L, R_CUTOFF, L_E_CUTOFF);
-    o.alive = false;
-  } else if (L.ev >= P.max_coll) {
-    die<F32>(P, led, L, R_CAP_COLL, L_E_CAP);
-    o.alive = false;
-  } else if (P.track_time && L.tal >= P.max_life) {
-    die<F32>(P, led, L, R_CAP_TIME, L_E_CAP);
-    o.alive = false;
-  }
+  terminate<F32>(P, led, L, o);
 }
 
 }  // namespace karl

@@ -162,12 +162,18 @@ __global__ void __launch_bounds__(256, 2) multi_kernel(SlotDesc* D, SlotCtl* C, 
                                                     unsigned long long timeout_ns) {
   const unsigned long long deadline = globaltimer_ns() + timeout_ns;
   __shared__ WarpQueue wq[WARPS];
-  if (threadIdx.x < WARPS) wq[threadIdx.x].top = 0;
+  __shared__ RareBuf rbuf[WARPS];
+  if (threadIdx.x < WARPS) {
+    wq[threadIdx.x].top = 0;
+    rbuf[threadIdx.x].n = 0;
+    rbuf[threadIdx.x].r = 0;
+  }
   __syncthreads();
   Control* ctl = &M->c;
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   WarpQueue& Q = wq[threadIdx.x >> 5];
+  RareBuf& Rb = rbuf[threadIdx.x >> 5];
   bool has = false;
   Lane L;
   L.slot = 0;
@@ -176,6 +182,7 @@ __global__ void __launch_bounds__(256, 2) multi_kernel(SlotDesc* D, SlotCtl* C, 
   EventOut o;
   o.flights = o.colls = o.recoil = o.excit = 0;
   o.chan = -1;
+  o.parked = false;
   unsigned long long idle_iters = 0, busy_iters = 0, busy_lane_iters = 0, started = 0;
   unsigned idle_ns = 128;
   RingPort port;
@@ -183,6 +190,7 @@ __global__ void __launch_bounds__(256, 2) multi_kernel(SlotDesc* D, SlotCtl* C, 
   port.ctl = ctl;
   port.deadline = deadline;
   port.q = &Q;
+  port.rare = &Rb;
   port.local = true;
   port.spilled = 0;
   port.slot_live = nullptr;
@@ -192,6 +200,16 @@ __global__ void __launch_bounds__(256, 2) multi_kernel(SlotDesc* D, SlotCtl* C, 
     lpass = ld_acquire_i(&C[s].pass);
     lpass = lpass == 2 ? 2 : 1;
     Pl = &D[s].P[lpass - 1];
+  };
+  // per-lane sums belong to the request of the lane's particle: they go to
+  // its ledger whenever the lane lets the particle go (death, park, hand-back)
+  auto flush_sums = [&]() {
+    unsigned long long* led = Pl->ledger;
+    if (o.flights) atomicAdd(led + L_N_FLIGHT, o.flights);
+    if (o.colls) atomicAdd(led + L_N_COLL, o.colls);
+    if (o.recoil) atomicAdd(led + L_LOSS_RECOIL, o.recoil);
+    if (o.excit) atomicAdd(led + L_LOSS_EXCIT, o.excit);
+    o.flights = o.colls = o.recoil = o.excit = 0;
   };
   // passes this lane saw empty: one from a claim (lane 0), one from a death
   int trigA = 0, tslotA = 0, tpassA = 1, trigB = 0, tslotB = 0, tpassB = 1;
@@ -230,6 +248,25 @@ __global__ void __launch_bounds__(256, 2) multi_kernel(SlotDesc* D, SlotCtl* C, 
       }
       if (__shfl_sync(FULL, stop, 0)) break;
       port.local = __shfl_sync(FULL, local, 0) != 0;
+    }
+
+    // ---- idle lanes first resume particles handed back for a batch ----
+    __syncwarp();
+    if (Rb.r > 0) {
+      const unsigned needr = __ballot_sync(FULL, !has);
+      const int r0 = Rb.r;
+      const int tr = min(__popc(needr), r0);
+      if (!has) {
+        const int rank = __popc(needr & lt);
+        if (rank < tr) {
+          L = Rb.s[RB - r0 + rank];
+          has = true;
+          bind(L.slot);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) Rb.r = r0 - tr;
+      __syncwarp();
     }
 
     // ---- idle lanes take the warp's own products first (newest first) ----
@@ -357,6 +394,42 @@ __global__ void __launch_bounds__(256, 2) multi_kernel(SlotDesc* D, SlotCtl* C, 
       }
     }
 
+    // ---- parked rare collisions: once enough have gathered, free lanes and
+    // then busy ones -- whose particles wait in the slots the batch frees --
+    // perform them together.  When the primaries are used up the products of
+    // parked collisions may be the work that is left, so they go at once ----
+    __syncwarp();
+    int rk = -1;
+    const int nr = min(Rb.n, RB - Rb.r);
+    const unsigned hm = __ballot_sync(FULL, has);
+    const bool batch = nr >= RB_TRIGGER || (nr > 0 && (hm == 0 || !port.local));
+    if (batch) {
+      const int nfree = 32 - __popc(hm);
+      const int rank = has ? nfree + __popc(hm & lt) : __popc(~hm & lt);
+      const bool take = rank < nr;
+      const bool give = take && has;
+      Lane back;
+      if (give) {
+        flush_sums();                              // the lane changes particle
+        back = L;
+      }
+      if (take) {
+        L = Rb.s[nr - 1 - rank];
+        rk = Rb.ch[nr - 1 - rank];
+        has = true;
+        bind(L.slot);
+      }
+      __syncwarp();                                // every parked slot has been read
+      const int r0 = Rb.r;
+      if (give) Rb.s[RB - r0 - 1 - (rank - nfree)] = back;   // stays counted as live
+      __syncwarp();
+      if (lane == 0) {
+        Rb.r = r0 + max(nr - nfree, 0);
+        Rb.n = 0;
+      }
+      __syncwarp();
+    }
+
     // ---- one event ----
     bool died = false;
     const unsigned busy = __ballot_sync(FULL, has);
@@ -364,13 +437,29 @@ __global__ void __launch_bounds__(256, 2) multi_kernel(SlotDesc* D, SlotCtl* C, 
       idle_ns = 128;
       busy_lane_iters += __popc(busy);
       ++busy_iters;
-      if (has) {
+      if (has && rk >= 0) {
+        port.slot_live = &C[L.slot].word[lpass - 1];
+        unsigned long long w[4];
+        parked_block(*Pl, L, w);
+        o.alive = true;
+        o.parked = false;
+        o.chan = -1;
+        rare_kinematics<F32>(*Pl, Pl->ledger, L, o, port, rk, w);
+        if (!o.alive) { has = false; died = true; }
+      } else if (has) {
         port.slot_live = &C[L.slot].word[lpass - 1];
         event<F32>(*Pl, Pl->ledger, L, o, port);
-        if (!o.alive) { has = false; died = true; }
+        if (!o.alive) {
+          has = false;
+          died = !o.parked;
+          if (o.parked) flush_sums();
+        }
       }
       __syncwarp();
-      if (lane == 0 && Q.top > WQ) Q.top = WQ;
+      if (lane == 0) {
+        if (Q.top > WQ) Q.top = WQ;
+        if (Rb.n > RB - Rb.r) Rb.n = RB - Rb.r;
+      }
       // channel counts, one add per distinct (request, channel) per warp
       const unsigned mc = __ballot_sync(FULL, o.chan >= 0);
       if (o.chan >= 0) {
@@ -381,13 +470,7 @@ __global__ void __launch_bounds__(256, 2) multi_kernel(SlotDesc* D, SlotCtl* C, 
       }
       o.chan = -1;
       if (died) {
-        // per-lane sums go to the request's ledger with the particle's death
-        unsigned long long* led = Pl->ledger;
-        atomicAdd(led + L_N_FLIGHT, o.flights);
-        atomicAdd(led + L_N_COLL, o.colls);
-        if (o.recoil) atomicAdd(led + L_LOSS_RECOIL, o.recoil);
-        if (o.excit) atomicAdd(led + L_LOSS_EXCIT, o.excit);
-        o.flights = o.colls = o.recoil = o.excit = 0;
+        flush_sums();
         const unsigned long long o2 =
             atomicAdd(&C[L.slot].word[lpass - 1], (unsigned long long)0 - 1ULL);
         if (pass_emptied(o2, 1ULL, D[L.slot].n_prim)) { trigB = 1; tslotB = L.slot; tpassB = lpass; }

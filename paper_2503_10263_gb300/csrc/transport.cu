@@ -63,10 +63,15 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const Params Pk, Ring
   __shared__ Shared S;
   __shared__ Params SP;
   __shared__ WarpQueue wq[WARPS];
+  __shared__ RareBuf rbuf[WARPS];
   if (threadIdx.x == 0) SP = Pk;
   for (int i = threadIdx.x; i < LEDGER; i += blockDim.x) S.ledger[i] = 0;
   for (int i = threadIdx.x; i < MAXCH; i += blockDim.x) S.chan[i] = 0;
-  if (threadIdx.x < WARPS) wq[threadIdx.x].top = 0;
+  if (threadIdx.x < WARPS) {
+    wq[threadIdx.x].top = 0;
+    rbuf[threadIdx.x].n = 0;
+    rbuf[threadIdx.x].r = 0;
+  }
   __syncthreads();
   stage_tables(SP, Pk, dyn, dyn_doubles);
   __syncthreads();
@@ -75,9 +80,12 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const Params Pk, Ring
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   WarpQueue& Q = wq[threadIdx.x >> 5];
+  RareBuf& Rb = rbuf[threadIdx.x >> 5];
+  bool eager = false;
   bool has = false;
   Lane L;
   EventOut o;
+  o.parked = false;
   o.flights = 0;
   o.colls = 0;
   o.recoil = 0;
@@ -91,6 +99,7 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const Params Pk, Ring
   port.ctl = ctl;
   port.deadline = deadline;
   port.q = &Q;
+  port.rare = &Rb;
   port.local = true;
   port.spilled = 0;
   port.slot_live = nullptr;
@@ -111,7 +120,30 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const Params Pk, Ring
         }
       }
       if (__shfl_sync(FULL, stop, 0)) break;
-      port.local = ld_relaxed(&ctl->prim_next) < (unsigned long long)P.n_prim;
+      const unsigned long long pn = ld_relaxed(&ctl->prim_next);
+      port.local = pn < (unsigned long long)P.n_prim;
+      // The last primaries' histories set the end of the pass: from about two
+      // primaries per lane before the end, parked collisions go at once so
+      // those histories are not held up.
+      eager = pn + 2ULL * gridDim.x * blockDim.x >= (unsigned long long)P.n_prim;
+    }
+
+    // ---- idle lanes first resume particles handed back for a batch ----
+    __syncwarp();
+    if (Rb.r > 0) {
+      const unsigned needr = __ballot_sync(FULL, !has);
+      const int r0 = Rb.r;
+      const int tr = min(__popc(needr), r0);
+      if (!has) {
+        const int rank = __popc(needr & lt);
+        if (rank < tr) {
+          L = Rb.s[RB - r0 + rank];
+          has = true;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) Rb.r = r0 - tr;
+      __syncwarp();
     }
 
     // ---- idle lanes take the warp's own products first (newest first) ----
@@ -154,11 +186,12 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const Params Pk, Ring
     const unsigned need = __ballot_sync(FULL, !has);
     if (need) {
       const int k = __popc(need);
-      unsigned long long base = 0;
-      int got = 0, src = 0;
+      unsigned long long rbase = 0, pbase = 0;
+      int rgot = 0, pgot = 0;
       if (lane == 0) {
         // Count the lanes as active only when work is visible, then claim it:
-        // idle warps that find nothing leave the counter alone.
+        // idle warps that find nothing leave the counter alone.  Lanes the
+        // ring cannot fill take primaries in the same step.
         unsigned long long h = ld_relaxed(&ctl->head), t = ld_relaxed(&ctl->tail);
         const unsigned long long pn = ld_relaxed(&ctl->prim_next);
         const bool ring_work = h < t;
@@ -169,33 +202,35 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const Params Pk, Ring
           for (int tries = 0; tries < 16 && h < t; ++tries) {
             unsigned long long take = t - h < (unsigned long long)k ? t - h : (unsigned long long)k;
             unsigned long long old = atomicCAS(&ctl->head, h, h + take);
-            if (old == h) { base = h; got = (int)take; src = 1; break; }
+            if (old == h) { rbase = h; rgot = (int)take; break; }
             h = old;
             t = ld_relaxed(&ctl->tail);
           }
-          if (got == 0 && prim_work) {
-            unsigned long long p0 = atomicAdd(&ctl->prim_next, (unsigned long long)k);
+          if (rgot < k && prim_work) {
+            const int want = k - rgot;
+            unsigned long long p0 = atomicAdd(&ctl->prim_next, (unsigned long long)want);
             if (p0 < (unsigned long long)P.n_prim) {
               unsigned long long left = (unsigned long long)P.n_prim - p0;
-              base = p0;
-              got = left < (unsigned long long)k ? (int)left : k;
-              src = 2;
+              pbase = p0;
+              pgot = left < (unsigned long long)want ? (int)left : want;
             }
           }
-          if (got < k) atomicAdd((unsigned long long*)&ctl->active, (unsigned long long)(got - k));
+          if (rgot + pgot < k)
+            atomicAdd((unsigned long long*)&ctl->active, (unsigned long long)(rgot + pgot - k));
         }
       }
-      base = __shfl_sync(FULL, base, 0);
-      got = __shfl_sync(FULL, got, 0);
-      src = __shfl_sync(FULL, src, 0);
+      rbase = __shfl_sync(FULL, rbase, 0);
+      pbase = __shfl_sync(FULL, pbase, 0);
+      rgot = __shfl_sync(FULL, rgot, 0);
+      pgot = __shfl_sync(FULL, pgot, 0);
       bool born_dead = false;
-      if (!has && got > 0) {
+      if (!has && rgot + pgot > 0) {
         const int rank = __popc(need & lt);
-        if (rank < got) {
-          const unsigned long long idx = base + rank;
-          if (src == 1) {
-            has = ring_get(R, ctl, idx, L, deadline);
+        if (rank < rgot + pgot) {
+          if (rank < rgot) {
+            has = ring_get(R, ctl, rbase + rank, L, deadline);
           } else {
+            const unsigned long long idx = pbase + (rank - rgot);
             L.z = P.pz[idx];
             L.eq = quant_e(P.pe[idx]);
             L.mu = P.pmu[idx];
@@ -223,6 +258,39 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const Params Pk, Ring
         __threadfence();
         atomicAdd((unsigned long long*)&ctl->active, (unsigned long long)(-(long long)__popc(md)));
       }
+    }
+
+    // ---- parked rare collisions: once enough have gathered, free lanes and
+    // then busy ones -- whose particles wait in the slots the batch frees --
+    // perform them together; near the end of the pass, at once ----
+    __syncwarp();
+    int rk = -1;
+    const int nr = min(Rb.n, RB - Rb.r);
+    const unsigned hm = __ballot_sync(FULL, has);
+    const bool batch = nr >= RB_TRIGGER || (nr > 0 && (hm == 0 || eager));
+    if (batch) {
+      const int nfree = 32 - __popc(hm);
+      const int rank = has ? nfree + __popc(hm & lt) : __popc(~hm & lt);
+      const bool take = rank < nr;
+      const bool give = take && has;
+      Lane back;
+      if (give) {
+        back = L;
+      }
+      if (take) {
+        L = Rb.s[nr - 1 - rank];
+        rk = Rb.ch[nr - 1 - rank];
+        has = true;
+      }
+      __syncwarp();                                // every parked slot has been read
+      const int r0 = Rb.r;
+      if (give) Rb.s[RB - r0 - 1 - (rank - nfree)] = back;   // stays counted as live
+      __syncwarp();
+      if (lane == 0) {
+        Rb.r = r0 + max(nr - nfree, 0);
+        Rb.n = 0;
+      }
+      __syncwarp();
     }
 
     const unsigned busy = __ballot_sync(FULL, has);
@@ -256,12 +324,23 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const Params Pk, Ring
 
     // ---- one event ----
     bool died = false;
-    if (has) {
-      event<F32>(P, S.ledger, L, o, port);
+    if (has && rk >= 0) {
+      unsigned long long w[4];
+      parked_block(P, L, w);
+      o.alive = true;
+      o.parked = false;
+      o.chan = -1;
+      rare_kinematics<F32>(P, S.ledger, L, o, port, rk, w);
       if (!o.alive) { has = false; died = true; }
+    } else if (has) {
+      event<F32>(P, S.ledger, L, o, port);
+      if (!o.alive) { has = false; died = !o.parked; }
     }
     __syncwarp();
-    if (lane == 0 && Q.top > WQ) Q.top = WQ;          // pushes past the end went to the ring
+    if (lane == 0) {
+      if (Q.top > WQ) Q.top = WQ;                     // pushes past the end went to the ring
+      if (Rb.n > RB - Rb.r) Rb.n = RB - Rb.r;         // parks past the end were done in line
+    }
 
     // ---- channel counts, one shared-memory add per distinct channel per warp ----
     const unsigned mc = __ballot_sync(FULL, o.chan >= 0);
@@ -312,8 +391,10 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const Params Pk, Ring
 // ---------------------------------------------------------------------------
 // host-callable launchers (used by the C ABI in karl_abi.cu)
 
-// dynamic shared memory for the staged tables: at most this much per block
-constexpr int DYN_MAX_BYTES = 120 * 1024;
+// dynamic shared memory for the staged tables: at most this much per block,
+// so that two blocks of 256 threads (with ~35 KB of static shared memory for
+// the warp queues and parked collisions) still fit one SM's 227 KB
+constexpr int DYN_MAX_BYTES = 76 * 1024;
 
 // Doubles of dynamic shared memory the staged tables of P need (0: too big,
 // read them from global memory).
