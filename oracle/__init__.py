@@ -60,7 +60,8 @@ class _Problem(C.Structure):
         ("e_max_ev", C.c_double), ("n_channels", C.c_int32), ("kind", C.POINTER(C.c_int32)),
         ("species_in", C.POINTER(C.c_int32)), ("species_out", C.POINTER(C.c_int32)),
         ("loss_ev", C.POINTER(C.c_double)), ("sigma_m2", C.POINTER(C.c_double)),
-        ("ioniz_eps_ev", C.c_double),
+        ("ioniz_eps_ev", C.c_double), ("target", C.POINTER(C.c_int32)),
+        ("gas_drift_mps", C.c_double),
     ]
 
 
@@ -97,6 +98,11 @@ def _load():
                                     C.POINTER(C.c_uint64), C.POINTER(C.c_double),
                                     C.POINTER(C.c_double), C.POINTER(C.c_int)]
         lib.orc_collide.restype = C.c_int
+        lib.orc_elastic_moving_target.argtypes = [
+            C.POINTER(_Problem), C.c_double, C.c_double, C.c_double, C.POINTER(C.c_uint64),
+            C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_double),
+            C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        lib.orc_elastic_moving_target.restype = None
         _lib = lib
     return _lib
 
@@ -114,6 +120,7 @@ class _Marshal:
         self.sin = np.array([c.species_in for c in prob.channels], np.int32)
         self.sout = np.array([c.species_out for c in prob.channels], np.int32)
         self.loss = np.array([c.loss_ev for c in prob.channels], np.float64)
+        self.target = np.array([getattr(c, "target", 0) for c in prob.channels], np.int32)
         self.sigma = (prob.sigma_matrix() if prob.channels
                       else np.zeros((0, prob.n_energy))).astype(np.float64)
         self.sigma = np.ascontiguousarray(self.sigma)
@@ -143,6 +150,8 @@ class _Marshal:
         s.loss_ev = _ptr(self.loss, C.c_double)
         s.sigma_m2 = _ptr(self.sigma, C.c_double)
         s.ioniz_eps_ev = prob.ioniz_eps_ev
+        s.target = _ptr(self.target, C.c_int32)
+        s.gas_drift_mps = float(getattr(prob, "gas_drift_mps", 0.0))
         self.s = s
 
 
@@ -258,3 +267,22 @@ def collide(prob, channel: int, species: int, e_ev: float, mu: float, words):
     n = lib.orc_collide(C.byref(m.s), channel, species, e_ev, mu, _ptr(w, C.c_uint64),
                         _ptr(oe, C.c_double), _ptr(om, C.c_double), _ptr(osp, C.c_int))
     return [(float(oe[i]), float(om[i]), int(osp[i])) for i in range(n)]
+
+
+def elastic_moving_target(prob, m1_ev: float, e_ev: float, mu: float, words, ctr, key):
+    """One elastic collision with a moving target: event block `words`, target
+    blocks from counter (ctr[0], ctr[1], ctr[2], k) and key; returns
+    (E', mu', velocities[12])."""
+    lib = _load()
+    m = _Marshal(prob)
+    w = np.array(words, np.uint64)
+    c = np.array(ctr, np.uint64)
+    k = np.array(key, np.uint64)
+    oe = np.zeros(1)
+    om = np.zeros(1)
+    v = np.zeros(12)
+    lib.orc_elastic_moving_target(C.byref(m.s), m1_ev, e_ev, mu, _ptr(w, C.c_uint64),
+                                  _ptr(c, C.c_uint64), _ptr(k, C.c_uint64),
+                                  _ptr(oe, C.c_double), _ptr(om, C.c_double),
+                                  _ptr(v, C.c_double))
+    return float(oe[0]), float(om[0]), v

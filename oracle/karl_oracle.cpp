@@ -19,7 +19,11 @@
  *  - sigma(E): linear interpolation in ln E on the input nodes, zero for
  *    E <= loss of the channel, clamped to the end nodes outside the grid;
  *  - lab kinetic energy with the target at rest; relativistic speed;
- *  - elastic: isotropic in the centre-of-mass frame;
+ *  - elastic: isotropic in the centre-of-mass frame; for a channel marked as
+ *    having a moving target (Sec. 3.3 Elastic: gas drift plus a Maxwell-
+ *    Boltzmann velocity), nonrelativistic velocities, the impactor's gyrophase
+ *    taken as 0 (the target distribution is symmetric about z), the relative
+ *    velocity rotated in the centre-of-mass frame;
  *  - ionization: secondary energy W in [0, (E-I)/2] with pdf ~ 1/(1+(W/eps)^2),
  *    the fast electron is the incident one, binary-encounter polar angles,
  *    secondary azimuth = primary azimuth - pi (Sec. 3.3, Ionization); the ion
@@ -54,7 +58,7 @@ enum { ELASTIC = 0, IONIZATION = 1, EXCITATION = 2, CLUSTERING = 3, RECOMBINATIO
 enum { SP_E = 0, SP_T2P = 1, SP_T3P = 2 };
 enum { R_EXIT0 = 0, R_EXIT1 = 1, R_CUTOFF = 2, R_CAP_COLL = 3, R_CAP_TIME = 4,
        R_RECOMB = 5, R_CLUSTER = 6, R_STALLED = 7 };
-enum { DOM_EVENT = 0, DOM_ION_BIRTH = 1, DOM_CLUSTER = 2, DOM_REDRAW = 3 };
+enum { DOM_EVENT = 0, DOM_ION_BIRTH = 1, DOM_CLUSTER = 2, DOM_REDRAW = 3, DOM_TARGET = 4 };
 
 /* ---------------- Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11) -------- */
 void mulhilo64(uint64_t a, uint64_t b, uint64_t* hi, uint64_t* lo) {
@@ -100,6 +104,117 @@ uint64_t child_node(uint64_t parent, uint32_t ev, uint32_t slot) {
 int64_t quant_e(double e_ev) { return (int64_t)std::floor(e_ev * Q_ENERGY); }
 /* an energy transfer, rounded to the nearest 2^-24 eV unit */
 int64_t quant_recoil(double de_ev) { return (int64_t)std::floor(de_ev * Q_ENERGY + 0.5); }
+
+/* The block of target-velocity draws number k of one collision (two per
+ * attempt of the rejection below). */
+typedef void (*TargetBlock)(void* ctx, uint64_t k, uint64_t w[4]);
+
+/* Velocity of the target of an elastic collision (Sec. 3.3 Elastic: the gas
+ * drift plus a draw from the Maxwell-Boltzmann distribution at the gas
+ * temperature).  Targets of velocity v2 are met at a rate proportional to the
+ * relative speed |v1 - v2|, so in the gas frame (impactor velocity u = v1 -
+ * drift) the thermal part w is drawn from |u - w| f(w), f the Maxwellian with
+ * per-component variance a^2 = kT/M, by the free-gas rejection method: the
+ * speed s = |w| from the mixture (|u| + s) s^2 exp(-s^2 / 2a^2) -- with
+ * probability |u| sqrt(pi) / (|u| sqrt(pi) + 2 sqrt(2) a) a Maxwell speed
+ * (s^2 / a^2 chi-square with 3 degrees of freedom), otherwise s^2 / 2a^2 ~
+ * Gamma(2, 1) -- and an isotropic direction, accepted with probability
+ * |u - w| / (|u| + s).  Attempt k uses blocks 2k and 2k + 1; after 64
+ * rejections the last draw stands.  Velocities in units of c. */
+void target_velocity(const orc_problem* p, const double v1[3], TargetBlock blk, void* ctx,
+                     double v2[3]) {
+  const double a = std::sqrt(KB_EV * p->gas_temperature_k / p->target_mass_ev);
+  const double ud = p->gas_drift_mps / C_LIGHT;
+  const double u[3] = {v1[0], v1[1], v1[2] - ud};
+  const double un = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  const double pmax = un * std::sqrt(M_PI) / (un * std::sqrt(M_PI) + 2.0 * std::sqrt(2.0) * a);
+  double w[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < 64; ++k) {
+    uint64_t b0[4], b1[4];
+    blk(ctx, 2 * (uint64_t)k, b0);
+    blk(ctx, 2 * (uint64_t)k + 1, b1);
+    const double l1 = -std::log(eta01(b0[1])), l2 = -std::log(eta01(b0[2]));
+    double s2;
+    if (u01(b0[0]) < pmax) {
+      const double c = std::cos(TWO_PI * u01(b0[3]));
+      s2 = a * a * (2.0 * l1 + 2.0 * l2 * c * c);       /* chi-square, 3 dof */
+    } else {
+      s2 = 2.0 * a * a * (l1 + l2);                      /* Gamma(2, 1) */
+    }
+    const double sp = std::sqrt(s2);
+    const double ct = 2.0 * u01(b1[0]) - 1.0;
+    const double st = std::sqrt(std::fmax(0.0, 1.0 - ct * ct));
+    const double ph = TWO_PI * u01(b1[1]);
+    w[0] = sp * st * std::cos(ph);
+    w[1] = sp * st * std::sin(ph);
+    w[2] = sp * ct;
+    const double g0 = u[0] - w[0], g1 = u[1] - w[1], g2 = u[2] - w[2];
+    const double gn = std::sqrt(g0 * g0 + g1 * g1 + g2 * g2);
+    if (u01(b1[2]) * (un + sp) < gn) break;
+  }
+  v2[0] = w[0];
+  v2[1] = w[1];
+  v2[2] = ud + w[2];
+}
+
+/* Elastic collision with a moving target (Sec. 3.3 Elastic).  The impactor
+ * velocity v1 = sqrt(2E/m1) (sin, 0, cos of the pitch) -- nonrelativistic,
+ * gyrophase 0, which loses nothing because the target distribution is
+ * symmetric about z.  In the centre-of-mass frame the relative velocity
+ * g = v1 - v2 keeps its length and turns by a polar angle chi with cos chi
+ * uniform in [-1, 1) (w[2]) and an azimuth 2 pi u (w[3]) measured from the
+ * plane of z and g; the impactor leaves with V + m2/(m1+m2) g'.  Velocities in
+ * units of c.  v (optional, 12 values): impactor and target before, impactor
+ * and target after. */
+void moving_target_elastic(const orc_problem* p, double m1, double e, double mu,
+                           const uint64_t w[4], TargetBlock blk, void* ctx, double* e_out,
+                           double* mu_out, double* v) {
+  const double m2 = p->target_mass_ev;
+  const double M = m1 + m2;
+  const double s1 = std::sqrt(2.0 * e / m1);
+  const double sperp = std::sqrt(std::fmax(0.0, 1.0 - mu * mu));
+  const double v1[3] = {s1 * sperp, 0.0, s1 * mu};
+  double v2[3];
+  target_velocity(p, v1, blk, ctx, v2);
+  double V[3], g[3];
+  for (int i = 0; i < 3; ++i) {
+    V[i] = (m1 * v1[i] + m2 * v2[i]) / M;
+    g[i] = v1[i] - v2[i];
+  }
+  const double gn = std::sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+  double gh[3] = {0.0, 0.0, 1.0};
+  if (gn > 0.0) for (int i = 0; i < 3; ++i) gh[i] = g[i] / gn;
+  /* e1: the part of z perpendicular to g (x if g is along z), e2 = gh x e1 */
+  double e1[3] = {-gh[2] * gh[0], -gh[2] * gh[1], 1.0 - gh[2] * gh[2]};
+  double n1 = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+  if (n1 < 1e-12) {
+    e1[0] = 1.0; e1[1] = 0.0; e1[2] = 0.0;
+    n1 = 1.0;
+  }
+  for (int i = 0; i < 3; ++i) e1[i] /= n1;
+  const double e2[3] = {gh[1] * e1[2] - gh[2] * e1[1], gh[2] * e1[0] - gh[0] * e1[2],
+                        gh[0] * e1[1] - gh[1] * e1[0]};
+  const double cchi = 2.0 * u01(w[2]) - 1.0;
+  const double schi = std::sqrt(std::fmax(0.0, 1.0 - cchi * cchi));
+  const double phi = TWO_PI * u01(w[3]);
+  const double cph = std::cos(phi), sph = std::sin(phi);
+  double g2[3], v1n[3];
+  for (int i = 0; i < 3; ++i) {
+    g2[i] = gn * (schi * cph * e1[i] + schi * sph * e2[i] + cchi * gh[i]);
+    v1n[i] = V[i] + m2 / M * g2[i];
+  }
+  const double sp2 = v1n[0] * v1n[0] + v1n[1] * v1n[1] + v1n[2] * v1n[2];
+  *e_out = 0.5 * m1 * sp2;
+  *mu_out = sp2 > 0.0 ? std::fmax(-1.0, std::fmin(1.0, v1n[2] / std::sqrt(sp2))) : 1.0;
+  if (v) {
+    for (int i = 0; i < 3; ++i) {
+      v[i] = v1[i];
+      v[3 + i] = v2[i];
+      v[6 + i] = v1n[i];
+      v[9 + i] = V[i] - m1 / M * g2[i];
+    }
+  }
+}
 
 struct Particle {
   double z;
@@ -416,7 +531,22 @@ struct Worker {
       if (ch < 0) ch = last;                                 /* rounding at the top end */
       T.chan_count[ch] += 1;
       int kind = p->kind[ch];
-      if (kind == ELASTIC) {
+      if (kind == ELASTIC && p->target && p->target[ch] == 1) {
+        /* moving target: its velocity from blocks of its own domain */
+        struct Ctx { Worker* self; uint32_t ev; uint64_t node; } cx = {this, P.ev - 1, P.node};
+        auto blk = [](void* c, uint64_t k, uint64_t out[4]) {
+          Ctx* q = (Ctx*)c;
+          q->self->block(q->ev, q->node, DOM_TARGET, k, out);
+        };
+        double e1, mu1;
+        moving_target_elastic(p, m, e, P.mu, w, blk, &cx, &e1, &mu1, nullptr);
+        /* energy given to the gas (negative when the gas heats the impactor) */
+        int64_t rq = quant_recoil(e - e1);
+        if (rq > P.eq) rq = P.eq;
+        T.ledger[ORC_E_LOSS_RECOIL] += rq;
+        P.eq -= rq;
+        P.mu = mu1;
+      } else if (kind == ELASTIC) {
         /* isotropic in CM; lab energy and polar angle for a target at rest */
         double g = m / p->target_mass_ev;
         double cchi = 2.0 * u01(w[2]) - 1.0;
@@ -612,6 +742,18 @@ void orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4
 }
 
 double orc_sigma(const orc_problem* p, int channel, double e_ev) { return sigma_at(p, channel, e_ev); }
+
+void orc_elastic_moving_target(const orc_problem* p, double m1_ev, double e_ev, double mu,
+                               const uint64_t w[4], const uint64_t ctr[3], const uint64_t key[2],
+                               double* out_e, double* out_mu, double* v) {
+  struct Ctx { const uint64_t* ctr; const uint64_t* key; } cx = {ctr, key};
+  auto blk = [](void* c, uint64_t k, uint64_t out[4]) {
+    Ctx* q = (Ctx*)c;
+    const uint64_t full[4] = {q->ctr[0], q->ctr[1], q->ctr[2], k};
+    philox4x64_10(full, q->key, out);
+  };
+  moving_target_elastic(p, m1_ev, e_ev, mu, w, blk, &cx, out_e, out_mu, v);
+}
 
 int orc_collide(const orc_problem* p, int ch, int species, double e_ev, double mu,
                 const uint64_t w[4], double* out_e, double* out_mu, int* out_species) {

@@ -55,6 +55,11 @@ typedef struct {
   const double* loss_ev;
   const double* sigma_m2;      /* [n_channels][n_energy] */
   double ioniz_eps_ev;
+  /* per channel: 0 target at rest, 1 moving target (gas drift along +z plus a
+     Maxwell-Boltzmann draw at the gas temperature; elastic channels only);
+     NULL: every target at rest */
+  const int32_t* target;
+  double gas_drift_mps;        /* drift velocity of the gas along +z */
 } orc_problem;
 
 typedef struct {
@@ -101,6 +106,18 @@ double orc_sigma(const orc_problem* p, int channel, double e_ev);
  * products written to out_* (the incident particle first, if it survives). */
 int orc_collide(const orc_problem* p, int channel, int species, double e_ev, double mu,
                 const uint64_t words[4], double* out_e, double* out_mu, int* out_species);
+
+/* Elastic collision with a moving target (the kinematics of a channel with
+ * target == 1), for single-collision checks: the impactor (mass m1_ev, energy
+ * e_ev, pitch cosine mu) meets a target whose velocity is drawn from Philox
+ * blocks with counter (ctr[0], ctr[1], ctr[2], k) and key key[0..1]; w[2],
+ * w[3] give the centre-of-mass angles.  Writes the impactor's energy and pitch
+ * cosine after the collision, and (if not NULL) the velocities in units of c:
+ * v[0..2] impactor before, v[3..5] target before, v[6..8] impactor after,
+ * v[9..11] target after. */
+void orc_elastic_moving_target(const orc_problem* p, double m1_ev, double e_ev, double mu,
+                               const uint64_t w[4], const uint64_t ctr[3], const uint64_t key[2],
+                               double* out_e, double* out_mu, double* v);
 
 #ifdef __cplusplus
 }

@@ -64,6 +64,7 @@ class Channel:
                           # clustering: product; recombination: partner field
     loss_ev: float
     sigma_m2: np.ndarray  # [n_energy] values at the table nodes
+    target: int = 0       # 0 target at rest; 1 moving (thermal + gas drift), elastic only
 
 
 @dataclasses.dataclass
@@ -91,6 +92,7 @@ class Problem:
     ioniz_eps_ev: float
     channels: List[Channel]
     n_passes: int = 1
+    gas_drift_mps: float = 0.0     # drift velocity of the gas along +z
 
     @property
     def n_channels(self) -> int:
@@ -280,6 +282,33 @@ def _problem(name: str, length: float, nz: int, n_seg: np.ndarray, full: bool,
         n_spec_bins=20000, spec_bin_ev=1.0, species_mass_ev=SPECIES_MASS_EV.copy(),
         target_mass_ev=M_T2_EV, n_energy=n_energy, e_min_ev=1.0, e_max_ev=2.0e4,
         ioniz_eps_ev=8.0, channels=chans, n_passes=2 if full else 1)
+
+
+def thermalization(n_primaries: int = 4000, seed: int = 1, density_m3: float = 1e22,
+                   length: float = 0.2, nz: int = 200, e_inj_ev: float = 8e-3,
+                   sigma_m2: float = 1e-19, temperature_k: float = 80.0,
+                   drift_mps: float = 0.0):
+    """Elastic thermalisation (Sec. 4): mono-energetic electrons injected in
+    the middle of a uniform T2 reservoir, moving along +z; elastic scattering
+    on a moving (Maxwell-Boltzmann, drifting) target is the only channel, with
+    a constant cross section; no energy cut, so every electron leaves through
+    an end."""
+    nodes = energy_nodes(64, 1e-5, 1.0)
+    chans = [Channel("elastic_moving_target", ELASTIC, E, -1, 0.0,
+                     np.full(nodes.shape, sigma_m2), target=1)]
+    prob = Problem(
+        name="thermalization", length_m=length, n_zbins=nz,
+        n_seg_m3=np.full(nz, density_m3, np.float64), area_m2=1.0,
+        activity_bq=activity_for(density_m3 * length, 1.0), e_cut_ev=0.0,
+        max_collisions=100_000_000, max_lifetime_s=math.inf, b_tesla=2.5,
+        gas_temperature_k=temperature_k, n_tebins=1, n_spec_bins=4000, spec_bin_ev=2.5e-5,
+        species_mass_ev=SPECIES_MASS_EV.copy(), target_mass_ev=M_T2_EV, n_energy=64,
+        e_min_ev=1e-5, e_max_ev=1.0, ioniz_eps_ev=8.0, channels=chans, n_passes=1,
+        gas_drift_mps=drift_mps)
+    z = np.full(n_primaries, 0.5 * length)
+    e = np.full(n_primaries, e_inj_ev)
+    mu = np.ones(n_primaries)
+    return prob, Primaries(z, e, mu, np.zeros(n_primaries, np.uint8), n_primaries)
 
 
 def config1(n_primaries: int = 10_000, seed: int = 1, density_m3: float = 1e19,
