@@ -99,6 +99,7 @@ typedef struct karl_geometry {
   double spec_bin_ev;          /* end-spectrum bin width, > 0 */
   double species_mass_ev[KARL_N_SPECIES];   /* rest energies */
   double target_mass_ev;       /* background gas molecule */
+  double gas_drift_mps;        /* drift velocity of the gas along +z (moving targets) */
 } karl_geometry;
 
 /* Cross-section tables (copied at create).  sigma of channel k at energy E is
@@ -115,6 +116,12 @@ typedef struct karl_xs {
   const double* loss_ev;       /* host, threshold / energy loss (>= 0) */
   const double* sigma_m2;      /* host, [n_channels][n_energy], >= 0 */
   double ioniz_eps_ev;         /* eps of the secondary-energy pdf 1/(1+(W/eps)^2) */
+  /* host, [n_channels] or NULL (all 0): 0 = target at rest; 1 = moving target
+   * (Sec. 3.3 Elastic: the gas drift plus a Maxwell-Boltzmann velocity at the
+   * gas temperature, drawn with the relative-speed weight of the collision
+   * rate; the impactor turned in the centre-of-mass frame).  1 is allowed for
+   * elastic channels only. */
+  const int32_t* target;
 } karl_xs;
 
 /* Primary particles (one beta electron and, with ions, one T2+ per decay,

@@ -30,11 +30,16 @@ template <> struct RT<false> {
   static __device__ __forceinline__ R tn(R x) { return tan(x); }
   static __device__ __forceinline__ R atn(R x) { return atan(x); }
   static __device__ __forceinline__ R cpi(R x) { return cospi(x); }
+  static __device__ __forceinline__ R spi(R x) { return sinpi(x); }
   static __device__ __forceinline__ R tab(const Params& P, int k, int i) {
     return __ldg(P.sig + (size_t)i * P.nch + k);      // [node][channel]
   }
   static __device__ __forceinline__ R energy(long long eq) { return (double)eq * (1.0 / 16777216.0); }
   static __device__ __forceinline__ long long quant_de(R de) {
+    return (long long)floor(de * 16777216.0 + 0.5);
+  }
+  // a transfer of either sign, rounded to the nearest 2^-24 eV
+  static __device__ __forceinline__ long long quant_signed(R de) {
     return (long long)floor(de * 16777216.0 + 0.5);
   }
 };
@@ -48,13 +53,19 @@ template <> struct RT<true> {
   static __device__ __forceinline__ R tn(R x) { return tanf(x); }
   static __device__ __forceinline__ R atn(R x) { return atanf(x); }
   static __device__ __forceinline__ R cpi(R x) { return cospif(x); }
+  static __device__ __forceinline__ R spi(R x) { return sinpif(x); }
   static __device__ __forceinline__ R tab(const Params& P, int k, int i) {
     return __ldg(P.sigf + (size_t)i * P.nch + k);     // [node][channel]
   }
-  // energy from 2^-24 eV units with 32-bit conversions (below 65 keV)
+  // energy from 2^-24 eV units with 32-bit conversions (below 65 keV; exact
+  // to FP32 rounding below 256 eV, where thermal energies live)
   static __device__ __forceinline__ R energy(long long eq) {
+    if (eq < (1LL << 32)) return (float)(unsigned)eq * (1.0f / 16777216.0f);
     return eq < (1LL << 40) ? (float)(unsigned)(eq >> 8) * (1.0f / 65536.0f)
                             : (float)eq * (1.0f / 16777216.0f);
+  }
+  static __device__ __forceinline__ long long quant_signed(R de) {
+    return (long long)floorf(de * 16777216.0f + 0.5f);
   }
   static __device__ __forceinline__ long long quant_de(R de) {
     const float x = de * 16777216.0f + 0.5f;
@@ -250,6 +261,94 @@ __device__ __forceinline__ void thermal(const Params& P, const unsigned long lon
   double e = P.kT * (-log(eta01d(w[0])) - log(eta01d(w[1])) * c * c);
   eq = quant_e(e);
   mu = 2.0 * u01d(w[3]) - 1.0;
+}
+
+// Elastic collision with a moving target (Sec. 3.3 Elastic: the target moves
+// with the gas drift plus a Maxwell-Boltzmann velocity; the impactor turns in
+// the centre-of-mass frame).  Nonrelativistic velocities in units of c; the
+// impactor's gyrophase is taken as 0 (the target distribution is symmetric
+// about z).  Targets are met at a rate proportional to the relative speed, so
+// the thermal part w of the target velocity (gas frame, impactor velocity u)
+// is drawn from |u - w| f(w) by the free-gas rejection method: speed from the
+// mixture (|u| + s) s^2 exp(-s^2/2a^2) -- a Maxwell speed with probability
+// |u| sqrt(pi) / (|u| sqrt(pi) + 2 sqrt(2) a), else s^2/2a^2 ~ Gamma(2) --,
+// isotropic direction, accepted with probability |u - w| / (|u| + s); attempt
+// k draws blocks 2k and 2k+1 of the collision's DOM_TARGET stream, and after
+// 64 rejections the last draw stands.  The centre-of-mass polar angle (cos
+// uniform, w[2]) and azimuth (w[3], from the plane of z and the relative
+// velocity) turn the relative velocity.
+template <bool F32>
+__device__ __noinline__ void moving_target_elastic(const Params& P, Lane& L,
+                                                   const unsigned long long w[4],
+                                                   unsigned long long& recoil) {
+  using T = RT<F32>;
+  using R = typename T::R;
+  const int s = L.sp;
+  const R m1 = (R)P.mass[s], m2 = (R)P.target_mass, M = m1 + m2;
+  const R e = T::energy(L.eq);
+  const R s1 = T::sq((R)2 * e / m1);
+  const R mu = (R)L.mu;
+  const R sperp = T::sq(fmax((R)0, (R)1 - mu * mu));
+  const R v1x = s1 * sperp, v1z = s1 * mu;
+  // target velocity
+  const R a = (R)P.target_a, ud = (R)P.drift_c;
+  const R uz = v1z - ud;
+  const R un = T::sq(v1x * v1x + uz * uz);
+  const R rpi = (R)1.7724538509055160273, r8 = (R)2.8284271247461900976;
+  const R pmax = un * rpi / (un * rpi + r8 * a);
+  R wx = (R)0, wy = (R)0, wz = (R)0;
+  for (int k = 0; k < 64; ++k) {
+    unsigned long long b0[4], b1[4];
+    const unsigned long long ctr2 = ((unsigned long long)P.pass << 8) | DOM_TARGET;
+    philox4x64_10((unsigned long long)(L.ev - 1), L.node, ctr2, 2ULL * k, P.seed, L.pid, b0);
+    philox4x64_10((unsigned long long)(L.ev - 1), L.node, ctr2, 2ULL * k + 1, P.seed, L.pid, b1);
+    const R l1 = -T::lg(T::eta(b0[1])), l2 = -T::lg(T::eta(b0[2]));
+    R s2;
+    if (T::u(b0[0]) < pmax) {
+      const R c = T::cpi((R)2 * T::u(b0[3]));
+      s2 = a * a * ((R)2 * l1 + (R)2 * l2 * c * c);     // chi-square, 3 degrees of freedom
+    } else {
+      s2 = (R)2 * a * a * (l1 + l2);                     // Gamma(2, 1)
+    }
+    const R sp = T::sq(s2);
+    const R ct = (R)2 * T::u(b1[0]) - (R)1;
+    const R st = T::sq(fmax((R)0, (R)1 - ct * ct));
+    const R ph = (R)2 * T::u(b1[1]);
+    wx = sp * st * T::cpi(ph);
+    wy = sp * st * T::spi(ph);
+    wz = sp * ct;
+    const R g0 = v1x - wx, g1 = -wy, g2 = uz - wz;
+    const R gn = T::sq(g0 * g0 + g1 * g1 + g2 * g2);
+    if (T::u(b1[2]) * (un + sp) < gn) break;
+  }
+  const R v2x = wx, v2y = wy, v2z = ud + wz;
+  // centre-of-mass velocity and relative velocity
+  const R Vx = (m1 * v1x + m2 * v2x) / M, Vy = (m2 * v2y) / M, Vz = (m1 * v1z + m2 * v2z) / M;
+  const R gx = v1x - v2x, gy = -v2y, gz = v1z - v2z;
+  const R gn = T::sq(gx * gx + gy * gy + gz * gz);
+  R hx = (R)0, hy = (R)0, hz = (R)1;
+  if (gn > (R)0) { hx = gx / gn; hy = gy / gn; hz = gz / gn; }
+  // e1: the part of z perpendicular to g (x if g is along z); e2 = h x e1
+  R ax = -hz * hx, ay = -hz * hy, az = (R)1 - hz * hz;
+  R n1 = T::sq(ax * ax + ay * ay + az * az);
+  if (n1 < (R)1e-12) { ax = (R)1; ay = (R)0; az = (R)0; n1 = (R)1; }
+  ax /= n1; ay /= n1; az /= n1;
+  const R bx = hy * az - hz * ay, by = hz * ax - hx * az, bz = hx * ay - hy * ax;
+  const R cchi = (R)2 * T::u(w[2]) - (R)1;
+  const R schi = T::sq(fmax((R)0, (R)1 - cchi * cchi));
+  const R phi = (R)2 * T::u(w[3]);
+  const R cph = T::cpi(phi), sph = T::spi(phi);
+  const R f = m2 / M * gn;
+  const R nx = Vx + f * (schi * cph * ax + schi * sph * bx + cchi * hx);
+  const R ny = Vy + f * (schi * cph * ay + schi * sph * by + cchi * hy);
+  const R nz = Vz + f * (schi * cph * az + schi * sph * bz + cchi * hz);
+  const R sp2 = nx * nx + ny * ny + nz * nz;
+  const R e1 = (R)0.5 * m1 * sp2;
+  long long rq = T::quant_signed(e - e1);          // energy given to the gas (either sign)
+  if (rq > L.eq) rq = L.eq;
+  recoil += (unsigned long long)rq;
+  L.eq -= rq;
+  L.mu = sp2 > (R)0 ? (double)fmin((R)1, fmax((R)-1, nz * T::rsq(sp2))) : 1.0;
 }
 
 // Terminator of Sec. 3.2 after a collision.
@@ -571,7 +670,9 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
   const int k = P.sc[s][chs];
   o.chan = k;
   const ChanDev ch = P.ch[k];
-  if (ch.kind == ELASTIC) {
+  if (ch.kind == ELASTIC && ch.target) {
+    moving_target_elastic<F32>(P, L, w, o.recoil);
+  } else if (ch.kind == ELASTIC) {
     // isotropic in CM, target at rest: lab polar angle and energy transfer
     const R g = (R)P.gam[s];
     const R cchi = (R)2 * T::u(w[2]) - (R)1;

@@ -24,7 +24,8 @@ inline bool geometry_ok(const karl_geometry* g) {
       !g->n_seg_m3 || !(g->area_m2 > 0) || !(g->activity_bq > 0) || !(g->e_cut_ev >= 0) ||
       !(g->max_lifetime_s > 0) || !(g->gas_temperature_k >= 0) || g->n_tebins < 1 ||
       g->n_tebins > 4096 || g->n_spec_bins < 1 || g->n_spec_bins > (1 << 24) ||
-      !(g->spec_bin_ev > 0) || !(g->target_mass_ev > 0))
+      !(g->spec_bin_ev > 0) || !(g->target_mass_ev > 0) || !host_finite(g->gas_drift_mps) ||
+      !(std::fabs(g->gas_drift_mps) < 1e7))
     return false;
   for (int s = 0; s < NSP; ++s)
     if (!(g->species_mass_ev[s] > 0)) return false;
@@ -49,6 +50,8 @@ inline bool xs_ok(const karl_xs* x) {
         !(x->loss_ev[k] >= 0) || !host_finite(x->loss_ev[k]))
       return false;
     if ((kd == CLUSTERING || kd == RECOMBINATION) && so < 0) return false;
+    if (x->target && (x->target[k] < 0 || x->target[k] > 1 || (x->target[k] == 1 && kd != ELASTIC)))
+      return false;
     if (kd == RECOMBINATION && si != SP_E && so != SP_E) return false;
     if (kd == RECOMBINATION && si == SP_E && so == SP_E) return false;
     per_sp[si]++;
@@ -96,7 +99,7 @@ struct ModelInfo {
   int n_energy = 0;
   double e_min = 1, e_max = 2, eps_ion = 8;
   int nch = 0;
-  int kind[MAXCH], sin[MAXCH], sout[MAXCH];
+  int kind[MAXCH], sin[MAXCH], sout[MAXCH], target[MAXCH];
   double loss[MAXCH];
 };
 
@@ -111,6 +114,7 @@ inline ModelInfo model_info(const karl_xs* x) {
     m.kind[k] = x->kind[k];
     m.sin[k] = x->species_in[k];
     m.sout[k] = x->species_out[k];
+    m.target[k] = x->target ? x->target[k] : 0;
     m.loss[k] = x->loss_ev[k];
   }
   return m;
@@ -136,6 +140,7 @@ inline void fill_params(Params& P, const karl_geometry& g, const ModelInfo& m, i
     P.ch[k].kind = m.kind[k];
     P.ch[k].sin = m.sin[k];
     P.ch[k].sout = m.sout[k];
+    P.ch[k].target = m.target[k];
     P.ch[k].loss_q = (long long)std::floor(m.loss[k] * HOST_Q_ENERGY);
     P.ch[k].thr_q = (long long)std::floor(m.loss[k] * HOST_Q_ENERGY);
     P.ch[k].loss_ev = m.loss[k];
@@ -157,6 +162,8 @@ inline void fill_params(Params& P, const karl_geometry& g, const ModelInfo& m, i
   P.eps_ion = m.eps_ion;
   P.inv_eps_ion = 1.0 / m.eps_ion;
   P.kT = HOST_KB_EV * g.gas_temperature_k;
+  P.drift_c = g.gas_drift_mps / 299792458.0;
+  P.target_a = std::sqrt(P.kT / g.target_mass_ev);
   P.ecut_q = (long long)std::floor(g.e_cut_ev * HOST_Q_ENERGY);
   P.max_coll = g.max_collisions;
   P.max_life = g.max_lifetime_s;

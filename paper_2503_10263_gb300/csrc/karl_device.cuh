@@ -24,11 +24,11 @@ enum { L_E_IN_PRIMARY = 0, L_E_IN_THERMAL = 1, L_E_EXIT0 = 2, L_E_EXIT1 = 3, L_E
        L_E_CAP = 5, L_E_RECOMB = 6, L_E_CLUSTER = 7, L_LOSS_IONIZ = 8, L_LOSS_EXCIT = 9,
        L_LOSS_RECOIL = 10, L_E_STALLED = 11, L_BIRTHS = 12, L_DEATHS = 15, L_N_COLL = 39,
        L_N_FLIGHT = 40, L_N_SPAWN_E = 41, L_N_SPAWN_ION = 42 };
-enum { DOM_EVENT = 0, DOM_ION_BIRTH = 1, DOM_CLUSTER = 2 };
+enum { DOM_EVENT = 0, DOM_ION_BIRTH = 1, DOM_CLUSTER = 2, DOM_TARGET = 4 };
 enum { ERR_NONE = 0, ERR_TIMEOUT = 4, ERR_CAPACITY = 6, ERR_CANCELLED = 7 };
 
 struct ChanDev {
-  int32_t kind, sin, sout, pad;
+  int32_t kind, sin, sout, target;   // target: 0 at rest, 1 moving (elastic)
   long long loss_q;        // loss in 2^-24 eV units (floor)
   long long thr_q;         // channel open iff eq > thr_q  (E > loss_ev exactly)
   double loss_ev;
@@ -64,6 +64,8 @@ struct Params {
   double gam[NSP];              // m / M_target
   double inv_1pg2[NSP];         // 1 / (1 + m/M)^2
   double target_mass, eps_ion, inv_eps_ion, kT;
+  double drift_c;               // gas drift along +z in units of c (moving targets)
+  double target_a;              // sqrt(kT / target mass): thermal velocity component, units of c
   long long ecut_q;
   unsigned max_coll;
   double max_life;

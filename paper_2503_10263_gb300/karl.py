@@ -52,7 +52,8 @@ class Geometry(C.Structure):
                 ("max_collisions", C.c_uint32), ("max_lifetime_s", C.c_double),
                 ("gas_temperature_k", C.c_double), ("n_tebins", C.c_int32),
                 ("n_spec_bins", C.c_int32), ("spec_bin_ev", C.c_double),
-                ("species_mass_ev", C.c_double * 3), ("target_mass_ev", C.c_double)]
+                ("species_mass_ev", C.c_double * 3), ("target_mass_ev", C.c_double),
+                ("gas_drift_mps", C.c_double)]
 
 
 class XS(C.Structure):
@@ -60,7 +61,7 @@ class XS(C.Structure):
                 ("n_channels", C.c_int32), ("kind", C.POINTER(C.c_int32)),
                 ("species_in", C.POINTER(C.c_int32)), ("species_out", C.POINTER(C.c_int32)),
                 ("loss_ev", C.POINTER(C.c_double)), ("sigma_m2", C.POINTER(C.c_double)),
-                ("ioniz_eps_ev", C.c_double)]
+                ("ioniz_eps_ev", C.c_double), ("target", C.POINTER(C.c_int32))]
 
 
 class Primaries(C.Structure):
@@ -205,39 +206,8 @@ class Context:
     def __init__(self, prob):
         self.prob = prob
         self._keep = []
-        g = Geometry()
-        nseg = np.ascontiguousarray(prob.n_seg_m3, np.float64)
-        self._keep.append(nseg)
-        g.length_m = prob.length_m
-        g.n_zbins = prob.n_zbins
-        g.n_seg_m3 = _dptr(nseg)
-        g.area_m2 = prob.area_m2
-        g.activity_bq = prob.activity_bq
-        g.e_cut_ev = prob.e_cut_ev
-        g.max_collisions = min(int(prob.max_collisions), 0xFFFFFFFF)
-        g.max_lifetime_s = prob.max_lifetime_s if math.isfinite(prob.max_lifetime_s) else math.inf
-        g.gas_temperature_k = prob.gas_temperature_k
-        g.n_tebins = prob.n_tebins
-        g.n_spec_bins = prob.n_spec_bins
-        g.spec_bin_ev = prob.spec_bin_ev
-        for i in range(3):
-            g.species_mass_ev[i] = float(prob.species_mass_ev[i])
-        g.target_mass_ev = prob.target_mass_ev
-        x = XS()
-        kind = np.array([c.kind for c in prob.channels], np.int32)
-        sin = np.array([c.species_in for c in prob.channels], np.int32)
-        sout = np.array([c.species_out for c in prob.channels], np.int32)
-        loss = np.array([c.loss_ev for c in prob.channels], np.float64)
-        sig = np.ascontiguousarray(prob.sigma_matrix() if prob.channels
-                                   else np.zeros((0, prob.n_energy)), np.float64)
-        self._keep += [kind, sin, sout, loss, sig]
-        x.n_energy = prob.n_energy
-        x.e_min_ev = prob.e_min_ev
-        x.e_max_ev = prob.e_max_ev
-        x.n_channels = prob.n_channels
-        x.kind, x.species_in, x.species_out = _iptr(kind), _iptr(sin), _iptr(sout)
-        x.loss_ev, x.sigma_m2 = _dptr(loss), _dptr(sig)
-        x.ioniz_eps_ev = prob.ioniz_eps_ev
+        g = _geometry(prob, self._keep)
+        x = _xs(prob, self._keep)
         self.ctx = karl_create(g, x)
         self.layout = karl_tally_layout(self.ctx)
 
@@ -432,6 +402,7 @@ def _geometry(prob, keep):
     for i in range(3):
         g.species_mass_ev[i] = float(prob.species_mass_ev[i])
     g.target_mass_ev = prob.target_mass_ev
+    g.gas_drift_mps = float(getattr(prob, "gas_drift_mps", 0.0))
     return g
 
 
@@ -441,9 +412,10 @@ def _xs(prob, keep):
     sin = np.array([c.species_in for c in prob.channels], np.int32)
     sout = np.array([c.species_out for c in prob.channels], np.int32)
     loss = np.array([c.loss_ev for c in prob.channels], np.float64)
+    target = np.array([getattr(c, "target", 0) for c in prob.channels], np.int32)
     sig = np.ascontiguousarray(prob.sigma_matrix() if prob.channels
                                else np.zeros((0, prob.n_energy)), np.float64)
-    keep += [kind, sin, sout, loss, sig]
+    keep += [kind, sin, sout, loss, target, sig]
     x.n_energy = prob.n_energy
     x.e_min_ev = prob.e_min_ev
     x.e_max_ev = prob.e_max_ev
@@ -451,6 +423,7 @@ def _xs(prob, keep):
     x.kind, x.species_in, x.species_out = _iptr(kind), _iptr(sin), _iptr(sout)
     x.loss_ev, x.sigma_m2 = _dptr(loss), _dptr(sig)
     x.ioniz_eps_ev = prob.ioniz_eps_ev
+    x.target = _iptr(target)
     return x
 
 

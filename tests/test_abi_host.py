@@ -67,6 +67,17 @@ def test_create_rejects_invalid_arguments_without_gpu(karl):
     p.channels[1].species_in = 7
     with pytest.raises(karl.KarlError):
         karl.Context(p)
+    # a moving target is defined for elastic channels only
+    for k, t in ((1, 1), (0, 2)):
+        p, _ = inputs.config1(n_primaries=10)
+        p.channels[k].target = t
+        with pytest.raises(karl.KarlError) as ei:
+            karl.Context(p)
+        assert ei.value.status == karl.EINVAL
+    p, _ = inputs.thermalization(n_primaries=10)
+    p.gas_drift_mps = math.inf
+    with pytest.raises(karl.KarlError):
+        karl.Context(p)
 
 
 def test_missing_library_fails_loudly(monkeypatch):
