@@ -61,7 +61,10 @@ class _Problem(C.Structure):
         ("species_in", C.POINTER(C.c_int32)), ("species_out", C.POINTER(C.c_int32)),
         ("loss_ev", C.POINTER(C.c_double)), ("sigma_m2", C.POINTER(C.c_double)),
         ("ioniz_eps_ev", C.c_double), ("target", C.POINTER(C.c_int32)),
-        ("gas_drift_mps", C.c_double),
+        ("gas_drift_mps", C.c_double), ("ang_set", C.POINTER(C.c_int32)),
+        ("ang_n_sets", C.c_int32), ("ang_n_bins", C.c_int32), ("ang_n_mu", C.c_int32),
+        ("ang_e_min_ev", C.POINTER(C.c_double)), ("ang_e_max_ev", C.POINTER(C.c_double)),
+        ("ang_threshold_ev", C.POINTER(C.c_double)), ("ang_pdf", C.POINTER(C.c_double)),
     ]
 
 
@@ -103,6 +106,8 @@ def _load():
             C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_double),
             C.POINTER(C.c_double), C.POINTER(C.c_double)]
         lib.orc_elastic_moving_target.restype = None
+        lib.orc_sample_angle.argtypes = [C.POINTER(_Problem), C.c_int, C.c_double, C.c_double]
+        lib.orc_sample_angle.restype = C.c_double
         _lib = lib
     return _lib
 
@@ -152,7 +157,46 @@ class _Marshal:
         s.ioniz_eps_ev = prob.ioniz_eps_ev
         s.target = _ptr(self.target, C.c_int32)
         s.gas_drift_mps = float(getattr(prob, "gas_drift_mps", 0.0))
+        self.ang = angular_sets(prob)
+        if self.ang is not None:
+            a = self.ang
+            s.ang_set = _ptr(a["set"], C.c_int32)
+            s.ang_n_sets, s.ang_n_bins, s.ang_n_mu = a["n_sets"], a["n_bins"], a["n_mu"]
+            s.ang_e_min_ev = _ptr(a["e_min"], C.c_double)
+            s.ang_e_max_ev = _ptr(a["e_max"], C.c_double)
+            s.ang_threshold_ev = _ptr(a["threshold"], C.c_double)
+            s.ang_pdf = _ptr(a["pdf"], C.c_double)
         self.s = s
+
+
+def angular_sets(prob):
+    """The problem's angle tables as flat arrays (None when every elastic
+    channel is isotropic).  All sets must share their bin and point counts."""
+    tabs = [getattr(c, "angular", None) for c in prob.channels]
+    used = [t for t in tabs if t is not None]
+    if not used:
+        return None
+    nb, nm = used[0].pdf.shape
+    order = {}
+    for t in used:
+        if t.pdf.shape != (nb, nm):
+            raise ValueError("angle tables must share their bins and points")
+        order.setdefault(id(t), len(order))
+    sets = sorted({id(t): t for t in used}.items(), key=lambda kv: order[kv[0]])
+    return {
+        "set": np.array([order[id(t)] if t is not None else -1 for t in tabs], np.int32),
+        "n_sets": len(sets), "n_bins": nb, "n_mu": nm,
+        "e_min": np.array([t.e_min_ev for _, t in sets], np.float64),
+        "e_max": np.array([t.e_max_ev for _, t in sets], np.float64),
+        "threshold": np.array([t.threshold_ev for _, t in sets], np.float64),
+        "pdf": np.ascontiguousarray(np.stack([t.pdf for _, t in sets]), np.float64),
+    }
+
+
+def sample_angle(prob, channel: int, e_ev: float, u: float) -> float:
+    lib = _load()
+    m = _Marshal(prob)
+    return float(lib.orc_sample_angle(C.byref(m.s), channel, e_ev, u))
 
 
 def _prims(pr, pid_offset: int = 0, n_decays: Optional[int] = None):

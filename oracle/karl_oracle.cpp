@@ -19,7 +19,12 @@
  *  - sigma(E): linear interpolation in ln E on the input nodes, zero for
  *    E <= loss of the channel, clamped to the end nodes outside the grid;
  *  - lab kinetic energy with the target at rest; relativistic speed;
- *  - elastic: isotropic in the centre-of-mass frame; for a channel marked as
+ *  - elastic: isotropic in the centre-of-mass frame unless the channel has a
+ *    scattering-angle table (Sec. 3.3 Elastic: the table's energy bin is
+ *    chosen and cos chi drawn from its piecewise-linear pdf by inverting the
+ *    cumulative integral; isotropic below the table's threshold energy, the
+ *    composition the paper uses for electrons); the angle is the centre-of-
+ *    mass polar angle, at the impact energy; for a channel marked as
  *    having a moving target (Sec. 3.3 Elastic: gas drift plus a Maxwell-
  *    Boltzmann velocity), nonrelativistic velocities, the impactor's gyrophase
  *    taken as 0 (the target distribution is symmetric about z), the relative
@@ -105,6 +110,37 @@ int64_t quant_e(double e_ev) { return (int64_t)std::floor(e_ev * Q_ENERGY); }
 /* an energy transfer, rounded to the nearest 2^-24 eV unit */
 int64_t quant_recoil(double de_ev) { return (int64_t)std::floor(de_ev * Q_ENERGY + 0.5); }
 
+/* cos(chi) of an elastic collision (Sec. 3.3 Elastic): isotropic (2u - 1)
+ * without a table or below the table's threshold energy; otherwise the
+ * impact-energy bin of the set is chosen (log-spaced bins, clamped at both
+ * ends) and cos chi drawn from its piecewise-linear pdf p on the nodes
+ * x_i = -1 + i h: with the cumulative integral C(x), find the interval
+ * [x_i, x_i+1] holding t = u C(1) and solve C(x_i) + p_i s + (p_i+1 - p_i)
+ * s^2 / 2h = t for s in [0, h]. */
+double sample_angle(const orc_problem* p, int ch, double e_imp, double u) {
+  const int set = p->ang_set ? p->ang_set[ch] : -1;
+  if (set < 0 || !(e_imp >= p->ang_threshold_ev[set])) return 2.0 * u - 1.0;
+  const int nb = p->ang_n_bins, n = p->ang_n_mu;
+  const double lo = p->ang_e_min_ev[set], hi = p->ang_e_max_ev[set];
+  int b = (int)std::floor(std::log(e_imp / lo) / std::log(hi / lo) * nb);
+  if (b < 0) b = 0;
+  if (b > nb - 1) b = nb - 1;
+  const double* pdf = p->ang_pdf + ((size_t)set * nb + b) * n;
+  const double h = 2.0 / (double)(n - 1);
+  std::vector<double> cum(n, 0.0);
+  for (int i = 0; i + 1 < n; ++i) cum[i + 1] = cum[i] + 0.5 * h * (pdf[i] + pdf[i + 1]);
+  const double t = u * cum[n - 1];
+  int i = 0;
+  while (i < n - 2 && cum[i + 1] <= t) ++i;
+  const double r = t - cum[i];
+  const double a = pdf[i], slope = (pdf[i + 1] - pdf[i]) / h;
+  const double disc = std::fmax(0.0, a * a + 2.0 * slope * r);
+  const double den = a + std::sqrt(disc);
+  double sv = den > 0.0 ? 2.0 * r / den : 0.0;
+  sv = std::fmin(std::fmax(sv, 0.0), h);
+  return std::fmin(1.0, -1.0 + (double)i * h + sv);
+}
+
 /* The block of target-velocity draws number k of one collision (two per
  * attempt of the rejection below). */
 typedef void (*TargetBlock)(void* ctx, uint64_t k, uint64_t w[4]);
@@ -166,7 +202,7 @@ void target_velocity(const orc_problem* p, const double v1[3], TargetBlock blk, 
  * plane of z and g; the impactor leaves with V + m2/(m1+m2) g'.  Velocities in
  * units of c.  v (optional, 12 values): impactor and target before, impactor
  * and target after. */
-void moving_target_elastic(const orc_problem* p, double m1, double e, double mu,
+void moving_target_elastic(const orc_problem* p, int ch, double m1, double e, double mu,
                            const uint64_t w[4], TargetBlock blk, void* ctx, double* e_out,
                            double* mu_out, double* v) {
   const double m2 = p->target_mass_ev;
@@ -194,7 +230,8 @@ void moving_target_elastic(const orc_problem* p, double m1, double e, double mu,
   for (int i = 0; i < 3; ++i) e1[i] /= n1;
   const double e2[3] = {gh[1] * e1[2] - gh[2] * e1[1], gh[2] * e1[0] - gh[0] * e1[2],
                         gh[0] * e1[1] - gh[1] * e1[0]};
-  const double cchi = 2.0 * u01(w[2]) - 1.0;
+  /* impact energy: the impactor's kinetic energy relative to the target */
+  const double cchi = sample_angle(p, ch, 0.5 * m1 * gn * gn, u01(w[2]));
   const double schi = std::sqrt(std::fmax(0.0, 1.0 - cchi * cchi));
   const double phi = TWO_PI * u01(w[3]);
   const double cph = std::cos(phi), sph = std::sin(phi);
@@ -539,7 +576,7 @@ struct Worker {
           q->self->block(q->ev, q->node, DOM_TARGET, k, out);
         };
         double e1, mu1;
-        moving_target_elastic(p, m, e, P.mu, w, blk, &cx, &e1, &mu1, nullptr);
+        moving_target_elastic(p, ch, m, e, P.mu, w, blk, &cx, &e1, &mu1, nullptr);
         /* energy given to the gas (negative when the gas heats the impactor) */
         int64_t rq = quant_recoil(e - e1);
         if (rq > P.eq) rq = P.eq;
@@ -547,9 +584,10 @@ struct Worker {
         P.eq -= rq;
         P.mu = mu1;
       } else if (kind == ELASTIC) {
-        /* isotropic in CM; lab energy and polar angle for a target at rest */
+        /* CM polar angle (isotropic or tabulated); lab energy and polar angle
+           for a target at rest, whose impact energy is the lab energy */
         double g = m / p->target_mass_ev;
-        double cchi = 2.0 * u01(w[2]) - 1.0;
+        double cchi = sample_angle(p, ch, e, u01(w[2]));
         double a = 1.0 + 2.0 * g * cchi + g * g;
         double ct = (cchi + g) / std::sqrt(a);
         /* energy given to the target, E - E' = E 2g(1 - cos chi)/(1+g)^2 */
@@ -743,6 +781,10 @@ void orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4
 
 double orc_sigma(const orc_problem* p, int channel, double e_ev) { return sigma_at(p, channel, e_ev); }
 
+double orc_sample_angle(const orc_problem* p, int channel, double e_ev, double u) {
+  return sample_angle(p, channel, e_ev, u);
+}
+
 void orc_elastic_moving_target(const orc_problem* p, double m1_ev, double e_ev, double mu,
                                const uint64_t w[4], const uint64_t ctr[3], const uint64_t key[2],
                                double* out_e, double* out_mu, double* v) {
@@ -752,7 +794,10 @@ void orc_elastic_moving_target(const orc_problem* p, double m1_ev, double e_ev, 
     const uint64_t full[4] = {q->ctr[0], q->ctr[1], q->ctr[2], k};
     philox4x64_10(full, q->key, out);
   };
-  moving_target_elastic(p, m1_ev, e_ev, mu, w, blk, &cx, out_e, out_mu, v);
+  int ch = 0;
+  for (int k = 0; k < p->n_channels; ++k)
+    if (p->kind[k] == ELASTIC) { ch = k; break; }
+  moving_target_elastic(p, ch, m1_ev, e_ev, mu, w, blk, &cx, out_e, out_mu, v);
 }
 
 int orc_collide(const orc_problem* p, int ch, int species, double e_ev, double mu,
@@ -764,7 +809,7 @@ int orc_collide(const orc_problem* p, int ch, int species, double e_ev, double m
   int kind = p->kind[ch];
   if (kind == ELASTIC) {
     double g = m / p->target_mass_ev;
-    double cchi = 2.0 * u01(w[2]) - 1.0;
+    double cchi = sample_angle(p, ch, e, u01(w[2]));
     double a = 1.0 + 2.0 * g * cchi + g * g;
     double ct = (cchi + g) / std::sqrt(a);
     int64_t rq = quant_recoil(e * 2.0 * g * (1.0 - cchi) / ((1.0 + g) * (1.0 + g)));

@@ -60,6 +60,19 @@ typedef struct {
      NULL: every target at rest */
   const int32_t* target;
   double gas_drift_mps;        /* drift velocity of the gas along +z */
+  /* scattering-angle distributions of elastic channels (Sec. 3.3 Elastic):
+     ang_set[k] = -1 (or ang_set NULL): isotropic in the centre-of-mass frame;
+     otherwise the set used by channel k.  A set is a pdf of cos(chi) on
+     ang_n_mu points evenly spaced over [-1, 1] (piecewise linear between
+     them) for each of ang_n_bins log-spaced impact-energy bins over
+     [ang_e_min_ev[s], ang_e_max_ev[s]]; below ang_threshold_ev[s] scattering
+     is isotropic. */
+  const int32_t* ang_set;
+  int32_t ang_n_sets, ang_n_bins, ang_n_mu;
+  const double* ang_e_min_ev;
+  const double* ang_e_max_ev;
+  const double* ang_threshold_ev;
+  const double* ang_pdf;       /* [sets][bins][n_mu] */
 } orc_problem;
 
 typedef struct {
@@ -118,6 +131,10 @@ int orc_collide(const orc_problem* p, int channel, int species, double e_ev, dou
 void orc_elastic_moving_target(const orc_problem* p, double m1_ev, double e_ev, double mu,
                                const uint64_t w[4], const uint64_t ctr[3], const uint64_t key[2],
                                double* out_e, double* out_mu, double* v);
+
+/* cos(chi) of an elastic collision of channel `channel` at impact energy
+ * e_ev for the uniform number u in [0, 1) (isotropic: 2u - 1). */
+double orc_sample_angle(const orc_problem* p, int channel, double e_ev, double u);
 
 #ifdef __cplusplus
 }

@@ -56,6 +56,18 @@ KIND_NAMES = ("elastic", "ionization", "excitation", "clustering", "recombinatio
 
 
 @dataclasses.dataclass
+class AngularTable:
+    """Scattering-angle distribution of an elastic channel (Sec. 3.3
+    Elastic): pdf values of cos(chi) on n_mu points evenly spaced over
+    [-1, 1], one row per log-spaced impact-energy bin over [e_min, e_max];
+    below threshold_ev the scattering is isotropic (a composition)."""
+    e_min_ev: float
+    e_max_ev: float
+    pdf: np.ndarray                # [n_bins][n_mu]
+    threshold_ev: float = 0.0
+
+
+@dataclasses.dataclass
 class Channel:
     name: str
     kind: int
@@ -65,6 +77,7 @@ class Channel:
     loss_ev: float
     sigma_m2: np.ndarray  # [n_energy] values at the table nodes
     target: int = 0       # 0 target at rest; 1 moving (thermal + gas drift), elastic only
+    angular: Optional[AngularTable] = None   # elastic only; None = isotropic
 
 
 @dataclasses.dataclass
@@ -282,6 +295,31 @@ def _problem(name: str, length: float, nz: int, n_seg: np.ndarray, full: bool,
         n_spec_bins=20000, spec_bin_ev=1.0, species_mass_ev=SPECIES_MASS_EV.copy(),
         target_mass_ev=M_T2_EV, n_energy=n_energy, e_min_ev=1.0, e_max_ev=2.0e4,
         ioniz_eps_ev=8.0, channels=chans, n_passes=2 if full else 1)
+
+
+def screened_rutherford_table(e_min_ev: float = 100.0, e_max_ev: float = 2.0e4,
+                              n_bins: int = 48, n_mu: int = 201, eta0_ev: float = 3.4,
+                              threshold_ev: float = 100.0) -> AngularTable:
+    """Synthetic stand-in for the paper's high-energy tables (its Elsepa data
+    is not available): the screened Rutherford (Wentzel) form
+    p(cos chi) ~ 1 / (1 + 2 eta - cos chi)^2 with eta = eta0 / E at each bin's
+    geometric-mean energy, tabulated on n_mu points; isotropic below
+    threshold_ev, as the paper composes them for electrons."""
+    edges = np.geomspace(e_min_ev, e_max_ev, n_bins + 1)
+    mid = np.sqrt(edges[:-1] * edges[1:])
+    mu = np.linspace(-1.0, 1.0, n_mu)
+    eta = eta0_ev / mid
+    pdf = 1.0 / (1.0 + 2.0 * eta[:, None] - mu[None, :]) ** 2
+    return AngularTable(e_min_ev, e_max_ev, np.ascontiguousarray(pdf), threshold_ev)
+
+
+def angular_config(n_primaries: int = 2000, seed: int = 1):
+    """Config-1 geometry and channels with the elastic channel's angles from a
+    screened-Rutherford table above 100 eV (isotropic below)."""
+    prob, prims = config1(n_primaries, seed)
+    prob.name = "config1_angular"
+    prob.channels[0].angular = screened_rutherford_table()
+    return prob, prims
 
 
 def thermalization(n_primaries: int = 4000, seed: int = 1, density_m3: float = 1e22,
