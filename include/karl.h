@@ -102,6 +102,30 @@ typedef struct karl_geometry {
   double gas_drift_mps;        /* drift velocity of the gas along +z (moving targets) */
 } karl_geometry;
 
+/* Scattering-angle distributions of elastic channels (copied at create).
+ * Sec. 3.3 (Elastic): the centre-of-mass polar angle chi is isotropic, drawn
+ * from a tabulated distribution, or from a composition of the two that is
+ * isotropic below a threshold energy.  A set s holds, for each of n_bins
+ * impact-energy bins log-spaced over [e_min_ev[s], e_max_ev[s]] (bin
+ * floor(n_bins ln(E/e_min)/ln(e_max/e_min)), clamped to the first and last),
+ * the pdf of cos chi at n_mu points evenly spaced over [-1, 1]; between the
+ * points the pdf is linear, and cos chi is drawn by inverting its cumulative
+ * integral.  Below threshold_ev[s] the angle is isotropic.  The impact energy
+ * is the lab energy for a target at rest and the relative kinetic energy of
+ * the impactor for a moving target.
+ * Errors (KARL_EINVAL at create): n_sets outside 1 .. KARL_MAX_CHANNELS,
+ * n_bins < 1, n_mu < 2 or > 4096, a set index outside [-1, n_sets), a set on a
+ * channel that is not elastic, e_min <= 0 or e_max <= e_min, a negative or
+ * non-finite threshold or pdf value, or a bin whose pdf integrates to zero. */
+typedef struct karl_angular {
+  int32_t n_sets, n_bins, n_mu;
+  const int32_t* set;          /* host, [n_channels]: -1 isotropic, else the set index */
+  const double* e_min_ev;      /* host, [n_sets] */
+  const double* e_max_ev;      /* host, [n_sets] */
+  const double* threshold_ev;  /* host, [n_sets] */
+  const double* pdf;           /* host, [n_sets][n_bins][n_mu], >= 0 (need not be normalised) */
+} karl_angular;
+
 /* Cross-section tables (copied at create).  sigma of channel k at energy E is
  * linear in ln E between the log-spaced nodes e_min * (e_max/e_min)^(i/(n-1)),
  * clamped outside, and zero for E <= loss_ev[k] (Sec. 3.3: the cross section
@@ -122,6 +146,8 @@ typedef struct karl_xs {
    * rate; the impactor turned in the centre-of-mass frame).  1 is allowed for
    * elastic channels only. */
   const int32_t* target;
+  /* host or NULL (every elastic channel isotropic in the centre-of-mass frame) */
+  const karl_angular* angular;
 } karl_xs;
 
 /* Primary particles (one beta electron and, with ions, one T2+ per decay,

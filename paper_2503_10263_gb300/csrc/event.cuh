@@ -34,6 +34,8 @@ template <> struct RT<false> {
   static __device__ __forceinline__ R tab(const Params& P, int k, int i) {
     return __ldg(P.sig + (size_t)i * P.nch + k);      // [node][channel]
   }
+  static __device__ __forceinline__ R angp(const Params& P, size_t i) { return __ldg(P.ang_pdf + i); }
+  static __device__ __forceinline__ R angc(const Params& P, size_t i) { return __ldg(P.ang_cum + i); }
   static __device__ __forceinline__ R energy(long long eq) { return (double)eq * (1.0 / 16777216.0); }
   static __device__ __forceinline__ long long quant_de(R de) {
     return (long long)floor(de * 16777216.0 + 0.5);
@@ -57,6 +59,8 @@ template <> struct RT<true> {
   static __device__ __forceinline__ R tab(const Params& P, int k, int i) {
     return __ldg(P.sigf + (size_t)i * P.nch + k);     // [node][channel]
   }
+  static __device__ __forceinline__ R angp(const Params& P, size_t i) { return __ldg(P.ang_pdff + i); }
+  static __device__ __forceinline__ R angc(const Params& P, size_t i) { return __ldg(P.ang_cumf + i); }
   // energy from 2^-24 eV units with 32-bit conversions (below 65 keV; exact
   // to FP32 rounding below 256 eV, where thermal energies live)
   static __device__ __forceinline__ R energy(long long eq) {
@@ -263,6 +267,53 @@ __device__ __forceinline__ void thermal(const Params& P, const unsigned long lon
   mu = 2.0 * u01d(w[3]) - 1.0;
 }
 
+// cos(chi) of an elastic collision from the angle table `set` at impact
+// energy e (Sec. 3.3 Elastic: the energy bin of the table is chosen and the
+// angle drawn from its piecewise-linear distribution).  The bin is the
+// log-spaced one holding e, clamped to the first and last.  With the pdf p_i
+// at x_i = -1 + i h and its cumulative integral C_i, t = u C_(n-1) falls in
+// the interval [x_i, x_i+1] of the largest i with C_i <= t (binary search),
+// and cos chi = x_i + s with s in [0, h] the root of
+// C_i + p_i s + (p_i+1 - p_i) s^2 / (2h) = t, taken in the form
+// s = 2r / (p_i + sqrt(p_i^2 + 2 r (p_i+1 - p_i) / h)), r = t - C_i, which
+// stays accurate when the pdf is flat.
+template <bool F32>
+__device__ __noinline__ typename RT<F32>::R table_cchi(const Params& P, int set,
+                                                       typename RT<F32>::R e,
+                                                       typename RT<F32>::R u) {
+  using T = RT<F32>;
+  using R = typename T::R;
+  const int nb = P.ang_nb, n = P.ang_nmu;
+  int b = (int)floor(T::lg(e * (R)P.ang_inv_lo[set]) * (R)P.ang_scale[set]);
+  b = b < 0 ? 0 : (b > nb - 1 ? nb - 1 : b);
+  const size_t row = ((size_t)set * nb + b) * n;
+  const R t = u * T::angc(P, row + n - 1);
+  int lo = 0, hi = n - 1;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (T::angc(P, row + mid) <= t) lo = mid; else hi = mid;
+  }
+  const R h = (R)P.ang_h;
+  const R r = t - T::angc(P, row + lo);
+  const R a = T::angp(P, row + lo);
+  const R slope = (T::angp(P, row + lo + 1) - a) * (R)P.ang_inv_h;
+  const R den = a + T::sq(fmax((R)0, a * a + (R)2 * slope * r));
+  R sv = den > (R)0 ? (R)2 * r / den : (R)0;
+  sv = fmin(fmax(sv, (R)0), h);
+  return fmin((R)1, (R)-1 + (R)lo * h + sv);
+}
+
+// cos(chi) of an elastic collision of channel ch at impact energy e for the
+// uniform u: isotropic (2u - 1) without a table or below its threshold.
+template <bool F32>
+__device__ __forceinline__ typename RT<F32>::R elastic_cchi(const Params& P, const ChanDev& ch,
+                                                            typename RT<F32>::R e,
+                                                            typename RT<F32>::R u) {
+  using R = typename RT<F32>::R;
+  if (ch.ang >= 0 && e >= (R)P.ang_thr[ch.ang]) return table_cchi<F32>(P, ch.ang, e, u);
+  return (R)2 * u - (R)1;
+}
+
 // Elastic collision with a moving target (Sec. 3.3 Elastic: the target moves
 // with the gas drift plus a Maxwell-Boltzmann velocity; the impactor turns in
 // the centre-of-mass frame).  Nonrelativistic velocities in units of c; the
@@ -278,7 +329,7 @@ __device__ __forceinline__ void thermal(const Params& P, const unsigned long lon
 // uniform, w[2]) and azimuth (w[3], from the plane of z and the relative
 // velocity) turn the relative velocity.
 template <bool F32>
-__device__ __noinline__ void moving_target_elastic(const Params& P, Lane& L,
+__device__ __noinline__ void moving_target_elastic(const Params& P, const ChanDev& ch, Lane& L,
                                                    const unsigned long long w[4],
                                                    unsigned long long& recoil) {
   using T = RT<F32>;
@@ -334,7 +385,8 @@ __device__ __noinline__ void moving_target_elastic(const Params& P, Lane& L,
   if (n1 < (R)1e-12) { ax = (R)1; ay = (R)0; az = (R)0; n1 = (R)1; }
   ax /= n1; ay /= n1; az /= n1;
   const R bx = hy * az - hz * ay, by = hz * ax - hx * az, bz = hx * ay - hy * ax;
-  const R cchi = (R)2 * T::u(w[2]) - (R)1;
+  // impact energy: the impactor's kinetic energy relative to the target
+  const R cchi = elastic_cchi<F32>(P, ch, (R)0.5 * m1 * gn * gn, T::u(w[2]));
   const R schi = T::sq(fmax((R)0, (R)1 - cchi * cchi));
   const R phi = (R)2 * T::u(w[3]);
   const R cph = T::cpi(phi), sph = T::spi(phi);
@@ -671,11 +723,12 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
   o.chan = k;
   const ChanDev ch = P.ch[k];
   if (ch.kind == ELASTIC && ch.target) {
-    moving_target_elastic<F32>(P, L, w, o.recoil);
+    moving_target_elastic<F32>(P, ch, L, w, o.recoil);
   } else if (ch.kind == ELASTIC) {
-    // isotropic in CM, target at rest: lab polar angle and energy transfer
+    // CM polar angle (isotropic or tabulated at the lab energy, which is the
+    // impact energy for a target at rest): lab polar angle and energy transfer
     const R g = (R)P.gam[s];
-    const R cchi = (R)2 * T::u(w[2]) - (R)1;
+    const R cchi = elastic_cchi<F32>(P, ch, e, T::u(w[2]));
     const R a = (R)1 + (R)2 * g * cchi + g * g;
     const R ct = (cchi + g) * T::rsq(a);
     // energy given to the target, E - E' = E 2g(1 - cos chi)/(1+g)^2

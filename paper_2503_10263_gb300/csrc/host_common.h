@@ -34,6 +34,38 @@ inline bool geometry_ok(const karl_geometry* g) {
   return true;
 }
 
+// Checks of the scattering-angle tables (no CUDA call): sets only on elastic
+// channels, ordered energy ranges, non-negative pdfs with a positive integral
+// in every bin.
+inline bool angular_ok(const karl_xs* x) {
+  const karl_angular* a = x->angular;
+  if (!a) return true;
+  if (a->n_sets < 1 || a->n_sets > KARL_MAX_CHANNELS || a->n_bins < 1 || a->n_bins > (1 << 16) ||
+      a->n_mu < 2 || a->n_mu > 4096 || !a->set || !a->e_min_ev || !a->e_max_ev ||
+      !a->threshold_ev || !a->pdf)
+    return false;
+  for (int k = 0; k < x->n_channels; ++k) {
+    const int s = a->set[k];
+    if (s < -1 || s >= a->n_sets || (s >= 0 && x->kind[k] != ELASTIC)) return false;
+  }
+  for (int s = 0; s < a->n_sets; ++s) {
+    if (!(a->e_min_ev[s] > 0) || !(a->e_max_ev[s] > a->e_min_ev[s]) ||
+        !host_finite(a->e_max_ev[s]) || !(a->threshold_ev[s] >= 0) ||
+        !host_finite(a->threshold_ev[s]))
+      return false;
+    for (int b = 0; b < a->n_bins; ++b) {
+      const double* p = a->pdf + ((size_t)s * a->n_bins + b) * a->n_mu;
+      double sum = 0.0;
+      for (int i = 0; i < a->n_mu; ++i) {
+        if (!(p[i] >= 0) || !host_finite(p[i])) return false;
+        sum += p[i];
+      }
+      if (!(sum > 0) || !host_finite(sum)) return false;
+    }
+  }
+  return true;
+}
+
 // Cross-section checks of karl_create (no CUDA call).
 inline bool xs_ok(const karl_xs* x) {
   if (!x) return false;
@@ -63,7 +95,7 @@ inline bool xs_ok(const karl_xs* x) {
   }
   for (int s = 0; s < NSP; ++s)
     if (per_sp[s] > MAXSPCH || rec_sp[s] > 2) return false;
-  return true;
+  return angular_ok(x);
 }
 
 // Gas column to each face, face positions (the last face is L exactly), and
@@ -101,6 +133,11 @@ struct ModelInfo {
   int nch = 0;
   int kind[MAXCH], sin[MAXCH], sout[MAXCH], target[MAXCH];
   double loss[MAXCH];
+  // scattering-angle tables: set of each channel (-1 isotropic) and the sets'
+  // energy ranges; the pdf values go to the device separately
+  int ang[MAXCH];
+  int ang_sets = 0, ang_nb = 0, ang_nmu = 0;
+  double ang_lo[MAXCH], ang_hi[MAXCH], ang_thr[MAXCH];
 };
 
 inline ModelInfo model_info(const karl_xs* x) {
@@ -116,8 +153,41 @@ inline ModelInfo model_info(const karl_xs* x) {
     m.sout[k] = x->species_out[k];
     m.target[k] = x->target ? x->target[k] : 0;
     m.loss[k] = x->loss_ev[k];
+    m.ang[k] = x->angular ? x->angular->set[k] : -1;
+  }
+  if (const karl_angular* a = x->angular) {
+    m.ang_sets = a->n_sets;
+    m.ang_nb = a->n_bins;
+    m.ang_nmu = a->n_mu;
+    for (int s = 0; s < a->n_sets; ++s) {
+      m.ang_lo[s] = a->e_min_ev[s];
+      m.ang_hi[s] = a->e_max_ev[s];
+      m.ang_thr[s] = a->threshold_ev[s];
+    }
   }
   return m;
+}
+
+// Device copies of the angle tables: the pdf rows and their cumulative
+// integrals C(x_0) = 0, C(x_i+1) = C(x_i) + h (p_i + p_i+1) / 2 (exact for a
+// pdf linear between the points), in FP64 and FP32.  Empty without tables.
+inline void angular_tables(const karl_xs* x, std::vector<double>& pdf, std::vector<double>& cum,
+                           std::vector<float>& pdff, std::vector<float>& cumf) {
+  pdf.clear(); cum.clear(); pdff.clear(); cumf.clear();
+  const karl_angular* a = x->angular;
+  if (!a) return;
+  const int n = a->n_mu;
+  const size_t rows = (size_t)a->n_sets * a->n_bins;
+  const double h = 2.0 / (double)(n - 1);
+  pdf.assign(a->pdf, a->pdf + rows * n);
+  cum.assign(rows * n, 0.0);
+  for (size_t r = 0; r < rows; ++r) {
+    const double* p = pdf.data() + r * n;
+    double* c = cum.data() + r * n;
+    for (int i = 0; i + 1 < n; ++i) c[i + 1] = c[i] + 0.5 * h * (p[i] + p[i + 1]);
+  }
+  pdff.assign(pdf.begin(), pdf.end());
+  cumf.assign(cum.begin(), cum.end());
 }
 
 // Everything of Params that does not depend on device buffers.
@@ -144,6 +214,18 @@ inline void fill_params(Params& P, const karl_geometry& g, const ModelInfo& m, i
     P.ch[k].loss_q = (long long)std::floor(m.loss[k] * HOST_Q_ENERGY);
     P.ch[k].thr_q = (long long)std::floor(m.loss[k] * HOST_Q_ENERGY);
     P.ch[k].loss_ev = m.loss[k];
+    P.ch[k].ang = m.ang[k];
+  }
+  if (m.ang_sets > 0) {
+    P.ang_nb = m.ang_nb;
+    P.ang_nmu = m.ang_nmu;
+    P.ang_h = 2.0 / (double)(m.ang_nmu - 1);
+    P.ang_inv_h = 0.5 * (double)(m.ang_nmu - 1);
+    for (int s = 0; s < m.ang_sets; ++s) {
+      P.ang_inv_lo[s] = 1.0 / m.ang_lo[s];
+      P.ang_scale[s] = (double)m.ang_nb / std::log(m.ang_hi[s] / m.ang_lo[s]);
+      P.ang_thr[s] = m.ang_thr[s];
+    }
   }
   for (int s = 0; s < NSP; ++s) {
     int n = 0;

@@ -83,6 +83,8 @@ struct karl_ctx {
   int nq = 0;
   double colmax = 0;
   DevBuf<float> d_sigf;
+  DevBuf<double> d_ang_pdf, d_ang_cum;       // scattering-angle tables (empty: isotropic)
+  DevBuf<float> d_ang_pdff, d_ang_cumf;
   cudaStream_t cancel_stream = nullptr;
   // device work buffers
   DevBuf<double> d_pz, d_pe, d_pmu;
@@ -343,6 +345,12 @@ void base_params(const karl_ctx* c, Params& P, const karl_run_opts* o, int pass)
   P.ginv = c->nq > 0 ? c->d_ginv.p : nullptr;
   P.sig = c->d_sig_t.p;
   P.sigf = c->d_sigf.p;
+  if (c->model.ang_sets > 0) {
+    P.ang_pdf = c->d_ang_pdf.p;
+    P.ang_cum = c->d_ang_cum.p;
+    P.ang_pdff = c->d_ang_pdff.p;
+    P.ang_cumf = c->d_ang_cumf.p;
+  }
 }
 
 // One pass into the context's raw tally buffers (which are zeroed first).
@@ -608,6 +616,26 @@ karl_status karl_create(const karl_geometry* g, const karl_xs* x, karl_ctx** out
         cudaMemcpy(ctx->d_sig_t.p, sig_t.data(), sig_t.size() * 8, cudaMemcpyHostToDevice) ||
         cudaMemcpy(ctx->d_sigf.p, sigf.data(), sigf.size() * 4, cudaMemcpyHostToDevice))))
     return bail(KARL_ECUDA);
+  {
+    std::vector<double> apdf, acum;
+    std::vector<float> apdff, acumf;
+    try {
+      angular_tables(x, apdf, acum, apdff, acumf);
+    } catch (...) {
+      return bail(KARL_ENOMEM);
+    }
+    if (!apdf.empty()) {
+      const size_t na = apdf.size();
+      if (ctx->d_ang_pdf.ensure(na) || ctx->d_ang_cum.ensure(na) || ctx->d_ang_pdff.ensure(na) ||
+          ctx->d_ang_cumf.ensure(na))
+        return bail(KARL_ENOMEM);
+      if (cudaMemcpy(ctx->d_ang_pdf.p, apdf.data(), na * 8, cudaMemcpyHostToDevice) ||
+          cudaMemcpy(ctx->d_ang_cum.p, acum.data(), na * 8, cudaMemcpyHostToDevice) ||
+          cudaMemcpy(ctx->d_ang_pdff.p, apdff.data(), na * 4, cudaMemcpyHostToDevice) ||
+          cudaMemcpy(ctx->d_ang_cumf.p, acumf.data(), na * 4, cudaMemcpyHostToDevice))
+        return bail(KARL_ECUDA);
+    }
+  }
   if (transport_setup() != cudaSuccess ||
       cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) ||
       cudaStreamCreateWithFlags(&ctx->cancel_stream, cudaStreamNonBlocking) ||
@@ -783,6 +811,8 @@ void karl_destroy(karl_ctx* ctx) {
   if (ctx->d_cancel) cudaFree(ctx->d_cancel);
   if (ctx->cancel_stream) cudaStreamDestroy(ctx->cancel_stream);
   ctx->d_sig_t.release();
+  ctx->d_ang_pdf.release(); ctx->d_ang_cum.release(); ctx->d_ang_pdff.release();
+  ctx->d_ang_cumf.release();
   ctx->d_ginv.release();
   ctx->d_faces.release();
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);

@@ -29,6 +29,7 @@ enum { ERR_NONE = 0, ERR_TIMEOUT = 4, ERR_CAPACITY = 6, ERR_CANCELLED = 7 };
 
 struct ChanDev {
   int32_t kind, sin, sout, target;   // target: 0 at rest, 1 moving (elastic)
+  int32_t ang, pad;        // angle-table set of an elastic channel, -1 isotropic
   long long loss_q;        // loss in 2^-24 eV units (floor)
   long long thr_q;         // channel open iff eq > thr_q  (E > loss_ev exactly)
   double loss_ev;
@@ -56,6 +57,19 @@ struct Params {
   const float* sigf;            // same, FP32
   int nch;
   ChanDev ch[MAXCH];
+  // scattering-angle tables of elastic channels (Sec. 3.3 Elastic): per set
+  // and impact-energy bin, the pdf of cos chi on n_mu even points over
+  // [-1, 1] and its cumulative integral (trapezoids: exact for the
+  // piecewise-linear pdf); NULL when every channel is isotropic
+  int ang_nb, ang_nmu;
+  double ang_h, ang_inv_h;      // point spacing 2 / (n_mu - 1) and its inverse
+  const double* ang_pdf;        // [sets][bins][n_mu]
+  const double* ang_cum;        // [sets][bins][n_mu], starts at 0
+  const float* ang_pdff;        // FP32 copies
+  const float* ang_cumf;
+  double ang_inv_lo[MAXCH];     // 1 / e_min of each set
+  double ang_scale[MAXCH];      // n_bins / ln(e_max / e_min)
+  double ang_thr[MAXCH];        // isotropic below this impact energy
   int nsc[NSP];
   int8_t sc[NSP][MAXSPCH];      // active channels per species, in selection order
   // species and targets

@@ -125,6 +125,11 @@ struct karl_server {
   double* d_sig_t = nullptr;
   float* d_sigf = nullptr;
   double* d_sig_cm = nullptr;
+  // scattering-angle tables (NULL: every elastic channel isotropic)
+  double* d_ang_pdf = nullptr;
+  double* d_ang_cum = nullptr;
+  float* d_ang_pdff = nullptr;
+  float* d_ang_cumf = nullptr;
   // device control
   SlotDesc* d_desc = nullptr;
   SlotCtl* d_ctl = nullptr;
@@ -315,6 +320,10 @@ karl_status admit(karl_server* srv, Request& r) {
     P.ginv = r.tabs.nq > 0 ? ginv : nullptr;
     P.sig = srv->d_sig_t;
     P.sigf = srv->d_sigf;
+    P.ang_pdf = srv->d_ang_pdf;
+    P.ang_cum = srv->d_ang_cum;
+    P.ang_pdff = srv->d_ang_pdff;
+    P.ang_cumf = srv->d_ang_cumf;
     P.pid_offset = r.pid_offset;
     P.n_prim = (long long)z.n;
     P.pz = pz; P.pe = pe; P.pmu = pmu; P.psp = psp;
@@ -612,6 +621,26 @@ karl_status karl_server_create(const karl_xs* xs, const karl_server_opts* opts,
        cudaMemcpy(srv->d_sig_cm, srv->sigma.data(), srv->sigma.size() * 8,
                   cudaMemcpyHostToDevice)))
     return bail(KARL_ECUDA);
+  {
+    std::vector<double> apdf, acum;
+    std::vector<float> apdff, acumf;
+    try {
+      angular_tables(xs, apdf, acum, apdff, acumf);
+    } catch (...) {
+      return bail(KARL_ENOMEM);
+    }
+    if (!apdf.empty()) {
+      const size_t na = apdf.size();
+      if (cudaMalloc(&srv->d_ang_pdf, na * 8) || cudaMalloc(&srv->d_ang_cum, na * 8) ||
+          cudaMalloc(&srv->d_ang_pdff, na * 4) || cudaMalloc(&srv->d_ang_cumf, na * 4))
+        return bail(KARL_ENOMEM);
+      if (cudaMemcpy(srv->d_ang_pdf, apdf.data(), na * 8, cudaMemcpyHostToDevice) ||
+          cudaMemcpy(srv->d_ang_cum, acum.data(), na * 8, cudaMemcpyHostToDevice) ||
+          cudaMemcpy(srv->d_ang_pdff, apdff.data(), na * 4, cudaMemcpyHostToDevice) ||
+          cudaMemcpy(srv->d_ang_cumf, acumf.data(), na * 4, cudaMemcpyHostToDevice))
+        return bail(KARL_ECUDA);
+    }
+  }
   if (cudaMemset(srv->d_ctl, 0, sizeof(SlotCtl) * MAX_SLOTS) ||
       cudaMemset(srv->d_M, 0, sizeof(MultiCtl)) || cudaMemset(srv->d_cancel, 0, sizeof(int)) ||
       cudaStreamCreateWithFlags(&srv->kstream, cudaStreamNonBlocking) ||
@@ -769,6 +798,8 @@ void karl_server_destroy(karl_server* srv) {
     cudaFree(R.pid); cudaFree(R.ev); cudaFree(R.sj); cudaFree(R.seq);
   }
   cudaFree(srv->d_sig_t); cudaFree(srv->d_sigf); cudaFree(srv->d_sig_cm);
+  cudaFree(srv->d_ang_pdf); cudaFree(srv->d_ang_cum); cudaFree(srv->d_ang_pdff);
+  cudaFree(srv->d_ang_cumf);
   cudaFree(srv->d_desc); cudaFree(srv->d_ctl); cudaFree(srv->d_M); cudaFree(srv->d_cancel);
   cudaFree(srv->d_arena);
   if (srv->h_desc) cudaFreeHost(srv->h_desc);

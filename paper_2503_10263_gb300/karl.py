@@ -56,12 +56,20 @@ class Geometry(C.Structure):
                 ("gas_drift_mps", C.c_double)]
 
 
+class Angular(C.Structure):
+    _fields_ = [("n_sets", C.c_int32), ("n_bins", C.c_int32), ("n_mu", C.c_int32),
+                ("set", C.POINTER(C.c_int32)), ("e_min_ev", C.POINTER(C.c_double)),
+                ("e_max_ev", C.POINTER(C.c_double)), ("threshold_ev", C.POINTER(C.c_double)),
+                ("pdf", C.POINTER(C.c_double))]
+
+
 class XS(C.Structure):
     _fields_ = [("n_energy", C.c_int32), ("e_min_ev", C.c_double), ("e_max_ev", C.c_double),
                 ("n_channels", C.c_int32), ("kind", C.POINTER(C.c_int32)),
                 ("species_in", C.POINTER(C.c_int32)), ("species_out", C.POINTER(C.c_int32)),
                 ("loss_ev", C.POINTER(C.c_double)), ("sigma_m2", C.POINTER(C.c_double)),
-                ("ioniz_eps_ev", C.c_double), ("target", C.POINTER(C.c_int32))]
+                ("ioniz_eps_ev", C.c_double), ("target", C.POINTER(C.c_int32)),
+                ("angular", C.POINTER(Angular))]
 
 
 class Primaries(C.Structure):
@@ -424,7 +432,44 @@ def _xs(prob, keep):
     x.loss_ev, x.sigma_m2 = _dptr(loss), _dptr(sig)
     x.ioniz_eps_ev = prob.ioniz_eps_ev
     x.target = _iptr(target)
+    ang = _angular(prob, keep)
+    if ang is not None:
+        x.angular = C.pointer(ang)
     return x
+
+
+def _angular(prob, keep):
+    """karl_angular of the problem's elastic-channel angle tables (one set per
+    distinct table object, in channel order), or None when all are isotropic."""
+    tabs = [getattr(c, "angular", None) for c in prob.channels]
+    sets, index = [], []
+    for t in tabs:
+        if t is None:
+            index.append(-1)
+            continue
+        for i, u in enumerate(sets):
+            if u is t:
+                index.append(i)
+                break
+        else:
+            sets.append(t)
+            index.append(len(sets) - 1)
+    if not sets:
+        return None
+    nb, nm = np.asarray(sets[0].pdf).shape
+    if any(np.asarray(t.pdf).shape != (nb, nm) for t in sets):
+        raise ValueError("angle tables of one problem must share their bin and point counts")
+    a = Angular()
+    idx = np.array(index, np.int32)
+    lo = np.array([t.e_min_ev for t in sets], np.float64)
+    hi = np.array([t.e_max_ev for t in sets], np.float64)
+    thr = np.array([t.threshold_ev for t in sets], np.float64)
+    pdf = np.ascontiguousarray(np.stack([np.asarray(t.pdf, np.float64) for t in sets]))
+    keep += [idx, lo, hi, thr, pdf, a]
+    a.n_sets, a.n_bins, a.n_mu = len(sets), nb, nm
+    a.set, a.e_min_ev, a.e_max_ev = _iptr(idx), _dptr(lo), _dptr(hi)
+    a.threshold_ev, a.pdf = _dptr(thr), _dptr(pdf)
+    return a
 
 
 class Server:

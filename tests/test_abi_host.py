@@ -86,3 +86,25 @@ def test_missing_library_fails_loudly(monkeypatch):
     monkeypatch.setattr(k, "LIB_PATH", "/nonexistent/libkarl.so")
     with pytest.raises(ImportError):
         k.load()
+
+
+def test_create_rejects_invalid_angle_tables_without_gpu(karl):
+    def with_table(k=0, **kw):
+        p, _ = inputs.config1(n_primaries=10)
+        t = inputs.screened_rutherford_table(n_bins=4, n_mu=9)
+        for f, v in kw.items():
+            setattr(t, f, v)
+        p.channels[k].angular = t
+        return p
+
+    x = np.linspace(-1, 1, 9)
+    zero_bin = np.stack([1.0 + 0 * x, 0 * x, 1.0 + x, 1.0 - x])
+    neg = np.tile(1.0 - 1.5 * x, (4, 1))
+    for p in (with_table(k=1),                       # ionization: no angle table
+              with_table(e_min_ev=0.0), with_table(e_max_ev=50.0),
+              with_table(threshold_ev=-1.0), with_table(threshold_ev=math.nan),
+              with_table(pdf=zero_bin), with_table(pdf=neg),
+              with_table(pdf=np.ones((4, 1)))):
+        with pytest.raises(karl.KarlError) as ei:
+            karl.Context(p)
+        assert ei.value.status == karl.EINVAL
