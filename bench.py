@@ -129,7 +129,7 @@ def _oracle_sample(n_decays_total: int, seconds: float, threads: int):
         t0 = time.perf_counter()
         r = oracle.run(prob, prims, seed=1, n_threads=threads)
         dt = time.perf_counter() - t0
-        return int(r["ledger"][39]), dt
+        return int(r["ledger"][oracle.N_COLLISIONS]), dt
 
     c0, t0 = run(500)
     rate = c0 / max(t0, 1e-6)

@@ -46,10 +46,10 @@ typedef enum karl_status {
   KARL_ENOTFOUND = 9    /* unknown request id */
 } karl_status;
 
-enum { KARL_N_SPECIES = 3, KARL_N_REASONS = 8, KARL_LEDGER_LEN = 64, KARL_MAX_CHANNELS = 16 };
+enum { KARL_N_SPECIES = 4, KARL_N_REASONS = 8, KARL_LEDGER_LEN = 64, KARL_MAX_CHANNELS = 16 };
 
-/* tracked species (Sec. 3.8, Species: electron, T2+, T3+) */
-enum { KARL_ELECTRON = 0, KARL_T2P = 1, KARL_T3P = 2 };
+/* tracked species (Sec. 3.8, Species: electron, T2+, T3+, T+) */
+enum { KARL_ELECTRON = 0, KARL_T2P = 1, KARL_T3P = 2, KARL_TP = 3 };
 
 /* interaction kinds (Sec. 3.3) */
 enum {
@@ -74,9 +74,9 @@ enum {
   KARL_L_E_CUTOFF = 4, KARL_L_E_CAP = 5, KARL_L_E_RECOMB = 6, KARL_L_E_CLUSTER = 7,
   KARL_L_E_LOSS_IONIZ = 8, KARL_L_E_LOSS_EXCIT = 9, KARL_L_E_LOSS_RECOIL = 10,
   KARL_L_E_STALLED = 11,
-  KARL_L_BIRTHS = 12,        /* [3] */
-  KARL_L_DEATHS = 15,        /* [3][8] */
-  KARL_L_N_COLLISIONS = 39, KARL_L_N_FLIGHTS = 40, KARL_L_N_SPAWN_E = 41, KARL_L_N_SPAWN_ION = 42
+  KARL_L_BIRTHS = 12,        /* [4] */
+  KARL_L_DEATHS = 16,        /* [4][8] */
+  KARL_L_N_COLLISIONS = 48, KARL_L_N_FLIGHTS = 49, KARL_L_N_SPAWN_E = 50, KARL_L_N_SPAWN_ION = 51
 };
 
 /* Geometry, gas and terminator settings (copied at create).
@@ -166,18 +166,18 @@ typedef struct karl_primaries {
 
 /* Output tallies (caller-owned, zeroed by the run).  Layouts are row-major. */
 typedef struct karl_tallies {
-  uint64_t* spectrum;          /* [2][3][n_spec_bins+1] particles leaving at z=0 / z=L */
-  uint64_t* time_fx;           /* [3][n_zbins+2][n_tebins] time in segment, LSB 2^-50 s;
+  uint64_t* spectrum;          /* [2][4][n_spec_bins+1] particles leaving at z=0 / z=L */
+  uint64_t* time_fx;           /* [4][n_zbins+2][n_tebins] time in segment, LSB 2^-50 s;
                                   rows 0 and n_zbins+1 are the under/overflow bins */
-  uint64_t* cross_pos;         /* [3][n_zbins+1] face crossings towards +z */
-  uint64_t* cross_neg;         /* [3][n_zbins+1] face crossings towards -z */
-  uint64_t* recomb;            /* [3][n_zbins] deletions logged in each species' field */
+  uint64_t* cross_pos;         /* [4][n_zbins+1] face crossings towards +z */
+  uint64_t* cross_neg;         /* [4][n_zbins+1] face crossings towards -z */
+  uint64_t* recomb;            /* [4][n_zbins] deletions logged in each species' field */
   int64_t* ledger;             /* [KARL_LEDGER_LEN] */
   uint64_t* chan_count;        /* [n_channels] collisions per channel */
   uint64_t* per_primary;       /* [n] collisions in each primary's tree, or NULL */
-  double* density;             /* [3][n_zbins] Eq. target_field_density, or NULL */
-  double* current;             /* [3][n_zbins+1] (N+ - N-)/(A t_sim), or NULL */
-  double* field;               /* [3][n_zbins][n_tebins] pass-1 densities, or NULL */
+  double* density;             /* [4][n_zbins] Eq. target_field_density, or NULL */
+  double* current;             /* [4][n_zbins+1] (N+ - N-)/(A t_sim), or NULL */
+  double* field;               /* [4][n_zbins][n_tebins] pass-1 densities, or NULL */
   int32_t on_device;
 } karl_tallies;
 
@@ -210,7 +210,7 @@ karl_status karl_run(karl_ctx* ctx, const karl_primaries* prim, const karl_run_o
 
 /* One pass over a primary-id range, raw integer tallies only, ADDED to out
  * (density/current/field untouched).  pass = 2 builds the target fields from
- * field_time_in (host, [3][n_zbins+2][n_tebins], the pass-1 time tallies
+ * field_time_in (host, [4][n_zbins+2][n_tebins], the pass-1 time tallies
  * summed over every shard) and prim->n_decays.  This is the host-side
  * exchange step of a run split over ranks (Sec. 3.6: additive sync). */
 karl_status karl_run_pass(karl_ctx* ctx, const karl_primaries* prim, const karl_run_opts* opts,
@@ -232,7 +232,7 @@ karl_status karl_run_pass(karl_ctx* ctx, const karl_primaries* prim, const karl_
  *
  * Arguments as karl_run_pass, except:
  *  - prim->on_device and out->on_device must be 1 (device pointers only), and
- *    for pass 2 field_time_in is a DEVICE array [3][n_zbins+2][n_tebins];
+ *    for pass 2 field_time_in is a DEVICE array [4][n_zbins+2][n_tebins];
  *  - the pass's raw integer tallies OVERWRITE out's buffers (the call zeroes
  *    them first) where karl_run_pass adds to them; per_primary may be NULL;
  *    density, current and field are not touched.

@@ -23,15 +23,15 @@ _SRC = os.path.join(_HERE, "karl_oracle.cpp")
 _HDR = os.path.join(_HERE, "karl_oracle.h")
 _LIB = os.path.join(_HERE, "libkarl_oracle.so")
 
-N_SPECIES = 3
+N_SPECIES = 4
 N_REASONS = 8
 LEDGER_LEN = 64
 # ledger slots (mirrors karl_oracle.h)
 E_IN_PRIMARY, E_IN_THERMAL, E_EXIT0, E_EXIT1, E_CUTOFF, E_CAP, E_RECOMB, E_CLUSTER, \
     E_LOSS_IONIZ, E_LOSS_EXCIT, E_LOSS_RECOIL, E_STALLED = range(12)
 BIRTHS = 12
-DEATHS = 15
-N_COLLISIONS, N_FLIGHTS, N_SPAWN_E, N_SPAWN_ION = 39, 40, 41, 42
+DEATHS = 16
+N_COLLISIONS, N_FLIGHTS, N_SPAWN_E, N_SPAWN_ION = 48, 49, 50, 51
 REASONS = ("exit0", "exit1", "cutoff", "cap_coll", "cap_time", "recomb", "cluster", "stalled")
 
 _lib = None
@@ -55,7 +55,7 @@ class _Problem(C.Structure):
         ("area_m2", C.c_double), ("activity_bq", C.c_double), ("e_cut_ev", C.c_double),
         ("max_collisions", C.c_uint32), ("max_lifetime_s", C.c_double),
         ("gas_temperature_k", C.c_double), ("n_tebins", C.c_int32), ("n_spec_bins", C.c_int32),
-        ("spec_bin_ev", C.c_double), ("species_mass_ev", C.c_double * 3),
+        ("spec_bin_ev", C.c_double), ("species_mass_ev", C.c_double * N_SPECIES),
         ("target_mass_ev", C.c_double), ("n_energy", C.c_int32), ("e_min_ev", C.c_double),
         ("e_max_ev", C.c_double), ("n_channels", C.c_int32), ("kind", C.POINTER(C.c_int32)),
         ("species_in", C.POINTER(C.c_int32)), ("species_out", C.POINTER(C.c_int32)),

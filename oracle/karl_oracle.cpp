@@ -60,7 +60,7 @@ const double Q_ENERGY = 16777216.0;             /* 2^24 units per eV */
 const double Q_TIME = 1125899906842624.0;       /* 2^50 units per s */
 
 enum { ELASTIC = 0, IONIZATION = 1, EXCITATION = 2, CLUSTERING = 3, RECOMBINATION = 4 };
-enum { SP_E = 0, SP_T2P = 1, SP_T3P = 2 };
+enum { SP_E = 0, SP_T2P = 1, SP_T3P = 2, SP_TP = 3 };
 enum { R_EXIT0 = 0, R_EXIT1 = 1, R_CUTOFF = 2, R_CAP_COLL = 3, R_CAP_TIME = 4,
        R_RECOMB = 5, R_CLUSTER = 6, R_STALLED = 7 };
 enum { DOM_EVENT = 0, DOM_ION_BIRTH = 1, DOM_CLUSTER = 2, DOM_REDRAW = 3, DOM_TARGET = 4 };

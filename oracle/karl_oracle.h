@@ -19,16 +19,16 @@
 extern "C" {
 #endif
 
-enum { ORC_N_SPECIES = 3, ORC_N_REASONS = 8, ORC_LEDGER_LEN = 64 };
+enum { ORC_N_SPECIES = 4, ORC_N_REASONS = 8, ORC_LEDGER_LEN = 64 };
 
 /* ledger layout (int64): energies in units of 2^-24 eV, then counters */
 enum {
   ORC_E_IN_PRIMARY = 0, ORC_E_IN_THERMAL = 1, ORC_E_EXIT0 = 2, ORC_E_EXIT1 = 3,
   ORC_E_CUTOFF = 4, ORC_E_CAP = 5, ORC_E_RECOMB = 6, ORC_E_CLUSTER = 7,
   ORC_E_LOSS_IONIZ = 8, ORC_E_LOSS_EXCIT = 9, ORC_E_LOSS_RECOIL = 10, ORC_E_STALLED = 11,
-  ORC_BIRTHS = 12,              /* [3] */
-  ORC_DEATHS = 15,              /* [3][8] */
-  ORC_N_COLLISIONS = 39, ORC_N_FLIGHTS = 40, ORC_N_SPAWN_E = 41, ORC_N_SPAWN_ION = 42
+  ORC_BIRTHS = 12,              /* [4] */
+  ORC_DEATHS = 16,              /* [4][8] */
+  ORC_N_COLLISIONS = 48, ORC_N_FLIGHTS = 49, ORC_N_SPAWN_E = 50, ORC_N_SPAWN_ION = 51
 };
 
 typedef struct {
@@ -86,17 +86,17 @@ typedef struct {
 } orc_primaries;
 
 typedef struct {
-  uint64_t* spectrum;          /* [2][3][n_spec_bins+1] */
-  uint64_t* time_fx;           /* [3][n_zbins+2][n_tebins], LSB 2^-50 s */
-  uint64_t* cross_pos;         /* [3][n_zbins+1] */
-  uint64_t* cross_neg;         /* [3][n_zbins+1] */
-  uint64_t* recomb;            /* [3][n_zbins] */
+  uint64_t* spectrum;          /* [2][4][n_spec_bins+1] */
+  uint64_t* time_fx;           /* [4][n_zbins+2][n_tebins], LSB 2^-50 s */
+  uint64_t* cross_pos;         /* [4][n_zbins+1] */
+  uint64_t* cross_neg;         /* [4][n_zbins+1] */
+  uint64_t* recomb;            /* [4][n_zbins] */
   int64_t* ledger;             /* [ORC_LEDGER_LEN] */
   uint64_t* chan_count;        /* [n_channels] */
   uint64_t* per_primary;       /* [n] collisions in each primary's tree, may be NULL */
-  double* density;             /* [3][n_zbins], may be NULL */
-  double* current;             /* [3][n_zbins+1], may be NULL */
-  double* field;               /* [3][n_zbins][n_tebins] pass-1 densities, may be NULL */
+  double* density;             /* [4][n_zbins], may be NULL */
+  double* current;             /* [4][n_zbins+1], may be NULL */
+  double* field;               /* [4][n_zbins][n_tebins] pass-1 densities, may be NULL */
 } orc_tallies;
 
 /* mode 0: free flight by optical depth (one draw per flight);
@@ -106,7 +106,7 @@ int orc_run(const orc_problem* p, const orc_primaries* pr, uint64_t seed, int n_
 
 /* One pass only.  pass = 1: no recombination.  pass = 2: recombination with
  * the target fields built from field_time_in (raw pass-1 time tallies of the
- * whole run, [3][n_zbins+2][n_tebins]).  Output tallies are raw and
+ * whole run, [4][n_zbins+2][n_tebins]).  Output tallies are raw and
  * accumulated (+=) into out; density/current/field are not written. */
 int orc_run_pass(const orc_problem* p, const orc_primaries* pr, uint64_t seed, int pass,
                  const uint64_t* field_time_in, int mode, int n_threads, orc_tallies* out);

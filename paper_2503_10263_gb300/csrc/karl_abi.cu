@@ -69,7 +69,7 @@ struct karl_ctx {
   unsigned max_coll = 0;
   int nz = 0, ntb = 1, nspec = 1;
   double spec_bin = 1;
-  double mass[NSP] = {0, 0, 0};
+  double mass[NSP] = {};
   double target_mass = 1;
   int n_energy = 0, nch = 0;
   double e_min = 1, e_max = 2;

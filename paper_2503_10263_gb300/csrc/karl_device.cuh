@@ -10,7 +10,7 @@
 
 namespace karl {
 
-constexpr int NSP = 3;            // e-, T2+, T3+
+constexpr int NSP = 4;            // e-, T2+, T3+, T+
 constexpr int MAXCH = 16;         // channels in the tables
 constexpr int MAXSPCH = 10;       // active channels of one species
 constexpr int LEDGER = 64;
@@ -22,8 +22,8 @@ enum { R_EXIT0 = 0, R_EXIT1 = 1, R_CUTOFF = 2, R_CAP_COLL = 3, R_CAP_TIME = 4,
        R_RECOMB = 5, R_CLUSTER = 6, R_STALLED = 7 };
 enum { L_E_IN_PRIMARY = 0, L_E_IN_THERMAL = 1, L_E_EXIT0 = 2, L_E_EXIT1 = 3, L_E_CUTOFF = 4,
        L_E_CAP = 5, L_E_RECOMB = 6, L_E_CLUSTER = 7, L_LOSS_IONIZ = 8, L_LOSS_EXCIT = 9,
-       L_LOSS_RECOIL = 10, L_E_STALLED = 11, L_BIRTHS = 12, L_DEATHS = 15, L_N_COLL = 39,
-       L_N_FLIGHT = 40, L_N_SPAWN_E = 41, L_N_SPAWN_ION = 42 };
+       L_LOSS_RECOIL = 10, L_E_STALLED = 11, L_BIRTHS = 12, L_DEATHS = 16, L_N_COLL = 48,
+       L_N_FLIGHT = 49, L_N_SPAWN_E = 50, L_N_SPAWN_ION = 51 };
 enum { DOM_EVENT = 0, DOM_ION_BIRTH = 1, DOM_CLUSTER = 2, DOM_TARGET = 4 };
 enum { ERR_NONE = 0, ERR_TIMEOUT = 4, ERR_CAPACITY = 6, ERR_CANCELLED = 7 };
 
@@ -99,12 +99,12 @@ struct Params {
   const double* pmu;
   const uint8_t* psp;
   // raw tallies (device)
-  unsigned long long* spectrum;   // [2][3][nspec+1]
-  unsigned long long* time_pt;    // [3][nz+2][ntb] point adds
-  unsigned long long* time_rg;    // [3][nz+2][ntb] range adds (difference form)
-  unsigned long long* xpos_rg;    // [3][nz+2] face crossings +z (difference form)
-  unsigned long long* xneg_rg;    // [3][nz+2] face crossings -z (difference form)
-  unsigned long long* recomb;     // [3][nz]
+  unsigned long long* spectrum;   // [2][4][nspec+1]
+  unsigned long long* time_pt;    // [4][nz+2][ntb] point adds
+  unsigned long long* time_rg;    // [4][nz+2][ntb] range adds (difference form)
+  unsigned long long* xpos_rg;    // [4][nz+2] face crossings +z (difference form)
+  unsigned long long* xneg_rg;    // [4][nz+2] face crossings -z (difference form)
+  unsigned long long* recomb;     // [4][nz]
   unsigned long long* ledger;     // [64]
   unsigned long long* chan_count; // [nch]
   unsigned long long* per_primary;// [n_prim] or NULL

@@ -39,6 +39,7 @@ M_T_ATOM_U = 3.01604928          # tritium atom mass, u
 M_T2_EV = 2.0 * M_T_ATOM_U * AMU_EV          # neutral T2 (binding neglected)
 M_T2P_EV = M_T2_EV - ME_EV                   # T2+
 M_T3P_EV = 3.0 * M_T_ATOM_U * AMU_EV - ME_EV  # T3+
+M_TP_EV = M_T_ATOM_U * AMU_EV - ME_EV         # T+
 KB_EV_PER_K = 8.617333262e-5
 ALPHA_FS = 7.2973525693e-3
 PI_A0_SQ_M2 = math.pi * (5.29177210903e-11) ** 2   # 8.797e-21 m^2
@@ -46,10 +47,10 @@ RYDBERG_EV = 13.605693122994
 T_HALF_S = 12.32 * 365.25 * 86400.0          # tritium half-life
 
 # species and channel kinds (numeric values are part of the C ABI)
-E, T2P, T3P = 0, 1, 2
-N_SPECIES = 3
-SPECIES_MASS_EV = np.array([ME_EV, M_T2P_EV, M_T3P_EV], dtype=np.float64)
-SPECIES_NAMES = ("e-", "T2+", "T3+")
+E, T2P, T3P, TP = 0, 1, 2, 3
+N_SPECIES = 4
+SPECIES_MASS_EV = np.array([ME_EV, M_T2P_EV, M_T3P_EV, M_TP_EV], dtype=np.float64)
+SPECIES_NAMES = ("e-", "T2+", "T3+", "T+")
 
 ELASTIC, IONIZATION, EXCITATION, CLUSTERING, RECOMBINATION = 0, 1, 2, 3, 4
 KIND_NAMES = ("elastic", "ionization", "excitation", "clustering", "recombination")

@@ -22,7 +22,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libkarl.so")
 
-N_SPECIES = 3
+N_SPECIES = 4
 N_REASONS = 8
 LEDGER_LEN = 64
 MAX_CHANNELS = 16
@@ -35,8 +35,8 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW, ECAPACITY, ECANCELLED, EBUSY, EN
 # ledger slots
 E_IN_PRIMARY, E_IN_THERMAL, E_EXIT0, E_EXIT1, E_CUTOFF, E_CAP, E_RECOMB, E_CLUSTER, \
     E_LOSS_IONIZ, E_LOSS_EXCIT, E_LOSS_RECOIL, E_STALLED = range(12)
-BIRTHS, DEATHS = 12, 15
-N_COLLISIONS, N_FLIGHTS, N_SPAWN_E, N_SPAWN_ION = 39, 40, 41, 42
+BIRTHS, DEATHS = 12, 16
+N_COLLISIONS, N_FLIGHTS, N_SPAWN_E, N_SPAWN_ION = 48, 49, 50, 51
 
 
 class KarlError(RuntimeError):
@@ -52,7 +52,7 @@ class Geometry(C.Structure):
                 ("max_collisions", C.c_uint32), ("max_lifetime_s", C.c_double),
                 ("gas_temperature_k", C.c_double), ("n_tebins", C.c_int32),
                 ("n_spec_bins", C.c_int32), ("spec_bin_ev", C.c_double),
-                ("species_mass_ev", C.c_double * 3), ("target_mass_ev", C.c_double),
+                ("species_mass_ev", C.c_double * N_SPECIES), ("target_mass_ev", C.c_double),
                 ("gas_drift_mps", C.c_double)]
 
 
@@ -407,7 +407,7 @@ def _geometry(prob, keep):
     g.n_tebins = prob.n_tebins
     g.n_spec_bins = prob.n_spec_bins
     g.spec_bin_ev = prob.spec_bin_ev
-    for i in range(3):
+    for i in range(N_SPECIES):
         g.species_mass_ev[i] = float(prob.species_mass_ev[i])
     g.target_mass_ev = prob.target_mass_ev
     g.gas_drift_mps = float(getattr(prob, "gas_drift_mps", 0.0))

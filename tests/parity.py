@@ -13,6 +13,8 @@ import math
 import numpy as np
 
 P3 = 0.0027
+N_SPECIES = 4                  # e-, T2+, T3+, T+ (ledger layout of the C ABI and the oracle)
+BIRTHS, DEATHS = 12, 16
 
 
 def excursions_ok(z: np.ndarray) -> bool:
@@ -62,8 +64,8 @@ def batch_two_sample(ga: np.ndarray, ob: np.ndarray, min_se_frac: float = 0.0):
 def ledger_balances(L) -> bool:
     e_in = int(L[0]) + int(L[1])
     e_out = int(np.sum(L[2:12]))
-    births = np.asarray(L[12:15])
-    deaths = np.asarray(L[15:39]).reshape(3, 8).sum(axis=1)
+    births = np.asarray(L[BIRTHS:BIRTHS + N_SPECIES])
+    deaths = np.asarray(L[DEATHS:DEATHS + 8 * N_SPECIES]).reshape(N_SPECIES, 8).sum(axis=1)
     return e_in == e_out and np.array_equal(births, deaths)
 
 

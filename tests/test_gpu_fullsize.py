@@ -50,21 +50,22 @@ def pass1(karl, full):
 
 
 def _deaths(L):
-    return np.asarray(L[15:39], np.int64).reshape(3, 8)
+    return np.asarray(L[parity.DEATHS:parity.DEATHS + 8 * parity.N_SPECIES],
+                      np.int64).reshape(parity.N_SPECIES, 8)
 
 
 def _check_properties(karl, t, nz, raw):
     L = t["ledger"]
     assert parity.ledger_balances(L)
     d = _deaths(L)
-    spec = np.asarray(t["spectrum"], np.int64).reshape(2, 3, -1).sum(-1)
+    spec = np.asarray(t["spectrum"], np.int64).reshape(2, karl.N_SPECIES, -1).sum(-1)
     np.testing.assert_array_equal(spec[0], d[:, 0])      # exits at z = 0
     np.testing.assert_array_equal(spec[1], d[:, 1])      # exits at z = L
     assert int(np.sum(t["chan_count"])) == int(L[karl.N_COLLISIONS])
     assert int(np.sum(t["recomb"])) == int(d[:, 5].sum())
     if raw:
-        cp = np.asarray(t["cross_pos"], np.int64).reshape(3, nz + 1)
-        cn = np.asarray(t["cross_neg"], np.int64).reshape(3, nz + 1)
+        cp = np.asarray(t["cross_pos"], np.int64).reshape(karl.N_SPECIES, nz + 1)
+        cn = np.asarray(t["cross_neg"], np.int64).reshape(karl.N_SPECIES, nz + 1)
         np.testing.assert_array_equal(cn[:, 0], d[:, 0])
         np.testing.assert_array_equal(cp[:, nz], d[:, 1])
         assert not cp[:, 0].any() and not cn[:, nz].any()

@@ -31,7 +31,7 @@ def case():
 
 
 def _exit_stats(prob, t):
-    spec = np.asarray(t["spectrum"]).reshape(2, 3, -1)[:, 0, :].sum(0).astype(float)
+    spec = np.asarray(t["spectrum"]).reshape(2, inputs.N_SPECIES, -1)[:, 0, :].sum(0).astype(float)
     e = (np.arange(spec.size - 1) + 0.5) * prob.spec_bin_ev
     n = spec[:-1].sum()
     mean = (spec[:-1] * e).sum() / n

@@ -207,8 +207,8 @@ def test_caps_match_oracle(karl):
     assert parity.ledger_balances(g["ledger"])
     assert _same_histories(g, o) >= 0.99
     for r in (3, 4):                           # collision cap, lifetime cap
-        gs = g["ledger"][karl.DEATHS + r::8][:3].sum()
-        os_ = o["ledger"][karl.DEATHS + r::8][:3].sum()
+        gs = g["ledger"][karl.DEATHS + r::8][:karl.N_SPECIES].sum()
+        os_ = o["ledger"][karl.DEATHS + r::8][:karl.N_SPECIES].sum()
         assert gs > 0 and abs(int(gs) - int(os_)) <= max(3, 0.01 * os_)
 
 

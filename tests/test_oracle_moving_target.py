@@ -138,7 +138,7 @@ def test_elastic_thermalisation_gives_the_gas_temperature():
     # mean 2kT, variance 2(kT)^2.
     prob, prims = inputs.thermalization(n_primaries=2000, length=0.4)
     o = oracle.run(prob, prims, seed=3, n_threads=8)
-    spec = o["spectrum"].reshape(2, 3, -1)[:, 0, :].sum(0).astype(float)
+    spec = o["spectrum"].reshape(2, inputs.N_SPECIES, -1)[:, 0, :].sum(0).astype(float)
     assert spec[-1] == 0
     w = prob.spec_bin_ev
     e = (np.arange(spec.size - 1) + 0.5) * w

@@ -408,8 +408,9 @@ def test_thermal_product_is_maxwell_boltzmann():
 def _ledger_balances(L):
     e_in = L[oracle.E_IN_PRIMARY] + L[oracle.E_IN_THERMAL]
     e_out = L[oracle.E_EXIT0:oracle.E_STALLED + 1].sum()
-    births = L[oracle.BIRTHS:oracle.BIRTHS + 3]
-    deaths = L[oracle.DEATHS:oracle.DEATHS + 24].reshape(3, 8).sum(axis=1)
+    ns = oracle.N_SPECIES
+    births = L[oracle.BIRTHS:oracle.BIRTHS + ns]
+    deaths = L[oracle.DEATHS:oracle.DEATHS + 8 * ns].reshape(ns, 8).sum(axis=1)
     return e_in == e_out and np.array_equal(births, deaths)
 
 
