@@ -106,6 +106,11 @@ def _load():
             C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_double),
             C.POINTER(C.c_double), C.POINTER(C.c_double)]
         lib.orc_elastic_moving_target.restype = None
+        lib.orc_charge_exchange.argtypes = [
+            C.POINTER(_Problem), C.c_double, C.c_double, C.c_double, C.POINTER(C.c_uint64),
+            C.POINTER(C.c_uint64), C.POINTER(C.c_double), C.POINTER(C.c_double),
+            C.POINTER(C.c_double)]
+        lib.orc_charge_exchange.restype = None
         lib.orc_sample_angle.argtypes = [C.POINTER(_Problem), C.c_int, C.c_double, C.c_double]
         lib.orc_sample_angle.restype = C.c_double
         _lib = lib
@@ -329,4 +334,20 @@ def elastic_moving_target(prob, m1_ev: float, e_ev: float, mu: float, words, ctr
                                   _ptr(c, C.c_uint64), _ptr(k, C.c_uint64),
                                   _ptr(oe, C.c_double), _ptr(om, C.c_double),
                                   _ptr(v, C.c_double))
+    return float(oe[0]), float(om[0]), v
+
+
+def charge_exchange(prob, m1_ev: float, e_ev: float, mu: float, ctr, key):
+    """One charge exchange: target blocks from counter (ctr[0], ctr[1], ctr[2],
+    k) and key; returns (E', mu', target velocity[3] in units of c)."""
+    lib = _load()
+    m = _Marshal(prob)
+    c = np.array(ctr, np.uint64)
+    k = np.array(key, np.uint64)
+    oe = np.zeros(1)
+    om = np.zeros(1)
+    v = np.zeros(3)
+    lib.orc_charge_exchange(C.byref(m.s), m1_ev, e_ev, mu, _ptr(c, C.c_uint64),
+                            _ptr(k, C.c_uint64), _ptr(oe, C.c_double), _ptr(om, C.c_double),
+                            _ptr(v, C.c_double))
     return float(oe[0]), float(om[0]), v

@@ -34,7 +34,14 @@
  *    secondary azimuth = primary azimuth - pi (Sec. 3.3, Ionization); the ion
  *    gets a thermal target velocity (no recoil);
  *  - clustering: the product takes a thermal target's direction and the speed
- *    that keeps the target's kinetic energy with the product mass;
+ *    that keeps the target's kinetic energy with the product mass; three-body
+ *    clustering (Sec. 3.3 Clustering, Eq. clustering_tertiary) has the rate
+ *    per unit path sigma_k(E) n(z)^2, its table holding k_ter / v, so that the
+ *    mean free path is v / (k_ter n^2) (Eq. clustering_test_tertiary_mfp);
+ *  - charge exchange (Sec. 3.3 Charge exchange): the impactor takes the
+ *    velocity of a target particle drawn as for a moving elastic target (gas
+ *    drift plus a Maxwell-Boltzmann velocity with the relative-speed weight),
+ *    keeps its species, and the change of kinetic energy goes to the gas;
  *  - recombination: the impactor is deleted, the partner's field logs one
  *    deletion in the segment (Sec. 3.3, Recombination);
  *  - two passes: pass 1 without recombination builds the target fields,
@@ -59,7 +66,8 @@ const double TWO_PI = 6.283185307179586476925286766559;
 const double Q_ENERGY = 16777216.0;             /* 2^24 units per eV */
 const double Q_TIME = 1125899906842624.0;       /* 2^50 units per s */
 
-enum { ELASTIC = 0, IONIZATION = 1, EXCITATION = 2, CLUSTERING = 3, RECOMBINATION = 4 };
+enum { ELASTIC = 0, IONIZATION = 1, EXCITATION = 2, CLUSTERING = 3, RECOMBINATION = 4,
+       CHARGE_EXCHANGE = 5, CLUSTERING3 = 6 };
 enum { SP_E = 0, SP_T2P = 1, SP_T3P = 2, SP_TP = 3 };
 enum { R_EXIT0 = 0, R_EXIT1 = 1, R_CUTOFF = 2, R_CAP_COLL = 3, R_CAP_TIME = 4,
        R_RECOMB = 5, R_CLUSTER = 6, R_STALLED = 7 };
@@ -253,6 +261,21 @@ void moving_target_elastic(const orc_problem* p, int ch, double m1, double e, do
   }
 }
 
+/* Charge exchange (Sec. 3.3 Charge exchange): the impactor of rest energy m1,
+ * kinetic energy e and pitch cosine mu takes the velocity of a target
+ * particle drawn as for a moving elastic target (target_velocity); its new
+ * kinetic energy is 1/2 m1 |v2|^2 and its pitch cosine v2_z / |v2|. */
+void charge_exchange(const orc_problem* p, double m1, double e, double mu, TargetBlock blk,
+                     void* ctx, double* e_out, double* mu_out, double v2[3]) {
+  const double s1 = std::sqrt(2.0 * e / m1);
+  const double sperp = std::sqrt(std::fmax(0.0, 1.0 - mu * mu));
+  const double v1[3] = {s1 * sperp, 0.0, s1 * mu};
+  target_velocity(p, v1, blk, ctx, v2);
+  const double sp2 = v2[0] * v2[0] + v2[1] * v2[1] + v2[2] * v2[2];
+  *e_out = 0.5 * m1 * sp2;
+  *mu_out = sp2 > 0.0 ? std::fmax(-1.0, std::fmin(1.0, v2[2] / std::sqrt(sp2))) : 1.0;
+}
+
 struct Particle {
   double z;
   int64_t eq;        /* kinetic energy, 2^-24 eV */
@@ -342,10 +365,13 @@ void flight_coefficients(const Run& R, int species, double e, double v, double* 
 }
 
 /* macroscopic rate per unit path length of channel k in segment j
- * (the inverse mean free path of Eq. mean_free_path, one term) */
+ * (the inverse mean free path of Eq. mean_free_path, one term); three-body
+ * clustering meets two gas molecules, so its rate goes with n^2 */
 double channel_rate(const Run& R, int k, const double* c, int j) {
   if (R.p->kind[k] == RECOMBINATION) return R.field[k].empty() ? 0.0 : c[k] * R.field[k][j];
-  return c[k] * R.p->n_seg_m3[j];
+  const double n = R.p->n_seg_m3[j];
+  if (R.p->kind[k] == CLUSTERING3) return c[k] * n * n;
+  return c[k] * n;
 }
 
 double total_rate(const Run& R, const double* c, int j) {
@@ -583,6 +609,21 @@ struct Worker {
         T.ledger[ORC_E_LOSS_RECOIL] += rq;
         P.eq -= rq;
         P.mu = mu1;
+      } else if (kind == CHARGE_EXCHANGE) {
+        /* the impactor leaves with a target particle's velocity */
+        struct Ctx { Worker* self; uint32_t ev; uint64_t node; } cx = {this, P.ev - 1, P.node};
+        auto blk = [](void* c, uint64_t k, uint64_t out[4]) {
+          Ctx* q = (Ctx*)c;
+          q->self->block(q->ev, q->node, DOM_TARGET, k, out);
+        };
+        double e1, mu1, v2[3];
+        charge_exchange(p, m, e, P.mu, blk, &cx, &e1, &mu1, v2);
+        /* kinetic energy handed to the gas (negative when the ion gains) */
+        int64_t rq = quant_recoil(e - e1);
+        if (rq > P.eq) rq = P.eq;
+        T.ledger[ORC_E_LOSS_RECOIL] += rq;
+        P.eq -= rq;
+        P.mu = mu1;
       } else if (kind == ELASTIC) {
         /* CM polar angle (isotropic or tabulated); lab energy and polar angle
            for a target at rest, whose impact energy is the lab energy */
@@ -648,7 +689,7 @@ struct Worker {
         }
         P.eq = eq1;
         P.mu = mu_p;
-      } else if (kind == CLUSTERING) {
+      } else if (kind == CLUSTERING || kind == CLUSTERING3) {
         /* incident ion consumed; product with a thermal target's energy */
         die(P, R_CLUSTER, ORC_E_CLUSTER);
         uint64_t wc[4];
@@ -800,6 +841,20 @@ void orc_elastic_moving_target(const orc_problem* p, double m1_ev, double e_ev, 
   moving_target_elastic(p, ch, m1_ev, e_ev, mu, w, blk, &cx, out_e, out_mu, v);
 }
 
+void orc_charge_exchange(const orc_problem* p, double m1_ev, double e_ev, double mu,
+                         const uint64_t ctr[3], const uint64_t key[2], double* out_e,
+                         double* out_mu, double* v2) {
+  struct Ctx { uint64_t ctr[3]; uint64_t key[2]; } cx = {{ctr[0], ctr[1], ctr[2]}, {key[0], key[1]}};
+  auto blk = [](void* c, uint64_t k, uint64_t out[4]) {
+    Ctx* q = (Ctx*)c;
+    const uint64_t full[4] = {q->ctr[0], q->ctr[1], q->ctr[2], k};
+    philox4x64_10(full, q->key, out);
+  };
+  double v[3];
+  charge_exchange(p, m1_ev, e_ev, mu, blk, &cx, out_e, out_mu, v);
+  if (v2) for (int i = 0; i < 3; ++i) v2[i] = v[i];
+}
+
 int orc_collide(const orc_problem* p, int ch, int species, double e_ev, double mu,
                 const uint64_t w[4], double* out_e, double* out_mu, int* out_species) {
   /* same kinematics as Worker::transport, for single-collision enumeration */
@@ -851,7 +906,7 @@ int orc_collide(const orc_problem* p, int ch, int species, double e_ev, double m
     out_species[1] = SP_E;
     return 2;
   }
-  if (kind == CLUSTERING) {
+  if (kind == CLUSTERING || kind == CLUSTERING3) {
     double kt = KB_EV * p->gas_temperature_k;
     double c = std::cos(TWO_PI * u01(w[2]));
     double ec = kt * (-std::log(eta01(w[0])) - std::log(eta01(w[1])) * c * c);

@@ -49,7 +49,9 @@ typedef struct {
   int32_t n_energy;
   double e_min_ev, e_max_ev;
   int32_t n_channels;
-  const int32_t* kind;         /* 0 elastic 1 ionization 2 excitation 3 clustering 4 recombination */
+  /* 0 elastic 1 ionization 2 excitation 3 clustering 4 recombination
+     5 charge exchange 6 three-body clustering (rate sigma_k(E) n^2) */
+  const int32_t* kind;
   const int32_t* species_in;
   const int32_t* species_out;
   const double* loss_ev;
@@ -131,6 +133,15 @@ int orc_collide(const orc_problem* p, int channel, int species, double e_ev, dou
 void orc_elastic_moving_target(const orc_problem* p, double m1_ev, double e_ev, double mu,
                                const uint64_t w[4], const uint64_t ctr[3], const uint64_t key[2],
                                double* out_e, double* out_mu, double* v);
+
+/* One charge exchange (Sec. 3.3 Charge exchange) of an impactor of rest
+ * energy m1_ev, kinetic energy e_ev and pitch cosine mu; the target velocity
+ * is drawn from the blocks (ctr[0], ctr[1], ctr[2], k) under key.  Writes the
+ * impactor's new energy and pitch cosine and, if v2 is not NULL, the target
+ * velocity it took (units of c). */
+void orc_charge_exchange(const orc_problem* p, double m1_ev, double e_ev, double mu,
+                         const uint64_t ctr[3], const uint64_t key[2], double* out_e,
+                         double* out_mu, double* v2);
 
 /* cos(chi) of an elastic collision of channel `channel` at impact energy
  * e_ev for the uniform number u in [0, 1) (isotropic: 2u - 1). */

@@ -53,7 +53,9 @@ SPECIES_MASS_EV = np.array([ME_EV, M_T2P_EV, M_T3P_EV, M_TP_EV], dtype=np.float6
 SPECIES_NAMES = ("e-", "T2+", "T3+", "T+")
 
 ELASTIC, IONIZATION, EXCITATION, CLUSTERING, RECOMBINATION = 0, 1, 2, 3, 4
-KIND_NAMES = ("elastic", "ionization", "excitation", "clustering", "recombination")
+CHARGE_EXCHANGE, CLUSTERING3 = 5, 6
+KIND_NAMES = ("elastic", "ionization", "excitation", "clustering", "recombination",
+              "charge_exchange", "clustering3")
 
 
 @dataclasses.dataclass
@@ -98,7 +100,7 @@ class Problem:
     n_tebins: int                  # energy bins of the time (density) tally
     n_spec_bins: int               # end-spectrum bins (+1 overflow)
     spec_bin_ev: float
-    species_mass_ev: np.ndarray    # [3]
+    species_mass_ev: np.ndarray    # [4]
     target_mass_ev: float          # background gas molecule (T2)
     n_energy: int
     e_min_ev: float
@@ -163,6 +165,25 @@ def elastic_sigma(e: np.ndarray, s0: float = 1e-19, e_s: float = 10.0) -> np.nda
 
 def recomb_sigma(e: np.ndarray, s_r: float = 1e-20) -> np.ndarray:
     return s_r * (1.0 / e)
+
+
+def rate_sigma(e: np.ndarray, k: float, m_ev: float) -> np.ndarray:
+    """Cross section standing in for a rate coefficient (Sec. 3.3 Clustering:
+    only rate coefficients are known, so the cross section is approximated):
+    k / v(E) for an impactor of rest energy m_ev (relativistic speed).  A
+    two-body k (m^3/s) gives m^2; a three-body k (m^6/s) gives the m^5
+    coefficient of a CLUSTERING3 channel, whose rate per unit path is
+    k n^2 / v."""
+    x = e / m_ev
+    v = 299792458.0 * np.sqrt(x * (2.0 + x)) / (1.0 + x)
+    return k / v
+
+
+def dissociative_ionization(nodes: np.ndarray, loss_ev: float = 18.1, m_k: float = 0.3) -> Channel:
+    """e- + T2 -> e- + e- + T+ + T (Eq. ionization_diss): an ionization whose
+    ion product is T+ (synthetic Born-Bethe table, 18.1 eV threshold)."""
+    return Channel("dissociative_ionization", IONIZATION, E, TP, loss_ev,
+                   born_bethe(nodes, loss_ev, m_k))
 
 
 def electron_channels(nodes: np.ndarray, full: bool) -> List[Channel]:

@@ -70,3 +70,63 @@ def bound_sigma(mean, xmax, n):
     with the given total mean: Var(X) <= E[X](xmax - E[X])."""
     m = mean / n
     return math.sqrt(max(n * m * (xmax - m), 0.0))
+
+
+# ---------------------------------------------------------------------------
+# charge exchange on a Maxwellian gas (Sec. 3.3 Charge exchange): the ion
+# takes the velocity w of a target met at a rate proportional to the relative
+# speed, i.e. w ~ |u - w| f(w), f the Maxwellian with per-component variance
+# a^2.  Written in units of a; both forms reduce the angular integral to
+# closed form.
+
+def _shell_relative_speed(x, x0):
+    """Mean of |u - w| over directions of w, |u| = x0, |w| = x (units of a):
+    ((x0 + x)^3 - |x0 - x|^3) / (6 x0 x)."""
+    if x <= 0.0:
+        return x0
+    return ((x0 + x) ** 3 - abs(x0 - x) ** 3) / (6.0 * x0 * x)
+
+
+def maxwell_mean_relative_speed(x):
+    """g(x) = E|u - w| over w ~ f for |u| = x (units of a):
+    sqrt(2/pi) exp(-x^2/2) + (x + 1/x) erf(x / sqrt 2)."""
+    if x < 1e-8:
+        return 2.0 * math.sqrt(2.0 / math.pi)
+    return (math.sqrt(2.0 / math.pi) * math.exp(-0.5 * x * x)
+            + (x + 1.0 / x) * math.erf(x / math.sqrt(2.0)))
+
+
+def cx_one_collision_speed_moments(x0):
+    """E[|w|^2] and E[|w|^4] (units of a) after one charge exchange of an ion
+    of speed x0."""
+    from scipy import integrate
+    w = lambda x, p: x ** p * math.exp(-0.5 * x * x) * _shell_relative_speed(x, x0)
+    hi = 12.0
+    z = integrate.quad(lambda x: w(x, 2), 0, hi, limit=200)[0]
+    m2 = integrate.quad(lambda x: w(x, 4), 0, hi, limit=200)[0] / z
+    m4 = integrate.quad(lambda x: w(x, 6), 0, hi, limit=200)[0] / z
+    return m2, m4
+
+
+def cx_stationary_speed_moments():
+    """E[|u|^2] and E[|u|^4] (units of a) of the ion velocity after a collision
+    once repeated charge exchange has forgotten the start: the chain
+    u' ~ |u - w| f(w) has the stationary density f(u) g(u)."""
+    from scipy import integrate
+    w = lambda x, p: x ** p * math.exp(-0.5 * x * x) * maxwell_mean_relative_speed(x)
+    hi = 12.0
+    z = integrate.quad(lambda x: w(x, 2), 0, hi, limit=200)[0]
+    m2 = integrate.quad(lambda x: w(x, 4), 0, hi, limit=200)[0] / z
+    m4 = integrate.quad(lambda x: w(x, 6), 0, hi, limit=200)[0] / z
+    return m2, m4
+
+
+def cx_one_collision_mean_wz(x0):
+    """E[w_z] (units of a) after one charge exchange of an ion moving along +z
+    with speed x0: targets moving against the ion are met more often."""
+    from scipy import integrate
+    g = lambda c, x: x * x * math.exp(-0.5 * x * x) * math.sqrt(
+        max(x0 * x0 + x * x - 2.0 * x0 * x * c, 0.0))
+    num = integrate.dblquad(lambda c, x: x * c * g(c, x), 0, 12.0, -1.0, 1.0)[0]
+    den = integrate.dblquad(g, 0, 12.0, -1.0, 1.0)[0]
+    return num / den
