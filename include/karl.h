@@ -57,7 +57,16 @@ enum {
   KARL_IONIZATION = 1,     /* E -> E - I - W, secondary electron W, ion species_out */
   KARL_EXCITATION = 2,     /* E -> E - loss, direction unchanged */
   KARL_CLUSTERING = 3,     /* ion -> species_out with a thermal target's energy */
-  KARL_RECOMBINATION = 4   /* impactor deleted; species_out = partner field */
+  KARL_RECOMBINATION = 4,  /* impactor deleted; species_out = partner field */
+  /* Sec. 3.3 Charge exchange: the ion (species_in not an electron) takes the
+   * velocity of a target particle, drawn as for a moving elastic target (gas
+   * drift plus Maxwell-Boltzmann, relative-speed weight); species kept,
+   * species_out unused, the change of kinetic energy goes to the gas */
+  KARL_CHARGE_EXCHANGE = 5,
+  /* Sec. 3.3 Clustering, Eq. clustering_tertiary: three-body clustering,
+   * rate per unit path sigma(E) n(z)^2 with the table holding k_ter / v(E)
+   * (m^5), so the mean free path is v / (k_ter n^2); product as CLUSTERING */
+  KARL_CLUSTERING3 = 6
 };
 
 /* termination reasons (Sec. 3.2 terminator and deletion logger) */
@@ -133,7 +142,10 @@ typedef struct karl_angular {
 typedef struct karl_xs {
   int32_t n_energy;            /* >= 2 */
   double e_min_ev, e_max_ev;   /* 0 < e_min < e_max */
-  int32_t n_channels;          /* 0 .. KARL_MAX_CHANNELS, selection order */
+  /* 0 .. KARL_MAX_CHANNELS, selection order; per impactor species at most 10
+   * channels, of which at most 2 have a rate that follows a field other than
+   * n(z) (recombination, three-body clustering) */
+  int32_t n_channels;
   const int32_t* kind;         /* host, [n_channels] */
   const int32_t* species_in;   /* host, impactor species */
   const int32_t* species_out;  /* host, see the kinds above; -1 = none */

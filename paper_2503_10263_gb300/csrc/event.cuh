@@ -202,8 +202,8 @@ struct WarpQueue {
   int top;
 };
 
-// Collisions in the rare channels (ionization with its products, clustering)
-// cost as much FP64 work as a whole ordinary event, and a warp pays that cost
+// Collisions in the rare channels (ionization with its products, clustering,
+// charge exchange) cost as much FP64 work as a whole ordinary event, and a warp pays that cost
 // in full for a single lane.  A lane that selects one parks its particle here
 // (state after the flight, channel chosen) and takes other work; when enough
 // have gathered the whole warp performs them together.  The kinematics draw
@@ -328,26 +328,21 @@ __device__ __forceinline__ typename RT<F32>::R elastic_cchi(const Params& P, con
 // 64 rejections the last draw stands.  The centre-of-mass polar angle (cos
 // uniform, w[2]) and azimuth (w[3], from the plane of z and the relative
 // velocity) turn the relative velocity.
+// The thermal part (wx, wy, wz) of the target velocity met by an impactor of
+// velocity (v1x, 0, v1z) (units of c), drawn as described above.
 template <bool F32>
-__device__ __noinline__ void moving_target_elastic(const Params& P, const ChanDev& ch, Lane& L,
-                                                   const unsigned long long w[4],
-                                                   unsigned long long& recoil) {
+__device__ __forceinline__ void draw_target(const Params& P, const Lane& L,
+                                            typename RT<F32>::R v1x, typename RT<F32>::R v1z,
+                                            typename RT<F32>::R& wx, typename RT<F32>::R& wy,
+                                            typename RT<F32>::R& wz) {
   using T = RT<F32>;
   using R = typename T::R;
-  const int s = L.sp;
-  const R m1 = (R)P.mass[s], m2 = (R)P.target_mass, M = m1 + m2;
-  const R e = T::energy(L.eq);
-  const R s1 = T::sq((R)2 * e / m1);
-  const R mu = (R)L.mu;
-  const R sperp = T::sq(fmax((R)0, (R)1 - mu * mu));
-  const R v1x = s1 * sperp, v1z = s1 * mu;
-  // target velocity
   const R a = (R)P.target_a, ud = (R)P.drift_c;
   const R uz = v1z - ud;
   const R un = T::sq(v1x * v1x + uz * uz);
   const R rpi = (R)1.7724538509055160273, r8 = (R)2.8284271247461900976;
   const R pmax = un * rpi / (un * rpi + r8 * a);
-  R wx = (R)0, wy = (R)0, wz = (R)0;
+  wx = (R)0; wy = (R)0; wz = (R)0;
   for (int k = 0; k < 64; ++k) {
     unsigned long long b0[4], b1[4];
     const unsigned long long ctr2 = ((unsigned long long)P.pass << 8) | DOM_TARGET;
@@ -372,7 +367,24 @@ __device__ __noinline__ void moving_target_elastic(const Params& P, const ChanDe
     const R gn = T::sq(g0 * g0 + g1 * g1 + g2 * g2);
     if (T::u(b1[2]) * (un + sp) < gn) break;
   }
-  const R v2x = wx, v2y = wy, v2z = ud + wz;
+}
+
+template <bool F32>
+__device__ __noinline__ void moving_target_elastic(const Params& P, const ChanDev& ch, Lane& L,
+                                                   const unsigned long long w[4],
+                                                   unsigned long long& recoil) {
+  using T = RT<F32>;
+  using R = typename T::R;
+  const int s = L.sp;
+  const R m1 = (R)P.mass[s], m2 = (R)P.target_mass, M = m1 + m2;
+  const R e = T::energy(L.eq);
+  const R s1 = T::sq((R)2 * e / m1);
+  const R mu = (R)L.mu;
+  const R sperp = T::sq(fmax((R)0, (R)1 - mu * mu));
+  const R v1x = s1 * sperp, v1z = s1 * mu;
+  R wx, wy, wz;
+  draw_target<F32>(P, L, v1x, v1z, wx, wy, wz);
+  const R v2x = wx, v2y = wy, v2z = (R)P.drift_c + wz;
   // centre-of-mass velocity and relative velocity
   const R Vx = (m1 * v1x + m2 * v2x) / M, Vy = (m2 * v2y) / M, Vz = (m1 * v1z + m2 * v2z) / M;
   const R gx = v1x - v2x, gy = -v2y, gz = v1z - v2z;
@@ -403,6 +415,31 @@ __device__ __noinline__ void moving_target_elastic(const Params& P, const ChanDe
   L.mu = sp2 > (R)0 ? (double)fmin((R)1, fmax((R)-1, nz * T::rsq(sp2))) : 1.0;
 }
 
+// Charge exchange (Sec. 3.3 Charge exchange): the ion takes the velocity v2 of
+// a target particle drawn as for a moving elastic target (draw_target plus
+// the gas drift); its kinetic energy becomes 1/2 m1 |v2|^2 (nonrelativistic)
+// and the difference, of either sign, goes to the gas; species unchanged.
+template <bool F32>
+__device__ __noinline__ void charge_exchange(const Params& P, Lane& L, unsigned long long& recoil) {
+  using T = RT<F32>;
+  using R = typename T::R;
+  const R m1 = (R)P.mass[L.sp];
+  const R e = T::energy(L.eq);
+  const R s1 = T::sq((R)2 * e / m1);
+  const R mu = (R)L.mu;
+  const R sperp = T::sq(fmax((R)0, (R)1 - mu * mu));
+  R wx, wy, wz;
+  draw_target<F32>(P, L, s1 * sperp, s1 * mu, wx, wy, wz);
+  const R vz = (R)P.drift_c + wz;
+  const R sp2 = wx * wx + wy * wy + vz * vz;
+  const R e1 = (R)0.5 * m1 * sp2;
+  long long rq = T::quant_signed(e - e1);
+  if (rq > L.eq) rq = L.eq;
+  recoil += (unsigned long long)rq;
+  L.eq -= rq;
+  L.mu = sp2 > (R)0 ? (double)fmin((R)1, fmax((R)-1, vz * T::rsq(sp2))) : 1.0;
+}
+
 // Terminator of Sec. 3.2 after a collision.
 template <bool F32>
 __device__ __forceinline__ void terminate(const Params& P, unsigned long long* led, Lane& L,
@@ -419,8 +456,9 @@ __device__ __forceinline__ void terminate(const Params& P, unsigned long long* l
   }
 }
 
-// Kinematics of an ionization (Sec. 3.3 Ionization: energy sharing, binary-
-// encounter angles, the slow electron and the ion as products) or a clustering
+// Kinematics of a charge exchange (Sec. 3.3), an ionization (Sec. 3.3
+// Ionization: energy sharing, binary-encounter angles, the slow electron and
+// the ion as products) or a clustering
 // (Sec. 3.3 Clustering: the impactor becomes the product ion with a thermal
 // target's motion) of the particle L, whose flight and channel choice are done
 // (L.ev already counts this collision; w is the event's random block).
@@ -431,6 +469,11 @@ __device__ __forceinline__ void rare_kinematics(const Params& P, unsigned long l
   using T = RT<F32>;
   using R = typename T::R;
   const ChanDev ch = P.ch[k];
+  if (ch.kind == CHARGE_EXCHANGE) {
+    charge_exchange<F32>(P, L, o.recoil);
+    terminate<F32>(P, led, L, o);
+    return;
+  }
   const R e = T::energy(L.eq);
   if (ch.kind == IONIZATION) {
     const long long avail = L.eq - ch.loss_q;
@@ -477,7 +520,7 @@ __device__ __forceinline__ void rare_kinematics(const Params& P, unsigned long l
     }
     L.eq = eq1;
     L.mu = (double)mu_p;
-  } else {  // CLUSTERING
+  } else {  // CLUSTERING, CLUSTERING3
     die<F32>(P, led, L, R_CLUSTER, L_E_CLUSTER);
     unsigned long long wc[4];
     const unsigned evc = L.ev - 1;
@@ -563,7 +606,7 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
       cv = (R)0;
     }
     coef[c] = cv;
-    if (ch.kind != RECOMBINATION) {
+    if (!field_kind(ch.kind)) {
       gas += cv;
     } else {
       if (nrec == 0) { rc0 = (double)cv; rcol0 = P.fcol[k]; rrate0 = P.frate[k]; }
@@ -711,7 +754,7 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
     for (int c = 0; c < MAXSPCH; ++c) {
       if (c >= nsc) break;
       const int kk = P.sc[s][c];
-      const double rk = (double)coef[c] * (P.ch[kk].kind == RECOMBINATION ? P.frate[kk][jc] : nj);
+      const double rk = (double)coef[c] * (field_kind(P.ch[kk].kind) ? P.frate[kk][jc] : nj);
       if (!(rk > 0.0)) continue;
       last = c;
       cum += rk;
@@ -745,7 +788,8 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
   } else if (ch.kind == EXCITATION) {
     L.eq -= ch.loss_q;
     o.excit += (unsigned long long)ch.loss_q;
-  } else if (ch.kind == IONIZATION || ch.kind == CLUSTERING) {
+  } else if (ch.kind == IONIZATION || ch.kind == CLUSTERING || ch.kind == CLUSTERING3 ||
+             ch.kind == CHARGE_EXCHANGE) {
     if (port.rare) {
       RareBuf* rb = port.rare;
       const int i = atomicAdd(&rb->n, 1);

@@ -78,16 +78,17 @@ inline bool xs_ok(const karl_xs* x) {
   int per_sp[NSP] = {0, 0, 0}, rec_sp[NSP] = {0, 0, 0};
   for (int k = 0; k < x->n_channels; ++k) {
     const int kd = x->kind[k], si = x->species_in[k], so = x->species_out[k];
-    if (kd < 0 || kd > RECOMBINATION || si < 0 || si >= NSP || so < -1 || so >= NSP ||
+    if (kd < 0 || kd > CLUSTERING3 || si < 0 || si >= NSP || so < -1 || so >= NSP ||
         !(x->loss_ev[k] >= 0) || !host_finite(x->loss_ev[k]))
       return false;
-    if ((kd == CLUSTERING || kd == RECOMBINATION) && so < 0) return false;
+    if ((kd == CLUSTERING || kd == CLUSTERING3 || kd == RECOMBINATION) && so < 0) return false;
+    if (kd == CHARGE_EXCHANGE && si == SP_E) return false;
     if (x->target && (x->target[k] < 0 || x->target[k] > 1 || (x->target[k] == 1 && kd != ELASTIC)))
       return false;
     if (kd == RECOMBINATION && si != SP_E && so != SP_E) return false;
     if (kd == RECOMBINATION && si == SP_E && so == SP_E) return false;
     per_sp[si]++;
-    if (kd == RECOMBINATION) rec_sp[si]++;
+    if (field_kind(kd)) rec_sp[si]++;
     for (int i = 0; i < x->n_energy; ++i) {
       const double v = x->sigma_m2[(size_t)k * x->n_energy + i];
       if (!(v >= 0) || !host_finite(v)) return false;
@@ -124,6 +125,25 @@ inline ColumnTables column_tables(const double* nseg, int nz, double length) {
     t.ginv[q] = k;
   }
   return t;
+}
+
+// Gas density squared per segment and its column to each face: the field of
+// three-body clustering, whose rate per unit path is sigma(E) n^2.
+inline void square_column(const double* nseg, int nz, double length, std::vector<double>& n2,
+                          std::vector<double>& col2) {
+  const double dz = length / nz;
+  n2.resize(nz);
+  col2.assign(nz + 1, 0.0);
+  for (int j = 0; j < nz; ++j) {
+    n2[j] = nseg[j] * nseg[j];
+    col2[j + 1] = col2[j] + n2[j] * dz;
+  }
+}
+
+inline bool has_kind(const karl_xs* x, int kind) {
+  for (int k = 0; k < x->n_channels; ++k)
+    if (x->kind[k] == kind) return true;
+  return false;
 }
 
 // The physics model shared by every run of a context or server.

@@ -84,6 +84,7 @@ struct karl_ctx {
   double colmax = 0;
   DevBuf<float> d_sigf;
   DevBuf<double> d_ang_pdf, d_ang_cum;       // scattering-angle tables (empty: isotropic)
+  DevBuf<double> d_n2, d_col2;               // n^2 and its column (three-body clustering)
   DevBuf<float> d_ang_pdff, d_ang_cumf;
   cudaStream_t cancel_stream = nullptr;
   // device work buffers
@@ -345,6 +346,11 @@ void base_params(const karl_ctx* c, Params& P, const karl_run_opts* o, int pass)
   P.ginv = c->nq > 0 ? c->d_ginv.p : nullptr;
   P.sig = c->d_sig_t.p;
   P.sigf = c->d_sigf.p;
+  for (int k = 0; k < c->nch; ++k)
+    if (c->kind[k] == CLUSTERING3) {
+      P.frate[k] = c->d_n2.p;
+      P.fcol[k] = c->d_col2.p;
+    }
   if (c->model.ang_sets > 0) {
     P.ang_pdf = c->d_ang_pdf.p;
     P.ang_cum = c->d_ang_cum.p;
@@ -616,6 +622,18 @@ karl_status karl_create(const karl_geometry* g, const karl_xs* x, karl_ctx** out
         cudaMemcpy(ctx->d_sig_t.p, sig_t.data(), sig_t.size() * 8, cudaMemcpyHostToDevice) ||
         cudaMemcpy(ctx->d_sigf.p, sigf.data(), sigf.size() * 4, cudaMemcpyHostToDevice))))
     return bail(KARL_ECUDA);
+  if (has_kind(x, CLUSTERING3)) {
+    std::vector<double> n2, col2;
+    try {
+      square_column(ctx->nseg.data(), ctx->nz, ctx->L, n2, col2);
+    } catch (...) {
+      return bail(KARL_ENOMEM);
+    }
+    if (ctx->d_n2.ensure(ctx->nz) || ctx->d_col2.ensure(ctx->nz + 1)) return bail(KARL_ENOMEM);
+    if (cudaMemcpy(ctx->d_n2.p, n2.data(), ctx->nz * 8, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(ctx->d_col2.p, col2.data(), (ctx->nz + 1) * 8, cudaMemcpyHostToDevice))
+      return bail(KARL_ECUDA);
+  }
   {
     std::vector<double> apdf, acum;
     std::vector<float> apdff, acumf;
@@ -813,6 +831,7 @@ void karl_destroy(karl_ctx* ctx) {
   ctx->d_sig_t.release();
   ctx->d_ang_pdf.release(); ctx->d_ang_cum.release(); ctx->d_ang_pdff.release();
   ctx->d_ang_cumf.release();
+  ctx->d_n2.release(); ctx->d_col2.release();
   ctx->d_ginv.release();
   ctx->d_faces.release();
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);

@@ -16,7 +16,15 @@ constexpr int MAXSPCH = 10;       // active channels of one species
 constexpr int LEDGER = 64;
 constexpr int NREASON = 8;
 
-enum { ELASTIC = 0, IONIZATION = 1, EXCITATION = 2, CLUSTERING = 3, RECOMBINATION = 4 };
+enum { ELASTIC = 0, IONIZATION = 1, EXCITATION = 2, CLUSTERING = 3, RECOMBINATION = 4,
+       CHARGE_EXCHANGE = 5, CLUSTERING3 = 6 };
+
+// channels whose rate per unit path follows a field other than the gas density
+// n(z): recombination (the partner's target field) and three-body clustering
+// (n(z)^2); their flights invert that field's column beside the gas column
+__host__ __device__ __forceinline__ bool field_kind(int kind) {
+  return kind == RECOMBINATION || kind == CLUSTERING3;
+}
 enum { SP_E = 0 };
 enum { R_EXIT0 = 0, R_EXIT1 = 1, R_CUTOFF = 2, R_CAP_COLL = 3, R_CAP_TIME = 4,
        R_RECOMB = 5, R_CLUSTER = 6, R_STALLED = 7 };

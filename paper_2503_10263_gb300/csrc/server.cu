@@ -108,6 +108,7 @@ struct Request {
   int n_passes = 1;
   karl_tallies out;
   ColumnTables tabs;
+  std::vector<double> n2, col2;      // three-body clustering field (empty if unused)
   // device pointers of the final pass and of the outputs, for collection
   unsigned long long *spec = nullptr, *rec = nullptr, *led = nullptr, *chan = nullptr;
   unsigned long long *time_out = nullptr, *cpos = nullptr, *cneg = nullptr;
@@ -307,6 +308,13 @@ karl_status admit(karl_server* srv, Request& r) {
   SCK(cudaMemcpyAsync(faces, r.tabs.faces.data(), (z.nz + 1) * 8, cudaMemcpyHostToDevice, cs));
   SCK(cudaMemcpyAsync(ginv, r.tabs.ginv.data(), (z.nq + 1) * 4, cudaMemcpyHostToDevice, cs));
   SCK(zero_by_copy(srv, tally0, tally_bytes, cs));
+  for (int c = 0; c < srv->model.nch; ++c)
+    if (srv->model.kind[c] == CLUSTERING3) {
+      SCK(cudaMemcpyAsync(frate + (size_t)c * z.nz, r.n2.data(), z.nz * 8,
+                          cudaMemcpyHostToDevice, cs));
+      SCK(cudaMemcpyAsync(fcol + (size_t)c * (z.nz + 1), r.col2.data(), (z.nz + 1) * 8,
+                          cudaMemcpyHostToDevice, cs));
+    }
   // descriptor
   const int final_pass = (r.n_passes == 2 && has_recombination(srv->model)) ? 2 : 1;
   SlotDesc& d = srv->h_desc[slot];
@@ -336,12 +344,11 @@ karl_status admit(karl_server* srv, Request& r) {
     P.ledger = pb[k].led;
     P.chan_count = pb[k].chan;
     P.per_primary = nullptr;
-    if (k == 1)
-      for (int c = 0; c < srv->model.nch; ++c)
-        if (srv->model.kind[c] == RECOMBINATION) {
-          P.frate[c] = frate + (size_t)c * z.nz;
-          P.fcol[c] = fcol + (size_t)c * (z.nz + 1);
-        }
+    for (int c = 0; c < srv->model.nch; ++c)
+      if ((k == 1 && srv->model.kind[c] == RECOMBINATION) || srv->model.kind[c] == CLUSTERING3) {
+        P.frate[c] = frate + (size_t)c * z.nz;
+        P.fcol[c] = fcol + (size_t)c * (z.nz + 1);
+      }
   }
   d.n_passes = final_pass;
   d.n_prim = (long long)z.n;
@@ -695,6 +702,9 @@ karl_status karl_server_submit(karl_server* srv, const karl_geometry* g, const k
     r.e.assign(pr->e_ev, pr->e_ev + pr->n);
     r.mu.assign(pr->mu, pr->mu + pr->n);
     r.sp.assign(pr->species, pr->species + pr->n);
+    bool three_body = false;
+    for (int c = 0; c < srv->model.nch; ++c) three_body |= srv->model.kind[c] == CLUSTERING3;
+    if (three_body) square_column(r.nseg.data(), g->n_zbins, g->length_m, r.n2, r.col2);
   } catch (...) {
     return sfail(srv, KARL_ENOMEM, "host copy of the request");
   }

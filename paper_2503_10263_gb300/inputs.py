@@ -481,3 +481,50 @@ def uniform_problem(n_seg_m3: float, length: float, nz: int, channels: List[Chan
 def beam(n: int, z0: float, e_ev: float, mu: float, species: int = E) -> Primaries:
     return Primaries(np.full(n, z0), np.full(n, e_ev), np.full(n, mu),
                      np.full(n, species, np.uint8), n)
+
+
+# ---------------------------------------------------------------------------
+# ion chemistry (Sec. 3.3 Clustering, Charge exchange, Ionization)
+
+def ion_chemistry_channels(nodes: np.ndarray, k_ter: float = 2.6e-41,
+                           sigma_cx: float = 1e-18) -> List[Channel]:
+    """T+ from dissociative ionization, its three-body clustering to T3+
+    (table k_ter / v) and its recombination with the electron field, and
+    T2+ charge exchange (constant synthetic cross section)."""
+    return [dissociative_ionization(nodes),
+            Channel("clustering3_T+", CLUSTERING3, TP, T3P, 0.0, rate_sigma(nodes, k_ter, M_TP_EV)),
+            Channel("recomb_T+_e", RECOMBINATION, TP, E, 0.0, recomb_sigma(nodes)),
+            Channel("charge_exchange_T2+", CHARGE_EXCHANGE, T2P, -1, 0.0,
+                    np.full_like(nodes, sigma_cx))]
+
+
+def chemistry_config(n_decays: int = 3000, seed: int = 1, column_m2: float = 2e21,
+                     length: float = 4.0, nz: int = 100, k_ter: float = 2.6e-39):
+    """Config-2 physics plus the further ion chemistry of ion_chemistry_channels,
+    with the three-body rate raised (default 100 x the paper's 2.6e-41 m^6/s)
+    so that T+ clusters within the column; two passes."""
+    n0 = parabolic_n0(column_m2, length)
+    prob = _problem("chemistry", length, nz, parabolic_segment_means(n0, length, nz), full=True)
+    prob.channels += ion_chemistry_channels(prob.energy_nodes(), k_ter=k_ter)
+    return prob, decay_primaries(prob, n_decays, seed)
+
+
+def ion_beam_problem(chans: List[Channel], n_seg: np.ndarray, length: float, e_min: float,
+                     e_max: float, **kw) -> Problem:
+    """Ion test geometry: the given gas profile, 64-node tables over
+    [e_min, e_max], no energy cut."""
+    prob = uniform_problem(1.0, length, len(n_seg), chans, n_energy=64, e_min=e_min, e_max=e_max,
+                           e_cut=0.0, **kw)
+    prob.n_seg_m3 = np.asarray(n_seg, np.float64)
+    return prob
+
+
+def charge_exchange_problem(n_m3: float, length: float, nz: int, t_k: float,
+                            sigma_m2: float = 1e-19, **kw) -> Problem:
+    """T2+ charge exchange as the only channel (constant cross section) in a
+    uniform T2 gas at temperature t_k."""
+    nodes = energy_nodes(64, 1e-5, 100.0)
+    ch = Channel("cx", CHARGE_EXCHANGE, T2P, -1, 0.0, np.full_like(nodes, sigma_m2))
+    prob = ion_beam_problem([ch], np.full(nz, n_m3), length, 1e-5, 100.0, **kw)
+    prob.gas_temperature_k = t_k
+    return prob

@@ -108,3 +108,24 @@ def test_create_rejects_invalid_angle_tables_without_gpu(karl):
         with pytest.raises(karl.KarlError) as ei:
             karl.Context(p)
         assert ei.value.status == karl.EINVAL
+
+
+def test_create_rejects_invalid_ion_chemistry_without_gpu(karl):
+    nodes = inputs.energy_nodes(64, 1.0, 2e4)
+    bad = [
+        # charge exchange of an electron
+        [inputs.Channel("cx", inputs.CHARGE_EXCHANGE, inputs.E, -1, 0.0, np.ones(64) * 1e-20)],
+        # three-body clustering without a product
+        [inputs.Channel("c3", inputs.CLUSTERING3, inputs.TP, -1, 0.0, np.ones(64) * 1e-40)],
+        # three field-rate channels on one species
+        [inputs.Channel("c3", inputs.CLUSTERING3, inputs.TP, inputs.T3P, 0.0, np.ones(64)),
+         inputs.Channel("r1", inputs.RECOMBINATION, inputs.TP, inputs.E, 0.0, np.ones(64)),
+         inputs.Channel("c3b", inputs.CLUSTERING3, inputs.TP, inputs.T3P, 0.0, np.ones(64))],
+        # unknown kind
+        [inputs.Channel("x", 7, inputs.TP, inputs.T3P, 0.0, np.ones(64))],
+    ]
+    for chans in bad:
+        p = inputs.uniform_problem(1e20, 1.0, 10, chans, n_energy=64)
+        with pytest.raises(karl.KarlError) as ei:
+            karl.Context(p)
+        assert ei.value.status == karl.EINVAL

@@ -1,0 +1,205 @@
+"""Ion chemistry on the GPU (Sec. 3.3 Clustering, Charge exchange,
+Ionization; Sec. 4 Clustering and Charge Exchange cases) against the FP64
+oracle and the closed forms the oracle is pinned to: three-body and
+rate-coefficient clustering of T+, the n(z)^2 column, charge exchange
+energies against quadrature of the relative-speed-weighted Maxwellian, T+
+from dissociative ionization, and a two-pass mixed run matched with the
+oracle, single and served."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2503_10263_gb300 import inputs
+from tests import closed_forms as cf
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_test_cases.json")))
+KB = 8.617333262e-5
+PREC = ["fp64", "fp32"]
+
+
+@pytest.fixture(scope="module")
+def karl():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2503_10263_gb300 import karl as k
+    return k
+
+
+def _prec(karl, name):
+    return karl.FP64 if name == "fp64" else karl.FP32
+
+
+def _quant(e):
+    return math.floor(e * 2**24) / 2**24
+
+
+@pytest.mark.parametrize("precision", PREC)
+@pytest.mark.parametrize("case", ["clustering_tp_tertiary", "clustering_tp_radiative"])
+def test_tp_clustering(karl, case, precision):
+    g = GOLD[case]
+    e0 = g["e_ion_ev"]
+    nodes = inputs.energy_nodes(64, e0, 10.0)
+    three = case.endswith("tertiary")
+    k = g["k_m6ps"] if three else g["k_m3ps"]
+    kind = inputs.CLUSTERING3 if three else inputs.CLUSTERING
+    ch = inputs.Channel("clust", kind, inputs.TP, inputs.T3P, 0.0,
+                        inputs.rate_sigma(nodes, k, inputs.M_TP_EV))
+    nm = g["n_m3"]
+    v_table = cf.speed(e0, inputs.M_TP_EV)
+    lam = v_table / (k * nm ** (2 if three else 1))
+    length, nz = 8.0 * lam, 40
+    prob = inputs.ion_beam_problem([ch], np.full(nz, nm), length, e0, 10.0)
+    n = g["n_events"]
+    beam = inputs.beam(n, 0.0, e0, 1.0, inputs.TP)
+    r = karl.Context(prob).run(beam, seed=13, precision=_prec(karl, precision))
+    assert parity.ledger_balances(r["ledger"])
+    z = np.linspace(0.0, length, nz + 1)
+    emp = r["cross_pos"][inputs.TP].astype(np.float64) / n
+    assert np.max(np.abs(emp[1:] - np.exp(-z[1:] / lam))) < 1.95 / math.sqrt(n)
+    time = r["time_fx"][inputs.TP].astype(np.float64).sum() / 2**50
+    count = int(r["chan_count"][0])
+    k_hat = count / time / nm ** (2 if three else 1)
+    assert k_hat * cf.speed(_quant(e0), inputs.M_TP_EV) / v_table == \
+        pytest.approx(k, rel=g["rel_err"])
+    assert r["ledger"][karl.BIRTHS + inputs.T3P] == count
+    if precision == "fp64":
+        o = oracle.run(prob, beam, seed=13, n_threads=8)
+        assert float(np.mean(r["per_primary"] == o["per_primary"])) >= 0.995
+        assert abs(count - int(o["chan_count"][0])) <= max(5, 1e-3 * count)
+
+
+@pytest.mark.parametrize("precision", PREC)
+def test_three_body_rate_follows_density_squared(karl, precision):
+    nz, length = 40, 1.0
+    n_seg = np.linspace(2e21, 2e22, nz)
+    dz = length / nz
+    s3 = 1.0 / float(np.sum(n_seg ** 2) * dz)
+    nodes = inputs.energy_nodes(64, 1e-3, 10.0)
+    ch = inputs.Channel("clust3", inputs.CLUSTERING3, inputs.TP, inputs.T3P, 0.0,
+                        np.full_like(nodes, s3))
+    prob = inputs.ion_beam_problem([ch], n_seg, length, 1e-3, 10.0)
+    n = 200_000
+    r = karl.Context(prob).run(inputs.beam(n, 0.0, 0.05, 1.0, inputs.TP), seed=14,
+                               precision=_prec(karl, precision), per_primary=False)
+    col2 = np.concatenate([[0.0], np.cumsum(n_seg ** 2) * dz])
+    emp = r["cross_pos"][inputs.TP].astype(np.float64) / n
+    assert np.max(np.abs(emp[1:] - np.exp(-s3 * col2[1:]))) < 1.95 / math.sqrt(n)
+
+
+@pytest.mark.parametrize("precision", PREC)
+def test_charge_exchange_one_collision_energy(karl, precision):
+    g = GOLD["charge_exchange"]
+    prob = inputs.charge_exchange_problem(2e20, 1.0, 10, g["t_k"], max_collisions=1)
+    n = 1_000_000
+    e0 = g["e_ion_ev"]
+    r = karl.Context(prob).run(inputs.beam(n, 0.0, e0, 1.0, inputs.T2P), seed=15,
+                               precision=_prec(karl, precision), per_primary=False)
+    L = r["ledger"]
+    assert parity.ledger_balances(L)
+    assert L[karl.N_COLLISIONS] == n and L[karl.DEATHS + inputs.T2P * 8 + 3] == n
+    m1, mt = inputs.M_T2P_EV, inputs.M_T2_EV
+    a2 = KB * g["t_k"] / mt
+    m2, m4 = cf.cx_one_collision_speed_moments(math.sqrt(2.0 * _quant(e0) / m1 / a2))
+    scale = 0.5 * m1 * a2
+    mean_e = L[karl.E_CAP] / 2**24 / n
+    sd = scale * math.sqrt(m4 - m2 * m2)
+    assert abs(mean_e - scale * m2) < 5 * sd / math.sqrt(n)
+
+
+def test_charge_exchange_matched_with_oracle(karl):
+    g = GOLD["charge_exchange"]
+    prob = inputs.charge_exchange_problem(2e20, 1.0, 10, g["t_k"], max_collisions=1)
+    n = 100_000
+    beam = inputs.beam(n, 0.0, g["e_ion_ev"], 1.0, inputs.T2P)
+    a = karl.Context(prob).run(beam, seed=15, per_primary=False)
+    o = oracle.run(prob, beam, seed=15, n_threads=8)
+    # same target draws: the summed energies agree to rounding of single draws
+    assert abs(int(a["ledger"][karl.E_CAP]) - int(o["ledger"][oracle.E_CAP])) <= \
+        1e-6 * int(o["ledger"][oracle.E_CAP])
+
+
+@pytest.mark.parametrize("precision", PREC)
+def test_charge_exchange_stationary_energy(karl, precision):
+    g = GOLD["charge_exchange"]
+    prob = inputs.charge_exchange_problem(1e21, 2.0, 20, g["t_k"], max_collisions=64)
+    n = 200_000
+    rng = np.random.default_rng(2)
+    prims = inputs.Primaries(np.full(n, 1.0), np.full(n, g["e_ion_ev"]), rng.uniform(-1, 1, n),
+                             np.full(n, inputs.T2P, np.uint8), n)
+    r = karl.Context(prob).run(prims, seed=16, precision=_prec(karl, precision),
+                               per_primary=False)
+    L = r["ledger"]
+    assert parity.ledger_balances(L)
+    assert L[karl.DEATHS + inputs.T2P * 8 + 3] == n
+    m1, mt = inputs.M_T2P_EV, inputs.M_T2_EV
+    a2 = KB * g["t_k"] / mt
+    m2, m4 = cf.cx_stationary_speed_moments()
+    scale = 0.5 * m1 * a2
+    mean_e = L[karl.E_CAP] / 2**24 / n
+    sd = scale * math.sqrt(m4 - m2 * m2)
+    assert abs(mean_e - scale * m2) < 5 * sd / math.sqrt(n)
+
+
+def test_dissociative_ionization_makes_tp(karl):
+    nodes = inputs.energy_nodes(2048, 1.0, 2e4)
+    chans = [inputs.Channel("ion", inputs.IONIZATION, inputs.E, inputs.T2P, 15.4,
+                            inputs.born_bethe(nodes, 15.4, 4.2)),
+             inputs.dissociative_ionization(nodes)]
+    prob = inputs.uniform_problem(1e20, 1.0, 10, chans, e_cut=1.0)
+    n = 50_000
+    beam = inputs.beam(n, 0.5, 200.0, 1.0)
+    r = karl.Context(prob).run(beam, seed=17)
+    o = oracle.run(prob, beam, seed=17, n_threads=8)
+    L, c = r["ledger"], r["chan_count"]
+    assert parity.ledger_balances(L)
+    assert c[1] > 0
+    assert L[karl.BIRTHS + inputs.TP] == c[1]
+    assert L[karl.BIRTHS + inputs.T2P] == c[0]
+    assert L[karl.N_SPAWN_ION] == c[0] + c[1]
+    assert float(np.mean(r["per_primary"] == o["per_primary"])) >= 0.995
+
+
+@pytest.fixture(scope="module")
+def mixed():
+    prob, prims = inputs.chemistry_config(3000, seed=2)
+    return prob, prims, oracle.run(prob, prims, seed=5, n_threads=8)
+
+
+def test_mixed_chemistry_two_pass_matched(karl, mixed):
+    prob, prims, o = mixed
+    g = karl.Context(prob).run(prims, seed=5)
+    assert parity.ledger_balances(g["ledger"])
+    assert float(np.mean(g["per_primary"] == o["per_primary"])) >= 0.99
+    assert parity.rel_l2(g["field"], o["field"]) < 1e-3
+    for k in ("spectrum", "cross_pos"):
+        z, p = parity.poisson_two_sample(g[k], o[k])
+        assert parity.excursions_ok(z) and p > 0.01, k
+    cg, co = g["chan_count"].astype(float), o["chan_count"].astype(float)
+    assert np.all(np.abs(cg - co) <= 5 * np.sqrt(cg + co) + 0.01 * co)
+    names = [c.name for c in prob.channels]
+    for nm in ("dissociative_ionization", "clustering3_T+", "charge_exchange_T2+"):
+        assert cg[names.index(nm)] > 0, nm
+
+
+@pytest.mark.parametrize("precision", PREC)
+def test_mixed_chemistry_served_equals_single_run(karl, mixed, precision):
+    prob, prims, _ = mixed
+    single = karl.Context(prob).run(prims, seed=5, precision=_prec(karl, precision),
+                                    per_primary=False)
+    srv = karl.Server(prob, precision=_prec(karl, precision))
+    try:
+        rid = srv.submit(prob, prims, seed=5)
+        srv.run_all()
+        done, t = srv.poll(rid)
+    finally:
+        srv.close()
+    assert done
+    for k in ("spectrum", "time_fx", "cross_pos", "cross_neg", "recomb", "ledger", "chan_count"):
+        np.testing.assert_array_equal(t[k], single[k], err_msg=k)

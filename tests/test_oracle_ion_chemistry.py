@@ -25,11 +25,8 @@ def _quant(e):
     return math.floor(e * 2**24) / 2**24
 
 
-def _ion_problem(chans, n_seg, length, e_min, e_max, **kw):
-    prob = inputs.uniform_problem(1.0, length, len(n_seg), chans, n_energy=64, e_min=e_min,
-                                  e_max=e_max, e_cut=0.0, **kw)
-    prob.n_seg_m3 = np.asarray(n_seg, np.float64)
-    return prob
+_ion_problem = inputs.ion_beam_problem
+_cx_problem = inputs.charge_exchange_problem
 
 
 def _attenuation(prob, r, n, lam, length, sp):
@@ -96,15 +93,6 @@ def test_three_body_rate_follows_density_squared():
 
 # ---------------------------------------------------------------------------
 # charge exchange (Sec. 3.3; Sec. 4 Charge Exchange: one exchange thermalises)
-
-def _cx_problem(n_m3, length, nz, t_k, **kw):
-    nodes = inputs.energy_nodes(64, 1e-5, 100.0)
-    ch = inputs.Channel("cx", inputs.CHARGE_EXCHANGE, inputs.T2P, -1, 0.0,
-                        np.full_like(nodes, 1e-19))
-    prob = _ion_problem([ch], np.full(nz, n_m3), length, 1e-5, 100.0, **kw)
-    prob.gas_temperature_k = t_k
-    return prob
-
 
 def test_charge_exchange_takes_the_target_velocity():
     prob = _cx_problem(1e20, 1.0, 10, 80.0)
