@@ -15,6 +15,13 @@ namespace karl {
 constexpr double HOST_Q_ENERGY = 16777216.0;    // 2^24 units per eV
 constexpr double HOST_KB_EV = 8.617333262e-5;   // Boltzmann constant, eV/K
 
+// Three-body clustering coefficients (k_ter / v, of order 1e-44 m^5) lie below
+// the FP32 range.  Their table rows are kept multiplied by 2^128 and the n^2
+// field by 2^-128: a power-of-two rescaling of both factors, exact in FP64,
+// that leaves every product sigma n^2 unchanged.
+constexpr double THREE_BODY_SCALE = 340282366920938463463374607431768211456.0;   // 2^128
+constexpr double THREE_BODY_HALF_INV = 1.0 / 18446744073709551616.0;             // 2^-64
+
 inline bool host_finite(double x) { return std::isfinite(x); }
 
 // Geometry checks of karl_create (no CUDA call).
@@ -92,6 +99,7 @@ inline bool xs_ok(const karl_xs* x) {
     for (int i = 0; i < x->n_energy; ++i) {
       const double v = x->sigma_m2[(size_t)k * x->n_energy + i];
       if (!(v >= 0) || !host_finite(v)) return false;
+      if (kd == CLUSTERING3 && !(v < 1e250)) return false;       // stays finite when scaled
     }
   }
   for (int s = 0; s < NSP; ++s)
@@ -127,15 +135,16 @@ inline ColumnTables column_tables(const double* nseg, int nz, double length) {
   return t;
 }
 
-// Gas density squared per segment and its column to each face: the field of
-// three-body clustering, whose rate per unit path is sigma(E) n^2.
+// Gas density squared per segment (times 2^-128) and its column to each face:
+// the field of three-body clustering, whose rate per unit path is sigma n^2.
 inline void square_column(const double* nseg, int nz, double length, std::vector<double>& n2,
                           std::vector<double>& col2) {
   const double dz = length / nz;
   n2.resize(nz);
   col2.assign(nz + 1, 0.0);
   for (int j = 0; j < nz; ++j) {
-    n2[j] = nseg[j] * nseg[j];
+    const double h = nseg[j] * THREE_BODY_HALF_INV;
+    n2[j] = h * h;
     col2[j + 1] = col2[j] + n2[j] * dz;
   }
 }
@@ -285,14 +294,15 @@ inline bool has_recombination(const ModelInfo& m) {
 }
 
 // [node][channel] copies of the cross sections (all channels of one node in
-// adjacent words) for the transport kernels.
+// adjacent words) for the transport kernels; three-body rows times 2^128.
 inline void node_major_tables(const karl_xs* x, std::vector<double>& sig_t, std::vector<float>& sigf) {
   const size_t n = (size_t)x->n_channels * x->n_energy;
   sig_t.assign(n, 0.0);
   sigf.assign(n, 0.0f);
   for (int k = 0; k < x->n_channels; ++k)
     for (int i = 0; i < x->n_energy; ++i) {
-      const double v = x->sigma_m2[(size_t)k * x->n_energy + i];
+      const double v = x->sigma_m2[(size_t)k * x->n_energy + i] *
+                       (x->kind[k] == CLUSTERING3 ? THREE_BODY_SCALE : 1.0);
       sig_t[(size_t)i * x->n_channels + k] = v;
       sigf[(size_t)i * x->n_channels + k] = (float)v;
     }
