@@ -147,7 +147,7 @@ class _Marshal:
         s.n_tebins = prob.n_tebins
         s.n_spec_bins = prob.n_spec_bins
         s.spec_bin_ev = prob.spec_bin_ev
-        for i in range(3):
+        for i in range(N_SPECIES):
             s.species_mass_ev[i] = float(prob.species_mass_ev[i])
         s.target_mass_ev = prob.target_mass_ev
         s.n_energy = prob.n_energy

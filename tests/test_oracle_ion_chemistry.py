@@ -64,7 +64,7 @@ def test_tp_clustering_attenuation_and_inferred_rate(case):
     count = int(r["chan_count"][0])
     k_hat = count / time / nm ** (2 if three else 1)
     assert k_hat * cf.speed(_quant(e0), inputs.M_TP_EV) / v_table == \
-        pytest.approx(k, rel=g["rel_err"])
+        pytest.approx(k, rel=g["rel_err"], abs=0)
     L = r["ledger"]
     assert L[oracle.DEATHS + inputs.TP * 8 + 6] == count          # T+ consumed
     assert L[oracle.BIRTHS + inputs.T3P] == count                 # one T3+ each
@@ -100,7 +100,7 @@ def test_charge_exchange_takes_the_target_velocity():
     for i in range(20):
         e1, mu1, v2 = oracle.charge_exchange(prob, m1, 10.0, 0.3, [i, 7, 4], [5, 11])
         s2 = float(np.dot(v2, v2))
-        assert e1 == pytest.approx(0.5 * m1 * s2, rel=1e-12)
+        assert e1 == pytest.approx(0.5 * m1 * s2, rel=1e-12, abs=0)
         assert mu1 == pytest.approx(v2[2] / math.sqrt(s2), abs=1e-12)
 
 

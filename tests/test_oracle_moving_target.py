@@ -67,10 +67,10 @@ def test_momentum_and_energy_are_conserved(species):
         k0 = 0.5 * m1 * v1 @ v1 + 0.5 * m2 * v2 @ v2
         k1 = 0.5 * m1 * v1n @ v1n + 0.5 * m2 * v2n @ v2n
         assert abs(k1 - k0) <= 1e-11 * k0
-        assert e1 == pytest.approx(0.5 * m1 * v1n @ v1n, rel=1e-12)
+        assert e1 == pytest.approx(0.5 * m1 * v1n @ v1n, rel=1e-12, abs=0)
         assert mu1 == pytest.approx(v1n[2] / np.linalg.norm(v1n), abs=1e-12)
         # the impactor before the collision is the one given
-        assert 0.5 * m1 * v1 @ v1 == pytest.approx(e, rel=1e-12)
+        assert 0.5 * m1 * v1 @ v1 == pytest.approx(e, rel=1e-12, abs=0)
         assert v1[2] / np.linalg.norm(v1) == pytest.approx(mu, abs=1e-12)
 
 
