@@ -339,7 +339,14 @@ __global__ void __launch_bounds__(256, 2) multi_kernel(SlotDesc* D, SlotCtl* C, 
               const unsigned long long old =
                   atomicAdd(word, ((unsigned long long)k << 32) + (unsigned long long)k);
               const long long next = (long long)(old >> 32);
-              if (next + k >= n) atomicAnd(&M->bitmap[wi], ~(1u << bit));
+              // Only the claim that takes the last primaries clears the bit.  A
+              // claim made on a pass that had just ended (state read as pass 1
+              // while the pass completed) gets nothing and must not clear it:
+              // the warp completing pass 1 sets the bit again for pass 2, and a
+              // late clear would leave pass 2's primaries unclaimed for good.
+              // The taking claim holds live particles, so the pass cannot end
+              // before its clear.
+              if (next < n && next + k >= n) atomicAnd(&M->bitmap[wi], ~(1u << bit));
               const long long left = n - next;
               const int g = left <= 0 ? 0 : (left < k ? (int)left : k);
               if (g < k) {

@@ -164,7 +164,7 @@ struct karl_server {
 namespace {
 
 karl_status sfail(karl_server* s, karl_status st, const char* fmt, ...) {
-  char buf[512];
+  char buf[2048];
   va_list ap;
   va_start(ap, fmt);
   vsnprintf(buf, sizeof buf, fmt, ap);
@@ -468,6 +468,29 @@ karl_status reap_launch(karl_server* srv) {
   if (hc.error != 0) {
     const karl_status st = hc.error == ERR_TIMEOUT ? KARL_ETIMEOUT
                          : hc.error == ERR_CANCELLED ? KARL_ECANCELLED : KARL_ECAPACITY;
+    // what the stopped launch left unfinished, for the error message
+    std::string detail;
+    {
+      MultiCtl hm;
+      std::vector<SlotCtl> hs(MAX_SLOTS);
+      if (cudaMemcpy(&hm, srv->d_M, sizeof hm, cudaMemcpyDeviceToHost) == cudaSuccess &&
+          cudaMemcpy(hs.data(), srv->d_ctl, sizeof(SlotCtl) * MAX_SLOTS,
+                     cudaMemcpyDeviceToHost) == cudaSuccess) {
+        char b[256];
+        snprintf(b, sizeof b, "; published %llu adopted %llu done %llu ring head %llu tail %llu",
+                 hm.published, hm.adopted, hm.done_count, hm.c.head, hm.c.tail);
+        detail += b;
+        for (auto& kv : srv->reqs) {
+          const Request& r = kv.second;
+          if (r.state != REQ_ADMITTED || srv->h_done[r.slot]) continue;
+          const SlotCtl& c = hs[r.slot];
+          snprintf(b, sizeof b, "; slot %d state %d pass %d claimed/live %llu/%llu %llu/%llu of %zu",
+                   r.slot, c.state, c.pass, c.word[0] >> 32, c.word[0] & 0xffffffffULL,
+                   c.word[1] >> 32, c.word[1] & 0xffffffffULL, r.z.size());
+          detail += b;
+        }
+      }
+    }
     for (auto& kv : srv->reqs) {
       Request& r = kv.second;
       if (r.state == REQ_ADMITTED && !srv->h_done[r.slot]) {
@@ -485,7 +508,7 @@ karl_status reap_launch(karl_server* srv) {
       // (re)allocate a larger ring
       return sfail(srv, KARL_ECAPACITY, "particle ring overflow; grown for later requests");
     }
-    return sfail(srv, st, "launch stopped (error %d)", hc.error);
+    return sfail(srv, st, "launch stopped (error %d)%s", hc.error, detail.c_str());
   }
   return KARL_OK;
 }

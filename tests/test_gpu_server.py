@@ -144,3 +144,30 @@ def test_empty_request_and_invalid_submit(karl):
     with pytest.raises(karl.KarlError):
         srv.poll(rid)                              # already collected
     srv.close()
+
+
+@pytest.mark.parametrize("prec_name", ["fp64", "fp32"])
+def test_many_small_requests_all_finish(karl, prec_name):
+    # many short two-pass requests in one launch: many pass transitions race
+    # with warps claiming primaries; every request must finish and equal its
+    # single run
+    prec = karl.FP32 if prec_name == "fp32" else karl.FP64
+    rng = np.random.default_rng(21)
+    reqs = []
+    for i in range(48):
+        col = rng.uniform(0.1, 1.0) * 5e21
+        length = rng.uniform(2.0, 10.0)
+        n0 = inputs.parabolic_n0(col, length)
+        prob = inputs._problem(f"s{i}", length, 100, inputs.parabolic_segment_means(n0, length, 100),
+                               full=True)
+        reqs.append((prob, inputs.decay_primaries(prob, int(rng.integers(5, 60)), 300 + i), 900 + i))
+    for rep in range(3):
+        srv = karl.Server(reqs[0][0], precision=prec, hbm_budget_bytes=2 << 30, timeout_s=30)
+        ids = [srv.submit(p, pr, s) for p, pr, s in reqs]
+        srv.run_all()
+        for (p, pr, s), rid in zip(reqs, ids):
+            done, t = srv.poll(rid)
+            assert done
+            if rep == 0:
+                _same(t, _single(karl, p, pr, s, prec))
+        srv.close()
