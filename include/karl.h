@@ -320,6 +320,13 @@ const char* karl_last_error(const karl_ctx* ctx);
  * karl_server_run_all(), which publishes them, runs them in one persistent
  * launch and collects every result.  The server API is not thread-safe:
  * serialise calls on one server.
+ *
+ * A launch holds every SM of the device from the first admitted request
+ * until karl_server_run_all() or karl_server_destroy() closes it.  Meanwhile
+ * other kernels on the device (a karl_run, a memset, another library's work)
+ * wait for it, and so do calls that synchronise the whole device
+ * (cudaDeviceSynchronize, cudaFree).  Contexts take their device memory from
+ * a stream-ordered pool, so creating and destroying them does not wait.
  */
 typedef struct karl_server karl_server;
 

@@ -35,26 +35,105 @@ namespace {
 const double Q_TIME = 1125899906842624.0;
 const double C_LIGHT = 299792458.0;
 
+// Device memory of contexts comes from a library-wide memory pool per device,
+// allocated and freed in stream order on a library stream.  A plain cudaFree
+// waits for every kernel on the device -- also for a served session's
+// persistent launch, which runs until its session closes, so a context freed
+// meanwhile (by a destructor, from any thread) would stall both.  Pool frees
+// wait for nothing, and the pool keeps freed memory for later contexts.
+struct DevicePools {
+  std::mutex m;
+  cudaMemPool_t pool[64] = {};
+  cudaStream_t stream[64] = {};
+};
+DevicePools& device_pools() {
+  static DevicePools d;
+  return d;
+}
+
+// The pool and the allocation stream of the current device (created once).
+cudaError_t current_pool(cudaMemPool_t* pool, cudaStream_t* st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  DevicePools& d = device_pools();
+  std::lock_guard<std::mutex> lk(d.m);
+  if (!d.pool[dev]) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    e = cudaMemPoolCreate(&p, &props);
+    if (e != cudaSuccess) return e;
+    unsigned long long keep = ~0ULL;                 // never hand freed memory back
+    e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    cudaStream_t s = nullptr;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(p);
+      return e;
+    }
+    d.pool[dev] = p;
+    d.stream[dev] = s;
+  }
+  *pool = d.pool[dev];
+  *st = d.stream[dev];
+  return cudaSuccess;
+}
+
+// Buffers replaced by a larger one while a call runs may still be read by work
+// that call queued; they are kept as `retired` and freed at the start of the
+// context's next call (every call returns only after its work is done).
 template <class T>
 struct DevBuf {
   T* p = nullptr;
   size_t n = 0;
+  cudaStream_t st = nullptr;                         // allocation stream of p's device
+  std::vector<T*> retired;
   cudaError_t ensure(size_t count) {
     if (count <= n && p) return cudaSuccess;
-    if (p) cudaFree(p);
+    if (p) retired.push_back(p);
     p = nullptr;
     n = 0;
-    cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
-    if (e == cudaSuccess) n = std::max<size_t>(count, 1);
-    else p = nullptr;
+    cudaMemPool_t pool;
+    cudaError_t e = current_pool(&pool, &st);
+    if (e != cudaSuccess) return e;
+    void* q = nullptr;
+    e = cudaMallocFromPoolAsync(&q, std::max<size_t>(count, 1) * sizeof(T), pool, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // usable from every stream
+    if (e == cudaSuccess) {
+      p = (T*)q;
+      n = std::max<size_t>(count, 1);
+    }
     return e;
   }
+  void drop_retired() {
+    for (T* q : retired) cudaFreeAsync(q, st);
+    retired.clear();
+  }
   void release() {
-    if (p) cudaFree(p);
+    drop_retired();
+    if (p) cudaFreeAsync(p, st);
     p = nullptr;
     n = 0;
   }
 };
+
+const int zero_word = 0;
+
+// A page-locked word holding 1: the source of the copy that cancels a run.
+const int* pinned_one() {
+  static int* one = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    if (cudaHostAlloc((void**)&one, sizeof(int), cudaHostAllocDefault) == cudaSuccess) *one = 1;
+    else one = nullptr;
+  });
+  return one;
+}
 
 }  // namespace
 
@@ -100,12 +179,27 @@ struct karl_ctx {
   DevBuf<unsigned long long> r_node, r_pid, r_seq;
   DevBuf<unsigned> r_ev, r_sj;
   unsigned long long ring_cap = 0;
-  Control* d_ctl = nullptr;
-  int* h_cancel = nullptr;      // pinned host word, source of the copy that cancels
-  int* d_cancel = nullptr;      // device word polled by the kernel
+  DevBuf<Control> d_ctlbuf;
+  DevBuf<int> d_cancelbuf;
+  Control* d_ctl = nullptr;     // = d_ctlbuf.p
+  int* d_cancel = nullptr;      // = d_cancelbuf.p, device word polled by the kernel
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   karl_run_stats stats;
   std::string err;
+  // every device buffer of the context
+  template <class F>
+  void each_buf(F f) {
+    f(d_nseg); f(d_colgas); f(d_faces); f(d_sig); f(d_sig_t); f(d_frate); f(d_fcol); f(d_time1);
+    f(d_ginv); f(d_sigf); f(d_ang_pdf); f(d_ang_cum); f(d_ang_pdff); f(d_ang_cumf); f(d_n2);
+    f(d_col2); f(d_pz); f(d_pe); f(d_pmu); f(d_psp); f(d_spec); f(d_tpt); f(d_trg); f(d_xpos);
+    f(d_xneg); f(d_recomb); f(d_ledger); f(d_chan); f(d_pp); f(d_time); f(d_cpos); f(d_cneg);
+    f(d_density); f(d_current); f(d_field); f(d_bad); f(r_z); f(r_mu); f(r_tal); f(r_eq);
+    f(r_node); f(r_pid); f(r_seq); f(r_ev); f(r_sj); f(d_ctlbuf); f(d_cancelbuf);
+  }
+  // buffers replaced during earlier calls (none of their work is in flight now)
+  void drop_retired() {
+    each_buf([](auto& b) { b.drop_retired(); });
+  }
 };
 
 namespace {
@@ -657,12 +751,12 @@ karl_status karl_create(const karl_geometry* g, const karl_xs* x, karl_ctx** out
   if (transport_setup() != cudaSuccess ||
       cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) ||
       cudaStreamCreateWithFlags(&ctx->cancel_stream, cudaStreamNonBlocking) ||
-      cudaMalloc(&ctx->d_ctl, sizeof(Control)) || cudaMalloc(&ctx->d_cancel, sizeof(int)) ||
-      cudaHostAlloc(&ctx->h_cancel, sizeof(int), cudaHostAllocDefault) ||
-      cudaMemset(ctx->d_cancel, 0, sizeof(int)) ||
+      ctx->d_ctlbuf.ensure(1) || ctx->d_cancelbuf.ensure(1) || !pinned_one() ||
+      cudaMemcpy(ctx->d_cancelbuf.p, &zero_word, sizeof(int), cudaMemcpyHostToDevice) ||
       cudaEventCreate(&ctx->ev0) || cudaEventCreate(&ctx->ev1))
     return bail(KARL_ECUDA);
-  *ctx->h_cancel = 1;
+  ctx->d_ctl = ctx->d_ctlbuf.p;
+  ctx->d_cancel = ctx->d_cancelbuf.p;
   *out = ctx;
   return KARL_OK;
 }
@@ -670,7 +764,7 @@ karl_status karl_create(const karl_geometry* g, const karl_xs* x, karl_ctx** out
 void karl_cancel(karl_ctx* ctx) {
   // a copy on a stream of its own runs while the transport kernel is running
   if (ctx && ctx->d_cancel && ctx->cancel_stream) {
-    cudaMemcpyAsync(ctx->d_cancel, ctx->h_cancel, sizeof(int), cudaMemcpyHostToDevice,
+    cudaMemcpyAsync(ctx->d_cancel, pinned_one(), sizeof(int), cudaMemcpyHostToDevice,
                     ctx->cancel_stream);
     cudaStreamSynchronize(ctx->cancel_stream);
   }
@@ -700,6 +794,7 @@ karl_status karl_run_pass(karl_ctx* ctx, const karl_primaries* pr, const karl_ru
                           int32_t pass, const uint64_t* field_time_in, karl_tallies* out) {
   if (!ctx) return KARL_EINVAL;
   ctx->err.clear();
+  ctx->drop_retired();
   if (!pr || !out || pr->n < 0) return fail(ctx, KARL_EINVAL, "NULL argument or n < 0");
   karl_status s = check_opts(ctx, o);
   if (s) return s;
@@ -755,6 +850,7 @@ karl_status karl_run(karl_ctx* ctx, const karl_primaries* pr, const karl_run_opt
                      karl_tallies* out) {
   if (!ctx) return KARL_EINVAL;
   ctx->err.clear();
+  ctx->drop_retired();
   if (!pr || !out || pr->n < 0) return fail(ctx, KARL_EINVAL, "NULL argument or n < 0");
   karl_status s = check_opts(ctx, o);
   if (s) return s;
@@ -814,29 +910,16 @@ karl_status karl_run(karl_ctx* ctx, const karl_primaries* pr, const karl_run_opt
 void karl_destroy(karl_ctx* ctx) {
   if (!ctx) return;
   if (ctx->own_stream) cudaStreamSynchronize(ctx->own_stream);
-  ctx->d_nseg.release(); ctx->d_colgas.release(); ctx->d_sig.release(); ctx->d_sigf.release();
-  ctx->d_frate.release(); ctx->d_fcol.release(); ctx->d_time1.release();
-  ctx->d_pz.release(); ctx->d_pe.release(); ctx->d_pmu.release(); ctx->d_psp.release();
-  ctx->d_spec.release(); ctx->d_tpt.release(); ctx->d_trg.release(); ctx->d_xpos.release();
-  ctx->d_xneg.release(); ctx->d_recomb.release(); ctx->d_ledger.release(); ctx->d_chan.release();
-  ctx->d_pp.release(); ctx->d_time.release(); ctx->d_cpos.release(); ctx->d_cneg.release();
-  ctx->d_density.release(); ctx->d_current.release(); ctx->d_field.release(); ctx->d_bad.release();
-  ctx->r_z.release(); ctx->r_mu.release(); ctx->r_tal.release(); ctx->r_eq.release();
-  ctx->r_node.release(); ctx->r_pid.release(); ctx->r_seq.release(); ctx->r_ev.release();
-  ctx->r_sj.release();
-  if (ctx->d_ctl) cudaFree(ctx->d_ctl);
-  if (ctx->h_cancel) cudaFreeHost(ctx->h_cancel);
-  if (ctx->d_cancel) cudaFree(ctx->d_cancel);
+  int prev = -1;
+  if (cudaGetDevice(&prev) == cudaSuccess && prev != ctx->device) cudaSetDevice(ctx->device);
+  ctx->each_buf([](auto& b) { b.release(); });
+  ctx->d_ctl = nullptr;
+  ctx->d_cancel = nullptr;
   if (ctx->cancel_stream) cudaStreamDestroy(ctx->cancel_stream);
-  ctx->d_sig_t.release();
-  ctx->d_ang_pdf.release(); ctx->d_ang_cum.release(); ctx->d_ang_pdff.release();
-  ctx->d_ang_cumf.release();
-  ctx->d_n2.release(); ctx->d_col2.release();
-  ctx->d_ginv.release();
-  ctx->d_faces.release();
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+  if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
   delete ctx;
 }
 

@@ -171,3 +171,28 @@ def test_many_small_requests_all_finish(karl, prec_name):
             if rep == 0:
                 _same(t, _single(karl, p, pr, s, prec))
         srv.close()
+
+
+def test_contexts_come_and_go_during_a_served_launch(karl):
+    # A served launch holds the device until its session closes.  A context
+    # made before it and destroyed while it runs (by a destructor, say), and
+    # a context created meanwhile, must not wait for it: a device-wide
+    # synchronising free there would stall the host until the launch's
+    # deadline while the launch waits for the host.
+    reqs = _requests(2, seed=5)
+    p, pr, s = reqs[0]
+    old = karl.Context(p)
+    srv = karl.Server(p, hbm_budget_bytes=1 << 30, timeout_s=30)
+    try:
+        rid = srv.submit(p, pr, s)              # admitted: the launch starts and stays up
+        t0 = time.time()
+        old.close()
+        new = karl.Context(p)
+        new.close()
+        dt = time.time() - t0
+        srv.run_all()
+        done, t = srv.poll(rid)
+    finally:
+        srv.close()
+    assert done and parity.ledger_balances(t["ledger"])
+    assert dt < 5.0, dt
