@@ -39,15 +39,14 @@ BYTES_PER_EVENT_FP32 = 80
 # kernel (pass 1) on the 1e6-decay case of this workload:
 #   FP64_OPS: FP64 add, multiply and fma thread-instructions executed with the
 #     predicate on (smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on);
-#     the same within 0.3 % on the 2e5-decay case;
 #   FP64_PIPE_CYCLES: SM-cycles the FP64 pipe was busy (sm__pipe_fp64_cycles_active),
 #     which also counts the lanes a divergent warp leaves idle;
 #   DRAM_BYTES: dram__bytes_read.sum + dram__bytes_write.sum, scaled to a launch
 #     by its collisions.
 # None: not measured for the kernel as it stands.
-FP64_OPS_PER_COLLISION = {"fp64": 192.3, "fp32": 29.8}
-FP64_PIPE_CYCLES_PER_COLLISION = {"fp64": 148.8, "fp32": 51.4}
-DRAM_BYTES_PER_COLLISION = {"fp64": 165320704 / 1665598248, "fp32": 258590208 / 1665593870}
+FP64_OPS_PER_COLLISION = {"fp64": 190.2, "fp32": 27.75}
+FP64_PIPE_CYCLES_PER_COLLISION = {"fp64": 146.9, "fp32": 50.2}
+DRAM_BYTES_PER_COLLISION = {"fp64": 199689216 / 1665598248, "fp32": 287443968 / 1665592961}
 FP64_OPS_PER_SM_CYCLE = 2
 WORKLOAD = ("config2: 1e7 decays (1e7 beta e- + 1e7 thermal T2+), parabolic profile with "
             "5e21 m^-2 column, L = 10 m, 1000 z segments, 7 e- channels + T2+ clustering + "
