@@ -31,8 +31,11 @@ template <> struct RT<false> {
   static __device__ __forceinline__ R atn(R x) { return atan(x); }
   static __device__ __forceinline__ R cpi(R x) { return cospi(x); }
   static __device__ __forceinline__ R spi(R x) { return sinpi(x); }
-  static __device__ __forceinline__ R tab(const Params& P, int k, int i) {
-    return __ldg(P.sig + (size_t)i * P.nch + k);      // [node][channel]
+  // value and slope to the next node of channel k at node i ([node][channel][2])
+  static __device__ __forceinline__ void tab2(const Params& P, int k, int i, R& a, R& s) {
+    const double2 t = __ldg((const double2*)P.sig + (size_t)i * P.nch + k);
+    a = t.x;
+    s = t.y;
   }
   static __device__ __forceinline__ R angp(const Params& P, size_t i) { return __ldg(P.ang_pdf + i); }
   static __device__ __forceinline__ R angc(const Params& P, size_t i) { return __ldg(P.ang_cum + i); }
@@ -56,8 +59,10 @@ template <> struct RT<true> {
   static __device__ __forceinline__ R atn(R x) { return atanf(x); }
   static __device__ __forceinline__ R cpi(R x) { return cospif(x); }
   static __device__ __forceinline__ R spi(R x) { return sinpif(x); }
-  static __device__ __forceinline__ R tab(const Params& P, int k, int i) {
-    return __ldg(P.sigf + (size_t)i * P.nch + k);     // [node][channel]
+  static __device__ __forceinline__ void tab2(const Params& P, int k, int i, R& a, R& s) {
+    const float2 t = __ldg((const float2*)P.sigf + (size_t)i * P.nch + k);
+    a = t.x;
+    s = t.y;
   }
   static __device__ __forceinline__ R angp(const Params& P, size_t i) { return __ldg(P.ang_pdff + i); }
   static __device__ __forceinline__ R angc(const Params& P, size_t i) { return __ldg(P.ang_cumf + i); }
@@ -113,10 +118,14 @@ __device__ __forceinline__ unsigned long long quant_t(double len, double inv_sz)
 }
 __device__ __forceinline__ long long quant_e(double e) { return (long long)floor(e * Q_E); }
 
-template <class R>
-__device__ __forceinline__ R speed(R e, R inv_m) {
-  R x = e * inv_m;
-  return (R)C_LIGHT * sqrt(x * ((R)2 + x)) / ((R)1 + x);
+// 1 / v for kinetic energy e (relativistic: v = c sqrt(x (2 + x)) / (1 + x),
+// x = e / m c^2); every use of the speed divides by it
+template <bool F32>
+__device__ __forceinline__ typename RT<F32>::R inv_speed(typename RT<F32>::R e,
+                                                         typename RT<F32>::R inv_m) {
+  using R = typename RT<F32>::R;
+  const R x = e * inv_m;
+  return ((R)1 + x) * RT<F32>::rsq(x * ((R)2 + x)) * (R)(1.0 / C_LIGHT);
 }
 
 struct Shared {
@@ -565,7 +574,7 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
   }
   const int s = L.sp;
   const R e = T::energy(L.eq);
-  const R v = speed<R>(e, (R)P.inv_mass[s]);
+  const R inv_v = inv_speed<F32>(e, (R)P.inv_mass[s]);
 
   unsigned long long w[4];
   philox4x64_10((unsigned long long)L.ev, L.node,
@@ -598,10 +607,11 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
     const ChanDev& ch = P.ch[k];
     R cv;
     if (ch.kind == RECOMBINATION && s != SP_E) {
-      cv = (R)1 / v;
+      cv = inv_v;
     } else if (L.eq > ch.thr_q) {
-      const R a0 = T::tab(P, k, ti);
-      cv = a0 + tf * (T::tab(P, k, ti + 1) - a0);
+      R a0, sl;
+      T::tab2(P, k, ti, a0, sl);
+      cv = a0 + tf * sl;
     } else {
       cv = (R)0;
     }
@@ -654,7 +664,7 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
       o.alive = false;
       return;
     }
-    const double tfl = (double)tau / r / (double)v;
+    const double tfl = (double)tau / r * (double)inv_v;
     atomicAdd(P.time_pt + tbase + (size_t)(jc + 1) * trow, (unsigned long long)(tfl * Q_T + 0.5));
     if (P.track_time) L.tal += tfl;
     zc = L.z;
@@ -701,7 +711,7 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
     }
     // time in each segment crossed (Sec. 2.2) as point adds at both ends and
     // one range add of the full-segment time, and the face crossings (Sec. 2.3)
-    inv_sz = 1.0 / (amu * (double)v);
+    inv_sz = (double)inv_v / amu;
     const size_t row0 = tbase + (size_t)(j0 + 1) * trow;
     if (jc == j0) {
       atomicAdd(P.time_pt + row0, quant_t(fabs(zc - L.z), inv_sz));
@@ -773,18 +783,19 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
     const R g = (R)P.gam[s];
     const R cchi = elastic_cchi<F32>(P, ch, e, T::u(w[2]));
     const R a = (R)1 + (R)2 * g * cchi + g * g;
-    const R ct = (cchi + g) * T::rsq(a);
+    const R ra = T::rsq(a);
+    const R ct = (cchi + g) * ra;
     // energy given to the target, E - E' = E 2g(1 - cos chi)/(1+g)^2
     const R de = e * ((R)2 * g) * ((R)1 - cchi) * (R)P.inv_1pg2[s];
     long long rq = T::quant_de(de);
     if (rq > L.eq) rq = L.eq;
     o.recoil += (unsigned long long)rq;
     L.eq -= rq;
-    const R st = T::sq(fmax((R)0, (R)1 - ct * ct));
+    // sin(theta_lab) sqrt(1 - mu^2) in one root: 1 - ct^2 = (1 - cchi^2) / a
     const R cphi = T::cpi((R)2 * T::u(w[3]));
     const R mu = (R)L.mu;
-    const R smu = T::sq(fmax((R)0, (R)1 - mu * mu));
-    L.mu = (double)fmin((R)1, fmax((R)-1, mu * ct + smu * st * cphi));
+    const R ss = T::sq(fmax((R)0, ((R)1 - cchi * cchi) * ((R)1 - mu * mu))) * ra;
+    L.mu = (double)fmin((R)1, fmax((R)-1, mu * ct + ss * cphi));
   } else if (ch.kind == EXCITATION) {
     L.eq -= ch.loss_q;
     o.excit += (unsigned long long)ch.loss_q;

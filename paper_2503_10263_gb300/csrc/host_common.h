@@ -293,19 +293,28 @@ inline bool has_recombination(const ModelInfo& m) {
   return false;
 }
 
-// [node][channel] copies of the cross sections (all channels of one node in
-// adjacent words) for the transport kernels; three-body rows times 2^128.
+// [node][channel][2] copies of the cross sections for the transport kernels:
+// each node's value and its difference to the next node (0 at the last), all
+// channels of one node adjacent, so one 16-byte (8-byte in FP32) load gives
+// both terms of the linear interpolation; three-body rows times 2^128.
 inline void node_major_tables(const karl_xs* x, std::vector<double>& sig_t, std::vector<float>& sigf) {
-  const size_t n = (size_t)x->n_channels * x->n_energy;
+  const int ne = x->n_energy, nc = x->n_channels;
+  const size_t n = (size_t)nc * ne * 2;
   sig_t.assign(n, 0.0);
   sigf.assign(n, 0.0f);
-  for (int k = 0; k < x->n_channels; ++k)
-    for (int i = 0; i < x->n_energy; ++i) {
-      const double v = x->sigma_m2[(size_t)k * x->n_energy + i] *
-                       (x->kind[k] == CLUSTERING3 ? THREE_BODY_SCALE : 1.0);
-      sig_t[(size_t)i * x->n_channels + k] = v;
-      sigf[(size_t)i * x->n_channels + k] = (float)v;
+  for (int k = 0; k < nc; ++k) {
+    const double scale = x->kind[k] == CLUSTERING3 ? THREE_BODY_SCALE : 1.0;
+    for (int i = 0; i < ne; ++i) {
+      const double v = x->sigma_m2[(size_t)k * ne + i] * scale;
+      const double vn = i + 1 < ne ? x->sigma_m2[(size_t)k * ne + i + 1] * scale : v;
+      const size_t at = ((size_t)i * nc + k) * 2;
+      sig_t[at] = v;
+      sig_t[at + 1] = vn - v;
+      const float f = (float)v, fn = (float)vn;
+      sigf[at] = f;
+      sigf[at + 1] = fn - f;
     }
+  }
 }
 
 }  // namespace karl

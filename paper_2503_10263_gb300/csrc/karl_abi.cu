@@ -701,9 +701,10 @@ karl_status karl_create(const karl_geometry* g, const karl_xs* x, karl_ctx** out
   std::vector<float> sigf;
   node_major_tables(x, sig_t, sigf);
   size_t nsig = std::max<size_t>(ctx->sigma.size(), 1);
+  size_t nsig2 = std::max<size_t>(sig_t.size(), 1);
   if (ctx->d_nseg.ensure(ctx->nz) || ctx->d_colgas.ensure(ctx->nz + 1) ||
       ctx->d_faces.ensure(ctx->nz + 1) ||
-      ctx->d_sig.ensure(nsig) || ctx->d_sig_t.ensure(nsig) || ctx->d_sigf.ensure(nsig) ||
+      ctx->d_sig.ensure(nsig) || ctx->d_sig_t.ensure(nsig2) || ctx->d_sigf.ensure(nsig2) ||
       ctx->d_ledger.ensure(LEDGER) || ctx->d_ginv.ensure(ctx->nq + 1))
     return bail(KARL_ENOMEM);
   if (cudaMemcpy(ctx->d_nseg.p, ctx->nseg.data(), ctx->nz * 8, cudaMemcpyHostToDevice) ||
