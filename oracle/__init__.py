@@ -93,6 +93,10 @@ def _load():
         lib.orc_run_pass.argtypes = [C.POINTER(_Problem), C.POINTER(_Prims), C.c_uint64, C.c_int,
                                      C.POINTER(C.c_uint64), C.c_int, C.c_int, C.POINTER(_Tallies)]
         lib.orc_run_pass.restype = C.c_int
+        lib.orc_run_cycle.argtypes = [C.POINTER(_Problem), C.POINTER(_Prims), C.c_uint64,
+                                      C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.c_double,
+                                      C.c_int, C.c_int, C.POINTER(_Tallies)]
+        lib.orc_run_cycle.restype = C.c_int
         lib.orc_philox4x64.argtypes = [C.POINTER(C.c_uint64)] * 3
         lib.orc_philox4x64.restype = None
         lib.orc_sigma.argtypes = [C.POINTER(_Problem), C.c_int, C.c_double]
@@ -288,6 +292,76 @@ def run_pass(prob, prims, seed: int, pass_index: int, field_time_in: Optional[np
     t["per_primary"] = t["per_primary"][:prims.n]
     t["chan_count"] = t["chan_count"][:prob.n_channels]
     return t
+
+
+def run_cycle(prob, prims, seed: int, field_time_in: Optional[np.ndarray],
+              field_recomb_in: Optional[np.ndarray], field_decays: float, pid_offset: int = 0,
+              mode: int = 0, n_threads: int = 1) -> Dict[str, np.ndarray]:
+    """One cycle of the continuous field update over a primary-id range:
+    recombination on, fields from the given summed tallies (None: zero)."""
+    lib = _load()
+    m = _Marshal(prob)
+    ps, keep = _prims(prims, pid_offset, prims.n_decays)
+    t = empty_tallies(prob, prims.n)
+    ts = _tallies_struct(t, with_norm=False)
+    fin = None if field_time_in is None else np.ascontiguousarray(field_time_in, np.uint64)
+    rin = None if field_recomb_in is None else np.ascontiguousarray(field_recomb_in, np.uint64)
+    rc = lib.orc_run_cycle(C.byref(m.s), C.byref(ps), C.c_uint64(seed),
+                           _ptr(fin, C.c_uint64) if fin is not None else None,
+                           _ptr(rin, C.c_uint64) if rin is not None else None,
+                           float(field_decays), mode, n_threads, C.byref(ts))
+    if rc != 0:
+        raise RuntimeError(f"oracle cycle failed: {rc}")
+    t["per_primary"] = t["per_primary"][:prims.n]
+    t["chan_count"] = t["chan_count"][:prob.n_channels]
+    return t
+
+
+RAW_KEYS = ("spectrum", "time_fx", "cross_pos", "cross_neg", "recomb", "ledger", "chan_count")
+
+
+def run_cycles(prob, prims, seed: int, n_cycles: int, mode: int = 0,
+               n_threads: int = 1) -> Dict[str, np.ndarray]:
+    """The paper's continuous field update (Sec. 3.6): the primaries in
+    n_cycles consecutive cycles of indices [c n / C, (c+1) n / C); cycle c runs
+    with the fields of the time and deletion tallies of the cycles before it,
+    t_sim from their share of the decays; the first with fields of zero.
+    Returns the raw tallies summed over the cycles, the density and current
+    of Eq. target_field_density and Sec. 2.3 over the whole run, and as
+    `field` the per-bin densities a next cycle would use."""
+    n = prims.n
+    tot = empty_tallies(prob, n)
+    for k in RAW_KEYS:
+        tot[k] = tot[k].astype(np.int64 if k == "ledger" else np.uint64)
+    tot["chan_count"] = tot["chan_count"][:prob.n_channels]
+    tot["per_primary"] = tot["per_primary"][:n]
+    for c in range(n_cycles):
+        lo, hi = c * n // n_cycles, (c + 1) * n // n_cycles
+        if hi <= lo:
+            continue
+        decays_before = prims.n_decays * lo / n
+        if lo == 0:
+            t = run_cycle(prob, prims.slice(lo, hi - lo), seed, None, None, 0.0, pid_offset=lo,
+                          mode=mode, n_threads=n_threads)
+        else:
+            t = run_cycle(prob, prims.slice(lo, hi - lo), seed, tot["time_fx"], tot["recomb"],
+                          decays_before, pid_offset=lo, mode=mode, n_threads=n_threads)
+        for k in RAW_KEYS:
+            tot[k] += t[k]
+        tot["per_primary"][lo:hi] = t["per_primary"]
+    # normalisation over the whole run: Eq. target_field_density, Sec. 2.3
+    nz, ntb = prob.n_zbins, prob.n_tebins
+    tsim = prims.n_decays / prob.activity_bq
+    vol = prob.length_m / nz * prob.area_m2
+    tt = tot["time_fx"][:, 1:nz + 1, :].astype(np.float64)           # [4][nz][ntb]
+    rec = tot["recomb"].astype(np.float64)                           # [4][nz]
+    tot["density"] = tt.sum(axis=2) / 2**50 / (tsim * vol) - rec / vol
+    tot["current"] = (tot["cross_pos"].astype(np.float64) -
+                      tot["cross_neg"].astype(np.float64)) / (prob.area_m2 * tsim)
+    ttot = tt.sum(axis=2, keepdims=True)
+    share = np.divide(tt, ttot, out=np.zeros_like(tt), where=ttot > 0)
+    tot["field"] = np.maximum(tt / 2**50 / (tsim * vol) - (rec / vol)[:, :, None] * share, 0.0)
+    return tot
 
 
 def philox4x64(ctr, key) -> np.ndarray:

@@ -45,7 +45,10 @@
  *  - recombination: the impactor is deleted, the partner's field logs one
  *    deletion in the segment (Sec. 3.3, Recombination);
  *  - two passes: pass 1 without recombination builds the target fields,
- *    pass 2 uses them frozen;
+ *    pass 2 uses them frozen; or the paper's continuous update (Sec. 3.6):
+ *    the primaries in consecutive cycles, each cycle with the fields of the
+ *    cycles before it, deletions included (Eq. target_field_density), the
+ *    first with fields of zero;
  *  - random numbers: Philox4x64-10 (Salmon et al., SC'11) keyed by
  *    (seed, primary id), counter (event index, lineage id, pass/domain, sub).
  */
@@ -741,12 +744,18 @@ struct Worker {
   }
 };
 
-/* Target fields for pass 2 from raw pass-1 time tallies (Eq. target_field_density
- * with N_gamma = 0 in pass 1; t_sim from Eq. simulated_time). */
-void build_fields(Run& R, const uint64_t* time_in, int64_t n_decays) {
+/* Target fields from summed time tallies and recombination deletions
+ * (Eq. target_field_density: n = sum t / (t_sim V) - N_gamma / V, t_sim of
+ * Eq. simulated_time over n_decays).  The partner's density in energy bin b
+ * of segment j takes its share of the segment's deletions in proportion to
+ * its time there; a density below zero counts as zero.  recomb_in NULL: no
+ * deletions (the fields of a two-pass run, whose pass 1 has none).
+ * Electron impactor: the ion partner's density; ion impactor: the electron
+ * field weighted by sigma(E_b) v(E_b) at the bin centres. */
+void build_fields(Run& R, const uint64_t* time_in, const uint64_t* recomb_in, double n_decays) {
   const orc_problem* p = R.p;
   int nz = p->n_zbins, ntb = p->n_tebins;
-  double tsim = (double)n_decays / p->activity_bq;
+  double tsim = n_decays / p->activity_bq;
   double vol = R.dz * p->area_m2;
   R.field.assign(p->n_channels, std::vector<double>());
   for (int k = 0; k < p->n_channels; ++k) {
@@ -754,19 +763,23 @@ void build_fields(Run& R, const uint64_t* time_in, int64_t n_decays) {
     int partner = p->species_out[k];
     std::vector<double> f(nz, 0.0);
     for (int j = 0; j < nz; ++j) {
+      const uint64_t* tj = time_in + ((size_t)partner * (nz + 2) + (j + 1)) * ntb;
+      double ttot = 0.0;
+      for (int b = 0; b < ntb; ++b) ttot += (double)tj[b];
+      const double del = recomb_in ? (double)recomb_in[(size_t)partner * nz + j] / vol : 0.0;
       double acc = 0.0;
       for (int b = 0; b < ntb; ++b) {
-        uint64_t t = time_in[((size_t)partner * (nz + 2) + (j + 1)) * ntb + b];
-        double n = (double)t / Q_TIME / (tsim * vol);
+        double n = (double)tj[b] / Q_TIME / (tsim * vol);
+        if (recomb_in && ttot > 0.0) n -= del * ((double)tj[b] / ttot);
         if (p->species_in[k] == SP_E) {
           acc += n;                                  /* ion density */
         } else {
           /* ion impactor: electron field weighted by sigma(E_b) v(E_b) */
           double eb = p->e_min_ev * std::pow(p->e_max_ev / p->e_min_ev, (b + 0.5) / ntb);
-          acc += n * sigma_at(p, k, eb) * speed(eb, p->species_mass_ev[SP_E]);
+          acc += std::fmax(n, 0.0) * sigma_at(p, k, eb) * speed(eb, p->species_mass_ev[SP_E]);
         }
       }
-      f[j] = acc;
+      f[j] = std::fmax(acc, 0.0);
     }
     R.field[k] = f;
   }
@@ -789,13 +802,20 @@ int check_problem(const orc_problem* p) {
   return 0;
 }
 
+/* One pass.  Pass 2 takes its target fields from field_time_in (and the
+ * deletions field_recomb_in, may be NULL) over field_decays decays; with
+ * zero_fields the recombination channels are present with fields of zero. */
 int do_pass(const orc_problem* p, const orc_primaries* pr, uint64_t seed, int pass,
-            const uint64_t* field_time_in, int mode, int n_threads, orc_tallies* out) {
+            const uint64_t* field_time_in, const uint64_t* field_recomb_in, double field_decays,
+            bool zero_fields, int mode, int n_threads, orc_tallies* out) {
   Run R;
   R.p = p; R.seed = seed; R.pass = pass; R.mode = mode;
   R.dz = p->length_m / p->n_zbins;
   R.field.assign(p->n_channels, std::vector<double>());
-  if (pass == 2 && field_time_in) build_fields(R, field_time_in, pr->n_decays);
+  if (pass == 2 && field_time_in) build_fields(R, field_time_in, field_recomb_in, field_decays);
+  if (pass == 2 && zero_fields)
+    for (int k = 0; k < p->n_channels; ++k)
+      if (p->kind[k] == RECOMBINATION) R.field[k].assign(p->n_zbins, 0.0);
   if (n_threads < 1) n_threads = 1;
   if ((int64_t)n_threads > pr->n) n_threads = (int)(pr->n > 0 ? pr->n : 1);
   std::vector<Worker> W(n_threads);
@@ -921,7 +941,17 @@ int orc_collide(const orc_problem* p, int ch, int species, double e_ev, double m
 int orc_run_pass(const orc_problem* p, const orc_primaries* pr, uint64_t seed, int pass,
                  const uint64_t* field_time_in, int mode, int n_threads, orc_tallies* out) {
   if (check_problem(p) || !pr || !out || (pass != 1 && pass != 2)) return 1;
-  return do_pass(p, pr, seed, pass, field_time_in, mode, n_threads, out);
+  return do_pass(p, pr, seed, pass, field_time_in, nullptr, (double)pr->n_decays, false, mode,
+                 n_threads, out);
+}
+
+int orc_run_cycle(const orc_problem* p, const orc_primaries* pr, uint64_t seed,
+                  const uint64_t* field_time_in, const uint64_t* field_recomb_in,
+                  double field_decays, int mode, int n_threads, orc_tallies* out) {
+  if (check_problem(p) || !pr || !out) return 1;
+  if (field_time_in && !(field_decays > 0.0)) return 1;
+  return do_pass(p, pr, seed, 2, field_time_in, field_recomb_in, field_decays, !field_time_in,
+                 mode, n_threads, out);
 }
 
 int orc_run(const orc_problem* p, const orc_primaries* pr, uint64_t seed, int n_passes,
@@ -930,7 +960,7 @@ int orc_run(const orc_problem* p, const orc_primaries* pr, uint64_t seed, int n_
   int nz = p->n_zbins, ntb = p->n_tebins;
   size_t ntime = (size_t)ORC_N_SPECIES * (nz + 2) * ntb;
   /* pass 1 into out; if two passes, keep its time tally and rerun */
-  int rc = do_pass(p, pr, seed, 1, nullptr, mode, n_threads, out);
+  int rc = do_pass(p, pr, seed, 1, nullptr, nullptr, 0.0, false, mode, n_threads, out);
   if (rc) return rc;
   std::vector<uint64_t> time1(out->time_fx, out->time_fx + ntime);
   if (n_passes == 2) {
@@ -942,7 +972,8 @@ int orc_run(const orc_problem* p, const orc_primaries* pr, uint64_t seed, int n_
     std::memset(out->ledger, 0, sizeof(int64_t) * ORC_LEDGER_LEN);
     std::memset(out->chan_count, 0, sizeof(uint64_t) * p->n_channels);
     if (out->per_primary) std::memset(out->per_primary, 0, sizeof(uint64_t) * pr->n);
-    rc = do_pass(p, pr, seed, 2, time1.data(), mode, n_threads, out);
+    rc = do_pass(p, pr, seed, 2, time1.data(), nullptr, (double)pr->n_decays, false, mode,
+                 n_threads, out);
     if (rc) return rc;
   }
   /* normalisation: Eq. target_field_density, current j = (N+ - N-)/(A t_sim) */

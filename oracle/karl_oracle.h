@@ -134,6 +134,16 @@ void orc_elastic_moving_target(const orc_problem* p, double m1_ev, double e_ev, 
                                const uint64_t w[4], const uint64_t ctr[3], const uint64_t key[2],
                                double* out_e, double* out_mu, double* v);
 
+/* One cycle of the continuous field update (Sec. 3.6, Eq. target_field_density):
+ * a pass with recombination whose target fields come from field_time_in
+ * ([4][n_zbins+2][n_tebins]) and the deletions field_recomb_in ([4][n_zbins],
+ * may be NULL) summed over the cycles before, with t_sim = field_decays /
+ * activity; field_time_in NULL: every field zero.  Raw tallies are ADDED to
+ * out.  Returns 0 on success. */
+int orc_run_cycle(const orc_problem* p, const orc_primaries* pr, uint64_t seed,
+                  const uint64_t* field_time_in, const uint64_t* field_recomb_in,
+                  double field_decays, int mode, int n_threads, orc_tallies* out);
+
 /* One charge exchange (Sec. 3.3 Charge exchange) of an impactor of rest
  * energy m1_ev, kinetic energy e_ev and pitch cosine mu; the target velocity
  * is drawn from the blocks (ctr[0], ctr[1], ctr[2], k) under key.  Writes the
