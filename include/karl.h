@@ -228,6 +228,35 @@ karl_status karl_run(karl_ctx* ctx, const karl_primaries* prim, const karl_run_o
 karl_status karl_run_pass(karl_ctx* ctx, const karl_primaries* prim, const karl_run_opts* opts,
                           int32_t pass, const uint64_t* field_time_in, karl_tallies* out);
 
+/* The paper's continuous field update (Sec. 3.6): the primaries run in
+ * n_cycles consecutive cycles, cycle c over indices [c n / C, (c+1) n / C),
+ * each with the target fields of every cycle before it -- Eq.
+ * target_field_density over their summed time tallies, with the -N/V term of
+ * the recombination deletions logged in the partner's field (a bin's density
+ * takes the segment's deletions in proportion to its time there, and counts
+ * as zero below zero), t_sim (Eq. simulated_time) from their share of
+ * prim->n_decays -- and the first cycle with fields of zero.  All cycles draw
+ * from the pass-2 random streams, so without recombination channels the
+ * result does not depend on n_cycles.  Returns in out the raw tallies summed
+ * over the cycles, the density and current of the whole run, and as `field`
+ * the per-bin densities (deletions included) a next cycle would use.
+ * opts->n_passes is ignored.  Errors: those of karl_run, KARL_EINVAL for
+ * n_cycles < 1. */
+karl_status karl_run_cycles(karl_ctx* ctx, const karl_primaries* prim, const karl_run_opts* opts,
+                            int32_t n_cycles, karl_tallies* out);
+
+/* One cycle of the continuous update over a primary-id range, raw tallies
+ * ADDED to out (the building block of karl_run_cycles for runs split over
+ * ranks): recombination on, with the fields of field_time_in (host,
+ * [4][n_zbins+2][n_tebins]) and field_recomb_in (host, [4][n_zbins], or NULL
+ * for no deletions) summed over the earlier cycles of every rank, t_sim =
+ * field_decays / activity; field_time_in NULL: fields of zero (the first
+ * cycle).  Errors: those of karl_run_pass, KARL_EINVAL for field_decays <= 0
+ * with fields given. */
+karl_status karl_run_cycle(karl_ctx* ctx, const karl_primaries* prim, const karl_run_opts* opts,
+                           const uint64_t* field_time_in, const uint64_t* field_recomb_in,
+                           double field_decays, karl_tallies* out);
+
 /* ---------------------------------------------------------------------------
  * One pass that allocates nothing.  The paper has no counterpart: this is a
  * deployment form of karl_run_pass, with the same kernel and results.

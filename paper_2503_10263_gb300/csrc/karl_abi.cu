@@ -181,6 +181,8 @@ struct karl_ctx {
   unsigned long long ring_cap = 0;
   DevBuf<Control> d_ctlbuf;
   DevBuf<int> d_cancelbuf;
+  // sums over the cycles of a continuous-update run
+  DevBuf<unsigned long long> c_spec, c_time, c_cpos, c_cneg, c_rec, c_led, c_chan, c_pp, d_recin;
   Control* d_ctl = nullptr;     // = d_ctlbuf.p
   int* d_cancel = nullptr;      // = d_cancelbuf.p, device word polled by the kernel
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -195,6 +197,7 @@ struct karl_ctx {
     f(d_xneg); f(d_recomb); f(d_ledger); f(d_chan); f(d_pp); f(d_time); f(d_cpos); f(d_cneg);
     f(d_density); f(d_current); f(d_field); f(d_bad); f(r_z); f(r_mu); f(r_tal); f(r_eq);
     f(r_node); f(r_pid); f(r_seq); f(r_ev); f(r_sj); f(d_ctlbuf); f(d_cancelbuf);
+    f(c_spec); f(c_time); f(c_cpos); f(c_cneg); f(c_rec); f(c_led); f(c_chan); f(c_pp); f(d_recin);
   }
   // buffers replaced during earlier calls (none of their work is in flight now)
   void drop_retired() {
@@ -290,31 +293,42 @@ struct FieldArgs {
   double loss[MAXCH];
 };
 
-// Target fields of pass 2 from the pass-1 time tally (Eq. target_field_density
-// with t_sim of Eq. simulated_time).  Electron impactor: ion density.  Ion
-// impactor: sum over electron energy bins of n_e(E_b) sigma(E_b) v(E_b).
-__global__ void k_build_fields(FieldArgs A, const unsigned long long* time1, const double* sig,
-                               double* frate, double* fcol) {
+// Target fields from summed time tallies (Eq. target_field_density with t_sim
+// of Eq. simulated_time) and, for the cycles of the continuous update, the
+// deletions logged in the partner's field (its -N/V term: a bin's density
+// takes the segment's deletions in proportion to its time; below zero it
+// counts as zero).  recomb NULL: no deletions (pass 2 of a two-pass run).
+// Electron impactor: ion density.  Ion impactor: sum over electron energy
+// bins of n_e(E_b) sigma(E_b) v(E_b).
+__global__ void k_build_fields(FieldArgs A, const unsigned long long* time1,
+                               const unsigned long long* recomb, const double* sig, double* frate,
+                               double* fcol) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= A.nch * A.nz) return;
   int k = t / A.nz, j = t % A.nz;
   if (A.kind[k] != RECOMBINATION) return;
   int partner = A.sout[k];
+  const unsigned long long* tj = time1 + ((size_t)partner * (A.nz + 2) + (j + 1)) * A.ntb;
+  double ttot = 0.0, del = 0.0;
+  if (recomb) {
+    for (int b = 0; b < A.ntb; ++b) ttot += (double)tj[b];
+    del = (double)recomb[(size_t)partner * A.nz + j] / A.vol;
+  }
   double acc = 0.0;
   for (int b = 0; b < A.ntb; ++b) {
-    unsigned long long tt = time1[((size_t)partner * (A.nz + 2) + (j + 1)) * A.ntb + b];
-    double n = (double)tt / Q_TIME / (A.tsim * A.vol);
+    double n = (double)tj[b] / Q_TIME / (A.tsim * A.vol);
+    if (recomb && ttot > 0.0) n -= del * ((double)tj[b] / ttot);
     if (A.sin[k] == SP_E) {
       acc += n;
     } else {
       double eb = A.e_min * pow(A.e_max / A.e_min, (b + 0.5) / A.ntb);
       double x = eb / A.me;
       double v = C_LIGHT * sqrt(x * (2.0 + x)) / (1.0 + x);
-      acc += n * sigma_interp(sig + (size_t)k * A.n_energy, A.n_energy, A.e_min, A.e_max,
-                              A.loss[k], eb) * v;
+      acc += fmax(n, 0.0) * sigma_interp(sig + (size_t)k * A.n_energy, A.n_energy, A.e_min,
+                                         A.e_max, A.loss[k], eb) * v;
     }
   }
-  frate[(size_t)k * A.nz + j] = acc;
+  frate[(size_t)k * A.nz + j] = fmax(acc, 0.0);
 }
 
 __global__ void k_field_columns(const double* frate, double* fcol, int nch, int nz, double dz) {
@@ -328,18 +342,27 @@ __global__ void k_field_columns(const double* frate, double* fcol, int nch, int 
   }
 }
 
+// field_del: the field output takes its deletions as the cycles' fields do
 __global__ void k_normalize(const unsigned long long* time, const unsigned long long* time1,
                             const unsigned long long* recomb, const unsigned long long* cpos,
                             const unsigned long long* cneg, double* density, double* current,
-                            double* field, int nz, int ntb, double tsim, double vol, double area) {
+                            double* field, int nz, int ntb, double tsim, double vol, double area,
+                            int field_del) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < NSP * nz) {
     int s = t / nz, j = t % nz;
-    double tsum = 0.0;
+    double tsum = 0.0, t1tot = 0.0;
+    if (field_del)
+      for (int b = 0; b < ntb; ++b) t1tot += (double)time1[((size_t)s * (nz + 2) + (j + 1)) * ntb + b];
+    const double del = field_del ? (double)recomb[(size_t)s * nz + j] / vol : 0.0;
     for (int b = 0; b < ntb; ++b) {
       size_t idx = ((size_t)s * (nz + 2) + (j + 1)) * ntb + b;
       tsum += (double)time[idx] / Q_TIME;
-      if (field) field[((size_t)s * nz + j) * ntb + b] = (double)time1[idx] / Q_TIME / (tsim * vol);
+      if (field) {
+        double nb = (double)time1[idx] / Q_TIME / (tsim * vol);
+        if (field_del && t1tot > 0.0) nb -= del * ((double)time1[idx] / t1tot);
+        field[((size_t)s * nz + j) * ntb + b] = field_del ? fmax(nb, 0.0) : nb;
+      }
     }
     if (density) density[(size_t)s * nz + j] =
         tsum / (tsim * vol) - (double)recomb[(size_t)s * nz + j] / vol;
@@ -571,15 +594,15 @@ karl_status run_one_pass(karl_ctx* ctx, const karl_primaries* pr, const karl_run
               (unsigned long long)ctx->ring_cap);
 }
 
-karl_status build_fields(karl_ctx* ctx, const unsigned long long* d_time1, int64_t n_decays,
-                         cudaStream_t st) {
+karl_status build_fields(karl_ctx* ctx, const unsigned long long* d_time1,
+                         const unsigned long long* d_recomb, double n_decays, cudaStream_t st) {
   FieldArgs A;
   std::memset(&A, 0, sizeof A);
   A.nz = ctx->nz;
   A.ntb = ctx->ntb;
   A.n_energy = ctx->n_energy;
   A.nch = ctx->nch;
-  A.tsim = (double)n_decays / ctx->activity;
+  A.tsim = n_decays / ctx->activity;
   A.vol = ctx->dz * ctx->area;
   A.dz = ctx->dz;
   A.e_min = ctx->e_min;
@@ -596,7 +619,7 @@ karl_status build_fields(karl_ctx* ctx, const unsigned long long* d_time1, int64
   CK(ctx->d_fcol.ensure(nk * (ctx->nz + 1)));
   CK(cudaMemsetAsync(ctx->d_frate.p, 0, nk * ctx->nz * 8, st));
   k_build_fields<<<grid_for((size_t)ctx->nch * ctx->nz, 256), 256, 0, st>>>(
-      A, d_time1, ctx->d_sig.p, ctx->d_frate.p, ctx->d_fcol.p);
+      A, d_time1, d_recomb, ctx->d_sig.p, ctx->d_frate.p, ctx->d_fcol.p);
   k_field_columns<<<1, 32, 0, st>>>(ctx->d_frate.p, ctx->d_fcol.p, ctx->nch, ctx->nz, ctx->dz);
   CK(cudaGetLastError());
   ctx->stats.kernel_launches += 2;
@@ -814,7 +837,8 @@ karl_status karl_run_pass(karl_ctx* ctx, const karl_primaries* pr, const karl_ru
   if (pass == 2) {
     CK(ctx->d_time1.ensure(n_time(ctx)));
     CK(cudaMemcpyAsync(ctx->d_time1.p, field_time_in, n_time(ctx) * 8, cudaMemcpyHostToDevice, st));
-    s = build_fields(ctx, (const unsigned long long*)ctx->d_time1.p, pr->n_decays, st);
+    s = build_fields(ctx, (const unsigned long long*)ctx->d_time1.p, nullptr,
+                     (double)pr->n_decays, st);
     if (s) return s;
   }
   bool pp = out->per_primary != nullptr && pr->n > 0;
@@ -874,7 +898,8 @@ karl_status karl_run(karl_ctx* ctx, const karl_primaries* pr, const karl_run_opt
   CK(ctx->d_time1.ensure(nt));
   CK(cudaMemcpyAsync(ctx->d_time1.p, ctx->d_time.p, nt * 8, cudaMemcpyDeviceToDevice, st));
   if (o->n_passes == 2 && has_recombination(ctx->model)) {
-    s = build_fields(ctx, (const unsigned long long*)ctx->d_time1.p, pr->n_decays, st);
+    s = build_fields(ctx, (const unsigned long long*)ctx->d_time1.p, nullptr,
+                     (double)pr->n_decays, st);
     if (s) return s;
     s = run_one_pass(ctx, pr, o, 2, pz, pe, pmu, psp, pp, st);
     if (s) return s;
@@ -888,7 +913,7 @@ karl_status karl_run(karl_ctx* ctx, const karl_primaries* pr, const karl_run_opt
   k_normalize<<<grid_for(n_cross(ctx), 256), 256, 0, st>>>(
       ctx->d_time.p, (const unsigned long long*)ctx->d_time1.p, ctx->d_recomb.p, ctx->d_cpos.p,
       ctx->d_cneg.p, ctx->d_density.p, ctx->d_current.p, ctx->d_field.p, ctx->nz, ctx->ntb, tsim,
-      vol, ctx->area);
+      vol, ctx->area, 0);
   CK(cudaGetLastError());
   ctx->stats.kernel_launches += 1;
   bool dev = out->on_device != 0;
@@ -900,6 +925,179 @@ karl_status karl_run(karl_ctx* ctx, const karl_primaries* pr, const karl_run_opt
       (s = copy_out(ctx, out->ledger, ctx->d_ledger.p, LEDGER * 8, dev, st)) ||
       (s = copy_out(ctx, out->chan_count, ctx->d_chan.p, (size_t)ctx->nch * 8, dev, st)) ||
       (s = copy_out(ctx, pp ? out->per_primary : nullptr, ctx->d_pp.p, (size_t)pr->n * 8, dev, st)) ||
+      (s = copy_out(ctx, out->density, ctx->d_density.p, (size_t)NSP * ctx->nz * 8, dev, st)) ||
+      (s = copy_out(ctx, out->current, ctx->d_current.p, n_cross(ctx) * 8, dev, st)) ||
+      (s = copy_out(ctx, out->field, ctx->d_field.p, (size_t)NSP * ctx->nz * ctx->ntb * 8, dev, st)))
+    return s;
+  CK(cudaStreamSynchronize(st));
+  return KARL_OK;
+}
+
+// Fields of zero for every recombination channel (the first cycle).
+karl_status zero_fields(karl_ctx* ctx, cudaStream_t st) {
+  size_t nk = (size_t)std::max(ctx->nch, 1);
+  CK(ctx->d_frate.ensure(nk * ctx->nz));
+  CK(ctx->d_fcol.ensure(nk * (ctx->nz + 1)));
+  CK(cudaMemsetAsync(ctx->d_frate.p, 0, nk * ctx->nz * 8, st));
+  CK(cudaMemsetAsync(ctx->d_fcol.p, 0, nk * (ctx->nz + 1) * 8, st));
+  return KARL_OK;
+}
+
+karl_status check_tally_ptrs(karl_ctx* ctx, const karl_tallies* out) {
+  if (!out->spectrum || !out->time_fx || !out->cross_pos || !out->cross_neg || !out->recomb ||
+      !out->ledger || (ctx->nch > 0 && !out->chan_count))
+    return fail(ctx, KARL_EINVAL, "tally buffer is NULL");
+  return KARL_OK;
+}
+
+karl_status karl_run_cycle(karl_ctx* ctx, const karl_primaries* pr, const karl_run_opts* o,
+                           const uint64_t* field_time_in, const uint64_t* field_recomb_in,
+                           double field_decays, karl_tallies* out) {
+  if (!ctx) return KARL_EINVAL;
+  ctx->err.clear();
+  ctx->drop_retired();
+  if (!pr || !out || pr->n < 0) return fail(ctx, KARL_EINVAL, "NULL argument or n < 0");
+  karl_status s = check_opts(ctx, o);
+  if (s) return s;
+  if (field_time_in && !(field_decays > 0.0) ) return fail(ctx, KARL_EINVAL, "field_decays must be > 0");
+  if ((s = check_tally_ptrs(ctx, out))) return s;
+  cudaStream_t st = o->stream ? (cudaStream_t)o->stream : ctx->own_stream;
+  const double *pz, *pe, *pmu;
+  const uint8_t* psp;
+  ctx->stats.kernel_launches = 0;
+  s = stage_primaries(ctx, pr, st, &pz, &pe, &pmu, &psp);
+  if (s) return s;
+  if (field_time_in) {
+    CK(ctx->d_time1.ensure(n_time(ctx)));
+    CK(cudaMemcpyAsync(ctx->d_time1.p, field_time_in, n_time(ctx) * 8, cudaMemcpyHostToDevice, st));
+    const unsigned long long* rec = nullptr;
+    if (field_recomb_in) {
+      CK(ctx->d_recin.ensure(n_recomb(ctx)));
+      CK(cudaMemcpyAsync(ctx->d_recin.p, field_recomb_in, n_recomb(ctx) * 8,
+                         cudaMemcpyHostToDevice, st));
+      rec = ctx->d_recin.p;
+    }
+    s = build_fields(ctx, (const unsigned long long*)ctx->d_time1.p, rec, field_decays, st);
+  } else {
+    s = zero_fields(ctx, st);
+  }
+  if (s) return s;
+  bool pp = out->per_primary != nullptr && pr->n > 0;
+  s = run_one_pass(ctx, pr, o, 2, pz, pe, pmu, psp, pp, st);
+  if (s) return s;
+  struct Item { void* dst; const void* src; size_t n; };
+  Item items[] = {
+      {out->spectrum, ctx->d_spec.p, n_spec(ctx)}, {out->time_fx, ctx->d_time.p, n_time(ctx)},
+      {out->cross_pos, ctx->d_cpos.p, n_cross(ctx)}, {out->cross_neg, ctx->d_cneg.p, n_cross(ctx)},
+      {out->recomb, ctx->d_recomb.p, n_recomb(ctx)}, {out->ledger, ctx->d_ledger.p, (size_t)LEDGER},
+      {out->chan_count, ctx->d_chan.p, (size_t)ctx->nch},
+      {pp ? out->per_primary : nullptr, ctx->d_pp.p, (size_t)pr->n}};
+  for (const Item& it : items) {
+    if (!it.dst || it.n == 0) continue;
+    if (out->on_device) {
+      k_accumulate<<<grid_for(it.n, 256), 256, 0, st>>>((unsigned long long*)it.dst,
+                                                         (const unsigned long long*)it.src, it.n);
+      CK(cudaGetLastError());
+      ctx->stats.kernel_launches += 1;
+    } else {
+      std::vector<unsigned long long> tmp(it.n);
+      CK(cudaMemcpyAsync(tmp.data(), it.src, it.n * 8, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      unsigned long long* d = (unsigned long long*)it.dst;
+      for (size_t i = 0; i < it.n; ++i) d[i] += tmp[i];
+    }
+  }
+  CK(cudaStreamSynchronize(st));
+  return KARL_OK;
+}
+
+karl_status karl_run_cycles(karl_ctx* ctx, const karl_primaries* pr, const karl_run_opts* o,
+                            int32_t n_cycles, karl_tallies* out) {
+  if (!ctx) return KARL_EINVAL;
+  ctx->err.clear();
+  ctx->drop_retired();
+  if (!pr || !out || pr->n < 0) return fail(ctx, KARL_EINVAL, "NULL argument or n < 0");
+  karl_status s = check_opts(ctx, o);
+  if (s) return s;
+  if (n_cycles < 1) return fail(ctx, KARL_EINVAL, "n_cycles must be >= 1");
+  if (!(pr->n_decays > 0)) return fail(ctx, KARL_EINVAL, "n_decays must be > 0");
+  if ((s = check_tally_ptrs(ctx, out))) return s;
+  cudaStream_t st = o->stream ? (cudaStream_t)o->stream : ctx->own_stream;
+  const double *pz, *pe, *pmu;
+  const uint8_t* psp;
+  std::memset(ctx->stats.kernel_ms, 0, sizeof ctx->stats.kernel_ms);
+  ctx->stats.kernel_launches = 0;
+  s = stage_primaries(ctx, pr, st, &pz, &pe, &pmu, &psp);
+  if (s) return s;
+  const size_t nt = n_time(ctx), nn = (size_t)std::max<int64_t>(pr->n, 1);
+  const bool pp = out->per_primary != nullptr && pr->n > 0;
+  struct Sum { DevBuf<unsigned long long>* cum; DevBuf<unsigned long long>* one; size_t n; };
+  Sum sums[] = {{&ctx->c_spec, &ctx->d_spec, n_spec(ctx)}, {&ctx->c_time, &ctx->d_time, nt},
+                {&ctx->c_cpos, &ctx->d_cpos, n_cross(ctx)}, {&ctx->c_cneg, &ctx->d_cneg, n_cross(ctx)},
+                {&ctx->c_rec, &ctx->d_recomb, n_recomb(ctx)}, {&ctx->c_led, &ctx->d_ledger, (size_t)LEDGER},
+                {&ctx->c_chan, &ctx->d_chan, (size_t)MAXCH}};
+  for (Sum& x : sums) {
+    CK(x.cum->ensure(x.n));
+    CK(cudaMemsetAsync(x.cum->p, 0, x.n * 8, st));
+  }
+  if (pp) CK(ctx->c_pp.ensure(nn));
+  double kms = 0.0;
+  int64_t colls = 0, flights = 0, parts = 0;
+  const int64_t n = pr->n;
+  for (int c = 0; c < n_cycles; ++c) {
+    const int64_t lo = n * c / n_cycles, hi = n * (c + 1) / n_cycles;
+    if (hi <= lo) continue;
+    if (lo == 0) {
+      s = zero_fields(ctx, st);
+    } else {
+      // the fields of every cycle before this one (Sec. 3.6)
+      s = build_fields(ctx, ctx->c_time.p, ctx->c_rec.p,
+                       (double)pr->n_decays * (double)lo / (double)n, st);
+    }
+    if (s) return s;
+    karl_primaries sl = *pr;
+    sl.n = hi - lo;
+    sl.pid_offset = pr->pid_offset + lo;
+    s = run_one_pass(ctx, &sl, o, 2, pz + lo, pe + lo, pmu + lo, psp + lo, pp, st);
+    if (s) return s;
+    kms += ctx->stats.kernel_ms[1];
+    colls += ctx->stats.collisions[1];
+    flights += ctx->stats.flights[1];
+    parts += ctx->stats.particles[1];
+    for (Sum& x : sums) {
+      k_accumulate<<<grid_for(x.n, 256), 256, 0, st>>>(x.cum->p, x.one->p, x.n);
+      CK(cudaGetLastError());
+      ctx->stats.kernel_launches += 1;
+    }
+    if (pp) CK(cudaMemcpyAsync(ctx->c_pp.p + lo, ctx->d_pp.p, (size_t)(hi - lo) * 8,
+                               cudaMemcpyDeviceToDevice, st));
+  }
+  ctx->stats.kernel_ms[0] = 0.0;
+  ctx->stats.kernel_ms[1] = kms;
+  ctx->stats.collisions[0] = 0;
+  ctx->stats.collisions[1] = colls;
+  ctx->stats.flights[1] = flights;
+  ctx->stats.particles[1] = parts;
+  // normalisation over the whole run (Eq. target_field_density, Sec. 2.3)
+  const double tsim = (double)pr->n_decays / ctx->activity;
+  const double vol = ctx->dz * ctx->area;
+  CK(ctx->d_density.ensure((size_t)NSP * ctx->nz));
+  CK(ctx->d_current.ensure(n_cross(ctx)));
+  CK(ctx->d_field.ensure((size_t)NSP * ctx->nz * ctx->ntb));
+  k_normalize<<<grid_for(n_cross(ctx), 256), 256, 0, st>>>(
+      ctx->c_time.p, ctx->c_time.p, ctx->c_rec.p, ctx->c_cpos.p, ctx->c_cneg.p, ctx->d_density.p,
+      ctx->d_current.p, ctx->d_field.p, ctx->nz, ctx->ntb, tsim, vol, ctx->area, 1);
+  CK(cudaGetLastError());
+  ctx->stats.kernel_launches += 1;
+  const bool dev = out->on_device != 0;
+  if ((s = copy_out(ctx, out->spectrum, ctx->c_spec.p, n_spec(ctx) * 8, dev, st)) ||
+      (s = copy_out(ctx, out->time_fx, ctx->c_time.p, nt * 8, dev, st)) ||
+      (s = copy_out(ctx, out->cross_pos, ctx->c_cpos.p, n_cross(ctx) * 8, dev, st)) ||
+      (s = copy_out(ctx, out->cross_neg, ctx->c_cneg.p, n_cross(ctx) * 8, dev, st)) ||
+      (s = copy_out(ctx, out->recomb, ctx->c_rec.p, n_recomb(ctx) * 8, dev, st)) ||
+      (s = copy_out(ctx, out->ledger, ctx->c_led.p, LEDGER * 8, dev, st)) ||
+      (s = copy_out(ctx, out->chan_count, ctx->c_chan.p, (size_t)ctx->nch * 8, dev, st)) ||
+      (s = copy_out(ctx, pp ? out->per_primary : nullptr, ctx->c_pp.p, (size_t)n * 8, dev, st)) ||
       (s = copy_out(ctx, out->density, ctx->d_density.p, (size_t)NSP * ctx->nz * 8, dev, st)) ||
       (s = copy_out(ctx, out->current, ctx->d_current.p, n_cross(ctx) * 8, dev, st)) ||
       (s = copy_out(ctx, out->field, ctx->d_field.p, (size_t)NSP * ctx->nz * ctx->ntb * 8, dev, st)))
@@ -1100,7 +1298,7 @@ extern "C" karl_status karl_run_pass_static(karl_ctx* ctx, const karl_primaries*
     }
     CK(cudaMemsetAsync(frate, 0, nk * ctx->nz * 8, st));
     k_build_fields<<<grid_for((size_t)ctx->nch * ctx->nz, 256), 256, 0, st>>>(
-        A, (const unsigned long long*)field_time_in, ctx->d_sig.p, frate, fcol);
+        A, (const unsigned long long*)field_time_in, nullptr, ctx->d_sig.p, frate, fcol);
     k_field_columns<<<1, 32, 0, st>>>(frate, fcol, ctx->nch, ctx->nz, ctx->dz);
     CK(cudaGetLastError());
     ctx->stats.kernel_launches += 2;

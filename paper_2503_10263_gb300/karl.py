@@ -123,6 +123,9 @@ def load() -> C.CDLL:
                                   C.c_void_p, P(Tallies)]
     lib.karl_run_pass_static.argtypes = [C.c_void_p, P(Primaries), P(RunOpts), C.c_int32,
                                          C.c_void_p, P(Tallies)]
+    lib.karl_run_cycles.argtypes = [C.c_void_p, P(Primaries), P(RunOpts), C.c_int32, P(Tallies)]
+    lib.karl_run_cycle.argtypes = [C.c_void_p, P(Primaries), P(RunOpts), C.c_void_p, C.c_void_p,
+                                   C.c_double, P(Tallies)]
     lib.karl_destroy.argtypes = [C.c_void_p]
     lib.karl_destroy.restype = None
     lib.karl_cancel.argtypes = [C.c_void_p]
@@ -134,7 +137,7 @@ def load() -> C.CDLL:
     lib.karl_tally_layout.argtypes = [C.c_void_p, P(Layout)]
     lib.karl_last_stats.argtypes = [C.c_void_p, P(RunStats)]
     for f in ("karl_create", "karl_run", "karl_run_pass", "karl_run_pass_static",
-              "karl_tally_layout", "karl_last_stats"):
+              "karl_run_cycles", "karl_run_cycle", "karl_tally_layout", "karl_last_stats"):
         getattr(lib, f).restype = C.c_int
     _lib = lib
     return lib
@@ -170,6 +173,16 @@ def karl_run_pass_static(ctx, prim: Primaries, opts: RunOpts, pass_index: int, f
     buffers only, tallies overwritten, nothing allocated by the call."""
     return load().karl_run_pass_static(ctx, C.byref(prim), C.byref(opts), pass_index,
                                        field_time_in, C.byref(tallies))
+
+
+def karl_run_cycles(ctx, prim: Primaries, opts: RunOpts, n_cycles: int, tallies: Tallies) -> int:
+    return load().karl_run_cycles(ctx, C.byref(prim), C.byref(opts), n_cycles, C.byref(tallies))
+
+
+def karl_run_cycle(ctx, prim: Primaries, opts: RunOpts, field_time_in, field_recomb_in,
+                   field_decays: float, tallies: Tallies) -> int:
+    return load().karl_run_cycle(ctx, C.byref(prim), C.byref(opts), field_time_in,
+                                 field_recomb_in, field_decays, C.byref(tallies))
 
 
 def karl_destroy(ctx) -> None:
@@ -307,6 +320,36 @@ class Context:
             fin = np.ascontiguousarray(field_time_in, np.uint64)
         self._check(karl_run_pass(self.ctx, ps, o, pass_index,
                                   fin.ctypes.data if fin is not None else None, ts))
+        t["per_primary"] = t["per_primary"][:prims.n]
+        t["chan_count"] = t["chan_count"][:self.prob.n_channels]
+        return t
+
+    def run_cycles(self, prims, seed: int, n_cycles: int, precision: int = FP64,
+                   per_primary: bool = True, **kw) -> Dict[str, np.ndarray]:
+        """The continuous field update over the whole run (karl_run_cycles)."""
+        ps, keep = self.host_primaries(prims)
+        t = self.empty_tallies(prims.n)
+        ts = self.host_tallies(t, per_primary)
+        o = self.opts(seed, 2, precision, **kw)
+        self._check(karl_run_cycles(self.ctx, ps, o, n_cycles, ts))
+        t["per_primary"] = t["per_primary"][:prims.n]
+        t["chan_count"] = t["chan_count"][:self.prob.n_channels]
+        return t
+
+    def run_cycle(self, prims, seed: int, field_time_in=None, field_recomb_in=None,
+                  field_decays: float = 0.0, pid_offset: int = 0, precision: int = FP64,
+                  **kw) -> Dict[str, np.ndarray]:
+        """One cycle over a primary-id range with the given fields, raw
+        tallies (karl_run_cycle)."""
+        ps, keep = self.host_primaries(prims, pid_offset)
+        t = self.empty_tallies(prims.n)
+        ts = self.host_tallies(t, True, with_norm=False)
+        o = self.opts(seed, 2, precision, **kw)
+        fin = None if field_time_in is None else np.ascontiguousarray(field_time_in, np.uint64)
+        rin = None if field_recomb_in is None else np.ascontiguousarray(field_recomb_in, np.uint64)
+        self._check(karl_run_cycle(self.ctx, ps, o, fin.ctypes.data if fin is not None else None,
+                                   rin.ctypes.data if rin is not None else None,
+                                   float(field_decays), ts))
         t["per_primary"] = t["per_primary"][:prims.n]
         t["chan_count"] = t["chan_count"][:self.prob.n_channels]
         return t
