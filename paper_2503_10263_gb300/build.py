@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libkarl.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 SOURCES = ["karl_abi.cu", "transport.cu", "multi.cu", "server.cu"]
-HEADERS = ["karl_device.cuh", "event.cuh", "multi.cuh", "host_common.h"]
+HEADERS = ["karl_device.cuh", "event.cuh", "multi.cuh", "host_common.h", "log_table.inc"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -24,7 +24,7 @@ template <> struct RT<false> {
   using R = double;
   static __device__ __forceinline__ R u(unsigned long long w) { return u01d(w); }
   static __device__ __forceinline__ R eta(unsigned long long w) { return eta01d(w); }
-  static __device__ __forceinline__ R lg(R x) { return log(x); }
+  static __device__ __forceinline__ R lg(R x) { return log_tab(x); }
   static __device__ __forceinline__ R sq(R x) { return sqrt(x); }
   static __device__ __forceinline__ R rsq(R x) { return rsqrt(x); }
   static __device__ __forceinline__ R tn(R x) { return tan(x); }

@@ -185,6 +185,30 @@ __device__ __forceinline__ unsigned long long child_node(unsigned long long pare
   return mix64(mix64(parent) ^ (((unsigned long long)ev << 2) | slot));
 }
 
+// ln x for positive normal x, table-driven (P. T. P. Tang, "Table-driven
+// implementation of the logarithm function in IEEE floating-point
+// arithmetic", ACM TOMS 16, 1990): x = 2^k m with m in [1, 2) in one of 256
+// cells of centre c_j, m = c_j (1 + r), |r| <= 1/512, and
+// ln x = k ln 2 + ln c_j + ln(1 + r), the last by its Taylor series to r^6
+// (truncation below 3e-20).  Absolute error about 2e-16 (the rounding of
+// 1/c_j carried into r) plus the rounding of k ln 2: the accuracy the flight
+// optical depth and the table position need, in about 9 FP64 operations.
+__device__ const double2 karl_log_cells[256] = {
+#include "log_table.inc"
+};
+
+__device__ __forceinline__ double log_tab(double x) {
+  const long long bits = __double_as_longlong(x);
+  const int k = (int)((bits >> 52) & 0x7ff) - 1023;
+  const int j = (int)((bits >> 44) & 0xff);
+  const double m = __longlong_as_double((bits & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+  const double2 c = __ldg(karl_log_cells + j);            // (ln c_j, 1 / c_j)
+  const double r = fma(m, c.y, -1.0);
+  const double p =
+      r * (1.0 + r * (-0.5 + r * (1.0 / 3.0 + r * (-0.25 + r * (0.2 - r * (1.0 / 6.0))))));
+  return fma((double)k, 0.69314718055994530942, c.x + p);
+}
+
 // uniforms from the top bits of a 64-bit word
 __device__ __forceinline__ double u01d(unsigned long long w) {
   return (double)(w >> 11) * (1.0 / 9007199254740992.0);
