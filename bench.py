@@ -44,9 +44,9 @@ BYTES_PER_EVENT_FP32 = 80
 #   DRAM_BYTES: dram__bytes_read.sum + dram__bytes_write.sum, scaled to a launch
 #     by its collisions.
 # None: not measured for the kernel as it stands.
-FP64_OPS_PER_COLLISION = {"fp64": 168.7, "fp32": 30.77}
-FP64_PIPE_CYCLES_PER_COLLISION = {"fp64": 133.9, "fp32": 52.4}
-DRAM_BYTES_PER_COLLISION = {"fp64": 210310912 / 1665598248, "fp32": 271645440 / 1665592914}
+FP64_OPS_PER_COLLISION = {"fp64": 127.4, "fp32": 30.77}
+FP64_PIPE_CYCLES_PER_COLLISION = {"fp64": 113.3, "fp32": 51.4}
+DRAM_BYTES_PER_COLLISION = {"fp64": 185384448 / 1665598248, "fp32": 267528960 / 1665592914}
 FP64_OPS_PER_SM_CYCLE = 2
 WORKLOAD = ("config2: 1e7 decays (1e7 beta e- + 1e7 thermal T2+), parabolic profile with "
             "5e21 m^-2 column, L = 10 m, 1000 z segments, 7 e- channels + T2+ clustering + "
