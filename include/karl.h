@@ -199,7 +199,7 @@ typedef struct karl_run_opts {
   uint64_t seed;
   int32_t n_passes;            /* 1, or 2 when recombination channels exist */
   int32_t precision;           /* KARL_FP64 (plain) or KARL_FP32 (precision form) */
-  int32_t block_size;          /* 0 = default */
+  int32_t block_size;          /* 0 = default (FP64 form 256, FP32 form 128) */
   int32_t blocks_per_sm;       /* 0 = occupancy maximum */
   double timeout_s;            /* kernel time limit; <= 0 = 600 s */
   void* stream;                /* cudaStream_t, NULL = the context's own stream */

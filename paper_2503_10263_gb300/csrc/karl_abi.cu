@@ -438,6 +438,13 @@ size_t n_cross_rg(const karl_ctx* c) { return (size_t)NSP * (c->nz + 2); }
 size_t n_cross(const karl_ctx* c) { return (size_t)NSP * (c->nz + 1); }
 size_t n_recomb(const karl_ctx* c) { return (size_t)NSP * c->nz; }
 
+// Default threads per block of the transport kernel (resident blocks per SM:
+// the occupancy maximum).  Measured on the config-2 step (5e6 decays): the
+// FP64 form is fastest with 256-thread blocks, 2 per SM; the FP32 form with
+// 128-thread blocks, 4 per SM (3.3e9 against 2.7e9 collisions/s; with
+// 256-thread blocks its pass 1 kept only 79 % of its lanes busy).
+int default_block(bool f32) { return f32 ? 128 : 256; }
+
 karl_status ensure_ring(karl_ctx* ctx, unsigned long long cap) {
   if (ctx->ring_cap >= cap) return KARL_OK;
   size_t n = (size_t)cap;
@@ -491,7 +498,7 @@ karl_status run_one_pass(karl_ctx* ctx, const karl_primaries* pr, const karl_run
   CK(ctx->d_chan.ensure(MAXCH));
   if (per_primary) CK(ctx->d_pp.ensure((size_t)std::max<int64_t>(pr->n, 1)));
   bool f32 = o->precision == KARL_FP32;
-  int block = o->block_size > 0 ? o->block_size : 256;
+  int block = o->block_size > 0 ? o->block_size : default_block(f32);
   int grid = 0;
   unsigned long long cap = ctx->ring_cap ? ctx->ring_cap : (1ULL << 22);
   double timeout = o->timeout_s > 0 ? o->timeout_s : 600.0;
@@ -1322,7 +1329,7 @@ extern "C" karl_status karl_run_pass_static(karl_ctx* ctx, const karl_primaries*
   P.per_primary = pp ? (unsigned long long*)out->per_primary : nullptr;
 
   const bool f32 = o->precision == KARL_FP32;
-  const int block = o->block_size > 0 ? o->block_size : 256;
+  const int block = o->block_size > 0 ? o->block_size : default_block(f32);
   int bps = 0;
   CK(transport_occupancy(f32, P, block, &bps));
   if (o->blocks_per_sm > 0) bps = std::min(bps, (int)o->blocks_per_sm);
