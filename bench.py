@@ -552,7 +552,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--decays", type=int, default=10_000_000)
-    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    # default: the plain method (config 2) in FP64, the batched and served
+    # forms (configs 4 and 5) in FP32, as their workloads specify
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default=None)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--timeout", type=float, default=600.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -566,6 +568,8 @@ def main():
     ap.add_argument("--compare-plain", action="store_true",
                     help="config4/config5: also run the requests one at a time through karl_run")
     args = ap.parse_args()
+    if args.precision is None:
+        args.precision = "fp64" if args.workload == "config2" else "fp32"
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "config4":
