@@ -51,3 +51,31 @@ def run_sharded(run_pass: Callable, prims, seed: int, n_passes: int, rank: int,
     for k in RAW_KEYS:
         out[k] = _allreduce_sum(t[k]) if world > 1 else t[k]
     return out
+
+
+def run_cycles_sharded(run_cycle: Callable, prims, seed: int, n_cycles: int, rank: int,
+                       world: int) -> Dict[str, np.ndarray]:
+    """The continuous field update (Sec. 3.6) split over `world` ranks: every
+    cycle's primary-id range [c n / C, (c+1) n / C) is split over the ranks,
+    each rank runs its part with the fields of the summed tallies of the
+    cycles before (the same on every rank), and one integer all-reduce per
+    cycle adds the cycle's raw tallies -- the paper's synchronisation step
+    after each cycle.  ``run_cycle(prims_slice, seed, field_time_in,
+    field_recomb_in, field_decays, pid_offset)`` is the per-rank cycle
+    (``karl.Context.run_cycle`` on a GPU).  Returns the raw tallies summed
+    over all cycles and ranks (identical on every rank)."""
+    n = prims.n
+    tot: Dict[str, np.ndarray] = {}
+    for c in range(n_cycles):
+        lo, hi = c * n // n_cycles, (c + 1) * n // n_cycles
+        if hi <= lo:
+            continue
+        a, b = shard_range(hi - lo, rank, world)
+        a, b = lo + a, lo + b
+        first = not tot
+        t = run_cycle(prims.slice(a, b - a), seed, None if first else tot["time_fx"],
+                      None if first else tot["recomb"], prims.n_decays * lo / n, a)
+        for k in RAW_KEYS:
+            s = _allreduce_sum(t[k]) if world > 1 else t[k]
+            tot[k] = s if k not in tot else tot[k] + s
+    return tot

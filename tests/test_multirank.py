@@ -51,6 +51,43 @@ def test_two_gloo_ranks_equal_single_run(tmp_path):
         np.testing.assert_array_equal(r0[k], full[k], err_msg=k)
 
 
+def _cycle_worker(rank, world, port, out_dir):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    prob, prims = _cycled_problem()
+
+    def run_cycle(p, seed, field, rec, decays, pid_offset):
+        return oracle.run_cycle(prob, p, seed, field, rec, decays, pid_offset=pid_offset)
+
+    t = shard.run_cycles_sharded(run_cycle, prims, seed=17, n_cycles=3, rank=rank, world=world)
+    np.savez(os.path.join(out_dir, f"cyc{rank}.npz"), **t)
+    dist.destroy_process_group()
+
+
+def _cycled_problem():
+    prob, prims = inputs.config2(n_decays=150, seed=8, column_m2=2e21, length=4.0, nz=100)
+    prob.activity_bq *= 1e9                                 # fields that matter
+    return prob, prims
+
+
+def test_two_gloo_ranks_cycles_equal_single_run(tmp_path):
+    # the continuous field update split over ranks, one all-reduce per cycle
+    oracle.build()
+    world = 2
+    mp.start_processes(_cycle_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world,
+                       join=True, start_method="spawn")
+    prob, prims = _cycled_problem()
+    full = oracle.run_cycles(prob, prims, 17, 3)
+    r0 = np.load(tmp_path / "cyc0.npz")
+    r1 = np.load(tmp_path / "cyc1.npz")
+    assert int(np.sum(full["recomb"])) > 0
+    for k in shard.RAW_KEYS:
+        np.testing.assert_array_equal(r0[k], r1[k], err_msg=k)
+        np.testing.assert_array_equal(r0[k], full[k], err_msg=k)
+
+
 def test_shard_ranges_cover_all_primaries():
     for n in (0, 1, 7, 1000):
         for world in (1, 2, 3, 8):
