@@ -7,10 +7,22 @@
 #include <cstring>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/karl.h"
 #include "karl_device.cuh"
 
 namespace karl {
+
+// A named range on a profiler's timeline (NVTX): passes, cycles, field
+// builds and server launches show up by name in Nsight; without a tool
+// attached the calls do nothing.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 constexpr double HOST_Q_ENERGY = 16777216.0;    // 2^24 units per eV
 constexpr double HOST_KB_EV = 8.617333262e-5;   // Boltzmann constant, eV/K

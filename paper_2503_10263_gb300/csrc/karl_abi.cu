@@ -487,6 +487,7 @@ void base_params(const karl_ctx* c, Params& P, const karl_run_opts* o, int pass)
 karl_status run_one_pass(karl_ctx* ctx, const karl_primaries* pr, const karl_run_opts* o,
                          int pass, const double* pz, const double* pe, const double* pmu,
                          const uint8_t* psp, bool per_primary, cudaStream_t st) {
+  TraceRange trace(pass == 1 ? "karl transport pass 1" : "karl transport pass 2");
   size_t nt = n_time(ctx);
   CK(ctx->d_spec.ensure(n_spec(ctx)));
   CK(ctx->d_tpt.ensure(nt));
@@ -603,6 +604,7 @@ karl_status run_one_pass(karl_ctx* ctx, const karl_primaries* pr, const karl_run
 
 karl_status build_fields(karl_ctx* ctx, const unsigned long long* d_time1,
                          const unsigned long long* d_recomb, double n_decays, cudaStream_t st) {
+  TraceRange trace("karl target fields");
   FieldArgs A;
   std::memset(&A, 0, sizeof A);
   A.nz = ctx->nz;
@@ -1062,6 +1064,9 @@ karl_status karl_run_cycles(karl_ctx* ctx, const karl_primaries* pr, const karl_
                        (double)pr->n_decays * (double)lo / (double)n, st);
     }
     if (s) return s;
+    char name[48];
+    snprintf(name, sizeof name, "karl cycle %d", c);
+    TraceRange trace(name);
     karl_primaries sl = *pr;
     sl.n = hi - lo;
     sl.pid_offset = pr->pid_offset + lo;

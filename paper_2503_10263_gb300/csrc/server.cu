@@ -233,6 +233,7 @@ karl_status launch(karl_server* srv) {
   SCK(multi_occupancy(f32, srv->opts.block_size, &bps));
   if (srv->opts.blocks_per_sm > 0) bps = std::min(bps, (int)srv->opts.blocks_per_sm);
   bps = std::max(bps, 1);
+  TraceRange trace("karl server launch");
   SCK(cudaEventRecord(srv->ev0, srv->kstream));
   SCK(launch_multi(f32, srv->d_desc, srv->d_ctl, srv->d_M, srv->ring, srv->d_cancel,
                    (unsigned long long)(srv->opts.timeout_s * 1e9), srv->num_sms * bps,
