@@ -10,6 +10,12 @@
  * mover rule of Sec. 3.1, the interactions of Sec. 3.3, the density-field and
  * current estimators of Secs. 2.2-2.3 and Eq. target_field_density) in FP64.
  * It shares no code with the GPU path.
+ *
+ * Pins (tests/test_oracle_*.py) fix every step against closed forms,
+ * quadrature, library routines and exact invariants.  The whole-run tallies
+ * of the full configurations (orc_run on configs 1 and 2) have no closed
+ * form: parity unpinned beyond their pinned parts and the invariants (exact
+ * ledgers, spectrum and crossing counts against deaths, shard additivity).
  */
 #ifndef KARL_ORACLE_H
 #define KARL_ORACLE_H
