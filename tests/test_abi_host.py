@@ -129,3 +129,21 @@ def test_create_rejects_invalid_ion_chemistry_without_gpu(karl):
         with pytest.raises(karl.KarlError) as ei:
             karl.Context(p)
         assert ei.value.status == karl.EINVAL
+
+
+def test_shipped_problems_pass_host_validation():
+    # karl_create checks every argument before its first CUDA call: without a
+    # GPU a valid problem fails later, with KARL_ECUDA, an invalid one with
+    # KARL_EINVAL.  Every problem builder of inputs.py must pass the checks.
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("with a GPU the problems are created for real by the GPU tests")
+    from paper_2503_10263_gb300 import karl as k
+    probs = [inputs.config1(n_primaries=10)[0], inputs.config2(n_decays=10)[0],
+             inputs.angular_config(n_primaries=10)[0], inputs.thermalization(n_primaries=10)[0],
+             inputs.chemistry_config(10)[0],
+             inputs.charge_exchange_problem(1e20, 1.0, 10, 80.0)]
+    for p in probs:
+        with pytest.raises(k.KarlError) as ei:
+            k.Context(p)
+        assert ei.value.status == k.ECUDA, p.name

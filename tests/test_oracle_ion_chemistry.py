@@ -185,3 +185,25 @@ def test_charge_exchange_direction_favours_head_on_targets():
     expect = cf.cx_one_collision_mean_wz(x0)
     assert expect < -0.1
     assert abs(wz.mean() - expect) < 5 * wz.std() / math.sqrt(n)
+
+
+def test_segment_stop_and_optical_depth_agree_for_three_body():
+    # Sec. 3.1's segment stop-and-redraw and one optical-depth draw per flight
+    # are equal in law; with the n^2 rate of three-body clustering on a ramp
+    # both give the survival exp(-s3 sum n_j^2 dz) at the far end
+    nz, length = 20, 1.0
+    n_seg = np.linspace(2e21, 2e22, nz)
+    dz = length / nz
+    s3 = 1.0 / float(np.sum(n_seg ** 2) * dz)
+    nodes = inputs.energy_nodes(64, 1e-3, 10.0)
+    ch = inputs.Channel("clust3", inputs.CLUSTERING3, inputs.TP, inputs.T3P, 0.0,
+                        np.full_like(nodes, s3))
+    prob = _ion_problem([ch], n_seg, length, 1e-3, 10.0)
+    n = 60_000
+    beam = inputs.beam(n, 0.0, 0.05, 1.0, inputs.TP)
+    a = oracle.run(prob, beam, seed=18, mode=0, n_threads=THREADS)
+    b = oracle.run(prob, beam, seed=19, mode=1, n_threads=THREADS)
+    p = math.exp(-1.0)
+    for r in (a, b):
+        k = int(r["cross_pos"][inputs.TP][-1])
+        assert abs(k - n * p) < 4 * math.sqrt(n * p * (1 - p)), k
