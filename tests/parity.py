@@ -97,3 +97,45 @@ def coarse_groups(x: np.ndarray, groups: int) -> np.ndarray:
     k, n = x.shape
     edges = np.linspace(0, n, groups + 1).astype(int)
     return np.stack([x[:, a:b].sum(1) for a, b in zip(edges[:-1], edges[1:])], axis=1)
+
+
+def excursion_bound(n: int, p: float) -> float:
+    """Largest count of bins beyond the threshold that chance allows in n
+    independent bins of tail probability p (mean + 3 standard deviations)."""
+    return n * p + 3.0 * math.sqrt(n * p * (1.0 - p)) + 1
+
+
+def deviation_summary(z: np.ndarray, dof: int) -> dict:
+    """Per-bin deviations z (in standard errors) of one tally: median and
+    largest |z|, the count beyond 3 with the count chance allows for a
+    t distribution of `dof` degrees of freedom (standard errors estimated from
+    batches), and the chi^2 p-value of sum z^2."""
+    from scipy import stats
+    z = np.asarray(z, np.float64).ravel()
+    n = int(z.size)
+    if n == 0:
+        return {"bins": 0, "median_abs_z": 0.0, "max_abs_z": 0.0, "beyond_3": 0,
+                "allowed_beyond_3": 1.0, "chi2_p": 1.0}
+    p3 = float(2.0 * stats.t.sf(3.0, dof))
+    # sum of squared t variables: compare with n * dof/(dof-2) mean by a
+    # chi^2 of the rescaled statistic (close for dof >= 30)
+    scale = dof / (dof - 2.0) if dof > 2 else 1.0
+    chi2 = float(np.sum(z ** 2) / scale)
+    return {"bins": n, "median_abs_z": float(np.median(np.abs(z))),
+            "max_abs_z": float(np.max(np.abs(z))), "beyond_3": int(np.sum(np.abs(z) > 3.0)),
+            "allowed_beyond_3": excursion_bound(n, p3), "chi2_p": float(stats.chi2.sf(chi2, n))}
+
+
+def batches_vs_total(g_batches: np.ndarray, o_total: np.ndarray, min_mean: float = 0.0):
+    """z-scores of the summed batches of one implementation against the total
+    of another run of the same primaries, with the variance of either total
+    estimated from the batches (both totals have it when they agree in law).
+    Bins whose batch mean is at most min_mean, or have no spread, are left out."""
+    g = np.asarray(g_batches, np.float64)
+    k = g.shape[0]
+    g = g.reshape(k, -1)
+    o = np.asarray(o_total, np.float64).ravel()
+    var_tot = k * g.var(axis=0, ddof=1)
+    keep = (var_tot > 0) & (g.mean(axis=0) > min_mean)
+    z = (g.sum(axis=0)[keep] - o[keep]) / np.sqrt(2.0 * var_tot[keep])
+    return z, k - 1

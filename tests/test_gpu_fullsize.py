@@ -1,18 +1,29 @@
 """Parity at the full size of the two-pass plain method: 1e7 tritium decays
-(2e7 primaries) on the 10 m, 1000-segment parabolic column, FP64, in the
-launch configuration the benchmark times (default launch shape, host buffers
-through karl_run / karl_run_pass).
+(2e7 primaries) on the 10 m, 1000-segment parabolic column, in the launch
+configuration the benchmark times (default launch shape, host buffers through
+karl_run / karl_run_pass).
 
-The oracle cannot run 3e10 collisions in a test, so:
-  * pass 1 (gas only) histories are independent of one another: a sample of
-    primary-id ranges is re-run one by one through the oracle with the same
-    seed and ids, and the per-primary collision counts must coincide;
-  * every whole-run tally is checked through properties that hold at any
-    size: energy and particle ledger balance, spectrum counts equal exit
-    deaths, end-face crossings equal exit deaths, channel counts sum to the
-    collisions, recombination-partner deletions equal recombination deaths;
-  * integer tallies are bit-reproducible run to run (integer atomics commute).
+* Pass 1 (gas only) is run whole by the oracle (about 1.7e10 collisions, a few
+  minutes on the host's cores): every primary's history is compared, and the
+  recombination target field of Eq. target_field_density (the pass-1
+  densities per species, segment and energy bin) must agree within 1e-3
+  relative L2.
+* Pass 2 is run on the GPU with the oracle's own pass-1 time tally, so both
+  sides recombine against the same frozen fields; sampled primary-id ranges
+  are re-run by the oracle and their histories compared.
+* The FP32 precision form runs the same workload against the FP64 oracle:
+  every tally bin is compared in standard errors estimated from primary-id
+  batches (3-sigma excursion count and chi^2), and the field's relative L2 is
+  reported beside its noise floor.
+* Properties that hold at any size (ledger balance, spectrum counts equal exit
+  deaths, end-face crossings equal exit deaths, channel counts sum to the
+  collisions, recombination-partner deletions equal recombination deaths) and
+  bit-reproducibility of the integer tallies are checked on the whole runs.
 """
+import math
+import os
+import time
+
 import numpy as np
 import pytest
 
@@ -25,6 +36,7 @@ pytestmark = pytest.mark.gpu
 SEED = 1000
 RAW = ("spectrum", "time_fx", "cross_pos", "cross_neg", "recomb", "ledger", "chan_count",
        "per_primary")
+THREADS = os.cpu_count() or 1
 
 
 @pytest.fixture(scope="module")
@@ -49,6 +61,23 @@ def pass1(karl, full):
     return a, b
 
 
+@pytest.fixture(scope="module")
+def oracle_pass1(full):
+    prob, prims = full
+    t0 = time.perf_counter()
+    o = oracle.run_pass(prob, prims, SEED, 1, n_decays=prims.n_decays, n_threads=THREADS)
+    print(f"\nPARITY oracle full pass 1: {int(o['ledger'][oracle.N_COLLISIONS])} collisions "
+          f"in {time.perf_counter() - t0:.1f} s on {THREADS} threads")
+    return o
+
+
+def _field(prob, prims, time_fx):
+    """Pass-1 densities of Eq. target_field_density, [4][nz][ntb]."""
+    tsim = prims.n_decays / prob.activity_bq
+    vol = prob.length_m / prob.n_zbins * prob.area_m2
+    return np.asarray(time_fx, np.float64)[:, 1:-1, :] / 2.0**50 / (tsim * vol)
+
+
 def _deaths(L):
     return np.asarray(L[parity.DEATHS:parity.DEATHS + 8 * parity.N_SPECIES],
                       np.int64).reshape(parity.N_SPECIES, 8)
@@ -71,21 +100,26 @@ def _check_properties(karl, t, nz, raw):
         assert not cp[:, 0].any() and not cn[:, nz].any()
 
 
-def test_full_pass1_sampled_histories_match_oracle(karl, full, pass1):
+def _sampled_ranges(n, width=256, n_ranges=64, seed=20250313):
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(n // width, n_ranges, replace=False)) * width, width
+
+
+def test_full_pass1_matches_oracle(karl, full, pass1, oracle_pass1):
     prob, prims = full
-    g = pass1[0]
+    g, o = pass1[0], oracle_pass1
     assert g["per_primary"].shape == (prims.n,)
-    rng = np.random.default_rng(20250313)
-    width, n_ranges = 256, 64
-    starts = np.sort(rng.choice(prims.n // width, n_ranges, replace=False)) * width
-    same = total = 0
-    for a in starts:
-        sub = prims.slice(int(a), width)
-        o = oracle.run_pass(prob, sub, SEED, 1, pid_offset=int(a), n_decays=prims.n_decays,
-                            n_threads=16)
-        same += int(np.sum(g["per_primary"][a:a + width] == o["per_primary"]))
-        total += width
-    assert same / total >= 0.99, same / total
+    same = float(np.mean(g["per_primary"] == o["per_primary"]))
+    fg, fo = _field(prob, prims, g["time_fx"]), _field(prob, prims, o["time_fx"])
+    l2 = parity.rel_l2(fg, fo)
+    print(f"PARITY FP64 pass 1 full: histories identical {same:.5f}, field rel L2 {l2:.3e}")
+    assert same >= 0.99, same
+    assert l2 < 1e-3, l2
+    nc_g, nc_o = int(g["ledger"][karl.N_COLLISIONS]), int(o["ledger"][karl.N_COLLISIONS])
+    assert abs(nc_g - nc_o) <= 1e-3 * nc_o
+    for k in ("spectrum", "cross_pos", "cross_neg"):
+        z, p = parity.poisson_two_sample(g[k], o[k])
+        assert parity.excursions_ok(z) and p > 0.01, k
 
 
 def test_full_pass1_properties_and_reproducibility(karl, full, pass1):
@@ -97,7 +131,31 @@ def test_full_pass1_properties_and_reproducibility(karl, full, pass1):
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)
 
 
-def test_full_two_pass_run_properties(karl, full):
+def test_full_pass2_matches_oracle(karl, full, oracle_pass1):
+    """Pass 2 over every primary on the GPU, recombining against the fields of
+    the oracle's pass 1; sampled id ranges re-run by the oracle with the same
+    fields must follow the same histories."""
+    prob, prims = full
+    time1 = oracle_pass1["time_fx"]
+    ctx = karl.Context(prob)
+    g = ctx.run_pass(prims, SEED, 2, field_time_in=time1, n_decays=prims.n_decays)
+    _check_properties(karl, g, prob.n_zbins, raw=True)
+    L = g["ledger"]
+    assert int(L[karl.DEATHS + 5]) + int(L[karl.DEATHS + 8 + 5]) > 0    # recombination ran
+    starts, width = _sampled_ranges(prims.n)
+    same = total = 0
+    for a in starts:
+        sub = prims.slice(int(a), width)
+        o = oracle.run_pass(prob, sub, SEED, 2, field_time_in=time1, pid_offset=int(a),
+                            n_decays=prims.n_decays, n_threads=THREADS)
+        same += int(np.sum(g["per_primary"][a:a + width] == o["per_primary"]))
+        total += width
+    print(f"PARITY FP64 pass 2 full (oracle fields): sampled histories identical "
+          f"{same / total:.5f} of {total}")
+    assert same / total >= 0.99, same / total
+
+
+def test_full_two_pass_run_properties(karl, full, oracle_pass1):
     prob, prims = full
     ctx = karl.Context(prob)
     t = ctx.run(prims, seed=SEED)
@@ -106,4 +164,75 @@ def test_full_two_pass_run_properties(karl, full):
     for k in ("density", "current", "field"):
         assert np.all(np.isfinite(t[k])), k
     assert np.all(t["field"] >= 0)
-    assert t["field"].any()
+    # the returned target field is the pass-1 field, the oracle's within 1e-3
+    assert parity.rel_l2(t["field"], _field(prob, prims, oracle_pass1["time_fx"])) < 1e-3
+
+
+def _batches(run, prims, k, first, count):
+    edges = np.linspace(first, first + count, k + 1).astype(int)
+    out = {key: [] for key in ("spectrum", "time_fx", "cross_pos", "cross_neg")}
+    for a, b in zip(edges[:-1], edges[1:]):
+        t = run(prims.slice(int(a), int(b - a)), int(a))
+        for key in out:
+            out[key].append(np.asarray(t[key], np.float64))
+    return {key: np.stack(v) for key, v in out.items()}
+
+
+def _report(tag, name, s):
+    print(f"PARITY {tag} {name}: bins {s['bins']}, median |z| {s['median_abs_z']:.3f}, "
+          f"max |z| {s['max_abs_z']:.2f}, beyond 3 sigma {s['beyond_3']} "
+          f"(chance allows {s['allowed_beyond_3']:.1f}), chi2 p {s['chi2_p']:.3g}")
+
+
+def test_full_fp32_two_pass_against_fp64_oracle(karl, full, oracle_pass1):
+    """The precision form on the whole workload against the FP64 oracle.
+    Pass 1: 64 primary-id batches of the FP32 form against the oracle's whole
+    pass 1.  Pass 2: a sixteenth of the primaries, both sides in 32 batches,
+    recombining against the oracle's pass-1 fields."""
+    prob, prims = full
+    ctx = karl.Context(prob)
+    kb = 64
+    gb = _batches(lambda p, off: ctx.run_pass(p, SEED, 1, pid_offset=off,
+                                              n_decays=prims.n_decays, precision=karl.FP32),
+                  prims, kb, 0, prims.n)
+    o1 = oracle_pass1
+    ok = True
+    for key in ("time_fx", "cross_pos", "cross_neg"):
+        z, dof = parity.batches_vs_total(gb[key], o1[key], min_mean=1.0)
+        s = parity.deviation_summary(z, dof)
+        _report("FP32 pass 1", key, s)
+        ok &= s["beyond_3"] <= s["allowed_beyond_3"] and s["chi2_p"] > 1e-3
+    z, p = parity.poisson_two_sample(gb["spectrum"].sum(0), o1["spectrum"])
+    print(f"PARITY FP32 pass 1 spectrum: Poisson bins {z.size}, beyond 3 sigma "
+          f"{int(np.sum(np.abs(z) > 3))}, chi2 p {p:.3g}")
+    ok &= parity.excursions_ok(z) and p > 1e-3
+    fg = _field(prob, prims, gb["time_fx"].sum(0))
+    fo = _field(prob, prims, o1["time_fx"])
+    l2 = parity.rel_l2(fg, fo)
+    # noise floor: the relative L2 by which two independent runs of the same
+    # law differ, from the batch variance of the time rows inside [0, L]
+    var_tot = kb * gb["time_fx"].var(axis=0, ddof=1)
+    o_rows = np.asarray(o1["time_fx"], np.float64)[:, 1:-1, :]
+    floor = math.sqrt(2.0 * var_tot[:, 1:-1, :].sum()) / np.linalg.norm(o_rows)
+    print(f"PARITY FP32 pass 1 field: rel L2 {l2:.3e} (noise floor of independent runs "
+          f"{floor:.3e})")
+    ok &= l2 < max(1e-3, 3.0 * floor)
+
+    sub_n = prims.n // 16
+    kb2 = 32
+    gb2 = _batches(lambda p, off: ctx.run_pass(p, SEED, 2, field_time_in=o1["time_fx"],
+                                               pid_offset=off, n_decays=prims.n_decays,
+                                               precision=karl.FP32), prims, kb2, 0, sub_n)
+    ob2 = _batches(lambda p, off: oracle.run_pass(prob, p, SEED, 2, field_time_in=o1["time_fx"],
+                                                  pid_offset=off, n_decays=prims.n_decays,
+                                                  n_threads=THREADS), prims, kb2, 0, sub_n)
+    for key in ("time_fx", "cross_pos", "cross_neg"):
+        z, _ = parity.batch_two_sample(gb2[key].reshape(kb2, -1), ob2[key].reshape(kb2, -1))
+        s = parity.deviation_summary(z, 2 * (kb2 - 1))
+        _report("FP32 pass 2", key, s)
+        ok &= s["beyond_3"] <= s["allowed_beyond_3"] and s["chi2_p"] > 1e-3
+    z, p = parity.poisson_two_sample(gb2["spectrum"].sum(0), ob2["spectrum"].sum(0))
+    print(f"PARITY FP32 pass 2 spectrum: Poisson bins {z.size}, beyond 3 sigma "
+          f"{int(np.sum(np.abs(z) > 3))}, chi2 p {p:.3g}")
+    ok &= parity.excursions_ok(z) and p > 1e-3
+    assert ok

@@ -118,6 +118,43 @@ def test_mean_free_path_moments_uniform():
 
 
 # ---------------------------------------------------------------------------
+# speed at the beta energies (Sec. 3.1: the particle speed carries the Lorentz
+# factor).  Every other speed-dependent pin runs at <= 500 eV, where
+# relativity moves v by < 0.1 %; here the time tally of a vacuum flight is held
+# to L / (|mu| v) with v = c sqrt(1 - 1/gamma^2), gamma = 1 + E / m c^2, at the
+# energies of the beta electrons (1 - 7 % from the Newtonian speed).
+
+ELECTRON_REST_EV = 510998.95            # CODATA 2018 m_e c^2
+C_SI = 299792458.0
+
+
+def vacuum_time_units(e_ev: float, mu: float, seg_len: float) -> float:
+    """Time a flight spends in one segment of length seg_len, in 2^-50 s."""
+    gamma = 1.0 + e_ev / ELECTRON_REST_EV
+    v = C_SI * math.sqrt(1.0 - 1.0 / (gamma * gamma))
+    return seg_len / (abs(mu) * v) * 2.0 ** 50
+
+
+@pytest.mark.parametrize("e_kev", [1.0, 5.0, 18.6])
+@pytest.mark.parametrize("mu", [1.0, -0.37])
+def test_speed_is_relativistic_at_beta_energies(e_kev, mu):
+    nz, length, n = 10, 1.0, 16
+    prob = _absorber_problem(np.zeros(nz), length, 1e-20)     # vacuum: straight to the end
+    z0 = 0.0 if mu > 0 else length
+    r = oracle.run(prob, inputs.beam(n, z0, e_kev * 1e3, mu), seed=1)
+    q = vacuum_time_units(e_kev * 1e3, mu, length / nz)
+    t = r["time_fx"][0, 1:-1, 0].astype(np.float64)
+    # each flight's time in a segment is rounded to one 2^-50 s unit
+    tol = 0.5 * n + 1e-6 * q
+    assert np.all(np.abs(t - n * q) <= tol), (t / n, q)
+    assert r["ledger"][oracle.DEATHS + (1 if mu > 0 else 0)] == n
+    # a Newtonian speed, sqrt(2E/m) c, is far outside that bound
+    v_newton = C_SI * math.sqrt(2.0 * e_kev * 1e3 / ELECTRON_REST_EV)
+    q_newton = length / nz / (abs(mu) * v_newton) * 2.0 ** 50
+    assert n * abs(q_newton - q) > 100 * tol
+
+
+# ---------------------------------------------------------------------------
 # channel choice with probability sigma_i n_i / sum (Sec. 2.1)
 
 def test_channel_frequencies_binomial():
@@ -442,6 +479,9 @@ def test_shards_sum_to_single_run_bit_exact():
     time1 = sum(t["time_fx"] for t in p1)
     p2 = [oracle.run_pass(prob, prims.slice(a, b - a), 5, 2, field_time_in=time1, pid_offset=a,
                           n_decays=prims.n_decays) for a, b in zip(cuts[:-1], cuts[1:])]
+    # a whole run's ledger counts the collisions and flights of both passes
+    every = slice(oracle.N_COLLISIONS_ALL, oracle.N_FLIGHTS_ALL + 1)
+    p2[0]["ledger"][every] += sum(t["ledger"][every] for t in p1)
     for k in ("spectrum", "time_fx", "cross_pos", "cross_neg", "recomb", "ledger", "chan_count"):
         np.testing.assert_array_equal(sum(t[k] for t in p2), full[k], err_msg=k)
     np.testing.assert_array_equal(np.concatenate([t["per_primary"] for t in p2]),
