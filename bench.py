@@ -48,6 +48,7 @@ FP64_OPS_PER_COLLISION = {"fp64": 127.4, "fp32": 30.77}
 FP64_PIPE_CYCLES_PER_COLLISION = {"fp64": 113.3, "fp32": 51.4}
 DRAM_BYTES_PER_COLLISION = {"fp64": 185384448 / 1665598248, "fp32": 267528960 / 1665592914}
 FP64_OPS_PER_SM_CYCLE = 2
+THREADS_PER_INSTRUCTION = {"fp64": 23.8, "fp32": 21.7}   # smsp__thread_inst_executed_per_inst_executed
 WORKLOAD = ("config2: 1e7 decays (1e7 beta e- + 1e7 thermal T2+), parabolic profile with "
             "5e21 m^-2 column, L = 10 m, 1000 z segments, 7 e- channels + T2+ clustering + "
             "e-/ion recombination, two passes")
@@ -117,8 +118,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _oracle_sample(n_decays_total: int, seconds: float, threads: int):
-    """Time the oracle as it stands on a bounded sample of the same workload."""
+def _oracle_sample(n_decays_total: int, seconds: float, threads: int, mode: int = 0):
+    """Time the oracle as it stands on a bounded sample of the same workload:
+    the first nd decays, pass 1 and then pass 2 with the fields of that pass 1.
+    Returns (collisions of both passes, seconds, nd)."""
     import oracle
     from paper_2503_10263_gb300 import inputs
     oracle.build()
@@ -126,16 +129,37 @@ def _oracle_sample(n_decays_total: int, seconds: float, threads: int):
     def run(nd):
         prob, prims = inputs.config2(n_decays=nd, seed=1)
         t0 = time.perf_counter()
-        r = oracle.run(prob, prims, seed=1, n_threads=threads)
+        r1 = oracle.run_pass(prob, prims, 1, 1, n_decays=nd, mode=mode, n_threads=threads)
+        r2 = oracle.run_pass(prob, prims, 1, 2, field_time_in=r1["time_fx"], n_decays=nd,
+                             mode=mode, n_threads=threads)
         dt = time.perf_counter() - t0
-        return int(r["ledger"][oracle.N_COLLISIONS]), dt
+        coll = int(r1["ledger"][oracle.N_COLLISIONS]) + int(r2["ledger"][oracle.N_COLLISIONS])
+        return coll, dt
 
-    c0, t0 = run(500)
+    c0, t0 = run(max(8, min(500, 64 * threads)))
+    nd0 = max(8, min(500, 64 * threads))
     rate = c0 / max(t0, 1e-6)
-    per_decay = c0 / 500
-    nd = int(min(n_decays_total, max(500, seconds * rate / max(per_decay, 1))))
+    per_decay = c0 / nd0
+    nd = int(min(n_decays_total, max(nd0, seconds * rate / max(per_decay, 1))))
     c, dt = run(nd)
     return c, dt, nd
+
+
+def _cpu_baseline(args, threads):
+    """The oracle on the host: all cores (optical-depth flights, the form the
+    GPU runs), plus one core and the paper-literal segment-stop form."""
+    c, secs, nd = _oracle_sample(args.decays, args.cpu_seconds, threads)
+    out = {"value": c / secs, "unit": "collision events/s", "cores": threads, "kind": "oracle",
+           "sample": f"first {nd} decays of the workload, pass 1 then pass 2 (collisions of "
+                     f"both counted), {secs:.1f} s on {threads} threads, optical-depth flights"}
+    c1, s1, n1 = _oracle_sample(args.decays, args.cpu_seconds / 3, 1)
+    out["one_core"] = {"value": c1 / s1, "cores": 1,
+                       "sample": f"first {n1} decays, both passes, {s1:.1f} s"}
+    ca, sa, na = _oracle_sample(args.decays, args.cpu_seconds / 3, threads, mode=1)
+    out["segment_stop"] = {"value": ca / sa, "cores": threads,
+                           "sample": f"first {na} decays, both passes, {sa:.1f} s, "
+                                     "flights stopped and redrawn at every segment face"}
+    return out
 
 
 def run_reference(args):
@@ -154,6 +178,184 @@ def run_reference(args):
     value = coll / secs
     sample = (f"first {nd} decays of the workload (both passes) per step, "
               f"{args.steps} timed steps after {args.warmup} warm-up")
+    line = {
+        "metric": "collision events/s", "value": value, "unit": "collision events/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD, "sample_decays": nd, "parallelism": "host threads"},
+        "cpu_baseline": {"value": value, "unit": "collision events/s", "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "collision events/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2503_10263_gb300 import inputs, karl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2503_10263_gb300 import build as kbuild
+    kbuild.build()
+
+    prob, prims = inputs.config2(n_decays=args.decays, seed=1)
+    n = prims.n
+    pid_offset = rank * n                           # each replica has its own primaries
+    ctx = karl.Context(prob)
+    prec = karl.FP32 if args.precision == "fp32" else karl.FP64
+    stream = torch.cuda.current_stream(dev)
+    pt = {"z_m": torch.from_numpy(prims.z_m).to(dev), "e_ev": torch.from_numpy(prims.e_ev).to(dev),
+          "mu": torch.from_numpy(prims.mu).to(dev),
+          "species": torch.from_numpy(prims.species).to(dev)}
+    tmpl = ctx.empty_tallies(0)
+    dt = {k: torch.zeros(v.shape, dtype=torch.float64 if v.dtype == np.float64 else torch.int64,
+                         device=dev) for k, v in tmpl.items() if k != "per_primary"}
+    pptr = {k: v.data_ptr() for k, v in pt.items()}
+    optr = {k: v.data_ptr() for k, v in dt.items()}
+
+    def step(i):
+        ctx.run_device(pptr, n, prims.n_decays, optr, seed=1000 + i, precision=prec,
+                       stream=stream.cuda_stream, pid_offset=pid_offset, timeout_s=args.timeout)
+        st = ctx.stats()
+        return st
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    coll = flights = parts = launches = 0
+    kms = []
+    occ = []
+    per_pass = []
+    ev0.record(stream)
+    for i in range(args.steps):
+        st = step(args.warmup + i)
+        coll += st.collisions[0] + st.collisions[1]
+        flights += st.flights[0] + st.flights[1]
+        parts += st.particles[0] + st.particles[1]
+        launches += st.kernel_launches
+        kms += [st.kernel_ms[0], st.kernel_ms[1]]
+        occ += [st.lane_occupancy[0], st.lane_occupancy[1]]
+        per_pass += [int(st.collisions[0]), int(st.collisions[1])]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1000.0
+    led = dt["ledger"].cpu().numpy()
+    ok_balance = int(led[0]) + int(led[1]) == int(led[2:12].sum())
+
+    # whole-job aggregation: collisions summed, time = max over ranks
+    tot = torch.tensor([float(coll), float(flights), float(prims.n_decays * args.steps)],
+                       dtype=torch.float64, device=dev)
+    tmax = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    coll_all, flights_all, decays_all = tot.tolist()
+    tm = float(tmax.item())
+    value = coll_all / tm
+
+    # e2e: the same metric through the public API with host buffers (pinned
+    # primaries copied in, tallies read back, every step)
+    e2e = None
+    if args.e2e_steps > 0:
+        hp = {k: torch.from_numpy(getattr(prims, k) if k != "species" else prims.species)
+              .pin_memory() for k in ("z_m", "e_ev", "mu")}
+        hp["species"] = torch.from_numpy(prims.species).pin_memory()
+        hprims = karl.Primaries(n, hp["z_m"].data_ptr(), hp["e_ev"].data_ptr(),
+                                hp["mu"].data_ptr(), hp["species"].data_ptr(), prims.n_decays,
+                                pid_offset, 0)
+        host_t = ctx.empty_tallies(0)
+        del host_t["per_primary"]
+        ts = karl.Tallies()
+        for k, v in host_t.items():
+            setattr(ts, k, v.ctypes.data)
+        ts.on_device = 0
+        h2d = sum(int(v.numel() * v.element_size()) for v in hp.values())
+        d2h = sum(int(v.nbytes) for v in host_t.values())
+        ecoll = 0
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for i in range(args.e2e_steps):
+            o = ctx.opts(seed=5000 + i, precision=prec, stream=stream.cuda_stream,
+                         timeout_s=args.timeout)
+            stt = karl.karl_run(ctx.ctx, hprims, o, ts)
+            if stt != karl.OK:
+                raise RuntimeError(karl.karl_last_error(ctx.ctx))
+            s2 = ctx.stats()
+            ecoll += s2.collisions[0] + s2.collisions[1]
+        e_el = time.perf_counter() - t0
+        et = torch.tensor([float(ecoll)], dtype=torch.float64, device=dev)
+        emax = torch.tensor([e_el], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(et, op=dist.ReduceOp.SUM)
+            dist.all_reduce(emax, op=dist.ReduceOp.MAX)
+        e2e = {"value": float(et.item()) / float(emax.item()), "unit": "collision events/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    hbm, peak_kind = _peaks()
+    bpe = BYTES_PER_EVENT_FP32 if prec == karl.FP32 else BYTES_PER_EVENT_FP64
+    per_launch_events = coll / max(len(kms), 1)
+    avg_ms = sum(kms) / max(len(kms), 1)
+    launch_rate = per_launch_events / (avg_ms / 1000.0)          # collisions/s inside the kernel
+    hbm_achieved = bpe * launch_rate / 1e9
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_ghz = (clocks["sm_mhz"] if clocks else 2070.0) / 1000.0
+    ops = FP64_OPS_PER_COLLISION[args.precision]
+    cyc = FP64_PIPE_CYCLES_PER_COLLISION[args.precision]
+    dram = DRAM_BYTES_PER_COLLISION[args.precision]
+    traffic = dram * per_launch_events if dram else None
+    # roofline of the hot-path byte model: an event-based form reads and
+    # writes each particle's state once per collision event
+    roofline = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm, "unit": "GB/s",
+                "frac": hbm_achieved / hbm, "traffic": traffic,
+                "model": f"{bpe} B per collision event (particle state read + written once per "
+                         f"event) x collisions of a launch / launch time; {peak_kind} copy "
+                         f"bandwidth",
+                "kernel": "karl::transport_kernel"}
+    # what actually bounds this register-resident kernel: the FP64 pipe
+    fp64_issue = None
+    if ops:
+        peak = FP64_OPS_PER_SM_CYCLE * n_sm * clk_ghz
+        fp64_issue = {"achieved": ops * launch_rate / 1e9, "peak": peak,
+                      "unit": "G FP64 thread-ops/s", "frac": ops * launch_rate / 1e9 / peak,
+                      "ops_per_collision": ops,
+                      "threads_per_warp_instruction": THREADS_PER_INSTRUCTION[args.precision],
+                      "model": f"FP64 add/mul/fma thread-instructions per collision (ncu) "
+                               f"against {FP64_OPS_PER_SM_CYCLE} per SM per cycle x {n_sm} SMs "
+                               f"x median SM clock under load"}
+    fp64_pipe = None
+    if cyc:
+        fp64_pipe = {"busy_frac": cyc * launch_rate / 1e9 / (n_sm * clk_ghz),
+                     "cycles_per_collision": cyc,
+                     "note": "FP64 pipe busy cycles over SM cycles (idle lanes of a divergent "
+                             "warp and FP64 compares and conversions included)"}
     line = {
         "metric": "collision events/s", "value": value, "unit": "collision events/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -328,10 +530,6 @@ def run_ours(args):
                      "note": "FP64 pipe busy cycles over SM cycles; the gap to roofline.frac is "
                              "FP64 issue slots spent on idle or divergent lanes and on FP64 "
                              "instructions other than add/mul/fma (compares, conversions)"}
-    hbm_model = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm, "unit": "GB/s",
-                 "frac": hbm_achieved / hbm,
-                 "model": f"{bpe} B per collision event (event-based state read+write), "
-                          f"{peak_kind} peak"}
     line = {
         "metric": "collision events/s", "value": value, "unit": "collision events/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -344,22 +542,20 @@ def run_ours(args):
         "collisions_per_step": coll / args.steps,
         "transport_kernel_ms": kms,
         "collisions_per_launch": per_pass,
+        "ns_per_collision_by_pass": [
+            round(1e6 * sum(kms[0::2]) / max(sum(per_pass[0::2]), 1), 4),
+            round(1e6 * sum(kms[1::2]) / max(sum(per_pass[1::2]), 1), 4)],
         "lane_occupancy": [round(x, 4) for x in occ],
         "ledger_balanced": ok_balance,
         "gpu_launches": launches,
         "roofline": roofline,
+        "fp64_issue": fp64_issue,
         "fp64_pipe": fp64_pipe,
-        "hbm_model": hbm_model,
         "e2e": e2e,
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:
-        threads = os.cpu_count() or 1
-        c, secs, nd = _oracle_sample(args.decays, args.cpu_seconds, threads)
-        line["cpu_baseline"] = {"value": c / secs, "unit": "collision events/s", "cores": threads,
-                                "kind": "oracle",
-                                "sample": f"first {nd} decays of the workload, both passes, "
-                                          f"{secs:.1f} s on {threads} threads"}
+        line["cpu_baseline"] = _cpu_baseline(args, os.cpu_count() or 1)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -404,7 +600,7 @@ def run_batch(args):
         d2h = 0
         for rid in ids:
             done, t = srv.poll(rid)
-            coll += int(t["ledger"][karl.N_COLLISIONS])
+            coll += int(t["ledger"][karl.N_COLLISIONS_ALL])
             d2h += sum(v.nbytes for v in t.values())
         st = srv.stats()
         srv.close()
@@ -457,7 +653,7 @@ def plain_sequential(batch, prec, timeout):
         ctx = karl.Context(p)
         t = ctx.run(pr, seed=s, precision=prec, per_primary=False, timeout_s=timeout)
         st = ctx.stats()
-        coll += int(t["ledger"][karl.N_COLLISIONS])
+        coll += int(t["ledger"][karl.N_COLLISIONS_ALL])
         kms += float(st.kernel_ms[0]) + float(st.kernel_ms[1])
         ctx.close()
     wall = time.perf_counter() - t0
@@ -496,7 +692,7 @@ def run_serve(args):
             done, t = srv.poll(rid)
             if done:
                 lat.append(time.perf_counter() - t0 - open_ids.pop(rid))
-                coll += int(t["ledger"][karl.N_COLLISIONS])
+                coll += int(t["ledger"][karl.N_COLLISIONS_ALL])
         time.sleep(0.0005)
     wall = time.perf_counter() - t0
     srv.run_all()
@@ -538,7 +734,7 @@ def plain_serve(reqs, prec, timeout):
         t = ctx.run(pr, seed=s, precision=prec, per_primary=False, timeout_s=timeout)
         ctx.close()
         lat.append(time.perf_counter() - t0 - ta)
-        coll += int(t["ledger"][karl.N_COLLISIONS])
+        coll += int(t["ledger"][karl.N_COLLISIONS_ALL])
     wall = time.perf_counter() - t0
     return {"p50_latency_s": _percentile(lat, 50), "p99_latency_s": _percentile(lat, 99),
             "sustained_collisions_per_s": coll / wall, "requests": len(reqs),

@@ -85,7 +85,12 @@ enum {
   KARL_L_E_STALLED = 11,
   KARL_L_BIRTHS = 12,        /* [4] */
   KARL_L_DEATHS = 16,        /* [4][8] */
-  KARL_L_N_COLLISIONS = 48, KARL_L_N_FLIGHTS = 49, KARL_L_N_SPAWN_E = 50, KARL_L_N_SPAWN_ION = 51
+  KARL_L_N_COLLISIONS = 48, KARL_L_N_FLIGHTS = 49, KARL_L_N_SPAWN_E = 50, KARL_L_N_SPAWN_ION = 51,
+  /* collisions and flights of every pass that wrote this ledger: both passes of
+   * a two-pass karl_run or served request (whose other slots hold the last
+   * pass), the sum over the cycles of karl_run_cycles, and the pass itself for
+   * karl_run_pass, karl_run_cycle and karl_run_pass_static (added to out) */
+  KARL_L_N_COLLISIONS_ALL = 52, KARL_L_N_FLIGHTS_ALL = 53
 };
 
 /* Geometry, gas and terminator settings (copied at create).
@@ -278,12 +283,20 @@ karl_status karl_run_cycle(karl_ctx* ctx, const karl_primaries* prim, const karl
  *    them first) where karl_run_pass adds to them; per_primary may be NULL;
  *    density, current and field are not touched.
  * Scratch: control block, time and crossing difference arrays, pass-2 field
- * tables, and a particle ring that gets the rest (a power of two, 2^16 to
- * 2^22 particles).  The difference arrays, 2 * 3 * (n_zbins + 2) * n_tebins
- * * 8 bytes plus the pass-2 tables, must fit beside the smallest ring (4 MiB):
- * a geometry that does not fit is rejected with KARL_ECAPACITY before any
- * launch, and so is a run whose particles overflow the ring, which cannot
- * grow here.
+ * tables, and a particle ring of 64-byte cells that gets the rest.  The fixed
+ * part is about 2 * 4 * (n_zbins + 2) * n_tebins * 8 bytes (time) +
+ * 2 * 4 * (n_zbins + 2) * 8 bytes (crossings) + for pass 2
+ * 2 * n_channels * (n_zbins + 1) * 8 bytes (field tables); the ring is the
+ * largest power of two of cells with fixed + 64 * cells <= 64 MiB, from 2^16
+ * up to 2^19 cells (2^19 for config-sized geometries, 1000 segments and 64
+ * energy bins).  karl_run_pass starts at 2^22 cells and grows on overflow, so
+ * a workload that succeeds there can fail here: a geometry whose fixed part
+ * does not fit beside the smallest ring (4 MiB) is rejected with
+ * KARL_ECAPACITY before any launch, and so is a run whose particles overflow
+ * the ring, which cannot grow here.
+ * Pointers: every primary array, tally buffer and field_time_in must be device
+ * (or managed) memory of the context's device; anything else is rejected with
+ * KARL_EINVAL before any launch (checked with cudaPointerGetAttributes).
  * Set-up: the first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture on the device.
@@ -380,8 +393,8 @@ karl_status karl_server_create(const karl_xs* xs, const karl_server_opts* opts,
  * valid until karl_server_poll reports the request done; per_primary is not
  * used.  n_passes as in karl_run_opts.  The request is admitted at once if a
  * slot and arena space are free, else as earlier requests finish.
- * Errors: KARL_EINVAL (bad geometry, primaries, buffers, or a footprint
- * larger than the whole budget), KARL_ENOMEM. */
+ * Errors: KARL_EINVAL (bad geometry, primaries, buffers, more than 2^31 - 1
+ * primaries, or a footprint larger than the whole budget), KARL_ENOMEM. */
 karl_status karl_server_submit(karl_server* srv, const karl_geometry* geom,
                                const karl_primaries* prim, uint64_t seed, int32_t n_passes,
                                karl_tallies* out, uint64_t* req_id);
@@ -405,7 +418,7 @@ karl_status karl_server_run_all(karl_server* srv);
 
 typedef struct karl_server_stats {
   int64_t submitted, admitted, completed, collected, waiting;
-  int64_t collisions;          /* summed over collected requests (both passes' last-pass ledgers) */
+  int64_t collisions;          /* collisions of every pass, summed over collected requests */
   int64_t kernel_launches;
   int64_t arena_bytes_in_use, arena_bytes_peak;
   double lane_occupancy;       /* of the last finished launch */

@@ -549,6 +549,7 @@ struct Worker {
       double eta = eta01(w[0]);
       double tau = -std::log(eta);                 /* Eq. distance_from_mfp, in optical depth */
       T.ledger[ORC_N_FLIGHTS] += 1;
+      T.ledger[ORC_N_FLIGHTS_ALL] += 1;
       flight_coefficients(*R, s, e, v, coef.data());
       int b = tebin(p, e);
       double amu = std::fabs(P.mu);
@@ -583,6 +584,7 @@ struct Worker {
       P.ev += 1;
       tree_collisions += 1;
       T.ledger[ORC_N_COLLISIONS] += 1;
+      T.ledger[ORC_N_COLLISIONS_ALL] += 1;
       double rtot = total_rate(*R, coef.data(), j);
       double target = u01(w[1]) * rtot;
       int ch = -1, last = -1;
@@ -964,6 +966,9 @@ int orc_run(const orc_problem* p, const orc_primaries* pr, uint64_t seed, int n_
   if (rc) return rc;
   std::vector<uint64_t> time1(out->time_fx, out->time_fx + ntime);
   if (n_passes == 2) {
+    /* the run's counts of both passes survive the reset of the pass-1 tallies */
+    const int64_t coll1 = out->ledger[ORC_N_COLLISIONS_ALL];
+    const int64_t flights1 = out->ledger[ORC_N_FLIGHTS_ALL];
     std::memset(out->spectrum, 0, sizeof(uint64_t) * 2 * ORC_N_SPECIES * (p->n_spec_bins + 1));
     std::memset(out->time_fx, 0, sizeof(uint64_t) * ntime);
     std::memset(out->cross_pos, 0, sizeof(uint64_t) * ORC_N_SPECIES * (nz + 1));
@@ -975,6 +980,8 @@ int orc_run(const orc_problem* p, const orc_primaries* pr, uint64_t seed, int n_
     rc = do_pass(p, pr, seed, 2, time1.data(), nullptr, (double)pr->n_decays, false, mode,
                  n_threads, out);
     if (rc) return rc;
+    out->ledger[ORC_N_COLLISIONS_ALL] += coll1;
+    out->ledger[ORC_N_FLIGHTS_ALL] += flights1;
   }
   /* normalisation: Eq. target_field_density, current j = (N+ - N-)/(A t_sim) */
   double dz = p->length_m / nz;

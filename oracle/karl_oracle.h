@@ -34,7 +34,10 @@ enum {
   ORC_E_LOSS_IONIZ = 8, ORC_E_LOSS_EXCIT = 9, ORC_E_LOSS_RECOIL = 10, ORC_E_STALLED = 11,
   ORC_BIRTHS = 12,              /* [4] */
   ORC_DEATHS = 16,              /* [4][8] */
-  ORC_N_COLLISIONS = 48, ORC_N_FLIGHTS = 49, ORC_N_SPAWN_E = 50, ORC_N_SPAWN_ION = 51
+  ORC_N_COLLISIONS = 48, ORC_N_FLIGHTS = 49, ORC_N_SPAWN_E = 50, ORC_N_SPAWN_ION = 51,
+  /* collisions and flights of every pass of the run (orc_run: both passes;
+   * one pass: equal to ORC_N_COLLISIONS / ORC_N_FLIGHTS) */
+  ORC_N_COLLISIONS_ALL = 52, ORC_N_FLIGHTS_ALL = 53
 };
 
 typedef struct {

@@ -31,7 +31,8 @@ enum { R_EXIT0 = 0, R_EXIT1 = 1, R_CUTOFF = 2, R_CAP_COLL = 3, R_CAP_TIME = 4,
 enum { L_E_IN_PRIMARY = 0, L_E_IN_THERMAL = 1, L_E_EXIT0 = 2, L_E_EXIT1 = 3, L_E_CUTOFF = 4,
        L_E_CAP = 5, L_E_RECOMB = 6, L_E_CLUSTER = 7, L_LOSS_IONIZ = 8, L_LOSS_EXCIT = 9,
        L_LOSS_RECOIL = 10, L_E_STALLED = 11, L_BIRTHS = 12, L_DEATHS = 16, L_N_COLL = 48,
-       L_N_FLIGHT = 49, L_N_SPAWN_E = 50, L_N_SPAWN_ION = 51 };
+       L_N_FLIGHT = 49, L_N_SPAWN_E = 50, L_N_SPAWN_ION = 51, L_N_COLL_ALL = 52,
+       L_N_FLIGHT_ALL = 53 };
 enum { DOM_EVENT = 0, DOM_ION_BIRTH = 1, DOM_CLUSTER = 2, DOM_TARGET = 4 };
 enum { ERR_NONE = 0, ERR_TIMEOUT = 4, ERR_CAPACITY = 6, ERR_CANCELLED = 7 };
 

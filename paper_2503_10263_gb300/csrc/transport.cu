@@ -377,6 +377,8 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const Params Pk, Ring
     atomicAdd(&ctl->busy_lane_iters, busy_lane_iters);
     atomicAdd(&S.ledger[L_N_FLIGHT], f);
     atomicAdd(&S.ledger[L_N_COLL], c);
+    atomicAdd(&S.ledger[L_N_FLIGHT_ALL], f);
+    atomicAdd(&S.ledger[L_N_COLL_ALL], c);
     atomicAdd(&S.ledger[L_LOSS_RECOIL], rc);
     atomicAdd(&S.ledger[L_LOSS_EXCIT], ex);
     atomicAdd(&ctl->particles, st);

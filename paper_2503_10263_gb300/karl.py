@@ -37,6 +37,7 @@ E_IN_PRIMARY, E_IN_THERMAL, E_EXIT0, E_EXIT1, E_CUTOFF, E_CAP, E_RECOMB, E_CLUST
     E_LOSS_IONIZ, E_LOSS_EXCIT, E_LOSS_RECOIL, E_STALLED = range(12)
 BIRTHS, DEATHS = 12, 16
 N_COLLISIONS, N_FLIGHTS, N_SPAWN_E, N_SPAWN_ION = 48, 49, 50, 51
+N_COLLISIONS_ALL, N_FLIGHTS_ALL = 52, 53     # every pass of the run
 
 
 class KarlError(RuntimeError):

@@ -20,6 +20,7 @@ from typing import Callable, Dict
 import numpy as np
 
 RAW_KEYS = ("spectrum", "time_fx", "cross_pos", "cross_neg", "recomb", "ledger", "chan_count")
+N_ALL = slice(52, 54)      # ledger slots of the collisions and flights of every pass
 
 
 def shard_range(n: int, rank: int, world: int):
@@ -40,13 +41,17 @@ def _allreduce_sum(arr: np.ndarray) -> np.ndarray:
 def run_sharded(run_pass: Callable, prims, seed: int, n_passes: int, rank: int,
                 world: int) -> Dict[str, np.ndarray]:
     """All passes of a run split over `world` ranks; returns the summed raw
-    tallies of the last pass (identical on every rank)."""
+    tallies of the last pass, whose ledger counts the collisions and flights
+    of both passes in its all-pass slots as karl_run does (identical on every
+    rank)."""
     a, b = shard_range(prims.n, rank, world)
     mine = prims.slice(a, b - a)
     t = run_pass(mine, seed, 1, None, a, prims.n_decays)
     if n_passes == 2:
         time1 = _allreduce_sum(t["time_fx"]) if world > 1 else t["time_fx"]
+        all1 = t["ledger"][N_ALL].copy()
         t = run_pass(mine, seed, 2, time1, a, prims.n_decays)
+        t["ledger"][N_ALL] += all1          # collisions and flights of both passes
     out = {}
     for k in RAW_KEYS:
         out[k] = _allreduce_sum(t[k]) if world > 1 else t[k]

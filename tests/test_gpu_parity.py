@@ -151,6 +151,25 @@ def test_gpu_beam_survival_closed_form(karl):
         assert np.max(np.abs(emp[1:] - surv[1:])) < 1.95 / math.sqrt(n)
 
 
+@pytest.mark.parametrize("e_kev", [1.0, 5.0, 18.6])
+def test_gpu_speed_is_relativistic_at_beta_energies(karl, e_kev):
+    """Vacuum flights of beta-energy electrons: the time tally per segment is
+    L / (|mu| v) with v = c sqrt(1 - 1/gamma^2) (Sec. 3.1's Lorentz factor),
+    to one 2^-50 s unit per flight in FP64 and to FP32 rounding in the
+    precision form."""
+    from tests.test_oracle_pins import _absorber_problem, vacuum_time_units
+    nz, length, n = 10, 1.0, 64
+    prob = _absorber_problem(np.zeros(nz), length, 1e-20)
+    for mu in (1.0, -0.37):
+        z0 = 0.0 if mu > 0 else length
+        q = vacuum_time_units(e_kev * 1e3, mu, length / nz)
+        for prec, rel in ((karl.FP64, 1e-12), (karl.FP32, 2e-6)):
+            g = karl.Context(prob).run(inputs.beam(n, z0, e_kev * 1e3, mu), seed=1, precision=prec)
+            t = g["time_fx"][0, 1:-1, 0].astype(np.float64)
+            tol = 0.5 * n + rel * n * q
+            assert np.all(np.abs(t - n * q) <= tol), (prec, mu, t / n, q)
+
+
 def test_gpu_channel_frequencies(karl):
     nodes = inputs.energy_nodes(2048, 1.0, 2e4)
     prob = inputs.uniform_problem(1e19, 1.0, 10, inputs.electron_channels(nodes, False),
@@ -274,6 +293,8 @@ def test_shards_sum_to_single_run_bit_exact(karl):
     time1 = sum(t["time_fx"] for t in p1)
     p2 = [ctx.run_pass(prims.slice(a, b - a), 3, 2, field_time_in=time1, pid_offset=a,
                        n_decays=prims.n_decays) for a, b in zip(cuts[:-1], cuts[1:])]
+    p2[0]["ledger"][karl.N_COLLISIONS_ALL:karl.N_FLIGHTS_ALL + 1] += \
+        sum(t["ledger"][karl.N_COLLISIONS_ALL:karl.N_FLIGHTS_ALL + 1] for t in p1)
     for k in RAW:
         np.testing.assert_array_equal(sum(t[k] for t in p2), full[k], err_msg=k)
     again = ctx.run(prims, seed=3)
