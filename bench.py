@@ -136,8 +136,8 @@ def _oracle_sample(n_decays_total: int, seconds: float, threads: int, mode: int 
         coll = int(r1["ledger"][oracle.N_COLLISIONS]) + int(r2["ledger"][oracle.N_COLLISIONS])
         return coll, dt
 
-    c0, t0 = run(max(8, min(500, 64 * threads)))
     nd0 = max(8, min(500, 64 * threads))
+    c0, t0 = run(nd0)
     rate = c0 / max(t0, 1e-6)
     per_decay = c0 / nd0
     nd = int(min(n_decays_total, max(nd0, seconds * rate / max(per_decay, 1))))
@@ -356,180 +356,6 @@ def run_ours(args):
                      "cycles_per_collision": cyc,
                      "note": "FP64 pipe busy cycles over SM cycles (idle lanes of a divergent "
                              "warp and FP64 compares and conversions included)"}
-    line = {
-        "metric": "collision events/s", "value": value, "unit": "collision events/s",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000.0 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": WORKLOAD, "sample_decays": nd, "parallelism": "host threads"},
-        "cpu_baseline": {"value": value, "unit": "collision events/s", "cores": threads,
-                         "kind": "oracle", "sample": sample},
-        "e2e": {"value": value, "unit": "collision events/s", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
-
-
-def run_ours(args):
-    import torch
-    import torch.distributed as dist
-
-    from paper_2503_10263_gb300 import inputs, karl
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-
-    from paper_2503_10263_gb300 import build as kbuild
-    kbuild.build()
-
-    prob, prims = inputs.config2(n_decays=args.decays, seed=1)
-    n = prims.n
-    pid_offset = rank * n                           # each replica has its own primaries
-    ctx = karl.Context(prob)
-    prec = karl.FP32 if args.precision == "fp32" else karl.FP64
-    stream = torch.cuda.current_stream(dev)
-    pt = {"z_m": torch.from_numpy(prims.z_m).to(dev), "e_ev": torch.from_numpy(prims.e_ev).to(dev),
-          "mu": torch.from_numpy(prims.mu).to(dev),
-          "species": torch.from_numpy(prims.species).to(dev)}
-    tmpl = ctx.empty_tallies(0)
-    dt = {k: torch.zeros(v.shape, dtype=torch.float64 if v.dtype == np.float64 else torch.int64,
-                         device=dev) for k, v in tmpl.items() if k != "per_primary"}
-    pptr = {k: v.data_ptr() for k, v in pt.items()}
-    optr = {k: v.data_ptr() for k, v in dt.items()}
-
-    def step(i):
-        ctx.run_device(pptr, n, prims.n_decays, optr, seed=1000 + i, precision=prec,
-                       stream=stream.cuda_stream, pid_offset=pid_offset, timeout_s=args.timeout)
-        st = ctx.stats()
-        return st
-
-    for i in range(args.warmup):
-        step(i)
-    torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    sampler.start()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    coll = flights = parts = launches = 0
-    kms = []
-    occ = []
-    per_pass = []
-    ev0.record(stream)
-    for i in range(args.steps):
-        st = step(args.warmup + i)
-        coll += st.collisions[0] + st.collisions[1]
-        flights += st.flights[0] + st.flights[1]
-        parts += st.particles[0] + st.particles[1]
-        launches += st.kernel_launches
-        kms += [st.kernel_ms[0], st.kernel_ms[1]]
-        occ += [st.lane_occupancy[0], st.lane_occupancy[1]]
-        per_pass += [int(st.collisions[0]), int(st.collisions[1])]
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    clocks = sampler.stop()
-    elapsed = ev0.elapsed_time(ev1) / 1000.0
-    led = dt["ledger"].cpu().numpy()
-    ok_balance = int(led[0]) + int(led[1]) == int(led[2:12].sum())
-
-    # whole-job aggregation: collisions summed, time = max over ranks
-    tot = torch.tensor([float(coll), float(flights), float(prims.n_decays * args.steps)],
-                       dtype=torch.float64, device=dev)
-    tmax = torch.tensor([elapsed], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    coll_all, flights_all, decays_all = tot.tolist()
-    tm = float(tmax.item())
-    value = coll_all / tm
-
-    # e2e: the same metric through the public API with host buffers (pinned
-    # primaries copied in, tallies read back, every step)
-    e2e = None
-    if args.e2e_steps > 0:
-        hp = {k: torch.from_numpy(getattr(prims, k) if k != "species" else prims.species)
-              .pin_memory() for k in ("z_m", "e_ev", "mu")}
-        hp["species"] = torch.from_numpy(prims.species).pin_memory()
-        hprims = karl.Primaries(n, hp["z_m"].data_ptr(), hp["e_ev"].data_ptr(),
-                                hp["mu"].data_ptr(), hp["species"].data_ptr(), prims.n_decays,
-                                pid_offset, 0)
-        host_t = ctx.empty_tallies(0)
-        del host_t["per_primary"]
-        ts = karl.Tallies()
-        for k, v in host_t.items():
-            setattr(ts, k, v.ctypes.data)
-        ts.on_device = 0
-        h2d = sum(int(v.numel() * v.element_size()) for v in hp.values())
-        d2h = sum(int(v.nbytes) for v in host_t.values())
-        ecoll = 0
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-        t0 = time.perf_counter()
-        for i in range(args.e2e_steps):
-            o = ctx.opts(seed=5000 + i, precision=prec, stream=stream.cuda_stream,
-                         timeout_s=args.timeout)
-            stt = karl.karl_run(ctx.ctx, hprims, o, ts)
-            if stt != karl.OK:
-                raise RuntimeError(karl.karl_last_error(ctx.ctx))
-            s2 = ctx.stats()
-            ecoll += s2.collisions[0] + s2.collisions[1]
-        e_el = time.perf_counter() - t0
-        et = torch.tensor([float(ecoll)], dtype=torch.float64, device=dev)
-        emax = torch.tensor([e_el], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(et, op=dist.ReduceOp.SUM)
-            dist.all_reduce(emax, op=dist.ReduceOp.MAX)
-        e2e = {"value": float(et.item()) / float(emax.item()), "unit": "collision events/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}
-
-    if rank != 0:
-        if world > 1:
-            dist.destroy_process_group()
-        return
-
-    hbm, peak_kind = _peaks()
-    bpe = BYTES_PER_EVENT_FP32 if prec == karl.FP32 else BYTES_PER_EVENT_FP64
-    per_launch_events = coll / max(len(kms), 1)
-    avg_ms = sum(kms) / max(len(kms), 1)
-    launch_rate = per_launch_events / (avg_ms / 1000.0)          # collisions/s inside the kernel
-    hbm_achieved = bpe * launch_rate / 1e9
-    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    clk_ghz = (clocks["sm_mhz"] if clocks else 2070.0) / 1000.0
-    ops = FP64_OPS_PER_COLLISION[args.precision]
-    cyc = FP64_PIPE_CYCLES_PER_COLLISION[args.precision]
-    dram = DRAM_BYTES_PER_COLLISION[args.precision]
-    traffic = dram * per_launch_events if dram else None
-    if ops:
-        peak = FP64_OPS_PER_SM_CYCLE * n_sm * clk_ghz
-        roofline = {"bound": "alu", "achieved": ops * launch_rate / 1e9, "peak": peak,
-                    "unit": "G FP64 thread-ops/s", "frac": ops * launch_rate / 1e9 / peak,
-                    "traffic": traffic,
-                    "model": f"{ops:.0f} FP64 add/mul/fma thread-instructions per collision (ncu); "
-                             f"peak = {FP64_OPS_PER_SM_CYCLE} per SM per cycle x {n_sm} SMs x "
-                             f"median SM clock under load",
-                    "kernel": "karl::transport_kernel"}
-    else:
-        roofline = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm, "unit": "GB/s",
-                    "frac": hbm_achieved / hbm, "traffic": traffic,
-                    "model": f"{bpe} B per collision event (state read+write), {peak_kind} peak",
-                    "kernel": "karl::transport_kernel"}
-    fp64_pipe = None
-    if cyc:
-        fp64_pipe = {"busy_frac": cyc * launch_rate / 1e9 / (n_sm * clk_ghz),
-                     "cycles_per_collision": cyc,
-                     "note": "FP64 pipe busy cycles over SM cycles; the gap to roofline.frac is "
-                             "FP64 issue slots spent on idle or divergent lanes and on FP64 "
-                             "instructions other than add/mul/fma (compares, conversions)"}
     line = {
         "metric": "collision events/s", "value": value, "unit": "collision events/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
