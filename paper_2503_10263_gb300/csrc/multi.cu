@@ -40,9 +40,14 @@ __device__ double sigma_cm(const double* sig, int n, double e_min, double log_ra
 // Warp-cooperative end of pass p of request s (Eq. target_field_density for
 // the fields; Sec. 2.3 for the current).
 __device__ void complete_pass(SlotDesc* D, SlotCtl* C, MultiCtl* M, int s, int p, int lane) {
-  const int from = p == 1 ? SLOT_PASS1 : SLOT_PASS2;
-  int ok = 0;
-  if (lane == 0) ok = atomicCAS(&C[s].state, from, SLOT_TRANS) == from;
+  // the request is alive until this completes, so its generation is current
+  int ok = 0, gen_bits = 0;
+  if (lane == 0) {
+    gen_bits = ld_acquire_i(&C[s].state) & ~0xff;
+    const int from = gen_bits | (p == 1 ? SLOT_PASS1 : SLOT_PASS2);
+    ok = atomicCAS(&C[s].state, from, gen_bits | SLOT_TRANS) == from;
+  }
+  gen_bits = __shfl_sync(FULL, gen_bits, 0);
   if (!__shfl_sync(FULL, ok, 0)) return;                 // someone else already did it
   SlotDesc& d = D[s];
   const Params& P = d.P[p - 1];
@@ -98,7 +103,7 @@ __device__ void complete_pass(SlotDesc* D, SlotCtl* C, MultiCtl* M, int s, int p
     if (lane == 0) {
       *(volatile int*)&C[s].pass = 2;
       __threadfence();
-      st_release_i(&C[s].state, SLOT_PASS2);
+      st_release_i(&C[s].state, gen_bits | SLOT_PASS2);
       if (d.n_prim > 0) atomicOr(&M->bitmap[s >> 5], 1u << (s & 31));
     }
     return;
@@ -142,7 +147,7 @@ __device__ void complete_pass(SlotDesc* D, SlotCtl* C, MultiCtl* M, int s, int p
   __syncwarp();
   __threadfence_system();
   if (lane == 0) {
-    st_release_i(&C[s].state, SLOT_DONE);
+    st_release_i(&C[s].state, gen_bits | SLOT_DONE);
     atomicAdd(&M->done_count, 1ULL);
     *(volatile int*)d.done_flag = 1;
     __threadfence_system();
@@ -153,7 +158,43 @@ __device__ void complete_pass(SlotDesc* D, SlotCtl* C, MultiCtl* M, int s, int p
 // particle and every primary claimed.
 __device__ __forceinline__ bool pass_emptied(unsigned long long old, unsigned long long dec,
                                              long long n_prim) {
-  return (old & 0xffffffffULL) == dec && (long long)(old >> 32) >= n_prim;
+  return word_live(old) == dec && word_next(old) >= n_prim;
+}
+
+// Claim up to k primaries of the current pass of the request in slot s, whose
+// state the caller read as st (a pass state).  The claim is a compare-and-swap
+// on the pass word that adds the same count to the next primary and to the
+// live particles, only while the word carries the generation of st and
+// primaries remain, so it never takes primaries past the end and never
+// touches a later request in the slot.  Returns the count claimed (0 if
+// none) and the first index; clears the slot's bit when it takes the last.
+__device__ __forceinline__ int claim_primaries(SlotDesc* D, SlotCtl* C, MultiCtl* M, int s, int st,
+                                               int k, unsigned long long* first) {
+  const int p = state_kind(st) == SLOT_PASS2 ? 2 : 1;
+  unsigned long long* word = &C[s].word[p - 1];
+  // the descriptor of the generation read in st (admission writes the new
+  // generation's pass words before its descriptor, so a newer descriptor
+  // comes with a newer word, which the generation test below rejects)
+  const long long n = (long long)ld_acquire((const unsigned long long*)&D[s].n_prim);
+  const unsigned long long gen = (unsigned long long)(state_gen(st) & 31u);
+  unsigned long long old = ld_acquire(word);
+  for (int tries = 0; tries < 64; ++tries) {
+    if (word_gen(old) != gen) return 0;               // the slot holds another request now
+    const long long next = word_next(old);
+    const long long left = n - next;
+    if (left <= 0) return 0;                          // every primary of this pass claimed
+    const int g = left < k ? (int)left : k;
+    const unsigned long long nw =
+        old + ((unsigned long long)g << WORD_NEXT_SHIFT) + (unsigned long long)g;
+    const unsigned long long prev = atomicCAS(word, old, nw);
+    if (prev == old) {
+      if (next + g >= n) atomicAnd(&M->bitmap[s >> 5], ~(1u << (s & 31)));
+      *first = (unsigned long long)next;
+      return g;
+    }
+    old = prev;
+  }
+  return 0;                                           // contended: look elsewhere
 }
 
 template <bool F32>
@@ -205,14 +246,20 @@ __global__ void __launch_bounds__(256, 2) multi_kernel(SlotDesc* D, SlotCtl* C, 
   // its ledger whenever the lane lets the particle go (death, park, hand-back)
   auto flush_sums = [&]() {
     unsigned long long* led = Pl->ledger;
-    if (o.flights) atomicAdd(led + L_N_FLIGHT, o.flights);
-    if (o.colls) atomicAdd(led + L_N_COLL, o.colls);
+    if (o.flights) {
+      atomicAdd(led + L_N_FLIGHT, o.flights);
+      atomicAdd(led + L_N_FLIGHT_ALL, o.flights);
+    }
+    if (o.colls) {
+      atomicAdd(led + L_N_COLL, o.colls);
+      atomicAdd(led + L_N_COLL_ALL, o.colls);
+    }
     if (o.recoil) atomicAdd(led + L_LOSS_RECOIL, o.recoil);
     if (o.excit) atomicAdd(led + L_LOSS_EXCIT, o.excit);
     o.flights = o.colls = o.recoil = o.excit = 0;
   };
-  // passes this lane saw empty: one from a claim (lane 0), one from a death
-  int trigA = 0, tslotA = 0, tpassA = 1, trigB = 0, tslotB = 0, tpassB = 1;
+  // a pass this lane saw empty (by the death of a particle or a primary born dead)
+  int trigB = 0, tslotB = 0, tpassB = 1;
 
   for (long long iter = 0;; ++iter) {
     if ((iter & 63) == 0) {
@@ -236,7 +283,7 @@ __global__ void __launch_bounds__(256, 2) multi_kernel(SlotDesc* D, SlotCtl* C, 
           if (old == ad) {
             const int s = (int)ld_acquire_i((const int*)&M->pubq[ad % MAX_SLOTS]);
             // (requests without primaries are finished by the host, never published)
-            if (ld_acquire_i(&C[s].state) == SLOT_PASS1)
+            if (state_kind(ld_acquire_i(&C[s].state)) == SLOT_PASS1)
               atomicOr(&M->bitmap[s >> 5], 1u << (s & 31));
             ++ad;
           } else {
@@ -332,29 +379,21 @@ __global__ void __launch_bounds__(256, 2) multi_kernel(SlotDesc* D, SlotCtl* C, 
               bits &= bits - 1;
               const int s = wi * 32 + bit;
               const int st = ld_acquire_i(&C[s].state);
-              if (st != SLOT_PASS1 && st != SLOT_PASS2) continue;
-              const int p = st == SLOT_PASS2 ? 2 : 1;
-              const long long n = D[s].n_prim;
-              unsigned long long* word = &C[s].word[p - 1];
-              const unsigned long long old =
-                  atomicAdd(word, ((unsigned long long)k << 32) + (unsigned long long)k);
-              const long long next = (long long)(old >> 32);
-              // Only the claim that takes the last primaries clears the bit.  A
-              // claim made on a pass that had just ended (state read as pass 1
-              // while the pass completed) gets nothing and must not clear it:
-              // the warp completing pass 1 sets the bit again for pass 2, and a
-              // late clear would leave pass 2's primaries unclaimed for good.
+              if (state_kind(st) != SLOT_PASS1 && state_kind(st) != SLOT_PASS2) continue;
+              // Only the claim that takes the last primaries clears the bit; a
+              // claim on a pass that has ended takes nothing and leaves the bit
+              // alone (the warp completing pass 1 sets it again for pass 2).
               // The taking claim holds live particles, so the pass cannot end
               // before its clear.
-              if (next < n && next + k >= n) atomicAnd(&M->bitmap[wi], ~(1u << bit));
-              const long long left = n - next;
-              const int g = left <= 0 ? 0 : (left < k ? (int)left : k);
-              if (g < k) {
-                const unsigned long long dec = (unsigned long long)(k - g);
-                const unsigned long long o2 = atomicAdd(word, (unsigned long long)0 - dec);
-                if (pass_emptied(o2, dec, n)) { trigA = 1; tslotA = s; tpassA = p; }
+              unsigned long long first = 0;
+              const int g = claim_primaries(D, C, M, s, st, k, &first);
+              if (g > 0) {
+                got = g;
+                base = first;
+                src = 2;
+                gslot = s;
+                gpass = state_kind(st) == SLOT_PASS2 ? 2 : 1;
               }
-              if (g > 0) { got = g; base = (unsigned long long)next; src = 2; gslot = s; gpass = p; }
             }
           }
         }
@@ -485,20 +524,17 @@ __global__ void __launch_bounds__(256, 2) multi_kernel(SlotDesc* D, SlotCtl* C, 
     }
 
     // ---- passes that just emptied: the whole warp finishes them ----
-    for (int round = 0; round < 2; ++round) {
-      const int tr = round == 0 ? trigA : trigB;
-      const int ts = round == 0 ? tslotA : tslotB;
-      const int tp = round == 0 ? tpassA : tpassB;
-      unsigned mt = __ballot_sync(FULL, tr);
+    {
+      unsigned mt = __ballot_sync(FULL, trigB);
       while (mt) {
         const int srcl = __ffs(mt) - 1;
-        const int s = __shfl_sync(FULL, ts, srcl);
-        const int p = __shfl_sync(FULL, tp, srcl);
+        const int s = __shfl_sync(FULL, tslotB, srcl);
+        const int p = __shfl_sync(FULL, tpassB, srcl);
         complete_pass(D, C, M, s, p, lane);
         mt &= mt - 1;
       }
     }
-    trigA = trigB = 0;
+    trigB = 0;
 
     if (!busy) {
       // leave when the host has closed the session and every published

@@ -2,12 +2,21 @@
 //
 // Many independent source configurations (requests) share one persistent
 // launch.  Each request owns a slot: its parameter blocks for pass 1 and pass
-// 2, its tally buffers, and a control line with, per pass, one 64-bit word
-// "next primary << 32 | live particles".  Claims and deaths are single atomics
-// on that word, so a pass of a request is complete exactly when a decrement
-// leaves no live particle with every primary claimed; the warp that observes
-// it builds the request's target fields (pass 1 -> 2) or finalises and
-// normalises its outputs (last pass) inside the kernel.
+// 2, its tally buffers, and a control line with the slot state and, per pass,
+// one 64-bit word "generation | next primary | live particles".  Claims are a
+// compare-and-swap on that word that never takes primaries past the end;
+// products and deaths are single atomics on the live count, so a pass of a
+// request is complete exactly when a decrement leaves no live particle with
+// every primary claimed; the warp that observes it builds the request's
+// target fields (pass 1 -> 2) or finalises and normalises its outputs (last
+// pass) inside the kernel.
+//
+// A slot is reused by later requests.  The host gives each admission a new
+// generation, carried in the state word (bits 8 and up) and, modulo 32, in the
+// top bits of the pass words; a claim succeeds only on a word of the
+// generation whose state the claiming lane read, so a lane delayed across a
+// request's completion and the admission of the next request into its slot
+// cannot take the new request's primaries under the old request's pass.
 #pragma once
 #include "karl_device.cuh"
 
@@ -16,9 +25,29 @@ namespace karl {
 constexpr int MAX_SLOTS = 1024;          // request slots (10 bits in the particle word)
 enum { SLOT_EMPTY = 0, SLOT_PASS1 = 1, SLOT_PASS2 = 2, SLOT_TRANS = 3, SLOT_DONE = 4 };
 
+// pass word: generation (5 bits) | next primary (31 bits) | live particles (28 bits)
+constexpr int WORD_NEXT_SHIFT = 28;
+constexpr int WORD_GEN_SHIFT = 59;
+constexpr unsigned long long WORD_LIVE_MASK = (1ULL << WORD_NEXT_SHIFT) - 1;
+constexpr unsigned long long WORD_NEXT_MASK = (1ULL << (WORD_GEN_SHIFT - WORD_NEXT_SHIFT)) - 1;
+constexpr long long MAX_REQUEST_PRIMARIES = (1LL << 31) - 1;
+
+__host__ __device__ __forceinline__ unsigned long long word_gen(unsigned long long w) {
+  return w >> WORD_GEN_SHIFT;
+}
+__host__ __device__ __forceinline__ long long word_next(unsigned long long w) {
+  return (long long)((w >> WORD_NEXT_SHIFT) & WORD_NEXT_MASK);
+}
+__host__ __device__ __forceinline__ unsigned long long word_live(unsigned long long w) {
+  return w & WORD_LIVE_MASK;
+}
+// slot state word: generation << 8 | SLOT_*
+__host__ __device__ __forceinline__ int state_kind(int st) { return st & 0xff; }
+__host__ __device__ __forceinline__ unsigned state_gen(int st) { return (unsigned)st >> 8; }
+
 struct SlotCtl {
-  unsigned long long word[2];            // per pass: next primary << 32 | live particles
-  int state;                             // SLOT_*
+  unsigned long long word[2];            // per pass: generation | next primary | live
+  int state;                             // generation << 8 | SLOT_*
   int pass;                              // pass being run (1 or 2)
   char pad[104];
 };

@@ -111,6 +111,7 @@ struct Request {
   std::vector<double> n2, col2;      // three-body clustering field (empty if unused)
   // device pointers of the final pass and of the outputs, for collection
   unsigned long long *spec = nullptr, *rec = nullptr, *led = nullptr, *chan = nullptr;
+  unsigned long long* led1 = nullptr;   // pass-1 ledger of a two-pass request, else NULL
   unsigned long long *time_out = nullptr, *cpos = nullptr, *cneg = nullptr;
   double *density = nullptr, *current = nullptr, *field = nullptr;
   karl_status fail = KARL_OK;
@@ -146,6 +147,8 @@ struct karl_server {
   unsigned* h_pubq = nullptr;
   unsigned long long* h_pubval = nullptr;
   int* h_done = nullptr;                       // mapped: written by the kernel
+  int* h_state = nullptr;                      // pinned: slot states being published
+  std::vector<unsigned> slot_gen;              // admissions into each slot so far (mod 2^24)
   int* d_done = nullptr;
   int* h_flag = nullptr;                       // pinned 1 (shutdown / cancel source)
   char* h_zero = nullptr;                      // pinned zeros: clears device memory by copy
@@ -371,14 +374,25 @@ karl_status admit(karl_server* srv, Request& r) {
   r.spec = pb[fp].spec;
   r.rec = pb[fp].rec;
   r.led = pb[fp].led;
+  r.led1 = fp == 1 ? pb[0].led : nullptr;
   r.chan = pb[fp].chan;
+  // A new generation for the slot.  Written in three ordered copies: the
+  // control line with this generation's pass words and the state still empty,
+  // then the descriptor, then the state "pass 1".  A lane that read the
+  // previous request's state claims only on words of that generation, and a
+  // lane that sees this descriptor also sees this generation's words.
+  const unsigned gen = srv->slot_gen[slot] = (srv->slot_gen[slot] + 1) & 0xffffffu;
   SlotCtl& c = srv->h_ctl[slot];
   std::memset(&c, 0, sizeof c);
-  c.state = SLOT_PASS1;
+  c.word[0] = c.word[1] = (unsigned long long)(gen & 31u) << WORD_GEN_SHIFT;
+  c.state = (int)(gen << 8) | SLOT_EMPTY;
   c.pass = 1;
   srv->h_done[slot] = 0;
-  SCK(cudaMemcpyAsync(srv->d_desc + slot, &d, sizeof d, cudaMemcpyHostToDevice, cs));
+  srv->h_state[slot] = (int)(gen << 8) | SLOT_PASS1;
   SCK(cudaMemcpyAsync(srv->d_ctl + slot, &c, sizeof c, cudaMemcpyHostToDevice, cs));
+  SCK(cudaMemcpyAsync(srv->d_desc + slot, &d, sizeof d, cudaMemcpyHostToDevice, cs));
+  SCK(cudaMemcpyAsync(&srv->d_ctl[slot].state, srv->h_state + slot, sizeof(int),
+                      cudaMemcpyHostToDevice, cs));
   srv->slot_req[slot] = 1;
   if (z.n == 0) {
     // nothing to transport: zero outputs, finished at once
@@ -415,6 +429,9 @@ karl_status collect(karl_server* srv, Request& r) {
   SCK(cudaMemcpyAsync(o.cross_neg, r.cneg, z.cross * 8, cudaMemcpyDeviceToHost, cs));
   SCK(cudaMemcpyAsync(o.recomb, r.rec, z.rec * 8, cudaMemcpyDeviceToHost, cs));
   SCK(cudaMemcpyAsync(o.ledger, r.led, LEDGER * 8, cudaMemcpyDeviceToHost, cs));
+  unsigned long long led1[2] = {0, 0};
+  if (r.led1)
+    SCK(cudaMemcpyAsync(led1, r.led1 + L_N_COLL_ALL, sizeof led1, cudaMemcpyDeviceToHost, cs));
   if (o.chan_count && srv->model.nch)
     SCK(cudaMemcpyAsync(o.chan_count, r.chan, (size_t)srv->model.nch * 8, cudaMemcpyDeviceToHost,
                         cs));
@@ -432,7 +449,10 @@ karl_status collect(karl_server* srv, Request& r) {
     std::memset(o.ledger, 0, LEDGER * 8);
     if (o.chan_count && srv->model.nch) std::memset(o.chan_count, 0, (size_t)srv->model.nch * 8);
   }
-  srv->stats.collisions += ((int64_t*)o.ledger)[L_N_COLL];
+  // the ledger is the last pass's; its all-pass counts take pass 1's as well
+  ((int64_t*)o.ledger)[L_N_COLL_ALL] += (int64_t)led1[0];
+  ((int64_t*)o.ledger)[L_N_FLIGHT_ALL] += (int64_t)led1[1];
+  srv->stats.collisions += ((int64_t*)o.ledger)[L_N_COLL_ALL];
   srv->arena.release(r.off, r.bytes);
   srv->slot_req[r.slot] = -1;
   r.state = REQ_FINISHED;
@@ -464,7 +484,8 @@ karl_status reap_launch(karl_server* srv) {
           : 0.0;
   if (hc.error == ERR_CAPACITY) {
     // products overflowed the shared ring: grow it for the next launch
-    srv->ring_cap *= 4;
+    // (at most 2^26 cells: a request's live count has 28 bits in its pass word)
+    if (srv->ring_cap < (1ULL << 26)) srv->ring_cap *= 4;
   }
   if (hc.error != 0) {
     const karl_status st = hc.error == ERR_TIMEOUT ? KARL_ETIMEOUT
@@ -485,9 +506,9 @@ karl_status reap_launch(karl_server* srv) {
           const Request& r = kv.second;
           if (r.state != REQ_ADMITTED || srv->h_done[r.slot]) continue;
           const SlotCtl& c = hs[r.slot];
-          snprintf(b, sizeof b, "; slot %d state %d pass %d claimed/live %llu/%llu %llu/%llu of %zu",
-                   r.slot, c.state, c.pass, c.word[0] >> 32, c.word[0] & 0xffffffffULL,
-                   c.word[1] >> 32, c.word[1] & 0xffffffffULL, r.z.size());
+          snprintf(b, sizeof b, "; slot %d state %d gen %u pass %d claimed/live %lld/%llu %lld/%llu of %zu",
+                   r.slot, state_kind(c.state), state_gen(c.state), c.pass, word_next(c.word[0]),
+                   word_live(c.word[0]), word_next(c.word[1]), word_live(c.word[1]), r.z.size());
           detail += b;
         }
       }
@@ -639,12 +660,14 @@ karl_status karl_server_create(const karl_xs* xs, const karl_server_opts* opts,
       cudaHostAlloc(&srv->h_pubq, sizeof(unsigned) * MAX_SLOTS, cudaHostAllocDefault) ||
       cudaHostAlloc(&srv->h_pubval, sizeof(unsigned long long) * MAX_SLOTS, cudaHostAllocDefault) ||
       cudaHostAlloc(&srv->h_done, sizeof(int) * MAX_SLOTS, cudaHostAllocMapped) ||
+      cudaHostAlloc(&srv->h_state, sizeof(int) * MAX_SLOTS, cudaHostAllocDefault) ||
       cudaHostGetDevicePointer(&srv->d_done, srv->h_done, 0) ||
       cudaHostAlloc(&srv->h_flag, sizeof(int), cudaHostAllocDefault) ||
       cudaHostAlloc(&srv->h_zero, ZERO_CHUNK, cudaHostAllocDefault))
     return bail(KARL_ENOMEM);
   std::memset(srv->h_zero, 0, ZERO_CHUNK);
   std::memset(srv->h_done, 0, sizeof(int) * MAX_SLOTS);
+  srv->slot_gen.assign(MAX_SLOTS, 0);
   srv->arena.init((size_t)o.hbm_budget_bytes);
   if (sig_t.size() &&
       (cudaMemcpy(srv->d_sig_t, sig_t.data(), sig_t.size() * 8, cudaMemcpyHostToDevice) ||
@@ -705,6 +728,8 @@ karl_status karl_server_submit(karl_server* srv, const karl_geometry* g, const k
   srv->err.clear();
   if (!geometry_ok(g)) return sfail(srv, KARL_EINVAL, "invalid geometry");
   if (!pr || pr->n < 0 || pr->on_device) return sfail(srv, KARL_EINVAL, "primaries: host arrays");
+  if (pr->n > MAX_REQUEST_PRIMARIES)
+    return sfail(srv, KARL_EINVAL, "a request holds at most 2^31 - 1 primaries");
   if (pr->n > 0 && (!pr->z_m || !pr->e_ev || !pr->mu || !pr->species))
     return sfail(srv, KARL_EINVAL, "primaries: NULL array");
   if (!(pr->n_decays > 0)) return sfail(srv, KARL_EINVAL, "n_decays must be > 0");
@@ -841,6 +866,7 @@ void karl_server_destroy(karl_server* srv) {
   if (srv->h_pubq) cudaFreeHost(srv->h_pubq);
   if (srv->h_pubval) cudaFreeHost(srv->h_pubval);
   if (srv->h_done) cudaFreeHost(srv->h_done);
+  if (srv->h_state) cudaFreeHost(srv->h_state);
   if (srv->h_flag) cudaFreeHost(srv->h_flag);
   if (srv->h_zero) cudaFreeHost(srv->h_zero);
   if (srv->ev0) cudaEventDestroy(srv->ev0);

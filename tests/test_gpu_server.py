@@ -196,3 +196,75 @@ def test_contexts_come_and_go_during_a_served_launch(karl):
         srv.close()
     assert done and parity.ledger_balances(t["ledger"])
     assert dt < 5.0, dt
+
+
+def _tiny_requests(n, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        col = rng.uniform(0.1, 1.0) * 5e21
+        length = rng.uniform(0.5, 2.0)
+        n0 = inputs.parabolic_n0(col, length)
+        prob = inputs._problem(f"t{i}", length, 50, inputs.parabolic_segment_means(n0, length, 50),
+                               full=True)
+        out.append((prob, inputs.decay_primaries(prob, int(rng.integers(1, 12)), 500 + i),
+                    4000 + i))
+    return out
+
+
+@pytest.mark.parametrize("prec_name", ["fp64", "fp32"])
+def test_slots_recycled_quickly_in_a_running_launch(karl, prec_name):
+    """Two slots and 96 tiny two-pass requests, all submitted at once and
+    collected by polling while the launch keeps running: each slot is reused
+    about 48 times, so warps scanning for primaries keep meeting slots whose
+    request has just finished and been replaced.  A claim must only ever take
+    primaries of the request (generation) whose state it read; every result
+    equals its single run bit for bit."""
+    prec = karl.FP32 if prec_name == "fp32" else karl.FP64
+    reqs = _tiny_requests(96, seed=33)
+    srv = karl.Server(reqs[0][0], precision=prec, max_slots=2, hbm_budget_bytes=1 << 30,
+                      timeout_s=60)
+    ids = [srv.submit(p, pr, s) for p, pr, s in reqs]
+    assert srv.stats().waiting == len(reqs) - 2
+    results = {}
+    t0 = time.time()
+    while len(results) < len(reqs):
+        assert time.time() - t0 < 60
+        for j, rid in enumerate(ids):
+            if j not in results:
+                done, t = srv.poll(rid)
+                if done:
+                    results[j] = t
+        time.sleep(0.0005)
+    st = srv.stats()
+    srv.run_all()
+    srv.close()
+    assert st.completed == len(reqs)
+    for i, (p, pr, s) in enumerate(reqs):
+        assert parity.ledger_balances(results[i]["ledger"])
+        _same(results[i], _single(karl, p, pr, s, prec))
+
+
+def test_served_request_matches_oracle(karl):
+    """A request served in a mix follows the FP64 oracle's histories: same
+    tallies in law and the same recombination target field (within 1e-3
+    relative L2) -- not only the single-run CUDA path's."""
+    import oracle
+    reqs = _requests(5, seed=13)
+    p, pr, s = reqs[1]
+    srv = karl.Server(p, hbm_budget_bytes=2 << 30, timeout_s=120)
+    ids = [srv.submit(q, qr, qs) for q, qr, qs in reqs]
+    srv.run_all()
+    _, t = srv.poll(ids[1])
+    srv.close()
+    o = oracle.run(p, pr, seed=s, n_threads=8)
+    assert parity.ledger_balances(t["ledger"])
+    assert parity.rel_l2(t["field"], o["field"]) < 1e-3
+    nc_g, nc_o = int(t["ledger"][karl.N_COLLISIONS_ALL]), int(o["ledger"][oracle.N_COLLISIONS_ALL])
+    assert abs(nc_g - nc_o) <= 2e-3 * nc_o, (nc_g, nc_o)
+    for k in ("spectrum", "cross_pos", "cross_neg"):
+        z, pv = parity.poisson_two_sample(t[k], o[k])
+        assert parity.excursions_ok(z) and pv > 0.01, k
+    # matched streams: the channel counts of the last pass agree closely
+    cg, co = t["chan_count"].astype(np.float64), o["chan_count"].astype(np.float64)
+    assert np.all(np.abs(cg - co) <= 4 * np.sqrt(np.maximum(cg + co, 1.0)) + 0.002 * co)
