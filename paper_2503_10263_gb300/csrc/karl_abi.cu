@@ -912,6 +912,13 @@ karl_status karl_run(karl_ctx* ctx, const karl_primaries* pr, const karl_run_opt
     if (s) return s;
     s = run_one_pass(ctx, pr, o, 2, pz, pe, pmu, psp, pp, st);
     if (s) return s;
+    // the ledger holds pass 2; its all-pass counts take pass 1's as well
+    const unsigned long long all[2] = {
+        (unsigned long long)(ctx->stats.collisions[0] + ctx->stats.collisions[1]),
+        (unsigned long long)(ctx->stats.flights[0] + ctx->stats.flights[1])};
+    CK(cudaMemcpyAsync(ctx->d_ledger.p + L_N_COLL_ALL, all, sizeof all, cudaMemcpyHostToDevice,
+                       st));
+    CK(cudaStreamSynchronize(st));
   }
   // normalisation (Eq. target_field_density, Eq. simulated_time, Sec. 2.3)
   double tsim = (double)pr->n_decays / ctx->activity;
@@ -1155,7 +1162,7 @@ namespace {
 
 constexpr int SCRATCH_MAX_DEVICES = 64;
 constexpr unsigned long long SCRATCH_RING_MIN = 1ULL << 16;   // particles
-constexpr unsigned long long SCRATCH_RING_MAX = 1ULL << 22;
+constexpr unsigned long long SCRATCH_RING_MAX = 1ULL << 19;   // 32 MiB of 64-byte cells
 
 std::mutex g_scratch_mu;
 unsigned char* g_scratch_addr[SCRATCH_MAX_DEVICES];           // zero-initialised
@@ -1193,6 +1200,25 @@ struct Carve {
 
 size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// A pointer the kernels may dereference on ctx->device: device memory (or
+// managed memory) of that device.  cudaPointerGetAttributes allocates
+// nothing; a host array passed here would otherwise be read by a kernel.
+karl_status check_device_ptr(karl_ctx* ctx, const void* p, const char* what) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();                           // clear the sticky-free error state
+    return fail(ctx, KARL_EINVAL, "%s: not a CUDA device pointer", what);
+  }
+  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+    return fail(ctx, KARL_EINVAL, "%s: host memory; karl_run_pass_static reads device memory only",
+                what);
+  if (a.type == cudaMemoryTypeDevice && a.device != ctx->device)
+    return fail(ctx, KARL_EINVAL, "%s: memory of device %d, the context is on device %d", what,
+                a.device, ctx->device);
+  return KARL_OK;
+}
+
 // z eq mu node tal pid seq (8 bytes each), ev sj (4 bytes each) per ring cell
 size_t ring_bytes(unsigned long long cap) {
   return 7 * round256((size_t)cap * 8) + 2 * round256((size_t)cap * 4);
@@ -1218,6 +1244,20 @@ extern "C" karl_status karl_run_pass_static(karl_ctx* ctx, const karl_primaries*
   if (!out->spectrum || !out->time_fx || !out->cross_pos || !out->cross_neg || !out->recomb ||
       !out->ledger || (ctx->nch > 0 && !out->chan_count))
     return fail(ctx, KARL_EINVAL, "tally buffer is NULL");
+  // every array the kernels touch must be memory of this context's device
+  {
+    const struct { const void* p; const char* what; bool need; } ptrs[] = {
+        {pr->z_m, "primaries z_m", pr->n > 0}, {pr->e_ev, "primaries e_ev", pr->n > 0},
+        {pr->mu, "primaries mu", pr->n > 0}, {pr->species, "primaries species", pr->n > 0},
+        {out->spectrum, "tallies spectrum", true}, {out->time_fx, "tallies time_fx", true},
+        {out->cross_pos, "tallies cross_pos", true}, {out->cross_neg, "tallies cross_neg", true},
+        {out->recomb, "tallies recomb", true}, {out->ledger, "tallies ledger", true},
+        {out->chan_count, "tallies chan_count", ctx->nch > 0},
+        {out->per_primary, "tallies per_primary", out->per_primary != nullptr && pr->n > 0},
+        {field_time_in, "field_time_in", pass == 2}};
+    for (const auto& q : ptrs)
+      if (q.need && (s = check_device_ptr(ctx, q.p, q.what)) != KARL_OK) return s;
+  }
 
   // the scratch plan, checked before any device call
   const size_t nt = n_time(ctx), nx = n_cross_rg(ctx);

@@ -84,7 +84,8 @@ def test_static_pass_equals_run_pass_twice(karl, prec_name):
 
 def test_static_pass_rejects_what_it_cannot_hold(karl):
     import torch
-    # tallies of 3 x 100002 x 64 x 8 bytes x 2 do not fit the 64 MiB array
+    # time difference arrays of 2 x 4 x 100002 x 64 x 8 bytes (410 MB) do not
+    # fit the 64 MiB array
     nz = 100_000
     big = inputs._problem("big", 10.0, nz, np.full(nz, 1e19), full=False, n_tebins=64)
     _, prims = inputs.config1(n_primaries=10)
@@ -103,3 +104,41 @@ def test_static_pass_rejects_what_it_cannot_hold(karl):
     ts = ctx2.host_tallies(t, True, with_norm=False)
     st = karl.karl_run_pass_static(ctx2.ctx, ps, ctx2.opts(1, 1), 1, None, ts)
     assert st == karl.EINVAL
+    # device primaries and tallies but a host pass-1 time tally for pass 2 (the
+    # form karl_run_pass takes): refused before any launch, not read by a kernel
+    dp2, pp2 = _device_prims(torch, prims)
+    d2, p2 = _device_tallies(torch, ctx2, prims.n)
+    host_time = np.zeros(ctx2.empty_tallies(1)["time_fx"].size, np.uint64)
+    with pytest.raises(karl.KarlError) as e2:
+        ctx2.run_pass_static_device(pp2, prims.n, prims.n_decays, p2, 1, 2,
+                                    field_time_in=host_time.ctypes.data)
+    assert e2.value.status == karl.EINVAL and "field_time_in" in str(e2.value)
+    # a host tally buffer among device ones
+    host_ledger = np.zeros(karl.LEDGER_LEN, np.int64)
+    p3 = dict(p2, ledger=host_ledger.ctypes.data)
+    with pytest.raises(karl.KarlError) as e3:
+        ctx2.run_pass_static_device(pp2, prims.n, prims.n_decays, p3, 1, 1)
+    assert e3.value.status == karl.EINVAL and "ledger" in str(e3.value)
+    # the context still runs
+    ctx2.run_pass_static_device(pp2, prims.n, prims.n_decays, p2, 1, 1)
+
+
+def test_static_pass_leaves_free_device_memory_unchanged(karl):
+    """The property the entry point exists for: a call takes no device memory.
+    After a first call (which looks up the scratch array's address), free
+    device memory is the same before and after each further call."""
+    import torch
+    prob, prims = inputs.config2(n_decays=2000, seed=6)
+    ctx = karl.Context(prob)
+    dp, pp = _device_prims(torch, prims)
+    d1, p1 = _device_tallies(torch, ctx, prims.n)
+    d2, p2 = _device_tallies(torch, ctx, prims.n)
+    ctx.run_pass_static_device(pp, prims.n, prims.n_decays, p1, 3, 1)        # set-up call
+    torch.cuda.synchronize()
+    for call in range(2):
+        free0 = torch.cuda.mem_get_info()[0]
+        ctx.run_pass_static_device(pp, prims.n, prims.n_decays, p1, 3, 1)
+        ctx.run_pass_static_device(pp, prims.n, prims.n_decays, p2, 3, 2,
+                                   field_time_in=d1["time_fx"].data_ptr())
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0, call
