@@ -204,7 +204,7 @@ typedef struct karl_run_opts {
   uint64_t seed;
   int32_t n_passes;            /* 1, or 2 when recombination channels exist */
   int32_t precision;           /* KARL_FP64 (plain) or KARL_FP32 (precision form) */
-  int32_t block_size;          /* 0 = default (FP64 form 256, FP32 form 128) */
+  int32_t block_size;          /* threads per block, a multiple of 32 up to 512; 0 = default */
   int32_t blocks_per_sm;       /* 0 = occupancy maximum */
   double timeout_s;            /* kernel time limit; <= 0 = 600 s */
   void* stream;                /* cudaStream_t, NULL = the context's own stream */
@@ -332,6 +332,13 @@ typedef struct karl_run_stats {
   int32_t grid_blocks, block_size;
   int32_t queue_capacity;
   int64_t kernel_launches;
+  /* per pass: device time from the claim of the last primary to the end of
+   * the launch (the pass tail, when lanes run out of work), and the products
+   * that went through the shared device ring rather than a warp's queue */
+  double tail_ms[2];
+  int64_t spilled[2];
+  /* per pass: share of warp iterations in which the warp held no particle */
+  double idle_warp_frac[2];
 } karl_run_stats;
 karl_status karl_last_stats(const karl_ctx* ctx, karl_run_stats* out);
 

@@ -19,6 +19,15 @@ constexpr double C_LIGHT = 299792458.0;
 constexpr unsigned FULL = 0xffffffffu;
 constexpr long long SPIN_LIMIT = 1LL << 26;    // bounded waits on ring cells
 
+// Explicitly rounded products and fused multiply-adds.  Every product that
+// feeds a sum in the event is written with these, so the compiler cannot fuse
+// a multiply into an add in one kernel and not in another: the single-run and
+// the multi-request kernels then give the same bits.
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
 template <bool F32> struct RT;
 template <> struct RT<false> {
   using R = double;
@@ -36,6 +45,12 @@ template <> struct RT<false> {
     const double2 t = __ldg((const double2*)P.sig + (size_t)i * P.nch + k);
     a = t.x;
     s = t.y;
+  }
+  // cumulative value and slope of the species' gas channels 0..c at node i
+  static __device__ __forceinline__ void cum2(const Params& P, int s, int i, int c, R& a, R& sl) {
+    const double2 t = __ldg((const double2*)P.cum + P.cum_off[s] + (size_t)i * P.ncg[s] + c);
+    a = t.x;
+    sl = t.y;
   }
   static __device__ __forceinline__ R angp(const Params& P, size_t i) { return __ldg(P.ang_pdf + i); }
   static __device__ __forceinline__ R angc(const Params& P, size_t i) { return __ldg(P.ang_cum + i); }
@@ -63,6 +78,11 @@ template <> struct RT<true> {
     const float2 t = __ldg((const float2*)P.sigf + (size_t)i * P.nch + k);
     a = t.x;
     s = t.y;
+  }
+  static __device__ __forceinline__ void cum2(const Params& P, int s, int i, int c, R& a, R& sl) {
+    const float2 t = __ldg((const float2*)P.cumf + P.cum_off[s] + (size_t)i * P.ncg[s] + c);
+    a = t.x;
+    sl = t.y;
   }
   static __device__ __forceinline__ R angp(const Params& P, size_t i) { return __ldg(P.ang_pdff + i); }
   static __device__ __forceinline__ R angc(const Params& P, size_t i) { return __ldg(P.ang_cumf + i); }
@@ -559,6 +579,92 @@ __device__ __forceinline__ void parked_block(const Params& P, const Lane& L,
                 ((unsigned long long)P.pass << 8) | DOM_EVENT, 0ULL, P.seed, L.pid, w);
 }
 
+// Order of doubles by their bit patterns: for x >= +0.0 and any y that is not
+// NaN or -0.0, x <= y exactly when bits(x) <= bits(y) as signed integers (a
+// negative y has a negative pattern).  Column and position comparisons use
+// it, so the segment searches take no FP64 instruction.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+// larger and smaller of two doubles >= +0.0, by their bits
+__device__ __forceinline__ double dmax_nn(double a, double b) {
+  return __longlong_as_double(max(dbits(a), dbits(b)));
+}
+__device__ __forceinline__ double dmin_nn(double a, double b) {
+  return __longlong_as_double(min(dbits(a), dbits(b)));
+}
+
+// Coefficient of channel k in this flight: sigma_k(E) interpolated at node
+// interval ti, 0 at or below its loss; 1/v for an ion recombining with the
+// electron field (whose per-segment value already carries sigma v).
+template <bool F32>
+__device__ __forceinline__ typename RT<F32>::R channel_coef(const Params& P, int k, int s,
+                                                            long long eq, int ti,
+                                                            typename RT<F32>::R tf,
+                                                            typename RT<F32>::R inv_v) {
+  using R = typename RT<F32>::R;
+  const ChanDev& ch = P.ch[k];
+  if (ch.kind == RECOMBINATION && s != SP_E) return inv_v;
+  if (eq > ch.thr_q) {
+    R a0, sl;
+    RT<F32>::tab2(P, k, ti, a0, sl);
+    return fma_rn(tf, sl, a0);
+  }
+  return (R)0;
+}
+
+// Channel choice of the per-channel path: the first channel c (selection
+// order) with target < sum of the rates up to c; rates sigma_c n_j for gas
+// channels and sigma_c times the channel's field at jc for field channels.
+template <bool F32>
+__device__ __noinline__ int select_per_channel(const Params& P, int s, long long eq, int ti,
+                                               typename RT<F32>::R tf, typename RT<F32>::R inv_v,
+                                               int nrec, int jc, unsigned long long w1) {
+  using T = RT<F32>;
+  using R = typename T::R;
+  const int nsc = P.nsc[s];
+  int chs = -1, last = -1;
+  if (nrec == 0) {
+    // gas channels only: the density of segment jc factors out
+    R gas = (R)0;
+    for (int c = 0; c < nsc; ++c) gas += channel_coef<F32>(P, P.sc[s][c], s, eq, ti, tf, inv_v);
+    const R target = mul_rn(T::u(w1), gas);
+    R cum = (R)0;
+    for (int c = 0; c < nsc; ++c) {
+      const R cv = channel_coef<F32>(P, P.sc[s][c], s, eq, ti, tf, inv_v);
+      if (!(cv > (R)0)) continue;
+      last = c;
+      cum += cv;
+      if (target < cum) { chs = c; break; }
+    }
+  } else {
+    const double nj = P.nseg[jc];
+    double rtot = 0.0;
+    for (int c = 0; c < nsc; ++c) {
+      const int kk = P.sc[s][c];
+      rtot = fma_rn((double)channel_coef<F32>(P, kk, s, eq, ti, tf, inv_v),
+                    field_kind(P.ch[kk].kind) ? P.frate[kk][jc] : nj, rtot);
+    }
+    const double target = mul_rn(u01d(w1), rtot);
+    double cum = 0.0;
+    for (int c = 0; c < nsc; ++c) {
+      const int kk = P.sc[s][c];
+      const double rk = mul_rn((double)channel_coef<F32>(P, kk, s, eq, ti, tf, inv_v),
+                               field_kind(P.ch[kk].kind) ? P.frate[kk][jc] : nj);
+      if (!(rk > 0.0)) continue;
+      last = c;
+      cum += rk;
+      if (target < cum) { chs = c; break; }
+    }
+  }
+  if (chs < 0) chs = last;                  // rounding at the top end
+  return chs < 0 ? 0 : chs;
+}
+
+// Quantised time of a path of length len at 1/(|mu| v) = inv_szq / Q_T:
+// round(len * inv_szq) in 2^-50 s units.
+__device__ __forceinline__ unsigned long long quant_len(double len, double inv_szq) {
+  return (unsigned long long)fma_rn(len, inv_szq, 0.5);
+}
+
 template <bool F32>
 __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOut& o,
                       RingPort& port) {
@@ -574,7 +680,6 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
   }
   const int s = L.sp;
   const R e = T::energy(L.eq);
-  const R inv_v = inv_speed<F32>(e, (R)P.inv_mass[s]);
 
   unsigned long long w[4];
   philox4x64_10((unsigned long long)L.ev, L.node,
@@ -582,17 +687,43 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
   const R tau = -T::lg(T::eta(w[0]));
   o.flights += 1;
 
-  // per-flight coefficients: sigma_k(E) (gas, electron recombination) or 1/v
-  // (ion recombining with the electron field, whose rate already has sigma v)
-  const int nsc = P.nsc[s];
-  R coef[MAXSPCH];
-  const R le = T::lg(e * (R)P.inv_e_min);       // ln(E / e_min), shared by both lookups
+  // position of ln E among the table nodes (shared by both lookups)
+  const R le = T::lg(e * (R)P.inv_e_min);
   const R lx = le * (R)P.inv_h;
   int ti = (int)floor(lx);
   R tf;
-  if (ti < 0) { ti = 0; tf = (R)0; }
-  else if (ti > P.n_energy - 2) { ti = P.n_energy - 2; tf = (R)1; }
+  bool inside = true;
+  if (ti < 0) { ti = 0; tf = (R)0; inside = false; }
+  else if (ti > P.n_energy - 2) { ti = P.n_energy - 2; tf = (R)1; inside = false; }
   else { tf = lx - (R)ti; }
+
+  // 1/v and 1/(|mu| v) (relativistic: v = c sqrt(x (2 + x)) / (1 + x), x = E / m c^2);
+  // both from one reciprocal root, and the time quantum folded into the second
+  const double amu = fabs(L.mu);
+  const bool still = L.mu == 0.0;
+  const R x = mul_rn(e, (R)P.inv_mass[s]);
+  R inv_v;
+  double inv_szq;                          // Q_T / (|mu| v): time units per metre along z
+  if constexpr (F32) {
+    inv_v = mul_rn(mul_rn((R)1 + x, (R)(1.0 / C_LIGHT)), T::rsq(mul_rn(x, (R)2 + x)));
+    const float amuf = (float)amu;
+    inv_szq = still ? 0.0
+            : amuf > 1e-20f ? (double)mul_rn(mul_rn(inv_v, __frcp_rn(amuf)), (float)Q_T)
+                            : mul_rn((double)inv_v, Q_T / amu);  // keeps FP32 in range
+  } else {
+    const double m2 = still ? 1.0 : mul_rn(L.mu, L.mu);
+    const double base =
+        mul_rn(mul_rn((R)1 + x, 1.0 / C_LIGHT), rsqrt(mul_rn(m2, mul_rn(x, (R)2 + x))));
+    inv_v = still ? base : mul_rn(base, amu);
+    inv_szq = mul_rn(base, Q_T);
+  }
+
+  // ---- rate coefficients of this flight ----
+  const int nsc = P.nsc[s];
+  const int ncg = P.ncg[s];
+  // cumulative tables: the species' gas channels lead its selection order and
+  // no channel threshold falls inside this node interval
+  const bool fast = ncg > 0 && inside && !P.mixed[s * P.n_energy + ti];
   R gas = (R)0;
   int nrec = 0;
   double rc0 = 0.0, rc1 = 0.0;
@@ -600,28 +731,29 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
   const double* rcol1 = P.colgas;
   const double* rrate0 = P.nseg;
   const double* rrate1 = P.nseg;
-#pragma unroll
-  for (int c = 0; c < MAXSPCH; ++c) {
-    if (c >= nsc) break;
-    const int k = P.sc[s][c];
-    const ChanDev& ch = P.ch[k];
-    R cv;
-    if (ch.kind == RECOMBINATION && s != SP_E) {
-      cv = inv_v;
-    } else if (L.eq > ch.thr_q) {
-      R a0, sl;
-      T::tab2(P, k, ti, a0, sl);
-      cv = a0 + tf * sl;
-    } else {
-      cv = (R)0;
-    }
-    coef[c] = cv;
-    if (!field_kind(ch.kind)) {
-      gas += cv;
-    } else {
+  if (fast) {
+    R a0, sl;
+    T::cum2(P, s, ti, ncg - 1, a0, sl);
+    gas = fma_rn(tf, sl, a0);
+    for (int c = ncg; c < nsc; ++c) {       // field channels follow the gas channels
+      const int k = P.sc[s][c];
+      const R cv = channel_coef<F32>(P, k, s, L.eq, ti, tf, inv_v);
       if (nrec == 0) { rc0 = (double)cv; rcol0 = P.fcol[k]; rrate0 = P.frate[k]; }
       else { rc1 = (double)cv; rcol1 = P.fcol[k]; rrate1 = P.frate[k]; }
       ++nrec;
+    }
+  } else {
+#pragma unroll 1
+    for (int c = 0; c < nsc; ++c) {
+      const int k = P.sc[s][c];
+      const R cv = channel_coef<F32>(P, k, s, L.eq, ti, tf, inv_v);
+      if (!field_kind(P.ch[k].kind)) {
+        gas += cv;
+      } else {
+        if (nrec == 0) { rc0 = (double)cv; rcol0 = P.fcol[k]; rrate0 = P.frate[k]; }
+        else { rc1 = (double)cv; rcol1 = P.fcol[k]; rrate1 = P.frate[k]; }
+        ++nrec;
+      }
     }
   }
   // energy bin of the time tally
@@ -638,24 +770,24 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
   // G(k) = optical-depth column of the whole rate to face k, and the rate in
   // segment j (the column tables may live in shared memory: plain loads)
   auto colsum = [&](int k) -> double {
-    double g = gasd * P.colgas[k];
-    if (nrec > 0) g += rc0 * rcol0[k];
-    if (nrec > 1) g += rc1 * rcol1[k];
+    double g = mul_rn(gasd, P.colgas[k]);
+    if (nrec > 0) g = fma_rn(rc0, rcol0[k], g);
+    if (nrec > 1) g = fma_rn(rc1, rcol1[k], g);
     return g;
   };
   auto segrate = [&](int j) -> double {
-    double r = gasd * P.nseg[j];
-    if (nrec > 0) r += rc0 * rrate0[j];
-    if (nrec > 1) r += rc1 * rrate1[j];
+    double r = mul_rn(gasd, P.nseg[j]);
+    if (nrec > 0) r = fma_rn(rc0, rrate0[j], r);
+    if (nrec > 1) r = fma_rn(rc1, rrate1[j], r);
     return r;
   };
 
   const int j0 = L.j;
+  const int nz = P.nz;
   double zc;
   int jc;
   int exit_end = -1;
-  double inv_sz = 0.0;
-  if (L.mu == 0.0) {
+  if (still) {
     // no motion along z: collide in place after path tau / rate
     jc = j0;
     const double r = segrate(jc);
@@ -664,70 +796,109 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
       o.alive = false;
       return;
     }
-    const double tfl = (double)tau / r * (double)inv_v;
-    atomicAdd(P.time_pt + tbase + (size_t)(jc + 1) * trow, (unsigned long long)(tfl * Q_T + 0.5));
+    const double tfl = mul_rn((double)tau / r, (double)inv_v);
+    atomicAdd(P.time_pt + tbase + (size_t)(jc + 1) * trow, quant_len(tfl, Q_T));
     if (P.track_time) L.tal += tfl;
     zc = L.z;
   } else {
-    // One code path for both directions: the flight ends where the column of
-    // the rate, G, reaches G(z0) +- tau |mu| (optical depth along the path).
     const bool up = L.mu > 0.0;
-    const double amu = fabs(L.mu);
-    const int nz = P.nz;
-    const double g0 = colsum(j0) + segrate(j0) * (L.z - P.faces[j0]);
-    const double delta = (double)tau * amu;
-    const double target = up ? g0 + delta : g0 - delta;
-    const bool ex = up ? !(target < colsum(nz)) : !(target > 0.0);
+    bool ex;
+    if (nrec == 0) {
+      // Gas only: the rate is sigma_gas n_j, so the flight ends where the gas
+      // column C reaches C(z0) +- D with D = tau |mu| / sigma_gas.
+      double tgt = 0.0;
+      if (!(gasd > 0.0)) {
+        ex = true;                          // no channel: straight to an end
+      } else {
+        double D;
+        if constexpr (F32) D = (double)mul_rn(mul_rn(tau, (R)amu), __frcp_rn(gas));
+        else D = mul_rn((double)tau, amu) / gasd;
+        const double c0 = fma_rn(P.nseg[j0], L.z - P.faces[j0], P.colgas[j0]);
+        tgt = up ? c0 + D : c0 - D;
+        const long long tb = dbits(tgt);
+        ex = up ? tb >= dbits(P.colgas[nz]) : tb <= 0;
+        if (!ex) {
+          // largest k with C(k) <= target, in [j0, nz) going up, [0, j0] going down
+          int lo = up ? j0 : 0, hi = up ? nz : j0 + 1;
+          if (P.nq > 0) {
+            const float q = (float)tgt * P.nq_over_colmax_f;
+            if (q >= 0.0f && q < (float)P.nq) {
+              const int qi = (int)q;
+              const int a = max(lo, P.ginv[qi] - 1), bb = min(hi, P.ginv[qi + 1] + 1);
+              if (a < bb && dbits(P.colgas[a]) <= tb && tb < dbits(P.colgas[bb])) {
+                lo = a;
+                hi = bb;
+              }
+            }
+          }
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (dbits(P.colgas[mid]) <= tb) lo = mid; else hi = mid;
+          }
+          jc = lo;
+          const double fj = P.faces[jc];
+          zc = fma_rn(tgt - P.colgas[jc], P.invn[jc], fj);
+          zc = dmin_nn(dmax_nn(zc, fj), P.faces[jc + 1]);
+          zc = up ? dmax_nn(zc, L.z) : dmin_nn(zc, L.z);
+        }
+      }
+    } else {
+      // With field channels the flight inverts the column of the whole rate,
+      // bracketed where the gas column alone would end (the fields add little
+      // rate); the bracket is checked against the exact columns.
+      const double g0 = fma_rn(segrate(j0), L.z - P.faces[j0], colsum(j0));
+      const double delta = mul_rn((double)tau, amu);
+      const double target = up ? g0 + delta : g0 - delta;
+      ex = up ? !(target < colsum(nz)) : !(target > 0.0);
+      if (!ex) {
+        int lo = up ? j0 : 0, hi = up ? nz : j0 + 1;
+        if (gasd > 0.0 && P.nq > 0) {
+          const float q = (float)target * P.nq_over_colmax_f * __frcp_rn((float)gas);
+          if (q >= 0.0f && q < (float)P.nq) {
+            const int qi = (int)q;
+            const int a = max(lo, P.ginv[qi] - 1), bb = min(hi, P.ginv[qi + 1] + 1);
+            if (a < bb && colsum(a) <= target && target < colsum(bb)) { lo = a; hi = bb; }
+          }
+        }
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (colsum(mid) <= target) lo = mid; else hi = mid;
+        }
+        jc = lo;
+        const double fj = P.faces[jc], fj1 = P.faces[jc + 1];
+        const double gap = target - colsum(jc);
+        const double r = segrate(jc);
+        if (F32) zc = fj + (double)((float)gap / (float)r);
+        else zc = fj + gap / r;
+        zc = fmin(fmax(zc, fj), fj1);
+        zc = up ? fmax(zc, L.z) : fmin(zc, L.z);
+      }
+    }
     if (ex) {
       exit_end = up ? 1 : 0;
       zc = up ? P.L : 0.0;
       jc = up ? nz - 1 : 0;
-    } else {
-      // largest k with G(k) <= target, in [j0, nz) going up, [0, j0] going down
-      int lo = up ? j0 : 0, hi = up ? nz : j0 + 1;
-      if (nrec == 0 && gasd > 0.0 && P.nq > 0) {
-        // bracket from the inverse gas-column table (exact with gas only).
-        // Only a hint: it is checked against the exact columns below, so it
-        // is computed in FP32 (a double divide costs the FP64 pipe ~10 ops).
-        const float q = (float)target * P.nq_over_colmax_f * __frcp_rn((float)gas);
-        if (q >= 0.0f && q < (float)P.nq) {
-          const int qi = (int)q;
-          const int a = max(lo, P.ginv[qi] - 1), bb = min(hi, P.ginv[qi + 1] + 1);
-          if (a < bb && colsum(a) <= target && target < colsum(bb)) { lo = a; hi = bb; }
-        }
-      }
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (colsum(mid) <= target) lo = mid; else hi = mid;
-      }
-      jc = lo;
-      const double fj = P.faces[jc], fj1 = P.faces[jc + 1];
-      const double gap = target - colsum(jc);
-      const double r = segrate(jc);
-      if (F32) zc = fj + (double)((float)gap / (float)r);
-      else zc = fj + gap / r;
-      zc = fmin(fmax(zc, fj), fj1);
-      zc = up ? fmax(zc, L.z) : fmin(zc, L.z);
     }
-    // time in each segment crossed (Sec. 2.2) as point adds at both ends and
-    // one range add of the full-segment time, and the face crossings (Sec. 2.3)
-    inv_sz = (double)inv_v / amu;
-    const size_t row0 = tbase + (size_t)(j0 + 1) * trow;
-    if (jc == j0) {
-      atomicAdd(P.time_pt + row0, quant_t(fabs(zc - L.z), inv_sz));
-    } else {
-      const double fs = P.faces[up ? j0 + 1 : j0];
-      atomicAdd(P.time_pt + row0, quant_t(fabs(fs - L.z), inv_sz));
-      const unsigned long long qf = quant_t(P.dz, inv_sz);
-      const double fe = P.faces[up ? jc : jc + 1];
-      atomicAdd(P.time_pt + tbase + (size_t)(jc + 1) * trow, ex ? qf : quant_t(fabs(zc - fe), inv_sz));
+    // time in each segment crossed (Sec. 2.2): the start and end segments as
+    // point adds, the full segments between as one range add; the face
+    // crossings (Sec. 2.3) as one range add.  One instruction stream for a
+    // flight within one segment and one across many.
+    const bool same = jc == j0;
+    const double fs = P.faces[up ? j0 + 1 : j0];
+    const double fe = P.faces[up ? jc : jc + 1];
+    const unsigned long long q0 = quant_len(fabs((same ? zc : fs) - L.z), inv_szq);
+    const unsigned long long qf = quant_len(P.dz, inv_szq);
+    const unsigned long long qe = quant_len(fabs(zc - fe), inv_szq);
+    atomicAdd(P.time_pt + tbase + (size_t)(j0 + 1) * trow, q0);
+    if (!same) {
+      atomicAdd(P.time_pt + tbase + (size_t)(jc + 1) * trow, ex ? qf : qe);
       const int lo_seg = min(j0, jc), hi_seg = max(j0, jc);
       range_add(P.time_rg + tbase, lo_seg + 2, hi_seg, trow, qf);   // full segments
     }
     const int fa = up ? j0 + 1 : (ex ? 0 : jc + 1);
     const int fb = up ? (ex ? nz : jc) : j0;
     range_add((up ? P.xpos_rg : P.xneg_rg) + xbase, fa, fb, 1, 1ULL);
-    if (P.track_time) L.tal += fabs(zc - L.z) * inv_sz;
+    if (P.track_time) L.tal = fma_rn(fabs(zc - L.z), mul_rn(inv_szq, 1.0 / Q_T), L.tal);
   }
   if (exit_end >= 0) {
     long long bin = L.eq / P.spec_bin_q;
@@ -743,35 +914,48 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
   // ---- collision in segment jc: channel with probability rate_k / rate_tot ----
   L.ev += 1;
   o.colls += 1;
-  int chs = -1, last = -1;
-  if (nrec == 0) {
-    // gas channels only: the density of segment jc factors out
-    const R target = T::u(w[1]) * gas;
-    R cum = (R)0;
-#pragma unroll
-    for (int c = 0; c < MAXSPCH; ++c) {
-      if (c >= nsc) break;
-      if (!(coef[c] > (R)0)) continue;
-      last = c;
-      cum += coef[c];
-      if (target < cum) { chs = c; break; }
+  int chs = -1;
+  if (fast) {
+    // the first channel c with target < (cumulative sigma up to c) x density;
+    // a target past every gas channel falls to the field channels
+    R tg;
+    bool gas_part = true;
+    if (nrec == 0) {
+      tg = mul_rn(T::u(w[1]), gas);
+    } else {
+      const double nj = P.nseg[jc];
+      const double target = mul_rn(u01d(w[1]), segrate(jc));
+      const double gasj = mul_rn(gasd, nj);
+      if (target < gasj) {
+        tg = (R)mul_rn(target, P.invn[jc]);
+      } else {
+        gas_part = false;
+        tg = (R)0;
+        double cum = gasj;
+        int last = -1;
+        for (int c = ncg; c < nsc; ++c) {
+          const int kk = P.sc[s][c];
+          const double rk = mul_rn(c == ncg ? rc0 : rc1, P.frate[kk][jc]);
+          if (!(rk > 0.0)) continue;
+          last = c;
+          cum += rk;
+          if (target < cum) { chs = c; break; }
+        }
+        if (chs < 0) chs = last;
+      }
     }
+    if (gas_part) {
+      for (int c = 0; c < ncg; ++c) {
+        R a0, sl;
+        T::cum2(P, s, ti, c, a0, sl);
+        if (tg < fma_rn(tf, sl, a0)) { chs = c; break; }
+      }
+    }
+    if (chs < 0)                        // rounding at the top end
+      chs = select_per_channel<F32>(P, s, L.eq, ti, tf, inv_v, nrec, jc, w[1]);
   } else {
-    const double nj = P.nseg[jc];
-    const double target = u01d(w[1]) * segrate(jc);
-    double cum = 0.0;
-#pragma unroll
-    for (int c = 0; c < MAXSPCH; ++c) {
-      if (c >= nsc) break;
-      const int kk = P.sc[s][c];
-      const double rk = (double)coef[c] * (field_kind(P.ch[kk].kind) ? P.frate[kk][jc] : nj);
-      if (!(rk > 0.0)) continue;
-      last = c;
-      cum += rk;
-      if (target < cum) { chs = c; break; }
-    }
+    chs = select_per_channel<F32>(P, s, L.eq, ti, tf, inv_v, nrec, jc, w[1]);
   }
-  if (chs < 0) chs = last;
   const int k = P.sc[s][chs];
   o.chan = k;
   const ChanDev ch = P.ch[k];
@@ -782,20 +966,21 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
     // impact energy for a target at rest): lab polar angle and energy transfer
     const R g = (R)P.gam[s];
     const R cchi = elastic_cchi<F32>(P, ch, e, T::u(w[2]));
-    const R a = (R)1 + (R)2 * g * cchi + g * g;
+    const R a = fma_rn(mul_rn((R)2, g), cchi, fma_rn(g, g, (R)1));
     const R ra = T::rsq(a);
-    const R ct = (cchi + g) * ra;
+    const R ct = mul_rn(cchi + g, ra);
     // energy given to the target, E - E' = E 2g(1 - cos chi)/(1+g)^2
-    const R de = e * ((R)2 * g) * ((R)1 - cchi) * (R)P.inv_1pg2[s];
+    const R de = mul_rn(mul_rn(mul_rn(e, mul_rn((R)2, g)), (R)1 - cchi), (R)P.inv_1pg2[s]);
     long long rq = T::quant_de(de);
     if (rq > L.eq) rq = L.eq;
     o.recoil += (unsigned long long)rq;
     L.eq -= rq;
     // sin(theta_lab) sqrt(1 - mu^2) in one root: 1 - ct^2 = (1 - cchi^2) / a
-    const R cphi = T::cpi((R)2 * T::u(w[3]));
+    const R cphi = T::cpi(mul_rn((R)2, T::u(w[3])));
     const R mu = (R)L.mu;
-    const R ss = T::sq(fmax((R)0, ((R)1 - cchi * cchi) * ((R)1 - mu * mu))) * ra;
-    L.mu = (double)fmin((R)1, fmax((R)-1, mu * ct + ss * cphi));
+    const R ss = mul_rn(T::sq(fmax((R)0, mul_rn(fma_rn(-cchi, cchi, (R)1), fma_rn(-mu, mu, (R)1)))),
+                        ra);
+    L.mu = (double)fmin((R)1, fmax((R)-1, fma_rn(mu, ct, mul_rn(ss, cphi))));
   } else if (ch.kind == EXCITATION) {
     L.eq -= ch.loss_q;
     o.excit += (unsigned long long)ch.loss_q;

@@ -119,10 +119,11 @@ inline bool xs_ok(const karl_xs* x) {
   return angular_ok(x);
 }
 
-// Gas column to each face, face positions (the last face is L exactly), and
-// the inverse column on nq even steps (a search bracket for the flights).
+// Gas column to each face, face positions (the last face is L exactly), the
+// inverse density of each segment (0 without gas), and the inverse column on
+// nq even steps (a search bracket for the flights).
 struct ColumnTables {
-  std::vector<double> col, faces;
+  std::vector<double> col, faces, invn;
   std::vector<int> ginv;
   int nq = 0;
   double colmax = 0.0;
@@ -132,12 +133,16 @@ inline ColumnTables column_tables(const double* nseg, int nz, double length) {
   ColumnTables t;
   const double dz = length / nz;
   t.col.assign(nz + 1, 0.0);
-  for (int j = 0; j < nz; ++j) t.col[j + 1] = t.col[j] + nseg[j] * dz;
+  t.invn.assign(nz, 0.0);
+  for (int j = 0; j < nz; ++j) {
+    t.col[j + 1] = t.col[j] + nseg[j] * dz;
+    t.invn[j] = nseg[j] > 0 ? 1.0 / nseg[j] : 0.0;
+  }
   t.faces.resize(nz + 1);
   for (int k = 0; k < nz; ++k) t.faces[k] = (double)k * dz;
   t.faces[nz] = length;
   t.colmax = t.col[nz];
-  t.nq = t.colmax > 0 ? std::min(8192, std::max(1024, 2 * nz)) : 0;
+  t.nq = t.colmax > 0 ? std::min(8192, std::max(256, nz)) : 0;
   t.ginv.assign(t.nq + 1, 0);
   for (int q = 0, k = 0; q <= t.nq; ++q) {
     const double c = (double)q * t.colmax / t.nq;
@@ -231,6 +236,21 @@ inline void angular_tables(const karl_xs* x, std::vector<double>& pdf, std::vect
   cumf.assign(cum.begin(), cum.end());
 }
 
+// Gas channels (rate sigma n(z)) that lead species s's selection order and
+// are followed by field channels only: their count, or 0 when a gas channel
+// follows a field channel (then every flight takes the per-channel path).
+inline int leading_gas_channels(const ModelInfo& m, int s) {
+  int n = 0;
+  bool field_seen = false;
+  for (int k = 0; k < m.nch; ++k) {
+    if (m.sin[k] != s) continue;
+    if (field_kind(m.kind[k])) field_seen = true;
+    else if (field_seen) return 0;
+    else ++n;
+  }
+  return n;
+}
+
 // Everything of Params that does not depend on device buffers.
 inline void fill_params(Params& P, const karl_geometry& g, const ModelInfo& m, int pass,
                         unsigned long long seed, int nq, double colmax) {
@@ -276,6 +296,8 @@ inline void fill_params(Params& P, const karl_geometry& g, const ModelInfo& m, i
       if (n < MAXSPCH) P.sc[s][n++] = (int8_t)k;
     }
     P.nsc[s] = n;
+    P.ncg[s] = leading_gas_channels(m, s);
+    P.cum_off[s] = s == 0 ? 0 : P.cum_off[s - 1] + P.ncg[s - 1] * m.n_energy;
     P.mass[s] = g.species_mass_ev[s];
     P.inv_mass[s] = 1.0 / g.species_mass_ev[s];
     P.gam[s] = g.species_mass_ev[s] / g.target_mass_ev;
@@ -297,6 +319,57 @@ inline void fill_params(Params& P, const karl_geometry& g, const ModelInfo& m, i
   P.spec_bin_q = (long long)std::llround(g.spec_bin_ev * HOST_Q_ENERGY);
   P.seed = seed;
   P.pass = pass;
+}
+
+// Cumulative gas cross sections for the channel choice and the total rate.
+// For species s, node interval i and its c-th leading gas channel, the sum
+// over channels 0..c that are open across the whole interval (E_i above the
+// channel's loss) of the node value and of the difference to the next node:
+// sigma_0 + ... + sigma_c at energy E in the interval is value + t * slope,
+// t the position of ln E in the interval.  Where a channel threshold falls
+// inside an interval (open for part of it) the interval is marked, and
+// flights there take the per-channel path.  Layout: species s from offset
+// sum_{s' < s} ncg(s') * n_energy, then [node][channel] pairs (value, slope);
+// marks [NSP][n_energy] (the last node marked: no interval above it).
+inline void gas_cum_tables(const karl_xs* x, const ModelInfo& m, std::vector<double>& cum,
+                           std::vector<float>& cumf, std::vector<unsigned char>& mixed) {
+  const int ne = x->n_energy;
+  cum.clear();
+  mixed.assign((size_t)NSP * ne, 1);
+  for (int s = 0; s < NSP; ++s) {
+    const int ng = leading_gas_channels(m, s);
+    if (ng == 0) continue;
+    std::vector<int> ks;
+    for (int k = 0; k < m.nch && (int)ks.size() < ng; ++k)
+      if (m.sin[k] == s) ks.push_back(k);
+    const size_t base = cum.size();
+    cum.resize(base + (size_t)ne * ng * 2, 0.0);
+    for (int i = 0; i + 1 < ne; ++i) {
+      const double ei = m.e_min * std::pow(m.e_max / m.e_min, (double)i / (ne - 1));
+      const double ej = m.e_min * std::pow(m.e_max / m.e_min, (double)(i + 1) / (ne - 1));
+      bool mix = false;
+      double a = 0.0, b = 0.0;
+      for (int c = 0; c < ng; ++c) {
+        const int k = ks[c];
+        const double loss = m.loss[k];
+        // margins of 1e-5 cover the rounding of ln E into the interval index
+        // (FP32 in the precision form); an interval is 0.5 % of E wide
+        const bool open = ei > loss * (1.0 + 1e-5) + 1e-300;
+        const bool closed = ej * (1.0 + 1e-5) <= loss;
+        if (!open && !closed) mix = true;
+        if (open) {
+          const double v = x->sigma_m2[(size_t)k * ne + i];
+          const double vn = x->sigma_m2[(size_t)k * ne + i + 1];
+          a += v;
+          b += vn - v;
+        }
+        cum[base + ((size_t)i * ng + c) * 2] = a;
+        cum[base + ((size_t)i * ng + c) * 2 + 1] = b;
+      }
+      mixed[(size_t)s * ne + i] = mix ? 1 : 0;
+    }
+  }
+  cumf.assign(cum.begin(), cum.end());
 }
 
 inline bool has_recombination(const ModelInfo& m) {

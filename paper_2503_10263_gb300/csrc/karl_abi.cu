@@ -158,6 +158,9 @@ struct karl_ctx {
   std::vector<double> loss;
   // device tables
   DevBuf<double> d_nseg, d_colgas, d_faces, d_sig, d_sig_t, d_frate, d_fcol, d_time1;
+  DevBuf<double> d_invn, d_cum;              // 1/n per segment; cumulative gas cross sections
+  DevBuf<float> d_cumf;
+  DevBuf<unsigned char> d_mixed;
   DevBuf<int> d_ginv;
   int nq = 0;
   double colmax = 0;
@@ -192,6 +195,7 @@ struct karl_ctx {
   template <class F>
   void each_buf(F f) {
     f(d_nseg); f(d_colgas); f(d_faces); f(d_sig); f(d_sig_t); f(d_frate); f(d_fcol); f(d_time1);
+    f(d_invn); f(d_cum); f(d_cumf); f(d_mixed);
     f(d_ginv); f(d_sigf); f(d_ang_pdf); f(d_ang_cum); f(d_ang_pdff); f(d_ang_cumf); f(d_n2);
     f(d_col2); f(d_pz); f(d_pe); f(d_pmu); f(d_psp); f(d_spec); f(d_tpt); f(d_trg); f(d_xpos);
     f(d_xneg); f(d_recomb); f(d_ledger); f(d_chan); f(d_pp); f(d_time); f(d_cpos); f(d_cneg);
@@ -443,7 +447,7 @@ size_t n_recomb(const karl_ctx* c) { return (size_t)NSP * c->nz; }
 // FP64 form is fastest with 256-thread blocks, 2 per SM; the FP32 form with
 // 128-thread blocks, 4 per SM (3.3e9 against 2.7e9 collisions/s; with
 // 256-thread blocks its pass 1 kept only 79 % of its lanes busy).
-int default_block(bool f32) { return f32 ? 128 : 256; }
+int default_block(bool) { return 256; }
 
 karl_status ensure_ring(karl_ctx* ctx, unsigned long long cap) {
   if (ctx->ring_cap >= cap) return KARL_OK;
@@ -470,6 +474,10 @@ void base_params(const karl_ctx* c, Params& P, const karl_run_opts* o, int pass)
   P.ginv = c->nq > 0 ? c->d_ginv.p : nullptr;
   P.sig = c->d_sig_t.p;
   P.sigf = c->d_sigf.p;
+  P.invn = c->d_invn.p;
+  P.cum = c->d_cum.p;
+  P.cumf = c->d_cumf.p;
+  P.mixed = c->d_mixed.p;
   for (int k = 0; k < c->nch; ++k)
     if (c->kind[k] == CLUSTERING3) {
       P.frate[k] = c->d_n2.p;
@@ -501,7 +509,13 @@ karl_status run_one_pass(karl_ctx* ctx, const karl_primaries* pr, const karl_run
   bool f32 = o->precision == KARL_FP32;
   int block = o->block_size > 0 ? o->block_size : default_block(f32);
   int grid = 0;
-  unsigned long long cap = ctx->ring_cap ? ctx->ring_cap : (1ULL << 22);
+  // The shared product ring: a power of two of cells, at least 2^22 and
+  // about one cell per primary up to 2^24 (1 GiB), so that in a large pass the
+  // spilled products rarely fill it to the level at which lanes stop taking
+  // new primaries; it grows (the pass rerun) only if it overflows.
+  unsigned long long want = 1ULL << 22;
+  while (want < (unsigned long long)pr->n && want < (1ULL << 24)) want <<= 1;
+  unsigned long long cap = ctx->ring_cap > want ? ctx->ring_cap : want;
   double timeout = o->timeout_s > 0 ? o->timeout_s : 600.0;
   for (int attempt = 0; attempt < 4; ++attempt) {
     karl_status rs = ensure_ring(ctx, cap);
@@ -567,6 +581,13 @@ karl_status run_one_pass(karl_ctx* ctx, const karl_primaries* pr, const karl_run
     int pi = pass - 1;
     ctx->stats.kernel_ms[pi] = ms;
     ctx->stats.particles[pi] = (int64_t)hc.particles;
+    ctx->stats.spilled[pi] = (int64_t)hc.spilled;
+    ctx->stats.idle_warp_frac[pi] =
+        hc.busy_iters + hc.idle_iters
+            ? (double)hc.idle_iters / (double)(hc.busy_iters + hc.idle_iters)
+            : 0.0;
+    ctx->stats.tail_ms[pi] =
+        hc.t_end > hc.t_claimed && hc.t_claimed ? (double)(hc.t_end - hc.t_claimed) * 1e-6 : 0.0;
     ctx->stats.lane_occupancy[pi] =
         hc.busy_iters + hc.idle_iters
             ? (double)hc.busy_lane_iters / (32.0 * (double)(hc.busy_iters + hc.idle_iters))
@@ -647,8 +668,8 @@ karl_status check_opts(karl_ctx* ctx, const karl_run_opts* o) {
   if (!o) return fail(ctx, KARL_EINVAL, "opts is NULL");
   if (o->precision != KARL_FP64 && o->precision != KARL_FP32)
     return fail(ctx, KARL_EINVAL, "precision must be KARL_FP64 or KARL_FP32");
-  if (o->block_size != 0 && (o->block_size < 32 || o->block_size > 256 || o->block_size % 32))
-    return fail(ctx, KARL_EINVAL, "block_size must be a multiple of 32 in [32, 256]");
+  if (o->block_size != 0 && (o->block_size < 32 || o->block_size > 512 || o->block_size % 32))
+    return fail(ctx, KARL_EINVAL, "block_size must be a multiple of 32 in [32, 512]");
   return KARL_OK;
 }
 
@@ -729,11 +750,26 @@ karl_status karl_create(const karl_geometry* g, const karl_xs* x, karl_ctx** out
   const ColumnTables tabs = column_tables(ctx->nseg.data(), ctx->nz, ctx->L);
   ctx->nq = tabs.nq;
   ctx->colmax = tabs.colmax;
-  std::vector<double> sig_t;
-  std::vector<float> sigf;
-  node_major_tables(x, sig_t, sigf);
+  std::vector<double> sig_t, cum;
+  std::vector<float> sigf, cumf;
+  std::vector<unsigned char> mixed;
+  try {
+    node_major_tables(x, sig_t, sigf);
+    gas_cum_tables(x, ctx->model, cum, cumf, mixed);
+  } catch (...) {
+    return bail(KARL_ENOMEM);
+  }
   size_t nsig = std::max<size_t>(ctx->sigma.size(), 1);
   size_t nsig2 = std::max<size_t>(sig_t.size(), 1);
+  const size_t ncum = std::max<size_t>(cum.size(), 2);
+  if (ctx->d_invn.ensure(ctx->nz) || ctx->d_cum.ensure(ncum) || ctx->d_cumf.ensure(ncum) ||
+      ctx->d_mixed.ensure(mixed.size()) ||
+      cudaMemcpy(ctx->d_invn.p, tabs.invn.data(), ctx->nz * 8, cudaMemcpyHostToDevice) ||
+      cudaMemcpy(ctx->d_mixed.p, mixed.data(), mixed.size(), cudaMemcpyHostToDevice) ||
+      (!cum.empty() &&
+       (cudaMemcpy(ctx->d_cum.p, cum.data(), cum.size() * 8, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(ctx->d_cumf.p, cumf.data(), cumf.size() * 4, cudaMemcpyHostToDevice))))
+    return bail(KARL_ENOMEM);
   if (ctx->d_nseg.ensure(ctx->nz) || ctx->d_colgas.ensure(ctx->nz + 1) ||
       ctx->d_faces.ensure(ctx->nz + 1) ||
       ctx->d_sig.ensure(nsig) || ctx->d_sig_t.ensure(nsig2) || ctx->d_sigf.ensure(nsig2) ||
@@ -1403,6 +1439,13 @@ extern "C" karl_status karl_run_pass_static(karl_ctx* ctx, const karl_primaries*
   const int pi = pass - 1;
   ctx->stats.kernel_ms[pi] = ms;
   ctx->stats.particles[pi] = (int64_t)hc.particles;
+  ctx->stats.spilled[pi] = (int64_t)hc.spilled;
+  ctx->stats.idle_warp_frac[pi] =
+      hc.busy_iters + hc.idle_iters
+          ? (double)hc.idle_iters / (double)(hc.busy_iters + hc.idle_iters)
+          : 0.0;
+  ctx->stats.tail_ms[pi] =
+      hc.t_end > hc.t_claimed && hc.t_claimed ? (double)(hc.t_end - hc.t_claimed) * 1e-6 : 0.0;
   ctx->stats.lane_occupancy[pi] =
       hc.busy_iters + hc.idle_iters
           ? (double)hc.busy_lane_iters / (32.0 * (double)(hc.busy_iters + hc.idle_iters))

@@ -53,6 +53,7 @@ struct Params {
   const double* colgas;    // [nz+1] column to each face, sum_{i<k} n_i dz
   const double* faces;     // [nz+1] face positions k*dz (face nz = L exactly)
   const int* ginv;         // [nq+1] largest face k with colgas[k] <= q * colmax / nq
+  const double* invn;      // [nz] 1 / n_j (0 in a segment without gas)
   int nq;
   double nq_over_colmax;   // nq / colgas[nz] (0 if the column is empty)
   float nq_over_colmax_f;  // same in FP32 (search hints only)
@@ -64,6 +65,15 @@ struct Params {
   double e_min, inv_e_min, log_ratio_h, inv_h;   // h = ln(e_max/e_min)/(n-1)
   const double* sig;            // [n_energy][nch], the channels of one node together
   const float* sigf;            // same, FP32
+  // cumulative cross sections of each species' leading gas channels over the
+  // channels open in a node interval, pairs (value, slope) at
+  // [cum_off[s] + i * ncg[s] + c]; intervals holding a channel threshold are
+  // marked in mixed[s * n_energy + i] (per-channel path there)
+  const double* cum;
+  const float* cumf;
+  const unsigned char* mixed;
+  int ncg[NSP];                 // leading gas channels of the species (0: per-channel path)
+  int cum_off[NSP];
   int nch;
   ChanDev ch[MAXCH];
   // scattering-angle tables of elastic channels (Sec. 3.3 Elastic): per set
@@ -151,6 +161,8 @@ struct Control {
   unsigned long long busy_iters;      // warp iterations with at least one
   unsigned long long busy_lane_iters; // lanes holding a particle, summed over busy iterations
   unsigned long long spilled;         // products sent to the shared ring
+  // device clock (ns): first block started, last primary claimed, last warp left
+  unsigned long long t_start, t_claimed, t_end;
 };
 
 // ------------------------------------------------------------------------
@@ -204,10 +216,14 @@ __device__ __forceinline__ double log_tab(double x) {
   const int j = (int)((bits >> 44) & 0xff);
   const double m = __longlong_as_double((bits & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
   const double2 c = __ldg(karl_log_cells + j);            // (ln c_j, 1 / c_j)
-  const double r = fma(m, c.y, -1.0);
-  const double p =
-      r * (1.0 + r * (-0.5 + r * (1.0 / 3.0 + r * (-0.25 + r * (0.2 - r * (1.0 / 6.0))))));
-  return fma((double)k, 0.69314718055994530942, c.x + p);
+  const double r = __fma_rn(m, c.y, -1.0);
+  // Horner's form with explicit fused multiply-adds (the same bits in every kernel)
+  double t = __fma_rn(r, -1.0 / 6.0, 0.2);
+  t = __fma_rn(r, t, -0.25);
+  t = __fma_rn(r, t, 1.0 / 3.0);
+  t = __fma_rn(r, t, -0.5);
+  t = __fma_rn(r, t, 1.0);
+  return __fma_rn((double)k, 0.69314718055994530942, __dadd_rn(c.x, __dmul_rn(r, t)));
 }
 
 // uniforms from the top bits of a 64-bit word

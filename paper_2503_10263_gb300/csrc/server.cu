@@ -126,6 +126,9 @@ struct karl_server {
   std::vector<double> sigma;                   // channel-major host copy
   double* d_sig_t = nullptr;
   float* d_sigf = nullptr;
+  double* d_cum = nullptr;                     // cumulative gas cross sections
+  float* d_cumf = nullptr;
+  unsigned char* d_mixed = nullptr;
   double* d_sig_cm = nullptr;
   // scattering-angle tables (NULL: every elastic channel isotropic)
   double* d_ang_pdf = nullptr;
@@ -204,7 +207,7 @@ cudaError_t zero_by_copy(const karl_server* srv, void* dst, size_t bytes, cudaSt
 size_t footprint(const Sizes& z) {
   size_t b = 0;
   b += 3 * up(z.n * 8) + up(z.n);                                   // primaries
-  b += up(z.nz * 8) + 2 * up((z.nz + 1) * 8) + up((z.nq + 1) * 4);  // tables
+  b += 2 * up(z.nz * 8) + 2 * up((z.nz + 1) * 8) + up((z.nq + 1) * 4);  // tables
   const size_t tallies = up(z.nspec * 8) + 2 * up(z.nt * 8) + 2 * up(z.cross_rg * 8) +
                          up(z.rec * 8) + up(LEDGER * 8) + up(MAXCH * 8);
   b += 2 * tallies;                                                 // both passes
@@ -269,6 +272,7 @@ karl_status admit(karl_server* srv, Request& r) {
   double* pmu = (double*)take(z.n * 8);
   uint8_t* psp = (uint8_t*)take(z.n);
   double* nseg = (double*)take(z.nz * 8);
+  double* invn = (double*)take(z.nz * 8);
   double* col = (double*)take((z.nz + 1) * 8);
   double* faces = (double*)take((z.nz + 1) * 8);
   int* ginv = (int*)take((z.nq + 1) * 4);
@@ -308,6 +312,7 @@ karl_status admit(karl_server* srv, Request& r) {
     SCK(cudaMemcpyAsync(psp, r.sp.data(), z.n, cudaMemcpyHostToDevice, cs));
   }
   SCK(cudaMemcpyAsync(nseg, r.nseg.data(), z.nz * 8, cudaMemcpyHostToDevice, cs));
+  SCK(cudaMemcpyAsync(invn, r.tabs.invn.data(), z.nz * 8, cudaMemcpyHostToDevice, cs));
   SCK(cudaMemcpyAsync(col, r.tabs.col.data(), (z.nz + 1) * 8, cudaMemcpyHostToDevice, cs));
   SCK(cudaMemcpyAsync(faces, r.tabs.faces.data(), (z.nz + 1) * 8, cudaMemcpyHostToDevice, cs));
   SCK(cudaMemcpyAsync(ginv, r.tabs.ginv.data(), (z.nq + 1) * 4, cudaMemcpyHostToDevice, cs));
@@ -332,6 +337,10 @@ karl_status admit(karl_server* srv, Request& r) {
     P.ginv = r.tabs.nq > 0 ? ginv : nullptr;
     P.sig = srv->d_sig_t;
     P.sigf = srv->d_sigf;
+    P.invn = invn;
+    P.cum = srv->d_cum;
+    P.cumf = srv->d_cumf;
+    P.mixed = srv->d_mixed;
     P.ang_pdf = srv->d_ang_pdf;
     P.ang_cum = srv->d_ang_cum;
     P.ang_pdff = srv->d_ang_pdff;
@@ -643,10 +652,21 @@ karl_status karl_server_create(const karl_xs* xs, const karl_server_opts* opts,
   if (cudaGetDevice(&srv->device) ||
       cudaDeviceGetAttribute(&srv->num_sms, cudaDevAttrMultiProcessorCount, srv->device))
     return bail(KARL_ECUDA);
-  std::vector<double> sig_t;
-  std::vector<float> sigf;
+  std::vector<double> sig_t, cum;
+  std::vector<float> sigf, cumf;
+  std::vector<unsigned char> mixed;
   node_major_tables(xs, sig_t, sigf);
+  gas_cum_tables(xs, srv->model, cum, cumf, mixed);
   const size_t nsig = std::max<size_t>(sig_t.size(), 1);
+  const size_t ncum = std::max<size_t>(cum.size(), 2);
+  if (cudaMalloc(&srv->d_cum, ncum * 8) || cudaMalloc(&srv->d_cumf, ncum * 4) ||
+      cudaMalloc(&srv->d_mixed, mixed.size()))
+    return bail(KARL_ENOMEM);
+  if (cudaMemcpy(srv->d_mixed, mixed.data(), mixed.size(), cudaMemcpyHostToDevice) ||
+      (!cum.empty() &&
+       (cudaMemcpy(srv->d_cum, cum.data(), cum.size() * 8, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(srv->d_cumf, cumf.data(), cumf.size() * 4, cudaMemcpyHostToDevice))))
+    return bail(KARL_ECUDA);
   srv->sigma.assign(xs->sigma_m2, xs->sigma_m2 + (size_t)xs->n_channels * xs->n_energy);
   if (cudaMalloc(&srv->d_sig_t, nsig * 8) || cudaMalloc(&srv->d_sigf, nsig * 4) ||
       cudaMalloc(&srv->d_sig_cm, nsig * 8) ||
@@ -857,6 +877,7 @@ void karl_server_destroy(karl_server* srv) {
     cudaFree(R.pid); cudaFree(R.ev); cudaFree(R.sj); cudaFree(R.seq);
   }
   cudaFree(srv->d_sig_t); cudaFree(srv->d_sigf); cudaFree(srv->d_sig_cm);
+  cudaFree(srv->d_cum); cudaFree(srv->d_cumf); cudaFree(srv->d_mixed);
   cudaFree(srv->d_ang_pdf); cudaFree(srv->d_ang_cum); cudaFree(srv->d_ang_pdff);
   cudaFree(srv->d_ang_cumf);
   cudaFree(srv->d_desc); cudaFree(srv->d_ctl); cudaFree(srv->d_M); cudaFree(srv->d_cancel);

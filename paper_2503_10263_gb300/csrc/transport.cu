@@ -22,24 +22,27 @@ namespace karl {
 // shared memory when they fit; the event code reads them through P's pointers.
 __device__ void stage_tables(Params& SP, const Params& Pk, double* dyn, int dyn_doubles) {
   const int nz = Pk.nz;
-  int need = (3 * nz + 2) + (Pk.nq + 1 + 1) / 2 + 1;
+  int need = (4 * nz + 2) + (Pk.nq + 1 + 1) / 2 + 1;
   for (int k = 0; k < Pk.nch; ++k)
     if (Pk.fcol[k]) need += 2 * nz + 1;
   if (need > dyn_doubles) return;                   // stay in global memory
   double* col = dyn;
   double* fac = col + (nz + 1);
   double* nseg = fac + (nz + 1);
-  int* ginv = (int*)(nseg + nz);
+  double* invn = nseg + nz;
+  int* ginv = (int*)(invn + nz);
   double* next = (double*)(ginv + ((Pk.nq + 2) & ~1));
   for (int i = threadIdx.x; i <= nz; i += blockDim.x) col[i] = Pk.colgas[i];
   for (int i = threadIdx.x; i <= nz; i += blockDim.x) fac[i] = Pk.faces[i];
   for (int i = threadIdx.x; i < nz; i += blockDim.x) nseg[i] = Pk.nseg[i];
+  for (int i = threadIdx.x; i < nz; i += blockDim.x) invn[i] = Pk.invn[i];
   if (Pk.ginv)
     for (int i = threadIdx.x; i <= Pk.nq; i += blockDim.x) ginv[i] = Pk.ginv[i];
   if (threadIdx.x == 0) {
     SP.colgas = col;
     SP.faces = fac;
     SP.nseg = nseg;
+    SP.invn = invn;
     if (Pk.ginv) SP.ginv = ginv;
   }
   for (int k = 0; k < Pk.nch; ++k) {
@@ -54,20 +57,25 @@ __device__ void stage_tables(Params& SP, const Params& Pk, double* dyn, int dyn_
 }
 
 template <bool F32>
-__global__ void __launch_bounds__(256, 2) transport_kernel(const Params Pk, Ring R, Control* ctl,
+__global__ void __launch_bounds__(512, 1) transport_kernel(const Params Pk, Ring R, Control* ctl,
                                                         const volatile int* cancel,
                                                         unsigned long long timeout_ns,
                                                         int dyn_doubles) {
   const unsigned long long deadline = globaltimer_ns() + timeout_ns;
+  if (threadIdx.x == 0 && ld_relaxed(&ctl->t_start) == 0)
+    atomicCAS(&ctl->t_start, 0ULL, deadline - timeout_ns);
+  // dynamic shared memory: the staged tables (dyn_doubles), then one product
+  // queue and one batch of parked collisions per warp of the block
   extern __shared__ double dyn[];
   __shared__ Shared S;
   __shared__ Params SP;
-  __shared__ WarpQueue wq[WARPS];
-  __shared__ RareBuf rbuf[WARPS];
+  const int nwarps = blockDim.x >> 5;
+  WarpQueue* wq = (WarpQueue*)(dyn + dyn_doubles);
+  RareBuf* rbuf = (RareBuf*)(wq + nwarps);
   if (threadIdx.x == 0) SP = Pk;
   for (int i = threadIdx.x; i < LEDGER; i += blockDim.x) S.ledger[i] = 0;
   for (int i = threadIdx.x; i < MAXCH; i += blockDim.x) S.chan[i] = 0;
-  if (threadIdx.x < WARPS) {
+  if (threadIdx.x < nwarps) {
     wq[threadIdx.x].top = 0;
     rbuf[threadIdx.x].n = 0;
     rbuf[threadIdx.x].r = 0;
@@ -94,6 +102,11 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const Params Pk, Ring
   unsigned long long started = 0;
   unsigned long long idle_iters = 0, busy_iters = 0, busy_lane_iters = 0;
   unsigned idle_ns = 128;
+  // A warp that still holds particles but found nothing for its idle lanes
+  // skips its next refill attempts (1, 3, 7, ... up to 63 iterations): once
+  // the primaries are used up, warps with a few long histories left would
+  // otherwise contend for the ring head on every iteration.
+  int refill_skip = 0, refill_backoff = 0;
   RingPort port;
   port.R = &R;
   port.ctl = ctl;
@@ -183,7 +196,11 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const Params Pk, Ring
     }
 
     // ---- other idle lanes take work: products from the ring, then primaries ----
-    const unsigned need = __ballot_sync(FULL, !has);
+    unsigned need = __ballot_sync(FULL, !has);
+    if (need && need != FULL && refill_skip > 0) {
+      --refill_skip;
+      need = 0;
+    }
     if (need) {
       const int k = __popc(need);
       unsigned long long rbase = 0, pbase = 0;
@@ -191,11 +208,15 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const Params Pk, Ring
       if (lane == 0) {
         // Count the lanes as active only when work is visible, then claim it:
         // idle warps that find nothing leave the counter alone.  Lanes the
-        // ring cannot fill take primaries in the same step.
+        // ring cannot fill take primaries in the same step -- also when a
+        // contended claim on the ring fails -- unless the ring is three
+        // quarters full (products first, so it cannot overflow).  Holding
+        // lanes back for a ring only a quarter full left a quarter of the
+        // FP32 form's lanes idle while every warp fought for the ring head.
         unsigned long long h = ld_relaxed(&ctl->head), t = ld_relaxed(&ctl->tail);
         const unsigned long long pn = ld_relaxed(&ctl->prim_next);
         const bool ring_work = h < t;
-        const bool prim_work = pn < (unsigned long long)P.n_prim && t - h < R.cap / 4;
+        const bool prim_work = pn < (unsigned long long)P.n_prim && t - h < R.cap / 4 * 3;
         if (ring_work || prim_work) {
           atomicAdd((unsigned long long*)&ctl->active, (unsigned long long)k);
           __threadfence();
@@ -213,6 +234,7 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const Params Pk, Ring
               unsigned long long left = (unsigned long long)P.n_prim - p0;
               pbase = p0;
               pgot = left < (unsigned long long)want ? (int)left : want;
+              if (left <= (unsigned long long)want) atomicMax(&ctl->t_claimed, globaltimer_ns());
             }
           }
           if (rgot + pgot < k)
@@ -223,6 +245,13 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const Params Pk, Ring
       pbase = __shfl_sync(FULL, pbase, 0);
       rgot = __shfl_sync(FULL, rgot, 0);
       pgot = __shfl_sync(FULL, pgot, 0);
+      if (rgot + pgot == 0) {
+        refill_backoff = refill_backoff * 2 + 1;
+        if (refill_backoff > 63) refill_backoff = 63;
+        refill_skip = refill_backoff;
+      } else {
+        refill_backoff = 0;
+      }
       bool born_dead = false;
       if (!has && rgot + pgot > 0) {
         const int rank = __popc(need & lt);
@@ -371,6 +400,7 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const Params Pk, Ring
     ex += __shfl_down_sync(FULL, ex, off);
   }
   if (lane == 0) {
+    atomicMax(&ctl->t_end, globaltimer_ns());
     atomicAdd(&ctl->idle_iters, idle_iters);
     atomicAdd(&ctl->spilled, sp);
     atomicAdd(&ctl->busy_iters, busy_iters);
@@ -394,24 +424,33 @@ __global__ void __launch_bounds__(256, 2) transport_kernel(const Params Pk, Ring
 // host-callable launchers (used by the C ABI in karl_abi.cu)
 
 // dynamic shared memory for the staged tables: at most this much per block,
-// so that two blocks of 256 threads (with ~35 KB of static shared memory for
-// the warp queues and parked collisions) still fit one SM's 227 KB
+// so that two blocks of 256 threads (with ~33 KB more for their warp queues
+// and parked collisions) still fit one SM's 227 KB; blocks of 128 threads
+// need half the queue memory and fit four to an SM with config-sized tables
 constexpr int DYN_MAX_BYTES = 76 * 1024;
+// per-warp queues in dynamic shared memory (after the tables)
+constexpr int QUEUE_BYTES_PER_WARP = (int)(sizeof(WarpQueue) + sizeof(RareBuf));
+static_assert(sizeof(WarpQueue) % 8 == 0 && sizeof(RareBuf) % 8 == 0, "queue alignment");
+
 
 // Doubles of dynamic shared memory the staged tables of P need (0: too big,
 // read them from global memory).
 int transport_dyn_doubles(const Params& P) {
-  int need = (3 * P.nz + 2) + (P.nq + 1 + 1) / 2 + 1;
+  int need = (4 * P.nz + 2) + (P.nq + 1 + 1) / 2 + 1;
   for (int k = 0; k < P.nch; ++k)
     if (P.fcol[k]) need += 2 * P.nz + 1;
   return need * 8 <= DYN_MAX_BYTES ? need : 0;
+}
+
+size_t transport_dyn_bytes(const Params& P, int block) {
+  return (size_t)transport_dyn_doubles(P) * 8 + (size_t)(block / 32) * QUEUE_BYTES_PER_WARP;
 }
 
 cudaError_t launch_transport(bool f32, const Params& P, const Ring& R, Control* ctl,
                              const volatile int* cancel, unsigned long long timeout_ns, int grid,
                              int block, cudaStream_t st) {
   const int dd = transport_dyn_doubles(P);
-  const size_t bytes = (size_t)dd * 8;
+  const size_t bytes = transport_dyn_bytes(P, block);
   if (f32)
     transport_kernel<true><<<grid, block, bytes, st>>>(P, R, ctl, cancel, timeout_ns, dd);
   else
@@ -421,14 +460,15 @@ cudaError_t launch_transport(bool f32, const Params& P, const Ring& R, Control* 
 
 cudaError_t transport_setup() {
   cudaError_t e = cudaFuncSetAttribute(transport_kernel<true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, DYN_MAX_BYTES);
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       DYN_MAX_BYTES + 16 * QUEUE_BYTES_PER_WARP);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(transport_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              DYN_MAX_BYTES);
+                              DYN_MAX_BYTES + 16 * QUEUE_BYTES_PER_WARP);
 }
 
 cudaError_t transport_occupancy(bool f32, const Params& P, int block, int* blocks_per_sm) {
-  const size_t bytes = (size_t)transport_dyn_doubles(P) * 8;
+  const size_t bytes = transport_dyn_bytes(P, block);
   if (f32)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, transport_kernel<true>,
                                                          block, bytes);

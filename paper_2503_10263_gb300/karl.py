@@ -102,7 +102,9 @@ class RunStats(C.Structure):
                 ("flights", C.c_int64 * 2), ("particles", C.c_int64 * 2),
                 ("lane_occupancy", C.c_double * 2),
                 ("grid_blocks", C.c_int32), ("block_size", C.c_int32),
-                ("queue_capacity", C.c_int32), ("kernel_launches", C.c_int64)]
+                ("queue_capacity", C.c_int32), ("kernel_launches", C.c_int64),
+                ("tail_ms", C.c_double * 2), ("spilled", C.c_int64 * 2),
+                ("idle_warp_frac", C.c_double * 2)]
 
 
 _lib = None
