@@ -116,6 +116,11 @@ def _load():
             C.POINTER(C.c_uint64), C.POINTER(C.c_double), C.POINTER(C.c_double),
             C.POINTER(C.c_double)]
         lib.orc_charge_exchange.restype = None
+        lib.orc_ionization_moving_target.argtypes = [
+            C.POINTER(_Problem), C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
+            C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
+            C.POINTER(C.c_double)]
+        lib.orc_ionization_moving_target.restype = None
         lib.orc_sample_angle.argtypes = [C.POINTER(_Problem), C.c_int, C.c_double, C.c_double]
         lib.orc_sample_angle.restype = C.c_double
         _lib = lib
@@ -426,3 +431,28 @@ def charge_exchange(prob, m1_ev: float, e_ev: float, mu: float, ctr, key):
                             _ptr(k, C.c_uint64), _ptr(oe, C.c_double), _ptr(om, C.c_double),
                             _ptr(v, C.c_double))
     return float(oe[0]), float(om[0]), v
+
+
+def ionization_moving_target(prob, channel: int, m1_ev: float, e_ev: float, mu: float,
+                             m_ion_ev: float, words, ctr, key, marshal=None) -> dict:
+    """One ionization with a moving target: event block `words` (w[2] shares
+    the energy, w[3] the azimuth), target blocks from counter (ctr[0], ctr[1],
+    ctr[2], k) and key.  Returns the impactor's, ejected electron's and ion's
+    energies and pitch cosines and the impact energy E_i.  Pass the result of
+    marshal_problem(prob) as `marshal` to skip re-marshalling in loops."""
+    lib = _load()
+    m = marshal if marshal is not None else _Marshal(prob)
+    w = np.array(words, np.uint64)
+    c = np.array(ctr, np.uint64)
+    k = np.array(key, np.uint64)
+    out = np.zeros(7)
+    lib.orc_ionization_moving_target(C.byref(m.s), channel, m1_ev, e_ev, mu, m_ion_ev,
+                                     _ptr(w, C.c_uint64), _ptr(c, C.c_uint64),
+                                     _ptr(k, C.c_uint64), _ptr(out, C.c_double))
+    return {"e1": out[0], "mu1": out[1], "e2": out[2], "mu2": out[3], "eion": out[4],
+            "muion": out[5], "ei": out[6]}
+
+
+def marshal_problem(prob):
+    """The oracle's C view of a problem, reusable across single-collision calls."""
+    return _Marshal(prob)

@@ -32,7 +32,11 @@
  *  - ionization: secondary energy W in [0, (E-I)/2] with pdf ~ 1/(1+(W/eps)^2),
  *    the fast electron is the incident one, binary-encounter polar angles,
  *    secondary azimuth = primary azimuth - pi (Sec. 3.3, Ionization); the ion
- *    gets a thermal target velocity (no recoil);
+ *    gets a thermal target velocity (no recoil); for a channel with a moving
+ *    target the target velocity is drawn as for elastic scattering and redrawn
+ *    while the impact energy relative to it is not above I, the sharing and
+ *    angles happen in the target's frame, the ion takes the target velocity,
+ *    and the lab energy the gas gives or takes goes to the recoil ledger;
  *  - clustering: the product takes a thermal target's direction and the speed
  *    that keeps the target's kinetic energy with the product mass; three-body
  *    clustering (Sec. 3.3 Clustering, Eq. clustering_tertiary) has the rate
@@ -277,6 +281,102 @@ void charge_exchange(const orc_problem* p, double m1, double e, double mu, Targe
   const double sp2 = v2[0] * v2[0] + v2[1] * v2[1] + v2[2] * v2[2];
   *e_out = 0.5 * m1 * sp2;
   *mu_out = sp2 > 0.0 ? std::fmax(-1.0, std::fmin(1.0, v2[2] / std::sqrt(sp2))) : 1.0;
+}
+
+/* Target-velocity blocks of redraw r: blocks 128 r + k of the collision's
+ * target stream (each target_velocity call reads at most 128 blocks). */
+struct RedrawCtx {
+  TargetBlock inner;
+  void* inner_ctx;
+  uint64_t base;
+};
+void redraw_block(void* c, uint64_t k, uint64_t out[4]) {
+  RedrawCtx* q = (RedrawCtx*)c;
+  q->inner(q->inner_ctx, q->base + k, out);
+}
+
+/* Outcome of an ionization with a moving target: kinetic energies (eV) and
+ * pitch cosines of the impactor, the ejected electron and the ion, and the
+ * impact energy E_i. */
+struct IonOut {
+  double e1, mu1, e2, mu2, eion, muion, ei;
+};
+
+/* Ionization with a moving target (Sec. 3.3 Ionization).  The target
+ * velocity v2 is drawn as for a moving elastic target (target_velocity);
+ * while the impact energy -- the impactor's kinetic energy relative to the
+ * target, E_i = 1/2 m1 |v1 - v2|^2 -- is not above the ionization energy I, a
+ * new target velocity is drawn (redraw r reads blocks 128 r + k; after 64
+ * redraws the target is taken at rest, whose impact energy is the lab energy,
+ * above I because the channel was chosen).  In the target's frame E_i is
+ * shared as for a target at rest: the ejected electron gets W from the
+ * truncated 1/(1 + (W/eps)^2) law on [0, (E_i - I)/2] (u = w[2]), the
+ * impactor E_i - I - W; their polar angles about the relative velocity are
+ * the binary-encounter ones, cos^2 = energy / (E_i - I), at azimuths phi
+ * (w[3]) and phi - pi measured from the plane of z and the relative velocity.
+ * Adding v2 takes both back to the lab; the ion leaves with v2 (no recoil).
+ * Nonrelativistic velocities in units of c, impactor gyrophase 0 (the target
+ * distribution is symmetric about z). */
+void moving_target_ionization(const orc_problem* p, int ch, double m1, double e, double mu,
+                              double m_ion, const uint64_t w[4], TargetBlock blk, void* ctx,
+                              IonOut* o) {
+  const double me = p->species_mass_ev[SP_E];
+  const double ion_e = p->loss_ev[ch];
+  const double s1 = std::sqrt(2.0 * e / m1);
+  const double sperp = std::sqrt(std::fmax(0.0, 1.0 - mu * mu));
+  const double v1[3] = {s1 * sperp, 0.0, s1 * mu};
+  double v2[3] = {0.0, 0.0, 0.0}, g[3] = {v1[0], v1[1], v1[2]};
+  double ei = e;
+  for (int r = 0; r < 64; ++r) {
+    RedrawCtx rc = {blk, ctx, 128 * (uint64_t)r};
+    double t[3];
+    target_velocity(p, v1, redraw_block, &rc, t);
+    const double d[3] = {v1[0] - t[0], v1[1] - t[1], v1[2] - t[2]};
+    const double er = 0.5 * m1 * (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    if (er > ion_e) {
+      for (int i = 0; i < 3; ++i) { v2[i] = t[i]; g[i] = d[i]; }
+      ei = er;
+      break;
+    }
+  }
+  /* energy sharing in the target's frame */
+  const double avail = ei - ion_e;
+  const double eps = p->ioniz_eps_ev;
+  const double wmax = 0.5 * avail;
+  double wsec = eps * std::tan(u01(w[2]) * std::atan(wmax / eps));
+  wsec = std::fmin(std::fmax(wsec, 0.0), wmax);
+  const double e1 = avail - wsec;
+  const double cp = std::sqrt(e1 / avail), sp = std::sqrt(wsec / avail);
+  /* basis: gh along the relative velocity, b1 the part of z perpendicular to
+     it (x if it is along z), b2 = gh x b1 */
+  const double gn = std::sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+  double gh[3] = {0.0, 0.0, 1.0};
+  if (gn > 0.0) for (int i = 0; i < 3; ++i) gh[i] = g[i] / gn;
+  double b1[3] = {-gh[2] * gh[0], -gh[2] * gh[1], 1.0 - gh[2] * gh[2]};
+  double n1 = std::sqrt(b1[0] * b1[0] + b1[1] * b1[1] + b1[2] * b1[2]);
+  if (n1 < 1e-12) { b1[0] = 1.0; b1[1] = 0.0; b1[2] = 0.0; n1 = 1.0; }
+  for (int i = 0; i < 3; ++i) b1[i] /= n1;
+  const double b2[3] = {gh[1] * b1[2] - gh[2] * b1[1], gh[2] * b1[0] - gh[0] * b1[2],
+                        gh[0] * b1[1] - gh[1] * b1[0]};
+  const double phi = TWO_PI * u01(w[3]);
+  const double cph = std::cos(phi), sph = std::sin(phi);
+  const double u1 = std::sqrt(2.0 * e1 / m1), u2 = std::sqrt(2.0 * wsec / me);
+  double va[3], vb[3];
+  for (int i = 0; i < 3; ++i) {
+    const double side = cph * b1[i] + sph * b2[i];
+    va[i] = v2[i] + u1 * (cp * gh[i] + sp * side);        /* impactor */
+    vb[i] = v2[i] + u2 * (sp * gh[i] - cp * side);        /* ejected electron (phi - pi) */
+  }
+  const double qa = va[0] * va[0] + va[1] * va[1] + va[2] * va[2];
+  const double qb = vb[0] * vb[0] + vb[1] * vb[1] + vb[2] * vb[2];
+  const double q2 = v2[0] * v2[0] + v2[1] * v2[1] + v2[2] * v2[2];
+  o->e1 = 0.5 * m1 * qa;
+  o->mu1 = qa > 0.0 ? std::fmax(-1.0, std::fmin(1.0, va[2] / std::sqrt(qa))) : 1.0;
+  o->e2 = 0.5 * me * qb;
+  o->mu2 = qb > 0.0 ? std::fmax(-1.0, std::fmin(1.0, vb[2] / std::sqrt(qb))) : 1.0;
+  o->eion = 0.5 * m_ion * q2;
+  o->muion = q2 > 0.0 ? std::fmax(-1.0, std::fmin(1.0, v2[2] / std::sqrt(q2))) : 1.0;
+  o->ei = ei;
 }
 
 struct Particle {
@@ -649,6 +749,43 @@ struct Worker {
         int64_t lq = quant_e(p->loss_ev[ch]);
         P.eq -= lq;
         T.ledger[ORC_E_LOSS_EXCIT] += lq;
+      } else if (kind == IONIZATION && p->target && p->target[ch] == 1) {
+        /* moving target: impact energy relative to the target, the lab
+           energies of the two electrons and the ion's velocity from it */
+        struct Ctx { Worker* self; uint32_t ev; uint64_t node; } cx = {this, P.ev - 1, P.node};
+        auto blk = [](void* c, uint64_t k, uint64_t out[4]) {
+          Ctx* q = (Ctx*)c;
+          q->self->block(q->ev, q->node, DOM_TARGET, k, out);
+        };
+        const int ion = p->species_out[ch];
+        const double m_ion = ion >= 0 ? p->species_mass_ev[ion] : p->target_mass_ev;
+        IonOut io;
+        moving_target_ionization(p, ch, m, e, P.mu, m_ion, w, blk, &cx, &io);
+        const int64_t iq = quant_e(p->loss_ev[ch]);
+        const int64_t eq1 = quant_e(io.e1), wq = quant_e(io.e2);
+        T.ledger[ORC_E_LOSS_IONIZ] += iq;
+        /* what the gas gave or took, so the ledger stays exact */
+        T.ledger[ORC_E_LOSS_RECOIL] += P.eq - iq - eq1 - wq;
+        const uint32_t ev_coll = P.ev - 1;
+        Particle S;
+        S.z = P.z; S.eq = wq; S.mu = io.mu2; S.node = child_node(P.node, ev_coll, 0);
+        S.t_alive = 0.0; S.ev = 0; S.species = SP_E;
+        T.ledger[ORC_BIRTHS + SP_E] += 1;
+        T.ledger[ORC_N_SPAWN_E] += 1;
+        if (S.eq < ecut_q) die(S, R_CUTOFF, ORC_E_CUTOFF);
+        else stack.push_back(S);
+        if (ion >= 0) {
+          Particle I;
+          I.z = P.z; I.node = child_node(P.node, ev_coll, 1);
+          I.t_alive = 0.0; I.ev = 0; I.species = ion;
+          I.eq = quant_e(io.eion); I.mu = io.muion;
+          T.ledger[ORC_E_IN_THERMAL] += I.eq;
+          T.ledger[ORC_BIRTHS + ion] += 1;
+          T.ledger[ORC_N_SPAWN_ION] += 1;
+          stack.push_back(I);
+        }
+        P.eq = eq1;
+        P.mu = io.mu1;
       } else if (kind == IONIZATION) {
         int64_t iq = quant_e(p->loss_ev[ch]);
         int64_t avail = P.eq - iq;
@@ -861,6 +998,21 @@ void orc_elastic_moving_target(const orc_problem* p, double m1_ev, double e_ev, 
   for (int k = 0; k < p->n_channels; ++k)
     if (p->kind[k] == ELASTIC) { ch = k; break; }
   moving_target_elastic(p, ch, m1_ev, e_ev, mu, w, blk, &cx, out_e, out_mu, v);
+}
+
+void orc_ionization_moving_target(const orc_problem* p, int channel, double m1_ev, double e_ev,
+                                  double mu, double m_ion_ev, const uint64_t w[4],
+                                  const uint64_t ctr[3], const uint64_t key[2], double out[7]) {
+  struct Ctx { uint64_t ctr[3]; uint64_t key[2]; } cx = {{ctr[0], ctr[1], ctr[2]}, {key[0], key[1]}};
+  auto blk = [](void* c, uint64_t k, uint64_t o4[4]) {
+    Ctx* q = (Ctx*)c;
+    const uint64_t full[4] = {q->ctr[0], q->ctr[1], q->ctr[2], k};
+    philox4x64_10(full, q->key, o4);
+  };
+  IonOut io;
+  moving_target_ionization(p, channel, m1_ev, e_ev, mu, m_ion_ev, w, blk, &cx, &io);
+  out[0] = io.e1; out[1] = io.mu1; out[2] = io.e2; out[3] = io.mu2;
+  out[4] = io.eion; out[5] = io.muion; out[6] = io.ei;
 }
 
 void orc_charge_exchange(const orc_problem* p, double m1_ev, double e_ev, double mu,

@@ -67,8 +67,8 @@ typedef struct {
   const double* sigma_m2;      /* [n_channels][n_energy] */
   double ioniz_eps_ev;
   /* per channel: 0 target at rest, 1 moving target (gas drift along +z plus a
-     Maxwell-Boltzmann draw at the gas temperature; elastic channels only);
-     NULL: every target at rest */
+     Maxwell-Boltzmann draw at the gas temperature; elastic and ionization
+     channels); NULL: every target at rest */
   const int32_t* target;
   double gas_drift_mps;        /* drift velocity of the gas along +z */
   /* scattering-angle distributions of elastic channels (Sec. 3.3 Elastic):
@@ -152,6 +152,17 @@ void orc_elastic_moving_target(const orc_problem* p, double m1_ev, double e_ev, 
 int orc_run_cycle(const orc_problem* p, const orc_primaries* pr, uint64_t seed,
                   const uint64_t* field_time_in, const uint64_t* field_recomb_in,
                   double field_decays, int mode, int n_threads, orc_tallies* out);
+
+/* One ionization with a moving target (Sec. 3.3 Ionization) of channel
+ * `channel`, impactor of rest energy m1_ev, kinetic energy e_ev and pitch
+ * cosine mu, ion of rest energy m_ion_ev: w[2], w[3] share the energy and set
+ * the azimuth; target velocities come from the blocks (ctr[0], ctr[1], ctr[2],
+ * k) under key (redraw r: k from 128 r).  out: impactor energy and pitch
+ * cosine, ejected electron energy and pitch cosine, ion energy and pitch
+ * cosine, impact energy E_i (all eV). */
+void orc_ionization_moving_target(const orc_problem* p, int channel, double m1_ev, double e_ev,
+                                  double mu, double m_ion_ev, const uint64_t w[4],
+                                  const uint64_t ctr[3], const uint64_t key[2], double out[7]);
 
 /* One charge exchange (Sec. 3.3 Charge exchange) of an impactor of rest
  * energy m1_ev, kinetic energy e_ev and pitch cosine mu; the target velocity
