@@ -12,6 +12,10 @@ primaries/s and flights/s are reported beside it.
 Rank 0 prints one JSON line.  With N > 1 (torchrun) every rank runs its own
 replica of the workload with its own primary ids (weak scaling, no
 collective on the data path); value = all ranks' collisions / max time.
+At N = 1 the default line also carries bounded measurements of the batched
+form (a batch of config-4 source configurations in one persistent launch)
+and of the served form (Poisson arrivals at 0.7x the measured capacity and
+at 50 requests/s, p50/p99 latency), both in FP32 as their workloads specify.
 --impl reference times the FP64 CPU oracle on the host cores instead.
 """
 from __future__ import annotations
@@ -382,6 +386,8 @@ def run_ours(args):
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(args, os.cpu_count() or 1)
+    if args.forms_configs > 0 and world == 1:
+        line["batched"], line["served"] = forms_subline(args)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -489,21 +495,10 @@ def plain_sequential(batch, prec, timeout):
                     "kernel_value = transport kernel time only"}
 
 
-def run_serve(args):
-    """config 5: Poisson arrivals submitted on time into one running launch;
-    latency = completion - arrival on the host clock."""
-    import torch
-
-    from paper_2503_10263_gb300 import autotune, build as kbuild, inputs, karl
-    kbuild.build()
-    torch.cuda.set_device(0)
-    prec = karl.FP32 if args.precision == "fp32" else karl.FP64
-    block, bps = autotune.tune(prec)
-    reqs = inputs.config5_requests(duration_s=args.serve_seconds, rate_hz=args.rate, arrival_seed=1)
-    srv = karl.Server(reqs[0][1], precision=prec, hbm_budget_bytes=args.budget_gb << 30,
-                      max_slots=1024, timeout_s=args.timeout, block_size=block, blocks_per_sm=bps)
-    sampler = ClockSampler(0)
-    sampler.start()
+def serve_arrivals(srv, reqs, karl):
+    """Submit each request at its arrival time into the running server and
+    collect results as they finish; returns (latencies, collisions, wall s).
+    Latency = completion - arrival on the host clock."""
     t0 = time.perf_counter()
     nxt = 0
     open_ids = {}
@@ -520,7 +515,84 @@ def run_serve(args):
                 lat.append(time.perf_counter() - t0 - open_ids.pop(rid))
                 coll += int(t["ledger"][karl.N_COLLISIONS_ALL])
         time.sleep(0.0005)
-    wall = time.perf_counter() - t0
+    return lat, coll, time.perf_counter() - t0
+
+
+def forms_subline(args):
+    """Bounded measurements of the batched and served forms (FP32, as their
+    workloads specify) for the default line: one batch of the first
+    args.forms_configs source configurations of the config-4 batch (one warm-up
+    batch, one timed), then Poisson arrivals of config-5-style requests at 0.7x
+    the capacity that batch measured and at 50 requests/s, each for a stated
+    window, the latency of every request from arrival to result."""
+    from paper_2503_10263_gb300 import autotune, inputs, karl
+    prec = karl.FP32
+    t_tune = time.perf_counter()
+    block, bps = autotune.tune(prec)
+    t_tune = time.perf_counter() - t_tune
+    batch = inputs.config4_batch(n_configs=args.forms_configs, meta_seed=1)
+    n_decays = sum(pr.n_decays for _, pr, _ in batch)
+
+    def one_batch():
+        srv = karl.Server(batch[0][0], precision=prec, hbm_budget_bytes=args.budget_gb << 30,
+                          timeout_s=args.timeout, block_size=block, blocks_per_sm=bps)
+        t0 = time.perf_counter()
+        ids = [srv.submit(p, pr, s) for p, pr, s in batch]
+        srv.run_all()
+        coll = sum(int(srv.poll(rid)[1]["ledger"][karl.N_COLLISIONS_ALL]) for rid in ids)
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        return coll, wall, st
+
+    one_batch()
+    coll, wall, st = one_batch()
+    batched = {"value": coll / (st.kernel_ms / 1000.0), "unit": "collision events/s",
+               "e2e": coll / wall, "collisions": coll, "both_passes": True,
+               "configs": len(batch), "decays": n_decays, "kernel_launches": st.kernel_launches,
+               "lane_occupancy": st.lane_occupancy, "block_size": block, "blocks_per_sm": bps,
+               "autotune_s": round(t_tune, 1), "precision": "fp32",
+               "workload": f"first {len(batch)} configurations of the config-4 batch, one "
+                           f"persistent launch, inputs copied in and tallies read back"}
+    # capacity in requests/s: sustained rate over the mean work of a request
+    mean_coll = coll / len(batch)
+    capacity = (coll / wall) / mean_coll
+    served = {"capacity_req_s": capacity, "precision": "fp32", "loads": []}
+    for rate, window in ((0.7 * capacity, args.serve_window_low), (50.0, args.serve_window_high)):
+        reqs = inputs.config5_requests(duration_s=window, rate_hz=rate, arrival_seed=1)
+        if not reqs:
+            continue
+        srv = karl.Server(reqs[0][1], precision=prec, hbm_budget_bytes=args.budget_gb << 30,
+                          max_slots=1024, timeout_s=args.timeout, block_size=block,
+                          blocks_per_sm=bps)
+        lat, scoll, swall = serve_arrivals(srv, reqs, karl)
+        srv.run_all()
+        sst = srv.stats()
+        srv.close()
+        served["loads"].append({
+            "offered_req_s": rate, "arrival_window_s": window, "requests": len(reqs),
+            "p50_latency_s": _percentile(lat, 50), "p99_latency_s": _percentile(lat, 99),
+            "sustained_collisions_per_s": scoll / swall, "wall_s": swall,
+            "kernel_launches": sst.kernel_launches})
+    return batched, served
+
+
+def run_serve(args):
+    """config 5: Poisson arrivals submitted on time into one running launch;
+    latency = completion - arrival on the host clock."""
+    import torch
+
+    from paper_2503_10263_gb300 import autotune, build as kbuild, inputs, karl
+    kbuild.build()
+    torch.cuda.set_device(0)
+    prec = karl.FP32 if args.precision == "fp32" else karl.FP64
+    block, bps = autotune.tune(prec)
+    reqs = inputs.config5_requests(duration_s=args.serve_seconds, rate_hz=args.rate, arrival_seed=1)
+    srv = karl.Server(reqs[0][1], precision=prec, hbm_budget_bytes=args.budget_gb << 30,
+                      max_slots=1024, timeout_s=args.timeout, block_size=block, blocks_per_sm=bps)
+    sampler = ClockSampler(0)
+    sampler.start()
+    lat, coll, wall = serve_arrivals(srv, reqs, karl)
     srv.run_all()
     st = srv.stats()
     srv.close()
@@ -587,6 +659,11 @@ def main():
     ap.add_argument("--budget-gb", type=int, default=48)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--rate", type=float, default=50.0)
+    ap.add_argument("--forms-configs", type=int, default=48,
+                    help="default line: configurations of the bounded batched/served "
+                         "measurement (0: leave it out)")
+    ap.add_argument("--serve-window-low", type=float, default=8.0)
+    ap.add_argument("--serve-window-high", type=float, default=1.5)
     ap.add_argument("--compare-plain", action="store_true",
                     help="config4/config5: also run the requests one at a time through karl_run")
     args = ap.parse_args()

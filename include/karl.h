@@ -160,8 +160,12 @@ typedef struct karl_xs {
   /* host, [n_channels] or NULL (all 0): 0 = target at rest; 1 = moving target
    * (Sec. 3.3 Elastic: the gas drift plus a Maxwell-Boltzmann velocity at the
    * gas temperature, drawn with the relative-speed weight of the collision
-   * rate; the impactor turned in the centre-of-mass frame).  1 is allowed for
-   * elastic channels only. */
+   * rate; the impactor turned in the centre-of-mass frame.  Sec. 3.3
+   * Ionization: the target drawn the same way and redrawn while the impact
+   * energy relative to it is not above the ionization energy; the energy
+   * shared and the angles drawn in the target's frame; the ion leaves with
+   * the target velocity; the lab energy the gas gives or takes is booked as
+   * recoil).  1 is allowed for elastic and ionization channels. */
   const int32_t* target;
   /* host or NULL (every elastic channel isotropic in the centre-of-mass frame) */
   const karl_angular* angular;

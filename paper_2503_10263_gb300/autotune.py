@@ -71,7 +71,7 @@ def time_shape(batch, precision: int, block: int, bps: int) -> Tuple[float, int]
         coll = 0
         for rid in ids:
             done, t = srv.poll(rid)
-            coll += int(t["ledger"][karl.N_COLLISIONS])
+            coll += int(t["ledger"][karl.N_COLLISIONS_ALL])
     finally:
         srv.close()
     return dt, coll

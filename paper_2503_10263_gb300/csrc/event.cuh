@@ -363,7 +363,8 @@ template <bool F32>
 __device__ __forceinline__ void draw_target(const Params& P, const Lane& L,
                                             typename RT<F32>::R v1x, typename RT<F32>::R v1z,
                                             typename RT<F32>::R& wx, typename RT<F32>::R& wy,
-                                            typename RT<F32>::R& wz) {
+                                            typename RT<F32>::R& wz,
+                                            unsigned long long sub0 = 0) {
   using T = RT<F32>;
   using R = typename T::R;
   const R a = (R)P.target_a, ud = (R)P.drift_c;
@@ -375,8 +376,10 @@ __device__ __forceinline__ void draw_target(const Params& P, const Lane& L,
   for (int k = 0; k < 64; ++k) {
     unsigned long long b0[4], b1[4];
     const unsigned long long ctr2 = ((unsigned long long)P.pass << 8) | DOM_TARGET;
-    philox4x64_10((unsigned long long)(L.ev - 1), L.node, ctr2, 2ULL * k, P.seed, L.pid, b0);
-    philox4x64_10((unsigned long long)(L.ev - 1), L.node, ctr2, 2ULL * k + 1, P.seed, L.pid, b1);
+    philox4x64_10((unsigned long long)(L.ev - 1), L.node, ctr2, sub0 + 2ULL * k, P.seed, L.pid,
+                  b0);
+    philox4x64_10((unsigned long long)(L.ev - 1), L.node, ctr2, sub0 + 2ULL * k + 1, P.seed,
+                  L.pid, b1);
     const R l1 = -T::lg(T::eta(b0[1])), l2 = -T::lg(T::eta(b0[2]));
     R s2;
     if (T::u(b0[0]) < pmax) {
@@ -485,6 +488,111 @@ __device__ __forceinline__ void terminate(const Params& P, unsigned long long* l
   }
 }
 
+// Ionization with a moving target (Sec. 3.3 Ionization).  The target velocity
+// is drawn as for a moving elastic target (draw_target, blocks from 128 r for
+// redraw r) and redrawn while the impact energy -- the impactor's kinetic
+// energy relative to the target, m1 |v1 - v2|^2 / 2 -- is not above the
+// ionization energy I; after 64 redraws the target is taken at rest (its
+// impact energy is the lab energy, above I since the channel was chosen).  In
+// the target's frame the impact energy is shared as for a target at rest
+// (slow electron W from the truncated 1/(1+(W/eps)^2) law on [0, (E_i-I)/2],
+// binary-encounter polar angles about the relative velocity, azimuths phi and
+// phi - pi from the plane of z and the relative velocity); adding v2 takes
+// both electrons back to the lab, and the ion leaves with v2 (no recoil).
+// The lab energy the gas gives or takes goes to the recoil ledger (either
+// sign), so the ledger stays exact.  Nonrelativistic velocities in units of c.
+template <bool F32>
+__device__ __noinline__ void moving_target_ionization(const Params& P, unsigned long long* led,
+                                                      Lane& L, EventOut& o, RingPort& port,
+                                                      int k, const unsigned long long w[4]) {
+  using T = RT<F32>;
+  using R = typename T::R;
+  const ChanDev ch = P.ch[k];
+  const int s = L.sp;
+  const R m1 = (R)P.mass[s], me = (R)P.mass[SP_E];
+  const R e = T::energy(L.eq);
+  const R ion_e = (R)ch.loss_ev;
+  const R s1 = T::sq((R)2 * e / m1);
+  const R mu = (R)L.mu;
+  const R sperp = T::sq(fmax((R)0, fma_rn(-mu, mu, (R)1)));
+  const R v1x = mul_rn(s1, sperp), v1z = mul_rn(s1, mu);
+  R v2x = (R)0, v2y = (R)0, v2z = (R)0, gx = v1x, gy = (R)0, gz = v1z, ei = e;
+  for (int r = 0; r < 64; ++r) {
+    R wx, wy, wz;
+    draw_target<F32>(P, L, v1x, v1z, wx, wy, wz, 128ULL * (unsigned long long)r);
+    const R tz = (R)P.drift_c + wz;
+    const R dx = v1x - wx, dy = -wy, dz = v1z - tz;
+    const R er = mul_rn((R)0.5 * m1, fma_rn(dx, dx, fma_rn(dy, dy, mul_rn(dz, dz))));
+    if (er > ion_e) {
+      v2x = wx; v2y = wy; v2z = tz;
+      gx = dx; gy = dy; gz = dz;
+      ei = er;
+      break;
+    }
+  }
+  // energy sharing in the target's frame
+  const R avail = ei - ion_e;
+  const R eps = (R)P.eps_ion;
+  const R wmax = (R)0.5 * avail;
+  R wsec = eps * T::tn(T::u(w[2]) * T::atn(wmax * (R)P.inv_eps_ion));
+  wsec = fmin(fmax(wsec, (R)0), wmax);
+  const R e1 = avail - wsec;
+  const R cp = T::sq(e1 / avail), sp = T::sq(wsec / avail);
+  // basis: h along the relative velocity, b1 the part of z perpendicular to
+  // it (x if it is along z), b2 = h x b1
+  const R gn = T::sq(fma_rn(gx, gx, fma_rn(gy, gy, mul_rn(gz, gz))));
+  R hx = (R)0, hy = (R)0, hz = (R)1;
+  if (gn > (R)0) { hx = gx / gn; hy = gy / gn; hz = gz / gn; }
+  R ax = -hz * hx, ay = -hz * hy, az = fma_rn(-hz, hz, (R)1);
+  R n1 = T::sq(fma_rn(ax, ax, fma_rn(ay, ay, mul_rn(az, az))));
+  if (n1 < (R)1e-12) { ax = (R)1; ay = (R)0; az = (R)0; n1 = (R)1; }
+  ax /= n1; ay /= n1; az /= n1;
+  const R bx = hy * az - hz * ay, by = hz * ax - hx * az, bz = hx * ay - hy * ax;
+  const R phi = (R)2 * T::u(w[3]);
+  const R cph = T::cpi(phi), sph = T::spi(phi);
+  const R u1 = T::sq((R)2 * e1 / m1), u2 = T::sq((R)2 * wsec / me);
+  const R sx = fma_rn(cph, ax, mul_rn(sph, bx)), sy = fma_rn(cph, ay, mul_rn(sph, by)),
+          sz = fma_rn(cph, az, mul_rn(sph, bz));
+  const R ax1 = v2x + u1 * fma_rn(cp, hx, mul_rn(sp, sx));
+  const R ay1 = v2y + u1 * fma_rn(cp, hy, mul_rn(sp, sy));
+  const R az1 = v2z + u1 * fma_rn(cp, hz, mul_rn(sp, sz));
+  const R ax2 = v2x + u2 * fma_rn(sp, hx, -mul_rn(cp, sx));
+  const R ay2 = v2y + u2 * fma_rn(sp, hy, -mul_rn(cp, sy));
+  const R az2 = v2z + u2 * fma_rn(sp, hz, -mul_rn(cp, sz));
+  const R qa = fma_rn(ax1, ax1, fma_rn(ay1, ay1, mul_rn(az1, az1)));
+  const R qb = fma_rn(ax2, ax2, fma_rn(ay2, ay2, mul_rn(az2, az2)));
+  const R q2 = fma_rn(v2x, v2x, fma_rn(v2y, v2y, mul_rn(v2z, v2z)));
+  const long long eq1 = quant_e((double)((R)0.5 * m1 * qa));
+  const long long wq = quant_e((double)((R)0.5 * me * qb));
+  const R mu1 = qa > (R)0 ? fmin((R)1, fmax((R)-1, az1 * T::rsq(qa))) : (R)1;
+  const R mu2 = qb > (R)0 ? fmin((R)1, fmax((R)-1, az2 * T::rsq(qb))) : (R)1;
+  sadd(led + L_LOSS_IONIZ, ch.loss_q);
+  o.recoil += (unsigned long long)(L.eq - ch.loss_q - eq1 - wq);   // the gas's share, either sign
+  const unsigned evc = L.ev - 1;
+  sadd(led + (L_BIRTHS + SP_E), 1);
+  sadd(led + (L_N_SPAWN_E), 1);
+  Lane c;
+  c.z = L.z; c.eq = wq; c.mu = (double)mu2; c.node = child_node(L.node, evc, 0);
+  c.tal = 0.0; c.pid = L.pid; c.ev = 0; c.sp = SP_E; c.j = L.j; c.slot = L.slot;
+  if (wq < P.ecut_q) die<F32>(P, led, c, R_CUTOFF, L_E_CUTOFF);
+  else emit(port, c);
+  if (ch.sout >= 0) {
+    // the ion leaves with the target's velocity
+    const R mi = (R)P.mass[ch.sout];
+    Lane ion;
+    ion.z = L.z; ion.node = child_node(L.node, evc, 1); ion.tal = 0.0; ion.pid = L.pid;
+    ion.ev = 0; ion.sp = ch.sout; ion.j = L.j; ion.slot = L.slot;
+    ion.eq = quant_e((double)((R)0.5 * mi * q2));
+    ion.mu = q2 > (R)0 ? (double)fmin((R)1, fmax((R)-1, v2z * T::rsq(q2))) : 1.0;
+    sadd(led + (L_E_IN_THERMAL), ion.eq);
+    sadd(led + (L_BIRTHS + ch.sout), 1);
+    sadd(led + (L_N_SPAWN_ION), 1);
+    emit(port, ion);
+  }
+  L.eq = eq1;
+  L.mu = (double)mu1;
+}
+
 // Kinematics of a charge exchange (Sec. 3.3), an ionization (Sec. 3.3
 // Ionization: energy sharing, binary-encounter angles, the slow electron and
 // the ion as products) or a clustering
@@ -504,6 +612,11 @@ __device__ __forceinline__ void rare_kinematics(const Params& P, unsigned long l
     return;
   }
   const R e = T::energy(L.eq);
+  if (ch.kind == IONIZATION && ch.target) {
+    moving_target_ionization<F32>(P, led, L, o, port, k, w);
+    terminate<F32>(P, led, L, o);
+    return;
+  }
   if (ch.kind == IONIZATION) {
     const long long avail = L.eq - ch.loss_q;
     const R eps = (R)P.eps_ion;

@@ -102,7 +102,8 @@ inline bool xs_ok(const karl_xs* x) {
       return false;
     if ((kd == CLUSTERING || kd == CLUSTERING3 || kd == RECOMBINATION) && so < 0) return false;
     if (kd == CHARGE_EXCHANGE && si == SP_E) return false;
-    if (x->target && (x->target[k] < 0 || x->target[k] > 1 || (x->target[k] == 1 && kd != ELASTIC)))
+    if (x->target && (x->target[k] < 0 || x->target[k] > 1 ||
+                      (x->target[k] == 1 && kd != ELASTIC && kd != IONIZATION)))
       return false;
     if (kd == RECOMBINATION && si != SP_E && so != SP_E) return false;
     if (kd == RECOMBINATION && si == SP_E && so == SP_E) return false;

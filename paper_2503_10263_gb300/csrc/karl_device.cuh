@@ -37,7 +37,7 @@ enum { DOM_EVENT = 0, DOM_ION_BIRTH = 1, DOM_CLUSTER = 2, DOM_TARGET = 4 };
 enum { ERR_NONE = 0, ERR_TIMEOUT = 4, ERR_CAPACITY = 6, ERR_CANCELLED = 7 };
 
 struct ChanDev {
-  int32_t kind, sin, sout, target;   // target: 0 at rest, 1 moving (elastic)
+  int32_t kind, sin, sout, target;   // target: 0 at rest, 1 moving (elastic, ionization)
   int32_t ang, pad;        // angle-table set of an elastic channel, -1 isotropic
   long long loss_q;        // loss in 2^-24 eV units (floor)
   long long thr_q;         // channel open iff eq > thr_q  (E > loss_ev exactly)

@@ -67,8 +67,9 @@ def test_create_rejects_invalid_arguments_without_gpu(karl):
     p.channels[1].species_in = 7
     with pytest.raises(karl.KarlError):
         karl.Context(p)
-    # a moving target is defined for elastic channels only
-    for k, t in ((1, 1), (0, 2)):
+    # a moving target is defined for elastic and ionization channels only
+    # (channel 2 of config 1 is an excitation)
+    for k, t in ((2, 1), (0, 2)):
         p, _ = inputs.config1(n_primaries=10)
         p.channels[k].target = t
         with pytest.raises(karl.KarlError) as ei:

@@ -201,8 +201,9 @@ def test_full_fp32_two_pass_against_fp64_oracle(karl, full, oracle_pass1):
     to an end, and its time in a segment goes as 1/|mu|, whose mean diverges
     (logarithmically, cut off only by the resolution of mu), so its pass-1 time
     tally and field are dominated by a few ions of small |mu|.  The few
-    histories FP32 rounding changes move such ions; that tally is compared by
-    its typical bin, and its L2 distance is reported."""
+    histories FP32 rounding changes move such ions (at full size one of them
+    can outweigh a bin's other ions); T3+ is compared by its face crossings,
+    and the L2 distance of its time tally is reported."""
     prob, prims = full
     ctx = karl.Context(prob)
     kb = 64
@@ -231,13 +232,13 @@ def test_full_fp32_two_pass_against_fp64_oracle(karl, full, oracle_pass1):
         print(f"PARITY FP32 pass 1 field {name}: rel L2 {l2[sp]:.3e} "
               f"(noise floor of independent runs {floor[sp]:.3e})")
     ok &= l2[0] < 1e-3 and l2[1] < 1e-3
-    # T3+: the typical bin agrees
-    t3g = gb["time_fx"].sum(0)[2, 1:-1, :].ravel()
-    t3o = np.asarray(o1["time_fx"], np.float64)[2, 1:-1, :].ravel()
-    on = t3o > 0
-    med = float(np.median(np.abs(t3g[on] - t3o[on]) / t3o[on])) if on.any() else 0.0
-    print(f"PARITY FP32 pass 1 T3+ time: median relative bin difference {med:.3e}")
-    ok &= med < 1e-2
+    # T3+: its face crossings (counts, finite variance) bin by bin; its time
+    # tally is reported above, not held to a bound (heavy tail)
+    for key in ("cross_pos", "cross_neg"):
+        z, dof = parity.batches_vs_total(gb[key][:, 2:3], np.asarray(o1[key])[2:3], min_mean=1.0)
+        s = parity.deviation_summary(z, dof)
+        _report("FP32 pass 1 (T3+)", key, s)
+        ok &= s["beyond_3"] <= s["allowed_beyond_3"] and s["chi2_p"] > 1e-3
 
     sub_n = prims.n // 16
     kb2 = 32
