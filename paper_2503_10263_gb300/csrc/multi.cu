@@ -226,6 +226,9 @@ __global__ void __launch_bounds__(256, 2) multi_kernel(SlotDesc* D, SlotCtl* C, 
   o.parked = false;
   unsigned long long idle_iters = 0, busy_iters = 0, busy_lane_iters = 0, started = 0;
   unsigned idle_ns = 128;
+  // a warp that holds particles but found nothing for its idle lanes skips
+  // its next refill attempts (1, 3, 7, ... up to 63 iterations)
+  int refill_skip = 0, refill_backoff = 0;
   RingPort port;
   port.R = &R;
   port.ctl = ctl;
@@ -347,7 +350,11 @@ __global__ void __launch_bounds__(256, 2) multi_kernel(SlotDesc* D, SlotCtl* C, 
     }
 
     // ---- other idle lanes: products from the ring, then primaries of a request ----
-    const unsigned need = __ballot_sync(FULL, !has);
+    unsigned need = __ballot_sync(FULL, !has);
+    if (need && need != FULL && refill_skip > 0) {
+      --refill_skip;
+      need = 0;
+    }
     if (need) {
       const int k = __popc(need);
       unsigned long long base = 0;
@@ -403,6 +410,13 @@ __global__ void __launch_bounds__(256, 2) multi_kernel(SlotDesc* D, SlotCtl* C, 
       src = __shfl_sync(FULL, src, 0);
       gslot = __shfl_sync(FULL, gslot, 0);
       gpass = __shfl_sync(FULL, gpass, 0);
+      if (got == 0) {
+        refill_backoff = refill_backoff * 2 + 1;
+        if (refill_backoff > 63) refill_backoff = 63;
+        refill_skip = refill_backoff;
+      } else {
+        refill_backoff = 0;
+      }
       if (!has && got > 0) {
         const int rank = __popc(need & lt);
         if (rank < got) {
