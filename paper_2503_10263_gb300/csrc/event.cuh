@@ -805,10 +805,10 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
   const R lx = le * (R)P.inv_h;
   int ti = (int)floor(lx);
   R tf;
-  bool inside = true;
-  if (ti < 0) { ti = 0; tf = (R)0; inside = false; }
-  else if (ti > P.n_energy - 2) { ti = P.n_energy - 2; tf = (R)1; inside = false; }
-  else { tf = lx - (R)ti; }
+  int row;                                 // row of the cumulative tables (-1: none)
+  if (ti < 0) { ti = 0; tf = (R)0; row = P.n_energy - 1; }          // below the first node
+  else if (ti > P.n_energy - 2) { ti = P.n_energy - 2; tf = (R)1; row = -1; }
+  else { tf = lx - (R)ti; row = ti; }
 
   // 1/v and 1/(|mu| v) (relativistic: v = c sqrt(x (2 + x)) / (1 + x), x = E / m c^2);
   // both from one reciprocal root, and the time quantum folded into the second
@@ -835,8 +835,22 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
   const int nsc = P.nsc[s];
   const int ncg = P.ncg[s];
   // cumulative tables: the species' gas channels lead its selection order and
-  // no channel threshold falls inside this node interval
-  const bool fast = ncg > 0 && inside && !P.mixed[s * P.n_energy + ti];
+  // at most one channel threshold falls inside this node interval
+  const int mark = ncg >= 0 && row >= 0 ? P.mixed[s * P.n_energy + row] : CUM_PER_CHANNEL;
+  const bool fast = mark != CUM_PER_CHANNEL;
+  // a channel that opens inside the interval: above its threshold, its own
+  // interpolated cross section joins the sums from its slot xslot on
+  int xslot = MAXSPCH;
+  R xval = (R)0;
+  if (fast && mark != CUM_PLAIN) {
+    const int kx = P.sc[s][mark];
+    if (L.eq > P.ch[kx].thr_q) {
+      R a0, sl;
+      T::tab2(P, kx, ti, a0, sl);
+      xval = fma_rn(tf, sl, a0);
+      xslot = mark;
+    }
+  }
   R gas = (R)0;
   int nrec = 0;
   double rc0 = 0.0, rc1 = 0.0;
@@ -845,9 +859,11 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
   const double* rrate0 = P.nseg;
   const double* rrate1 = P.nseg;
   if (fast) {
-    R a0, sl;
-    T::cum2(P, s, ti, ncg - 1, a0, sl);
-    gas = fma_rn(tf, sl, a0);
+    if (ncg > 0) {
+      R a0, sl;
+      T::cum2(P, s, row, ncg - 1, a0, sl);
+      gas = fma_rn(tf, sl, a0) + xval;
+    }
     for (int c = ncg; c < nsc; ++c) {       // field channels follow the gas channels
       const int k = P.sc[s][c];
       const R cv = channel_coef<F32>(P, k, s, L.eq, ti, tf, inv_v);
@@ -1060,8 +1076,8 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
     if (gas_part) {
       for (int c = 0; c < ncg; ++c) {
         R a0, sl;
-        T::cum2(P, s, ti, c, a0, sl);
-        if (tg < fma_rn(tf, sl, a0)) { chs = c; break; }
+        T::cum2(P, s, row, c, a0, sl);
+        if (tg < fma_rn(tf, sl, a0) + (c >= xslot ? xval : (R)0)) { chs = c; break; }
       }
     }
     if (chs < 0)                        // rounding at the top end

@@ -238,19 +238,21 @@ inline void angular_tables(const karl_xs* x, std::vector<double>& pdf, std::vect
 }
 
 // Gas channels (rate sigma n(z)) that lead species s's selection order and
-// are followed by field channels only: their count, or 0 when a gas channel
-// follows a field channel (then every flight takes the per-channel path).
+// are followed by field channels only: their count (0 with field channels
+// only), or -1 when a gas channel follows a field channel (then every flight
+// takes the per-channel path).
 inline int leading_gas_channels(const ModelInfo& m, int s) {
   int n = 0;
   bool field_seen = false;
   for (int k = 0; k < m.nch; ++k) {
     if (m.sin[k] != s) continue;
     if (field_kind(m.kind[k])) field_seen = true;
-    else if (field_seen) return 0;
+    else if (field_seen) return -1;
     else ++n;
   }
   return n;
 }
+
 
 // Everything of Params that does not depend on device buffers.
 inline void fill_params(Params& P, const karl_geometry& g, const ModelInfo& m, int pass,
@@ -298,7 +300,7 @@ inline void fill_params(Params& P, const karl_geometry& g, const ModelInfo& m, i
     }
     P.nsc[s] = n;
     P.ncg[s] = leading_gas_channels(m, s);
-    P.cum_off[s] = s == 0 ? 0 : P.cum_off[s - 1] + P.ncg[s - 1] * m.n_energy;
+    P.cum_off[s] = s == 0 ? 0 : P.cum_off[s - 1] + std::max(P.ncg[s - 1], 0) * m.n_energy;
     P.mass[s] = g.species_mass_ev[s];
     P.inv_mass[s] = 1.0 / g.species_mass_ev[s];
     P.gam[s] = g.species_mass_ev[s] / g.target_mass_ev;
@@ -327,19 +329,28 @@ inline void fill_params(Params& P, const karl_geometry& g, const ModelInfo& m, i
 // over channels 0..c that are open across the whole interval (E_i above the
 // channel's loss) of the node value and of the difference to the next node:
 // sigma_0 + ... + sigma_c at energy E in the interval is value + t * slope,
-// t the position of ln E in the interval.  Where a channel threshold falls
-// inside an interval (open for part of it) the interval is marked, and
-// flights there take the per-channel path.  Layout: species s from offset
-// sum_{s' < s} ncg(s') * n_energy, then [node][channel] pairs (value, slope);
-// marks [NSP][n_energy] (the last node marked: no interval above it).
+// t the position of ln E in the interval.  An interval inside which exactly
+// one channel opens is marked with that channel's slot (its own term is
+// added above its threshold); one where two or more open is marked for the
+// per-channel path.  The last row (index n_energy - 1, no interval above it)
+// holds energies below the first node: there the tables are clamped to the
+// first node and a channel is open at any energy when its loss is zero,
+// closed when its loss is at or above the first node; a loss between the two
+// sends the species to the per-channel path there.  Layout: species s from
+// offset sum_{s' < s} max(ncg(s'), 0) * n_energy, then [row][channel] pairs
+// (value, slope); marks [NSP][n_energy].
 inline void gas_cum_tables(const karl_xs* x, const ModelInfo& m, std::vector<double>& cum,
                            std::vector<float>& cumf, std::vector<unsigned char>& mixed) {
   const int ne = x->n_energy;
   cum.clear();
-  mixed.assign((size_t)NSP * ne, 1);
+  mixed.assign((size_t)NSP * ne, CUM_PER_CHANNEL);
   for (int s = 0; s < NSP; ++s) {
     const int ng = leading_gas_channels(m, s);
-    if (ng == 0) continue;
+    if (ng < 0) continue;
+    if (ng == 0) {                          // field channels only: nothing to add
+      for (int i = 0; i < ne; ++i) mixed[(size_t)s * ne + i] = CUM_PLAIN;
+      continue;
+    }
     std::vector<int> ks;
     for (int k = 0; k < m.nch && (int)ks.size() < ng; ++k)
       if (m.sin[k] == s) ks.push_back(k);
@@ -348,7 +359,7 @@ inline void gas_cum_tables(const karl_xs* x, const ModelInfo& m, std::vector<dou
     for (int i = 0; i + 1 < ne; ++i) {
       const double ei = m.e_min * std::pow(m.e_max / m.e_min, (double)i / (ne - 1));
       const double ej = m.e_min * std::pow(m.e_max / m.e_min, (double)(i + 1) / (ne - 1));
-      bool mix = false;
+      int n_mix = 0, slot = -1;
       double a = 0.0, b = 0.0;
       for (int c = 0; c < ng; ++c) {
         const int k = ks[c];
@@ -357,7 +368,7 @@ inline void gas_cum_tables(const karl_xs* x, const ModelInfo& m, std::vector<dou
         // (FP32 in the precision form); an interval is 0.5 % of E wide
         const bool open = ei > loss * (1.0 + 1e-5) + 1e-300;
         const bool closed = ej * (1.0 + 1e-5) <= loss;
-        if (!open && !closed) mix = true;
+        if (!open && !closed) { ++n_mix; slot = c; }
         if (open) {
           const double v = x->sigma_m2[(size_t)k * ne + i];
           const double vn = x->sigma_m2[(size_t)k * ne + i + 1];
@@ -367,8 +378,21 @@ inline void gas_cum_tables(const karl_xs* x, const ModelInfo& m, std::vector<dou
         cum[base + ((size_t)i * ng + c) * 2] = a;
         cum[base + ((size_t)i * ng + c) * 2 + 1] = b;
       }
-      mixed[(size_t)s * ne + i] = mix ? 1 : 0;
+      mixed[(size_t)s * ne + i] =
+          n_mix == 0 ? CUM_PLAIN : (n_mix == 1 ? (unsigned char)slot : CUM_PER_CHANNEL);
     }
+    // below the first node (clamped to it)
+    bool uniform = true;
+    double a = 0.0;
+    for (int c = 0; c < ng; ++c) {
+      const int k = ks[c];
+      const double loss = m.loss[k];
+      if (loss > 0.0 && loss < m.e_min) uniform = false;
+      if (loss == 0.0) a += x->sigma_m2[(size_t)k * ne];
+      cum[base + ((size_t)(ne - 1) * ng + c) * 2] = a;
+      cum[base + ((size_t)(ne - 1) * ng + c) * 2 + 1] = 0.0;
+    }
+    mixed[(size_t)s * ne + ne - 1] = uniform ? CUM_PLAIN : CUM_PER_CHANNEL;
   }
   cumf.assign(cum.begin(), cum.end());
 }

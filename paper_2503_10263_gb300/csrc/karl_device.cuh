@@ -26,6 +26,13 @@ __host__ __device__ __forceinline__ bool field_kind(int kind) {
   return kind == RECOMBINATION || kind == CLUSTERING3;
 }
 enum { SP_E = 0 };
+// Marks of the cumulative cross-section tables, per species and node
+// interval: the interval needs nothing more (CUM_PLAIN), one of its gas
+// channels opens inside it (the channel's slot: above the channel's threshold
+// its own interpolated cross section is added to the cumulative sums from its
+// slot on), or the per-channel path (CUM_PER_CHANNEL).
+constexpr unsigned char CUM_PLAIN = 255;
+constexpr unsigned char CUM_PER_CHANNEL = 254;
 enum { R_EXIT0 = 0, R_EXIT1 = 1, R_CUTOFF = 2, R_CAP_COLL = 3, R_CAP_TIME = 4,
        R_RECOMB = 5, R_CLUSTER = 6, R_STALLED = 7 };
 enum { L_E_IN_PRIMARY = 0, L_E_IN_THERMAL = 1, L_E_EXIT0 = 2, L_E_EXIT1 = 3, L_E_CUTOFF = 4,
