@@ -916,6 +916,11 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
   double zc;
   int jc;
   int exit_end = -1;
+  // flights with gas and field channels in gas-column units: the field
+  // channels' share rho = sigma_field / sigma_gas, and the field rate per
+  // unit of gas density at the end segment (for the channel choice)
+  bool gas_units = false;
+  double rho0 = 0.0, rho1 = 0.0, rf_end = 0.0;
   if (still) {
     // no motion along z: collide in place after path tau / rate
     jc = j0;
@@ -971,10 +976,81 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
           zc = up ? dmax_nn(zc, L.z) : dmin_nn(zc, L.z);
         }
       }
+    } else if (gasd > 0.0) {
+      // Gas and field channels, in gas-column units: the column of the whole
+      // rate over sigma_gas is G(k) = C(k) + rho0 F0(k) + rho1 F1(k), and the
+      // flight ends where G reaches G(z0) +- tau |mu| / sigma_gas.  As G >= C,
+      // it ends in the segment where the gas column alone reaches the target
+      // or before it: the integer-compared gas search gives that segment, one
+      // check of G confirms it (the fields add little rate), and otherwise the
+      // search goes on before it with G.
+      gas_units = true;
+      const double ig = 1.0 / gasd;
+      rho0 = mul_rn(rc0, ig);
+      rho1 = mul_rn(rc1, ig);
+      auto gcol = [&](int k) -> double {
+        double g = P.colgas[k];
+        if (nrec > 0) g = fma_rn(rho0, rcol0[k], g);
+        if (nrec > 1) g = fma_rn(rho1, rcol1[k], g);
+        return g;
+      };
+      auto frate = [&](int j) -> double {   // field rate per unit of gas density
+        double r = 0.0;
+        if (nrec > 0) r = mul_rn(rho0, rrate0[j]);
+        if (nrec > 1) r = fma_rn(rho1, rrate1[j], r);
+        return r;
+      };
+      const double c0 = fma_rn(P.nseg[j0] + frate(j0), L.z - P.faces[j0], gcol(j0));
+      const double D = mul_rn(mul_rn((double)tau, amu), ig);
+      const double tgt = up ? c0 + D : c0 - D;
+      ex = up ? !(tgt < gcol(nz)) : !(tgt > 0.0);
+      if (!ex) {
+        const long long tb = dbits(tgt);
+        int lo = up ? j0 : 0, hi = up ? nz : j0 + 1;
+        if (P.nq > 0) {
+          const float q = (float)tgt * P.nq_over_colmax_f;
+          if (q >= 0.0f && q < (float)P.nq) {
+            const int qi = (int)q;
+            const int a = max(lo, P.ginv[qi] - 1), bb = min(hi, P.ginv[qi + 1] + 1);
+            if (a < bb && dbits(P.colgas[a]) <= tb && tb < dbits(P.colgas[bb])) {
+              lo = a;
+              hi = bb;
+            }
+          }
+        }
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (dbits(P.colgas[mid]) <= tb) lo = mid; else hi = mid;
+        }
+        jc = lo;
+        double gj = gcol(jc);
+        if (!(gj <= tgt)) {
+          int l2 = up ? j0 : 0, h2 = jc;
+          while (h2 - l2 > 1) {
+            const int mid = (l2 + h2) >> 1;
+            if (gcol(mid) <= tgt) l2 = mid; else h2 = mid;
+          }
+          jc = l2;
+          gj = gcol(jc);
+        }
+        const double fj = P.faces[jc];
+        const double gap = tgt - gj;
+        const double nj = P.nseg[jc];
+        rf_end = frate(jc);
+        double off;
+        const double eps = mul_rn(rf_end, P.invn[jc]);
+        if (nj > 0.0 && fabs(eps) < 1e-6)
+          // 1 / (n + rf) = (1/n) (1 - eps + eps^2) to eps^3, eps = rf / n
+          off = mul_rn(gap, mul_rn(P.invn[jc], fma_rn(-eps, 1.0 - eps, 1.0)));
+        else
+          off = gap / (nj + rf_end);
+        zc = fj + off;
+        zc = dmin_nn(dmax_nn(zc, fj), P.faces[jc + 1]);
+        zc = up ? dmax_nn(zc, L.z) : dmin_nn(zc, L.z);
+      }
     } else {
-      // With field channels the flight inverts the column of the whole rate,
-      // bracketed where the gas column alone would end (the fields add little
-      // rate); the bracket is checked against the exact columns.
+      // Field channels only (no gas rate): the flight inverts the column of
+      // the fields, bracketed from the gas column where there is one.
       const double g0 = fma_rn(segrate(j0), L.z - P.faces[j0], colsum(j0));
       const double delta = mul_rn((double)tau, amu);
       const double target = up ? g0 + delta : g0 - delta;
@@ -1051,6 +1127,28 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
     bool gas_part = true;
     if (nrec == 0) {
       tg = mul_rn(T::u(w[1]), gas);
+    } else if (gas_units) {
+      // rates per unit of gas density: gas channels n_jc (then in sigma
+      // units for the cumulative tables), field channel i rho_i f_i(jc)
+      const double nj = P.nseg[jc];
+      const double tr = mul_rn(u01d(w[1]), nj + rf_end);
+      if (tr < nj) {
+        tg = (R)mul_rn(mul_rn(tr, P.invn[jc]), gasd);
+      } else {
+        gas_part = false;
+        tg = (R)0;
+        double cum = nj;
+        int last = -1;
+        for (int c = ncg; c < nsc; ++c) {
+          const int kk = P.sc[s][c];
+          const double rk = mul_rn(c == ncg ? rho0 : rho1, P.frate[kk][jc]);
+          if (!(rk > 0.0)) continue;
+          last = c;
+          cum += rk;
+          if (tr < cum) { chs = c; break; }
+        }
+        if (chs < 0) chs = last;
+      }
     } else {
       const double nj = P.nseg[jc];
       const double target = mul_rn(u01d(w[1]), segrate(jc));
