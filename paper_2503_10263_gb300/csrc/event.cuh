@@ -7,6 +7,8 @@
 // range adds, the terminator of Sec. 3.2, a channel chosen with probability
 // sigma_i n_i / sum_j sigma_j n_j, and its kinematics (Sec. 3.3).
 #pragma once
+#include <cooperative_groups.h>
+
 #include "karl_device.cuh"
 
 namespace karl {
@@ -225,7 +227,7 @@ struct EventOut {
 // list).  The queue spills to the shared ring when full, and once the
 // primaries are used up, so idle warps elsewhere can share the last work.
 constexpr int WQ = 32;
-constexpr int WARPS = 8;                  // 256-thread blocks
+constexpr int WARPS = 8;                  // multi-request kernel: blocks of up to 256 threads
 struct WarpQueue {
   Lane s[WQ];
   int top;
@@ -261,20 +263,36 @@ struct RingPort {
   unsigned long long* slot_live;
 };
 
+// Lanes that emit a product together take their queue slots, and past the
+// queue's end their ring cells, with one atomic per warp: the first lane of
+// the group reserves a range and every lane writes at its rank in the group.
 __device__ __forceinline__ void emit(RingPort& port, const Lane& p) {
+  namespace cg = cooperative_groups;
   if (port.slot_live) atomicAdd(port.slot_live, 1ULL);
-  if (port.local) {
-    const int i = atomicAdd(&port.q->top, 1);
+  bool placed = false;
+  if (port.local) {                        // uniform over the warp
+    cg::coalesced_group g = cg::coalesced_threads();
+    const int n = (int)g.size();
+    int base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(&port.q->top, n);
+    base = g.shfl(base, 0);
+    const int i = base + (int)g.thread_rank();
     if (i < WQ) {
       port.q->s[i] = p;
-      if (!port.slot_live)
-        atomicAdd((unsigned long long*)&port.ctl->active, 1ULL);   // held by this warp
-      return;
+      placed = true;
     }
+    const int kept = base >= WQ ? 0 : min(WQ - base, n);
+    if (!port.slot_live && g.thread_rank() == 0 && kept > 0)
+      atomicAdd((unsigned long long*)&port.ctl->active, (unsigned long long)kept);  // held by this warp
   }
-  unsigned long long pos = atomicAdd(&port.ctl->tail, 1ULL);
-  ring_put(*port.R, port.ctl, pos, p, port.deadline);
-  port.spilled += 1;
+  if (!placed) {
+    cg::coalesced_group g = cg::coalesced_threads();
+    unsigned long long base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(&port.ctl->tail, (unsigned long long)g.size());
+    base = g.shfl(base, 0);
+    ring_put(*port.R, port.ctl, base + g.thread_rank(), p, port.deadline);
+    port.spilled += 1;
+  }
 }
 
 template <bool F32>

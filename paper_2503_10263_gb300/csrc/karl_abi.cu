@@ -443,11 +443,12 @@ size_t n_cross(const karl_ctx* c) { return (size_t)NSP * (c->nz + 1); }
 size_t n_recomb(const karl_ctx* c) { return (size_t)NSP * c->nz; }
 
 // Default threads per block of the transport kernel (resident blocks per SM:
-// the occupancy maximum).  Measured on the config-2 step (5e6 decays): the
-// FP64 form is fastest with 256-thread blocks, 2 per SM; the FP32 form with
-// 128-thread blocks, 4 per SM (3.3e9 against 2.7e9 collisions/s; with
-// 256-thread blocks its pass 1 kept only 79 % of its lanes busy).
-int default_block(bool) { return 256; }
+// the occupancy maximum): one block of 512 threads per SM.  With at most 128
+// registers a thread that keeps as many warps resident as two blocks of 256,
+// and the single block's share of shared memory also holds the pass-2 field
+// tables.  Measured on the config-2 step (5e6 decays) against 256 x 2:
+// FP64 2.881e9 against 2.872e9 collisions/s, FP32 5.44e9 against 5.26e9.
+int default_block(bool) { return 512; }
 
 karl_status ensure_ring(karl_ctx* ctx, unsigned long long cap) {
   if (ctx->ring_cap >= cap) return KARL_OK;

@@ -433,23 +433,33 @@ constexpr int QUEUE_BYTES_PER_WARP = (int)(sizeof(WarpQueue) + sizeof(RareBuf));
 static_assert(sizeof(WarpQueue) % 8 == 0 && sizeof(RareBuf) % 8 == 0, "queue alignment");
 
 
+// Shared memory a block may give its staged tables: 76 KB for blocks of up
+// to 256 threads (two to an SM), and what a block of more threads, alone on
+// its SM, leaves beside its queues (then the pass-2 field tables fit too).
+constexpr int SMEM_PER_SM = 227 * 1024;
+constexpr int STATIC_SMEM_MARGIN = 4 * 1024;
+int dyn_table_budget(int block) {
+  if (block <= 256) return DYN_MAX_BYTES;
+  return SMEM_PER_SM - STATIC_SMEM_MARGIN - (block / 32) * QUEUE_BYTES_PER_WARP;
+}
+
 // Doubles of dynamic shared memory the staged tables of P need (0: too big,
 // read them from global memory).
-int transport_dyn_doubles(const Params& P) {
+int transport_dyn_doubles(const Params& P, int block) {
   int need = (4 * P.nz + 2) + (P.nq + 1 + 1) / 2 + 1;
   for (int k = 0; k < P.nch; ++k)
     if (P.fcol[k]) need += 2 * P.nz + 1;
-  return need * 8 <= DYN_MAX_BYTES ? need : 0;
+  return need * 8 <= dyn_table_budget(block) ? need : 0;
 }
 
 size_t transport_dyn_bytes(const Params& P, int block) {
-  return (size_t)transport_dyn_doubles(P) * 8 + (size_t)(block / 32) * QUEUE_BYTES_PER_WARP;
+  return (size_t)transport_dyn_doubles(P, block) * 8 + (size_t)(block / 32) * QUEUE_BYTES_PER_WARP;
 }
 
 cudaError_t launch_transport(bool f32, const Params& P, const Ring& R, Control* ctl,
                              const volatile int* cancel, unsigned long long timeout_ns, int grid,
                              int block, cudaStream_t st) {
-  const int dd = transport_dyn_doubles(P);
+  const int dd = transport_dyn_doubles(P, block);
   const size_t bytes = transport_dyn_bytes(P, block);
   if (f32)
     transport_kernel<true><<<grid, block, bytes, st>>>(P, R, ctl, cancel, timeout_ns, dd);
@@ -461,10 +471,10 @@ cudaError_t launch_transport(bool f32, const Params& P, const Ring& R, Control* 
 cudaError_t transport_setup() {
   cudaError_t e = cudaFuncSetAttribute(transport_kernel<true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       DYN_MAX_BYTES + 16 * QUEUE_BYTES_PER_WARP);
+                                       SMEM_PER_SM - STATIC_SMEM_MARGIN);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(transport_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              DYN_MAX_BYTES + 16 * QUEUE_BYTES_PER_WARP);
+                              SMEM_PER_SM - STATIC_SMEM_MARGIN);
 }
 
 cudaError_t transport_occupancy(bool f32, const Params& P, int block, int* blocks_per_sm) {

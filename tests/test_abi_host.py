@@ -148,3 +148,10 @@ def test_shipped_problems_pass_host_validation():
         with pytest.raises(k.KarlError) as ei:
             k.Context(p)
         assert ei.value.status == k.ECUDA, p.name
+
+
+def test_autotune_candidates_fit_the_multi_request_kernel():
+    """The server accepts blocks of 32..256 threads (multiples of 32)."""
+    from paper_2503_10263_gb300 import autotune
+    for block, bps in autotune.CANDIDATES:
+        assert 32 <= block <= 256 and block % 32 == 0 and bps >= 1

@@ -268,3 +268,15 @@ def test_served_request_matches_oracle(karl):
     # matched streams: the channel counts of the last pass agree closely
     cg, co = t["chan_count"].astype(np.float64), o["chan_count"].astype(np.float64)
     assert np.all(np.abs(cg - co) <= 4 * np.sqrt(np.maximum(cg + co, 1.0)) + 0.002 * co)
+
+
+def test_autotune_times_every_candidate_shape(karl, tmp_path, monkeypatch):
+    """The autotuner launches the multi-request kernel with each candidate
+    shape and caches a valid one."""
+    from paper_2503_10263_gb300 import autotune
+    monkeypatch.setenv("KARL_CACHE_DIR", str(tmp_path))
+    batch = inputs.config4_batch(n_configs=3, meta_seed=5, np_lo=200, np_hi=400)
+    for prec in (karl.FP64, karl.FP32):
+        shape = autotune.tune(prec, force=True, batch=batch)
+        assert shape in autotune.CANDIDATES
+        assert autotune.tune(prec) == shape                  # served from the cache
