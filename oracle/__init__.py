@@ -456,3 +456,97 @@ def ionization_moving_target(prob, channel: int, m1_ev: float, e_ev: float, mu: 
 def marshal_problem(prob):
     """The oracle's C view of a problem, reusable across single-collision calls."""
     return _Marshal(prob)
+
+
+# ---- orbit mode: the Boris mover in a tube (mirrors karl_oracle.h) ----
+OB_BIRTHS, OB_DEATHS = 0, 4
+OB_N_COLLISIONS, OB_N_FLIGHTS, OB_N_STEPS, OB_N_SPAWN_E, OB_N_SPAWN_ION = 36, 37, 38, 39, 40
+OB_LEDGER_LEN = 48
+ORBIT_REASONS = ("exit0", "exit1", "wall", "cutoff", "cap_coll", "cap_time", "cluster", "stalled")
+OE_IN_PRIMARY, OE_IN_THERMAL, OE_EXIT0, OE_EXIT1, OE_WALL, OE_CUTOFF, OE_CAP, OE_CLUSTER, \
+    OE_LOSS_IONIZ, OE_LOSS_EXCIT, OE_RECOIL, OE_STALLED, OE_FIELD_WORK = range(13)
+OE_LEN = 16
+
+
+class _Orbit(C.Structure):
+    _fields_ = [("b_t", C.c_double), ("tube_radius_m", C.c_double), ("n_rbins", C.c_int32),
+                ("e_z_vm", C.POINTER(C.c_double)), ("e_r_vm2", C.c_double),
+                ("dt_s", C.c_double * N_SPECIES), ("max_steps", C.c_uint64)]
+
+
+class _OrbitPrims(C.Structure):
+    _fields_ = [("n", C.c_int64), ("x_m", C.POINTER(C.c_double)), ("y_m", C.POINTER(C.c_double)),
+                ("z_m", C.POINTER(C.c_double)), ("e_ev", C.POINTER(C.c_double)),
+                ("mu", C.POINTER(C.c_double)), ("phi", C.POINTER(C.c_double)),
+                ("species", C.POINTER(C.c_uint8)), ("pid_offset", C.c_int64)]
+
+
+class _OrbitTallies(C.Structure):
+    _fields_ = [(k, C.POINTER(C.c_uint64)) for k in
+                ("spectrum", "time_z", "time_r", "cross_pos", "cross_neg", "rcross_out",
+                 "rcross_in", "wall")] + [
+        ("ledger", C.POINTER(C.c_int64)), ("energy", C.POINTER(C.c_double)),
+        ("chan_count", C.POINTER(C.c_uint64)), ("per_primary", C.POINTER(C.c_uint64)),
+        ("end_state", C.POINTER(C.c_double))]
+
+
+def empty_orbit_tallies(prob, orbit, n_primaries: int) -> Dict[str, np.ndarray]:
+    nz, nr = prob.n_zbins, orbit.n_rbins
+    return {
+        "spectrum": np.zeros((2, N_SPECIES, prob.n_spec_bins + 1), np.uint64),
+        "time_z": np.zeros((N_SPECIES, nz), np.uint64),
+        "time_r": np.zeros((N_SPECIES, nr), np.uint64),
+        "cross_pos": np.zeros((N_SPECIES, nz + 1), np.uint64),
+        "cross_neg": np.zeros((N_SPECIES, nz + 1), np.uint64),
+        "rcross_out": np.zeros((N_SPECIES, nr + 1), np.uint64),
+        "rcross_in": np.zeros((N_SPECIES, nr + 1), np.uint64),
+        "wall": np.zeros((N_SPECIES, nz), np.uint64),
+        "ledger": np.zeros(OB_LEDGER_LEN, np.int64),
+        "energy": np.zeros(OE_LEN, np.float64),
+        "chan_count": np.zeros(max(prob.n_channels, 1), np.uint64),
+        "per_primary": np.zeros(max(n_primaries, 1), np.uint64),
+        "end_state": np.zeros((max(n_primaries, 1), 8), np.float64),
+    }
+
+
+def orbit_run(prob, orbit, prims, seed: int = 1, n_threads: int = 1) -> Dict[str, np.ndarray]:
+    """Full-orbit run (Boris mover, Sec. 3.1) of `prims` (an
+    ``inputs.OrbitPrimaries``) in the tube described by `orbit` (an
+    ``inputs.Orbit``)."""
+    lib = _load()
+    if not hasattr(lib, "_orbit_ready"):
+        lib.orc_orbit_run.argtypes = [C.POINTER(_Problem), C.POINTER(_Orbit),
+                                      C.POINTER(_OrbitPrims), C.c_uint64, C.c_int,
+                                      C.POINTER(_OrbitTallies)]
+        lib.orc_orbit_run.restype = C.c_int
+        lib._orbit_ready = True
+    m = _Marshal(prob)
+    ez = None if orbit.e_z_vm is None else np.ascontiguousarray(orbit.e_z_vm, np.float64)
+    o = _Orbit()
+    o.b_t, o.tube_radius_m, o.n_rbins = orbit.b_t, orbit.tube_radius_m, orbit.n_rbins
+    o.e_z_vm = _ptr(ez, C.c_double) if ez is not None else None
+    o.e_r_vm2 = orbit.e_r_vm2
+    for i in range(N_SPECIES):
+        o.dt_s[i] = float(orbit.dt_s[i])
+    o.max_steps = int(orbit.max_steps)
+    arrs = [np.ascontiguousarray(getattr(prims, k), np.float64)
+            for k in ("x_m", "y_m", "z_m", "e_ev", "mu", "phi")]
+    sp = np.ascontiguousarray(prims.species, np.uint8)
+    ps = _OrbitPrims(prims.n, *[_ptr(a, C.c_double) for a in arrs], _ptr(sp, C.c_uint8),
+                     int(prims.pid_offset))
+    t = empty_orbit_tallies(prob, orbit, prims.n)
+    ts = _OrbitTallies()
+    for k in ("spectrum", "time_z", "time_r", "cross_pos", "cross_neg", "rcross_out",
+              "rcross_in", "wall", "chan_count", "per_primary"):
+        setattr(ts, k, _ptr(t[k], C.c_uint64))
+    ts.ledger = _ptr(t["ledger"], C.c_int64)
+    ts.energy = _ptr(t["energy"], C.c_double)
+    ts.end_state = _ptr(t["end_state"], C.c_double)
+    rc = lib.orc_orbit_run(C.byref(m.s), C.byref(o), C.byref(ps), C.c_uint64(seed), n_threads,
+                           C.byref(ts))
+    if rc != 0:
+        raise RuntimeError(f"oracle orbit run failed: {rc}")
+    t["per_primary"] = t["per_primary"][:prims.n]
+    t["end_state"] = t["end_state"][:prims.n]
+    t["chan_count"] = t["chan_count"][:prob.n_channels]
+    return t

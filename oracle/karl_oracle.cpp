@@ -971,6 +971,501 @@ int do_pass(const orc_problem* p, const orc_primaries* pr, uint64_t seed, int pa
   return 0;
 }
 
+
+/* ======================= orbit mode: Boris mover (Sec. 3.1) =======================
+ *
+ * Readings: the relativistic form of the Boris push (the paper's equations with
+ * the proper velocity u = gamma v, gamma of the half-accelerated velocity in
+ * the rotation); the initial velocity is taken as the half-step velocity; the
+ * time of a step goes to the z segment and radial bin of the step's midpoint;
+ * the optical depth of a step is the total rate of the midpoint's segment
+ * times the step's path length; with no electric field the kinetic energy is
+ * a constant of the motion and the cross sections are evaluated once per
+ * flight, otherwise at the energy of each step; a step that reaches the
+ * drawn optical depth, a z end, the wall or the lifetime cap is shortened to
+ * the fraction of its displacement where that happens (first of them; on a
+ * tie: wall, z end, lifetime, collision). */
+const double CHARGE_E[ORC_N_SPECIES] = {-1.0, 1.0, 1.0, 1.0};   /* units of e */
+enum { OEV_NONE = 0, OEV_WALL = 1, OEV_EXIT = 2, OEV_CAP = 3, OEV_COLL = 4 };
+
+struct OParticle {
+  double x[3];       /* position (m) */
+  double u[3];       /* proper velocity gamma v (m/s) */
+  uint64_t node;     /* lineage id */
+  double t_alive;
+  uint32_t ev;       /* collisions so far */
+  int species;
+};
+
+/* kinetic energy (eV) of proper velocity u: (gamma - 1) m with
+ * gamma - 1 = x / (gamma + 1), x = u^2 / c^2 (no cancellation when slow) */
+double kinetic_u(const double u[3], double m_ev) {
+  double x = (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) / (C_LIGHT * C_LIGHT);
+  double g = std::sqrt(1.0 + x);
+  return m_ev * x / (g + 1.0);
+}
+
+/* proper speed gamma v (m/s) of kinetic energy e: c sqrt(y (2 + y)), y = e / m */
+double proper_speed(double e_ev, double m_ev) {
+  double y = e_ev / m_ev;
+  return C_LIGHT * std::sqrt(y * (2.0 + y));
+}
+
+/* The direction at polar angle acos(ct) and azimuth (cp, sp) = (cos, sin)
+ * about the unit vector d, in the frame e1 = (z - d_z d) / s (the unit vector
+ * normal to d towards +z), e2 = d x e1 = (d_y, -d_x, 0) / s, s = sqrt(d_x^2 +
+ * d_y^2); for s below 1e-12, e1 = x, e2 = d x x.  Its z component is then
+ * d_z ct + s st cp, the guiding-centre update of the pitch cosine. */
+void turn(const double d[3], double ct, double cp, double sp, double out[3]) {
+  const double s = std::sqrt(d[0] * d[0] + d[1] * d[1]);
+  double e1[3], e2[3];
+  if (s > 1e-12) {
+    e1[0] = -d[2] * d[0] / s; e1[1] = -d[2] * d[1] / s; e1[2] = s;
+    e2[0] = d[1] / s; e2[1] = -d[0] / s; e2[2] = 0.0;
+  } else {
+    e1[0] = 1.0; e1[1] = 0.0; e1[2] = 0.0;
+    e2[0] = 0.0; e2[1] = d[2]; e2[2] = -d[1];
+  }
+  const double st = std::sqrt(std::fmax(0.0, 1.0 - ct * ct));
+  for (int i = 0; i < 3; ++i) out[i] = ct * d[i] + st * (cp * e1[i] + sp * e2[i]);
+}
+
+struct OrbitRun {
+  const orc_problem* p;
+  const orc_orbit* o;
+  uint64_t seed;
+  double dz;
+  double r_scale;    /* n_rbins / R */
+  bool fields;       /* some electric field is present */
+  uint64_t max_steps;
+};
+
+struct OTally {
+  std::vector<uint64_t> spectrum, time_z, time_r, cross_pos, cross_neg, rcross_out, rcross_in,
+      wall, chan_count;
+  std::vector<int64_t> ledger;
+  std::vector<double> energy;
+  void init(const orc_problem* p, const orc_orbit* o) {
+    int nz = p->n_zbins, nr = o->n_rbins;
+    spectrum.assign((size_t)2 * ORC_N_SPECIES * (p->n_spec_bins + 1), 0);
+    time_z.assign((size_t)ORC_N_SPECIES * nz, 0);
+    time_r.assign((size_t)ORC_N_SPECIES * nr, 0);
+    cross_pos.assign((size_t)ORC_N_SPECIES * (nz + 1), 0);
+    cross_neg.assign((size_t)ORC_N_SPECIES * (nz + 1), 0);
+    rcross_out.assign((size_t)ORC_N_SPECIES * (nr + 1), 0);
+    rcross_in.assign((size_t)ORC_N_SPECIES * (nr + 1), 0);
+    wall.assign((size_t)ORC_N_SPECIES * nz, 0);
+    chan_count.assign((size_t)p->n_channels, 0);
+    ledger.assign(ORC_OB_LEDGER_LEN, 0);
+    energy.assign(ORC_OE_LEN, 0.0);
+  }
+};
+
+struct OWorker {
+  const OrbitRun* R;
+  OTally T;
+  uint64_t pid;
+  uint64_t tree_collisions;
+
+  void block(uint32_t ev, uint64_t node, int domain, uint64_t sub, uint64_t w[4]) {
+    uint64_t ctr[4] = {(uint64_t)ev, node, (1ULL << 8) | (uint64_t)domain, sub};
+    uint64_t key[2] = {R->seed, pid};
+    philox4x64_10(ctr, key, w);
+  }
+  int seg(double z) const {
+    int j = (int)std::floor(z / R->dz);
+    if (j < 0) j = 0;
+    if (j > R->p->n_zbins - 1) j = R->p->n_zbins - 1;
+    return j;
+  }
+  int rbin(double x, double y) const {
+    int b = (int)std::floor(std::sqrt(x * x + y * y) * R->r_scale);
+    if (b < 0) b = 0;
+    if (b > R->o->n_rbins - 1) b = R->o->n_rbins - 1;
+    return b;
+  }
+  void die(const OParticle& P, int reason, int eslot, double e) {
+    T.ledger[ORC_OB_DEATHS + P.species * ORC_N_REASONS + reason] += 1;
+    T.energy[eslot] += e;
+  }
+  /* per-flight coefficients sigma_k(E) of the species' channels */
+  void coefficients(int s, double e, double* c) const {
+    const orc_problem* p = R->p;
+    for (int k = 0; k < p->n_channels; ++k)
+      c[k] = p->species_in[k] == s ? sigma_at(p, k, e) : 0.0;
+  }
+  double rate_k(int k, const double* c, int j) const {
+    const double n = R->p->n_seg_m3[j];
+    return R->p->kind[k] == CLUSTERING3 ? c[k] * n * n : c[k] * n;
+  }
+  double rate(const double* c, int j) const {
+    double r = 0.0;
+    for (int k = 0; k < R->p->n_channels; ++k) r += rate_k(k, c, j);
+    return r;
+  }
+  /* rate per unit path of a step in segment j: n_j times the two-body cross
+     sections plus n_j^2 times the three-body coefficients */
+  double step_rate(const double* c, int j) const {
+    double s1 = 0.0, s3 = 0.0;
+    for (int k = 0; k < R->p->n_channels; ++k) {
+      if (R->p->kind[k] == CLUSTERING3) s3 += c[k];
+      else s1 += c[k];
+    }
+    const double n = R->p->n_seg_m3[j];
+    return s1 * n + s3 * (n * n);
+  }
+  /* thermal product: Gamma(3/2, kT) energy and an isotropic direction */
+  void thermal3(uint32_t ev, uint64_t node, int domain, double* e, double d[3]) {
+    uint64_t w[4], w2[4];
+    block(ev, node, domain, 0, w);
+    block(ev, node, domain, 1, w2);
+    double kt = KB_EV * R->p->gas_temperature_k;
+    double c = std::cos(TWO_PI * u01(w[2]));
+    *e = kt * (-std::log(eta01(w[0])) - std::log(eta01(w[1])) * c * c);
+    double mu = 2.0 * u01(w[3]);
+    mu -= 1.0;
+    double st = std::sqrt(std::fmax(0.0, 1.0 - mu * mu));
+    double ph = TWO_PI * u01(w2[0]);
+    d[0] = st * std::cos(ph);
+    d[1] = st * std::sin(ph);
+    d[2] = mu;
+  }
+  void set_u(OParticle& P, double e, const double d[3]) {
+    double ps = proper_speed(e, R->p->species_mass_ev[P.species]);
+    for (int i = 0; i < 3; ++i) P.u[i] = ps * d[i];
+  }
+  /* time of a run of steps in one (segment, radial bin) cell */
+  void flush(int s, int cj, int cr, uint64_t n_full, double f_last, double dt) {
+    if (cj < 0) return;
+    double t = (double)n_full * dt + f_last * dt;
+    uint64_t q = (uint64_t)(t * Q_TIME + 0.5);
+    T.time_z[(size_t)s * R->p->n_zbins + cj] += q;
+    T.time_r[(size_t)s * R->o->n_rbins + cr] += q;
+  }
+  /* crossings of z faces and of the radial bin boundaries by a straight step
+   * from a to b (z ends and the wall are counted by the caller) */
+  void crossings(int s, const double a[3], const double b[3]) {
+    const int nz = R->p->n_zbins, nr = R->o->n_rbins;
+    int ja = seg(a[2]), jb = seg(b[2]);
+    for (int k = ja + 1; k <= jb; ++k) T.cross_pos[(size_t)s * (nz + 1) + k] += 1;
+    for (int k = jb + 1; k <= ja; ++k) T.cross_neg[(size_t)s * (nz + 1) + k] += 1;
+    int ra = rbin(a[0], a[1]), rb = rbin(b[0], b[1]);
+    for (int k = ra + 1; k <= rb; ++k) T.rcross_out[(size_t)s * (nr + 1) + k] += 1;
+    for (int k = rb + 1; k <= ra; ++k) T.rcross_in[(size_t)s * (nr + 1) + k] += 1;
+  }
+  void spectrum_add(int end, int s, double e) {
+    const orc_problem* p = R->p;
+    double x = std::floor(e / p->spec_bin_ev);
+    int64_t bin = x < 0.0 ? 0 : (x > (double)p->n_spec_bins ? p->n_spec_bins : (int64_t)x);
+    T.spectrum[((size_t)end * ORC_N_SPECIES + s) * (p->n_spec_bins + 1) + bin] += 1;
+  }
+  void write_end(double* es, const OParticle& P) {
+    if (!es || P.node != 0) return;
+    double e = kinetic_u(P.u, R->p->species_mass_ev[P.species]);
+    double v[8] = {P.x[0], P.x[1], P.x[2], e, P.u[0], P.u[1], P.u[2], P.t_alive};
+    for (int i = 0; i < 8; ++i) es[i] = v[i];
+  }
+
+  /* Follow one particle to its end; products go on the stack. */
+  void transport(OParticle P, std::vector<OParticle>& stack, double* es) {
+    const orc_problem* p = R->p;
+    const orc_orbit* o = R->o;
+    const int nz = p->n_zbins, nr = o->n_rbins;
+    const double L = p->length_m, R2 = o->tube_radius_m * o->tube_radius_m;
+    std::vector<double> coef((size_t)p->n_channels + 1, 0.0);
+    for (;;) {
+      const int s = P.species;
+      const double m = p->species_mass_ev[s];
+      const double e0 = kinetic_u(P.u, m);
+      if (!(e0 > 0.0)) { write_end(es, P); die(P, ORC_OR_STALLED, ORC_OE_STALLED, e0); return; }
+      uint64_t w[4];
+      block(P.ev, P.node, DOM_EVENT, 0, w);
+      const double tau = -std::log(eta01(w[0]));
+      T.ledger[ORC_OB_N_FLIGHTS] += 1;
+      coefficients(s, e0, coef.data());
+      const double dt = o->dt_s[s];
+      const double h = 0.5 * (CHARGE_E[s] * C_LIGHT * C_LIGHT / m) * dt;   /* q dt / 2m */
+      double acc = 0.0;
+      int cj = -1, cr = -1;          /* cell of the current run of steps */
+      uint64_t cn = 0;
+      int event = OEV_NONE, end = -1;
+      double e_step = e0;
+      for (uint64_t step = 0;; ++step) {
+        if (step >= R->max_steps) {
+          flush(s, cj, cr, cn, 0.0, dt);
+          T.energy[ORC_OE_FIELD_WORK] += kinetic_u(P.u, m) - e0;
+          write_end(es, P);
+          die(P, ORC_OR_STALLED, ORC_OE_STALLED, kinetic_u(P.u, m));
+          return;
+        }
+        T.ledger[ORC_OB_N_STEPS] += 1;
+        const double* x = P.x;
+        /* Boris push: half electric kick, magnetic rotation, half kick */
+        const double ef[3] = {o->e_r_vm2 * x[0], o->e_r_vm2 * x[1],
+                              o->e_z_vm ? o->e_z_vm[seg(x[2])] : 0.0};
+        double um[3];
+        for (int i = 0; i < 3; ++i) um[i] = P.u[i] + h * ef[i];
+        const double gm = std::sqrt(1.0 + (um[0] * um[0] + um[1] * um[1] + um[2] * um[2]) /
+                                              (C_LIGHT * C_LIGHT));
+        const double t = h * o->b_t / gm;
+        const double sf = 2.0 * t / (1.0 + t * t);
+        const double upx = um[0] + um[1] * t, upy = um[1] - um[0] * t;
+        double un[3] = {um[0] + upy * sf, um[1] - upx * sf, um[2]};
+        for (int i = 0; i < 3; ++i) un[i] += h * ef[i];
+        const double gn = std::sqrt(1.0 + (un[0] * un[0] + un[1] * un[1] + un[2] * un[2]) /
+                                              (C_LIGHT * C_LIGHT));
+        const double sc = dt / gn;
+        const double d[3] = {un[0] * sc, un[1] * sc, un[2] * sc};
+        const double ds = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        if (R->fields) {
+          e_step = kinetic_u(un, m);
+          coefficients(s, e_step, coef.data());
+        }
+        const int jm = seg(x[2] + 0.5 * d[2]);
+        const double dtau = step_rate(coef.data(), jm) * ds;
+        /* the first of wall, z end, lifetime cap and collision within the step */
+        double fb = 1.0;
+        event = OEV_NONE;
+        const double xn = x[0] + d[0], yn = x[1] + d[1], zn = x[2] + d[2];
+        if (xn * xn + yn * yn > R2) {
+          /* |p + f q|^2 = R^2 for the transverse parts p, q: the root in (0, 1] */
+          const double a = d[0] * d[0] + d[1] * d[1];
+          const double b = x[0] * d[0] + x[1] * d[1];
+          const double c = x[0] * x[0] + x[1] * x[1] - R2;
+          const double disc = std::sqrt(std::fmax(0.0, b * b - a * c));
+          double f = b > 0.0 ? -c / (b + disc) : (disc - b) / a;
+          f = std::fmin(1.0, std::fmax(0.0, f));
+          if (f <= fb) { fb = f; event = OEV_WALL; }
+        }
+        if (zn < 0.0 || zn > L) {
+          double f = zn < 0.0 ? -x[2] / d[2] : (L - x[2]) / d[2];
+          f = std::fmin(1.0, std::fmax(0.0, f));
+          if (event == OEV_NONE ? f <= fb : f < fb) { fb = f; event = OEV_EXIT; end = zn < 0.0 ? 0 : 1; }
+        }
+        if (P.t_alive + dt >= p->max_lifetime_s) {
+          double f = std::fmin(1.0, std::fmax(0.0, (p->max_lifetime_s - P.t_alive) / dt));
+          if (event == OEV_NONE ? f <= fb : f < fb) { fb = f; event = OEV_CAP; }
+        }
+        if (dtau > 0.0 && acc + dtau >= tau) {
+          double f = std::fmin(1.0, std::fmax(0.0, (tau - acc) / dtau));
+          if (event == OEV_NONE ? f <= fb : f < fb) { fb = f; event = OEV_COLL; }
+        }
+        if (event == OEV_NONE) {
+          const int mj = jm, mr = rbin(x[0] + 0.5 * d[0], x[1] + 0.5 * d[1]);
+          if (mj == cj && mr == cr) {
+            cn += 1;
+          } else {
+            flush(s, cj, cr, cn, 0.0, dt);
+            cj = mj; cr = mr; cn = 1;
+          }
+          const double b[3] = {xn, yn, zn};
+          crossings(s, x, b);
+          P.x[0] = xn; P.x[1] = yn; P.x[2] = zn;
+          P.t_alive += dt;
+          acc += dtau;
+          for (int i = 0; i < 3; ++i) P.u[i] = un[i];
+          continue;
+        }
+        /* the shortened last step */
+        const double dp[3] = {fb * d[0], fb * d[1], fb * d[2]};
+        const int mj = seg(x[2] + 0.5 * dp[2]), mr = rbin(x[0] + 0.5 * dp[0], x[1] + 0.5 * dp[1]);
+        if (mj == cj && mr == cr) {
+          flush(s, cj, cr, cn, fb, dt);
+        } else {
+          flush(s, cj, cr, cn, 0.0, dt);
+          flush(s, mj, mr, 0, fb, dt);
+        }
+        double b[3] = {x[0] + dp[0], x[1] + dp[1], x[2] + dp[2]};
+        if (event == OEV_EXIT) b[2] = end == 0 ? 0.0 : L;
+        crossings(s, x, b);
+        P.x[0] = b[0]; P.x[1] = b[1]; P.x[2] = b[2];
+        P.t_alive = event == OEV_CAP ? p->max_lifetime_s : P.t_alive + fb * dt;
+        for (int i = 0; i < 3; ++i) P.u[i] = un[i];
+        break;
+      }
+      const double e1 = kinetic_u(P.u, m);
+      T.energy[ORC_OE_FIELD_WORK] += e1 - e0;
+      if (event == OEV_WALL) {
+        T.wall[(size_t)s * nz + seg(P.x[2])] += 1;
+        const int ra = rbin(P.x[0], P.x[1]);
+        for (int k = ra + 1; k <= nr; ++k) T.rcross_out[(size_t)s * (nr + 1) + k] += 1;
+        write_end(es, P);
+        die(P, ORC_OR_WALL, ORC_OE_WALL, e1);
+        return;
+      }
+      if (event == OEV_EXIT) {
+        if (end == 1) T.cross_pos[(size_t)s * (nz + 1) + nz] += 1;
+        else T.cross_neg[(size_t)s * (nz + 1) + 0] += 1;
+        spectrum_add(end, s, e1);
+        write_end(es, P);
+        die(P, end == 0 ? ORC_OR_EXIT0 : ORC_OR_EXIT1, end == 0 ? ORC_OE_EXIT0 : ORC_OE_EXIT1, e1);
+        return;
+      }
+      if (event == OEV_CAP) {
+        write_end(es, P);
+        die(P, ORC_OR_CAP_TIME, ORC_OE_CAP, e1);
+        return;
+      }
+      /* ---- collision: channel with probability rate_k / rate_tot ---- */
+      const int j = seg(P.x[2]);
+      P.ev += 1;
+      tree_collisions += 1;
+      T.ledger[ORC_OB_N_COLLISIONS] += 1;
+      double rtot = rate(coef.data(), j);
+      double target = u01(w[1]) * rtot;
+      int ch = -1, last = -1;
+      double cum = 0.0;
+      for (int k = 0; k < p->n_channels; ++k) {
+        double rk = rate_k(k, coef.data(), j);
+        if (!(rk > 0.0)) continue;
+        last = k;
+        cum += rk;
+        if (target < cum) { ch = k; break; }
+      }
+      if (ch < 0) ch = last;
+      T.chan_count[ch] += 1;
+      const int kind = p->kind[ch];
+      const double ec = e1;
+      const double pu = std::sqrt(P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
+      const double dir[3] = {P.u[0] / pu, P.u[1] / pu, P.u[2] / pu};
+      const double ph = TWO_PI * u01(w[3]);
+      const double cph = std::cos(ph), sph = std::sin(ph);
+      const uint32_t ev_coll = P.ev - 1;
+      double enew = ec;
+      if (kind == ELASTIC) {
+        double g = m / p->target_mass_ev;
+        double cchi = sample_angle(p, ch, ec, u01(w[2]));
+        double a = 1.0 + 2.0 * g * cchi + g * g;
+        double ct = (cchi + g) / std::sqrt(a);
+        double loss = ec * 2.0 * g * (1.0 - cchi) / ((1.0 + g) * (1.0 + g));
+        enew = ec - loss;
+        T.energy[ORC_OE_RECOIL] += loss;
+        double nd[3];
+        turn(dir, ct, cph, sph, nd);
+        set_u(P, enew, nd);
+      } else if (kind == EXCITATION) {
+        enew = ec - p->loss_ev[ch];
+        T.energy[ORC_OE_LOSS_EXCIT] += p->loss_ev[ch];
+        set_u(P, enew, dir);
+      } else if (kind == IONIZATION) {
+        const double ion_e = p->loss_ev[ch];
+        const double avail = ec - ion_e;
+        const double eps = p->ioniz_eps_ev;
+        double wsec = eps * std::tan(u01(w[2]) * std::atan(0.5 * avail / eps));
+        if (wsec > 0.5 * avail) wsec = 0.5 * avail;
+        if (wsec < 0.0) wsec = 0.0;
+        enew = avail - wsec;
+        T.energy[ORC_OE_LOSS_IONIZ] += ion_e;
+        const double cp = avail > 0.0 ? std::sqrt(enew / avail) : 1.0;
+        const double sp = avail > 0.0 ? std::sqrt(wsec / avail) : 0.0;
+        double nd[3], sd[3];
+        turn(dir, cp, cph, sph, nd);
+        turn(dir, sp, -cph, -sph, sd);            /* secondary azimuth = primary azimuth - pi */
+        set_u(P, enew, nd);
+        OParticle S;
+        for (int i = 0; i < 3; ++i) S.x[i] = P.x[i];
+        S.species = SP_E; S.node = child_node(P.node, ev_coll, 0);
+        S.t_alive = 0.0; S.ev = 0;
+        set_u(S, wsec, sd);
+        T.ledger[ORC_OB_BIRTHS + SP_E] += 1;
+        T.ledger[ORC_OB_N_SPAWN_E] += 1;
+        if (wsec < p->e_cut_ev) die(S, ORC_OR_CUTOFF, ORC_OE_CUTOFF, wsec);
+        else stack.push_back(S);
+        const int ion = p->species_out[ch];
+        if (ion >= 0) {
+          OParticle I;
+          for (int i = 0; i < 3; ++i) I.x[i] = P.x[i];
+          I.species = ion; I.node = child_node(P.node, ev_coll, 1);
+          I.t_alive = 0.0; I.ev = 0;
+          double ei, di[3];
+          thermal3(0, I.node, DOM_ION_BIRTH, &ei, di);
+          set_u(I, ei, di);
+          T.energy[ORC_OE_IN_THERMAL] += ei;
+          T.ledger[ORC_OB_BIRTHS + ion] += 1;
+          T.ledger[ORC_OB_N_SPAWN_ION] += 1;
+          stack.push_back(I);
+        }
+      } else {                                   /* clustering: the product replaces the ion */
+        write_end(es, P);
+        die(P, ORC_OR_CLUSTER, ORC_OE_CLUSTER, ec);
+        OParticle C;
+        for (int i = 0; i < 3; ++i) C.x[i] = P.x[i];
+        C.species = p->species_out[ch];
+        C.node = child_node(P.node, ev_coll, 2);
+        C.t_alive = 0.0; C.ev = 0;
+        double ecl, dc[3];
+        thermal3(ev_coll, P.node, DOM_CLUSTER, &ecl, dc);
+        set_u(C, ecl, dc);
+        T.energy[ORC_OE_IN_THERMAL] += ecl;
+        T.ledger[ORC_OB_BIRTHS + C.species] += 1;
+        P = C;
+        continue;
+      }
+      /* ---- terminator (Sec. 3.2) ---- */
+      if (s == SP_E && enew < p->e_cut_ev) {
+        write_end(es, P); die(P, ORC_OR_CUTOFF, ORC_OE_CUTOFF, enew); return;
+      }
+      if (P.ev >= p->max_collisions) {
+        write_end(es, P); die(P, ORC_OR_CAP_COLL, ORC_OE_CAP, enew); return;
+      }
+      if (P.t_alive >= p->max_lifetime_s) {
+        write_end(es, P); die(P, ORC_OR_CAP_TIME, ORC_OE_CAP, enew); return;
+      }
+    }
+  }
+
+  void run_range(const orc_orbit_primaries* pr, int64_t lo, int64_t hi, uint64_t* per_primary,
+                 double* end_state) {
+    const orc_problem* p = R->p;
+    std::vector<OParticle> stack;
+    for (int64_t i = lo; i < hi; ++i) {
+      pid = (uint64_t)(pr->pid_offset + i);
+      tree_collisions = 0;
+      OParticle P;
+      P.x[0] = pr->x_m[i]; P.x[1] = pr->y_m[i]; P.x[2] = pr->z_m[i];
+      P.species = pr->species[i];
+      P.node = 0; P.t_alive = 0.0; P.ev = 0;
+      const double mu = pr->mu[i];
+      const double st = std::sqrt(std::fmax(0.0, 1.0 - mu * mu));
+      const double d[3] = {st * std::cos(pr->phi[i]), st * std::sin(pr->phi[i]), mu};
+      set_u(P, pr->e_ev[i], d);
+      double* es = end_state ? end_state + 8 * i : nullptr;
+      T.energy[ORC_OE_IN_PRIMARY] += pr->e_ev[i];
+      T.ledger[ORC_OB_BIRTHS + P.species] += 1;
+      if (P.species == SP_E && pr->e_ev[i] < p->e_cut_ev) {
+        write_end(es, P);
+        die(P, ORC_OR_CUTOFF, ORC_OE_CUTOFF, pr->e_ev[i]);
+      } else {
+        stack.push_back(P);
+      }
+      while (!stack.empty()) {
+        OParticle Q = stack.back();
+        stack.pop_back();
+        transport(Q, stack, Q.node == 0 ? es : nullptr);
+      }
+      if (per_primary) per_primary[i] += tree_collisions;
+    }
+  }
+};
+
+int check_orbit(const orc_problem* p, const orc_orbit* o, const orc_orbit_primaries* pr) {
+  if (check_problem(p) || !o || !pr || !(o->tube_radius_m > 0.0) || o->n_rbins < 1) return 1;
+  for (int s = 0; s < ORC_N_SPECIES; ++s)
+    if (!(o->dt_s[s] > 0.0)) return 1;
+  for (int k = 0; k < p->n_channels; ++k) {
+    const int kd = p->kind[k];
+    if (kd == RECOMBINATION || kd == CHARGE_EXCHANGE) return 2;
+    if ((kd == ELASTIC || kd == IONIZATION) && p->target && p->target[k] != 0) return 2;
+  }
+  const double R2 = o->tube_radius_m * o->tube_radius_m;
+  for (int64_t i = 0; i < pr->n; ++i) {
+    const double x = pr->x_m[i], y = pr->y_m[i], z = pr->z_m[i];
+    if (!(x * x + y * y < R2) || !(z >= 0.0 && z <= p->length_m) || pr->species[i] >= ORC_N_SPECIES)
+      return 3;
+  }
+  return 0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1160,6 +1655,48 @@ int orc_run(const orc_problem* p, const orc_primaries* pr, uint64_t seed, int n_
         out->current[idx] =
             ((double)out->cross_pos[idx] - (double)out->cross_neg[idx]) / (p->area_m2 * tsim);
       }
+  }
+  return 0;
+}
+
+
+int orc_orbit_run(const orc_problem* p, const orc_orbit* o, const orc_orbit_primaries* pr,
+                  uint64_t seed, int n_threads, orc_orbit_tallies* out) {
+  const int bad = check_orbit(p, o, pr);
+  if (bad) return bad;
+  if (!out) return 1;
+  OrbitRun R;
+  R.p = p; R.o = o; R.seed = seed;
+  R.dz = p->length_m / p->n_zbins;
+  R.r_scale = (double)o->n_rbins / o->tube_radius_m;
+  R.fields = o->e_r_vm2 != 0.0;
+  if (o->e_z_vm)
+    for (int j = 0; j < p->n_zbins; ++j) R.fields = R.fields || o->e_z_vm[j] != 0.0;
+  R.max_steps = o->max_steps ? o->max_steps : (1ULL << 40);
+  if (n_threads < 1) n_threads = 1;
+  if ((int64_t)n_threads > pr->n) n_threads = (int)(pr->n > 0 ? pr->n : 1);
+  std::vector<OWorker> W(n_threads);
+  std::vector<std::thread> th;
+  for (int t = 0; t < n_threads; ++t) {
+    W[t].R = &R;
+    W[t].T.init(p, o);
+    int64_t lo = pr->n * t / n_threads, hi = pr->n * (t + 1) / n_threads;
+    auto job = [&W, t, pr, lo, hi, out] { W[t].run_range(pr, lo, hi, out->per_primary, out->end_state); };
+    if (n_threads == 1) job();
+    else th.emplace_back(job);
+  }
+  for (auto& x : th) x.join();
+  for (int t = 0; t < n_threads; ++t) {
+    const OTally& T = W[t].T;
+    auto add = [](uint64_t* dst, const std::vector<uint64_t>& src) {
+      for (size_t i = 0; i < src.size(); ++i) dst[i] += src[i];
+    };
+    add(out->spectrum, T.spectrum); add(out->time_z, T.time_z); add(out->time_r, T.time_r);
+    add(out->cross_pos, T.cross_pos); add(out->cross_neg, T.cross_neg);
+    add(out->rcross_out, T.rcross_out); add(out->rcross_in, T.rcross_in);
+    add(out->wall, T.wall); add(out->chan_count, T.chan_count);
+    for (int i = 0; i < ORC_OB_LEDGER_LEN; ++i) out->ledger[i] += T.ledger[i];
+    for (int i = 0; i < ORC_OE_LEN; ++i) out->energy[i] += T.energy[i];
   }
   return 0;
 }

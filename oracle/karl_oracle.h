@@ -177,6 +177,81 @@ void orc_charge_exchange(const orc_problem* p, double m1_ev, double e_ev, double
  * e_ev for the uniform number u in [0, 1) (isotropic: 2u - 1). */
 double orc_sample_angle(const orc_problem* p, int channel, double e_ev, double u);
 
+
+/* ---- orbit mode: the Boris mover (Sec. 3.1) in a tube of radius R ----
+ *
+ * Full-orbit transport: position (x, y, z) and proper velocity u = gamma v are
+ * advanced by the relativistic Boris push with the species' time step in a
+ * uniform magnetic field b_t along +z and the electric field
+ * E = (e_r_vm2 x, e_r_vm2 y, e_z_vm[segment of z]).  Flights end where the
+ * optical depth accumulated over the steps reaches -ln(eta), at z = 0 or L,
+ * on the tube wall r = R, or at the lifetime cap; the collision kinematics
+ * are those of the guiding-centre path with the direction turned in three
+ * dimensions.  Channels: elastic and ionization with the target at rest,
+ * excitation, clustering and three-body clustering.  Energies are FP64 (no
+ * quantisation: the electric field changes them continuously). */
+enum {
+  ORC_OB_BIRTHS = 0,            /* [4] */
+  ORC_OB_DEATHS = 4,            /* [4][8], reasons below */
+  ORC_OB_N_COLLISIONS = 36, ORC_OB_N_FLIGHTS = 37, ORC_OB_N_STEPS = 38,
+  ORC_OB_N_SPAWN_E = 39, ORC_OB_N_SPAWN_ION = 40,
+  ORC_OB_LEDGER_LEN = 48
+};
+enum { ORC_OR_EXIT0 = 0, ORC_OR_EXIT1 = 1, ORC_OR_WALL = 2, ORC_OR_CUTOFF = 3,
+       ORC_OR_CAP_COLL = 4, ORC_OR_CAP_TIME = 5, ORC_OR_CLUSTER = 6, ORC_OR_STALLED = 7 };
+/* energy ledger (eV, FP64) */
+enum {
+  ORC_OE_IN_PRIMARY = 0, ORC_OE_IN_THERMAL = 1, ORC_OE_EXIT0 = 2, ORC_OE_EXIT1 = 3,
+  ORC_OE_WALL = 4, ORC_OE_CUTOFF = 5, ORC_OE_CAP = 6, ORC_OE_CLUSTER = 7,
+  ORC_OE_LOSS_IONIZ = 8, ORC_OE_LOSS_EXCIT = 9, ORC_OE_RECOIL = 10, ORC_OE_STALLED = 11,
+  ORC_OE_FIELD_WORK = 12,       /* kinetic energy gained from the electric field in flights */
+  ORC_OE_LEN = 16
+};
+
+typedef struct {
+  double b_t;                   /* uniform magnetic field along +z (T) */
+  double tube_radius_m;         /* wall radius R; particles reaching it end there */
+  int32_t n_rbins;              /* radial bins of width R / n_rbins */
+  const double* e_z_vm;         /* [n_zbins] axial electric field per segment (V/m), NULL: 0 */
+  double e_r_vm2;               /* radial electric field E_r = e_r_vm2 * r (V/m^2) */
+  double dt_s[ORC_N_SPECIES];   /* Boris time step per species (s) */
+  uint64_t max_steps;           /* steps per flight before a particle counts as stalled; 0: 2^40 */
+} orc_orbit;
+
+typedef struct {
+  int64_t n;
+  const double* x_m;
+  const double* y_m;
+  const double* z_m;
+  const double* e_ev;
+  const double* mu;             /* cosine of the angle to +z */
+  const double* phi;            /* azimuth of the transverse velocity (rad) */
+  const uint8_t* species;
+  int64_t pid_offset;
+} orc_orbit_primaries;
+
+typedef struct {
+  uint64_t* spectrum;           /* [2][4][n_spec_bins+1] energies at z = 0 and z = L */
+  uint64_t* time_z;             /* [4][n_zbins] time per z segment, LSB 2^-50 s */
+  uint64_t* time_r;             /* [4][n_rbins] time per radial bin, LSB 2^-50 s */
+  uint64_t* cross_pos;          /* [4][n_zbins+1] crossings of z faces along +z */
+  uint64_t* cross_neg;          /* [4][n_zbins+1] along -z */
+  uint64_t* rcross_out;         /* [4][n_rbins+1] outward crossings of r = k R / n_rbins */
+  uint64_t* rcross_in;          /* [4][n_rbins+1] inward crossings */
+  uint64_t* wall;               /* [4][n_zbins] particles ended on the wall, by z segment */
+  int64_t* ledger;              /* [ORC_OB_LEDGER_LEN] */
+  double* energy;               /* [ORC_OE_LEN] */
+  uint64_t* chan_count;         /* [n_channels] */
+  uint64_t* per_primary;        /* [n] collisions in each primary's tree, may be NULL */
+  double* end_state;            /* [n][8] x y z E ux uy uz t of each primary at its end, may be NULL */
+} orc_orbit_tallies;
+
+/* Raw tallies are ADDED to out.  Returns 0 on success, 1 for an invalid
+ * problem or orbit, 2 for a channel kind the orbit mode does not take, 3 for
+ * a primary outside the tube. */
+int orc_orbit_run(const orc_problem* p, const orc_orbit* o, const orc_orbit_primaries* pr,
+                  uint64_t seed, int n_threads, orc_orbit_tallies* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -528,3 +528,93 @@ def charge_exchange_problem(n_m3: float, length: float, nz: int, t_k: float,
     prob = ion_beam_problem([ch], np.full(nz, n_m3), length, 1e-5, 100.0, **kw)
     prob.gas_temperature_k = t_k
     return prob
+
+
+# ---------------------------------------------------------------------------
+# full-orbit transport in a tube (Sec. 3.1 Boris mover; Sec. 5 tube currents)
+
+C_LIGHT_MPS = 299792458.0
+
+
+@dataclasses.dataclass
+class Orbit:
+    """Fields and tube of a full-orbit run: uniform B along +z, the electric
+    field E = (e_r x, e_r y, e_z[segment]), a beam tube of radius R with
+    n_rbins radial bins, and the Boris time step of each species."""
+    b_t: float
+    tube_radius_m: float
+    n_rbins: int
+    dt_s: np.ndarray                 # [4]
+    e_z_vm: Optional[np.ndarray] = None   # [n_zbins] or None (no axial field)
+    e_r_vm2: float = 0.0
+    max_steps: int = 0               # steps per flight before "stalled"; 0 = 2^40
+
+
+@dataclasses.dataclass
+class OrbitPrimaries:
+    x_m: np.ndarray
+    y_m: np.ndarray
+    z_m: np.ndarray
+    e_ev: np.ndarray
+    mu: np.ndarray                   # cosine of the angle to +z
+    phi: np.ndarray                  # azimuth of the transverse velocity
+    species: np.ndarray              # uint8
+    pid_offset: int = 0
+
+    @property
+    def n(self) -> int:
+        return int(self.z_m.shape[0])
+
+
+def boris_dt(b_t: float, frac: float = 0.1) -> np.ndarray:
+    """Time step per species: frac / Omega_max, Omega_max = e B / m the
+    largest gyro frequency of the species (at rest), so that
+    dt < 1 / Omega_g,max (Eq. boris_timestep_requirement)."""
+    omega = abs(b_t) * C_LIGHT_MPS ** 2 / SPECIES_MASS_EV
+    return np.ascontiguousarray(frac / np.maximum(omega, 1e-300), np.float64)
+
+
+def ion_elastic_channels(nodes: np.ndarray, sigma_t2p: float = 3e-19,
+                         sigma_t3p: float = 3e-19) -> List[Channel]:
+    """Synthetic elastic scattering of T2+ and T3+ on T2 (constant cross
+    sections; the paper notes ion scattering cross sections far above the
+    electrons')."""
+    return [Channel("elastic_T2+", ELASTIC, T2P, -1, 0.0, np.full_like(nodes, sigma_t2p)),
+            Channel("elastic_T3+", ELASTIC, T3P, -1, 0.0, np.full_like(nodes, sigma_t3p))]
+
+
+def orbit_config(n_decays: int = 100_000, seed: int = 1, length: float = 1.0, nz: int = 100,
+                 density_m3: float = 5e19, b_t: float = 0.25, tube_radius_m: float = 0.045,
+                 n_rbins: int = 45, e_r_vm2: float = 20.0, lifetime_s: float = 2e-4):
+    """Tube section for the full-orbit mover: uniform T2 gas, the seven
+    electron channels with T2+ ionization, T2+ -> T3+ clustering and ion
+    elastic scattering; a beam tube of 45 mm radius (the WGTS tube), a
+    radial field of a weak space-charge potential and B = 0.25 T (a tenth of
+    the Sec. 5 example, to keep the number of steps per gyration affordable).
+    One beta electron and one thermal T2+ per decay, born uniformly over the
+    cross section and along z, isotropic (those born within two gyration
+    radii of the wall can reach it); a lifetime cap ends slow ions that
+    random-walk for long."""
+    nodes = energy_nodes(2048, 1.0, 2.0e4)
+    chans = electron_channels(nodes, True)
+    chans.append(Channel("clustering_T2+", CLUSTERING, T2P, T3P, 0.0, np.full_like(nodes, 1.91e-18)))
+    chans += ion_elastic_channels(nodes)
+    prob = uniform_problem(density_m3, length, nz, chans, max_lifetime_s=lifetime_s)
+    prob.name = "orbit_tube"
+    prob.b_tesla = b_t
+    orbit = Orbit(b_t=b_t, tube_radius_m=tube_radius_m, n_rbins=n_rbins, dt_s=boris_dt(b_t),
+                  e_r_vm2=e_r_vm2)
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 6]))
+    n = 2 * n_decays
+    r = tube_radius_m * np.sqrt(rng.uniform(0.0, 1.0, n))
+    a = rng.uniform(0.0, 2.0 * math.pi, n)
+    z = rng.uniform(0.0, length, n)
+    e = np.empty(n)
+    e[0::2] = sample_beta(rng, n_decays)
+    e[1::2] = sample_thermal_energy(rng, n_decays, prob.gas_temperature_k)
+    sp = np.empty(n, np.uint8)
+    sp[0::2] = E
+    sp[1::2] = T2P
+    prims = OrbitPrimaries(r * np.cos(a), r * np.sin(a), z, e, isotropic_mu(rng, n),
+                           rng.uniform(0.0, 2.0 * math.pi, n), sp)
+    return prob, orbit, prims
