@@ -316,6 +316,110 @@ karl_status karl_run_pass_static(karl_ctx* ctx, const karl_primaries* prim,
                                  const karl_run_opts* opts, int32_t pass,
                                  const uint64_t* field_time_in, karl_tallies* out);
 
+/* ---- Full-orbit transport in a beam tube (Sec. 3.1 Boris mover) ----
+ *
+ * Each particle carries its position (x, y, z) and proper velocity
+ * u = gamma v.  A step is one relativistic Boris push (Sec. 3.1: half an
+ * electric kick, the magnetic rotation, half a kick; the paper's equations
+ * with u = gamma v and gamma of the half-kicked velocity) with the species'
+ * time step in the uniform field b_t along +z and the electric field
+ * E = (e_r_vm2 x, e_r_vm2 y, e_z_vm[segment of z]).  The initial velocity is
+ * the half-step velocity.  A flight draws eta once and ends where the optical
+ * depth summed over its steps (the total rate of the step midpoint's segment
+ * times the step's path length; cross sections at the flight's starting
+ * energy without electric field, at each step's energy with one) reaches
+ * -ln eta, at z = 0 or L, where the path meets the wall r = tube_radius_m,
+ * or at the lifetime cap; that last step is shortened to the fraction of its
+ * displacement where it happens (on a tie: wall, z end, lifetime, collision).
+ * Collisions use the context's tables and the kinematics of Sec. 3.3 with
+ * directions turned in three dimensions (frame: the unit vector towards +z
+ * normal to the old direction, so the pitch update equals the guiding-centre
+ * one).  Channel kinds: elastic and ionization with the target at rest,
+ * excitation, clustering, three-body clustering; recombination, charge
+ * exchange and moving targets are refused (KARL_EINVAL).  Energies are FP64
+ * and not quantised (an electric field changes them continuously).
+ * Tallies are raw and ADDED to out's buffers (zero them first):
+ *   time_z [4][n_zbins], time_r [4][n_rbins]: time per z segment and per
+ *     radial bin (width R / n_rbins), u64 in units of 2^-50 s; the time of a
+ *     step goes to the cell of its midpoint, each run of steps in one cell
+ *     rounded once;
+ *   cross_pos / cross_neg [4][n_zbins+1]: crossings of z faces (the end faces
+ *     count the exits);
+ *   rcross_out / rcross_in [4][n_rbins+1]: crossings of the cylinders
+ *     r = k R / n_rbins between the radial bins of a step's ends (k = n_rbins:
+ *     the wall, outward only);
+ *   wall [4][n_zbins]: particles ended on the wall, by z segment (Sec. 5's
+ *     tube current);
+ *   spectrum [2][4][n_spec_bins+1]: kinetic energies at z = 0 and z = L in
+ *     bins of spec_bin_ev, the last bin collecting the overflow;
+ *   ledger [KARL_ORBIT_LEDGER] int64, energy [KARL_ORBIT_ENERGY] double:
+ *     slots below; chan_count [n_channels];
+ *   per_primary [n] (may be NULL): collisions in each primary's tree;
+ *   end_state [n][8] (may be NULL): x y z E ux uy uz t of each primary when
+ *     it ended (its clustering, for an ion that clusters).
+ * Every buffer is host memory.  opts: precision must be KARL_FP64, n_passes
+ * is ignored; block_size 0 = 256 (at most 256); timeout_s limits each of the
+ * kernel launches (one per product generation).  Errors: KARL_EINVAL (NULL
+ * or inconsistent arguments, a primary outside the tube or the column, a
+ * refused channel kind); KARL_ECAPACITY when one generation's products
+ * exceed max(2^20, 8 n_in) slots or more than 4096 generations are needed
+ * (tallies unspecified); KARL_ETIMEOUT; KARL_ECANCELLED (karl_cancel). */
+enum {
+  KARL_OB_BIRTHS = 0,           /* [4] */
+  KARL_OB_DEATHS = 4,           /* [4][8] by reason: exit z=0, exit z=L, wall, cutoff,
+                                   collision cap, lifetime cap, clustering, stalled */
+  KARL_OB_N_COLLISIONS = 36, KARL_OB_N_FLIGHTS = 37, KARL_OB_N_STEPS = 38,
+  KARL_OB_N_SPAWN_E = 39, KARL_OB_N_SPAWN_ION = 40,
+  KARL_ORBIT_LEDGER = 48
+};
+enum {
+  KARL_OE_IN_PRIMARY = 0, KARL_OE_IN_THERMAL = 1, KARL_OE_EXIT0 = 2, KARL_OE_EXIT1 = 3,
+  KARL_OE_WALL = 4, KARL_OE_CUTOFF = 5, KARL_OE_CAP = 6, KARL_OE_CLUSTER = 7,
+  KARL_OE_LOSS_IONIZ = 8, KARL_OE_LOSS_EXCIT = 9, KARL_OE_RECOIL = 10, KARL_OE_STALLED = 11,
+  KARL_OE_FIELD_WORK = 12,      /* kinetic energy gained from the electric field */
+  KARL_ORBIT_ENERGY = 16
+};
+typedef struct karl_orbit {
+  double b_t;                   /* magnetic field along +z (T) */
+  double tube_radius_m;         /* wall radius R > 0 */
+  int32_t n_rbins;              /* radial bins, 1 .. 2^20 */
+  int32_t pad;
+  const double* e_z_vm;         /* [n_zbins] axial field per segment (V/m), NULL: none */
+  double e_r_vm2;               /* radial field E_r = e_r_vm2 r (V/m^2) */
+  double dt_s[4];               /* Boris time step per species, > 0 */
+  uint64_t max_steps;           /* steps of one flight before the particle counts as
+                                   stalled; 0 = 2^40 */
+} karl_orbit;
+typedef struct karl_orbit_primaries {
+  int64_t n;
+  const double* x_m;
+  const double* y_m;
+  const double* z_m;            /* inside the tube: x^2 + y^2 < R^2, 0 <= z <= L */
+  const double* e_ev;
+  const double* mu;             /* cosine of the angle to +z */
+  const double* phi;            /* azimuth of the transverse velocity (rad) */
+  const uint8_t* species;
+  int64_t pid_offset;           /* primary id of element 0 (random streams) */
+} karl_orbit_primaries;
+typedef struct karl_orbit_tallies {
+  uint64_t* spectrum;
+  uint64_t* time_z;
+  uint64_t* time_r;
+  uint64_t* cross_pos;
+  uint64_t* cross_neg;
+  uint64_t* rcross_out;
+  uint64_t* rcross_in;
+  uint64_t* wall;
+  int64_t* ledger;
+  double* energy;
+  uint64_t* chan_count;
+  uint64_t* per_primary;
+  double* end_state;
+} karl_orbit_tallies;
+karl_status karl_run_orbit(karl_ctx* ctx, const karl_orbit* orbit,
+                           const karl_orbit_primaries* prim, const karl_run_opts* opts,
+                           karl_orbit_tallies* out);
+
 /* Request that a running karl_run on this context stop (thread-safe).  The
  * kernel polls the flag; the run returns KARL_ECANCELLED. */
 void karl_cancel(karl_ctx* ctx);

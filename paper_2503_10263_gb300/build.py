@@ -17,11 +17,14 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libkarl.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["karl_abi.cu", "transport.cu", "multi.cu", "server.cu"]
-HEADERS = ["karl_device.cuh", "event.cuh", "multi.cuh", "host_common.h", "log_table.inc"]
+SOURCES = ["karl_abi.cu", "transport.cu", "multi.cu", "server.cu", "orbit.cu"]
+HEADERS = ["karl_device.cuh", "event.cuh", "multi.cuh", "orbit.cuh", "host_common.h",
+           "log_table.inc"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]
+# the full-orbit push rounds every product and sum on its own, as the oracle does
+FILE_FLAGS = {"orbit.cu": ["-fmad=false"]}
 
 
 def _nvcc() -> str:
@@ -43,7 +46,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD_DIR, os.path.splitext(src)[0] + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *FILE_FLAGS.get(src, []), "-c", os.path.join(CSRC, src), "-o",
+               obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -19,6 +19,7 @@
 
 #include "../../include/karl.h"
 #include "host_common.h"
+#include "orbit.cuh"
 
 namespace karl {
 cudaError_t launch_transport(bool f32, const Params& P, const Ring& R, Control* ctl,
@@ -26,6 +27,9 @@ cudaError_t launch_transport(bool f32, const Params& P, const Ring& R, Control* 
                              int block, cudaStream_t st);
 cudaError_t transport_occupancy(bool f32, const Params& P, int block, int* blocks_per_sm);
 cudaError_t transport_setup();
+cudaError_t launch_orbit(const Params& P, const OrbitDev& O, int grid, int block,
+                         cudaStream_t st);
+cudaError_t orbit_occupancy(int block, int* blocks_per_sm);
 }  // namespace karl
 
 using namespace karl;
@@ -186,6 +190,14 @@ struct karl_ctx {
   DevBuf<int> d_cancelbuf;
   // sums over the cycles of a continuous-update run
   DevBuf<unsigned long long> c_spec, c_time, c_cpos, c_cneg, c_rec, c_led, c_chan, c_pp, d_recin;
+  // full-orbit runs: primaries, the lists of two generations, raw tallies
+  DevBuf<double> o_px, o_py, o_pz, o_pe, o_pmu, o_pphi, o_ez, o_energy, o_end;
+  DevBuf<uint8_t> o_psp, o_lsp[2];
+  DevBuf<double> o_lx[2], o_ly[2], o_lz[2], o_lux[2], o_luy[2], o_luz[2];
+  DevBuf<unsigned long long> o_lnode[2], o_lpid[2];
+  DevBuf<unsigned long long> o_tz, o_tr, o_xp, o_xn, o_ro, o_ri, o_wall, o_spec, o_led, o_chan,
+      o_pp, o_cnt;
+  DevBuf<int> o_err;
   Control* d_ctl = nullptr;     // = d_ctlbuf.p
   int* d_cancel = nullptr;      // = d_cancelbuf.p, device word polled by the kernel
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -202,6 +214,13 @@ struct karl_ctx {
     f(d_density); f(d_current); f(d_field); f(d_bad); f(r_z); f(r_mu); f(r_tal); f(r_eq);
     f(r_node); f(r_pid); f(r_seq); f(r_ev); f(r_sj); f(d_ctlbuf); f(d_cancelbuf);
     f(c_spec); f(c_time); f(c_cpos); f(c_cneg); f(c_rec); f(c_led); f(c_chan); f(c_pp); f(d_recin);
+    f(o_px); f(o_py); f(o_pz); f(o_pe); f(o_pmu); f(o_pphi); f(o_ez); f(o_energy); f(o_end);
+    f(o_psp); f(o_tz); f(o_tr); f(o_xp); f(o_xn); f(o_ro); f(o_ri); f(o_wall); f(o_spec);
+    f(o_led); f(o_chan); f(o_pp); f(o_cnt); f(o_err);
+    for (int g = 0; g < 2; ++g) {
+      f(o_lsp[g]); f(o_lx[g]); f(o_ly[g]); f(o_lz[g]); f(o_lux[g]); f(o_luy[g]); f(o_luz[g]);
+      f(o_lnode[g]); f(o_lpid[g]);
+    }
   }
   // buffers replaced during earlier calls (none of their work is in flight now)
   void drop_retired() {
@@ -1467,5 +1486,247 @@ extern "C" karl_status karl_run_pass_static(karl_ctx* ctx, const karl_primaries*
   CK(cudaStreamSynchronize(st));
   ctx->stats.collisions[pi] = led[L_N_COLL];
   ctx->stats.flights[pi] = led[L_N_FLIGHT];
+  return KARL_OK;
+}
+
+// ===========================================================================
+// Full-orbit transport (Sec. 3.1 Boris mover): one launch per generation of
+// particles, the products of one generation being the next one's list.
+
+namespace {
+
+constexpr double ORBIT_CHARGE[NSP] = {-1.0, 1.0, 1.0, 1.0};   // units of e
+constexpr int ORBIT_MAX_GENERATIONS = 4096;
+
+karl_status check_orbit(karl_ctx* ctx, const karl_orbit* ob, const karl_orbit_primaries* pr,
+                        const karl_run_opts* o, const karl_orbit_tallies* out) {
+  if (!ob || !pr || !o || !out) return fail(ctx, KARL_EINVAL, "NULL argument");
+  if (o->precision != KARL_FP64) return fail(ctx, KARL_EINVAL, "orbit runs are FP64 only");
+  if (o->block_size != 0 && (o->block_size < 32 || o->block_size > 256 || o->block_size % 32))
+    return fail(ctx, KARL_EINVAL, "block_size must be a multiple of 32 in [32, 256]");
+  if (!std::isfinite(ob->b_t) || !(ob->tube_radius_m > 0.0) || !std::isfinite(ob->tube_radius_m) ||
+      ob->n_rbins < 1 || ob->n_rbins > (1 << 20) || !std::isfinite(ob->e_r_vm2))
+    return fail(ctx, KARL_EINVAL, "invalid orbit field, radius or radial bins");
+  for (int s = 0; s < NSP; ++s)
+    if (!(ob->dt_s[s] > 0.0) || !std::isfinite(ob->dt_s[s]))
+      return fail(ctx, KARL_EINVAL, "time step of species %d must be positive", s);
+  if (ob->e_z_vm)
+    for (int j = 0; j < ctx->nz; ++j)
+      if (!std::isfinite(ob->e_z_vm[j])) return fail(ctx, KARL_EINVAL, "e_z_vm[%d] not finite", j);
+  for (int k = 0; k < ctx->nch; ++k) {
+    const int kd = ctx->kind[k];
+    if (kd == RECOMBINATION || kd == CHARGE_EXCHANGE)
+      return fail(ctx, KARL_EINVAL, "channel %d: kind %d is not available in orbit runs", k, kd);
+    if ((kd == ELASTIC || kd == IONIZATION) && ctx->model.target[k] != 0)
+      return fail(ctx, KARL_EINVAL, "channel %d: moving targets are not available in orbit runs", k);
+  }
+  if (pr->n < 0) return fail(ctx, KARL_EINVAL, "n < 0");
+  if (pr->n > 0 && (!pr->x_m || !pr->y_m || !pr->z_m || !pr->e_ev || !pr->mu || !pr->phi ||
+                    !pr->species))
+    return fail(ctx, KARL_EINVAL, "primary array is NULL");
+  const double R2 = ob->tube_radius_m * ob->tube_radius_m;
+  for (int64_t i = 0; i < pr->n; ++i) {
+    const double x = pr->x_m[i], y = pr->y_m[i], z = pr->z_m[i];
+    if (!(x * x + y * y < R2) || !(z >= 0.0 && z <= ctx->L) || pr->species[i] >= NSP ||
+        !(pr->e_ev[i] >= 0.0) || !std::isfinite(pr->e_ev[i]) || !(std::fabs(pr->mu[i]) <= 1.0) ||
+        !std::isfinite(pr->phi[i]))
+      return fail(ctx, KARL_EINVAL, "primary %lld outside the tube or invalid", (long long)i);
+  }
+  if (!out->spectrum || !out->time_z || !out->time_r || !out->cross_pos || !out->cross_neg ||
+      !out->rcross_out || !out->rcross_in || !out->wall || !out->ledger || !out->energy ||
+      (ctx->nch > 0 && !out->chan_count))
+    return fail(ctx, KARL_EINVAL, "tally buffer is NULL");
+  return KARL_OK;
+}
+
+// Host buffer `src` of n elements into device buffer b (n may be 0).
+template <class T>
+karl_status upload(karl_ctx* ctx, DevBuf<T>& b, const T* src, size_t n, cudaStream_t st) {
+  CK(b.ensure(n));
+  if (n) CK(cudaMemcpyAsync(b.p, src, n * sizeof(T), cudaMemcpyHostToDevice, st));
+  return KARL_OK;
+}
+
+template <class T>
+karl_status zeroed(karl_ctx* ctx, DevBuf<T>& b, size_t n, cudaStream_t st) {
+  CK(b.ensure(n));
+  CK(cudaMemsetAsync(b.p, 0, std::max<size_t>(n, 1) * sizeof(T), st));
+  return KARL_OK;
+}
+
+// Add device buffer b (n u64) into the host buffer dst.
+karl_status add_out(karl_ctx* ctx, const DevBuf<unsigned long long>& b, uint64_t* dst, size_t n,
+                    cudaStream_t st) {
+  if (!dst || !n) return KARL_OK;
+  std::vector<unsigned long long> h(n);
+  CK(cudaMemcpyAsync(h.data(), b.p, n * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (size_t i = 0; i < n; ++i) dst[i] += h[i];
+  return KARL_OK;
+}
+
+karl_status ensure_list(karl_ctx* ctx, int g, size_t n) {
+  CK(ctx->o_lx[g].ensure(n)); CK(ctx->o_ly[g].ensure(n)); CK(ctx->o_lz[g].ensure(n));
+  CK(ctx->o_lux[g].ensure(n)); CK(ctx->o_luy[g].ensure(n)); CK(ctx->o_luz[g].ensure(n));
+  CK(ctx->o_lnode[g].ensure(n)); CK(ctx->o_lpid[g].ensure(n)); CK(ctx->o_lsp[g].ensure(n));
+  return KARL_OK;
+}
+
+OrbitList list_of(karl_ctx* ctx, int g) {
+  OrbitList L;
+  L.x = ctx->o_lx[g].p; L.y = ctx->o_ly[g].p; L.z = ctx->o_lz[g].p;
+  L.ux = ctx->o_lux[g].p; L.uy = ctx->o_luy[g].p; L.uz = ctx->o_luz[g].p;
+  L.node = ctx->o_lnode[g].p; L.pid = ctx->o_lpid[g].p; L.sp = ctx->o_lsp[g].p;
+  return L;
+}
+
+}  // namespace
+
+extern "C" karl_status karl_run_orbit(karl_ctx* ctx, const karl_orbit* ob,
+                                      const karl_orbit_primaries* pr, const karl_run_opts* o,
+                                      karl_orbit_tallies* out) {
+  if (!ctx) return KARL_EINVAL;
+  ctx->err.clear();
+  ctx->drop_retired();
+  karl_status s = check_orbit(ctx, ob, pr, o, out);
+  if (s) return s;
+  TraceRange trace("karl orbit run");
+  cudaStream_t st = o->stream ? (cudaStream_t)o->stream : ctx->own_stream;
+  const size_t n = (size_t)pr->n, nz = (size_t)ctx->nz, nr = (size_t)ob->n_rbins;
+  std::memset(ctx->stats.kernel_ms, 0, sizeof ctx->stats.kernel_ms);
+  ctx->stats.kernel_launches = 0;
+  if ((s = upload(ctx, ctx->o_px, pr->x_m, n, st)) || (s = upload(ctx, ctx->o_py, pr->y_m, n, st)) ||
+      (s = upload(ctx, ctx->o_pz, pr->z_m, n, st)) || (s = upload(ctx, ctx->o_pe, pr->e_ev, n, st)) ||
+      (s = upload(ctx, ctx->o_pmu, pr->mu, n, st)) ||
+      (s = upload(ctx, ctx->o_pphi, pr->phi, n, st)) ||
+      (s = upload(ctx, ctx->o_psp, pr->species, n, st)) ||
+      (s = upload(ctx, ctx->o_ez, ob->e_z_vm, ob->e_z_vm ? nz : 0, st)))
+    return s;
+  const size_t nspec = n_spec(ctx), ncross = nz + 1;
+  if ((s = zeroed(ctx, ctx->o_tz, NSP * nz, st)) || (s = zeroed(ctx, ctx->o_tr, NSP * nr, st)) ||
+      (s = zeroed(ctx, ctx->o_xp, NSP * ncross, st)) ||
+      (s = zeroed(ctx, ctx->o_xn, NSP * ncross, st)) ||
+      (s = zeroed(ctx, ctx->o_ro, NSP * (nr + 1), st)) ||
+      (s = zeroed(ctx, ctx->o_ri, NSP * (nr + 1), st)) ||
+      (s = zeroed(ctx, ctx->o_wall, NSP * nz, st)) || (s = zeroed(ctx, ctx->o_spec, nspec, st)) ||
+      (s = zeroed(ctx, ctx->o_led, (size_t)KARL_ORBIT_LEDGER, st)) ||
+      (s = zeroed(ctx, ctx->o_chan, (size_t)std::max(ctx->nch, 1), st)) ||
+      (s = zeroed(ctx, ctx->o_energy, (size_t)KARL_ORBIT_ENERGY, st)) ||
+      (s = zeroed(ctx, ctx->o_pp, out->per_primary ? n : 0, st)) ||
+      (s = zeroed(ctx, ctx->o_end, out->end_state ? 8 * n : 0, st)) ||
+      (s = zeroed(ctx, ctx->o_cnt, 2, st)) || (s = zeroed(ctx, ctx->o_err, 1, st)))
+    return s;
+
+  Params P;
+  karl_run_opts o1 = *o;
+  o1.n_passes = 1;
+  base_params(ctx, P, &o1, 1);
+  P.pid_offset = pr->pid_offset;
+  OrbitDev O;
+  std::memset(&O, 0, sizeof O);
+  O.bz = ob->b_t;
+  O.R2 = ob->tube_radius_m * ob->tube_radius_m;
+  O.r_scale = (double)ob->n_rbins / ob->tube_radius_m;
+  O.er = ob->e_r_vm2;
+  for (int sp = 0; sp < NSP; ++sp) {
+    O.dt[sp] = ob->dt_s[sp];
+    O.h[sp] = 0.5 * (ORBIT_CHARGE[sp] * C_LIGHT * C_LIGHT / ctx->mass[sp]) * ob->dt_s[sp];
+  }
+  O.e_cut = ctx->e_cut;
+  O.spec_bin = ctx->spec_bin;
+  O.ez = ob->e_z_vm ? ctx->o_ez.p : nullptr;
+  O.nr = ob->n_rbins;
+  O.fields = ob->e_r_vm2 != 0.0;
+  if (ob->e_z_vm)
+    for (size_t j = 0; j < nz; ++j) O.fields = O.fields || ob->e_z_vm[j] != 0.0;
+  O.max_steps = ob->max_steps ? ob->max_steps : (1ULL << 40);
+  O.px = ctx->o_px.p; O.py = ctx->o_py.p; O.pz = ctx->o_pz.p; O.pe = ctx->o_pe.p;
+  O.pmu = ctx->o_pmu.p; O.pphi = ctx->o_pphi.p; O.psp = ctx->o_psp.p;
+  O.counters = ctx->o_cnt.p;
+  O.time_z = ctx->o_tz.p; O.time_r = ctx->o_tr.p; O.xpos = ctx->o_xp.p; O.xneg = ctx->o_xn.p;
+  O.rout = ctx->o_ro.p; O.rin = ctx->o_ri.p; O.wall = ctx->o_wall.p; O.spectrum = ctx->o_spec.p;
+  O.ledger = ctx->o_led.p; O.chan = ctx->o_chan.p;
+  O.per_primary = out->per_primary ? ctx->o_pp.p : nullptr;
+  O.energy = ctx->o_energy.p;
+  O.end_state = out->end_state ? ctx->o_end.p : nullptr;
+  O.error = ctx->o_err.p;
+  O.cancel = ctx->d_cancel;
+  const double timeout = o->timeout_s > 0 ? o->timeout_s : 600.0;
+  O.timeout_ns = (unsigned long long)(timeout * 1e9);
+
+  const int block = o->block_size > 0 ? o->block_size : 256;
+  int bps = 0;
+  CK(orbit_occupancy(block, &bps));
+  if (o->blocks_per_sm > 0) bps = std::min(bps, (int)o->blocks_per_sm);
+  if (bps < 1) bps = 1;
+  const int grid = ctx->num_sms * bps;
+  CK(cudaMemsetAsync(ctx->d_cancel, 0, sizeof(int), st));
+
+  long long n_in = (long long)n;
+  int cur = 0;                                        // list holding the current generation
+  float total_ms = 0.0f;
+  for (int gen = 0; n_in > 0; ++gen) {
+    if (gen >= ORBIT_MAX_GENERATIONS)
+      return fail(ctx, KARL_ECAPACITY, "more than %d product generations", ORBIT_MAX_GENERATIONS);
+    const unsigned long long cap =
+        std::max<unsigned long long>(1ULL << 20, 8ULL * (unsigned long long)n_in);
+    if ((s = ensure_list(ctx, 1 - cur, (size_t)cap))) return s;
+    if (gen > 0 && (s = ensure_list(ctx, cur, (size_t)n_in))) return s;
+    O.from_primaries = gen == 0;
+    O.n_in = n_in;
+    O.in = list_of(ctx, cur);
+    O.out = list_of(ctx, 1 - cur);
+    O.out_cap = cap;
+    CK(cudaMemsetAsync(ctx->o_cnt.p, 0, 2 * sizeof(unsigned long long), st));
+    CK(cudaEventRecord(ctx->ev0, st));
+    CK(launch_orbit(P, O, grid, block, st));
+    CK(cudaEventRecord(ctx->ev1, st));
+    unsigned long long cnt[2] = {0, 0};
+    int err = 0;
+    CK(cudaMemcpyAsync(cnt, ctx->o_cnt.p, sizeof cnt, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&err, ctx->o_err.p, sizeof err, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    total_ms += ms;
+    ctx->stats.kernel_launches += 1;
+    if (err == ERR_CAPACITY)
+      return fail(ctx, KARL_ECAPACITY, "generation %d: more than %llu products", gen, cap);
+    if (err == ERR_TIMEOUT) return fail(ctx, KARL_ETIMEOUT, "orbit kernel timed out");
+    if (err == ERR_CANCELLED) return fail(ctx, KARL_ECANCELLED, "run cancelled");
+    if (err != 0) return fail(ctx, KARL_ECUDA, "orbit kernel error %d", err);
+    n_in = (long long)cnt[1];
+    cur = 1 - cur;
+  }
+  ctx->stats.kernel_ms[0] = total_ms;
+  ctx->stats.grid_blocks = grid;
+  ctx->stats.block_size = block;
+  if ((s = add_out(ctx, ctx->o_spec, out->spectrum, nspec, st)) ||
+      (s = add_out(ctx, ctx->o_tz, out->time_z, NSP * nz, st)) ||
+      (s = add_out(ctx, ctx->o_tr, out->time_r, NSP * nr, st)) ||
+      (s = add_out(ctx, ctx->o_xp, out->cross_pos, NSP * ncross, st)) ||
+      (s = add_out(ctx, ctx->o_xn, out->cross_neg, NSP * ncross, st)) ||
+      (s = add_out(ctx, ctx->o_ro, out->rcross_out, NSP * (nr + 1), st)) ||
+      (s = add_out(ctx, ctx->o_ri, out->rcross_in, NSP * (nr + 1), st)) ||
+      (s = add_out(ctx, ctx->o_wall, out->wall, NSP * nz, st)) ||
+      (s = add_out(ctx, ctx->o_led, (uint64_t*)out->ledger, (size_t)KARL_ORBIT_LEDGER, st)) ||
+      (s = add_out(ctx, ctx->o_chan, out->chan_count, (size_t)ctx->nch, st)) ||
+      (s = add_out(ctx, ctx->o_pp, out->per_primary, out->per_primary ? n : 0, st)))
+    return s;
+  std::vector<double> e(KARL_ORBIT_ENERGY);
+  CK(cudaMemcpyAsync(e.data(), ctx->o_energy.p, e.size() * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int i = 0; i < KARL_ORBIT_ENERGY; ++i) out->energy[i] += e[i];
+  if (out->end_state && n) {
+    CK(cudaMemcpyAsync(out->end_state, ctx->o_end.p, 8 * n * sizeof(double),
+                       cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  long long led[KARL_ORBIT_LEDGER];
+  CK(cudaMemcpy(led, ctx->o_led.p, sizeof led, cudaMemcpyDeviceToHost));
+  ctx->stats.collisions[0] = led[OB_N_COLL];
+  ctx->stats.flights[0] = led[OB_N_FLIGHT];
+  ctx->stats.particles[0] = led[OB_BIRTHS] + led[OB_BIRTHS + 1] + led[OB_BIRTHS + 2] +
+                            led[OB_BIRTHS + 3];
   return KARL_OK;
 }

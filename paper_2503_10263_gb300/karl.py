@@ -38,6 +38,13 @@ E_IN_PRIMARY, E_IN_THERMAL, E_EXIT0, E_EXIT1, E_CUTOFF, E_CAP, E_RECOMB, E_CLUST
 BIRTHS, DEATHS = 12, 16
 N_COLLISIONS, N_FLIGHTS, N_SPAWN_E, N_SPAWN_ION = 48, 49, 50, 51
 N_COLLISIONS_ALL, N_FLIGHTS_ALL = 52, 53     # every pass of the run
+# full-orbit runs: integer ledger and energy ledger slots
+OB_BIRTHS, OB_DEATHS = 0, 4
+OB_N_COLLISIONS, OB_N_FLIGHTS, OB_N_STEPS, OB_N_SPAWN_E, OB_N_SPAWN_ION = 36, 37, 38, 39, 40
+ORBIT_LEDGER_LEN, ORBIT_ENERGY_LEN = 48, 16
+ORBIT_REASONS = ("exit0", "exit1", "wall", "cutoff", "cap_coll", "cap_time", "cluster", "stalled")
+OE_IN_PRIMARY, OE_IN_THERMAL, OE_EXIT0, OE_EXIT1, OE_WALL, OE_CUTOFF, OE_CAP, OE_CLUSTER, \
+    OE_LOSS_IONIZ, OE_LOSS_EXCIT, OE_RECOIL, OE_STALLED, OE_FIELD_WORK = range(13)
 
 
 class KarlError(RuntimeError):
@@ -92,6 +99,27 @@ class RunOpts(C.Structure):
                 ("timeout_s", C.c_double), ("stream", C.c_void_p)]
 
 
+class Orbit(C.Structure):
+    _fields_ = [("b_t", C.c_double), ("tube_radius_m", C.c_double), ("n_rbins", C.c_int32),
+                ("pad", C.c_int32), ("e_z_vm", C.c_void_p), ("e_r_vm2", C.c_double),
+                ("dt_s", C.c_double * N_SPECIES), ("max_steps", C.c_uint64)]
+
+
+class OrbitPrimaries(C.Structure):
+    _fields_ = [("n", C.c_int64)] + [(k, C.c_void_p) for k in
+                                     ("x_m", "y_m", "z_m", "e_ev", "mu", "phi", "species")] + [
+        ("pid_offset", C.c_int64)]
+
+
+ORBIT_TALLY_KEYS = ("spectrum", "time_z", "time_r", "cross_pos", "cross_neg", "rcross_out",
+                    "rcross_in", "wall", "ledger", "energy", "chan_count", "per_primary",
+                    "end_state")
+
+
+class OrbitTallies(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ORBIT_TALLY_KEYS]
+
+
 class Layout(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("spectrum", "time_fx", "cross", "recomb", "ledger",
                                            "chan_count", "density", "current", "field")]
@@ -129,6 +157,8 @@ def load() -> C.CDLL:
     lib.karl_run_cycles.argtypes = [C.c_void_p, P(Primaries), P(RunOpts), C.c_int32, P(Tallies)]
     lib.karl_run_cycle.argtypes = [C.c_void_p, P(Primaries), P(RunOpts), C.c_void_p, C.c_void_p,
                                    C.c_double, P(Tallies)]
+    lib.karl_run_orbit.argtypes = [C.c_void_p, P(Orbit), P(OrbitPrimaries), P(RunOpts),
+                                   P(OrbitTallies)]
     lib.karl_destroy.argtypes = [C.c_void_p]
     lib.karl_destroy.restype = None
     lib.karl_cancel.argtypes = [C.c_void_p]
@@ -140,7 +170,8 @@ def load() -> C.CDLL:
     lib.karl_tally_layout.argtypes = [C.c_void_p, P(Layout)]
     lib.karl_last_stats.argtypes = [C.c_void_p, P(RunStats)]
     for f in ("karl_create", "karl_run", "karl_run_pass", "karl_run_pass_static",
-              "karl_run_cycles", "karl_run_cycle", "karl_tally_layout", "karl_last_stats"):
+              "karl_run_cycles", "karl_run_cycle", "karl_tally_layout", "karl_last_stats",
+              "karl_run_orbit"):
         getattr(lib, f).restype = C.c_int
     _lib = lib
     return lib
@@ -186,6 +217,12 @@ def karl_run_cycle(ctx, prim: Primaries, opts: RunOpts, field_time_in, field_rec
                    field_decays: float, tallies: Tallies) -> int:
     return load().karl_run_cycle(ctx, C.byref(prim), C.byref(opts), field_time_in,
                                  field_recomb_in, field_decays, C.byref(tallies))
+
+
+def karl_run_orbit(ctx, orbit: Orbit, prim: OrbitPrimaries, opts: RunOpts,
+                   tallies: OrbitTallies) -> int:
+    return load().karl_run_orbit(ctx, C.byref(orbit), C.byref(prim), C.byref(opts),
+                                 C.byref(tallies))
 
 
 def karl_destroy(ctx) -> None:
@@ -324,6 +361,57 @@ class Context:
         self._check(karl_run_pass(self.ctx, ps, o, pass_index,
                                   fin.ctypes.data if fin is not None else None, ts))
         t["per_primary"] = t["per_primary"][:prims.n]
+        t["chan_count"] = t["chan_count"][:self.prob.n_channels]
+        return t
+
+    def empty_orbit_tallies(self, orbit, n_primaries: int) -> Dict[str, np.ndarray]:
+        p = self.prob
+        nz, nr = p.n_zbins, orbit.n_rbins
+        return {
+            "spectrum": np.zeros((2, N_SPECIES, p.n_spec_bins + 1), np.uint64),
+            "time_z": np.zeros((N_SPECIES, nz), np.uint64),
+            "time_r": np.zeros((N_SPECIES, nr), np.uint64),
+            "cross_pos": np.zeros((N_SPECIES, nz + 1), np.uint64),
+            "cross_neg": np.zeros((N_SPECIES, nz + 1), np.uint64),
+            "rcross_out": np.zeros((N_SPECIES, nr + 1), np.uint64),
+            "rcross_in": np.zeros((N_SPECIES, nr + 1), np.uint64),
+            "wall": np.zeros((N_SPECIES, nz), np.uint64),
+            "ledger": np.zeros(ORBIT_LEDGER_LEN, np.int64),
+            "energy": np.zeros(ORBIT_ENERGY_LEN, np.float64),
+            "chan_count": np.zeros(max(p.n_channels, 1), np.uint64),
+            "per_primary": np.zeros(max(n_primaries, 1), np.uint64),
+            "end_state": np.zeros((max(n_primaries, 1), 8), np.float64),
+        }
+
+    def run_orbit(self, orbit, prims, seed: int = 1, per_primary: bool = True,
+                  end_state: bool = True, precision: int = FP64, **kw) -> Dict[str, np.ndarray]:
+        """Full-orbit run (karl_run_orbit) of ``inputs.OrbitPrimaries`` in the
+        tube and fields of ``inputs.Orbit``; host buffers in and out."""
+        keep = []
+        ez = None
+        if orbit.e_z_vm is not None:
+            ez = np.ascontiguousarray(orbit.e_z_vm, np.float64)
+            keep.append(ez)
+        ob = Orbit(orbit.b_t, orbit.tube_radius_m, orbit.n_rbins, 0,
+                   ez.ctypes.data if ez is not None else None, orbit.e_r_vm2,
+                   (C.c_double * N_SPECIES)(*[float(x) for x in orbit.dt_s]),
+                   int(orbit.max_steps))
+        arrs = [np.ascontiguousarray(getattr(prims, k), np.float64)
+                for k in ("x_m", "y_m", "z_m", "e_ev", "mu", "phi")]
+        sp = np.ascontiguousarray(prims.species, np.uint8)
+        keep += arrs + [sp]
+        ps = OrbitPrimaries(prims.n, *[a.ctypes.data for a in arrs], sp.ctypes.data,
+                            int(prims.pid_offset))
+        t = self.empty_orbit_tallies(orbit, prims.n)
+        ts = OrbitTallies(*[t[k].ctypes.data for k in ORBIT_TALLY_KEYS])
+        if not per_primary:
+            ts.per_primary = None
+        if not end_state:
+            ts.end_state = None
+        o = self.opts(seed, 1, precision, **kw)
+        self._check(karl_run_orbit(self.ctx, ob, ps, o, ts))
+        t["per_primary"] = t["per_primary"][:prims.n]
+        t["end_state"] = t["end_state"][:prims.n]
         t["chan_count"] = t["chan_count"][:self.prob.n_channels]
         return t
 

@@ -1,0 +1,202 @@
+"""Full-orbit transport (the Boris mover of Sec. 3.1) on the GPU against the
+oracle and against the closed forms its pins use.
+
+The push is compiled without multiply-add contraction, like the oracle, so
+between collisions both sides compute the same positions; the histories part
+only where a library function (log, sin, cos, tan, atan) rounds differently
+in the last place and a discrete decision falls on that difference."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2503_10263_gb300 import inputs
+from tests import parity
+from tests.test_oracle_orbit import C, Q_TIME, _deaths, _msd_closed_form, _orbit, _prims, _vacuum
+
+pytestmark = pytest.mark.gpu
+
+THREADS = os.cpu_count() or 4
+
+
+@pytest.fixture(scope="module")
+def karl():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2503_10263_gb300 import build, karl as k
+    build.build()
+    return k
+
+
+def _gpu(karl, prob, orb, pr, seed=1, **kw):
+    ctx = karl.Context(prob)
+    try:
+        return ctx.run_orbit(orb, pr, seed=seed, **kw)
+    finally:
+        ctx.close()
+
+
+def test_tube_section_follows_the_oracle(karl):
+    """Tube section with ionization, clustering, ion scattering and a radial
+    field: collision counts per primary, the integer ledger and the tallies
+    follow the oracle's run of the same primaries."""
+    prob, orb, pr = inputs.orbit_config(n_decays=300, seed=3)
+    g = _gpu(karl, prob, orb, pr, seed=3)
+    o = oracle.orbit_run(prob, orb, pr, seed=3, n_threads=THREADS)
+    same = float(np.mean(g["per_primary"] == o["per_primary"]))
+    print(f"PARITY orbit tube section: histories identical {same:.4f} of {pr.n}")
+    assert same >= 0.99
+    lg, lo = g["ledger"].astype(float), o["ledger"].astype(float)
+    assert np.all(np.abs(lg - lo) <= 0.01 * lo + 3 * np.sqrt(lo + 1))
+    for key in ("time_z", "time_r"):
+        a, b = g[key].astype(float), o[key].astype(float)
+        assert abs(a.sum() - b.sum()) <= 0.01 * b.sum()
+    for key in ("wall", "spectrum", "cross_pos", "cross_neg", "rcross_out", "rcross_in"):
+        a, b = g[key].astype(float).sum(), o[key].astype(float).sum()
+        assert abs(a - b) <= 0.01 * b + 3 * math.sqrt(b + 1), key
+    E = g["energy"]
+    e_in = E[karl.OE_IN_PRIMARY] + E[karl.OE_IN_THERMAL] + E[karl.OE_FIELD_WORK]
+    assert abs(e_in - E[karl.OE_EXIT0:karl.OE_STALLED + 1].sum()) < 1e-9 * E[karl.OE_IN_PRIMARY]
+    assert g["ledger"][karl.OB_DEATHS + 8 * inputs.T2P + 6] > 0
+    assert g["wall"].sum() > 0
+
+
+@pytest.mark.parametrize("species,e_ev", [(inputs.E, 18600.0), (inputs.T2P, 10.0)])
+def test_gyration_decides_wall_hits_on_the_gpu(karl, species, e_ev):
+    """The gyration-circle geometry of the oracle pin: wall hit at 0.98 of
+    the circle's reach, exit at 1.02, for both charge signs."""
+    m = inputs.SPECIES_MASS_EV[species]
+    b, mu = 0.5, 0.2
+    pc = math.sqrt(e_ev * (e_ev + 2 * m))
+    r_l = pc * math.sqrt(1 - mu * mu) / (C * b)
+    sgn = -1.0 if species == inputs.E else 1.0
+    d = 5.0 * r_l
+    omega = b * C * C / (m + e_ev)
+    length = 8 * 2 * math.pi / omega * C * pc / (e_ev + m) * mu
+    prob = _vacuum(length=length)
+    for scale, wall in ((0.98, True), (1.02, False)):
+        orb = _orbit(b, tube_radius_m=(d + r_l) * scale, n_rbins=4)
+        t = _gpu(karl, prob, orb, _prims([d - r_l], [0.0], [0.0], [e_ev], [mu],
+                                         [sgn * 0.5 * math.pi], species))
+        assert _deaths(t, species, "wall") == (1 if wall else 0)
+        assert _deaths(t, species, "exit1") == (0 if wall else 1)
+
+
+def test_transit_field_work_and_exb_on_the_gpu(karl):
+    """Relativistic transit time, axial-field work with hyperbolic motion,
+    and the exact E x B slow mode, as in the oracle pins."""
+    m = inputs.ME_EV
+    # transit at 18.6 keV, mu = 0.7
+    prob = _vacuum(length=1.0)
+    orb = _orbit(0.5, tube_radius_m=0.05, n_rbins=5)
+    t = _gpu(karl, prob, orb, _prims([0.0], [0.0], [0.1], [18600.0], [0.7], [1.0], inputs.E))
+    v = C * math.sqrt(18600.0 * (18600.0 + 2 * m)) / (18600.0 + m)
+    expect = 0.9 / (0.7 * v) * Q_TIME
+    assert abs(float(t["time_z"].sum()) - expect) < 0.5 * (prob.n_zbins + 12) + 1e-12 * expect
+    # electrons accelerated by E_z = -1000 V/m from 100 eV over 1 m
+    orb = _orbit(0.5, tube_radius_m=0.05, n_rbins=5, e_z_vm=np.full(prob.n_zbins, -1000.0))
+    t = _gpu(karl, prob, orb, _prims([0.0] * 4, [0.0] * 4, [0.0] * 4, [100.0] * 4, [1.0] * 4,
+                                     [0.0] * 4, inputs.E))
+    assert abs(t["energy"][karl.OE_EXIT1] / 4 - 1100.0) < 0.11
+    pc0, pc1 = (math.sqrt(e * (e + 2 * m)) for e in (100.0, 1100.0))
+    t_exp = (pc1 - pc0) / (C * 1000.0) * Q_TIME
+    assert abs(float(t["time_z"].sum()) / 4 - t_exp) < 1e-4 * t_exp
+    # E x B slow mode of a T3+ ion
+    mi = inputs.M_T3P_EV
+    b, e_r, r0, t_cap = 0.5, 1e4, 0.01, 1e-4
+    om, kappa = b * C * C / mi, e_r * C * C / mi
+    om_s = 0.5 * (-om + math.sqrt(om * om - 4.0 * kappa))
+    vi = abs(om_s) * r0
+    e_kin = mi * (1.0 / math.sqrt(1.0 - (vi / C) ** 2) - 1.0)
+    prob = _vacuum(length=1.0, lifetime=t_cap)
+    orb = _orbit(b, tube_radius_m=0.05, n_rbins=5, e_r_vm2=e_r)
+    t = _gpu(karl, prob, orb, _prims([r0], [0.0], [0.5], [e_kin], [0.0],
+                                     [0.5 * math.pi if om_s > 0 else -0.5 * math.pi], inputs.T3P))
+    x, y = t["end_state"][0, 0], t["end_state"][0, 1]
+    turned = math.atan2(y, x)
+    assert abs(math.remainder(turned - om_s * t_cap, 2 * math.pi)) < 2e-3 * abs(om_s * t_cap)
+    assert abs(math.hypot(x, y) - r0) < 1e-3 * r0
+
+
+def test_cross_field_diffusion_on_the_gpu(karl):
+    """Classical cross-field spread of isotropically scattered electrons at
+    Omega = 3 nu (the oracle pin's closed form), with 20000 electrons."""
+    m = inputs.ME_EV
+    e, n_m3, sigma = 100.0, 1e20, 1e-19
+    v = C * math.sqrt(e * (e + 2 * m)) / (e + m)
+    nu = n_m3 * sigma * v
+    om = 3.0 * nu
+    b = om * (m + e) / (C * C)
+    t_cap = 10.0 / nu
+    nodes = inputs.energy_nodes(64, 1.0, 1e3)
+    ch = [inputs.Channel("elastic", inputs.ELASTIC, inputs.E, -1, 0.0, np.full_like(nodes, sigma))]
+    prob = inputs.uniform_problem(n_m3, 1000.0, 10, ch, n_energy=64, e_min=1.0, e_max=1e3,
+                                  e_cut=0.0, max_lifetime_s=t_cap, max_collisions=10**9)
+    prob.target_mass_ev = 1e18
+    orb = _orbit(b, frac=0.02, tube_radius_m=10.0, n_rbins=4)
+    dt = orb.dt_s[inputs.E]
+    om_eff = 2.0 * math.atan(0.5 * om * dt) / dt
+    n = 20000
+    rng = np.random.default_rng(12)
+    pr = _prims(np.zeros(n), np.zeros(n), np.full(n, 500.0), np.full(n, e),
+                rng.uniform(-1, 1, n), rng.uniform(0, 2 * math.pi, n), inputs.E)
+    t = _gpu(karl, prob, orb, pr, seed=4)
+    r2 = t["end_state"][:, 0] ** 2 + t["end_state"][:, 1] ** 2
+    expect = _msd_closed_form(v, nu, om_eff, t_cap)
+    se = r2.std() / math.sqrt(n)
+    print(f"PARITY orbit diffusion: <r^2> {r2.mean():.5e} closed form {expect:.5e} "
+          f"({(r2.mean() - expect) / se:+.2f} standard errors)")
+    assert abs(r2.mean() - expect) < 5 * se
+
+
+def test_orbit_reproduces_the_guiding_centre_kernel(karl):
+    """Uniform B, no electric field, uniform gas: the full-orbit kernel
+    follows the guiding-centre kernel's histories (the oracle pin's
+    reduction, here between the two CUDA paths)."""
+    prob, prims = inputs.config1(n_primaries=3000, seed=4, density_m3=2e20, length=0.5, nz=50)
+    prims.e_ev[:] = np.linspace(50.0, 600.0, prims.n)
+    orb = _orbit(0.02, frac=0.1, tube_radius_m=5.0, n_rbins=4)
+    rng = np.random.default_rng(9)
+    pr = inputs.OrbitPrimaries(np.zeros(prims.n), np.zeros(prims.n), prims.z_m.copy(),
+                               prims.e_ev.copy(), prims.mu.copy(),
+                               rng.uniform(0, 2 * math.pi, prims.n), prims.species.copy())
+    a = _gpu(karl, prob, orb, pr, seed=7)
+    ctx = karl.Context(prob)
+    try:
+        gc = ctx.run(prims, seed=7)
+    finally:
+        ctx.close()
+    same = float(np.mean(a["per_primary"] == gc["per_primary"]))
+    print(f"PARITY orbit vs guiding-centre kernel: histories identical {same:.4f}")
+    assert same > 0.95
+
+
+def test_orbit_rejects_what_it_does_not_model(karl):
+    """FP32, recombination channels and primaries outside the tube are
+    refused with KARL_EINVAL; the context stays usable."""
+    prob, orb, pr = inputs.orbit_config(n_decays=10, seed=1)
+    ctx = karl.Context(prob)
+    try:
+        with pytest.raises(karl.KarlError) as e:
+            ctx.run_orbit(orb, pr, precision=karl.FP32)
+        assert e.value.status == karl.EINVAL
+        bad = inputs.OrbitPrimaries(pr.x_m.copy(), pr.y_m.copy(), pr.z_m.copy(), pr.e_ev.copy(),
+                                    pr.mu.copy(), pr.phi.copy(), pr.species.copy())
+        bad.x_m[3] = 2 * orb.tube_radius_m
+        with pytest.raises(karl.KarlError) as e:
+            ctx.run_orbit(orb, bad)
+        assert e.value.status == karl.EINVAL
+        t = ctx.run_orbit(orb, pr)
+        assert t["ledger"][karl.OB_N_FLIGHTS] > 0
+    finally:
+        ctx.close()
+    prob2, _ = inputs.config2(n_decays=10)
+    ctx = karl.Context(prob2)
+    try:
+        with pytest.raises(karl.KarlError) as e:
+            ctx.run_orbit(orb, pr)
+        assert e.value.status == karl.EINVAL
+    finally:
+        ctx.close()
