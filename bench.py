@@ -15,7 +15,9 @@ collective on the data path); value = all ranks' collisions / max time.
 At N = 1 the default line also carries bounded measurements of the batched
 form (a batch of config-4 source configurations in one persistent launch)
 and of the served form (Poisson arrivals at 0.7x the measured capacity and
-at 50 requests/s, p50/p99 latency), both in FP32 as their workloads specify.
+at 50 requests/s, p50/p99 latency), both in FP32 as their workloads specify,
+and of the full-orbit (Boris mover) transport of a tube section
+(--workload orbit gives that workload its own line).
 --impl reference times the FP64 CPU oracle on the host cores instead.
 """
 from __future__ import annotations
@@ -40,19 +42,19 @@ BYTES_PER_EVENT_FP32 = 80
 # The transport kernel keeps particle state in registers and is bound by the
 # FP64 pipe (GB300 runs FP64 at 1/64 of FP32: 2 FP64 thread-instructions per
 # SM per cycle).  Work per collision, from ncu captures of the transport
-# kernel (pass 1) on the 1e6-decay case of this workload:
+# kernel (both passes, collision-weighted) on the 1e6-decay case of this
+# workload (profiles/transport_kernel_config2_1e6_counters.md):
 #   FP64_OPS: FP64 add, multiply and fma thread-instructions executed with the
 #     predicate on (smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on);
 #   FP64_PIPE_CYCLES: SM-cycles the FP64 pipe was busy (sm__pipe_fp64_cycles_active),
 #     which also counts the lanes a divergent warp leaves idle;
 #   DRAM_BYTES: dram__bytes_read.sum + dram__bytes_write.sum, scaled to a launch
 #     by its collisions.
-# None: not measured for the kernel as it stands.
-FP64_OPS_PER_COLLISION = {"fp64": 127.4, "fp32": 30.77}
-FP64_PIPE_CYCLES_PER_COLLISION = {"fp64": 113.3, "fp32": 51.4}
-DRAM_BYTES_PER_COLLISION = {"fp64": 185384448 / 1665598248, "fp32": 267528960 / 1665592914}
+FP64_OPS_PER_COLLISION = {"fp64": 120.1, "fp32": 26.29}
+FP64_PIPE_CYCLES_PER_COLLISION = {"fp64": 94.86, "fp32": 33.18}
+DRAM_BYTES_PER_COLLISION = {"fp64": 0.1259, "fp32": 0.2342}
 FP64_OPS_PER_SM_CYCLE = 2
-THREADS_PER_INSTRUCTION = {"fp64": 23.8, "fp32": 21.7}   # smsp__thread_inst_executed_per_inst_executed
+THREADS_PER_INSTRUCTION = {"fp64": 24.2, "fp32": 22.5}   # smsp__thread_inst_executed_per_inst_executed
 WORKLOAD = ("config2: 1e7 decays (1e7 beta e- + 1e7 thermal T2+), parabolic profile with "
             "5e21 m^-2 column, L = 10 m, 1000 z segments, 7 e- channels + T2+ clustering + "
             "e-/ion recombination, two passes")
@@ -388,6 +390,10 @@ def run_ours(args):
         line["cpu_baseline"] = _cpu_baseline(args, os.cpu_count() or 1)
     if args.forms_configs > 0 and world == 1:
         line["batched"], line["served"] = forms_subline(args)
+    if args.orbit_sub_ions > 0 and world == 1:
+        line["orbit"] = orbit_measure(args.orbit_sub_ions, 1, 1, args.timeout,
+                                      0.0 if args.no_cpu_baseline else 5.0)
+        line["orbit"]["workload"] = WORKLOAD_ORBIT
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -577,6 +583,95 @@ def forms_subline(args):
     return batched, served
 
 
+WORKLOAD_ORBIT = ("orbit ions: full-orbit Boris mover at B = 2.5 T with a radial field of "
+                  "2e3 V/m^2 in a 45 mm tube (45 radial bins), 1 m of 5e19 m^-3 T2 in 100 "
+                  "segments; thermal T2+ born over the cross section, T2+ -> T3+ clustering, "
+                  "ion elastic scattering; lifetime cap 1e-4 s (about 3.5e4 steps per ion)")
+# FP64 add/mul/fma thread-instructions per Boris step of the orbit kernel (ncu,
+# profiles/orbit_kernel_tube_counters.md); None until measured
+FP64_OPS_PER_STEP = None
+
+
+def orbit_measure(n_ions: int, steps: int, warmup: int, timeout: float, cpu_seconds: float):
+    """Full-orbit workload: `steps` timed runs of n_ions ions through
+    karl_run_orbit (host buffers, so the wall time includes the copies), the
+    kernel time from CUDA events; the oracle timed on a bounded sample."""
+    from paper_2503_10263_gb300 import inputs, karl
+    prob, orb, pr = inputs.orbit_ion_config(n_ions=n_ions, seed=1)
+    ctx = karl.Context(prob)
+    try:
+        for i in range(warmup):
+            ctx.run_orbit(orb, pr, seed=100 + i, timeout_s=timeout)
+        kms = wall = 0.0
+        nsteps = coll = launches = d2h = 0
+        for i in range(steps):
+            t0 = time.perf_counter()
+            t = ctx.run_orbit(orb, pr, seed=200 + i, timeout_s=timeout)
+            wall += time.perf_counter() - t0
+            d2h = sum(v.nbytes for v in t.values())
+            st = ctx.stats()
+            kms += st.kernel_ms[0]
+            launches += st.kernel_launches
+            nsteps += int(t["ledger"][karl.OB_N_STEPS])
+            coll += int(t["ledger"][karl.OB_N_COLLISIONS])
+    finally:
+        ctx.close()
+    out = {"value": nsteps / (kms / 1000.0), "unit": "Boris steps/s",
+           "collisions_per_s": coll / (kms / 1000.0), "steps_per_run": nsteps / steps,
+           "collisions_per_run": coll / steps, "kernel_launches_per_run": launches / steps,
+           "e2e": {"value": nsteps / wall, "unit": "Boris steps/s",
+                   "h2d_bytes_per_step": pr.n * 49, "d2h_bytes_per_step": d2h},
+           "ions": pr.n}
+    if FP64_OPS_PER_STEP:
+        peak = FP64_OPS_PER_SM_CYCLE * 152 * 2.07e9
+        out["fp64_issue"] = {"achieved": FP64_OPS_PER_STEP * out["value"] / 1e9,
+                             "peak": peak / 1e9, "unit": "G FP64 thread-ops/s",
+                             "frac": FP64_OPS_PER_STEP * out["value"] / peak,
+                             "ops_per_step": FP64_OPS_PER_STEP}
+    if cpu_seconds > 0:
+        import oracle
+        threads = os.cpu_count() or 1
+        m = 64
+        while True:
+            sub = inputs.OrbitPrimaries(*(getattr(pr, k)[:m] for k in
+                                          ("x_m", "y_m", "z_m", "e_ev", "mu", "phi", "species")))
+            t0 = time.perf_counter()
+            o = oracle.orbit_run(prob, orb, sub, seed=200, n_threads=threads)
+            dt = time.perf_counter() - t0
+            if dt > 0.25 * cpu_seconds or 2 * m > pr.n:
+                break
+            m *= 2
+        out["cpu_baseline"] = {"value": float(o["ledger"][oracle.OB_N_STEPS]) / dt,
+                               "unit": "Boris steps/s", "cores": threads, "kind": "oracle",
+                               "sample": f"first {m} primaries of the workload, {dt:.1f} s"}
+    return out
+
+
+def run_orbit_line(args):
+    """--workload orbit: the full-orbit workload's own JSON line."""
+    import torch
+    from paper_2503_10263_gb300 import build as kbuild
+    kbuild.build()
+    torch.cuda.set_device(0)
+    sampler = ClockSampler(0)
+    sampler.start()
+    t0 = time.perf_counter()
+    m = orbit_measure(args.orbit_ions, args.steps, args.warmup, args.timeout,
+                      0.0 if args.no_cpu_baseline else args.cpu_seconds)
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    line = {"metric": "Boris steps/s", "value": m["value"], "unit": "Boris steps/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * wall / max(args.steps + args.warmup, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_ORBIT, "ions": args.orbit_ions,
+                       "l2": "tallies L2-resident; particle state in registers"},
+            "clocks": clocks}
+    line.update({k: v for k, v in m.items() if k != "value"})
+    print(json.dumps(line), flush=True)
+
+
 def run_serve(args):
     """config 5: Poisson arrivals submitted on time into one running launch;
     latency = completion - arrival on the host clock."""
@@ -654,7 +749,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-s", type=float, default=10.0)
-    ap.add_argument("--workload", choices=["config2", "config4", "config5"], default="config2")
+    ap.add_argument("--workload", choices=["config2", "config4", "config5", "orbit"],
+                    default="config2")
+    ap.add_argument("--orbit-ions", type=int, default=1 << 20,
+                    help="ions of the full-orbit workload (--workload orbit)")
+    ap.add_argument("--orbit-sub-ions", type=int, default=1 << 17,
+                    help="ions of the default line's full-orbit measurement (0: leave it out)")
     ap.add_argument("--configs", type=int, default=256)
     ap.add_argument("--budget-gb", type=int, default=48)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -668,13 +768,15 @@ def main():
                     help="config4/config5: also run the requests one at a time through karl_run")
     args = ap.parse_args()
     if args.precision is None:
-        args.precision = "fp64" if args.workload == "config2" else "fp32"
+        args.precision = "fp64" if args.workload in ("config2", "orbit") else "fp32"
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "config4":
         run_batch(args)
     elif args.workload == "config5":
         run_serve(args)
+    elif args.workload == "orbit":
+        run_orbit_line(args)
     else:
         run_ours(args)
 

@@ -977,16 +977,19 @@ int do_pass(const orc_problem* p, const orc_primaries* pr, uint64_t seed, int pa
  * Readings: the relativistic form of the Boris push (the paper's equations with
  * the proper velocity u = gamma v, gamma of the half-accelerated velocity in
  * the rotation); the initial velocity is taken as the half-step velocity; the
- * time of a step goes to the z segment and radial bin of the step's midpoint;
+ * time of a step goes to the z segment and radial bin of the step's midpoint
+ * (segment floor(z n_zbins / L), radial bin floor(r n_rbins / R));
  * the optical depth of a step is the total rate of the midpoint's segment
- * times the step's path length; with no electric field the kinetic energy is
- * a constant of the motion and the cross sections are evaluated once per
- * flight, otherwise at the energy of each step; a step that reaches the
- * drawn optical depth, a z end, the wall or the lifetime cap is shortened to
- * the fraction of its displacement where that happens (first of them; on a
- * tie: wall, z end, lifetime, collision). */
+ * times the step's path length; the cross sections are those of the flight's
+ * starting energy, and with an electric field a flight also ends, without
+ * interaction, after the step in which the kinetic energy leaves its bin of
+ * the time tally's energy grid (Sec. 3.1: the movement stops when the
+ * particle leaves an energy bin of the density fields and a new distance is
+ * drawn); a step that reaches the drawn optical depth, a z end, the wall or
+ * the lifetime cap is shortened to the fraction of its displacement where
+ * that happens (first of them; on a tie: wall, z end, lifetime, collision). */
 const double CHARGE_E[ORC_N_SPECIES] = {-1.0, 1.0, 1.0, 1.0};   /* units of e */
-enum { OEV_NONE = 0, OEV_WALL = 1, OEV_EXIT = 2, OEV_CAP = 3, OEV_COLL = 4 };
+enum { OEV_NONE = 0, OEV_WALL = 1, OEV_EXIT = 2, OEV_CAP = 3, OEV_COLL = 4, OEV_EBIN = 5 };
 
 struct OParticle {
   double x[3];       /* position (m) */
@@ -1035,6 +1038,7 @@ struct OrbitRun {
   const orc_orbit* o;
   uint64_t seed;
   double dz;
+  double inv_dz;     /* n_zbins / L */
   double r_scale;    /* n_rbins / R */
   bool fields;       /* some electric field is present */
   uint64_t max_steps;
@@ -1073,7 +1077,7 @@ struct OWorker {
     philox4x64_10(ctr, key, w);
   }
   int seg(double z) const {
-    int j = (int)std::floor(z / R->dz);
+    int j = (int)std::floor(z * R->inv_dz);
     if (j < 0) j = 0;
     if (j > R->p->n_zbins - 1) j = R->p->n_zbins - 1;
     return j;
@@ -1173,23 +1177,44 @@ struct OWorker {
     const int nz = p->n_zbins, nr = o->n_rbins;
     const double L = p->length_m, R2 = o->tube_radius_m * o->tube_radius_m;
     std::vector<double> coef((size_t)p->n_channels + 1, 0.0);
+    uint64_t redraw = 0;             /* flights ended by an energy-bin change since the last event */
     for (;;) {
       const int s = P.species;
       const double m = p->species_mass_ev[s];
       const double e0 = kinetic_u(P.u, m);
       if (!(e0 > 0.0)) { write_end(es, P); die(P, ORC_OR_STALLED, ORC_OE_STALLED, e0); return; }
+      /* the collision's uniforms come from the event's block; after an
+         energy-bin stop the optical depth is drawn anew from redraw blocks */
       uint64_t w[4];
       block(P.ev, P.node, DOM_EVENT, 0, w);
-      const double tau = -std::log(eta01(w[0]));
+      double tau = -std::log(eta01(w[0]));
+      if (redraw > 0) {
+        uint64_t wr[4];
+        block(P.ev, P.node, DOM_REDRAW, redraw, wr);
+        tau = -std::log(eta01(wr[0]));
+      }
       T.ledger[ORC_OB_N_FLIGHTS] += 1;
       coefficients(s, e0, coef.data());
+      /* the flight's energy bin as bounds on u^2 (with an electric field) */
+      double u2_lo = -1.0, u2_hi = INFINITY;
+      if (R->fields) {
+        const int b = tebin(p, e0), ntb = p->n_tebins;
+        const double ratio = p->e_max_ev / p->e_min_ev;
+        if (b > 0) {
+          const double ps = proper_speed(p->e_min_ev * std::pow(ratio, (double)b / ntb), m);
+          u2_lo = ps * ps;
+        }
+        if (b < ntb - 1) {
+          const double ps = proper_speed(p->e_min_ev * std::pow(ratio, (double)(b + 1) / ntb), m);
+          u2_hi = ps * ps;
+        }
+      }
       const double dt = o->dt_s[s];
       const double h = 0.5 * (CHARGE_E[s] * C_LIGHT * C_LIGHT / m) * dt;   /* q dt / 2m */
       double acc = 0.0;
       int cj = -1, cr = -1;          /* cell of the current run of steps */
       uint64_t cn = 0;
       int event = OEV_NONE, end = -1;
-      double e_step = e0;
       for (uint64_t step = 0;; ++step) {
         if (step >= R->max_steps) {
           flush(s, cj, cr, cn, 0.0, dt);
@@ -1212,15 +1237,11 @@ struct OWorker {
         const double upx = um[0] + um[1] * t, upy = um[1] - um[0] * t;
         double un[3] = {um[0] + upy * sf, um[1] - upx * sf, um[2]};
         for (int i = 0; i < 3; ++i) un[i] += h * ef[i];
-        const double gn = std::sqrt(1.0 + (un[0] * un[0] + un[1] * un[1] + un[2] * un[2]) /
-                                              (C_LIGHT * C_LIGHT));
+        const double u2n = un[0] * un[0] + un[1] * un[1] + un[2] * un[2];
+        const double gn = std::sqrt(1.0 + u2n / (C_LIGHT * C_LIGHT));
         const double sc = dt / gn;
         const double d[3] = {un[0] * sc, un[1] * sc, un[2] * sc};
         const double ds = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        if (R->fields) {
-          e_step = kinetic_u(un, m);
-          coefficients(s, e_step, coef.data());
-        }
         const int jm = seg(x[2] + 0.5 * d[2]);
         const double dtau = step_rate(coef.data(), jm) * ds;
         /* the first of wall, z end, lifetime cap and collision within the step */
@@ -1250,7 +1271,8 @@ struct OWorker {
           double f = std::fmin(1.0, std::fmax(0.0, (tau - acc) / dtau));
           if (event == OEV_NONE ? f <= fb : f < fb) { fb = f; event = OEV_COLL; }
         }
-        if (event == OEV_NONE) {
+        if (event == OEV_NONE && (u2n < u2_lo || u2n >= u2_hi)) event = OEV_EBIN;
+        if (event == OEV_NONE || event == OEV_EBIN) {
           const int mj = jm, mr = rbin(x[0] + 0.5 * d[0], x[1] + 0.5 * d[1]);
           if (mj == cj && mr == cr) {
             cn += 1;
@@ -1264,7 +1286,9 @@ struct OWorker {
           P.t_alive += dt;
           acc += dtau;
           for (int i = 0; i < 3; ++i) P.u[i] = un[i];
-          continue;
+          if (event == OEV_NONE) continue;
+          flush(s, cj, cr, cn, 0.0, dt);       /* left the energy bin: a new flight */
+          break;
         }
         /* the shortened last step */
         const double dp[3] = {fb * d[0], fb * d[1], fb * d[2]};
@@ -1285,6 +1309,7 @@ struct OWorker {
       }
       const double e1 = kinetic_u(P.u, m);
       T.energy[ORC_OE_FIELD_WORK] += e1 - e0;
+      if (event == OEV_EBIN) { ++redraw; continue; }
       if (event == OEV_WALL) {
         T.wall[(size_t)s * nz + seg(P.x[2])] += 1;
         const int ra = rbin(P.x[0], P.x[1]);
@@ -1309,6 +1334,7 @@ struct OWorker {
       /* ---- collision: channel with probability rate_k / rate_tot ---- */
       const int j = seg(P.x[2]);
       P.ev += 1;
+      redraw = 0;
       tree_collisions += 1;
       T.ledger[ORC_OB_N_COLLISIONS] += 1;
       double rtot = rate(coef.data(), j);
@@ -1668,6 +1694,7 @@ int orc_orbit_run(const orc_problem* p, const orc_orbit* o, const orc_orbit_prim
   OrbitRun R;
   R.p = p; R.o = o; R.seed = seed;
   R.dz = p->length_m / p->n_zbins;
+  R.inv_dz = (double)p->n_zbins / p->length_m;
   R.r_scale = (double)o->n_rbins / o->tube_radius_m;
   R.fields = o->e_r_vm2 != 0.0;
   if (o->e_z_vm)

@@ -191,7 +191,7 @@ struct karl_ctx {
   // sums over the cycles of a continuous-update run
   DevBuf<unsigned long long> c_spec, c_time, c_cpos, c_cneg, c_rec, c_led, c_chan, c_pp, d_recin;
   // full-orbit runs: primaries, the lists of two generations, raw tallies
-  DevBuf<double> o_px, o_py, o_pz, o_pe, o_pmu, o_pphi, o_ez, o_energy, o_end;
+  DevBuf<double> o_px, o_py, o_pz, o_pe, o_pmu, o_pphi, o_ez, o_energy, o_end, o_u2edge;
   DevBuf<uint8_t> o_psp, o_lsp[2];
   DevBuf<double> o_lx[2], o_ly[2], o_lz[2], o_lux[2], o_luy[2], o_luz[2];
   DevBuf<unsigned long long> o_lnode[2], o_lpid[2];
@@ -215,6 +215,7 @@ struct karl_ctx {
     f(r_node); f(r_pid); f(r_seq); f(r_ev); f(r_sj); f(d_ctlbuf); f(d_cancelbuf);
     f(c_spec); f(c_time); f(c_cpos); f(c_cneg); f(c_rec); f(c_led); f(c_chan); f(c_pp); f(d_recin);
     f(o_px); f(o_py); f(o_pz); f(o_pe); f(o_pmu); f(o_pphi); f(o_ez); f(o_energy); f(o_end);
+    f(o_u2edge);
     f(o_psp); f(o_tz); f(o_tr); f(o_xp); f(o_xn); f(o_ro); f(o_ri); f(o_wall); f(o_spec);
     f(o_led); f(o_chan); f(o_pp); f(o_cnt); f(o_err);
     for (int g = 0; g < 2; ++g) {
@@ -1634,6 +1635,22 @@ extern "C" karl_status karl_run_orbit(karl_ctx* ctx, const karl_orbit* ob,
   }
   O.e_cut = ctx->e_cut;
   O.spec_bin = ctx->spec_bin;
+  O.inv_dz = (double)ctx->nz / ctx->L;
+  O.e_max = ctx->e_max;
+  // u^2 = (gamma v)^2 at the edges of the energy grid's bins, per species
+  {
+    const int ntb = ctx->ntb;
+    std::vector<double> edge((size_t)NSP * (ntb + 1));
+    const double ratio = ctx->e_max / ctx->e_min;
+    for (int sp = 0; sp < NSP; ++sp)
+      for (int k = 0; k <= ntb; ++k) {
+        const double y = ctx->e_min * std::pow(ratio, (double)k / ntb) / ctx->mass[sp];
+        const double ps = C_LIGHT * std::sqrt(y * (2.0 + y));
+        edge[(size_t)sp * (ntb + 1) + k] = ps * ps;
+      }
+    if ((s = upload(ctx, ctx->o_u2edge, edge.data(), edge.size(), st))) return s;
+    O.u2edge = ctx->o_u2edge.p;
+  }
   O.ez = ob->e_z_vm ? ctx->o_ez.p : nullptr;
   O.nr = ob->n_rbins;
   O.fields = ob->e_r_vm2 != 0.0;

@@ -14,12 +14,14 @@
 // rotation); the initial velocity taken as the half-step velocity; the time
 // of a step booked to the z segment and radial bin of its midpoint, a run of
 // steps in one cell rounded to the time unit once; the optical depth of a step
-// the rate of its midpoint's segment times its path length; without an
-// electric field the cross sections of a flight taken at its starting
-// energy (a constant of the motion), with one at the energy of each step; the
-// step that reaches the drawn optical depth, a z end, the wall or the
-// lifetime cap shortened to that fraction of its displacement (on a tie:
-// wall, z end, lifetime, collision).  Directions turn in the frame of the
+// the rate of its midpoint's segment times its path length; the cross
+// sections those of the flight's starting energy, and with an electric field
+// the flight ended, without interaction, after the step in which the kinetic
+// energy leaves its bin of the time tally's energy grid (Sec. 3.1: a new
+// distance is drawn when the particle leaves an energy bin); the step that
+// reaches the drawn optical depth, a z end, the wall or the lifetime cap
+// shortened to that fraction of its displacement (on a tie: wall, z end,
+// lifetime, collision).  Directions turn in the frame of the
 // unit vector towards +z normal to the old direction, so the pitch update is
 // the guiding-centre one.
 //
@@ -34,7 +36,8 @@ namespace karl {
 
 namespace {
 
-enum { EV_NONE = 0, EV_WALL = 1, EV_EXIT = 2, EV_CAP = 3, EV_COLL = 4 };
+enum { EV_NONE = 0, EV_WALL = 1, EV_EXIT = 2, EV_CAP = 3, EV_COLL = 4, EV_EBIN = 5 };
+constexpr int DOM_REDRAW = 3;          // optical depths drawn anew after an energy-bin stop
 
 struct OPart {
   double x, y, z, ux, uy, uz, t;
@@ -73,8 +76,8 @@ __device__ void turn(double d0, double d1, double d2, double ct, double cp, doub
   o2 = ct * d2 + st * (cp * a2 + sp * b2);
 }
 
-__device__ __forceinline__ int seg_of(const Params& P, double z) {
-  int j = (int)floor(z / P.dz);
+__device__ __forceinline__ int seg_of(const Params& P, const OrbitDev& O, double z) {
+  int j = (int)floor(z * O.inv_dz);
   return j < 0 ? 0 : (j > P.nz - 1 ? P.nz - 1 : j);
 }
 
@@ -184,22 +187,25 @@ __device__ __forceinline__ void flush_run(const Params& P, const OrbitDev& O, in
   atomicAdd(O.time_r + (size_t)s * O.nr + cr, q);
 }
 
-__device__ void crossings(const Params& P, const OrbitDev& O, int s, double ax, double ay,
-                          double az, double bx, double by, double bz) {
+// crossings of z faces and radial bin boundaries by a step from segment ja,
+// radial bin ra to segment jb, radial bin rb
+__device__ void crossings(const Params& P, const OrbitDev& O, int s, int ja, int ra, int jb,
+                          int rb) {
   const int nz = P.nz, nr = O.nr;
-  const int ja = seg_of(P, az), jb = seg_of(P, bz);
   for (int k = ja + 1; k <= jb; ++k) atomicAdd(O.xpos + (size_t)s * (nz + 1) + k, 1ULL);
   for (int k = jb + 1; k <= ja; ++k) atomicAdd(O.xneg + (size_t)s * (nz + 1) + k, 1ULL);
-  const int ra = rbin_of(O, ax, ay), rb = rbin_of(O, bx, by);
   for (int k = ra + 1; k <= rb; ++k) atomicAdd(O.rout + (size_t)s * (nr + 1) + k, 1ULL);
   for (int k = rb + 1; k <= ra; ++k) atomicAdd(O.rin + (size_t)s * (nr + 1) + k, 1ULL);
 }
 
 struct Flight {
-  double tau, acc, e0, e_step, s1, s3;
+  double tau, acc, e0, s1, s3;
+  double u2lo, u2hi;               // the flight's energy bin as bounds on u^2
   unsigned long long step;
-  int cj, cr;
+  int cj, cr;                      // cell of the current run of steps
   unsigned long long cn;
+  int js, rs;                      // segment and radial bin of the particle
+  unsigned redraw;                 // energy-bin stops since the last event
   unsigned long long w1, w2, w3;   // uniforms of the collision
 };
 
@@ -214,27 +220,47 @@ __device__ bool start_flight(const Params& P, const OrbitDev& O, OPart& Q, Fligh
   unsigned long long w[4];
   block4(P, Q.ev, Q.node, DOM_EVENT, 0, Q.pid, w);
   F.tau = -log(eta01d(w[0]));
+  if (F.redraw > 0) {
+    unsigned long long wr[4];
+    block4(P, Q.ev, Q.node, DOM_REDRAW, F.redraw, Q.pid, wr);
+    F.tau = -log(eta01d(wr[0]));
+  }
   F.w1 = w[1]; F.w2 = w[2]; F.w3 = w[3];
   F.acc = 0.0;
-  F.e_step = F.e0;
   rate_sums(P, Q.sp, F.e0, F.s1, F.s3);
+  F.u2lo = -1.0;
+  F.u2hi = INFINITY;
+  if (O.fields) {
+    const int ntb = P.ntb;
+    int b = 0;
+    if (ntb > 1) {
+      const double x = log(F.e0 / P.e_min) / log(O.e_max / P.e_min) * (double)ntb;
+      b = (int)floor(x);
+      b = b < 0 ? 0 : (b > ntb - 1 ? ntb - 1 : b);
+    }
+    const double* edge = O.u2edge + (size_t)Q.sp * (ntb + 1);
+    if (b > 0) F.u2lo = edge[b];
+    if (b < ntb - 1) F.u2hi = edge[b + 1];
+  }
   F.step = 0;
   F.cj = -1; F.cr = -1; F.cn = 0;
+  F.js = seg_of(P, O, Q.z);
+  F.rs = rbin_of(O, Q.x, Q.y);
   atomicAdd(O.ledger + OB_N_FLIGHT, 1ULL);
   return true;
 }
 
 // The collision at the end of a flight (Sec. 3.3 kinematics in three
 // dimensions).  Returns false if the particle ended.
-__device__ bool collide(const Params& P, const OrbitDev& O, OPart& Q, const Flight& F) {
+__device__ bool collide(const Params& P, const OrbitDev& O, OPart& Q, Flight& F) {
   const double TWO_PI = 6.283185307179586476925286766559;
   const int s = Q.sp;
   const double m = P.mass[s];
-  const int j = seg_of(P, Q.z);
+  const int j = seg_of(P, O, Q.z);
   Q.ev += 1;
   atomicAdd(O.ledger + OB_N_COLL, 1ULL);
   const double ec = kinetic_u(Q.ux, Q.uy, Q.uz, m);
-  const double esig = O.fields ? F.e_step : F.e0;
+  const double esig = F.e0;
   const double n = P.nseg[j];
   // channel k with probability rate_k / rate_tot (table order)
   double rtot = 0.0;
@@ -267,6 +293,7 @@ __device__ bool collide(const Params& P, const OrbitDev& O, OPart& Q, const Flig
   const double ph = TWO_PI * u01d(F.w3);
   const double cph = cos(ph), sph = sin(ph);
   const unsigned evc = Q.ev - 1;
+  F.redraw = 0;
   double enew = ec;
   if (cd.kind == ELASTIC) {
     const double g = P.gam[s];
@@ -386,6 +413,7 @@ __global__ void __launch_bounds__(256) orbit_kernel(const Params P, const OrbitD
       const long long i = (long long)atomicAdd(O.counters, 1ULL);
       if (i >= O.n_in) break;
       if (!load(P, O, i, Q)) continue;
+      F.redraw = 0;
       live = start_flight(P, O, Q, F);
       continue;
     }
@@ -404,7 +432,7 @@ __global__ void __launch_bounds__(256) orbit_kernel(const Params P, const OrbitD
     F.step += 1;
     steps += 1;
     // Boris push: half electric kick, magnetic rotation, half kick
-    const double ex = O.er * Q.x, ey = O.er * Q.y, ez = O.ez ? O.ez[seg_of(P, Q.z)] : 0.0;
+    const double ex = O.er * Q.x, ey = O.er * Q.y, ez = O.ez ? O.ez[F.js] : 0.0;
     const double umx = Q.ux + h * ex, umy = Q.uy + h * ey, umz = Q.uz + h * ez;
     const double gm = sqrt(1.0 + (umx * umx + umy * umy + umz * umz) / (C_LIGHT * C_LIGHT));
     const double t = h * O.bz / gm;
@@ -413,15 +441,12 @@ __global__ void __launch_bounds__(256) orbit_kernel(const Params P, const OrbitD
     const double unx = umx + upy * sf + h * ex;
     const double uny = umy - upx * sf + h * ey;
     const double unz = umz + h * ez;
-    const double gn = sqrt(1.0 + (unx * unx + uny * uny + unz * unz) / (C_LIGHT * C_LIGHT));
+    const double u2n = unx * unx + uny * uny + unz * unz;
+    const double gn = sqrt(1.0 + u2n / (C_LIGHT * C_LIGHT));
     const double sc = dt / gn;
     const double dx = unx * sc, dy = uny * sc, dz = unz * sc;
     const double ds = sqrt(dx * dx + dy * dy + dz * dz);
-    if (O.fields) {
-      F.e_step = kinetic_u(unx, uny, unz, m);
-      rate_sums(P, s, F.e_step, F.s1, F.s3);
-    }
-    const int jm = seg_of(P, Q.z + 0.5 * dz);
+    const int jm = seg_of(P, O, Q.z + 0.5 * dz);
     const double nm = P.nseg[jm];
     const double dtau = (F.s1 * nm + F.s3 * (nm * nm)) * ds;
     // the first of wall, z end, lifetime cap and collision within the step
@@ -450,7 +475,8 @@ __global__ void __launch_bounds__(256) orbit_kernel(const Params P, const OrbitD
       const double f = fmin(1.0, fmax(0.0, (F.tau - F.acc) / dtau));
       if (event == EV_NONE ? f <= fb : f < fb) { fb = f; event = EV_COLL; }
     }
-    if (event == EV_NONE) {
+    if (event == EV_NONE && (u2n < F.u2lo || u2n >= F.u2hi)) event = EV_EBIN;
+    if (event == EV_NONE || event == EV_EBIN) {
       const int mr = rbin_of(O, Q.x + 0.5 * dx, Q.y + 0.5 * dy);
       if (jm == F.cj && mr == F.cr) {
         F.cn += 1;
@@ -458,17 +484,27 @@ __global__ void __launch_bounds__(256) orbit_kernel(const Params P, const OrbitD
         flush_run(P, O, s, F.cj, F.cr, F.cn, 0.0, dt);
         F.cj = jm; F.cr = mr; F.cn = 1;
       }
-      if (seg_of(P, zn) != seg_of(P, Q.z) || rbin_of(O, xn, yn) != rbin_of(O, Q.x, Q.y))
-        crossings(P, O, s, Q.x, Q.y, Q.z, xn, yn, zn);
+      const int jb = seg_of(P, O, zn), rb = rbin_of(O, xn, yn);
+      if (jb != F.js || rb != F.rs) {
+        crossings(P, O, s, F.js, F.rs, jb, rb);
+        F.js = jb;
+        F.rs = rb;
+      }
       Q.x = xn; Q.y = yn; Q.z = zn;
       Q.t += dt;
       F.acc += dtau;
       Q.ux = unx; Q.uy = uny; Q.uz = unz;
+      if (event == EV_NONE) continue;
+      // left the energy bin: the run's time, then a new flight
+      flush_run(P, O, s, F.cj, F.cr, F.cn, 0.0, dt);
+      atomicAdd(O.energy + OE_FIELD_WORK, kinetic_u(Q.ux, Q.uy, Q.uz, m) - F.e0);
+      F.redraw += 1;
+      live = start_flight(P, O, Q, F);
       continue;
     }
     // the shortened last step of the flight
     const double px = fb * dx, py = fb * dy, pz = fb * dz;
-    const int mj = seg_of(P, Q.z + 0.5 * pz), mr = rbin_of(O, Q.x + 0.5 * px, Q.y + 0.5 * py);
+    const int mj = seg_of(P, O, Q.z + 0.5 * pz), mr = rbin_of(O, Q.x + 0.5 * px, Q.y + 0.5 * py);
     if (mj == F.cj && mr == F.cr) {
       flush_run(P, O, s, F.cj, F.cr, F.cn, fb, dt);
     } else {
@@ -477,14 +513,14 @@ __global__ void __launch_bounds__(256) orbit_kernel(const Params P, const OrbitD
     }
     const double bx = Q.x + px, by = Q.y + py;
     const double bz = event == EV_EXIT ? (end == 0 ? 0.0 : L) : Q.z + pz;
-    crossings(P, O, s, Q.x, Q.y, Q.z, bx, by, bz);
+    crossings(P, O, s, F.js, F.rs, seg_of(P, O, bz), rbin_of(O, bx, by));
     Q.x = bx; Q.y = by; Q.z = bz;
     Q.t = event == EV_CAP ? P.max_life : Q.t + fb * dt;
     Q.ux = unx; Q.uy = uny; Q.uz = unz;
     const double e1 = kinetic_u(Q.ux, Q.uy, Q.uz, m);
     atomicAdd(O.energy + OE_FIELD_WORK, e1 - F.e0);
     if (event == EV_WALL) {
-      atomicAdd(O.wall + (size_t)s * P.nz + seg_of(P, Q.z), 1ULL);
+      atomicAdd(O.wall + (size_t)s * P.nz + seg_of(P, O, Q.z), 1ULL);
       const int ra = rbin_of(O, Q.x, Q.y);
       for (int k = ra + 1; k <= O.nr; ++k) atomicAdd(O.rout + (size_t)s * (O.nr + 1) + k, 1ULL);
       die(P, O, Q, OR_WALL, OE_WALL, e1);

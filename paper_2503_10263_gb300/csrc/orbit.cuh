@@ -45,6 +45,9 @@ struct OrbitDev {
   double dt[NSP];               // Boris time step per species
   double h[NSP];                // q dt / 2m per species (m/s per V/m)
   double e_cut, spec_bin;       // energies in eV
+  double inv_dz;                // n_zbins / L (segment of z: floor(z inv_dz))
+  double e_max;                 // top of the energy grid (eV)
+  const double* u2edge;         // [4][n_tebins+1] u^2 at the energy-bin edges
   const double* ez;             // [nz] axial field per segment (V/m), NULL: none
   int nr;                       // radial bins
   int fields;                   // an electric field is present

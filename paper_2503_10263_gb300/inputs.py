@@ -618,3 +618,32 @@ def orbit_config(n_decays: int = 100_000, seed: int = 1, length: float = 1.0, nz
     prims = OrbitPrimaries(r * np.cos(a), r * np.sin(a), z, e, isotropic_mu(rng, n),
                            rng.uniform(0.0, 2.0 * math.pi, n), sp)
     return prob, orbit, prims
+
+
+def orbit_ion_config(n_ions: int = 1 << 20, seed: int = 1, length: float = 1.0, nz: int = 100,
+                     density_m3: float = 5e19, b_t: float = 2.5, tube_radius_m: float = 0.045,
+                     n_rbins: int = 45, e_r_vm2: float = 2e3, lifetime_s: float = 1e-4):
+    """Ions in a tube section for the full-orbit mover at the Sec. 5 field
+    (B = 2.5 T): thermal T2+ born uniformly over the cross section and along
+    z, isotropic, in uniform T2 gas; T2+ -> T3+ clustering and ion elastic
+    scattering; a 45 mm tube with a radial field (E x B rotation of about
+    800 rad/s); the lifetime cap of 1e-4 s bounds every history to about
+    4e4 Boris steps, so the histories are of similar length."""
+    nodes = energy_nodes(64, 1e-5, 100.0)
+    chans = [Channel("clustering_T2+", CLUSTERING, T2P, T3P, 0.0, np.full_like(nodes, 1.91e-18))]
+    chans += ion_elastic_channels(nodes)
+    prob = uniform_problem(density_m3, length, nz, chans, n_energy=64, e_min=1e-5, e_max=100.0,
+                           e_cut=0.0, max_lifetime_s=lifetime_s, n_spec_bins=1000,
+                           spec_bin_ev=1e-3)
+    prob.name = "orbit_ions"
+    prob.b_tesla = b_t
+    orbit = Orbit(b_t=b_t, tube_radius_m=tube_radius_m, n_rbins=n_rbins, dt_s=boris_dt(b_t),
+                  e_r_vm2=e_r_vm2)
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 7]))
+    r = tube_radius_m * np.sqrt(rng.uniform(0.0, 1.0, n_ions))
+    a = rng.uniform(0.0, 2.0 * math.pi, n_ions)
+    prims = OrbitPrimaries(r * np.cos(a), r * np.sin(a), rng.uniform(0.0, length, n_ions),
+                           sample_thermal_energy(rng, n_ions, prob.gas_temperature_k),
+                           isotropic_mu(rng, n_ions), rng.uniform(0.0, 2.0 * math.pi, n_ions),
+                           np.full(n_ions, T2P, np.uint8))
+    return prob, orbit, prims

@@ -200,3 +200,37 @@ def test_orbit_rejects_what_it_does_not_model(karl):
         assert e.value.status == karl.EINVAL
     finally:
         ctx.close()
+
+
+def test_energy_bin_restarts_on_the_gpu(karl):
+    """The Sec. 3.1 stop rule: an electron accelerated from 100 eV to 1100 eV
+    flies once per energy bin it passes (17 flights over 64 log bins)."""
+    nodes = inputs.energy_nodes(64, 1.0, 2e4)
+    ch = [inputs.Channel("elastic", inputs.ELASTIC, inputs.E, -1, 0.0, np.full_like(nodes, 1e-20))]
+    prob = inputs.uniform_problem(0.0, 1.0, 10, ch, n_energy=64, e_min=1.0, e_max=2e4,
+                                  e_cut=0.0, n_tebins=64, n_spec_bins=4000, spec_bin_ev=1.0)
+    orb = _orbit(0.5, tube_radius_m=0.05, n_rbins=5, e_z_vm=np.full(prob.n_zbins, -1000.0))
+    pr = _prims([0.0], [0.0], [0.0], [100.0], [1.0], [0.0], inputs.E)
+    t = _gpu(karl, prob, orb, pr)
+    o = oracle.orbit_run(prob, orb, pr)
+    assert int(t["ledger"][karl.OB_N_FLIGHTS]) == int(o["ledger"][oracle.OB_N_FLIGHTS]) == 17
+    assert np.array_equal(t["time_z"], o["time_z"])
+
+
+def test_ion_workload_follows_the_oracle(karl):
+    """The ion tube workload of the benchmark (B = 2.5 T, radial field,
+    clustering and ion scattering, lifetime cap): matched histories and
+    equal tallies up to the parting histories."""
+    prob, orb, pr = inputs.orbit_ion_config(n_ions=3000, seed=5)
+    g = _gpu(karl, prob, orb, pr, seed=5)
+    o = oracle.orbit_run(prob, orb, pr, seed=5, n_threads=THREADS)
+    same = float(np.mean(g["per_primary"] == o["per_primary"]))
+    print(f"PARITY orbit ions: histories identical {same:.4f} of {pr.n}")
+    assert same >= 0.99
+    end_same = float(np.mean(np.all(np.abs(g["end_state"] - o["end_state"]) <=
+                                    1e-9 * (np.abs(o["end_state"]) + 1e-12), axis=1)))
+    print(f"PARITY orbit ions: end states equal to 1e-9 {end_same:.4f}")
+    assert end_same >= 0.99
+    for key in ("time_z", "time_r"):
+        a, b = g[key].astype(float), o[key].astype(float)
+        assert np.abs(a - b).sum() <= 0.01 * b.sum()

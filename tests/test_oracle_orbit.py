@@ -265,3 +265,20 @@ def test_orbit_reproduces_guiding_centre_histories():
     assert abs(sa.sum() - sg.sum()) <= 3 * math.sqrt(sa.sum() + sg.sum())
     ta, tg = a["time_z"][inputs.E].astype(float), g["time_fx"][inputs.E, 1:-1, 0].astype(float)
     assert abs(ta.sum() - tg.sum()) < 0.02 * tg.sum()
+
+
+def test_flight_restarts_at_each_energy_bin():
+    """With an electric field a flight ends when the kinetic energy leaves its
+    bin of the time tally's energy grid and a new distance is drawn (Sec. 3.1
+    stop rule): an electron accelerated from 100 eV to 1100 eV through
+    vacuum over 64 log bins of [1 eV, 20 keV] flies once per bin it passes."""
+    m = inputs.ME_EV
+    nodes = inputs.energy_nodes(64, 1.0, 2e4)
+    ch = [inputs.Channel("elastic", inputs.ELASTIC, inputs.E, -1, 0.0, np.full_like(nodes, 1e-20))]
+    prob = inputs.uniform_problem(0.0, 1.0, 10, ch, n_energy=64, e_min=1.0, e_max=2e4,
+                                  e_cut=0.0, n_tebins=64, n_spec_bins=4000, spec_bin_ev=1.0)
+    orb = _orbit(0.5, tube_radius_m=0.05, n_rbins=5, e_z_vm=np.full(prob.n_zbins, -1000.0))
+    t = oracle.orbit_run(prob, orb, _prims([0.0], [0.0], [0.0], [100.0], [1.0], [0.0], inputs.E))
+    b = [math.floor(math.log(e) / math.log(2e4) * 64) for e in (100.0, 1100.0)]
+    assert int(t["ledger"][oracle.OB_N_FLIGHTS]) == b[1] - b[0] + 1 == 17
+    assert abs(t["energy"][oracle.OE_EXIT1] - 1100.0) < 0.11
