@@ -587,17 +587,20 @@ WORKLOAD_ORBIT = ("orbit ions: full-orbit Boris mover at B = 2.5 T with a radial
                   "2e3 V/m^2 in a 45 mm tube (45 radial bins), 1 m of 5e19 m^-3 T2 in 100 "
                   "segments; thermal T2+ born over the cross section, T2+ -> T3+ clustering, "
                   "ion elastic scattering; lifetime cap 1e-4 s (about 3.5e4 steps per ion)")
-# FP64 add/mul/fma thread-instructions per Boris step of the orbit kernel (ncu,
-# profiles/orbit_kernel_tube_counters.md); None until measured
-FP64_OPS_PER_STEP = None
+# Per Boris step of the orbit kernel (ncu, profiles/orbit_kernel_ions_counters.md):
+# FP64 add/mul/fma thread-instructions with the predicate on, and SM-cycles
+# the FP64 pipe was busy
+FP64_OPS_PER_STEP = 117.1
+FP64_PIPE_CYCLES_PER_STEP = 99.3
 
 
-def orbit_measure(n_ions: int, steps: int, warmup: int, timeout: float, cpu_seconds: float):
+def orbit_measure(n_ions: int, steps: int, warmup: int, timeout: float, cpu_seconds: float,
+                  lifetime_s: float = 1e-4):
     """Full-orbit workload: `steps` timed runs of n_ions ions through
     karl_run_orbit (host buffers, so the wall time includes the copies), the
     kernel time from CUDA events; the oracle timed on a bounded sample."""
     from paper_2503_10263_gb300 import inputs, karl
-    prob, orb, pr = inputs.orbit_ion_config(n_ions=n_ions, seed=1)
+    prob, orb, pr = inputs.orbit_ion_config(n_ions=n_ions, seed=1, lifetime_s=lifetime_s)
     ctx = karl.Context(prob)
     try:
         for i in range(warmup):
@@ -622,12 +625,16 @@ def orbit_measure(n_ions: int, steps: int, warmup: int, timeout: float, cpu_seco
            "e2e": {"value": nsteps / wall, "unit": "Boris steps/s",
                    "h2d_bytes_per_step": pr.n * 49, "d2h_bytes_per_step": d2h},
            "ions": pr.n}
-    if FP64_OPS_PER_STEP:
-        peak = FP64_OPS_PER_SM_CYCLE * 152 * 2.07e9
-        out["fp64_issue"] = {"achieved": FP64_OPS_PER_STEP * out["value"] / 1e9,
-                             "peak": peak / 1e9, "unit": "G FP64 thread-ops/s",
-                             "frac": FP64_OPS_PER_STEP * out["value"] / peak,
-                             "ops_per_step": FP64_OPS_PER_STEP}
+    # the orbit kernel is bound by the FP64 pipe: "alu" roofline against the
+    # FP64 issue rate of 2 thread-instructions per SM per cycle at 2.07 GHz
+    peak = FP64_OPS_PER_SM_CYCLE * 152 * 2.07e9
+    out["roofline"] = {"bound": "alu", "achieved": FP64_OPS_PER_STEP * out["value"] / 1e9,
+                       "peak": peak / 1e9, "unit": "G FP64 thread-ops/s",
+                       "frac": FP64_OPS_PER_STEP * out["value"] / peak,
+                       "ops_per_step": FP64_OPS_PER_STEP, "kernel": "karl::orbit_kernel",
+                       "traffic": None,
+                       "fp64_pipe_busy_frac": FP64_PIPE_CYCLES_PER_STEP * out["value"] /
+                       (152 * 2.07e9)}
     if cpu_seconds > 0:
         import oracle
         threads = os.cpu_count() or 1
@@ -657,7 +664,7 @@ def run_orbit_line(args):
     sampler.start()
     t0 = time.perf_counter()
     m = orbit_measure(args.orbit_ions, args.steps, args.warmup, args.timeout,
-                      0.0 if args.no_cpu_baseline else args.cpu_seconds)
+                      0.0 if args.no_cpu_baseline else args.cpu_seconds, args.orbit_lifetime)
     wall = time.perf_counter() - t0
     clocks = sampler.stop()
     line = {"metric": "Boris steps/s", "value": m["value"], "unit": "Boris steps/s",
@@ -666,6 +673,7 @@ def run_orbit_line(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD_ORBIT, "ions": args.orbit_ions,
+                       "lifetime_s": args.orbit_lifetime,
                        "l2": "tallies L2-resident; particle state in registers"},
             "clocks": clocks}
     line.update({k: v for k, v in m.items() if k != "value"})
@@ -753,6 +761,8 @@ def main():
                     default="config2")
     ap.add_argument("--orbit-ions", type=int, default=1 << 20,
                     help="ions of the full-orbit workload (--workload orbit)")
+    ap.add_argument("--orbit-lifetime", type=float, default=1e-4,
+                    help="lifetime cap of the full-orbit workload (shorter: a small profiling case)")
     ap.add_argument("--orbit-sub-ions", type=int, default=1 << 17,
                     help="ions of the default line's full-orbit measurement (0: leave it out)")
     ap.add_argument("--configs", type=int, default=256)

@@ -978,7 +978,8 @@ int do_pass(const orc_problem* p, const orc_primaries* pr, uint64_t seed, int pa
  * the proper velocity u = gamma v, gamma of the half-accelerated velocity in
  * the rotation); the initial velocity is taken as the half-step velocity; the
  * time of a step goes to the z segment and radial bin of the step's midpoint
- * (segment floor(z n_zbins / L), radial bin floor(r n_rbins / R));
+ * (segment floor(z n_zbins / L); radial bin k for (k R / n_rbins)^2 <= x^2 + y^2
+ * < ((k + 1) R / n_rbins)^2, the last bin open above);
  * the optical depth of a step is the total rate of the midpoint's segment
  * times the step's path length; the cross sections are those of the flight's
  * starting energy, and with an electric field a flight also ends, without
@@ -989,6 +990,7 @@ int do_pass(const orc_problem* p, const orc_primaries* pr, uint64_t seed, int pa
  * the lifetime cap is shortened to the fraction of its displacement where
  * that happens (first of them; on a tie: wall, z end, lifetime, collision). */
 const double CHARGE_E[ORC_N_SPECIES] = {-1.0, 1.0, 1.0, 1.0};   /* units of e */
+const double INV_C2 = 1.0 / (C_LIGHT * C_LIGHT);
 enum { OEV_NONE = 0, OEV_WALL = 1, OEV_EXIT = 2, OEV_CAP = 3, OEV_COLL = 4, OEV_EBIN = 5 };
 
 struct OParticle {
@@ -1040,6 +1042,7 @@ struct OrbitRun {
   double dz;
   double inv_dz;     /* n_zbins / L */
   double r_scale;    /* n_rbins / R */
+  std::vector<double> edge2;   /* [n_rbins + 1] squared radii of the radial bin edges */
   bool fields;       /* some electric field is present */
   uint64_t max_steps;
 };
@@ -1083,9 +1086,13 @@ struct OWorker {
     return j;
   }
   int rbin(double x, double y) const {
-    int b = (int)std::floor(std::sqrt(x * x + y * y) * R->r_scale);
+    const double q = x * x + y * y;
+    const int nr = R->o->n_rbins;
+    int b = (int)std::floor(std::sqrt(q) * R->r_scale);     /* a first guess */
     if (b < 0) b = 0;
-    if (b > R->o->n_rbins - 1) b = R->o->n_rbins - 1;
+    if (b > nr - 1) b = nr - 1;
+    while (b > 0 && R->edge2[b] > q) --b;
+    while (b < nr - 1 && R->edge2[b + 1] <= q) ++b;
     return b;
   }
   void die(const OParticle& P, int reason, int eslot, double e) {
@@ -1230,15 +1237,14 @@ struct OWorker {
                               o->e_z_vm ? o->e_z_vm[seg(x[2])] : 0.0};
         double um[3];
         for (int i = 0; i < 3; ++i) um[i] = P.u[i] + h * ef[i];
-        const double gm = std::sqrt(1.0 + (um[0] * um[0] + um[1] * um[1] + um[2] * um[2]) /
-                                              (C_LIGHT * C_LIGHT));
+        const double gm = std::sqrt(1.0 + (um[0] * um[0] + um[1] * um[1] + um[2] * um[2]) * INV_C2);
         const double t = h * o->b_t / gm;
         const double sf = 2.0 * t / (1.0 + t * t);
         const double upx = um[0] + um[1] * t, upy = um[1] - um[0] * t;
         double un[3] = {um[0] + upy * sf, um[1] - upx * sf, um[2]};
         for (int i = 0; i < 3; ++i) un[i] += h * ef[i];
         const double u2n = un[0] * un[0] + un[1] * un[1] + un[2] * un[2];
-        const double gn = std::sqrt(1.0 + u2n / (C_LIGHT * C_LIGHT));
+        const double gn = std::sqrt(1.0 + u2n * INV_C2);
         const double sc = dt / gn;
         const double d[3] = {un[0] * sc, un[1] * sc, un[2] * sc};
         const double ds = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
@@ -1696,6 +1702,11 @@ int orc_orbit_run(const orc_problem* p, const orc_orbit* o, const orc_orbit_prim
   R.dz = p->length_m / p->n_zbins;
   R.inv_dz = (double)p->n_zbins / p->length_m;
   R.r_scale = (double)o->n_rbins / o->tube_radius_m;
+  R.edge2.resize((size_t)o->n_rbins + 1);
+  for (int k = 0; k <= o->n_rbins; ++k) {
+    const double rk = o->tube_radius_m * (double)k / (double)o->n_rbins;
+    R.edge2[k] = rk * rk;
+  }
   R.fields = o->e_r_vm2 != 0.0;
   if (o->e_z_vm)
     for (int j = 0; j < p->n_zbins; ++j) R.fields = R.fields || o->e_z_vm[j] != 0.0;

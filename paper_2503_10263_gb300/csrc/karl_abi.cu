@@ -191,7 +191,8 @@ struct karl_ctx {
   // sums over the cycles of a continuous-update run
   DevBuf<unsigned long long> c_spec, c_time, c_cpos, c_cneg, c_rec, c_led, c_chan, c_pp, d_recin;
   // full-orbit runs: primaries, the lists of two generations, raw tallies
-  DevBuf<double> o_px, o_py, o_pz, o_pe, o_pmu, o_pphi, o_ez, o_energy, o_end, o_u2edge;
+  DevBuf<double> o_px, o_py, o_pz, o_pe, o_pmu, o_pphi, o_ez, o_energy, o_end, o_u2edge,
+      o_edge2;
   DevBuf<uint8_t> o_psp, o_lsp[2];
   DevBuf<double> o_lx[2], o_ly[2], o_lz[2], o_lux[2], o_luy[2], o_luz[2];
   DevBuf<unsigned long long> o_lnode[2], o_lpid[2];
@@ -215,7 +216,7 @@ struct karl_ctx {
     f(r_node); f(r_pid); f(r_seq); f(r_ev); f(r_sj); f(d_ctlbuf); f(d_cancelbuf);
     f(c_spec); f(c_time); f(c_cpos); f(c_cneg); f(c_rec); f(c_led); f(c_chan); f(c_pp); f(d_recin);
     f(o_px); f(o_py); f(o_pz); f(o_pe); f(o_pmu); f(o_pphi); f(o_ez); f(o_energy); f(o_end);
-    f(o_u2edge);
+    f(o_u2edge); f(o_edge2);
     f(o_psp); f(o_tz); f(o_tr); f(o_xp); f(o_xn); f(o_ro); f(o_ri); f(o_wall); f(o_spec);
     f(o_led); f(o_chan); f(o_pp); f(o_cnt); f(o_err);
     for (int g = 0; g < 2; ++g) {
@@ -1650,6 +1651,15 @@ extern "C" karl_status karl_run_orbit(karl_ctx* ctx, const karl_orbit* ob,
       }
     if ((s = upload(ctx, ctx->o_u2edge, edge.data(), edge.size(), st))) return s;
     O.u2edge = ctx->o_u2edge.p;
+    // squared radii of the radial bin edges
+    std::vector<double> e2((size_t)ob->n_rbins + 1);
+    for (int k = 0; k <= ob->n_rbins; ++k) {
+      const double rk = ob->tube_radius_m * (double)k / (double)ob->n_rbins;
+      e2[k] = rk * rk;
+    }
+    if ((s = upload(ctx, ctx->o_edge2, e2.data(), e2.size(), st))) return s;
+    O.edge2 = ctx->o_edge2.p;
+    CK(cudaStreamSynchronize(st));        // the host tables above go out of scope
   }
   O.ez = ob->e_z_vm ? ctx->o_ez.p : nullptr;
   O.nr = ob->n_rbins;

@@ -12,7 +12,9 @@
 // Readings (the same as the CPU oracle's): the relativistic Boris push (the
 // paper's equations with u = gamma v, gamma of the half-kicked velocity in the
 // rotation); the initial velocity taken as the half-step velocity; the time
-// of a step booked to the z segment and radial bin of its midpoint, a run of
+// of a step booked to the z segment and radial bin of its midpoint (segment
+// floor(z n_zbins / L); radial bin k for (k R / n_rbins)^2 <= x^2 + y^2 <
+// ((k + 1) R / n_rbins)^2, the last bin open above), a run of
 // steps in one cell rounded to the time unit once; the optical depth of a step
 // the rate of its midpoint's segment times its path length; the cross
 // sections those of the flight's starting energy, and with an electric field
@@ -38,6 +40,7 @@ namespace {
 
 enum { EV_NONE = 0, EV_WALL = 1, EV_EXIT = 2, EV_CAP = 3, EV_COLL = 4, EV_EBIN = 5 };
 constexpr int DOM_REDRAW = 3;          // optical depths drawn anew after an energy-bin stop
+constexpr double INV_C2 = 1.0 / (C_LIGHT * C_LIGHT);
 
 struct OPart {
   double x, y, z, ux, uy, uz, t;
@@ -81,9 +84,18 @@ __device__ __forceinline__ int seg_of(const Params& P, const OrbitDev& O, double
   return j < 0 ? 0 : (j > P.nz - 1 ? P.nz - 1 : j);
 }
 
+// radial bin of (x, y), searched from the bin b (the particle's bin, or a guess)
+__device__ __forceinline__ int rbin_from(const OrbitDev& O, double x, double y, int b) {
+  const double q = x * x + y * y;
+  while (b > 0 && __ldg(O.edge2 + b) > q) --b;
+  while (b < O.nr - 1 && __ldg(O.edge2 + b + 1) <= q) ++b;
+  return b;
+}
+
 __device__ __forceinline__ int rbin_of(const OrbitDev& O, double x, double y) {
   int b = (int)floor(sqrt(x * x + y * y) * O.r_scale);
-  return b < 0 ? 0 : (b > O.nr - 1 ? O.nr - 1 : b);
+  b = b < 0 ? 0 : (b > O.nr - 1 ? O.nr - 1 : b);
+  return rbin_from(O, x, y, b);
 }
 
 // cross section of channel k at energy e: linear in ln e between nodes, zero
@@ -434,7 +446,7 @@ __global__ void __launch_bounds__(256) orbit_kernel(const Params P, const OrbitD
     // Boris push: half electric kick, magnetic rotation, half kick
     const double ex = O.er * Q.x, ey = O.er * Q.y, ez = O.ez ? O.ez[F.js] : 0.0;
     const double umx = Q.ux + h * ex, umy = Q.uy + h * ey, umz = Q.uz + h * ez;
-    const double gm = sqrt(1.0 + (umx * umx + umy * umy + umz * umz) / (C_LIGHT * C_LIGHT));
+    const double gm = sqrt(1.0 + (umx * umx + umy * umy + umz * umz) * INV_C2);
     const double t = h * O.bz / gm;
     const double sf = 2.0 * t / (1.0 + t * t);
     const double upx = umx + umy * t, upy = umy - umx * t;
@@ -442,7 +454,7 @@ __global__ void __launch_bounds__(256) orbit_kernel(const Params P, const OrbitD
     const double uny = umy - upx * sf + h * ey;
     const double unz = umz + h * ez;
     const double u2n = unx * unx + uny * uny + unz * unz;
-    const double gn = sqrt(1.0 + u2n / (C_LIGHT * C_LIGHT));
+    const double gn = sqrt(1.0 + u2n * INV_C2);
     const double sc = dt / gn;
     const double dx = unx * sc, dy = uny * sc, dz = unz * sc;
     const double ds = sqrt(dx * dx + dy * dy + dz * dz);
@@ -477,14 +489,14 @@ __global__ void __launch_bounds__(256) orbit_kernel(const Params P, const OrbitD
     }
     if (event == EV_NONE && (u2n < F.u2lo || u2n >= F.u2hi)) event = EV_EBIN;
     if (event == EV_NONE || event == EV_EBIN) {
-      const int mr = rbin_of(O, Q.x + 0.5 * dx, Q.y + 0.5 * dy);
+      const int mr = rbin_from(O, Q.x + 0.5 * dx, Q.y + 0.5 * dy, F.rs);
       if (jm == F.cj && mr == F.cr) {
         F.cn += 1;
       } else {
         flush_run(P, O, s, F.cj, F.cr, F.cn, 0.0, dt);
         F.cj = jm; F.cr = mr; F.cn = 1;
       }
-      const int jb = seg_of(P, O, zn), rb = rbin_of(O, xn, yn);
+      const int jb = seg_of(P, O, zn), rb = rbin_from(O, xn, yn, F.rs);
       if (jb != F.js || rb != F.rs) {
         crossings(P, O, s, F.js, F.rs, jb, rb);
         F.js = jb;

@@ -40,7 +40,8 @@ struct OrbitList {
 struct OrbitDev {
   double bz;                    // magnetic field along +z (T)
   double R2;                    // wall radius squared
-  double r_scale;               // radial bins per metre
+  double r_scale;               // radial bins per metre (first guess of a bin)
+  const double* edge2;          // [nr+1] squared radii of the radial bin edges
   double er;                    // radial field per metre (V/m^2)
   double dt[NSP];               // Boris time step per species
   double h[NSP];                // q dt / 2m per species (m/s per V/m)
