@@ -12,7 +12,8 @@ primaries/s and flights/s are reported beside it.
 Rank 0 prints one JSON line.  With N > 1 (torchrun) every rank runs its own
 replica of the workload with its own primary ids (weak scaling, no
 collective on the data path); value = all ranks' collisions / max time.
-At N = 1 the default line also carries bounded measurements of the batched
+At N = 1 the default line also carries the FP32 precision form's rate on the
+same workload (one timed step), bounded measurements of the batched
 form (a batch of config-4 source configurations in one persistent launch)
 and of the served form (Poisson arrivals at 0.7x the measured capacity and
 at 50 requests/s, p50/p99 latency), both in FP32 as their workloads specify,
@@ -386,6 +387,28 @@ def run_ours(args):
         "e2e": e2e,
         "clocks": clocks,
     }
+    if args.other_precision and world == 1:
+        # the same workload in the other form (FP32 beside the FP64 line), one
+        # warm-up step and one timed step, device buffers, CUDA-event kernel time
+        other = karl.FP64 if prec == karl.FP32 else karl.FP32
+        oname = "fp64" if other == karl.FP64 else "fp32"
+        ctx.run_device(pptr, n, prims.n_decays, optr, seed=7000, precision=other,
+                       stream=stream.cuda_stream, timeout_s=args.timeout)
+        ctx.run_device(pptr, n, prims.n_decays, optr, seed=7001, precision=other,
+                       stream=stream.cuda_stream, timeout_s=args.timeout)
+        so = ctx.stats()
+        oc = [int(so.collisions[0]), int(so.collisions[1])]
+        om = [float(so.kernel_ms[0]), float(so.kernel_ms[1])]
+        line[oname] = {"value": sum(oc) / (sum(om) / 1000.0), "unit": "collision events/s",
+                       "transport_kernel_ms": om, "collisions_per_launch": oc,
+                       "ns_per_collision_by_pass": [round(1e6 * om[i] / max(oc[i], 1), 4)
+                                                    for i in range(2)],
+                       "lane_occupancy": [round(x, 4) for x in so.lane_occupancy],
+                       "fp64_ops_per_collision": FP64_OPS_PER_COLLISION[oname],
+                       "roofline": {"bound": "hbm", "frac": (BYTES_PER_EVENT_FP32 if oname == "fp32"
+                                                             else BYTES_PER_EVENT_FP64)
+                                    * sum(oc) / (sum(om) / 1000.0) / 1e9 / hbm,
+                                    "unit": "GB/s", "peak": hbm}}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(args, os.cpu_count() or 1)
     if args.forms_configs > 0 and world == 1:
@@ -761,6 +784,8 @@ def main():
                     default="config2")
     ap.add_argument("--orbit-ions", type=int, default=1 << 20,
                     help="ions of the full-orbit workload (--workload orbit)")
+    ap.add_argument("--other-precision", type=int, default=1,
+                    help="default line: also time the other form (FP32 beside FP64) once")
     ap.add_argument("--orbit-lifetime", type=float, default=1e-4,
                     help="lifetime cap of the full-orbit workload (shorter: a small profiling case)")
     ap.add_argument("--orbit-sub-ions", type=int, default=1 << 17,
