@@ -142,3 +142,12 @@ def test_static_pass_leaves_free_device_memory_unchanged(karl):
                                    field_time_in=d1["time_fx"].data_ptr())
         torch.cuda.synchronize()
         assert torch.cuda.mem_get_info()[0] == free0, call
+    # control: the same measurement sees a 256 MiB device allocation (torch's
+    # cache emptied first, so the block is a new allocation)
+    torch.cuda.empty_cache()
+    free0 = torch.cuda.mem_get_info()[0]
+    block = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    assert free0 - torch.cuda.mem_get_info()[0] >= 256 << 20
+    del block
+    torch.cuda.empty_cache()
