@@ -135,8 +135,10 @@ def test_cycled_run_fp32_follows_the_oracle(karl, cycled):
     assert float(np.mean(g["per_primary"] == o["per_primary"])) >= 0.9
     cg, co = g["chan_count"].astype(float), o["chan_count"].astype(float)
     assert np.all(np.abs(cg - co) <= 5 * np.sqrt(cg + co) + 0.03 * co)
+    # each species' target field within the 1e-3 relative L2 of the FP64
+    # form (measured: e- 5.2e-4, T2+ 3.1e-5, T3+ 9.0e-7)
     for sp, name in enumerate(inputs.SPECIES_NAMES):
         if np.any(o["field"][sp]):
-            print(f"PARITY FP32 cycled field {name}: rel L2 "
-                  f"{parity.rel_l2(g['field'][sp], o['field'][sp]):.3e}")
-    assert parity.rel_l2(g["field"], o["field"]) < 0.03
+            l2 = parity.rel_l2(g["field"][sp], o["field"][sp])
+            print(f"PARITY FP32 cycled field {name}: rel L2 {l2:.3e}")
+            assert l2 < 1e-3, name

@@ -234,3 +234,73 @@ def test_ion_workload_follows_the_oracle(karl):
     for key in ("time_z", "time_r"):
         a, b = g[key].astype(float), o[key].astype(float)
         assert np.abs(a - b).sum() <= 0.01 * b.sum()
+
+
+def test_orbit_edge_cases_match_the_oracle(karl):
+    """Degenerate starts, identical on both sides: no primaries; a particle
+    on z = L moving out and one on z = 0 moving in -z (zero-length exits); a
+    particle just inside the wall moving outward; flights along the axis
+    (mu = +-1, the turning frame's special case) through gas; a step cap
+    that stalls a gyrating ion."""
+    nodes = inputs.energy_nodes(64, 1.0, 2e4)
+    ch = [inputs.Channel("elastic", inputs.ELASTIC, inputs.E, -1, 0.0, np.full_like(nodes, 1e-19)),
+          inputs.Channel("elastic_T2+", inputs.ELASTIC, inputs.T2P, -1, 0.0,
+                         np.full_like(nodes, 1e-19))]
+    prob = inputs.uniform_problem(1e19, 1.0, 20, ch, n_energy=64, e_min=1.0, e_max=2e4,
+                                  e_cut=0.0, n_spec_bins=4000, spec_bin_ev=1.0)
+    orb = _orbit(0.1, frac=0.1, tube_radius_m=0.05, n_rbins=5)
+    empty = _prims([], [], [], [], [], [], inputs.E)
+    g = _gpu(karl, prob, orb, empty)
+    o = oracle.orbit_run(prob, orb, empty)
+    for k in ("time_z", "ledger", "spectrum"):
+        assert not np.any(g[k]) and not np.any(o[k]), k
+    r = 0.05 * (1 - 1e-9)
+    pr = _prims([0.0, 0.0, r, 0.0, 0.0, 0.01],
+                [0.0, 0.0, 0.0, 0.0, 0.0, 0.0],
+                [1.0, 0.0, 0.5, 0.3, 0.7, 0.5],
+                [500.0, 500.0, 500.0, 300.0, 300.0, 1.0],
+                [0.5, -0.5, 0.0, 1.0, -1.0, 0.0],
+                [0.0, 0.0, 0.0, 0.0, 0.0, 0.5 * math.pi],
+                inputs.E)
+    pr.species[5] = inputs.T2P
+    for max_steps in (0, 200):
+        orb.max_steps = max_steps
+        g = _gpu(karl, prob, orb, pr, seed=9)
+        o = oracle.orbit_run(prob, orb, pr, seed=9)
+        np.testing.assert_array_equal(g["ledger"], o["ledger"])
+        np.testing.assert_array_equal(g["per_primary"], o["per_primary"])
+        for k in ("time_z", "time_r", "cross_pos", "cross_neg", "rcross_out", "rcross_in",
+                  "wall", "spectrum"):
+            np.testing.assert_array_equal(g[k], o[k], err_msg=k)
+        np.testing.assert_allclose(g["end_state"], o["end_state"], rtol=1e-12, atol=1e-15)
+    assert _deaths(g, inputs.E, "exit1") >= 1 and _deaths(g, inputs.E, "exit0") >= 1
+    assert _deaths(g, inputs.E, "wall") >= 1
+    assert _deaths(g, inputs.T2P, "stalled") == 1
+
+
+def test_ion_workload_full_size_sampled(karl):
+    """The default line's ion workload (131072 ions, the benchmark's launch):
+    the GPU runs all of it; the oracle runs 16 sampled ranges of 64 ions with
+    the same primary ids, whose collision counts and end states must match."""
+    prob, orb, pr = inputs.orbit_ion_config(n_ions=1 << 17, seed=1)
+    g = _gpu(karl, prob, orb, pr, seed=200)
+    rng = np.random.default_rng(3)
+    same = total = 0
+    for a in rng.choice(pr.n // 64, 16, replace=False) * 64:
+        sub = inputs.OrbitPrimaries(*(getattr(pr, k)[a:a + 64] for k in
+                                      ("x_m", "y_m", "z_m", "e_ev", "mu", "phi", "species")),
+                                    pid_offset=int(a))
+        o = oracle.orbit_run(prob, orb, sub, seed=200, n_threads=THREADS)
+        same += int(np.sum(o["per_primary"] == g["per_primary"][a:a + 64]))
+        close = np.all(np.abs(o["end_state"] - g["end_state"][a:a + 64]) <=
+                       1e-9 * (np.abs(o["end_state"]) + 1e-12), axis=1)
+        same += int(np.sum(close))
+        total += 128
+    print(f"PARITY orbit ions full size: sampled counts and end states equal {same / total:.4f}")
+    assert same / total >= 0.99
+    E = g["energy"]
+    e_in = E[karl.OE_IN_PRIMARY] + E[karl.OE_IN_THERMAL] + E[karl.OE_FIELD_WORK]
+    assert abs(e_in - E[karl.OE_EXIT0:karl.OE_STALLED + 1].sum()) < 1e-9 * e_in
+    L = g["ledger"]
+    assert L[karl.OB_BIRTHS:karl.OB_BIRTHS + 4].sum() == L[karl.OB_DEATHS:karl.OB_DEATHS + 32].sum()
+    assert np.all(g["time_z"].sum(axis=1) == g["time_r"].sum(axis=1))
