@@ -57,8 +57,8 @@ template <> struct RT<false> {
   static __device__ __forceinline__ R angp(const Params& P, size_t i) { return __ldg(P.ang_pdf + i); }
   static __device__ __forceinline__ R angc(const Params& P, size_t i) { return __ldg(P.ang_cum + i); }
   static __device__ __forceinline__ R energy(long long eq) { return (double)eq * (1.0 / 16777216.0); }
-  static __device__ __forceinline__ long long quant_de(R de) {
-    return (long long)floor(de * 16777216.0 + 0.5);
+  static __device__ __forceinline__ long long quant_de(R de) {   // de >= 0
+    return trunc_nonneg(de * 16777216.0 + 0.5);
   }
   // a transfer of either sign, rounded to the nearest 2^-24 eV
   static __device__ __forceinline__ long long quant_signed(R de) {
@@ -793,7 +793,7 @@ __device__ __noinline__ int select_per_channel(const Params& P, int s, long long
 // Quantised time of a path of length len at 1/(|mu| v) = inv_szq / Q_T:
 // round(len * inv_szq) in 2^-50 s units.
 __device__ __forceinline__ unsigned long long quant_len(double len, double inv_szq) {
-  return (unsigned long long)fma_rn(len, inv_szq, 0.5);
+  return (unsigned long long)trunc_nonneg(fma_rn(len, inv_szq, 0.5));
 }
 
 template <bool F32>
@@ -821,7 +821,9 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
   // position of ln E among the table nodes (shared by both lookups)
   const R le = T::lg(e * (R)P.inv_e_min);
   const R lx = le * (R)P.inv_h;
-  int ti = (int)floor(lx);
+  int ti;
+  if constexpr (F32) ti = (int)floor(lx);
+  else ti = floor_or_m1(lx);                 // integer ops (below the first node: -1)
   R tf;
   int row;                                 // row of the cumulative tables (-1: none)
   if (ti < 0) { ti = 0; tf = (R)0; row = P.n_energy - 1; }          // below the first node
@@ -906,7 +908,8 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
   // energy bin of the time tally
   int b = 0;
   if (P.ntb > 1) {
-    b = (int)floor(le * (R)P.tb_scale);
+    if constexpr (F32) b = (int)floor(le * (R)P.tb_scale);
+    else b = floor_or_m1(le * P.tb_scale);
     b = b < 0 ? 0 : (b > P.ntb - 1 ? P.ntb - 1 : b);
   }
   const size_t trow = (size_t)P.ntb;                         // stride between z rows
@@ -1021,7 +1024,9 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
       const double c0 = fma_rn(P.nseg[j0] + frate(j0), L.z - P.faces[j0], gcol(j0));
       const double D = mul_rn(mul_rn((double)tau, amu), ig);
       const double tgt = up ? c0 + D : c0 - D;
-      ex = up ? !(tgt < gcol(nz)) : !(tgt > 0.0);
+      // G >= C everywhere (rho and the field columns are non-negative): a
+      // target below the gas column's top is below G's top too
+      ex = up ? !(tgt < P.colgas[nz]) && !(tgt < gcol(nz)) : !(tgt > 0.0);
       if (!ex) {
         const long long tb = dbits(tgt);
         int lo = up ? j0 : 0, hi = up ? nz : j0 + 1;

@@ -233,6 +233,24 @@ __device__ __forceinline__ double log_tab(double x) {
   return __fma_rn((double)k, 0.69314718055994530942, __dadd_rn(c.x, __dmul_rn(r, t)));
 }
 
+// Integer part of a double y >= 0 (below 2^63) from its bits: y = m 2^e with
+// the 53-bit significand m, so trunc(y) = m >> -e or m << e.  The same value
+// as the conversion instruction, without the FP64 pipe (where GB300's
+// double-to-integer conversions and roundings run at the FP64 rate).
+__device__ __forceinline__ long long trunc_nonneg(double y) {
+  const long long b = __double_as_longlong(y);
+  const int e = (int)(b >> 52) - 1075;
+  const long long m = (b & 0x000fffffffffffffLL) | 0x0010000000000000LL;
+  if (e < -52) return 0;
+  return e >= 0 ? (m << e) : (m >> -e);
+}
+
+// floor(x) for x < 2^31 as an int, -1 for every negative x (callers clamp
+// below at 0), by the sign bit and trunc_nonneg
+__device__ __forceinline__ int floor_or_m1(double x) {
+  return __double_as_longlong(x) < 0 ? -1 : (int)trunc_nonneg(x);
+}
+
 // uniforms from the top bits of a 64-bit word
 __device__ __forceinline__ double u01d(unsigned long long w) {
   return (double)(w >> 11) * (1.0 / 9007199254740992.0);
