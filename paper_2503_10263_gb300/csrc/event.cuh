@@ -41,6 +41,8 @@ template <> struct RT<false> {
   static __device__ __forceinline__ R tn(R x) { return tan(x); }
   static __device__ __forceinline__ R atn(R x) { return atan(x); }
   static __device__ __forceinline__ R cpi(R x) { return cospi(x); }
+  static __device__ __forceinline__ R max0(R x) { return dmax0(x); }
+  static __device__ __forceinline__ R clamp1(R x) { return dclamp1(x); }
   static __device__ __forceinline__ R spi(R x) { return sinpi(x); }
   // value and slope to the next node of channel k at node i ([node][channel][2])
   static __device__ __forceinline__ void tab2(const Params& P, int k, int i, R& a, R& s) {
@@ -56,7 +58,10 @@ template <> struct RT<false> {
   }
   static __device__ __forceinline__ R angp(const Params& P, size_t i) { return __ldg(P.ang_pdf + i); }
   static __device__ __forceinline__ R angc(const Params& P, size_t i) { return __ldg(P.ang_cum + i); }
-  static __device__ __forceinline__ R energy(long long eq) { return (double)eq * (1.0 / 16777216.0); }
+  // eq 2^-24 (for eq > 0 by lowering the exponent: exact, no FP64 multiply)
+  static __device__ __forceinline__ R energy(long long eq) {
+    return eq > 0 ? scale_down_pow2((double)eq, 24) : (double)eq * (1.0 / 16777216.0);
+  }
   static __device__ __forceinline__ long long quant_de(R de) {   // de >= 0
     return trunc_nonneg(de * 16777216.0 + 0.5);
   }
@@ -75,6 +80,8 @@ template <> struct RT<true> {
   static __device__ __forceinline__ R tn(R x) { return tanf(x); }
   static __device__ __forceinline__ R atn(R x) { return atanf(x); }
   static __device__ __forceinline__ R cpi(R x) { return cospif(x); }
+  static __device__ __forceinline__ R max0(R x) { return fmaxf(0.0f, x); }
+  static __device__ __forceinline__ R clamp1(R x) { return fminf(1.0f, fmaxf(-1.0f, x)); }
   static __device__ __forceinline__ R spi(R x) { return sinpif(x); }
   static __device__ __forceinline__ void tab2(const Params& P, int k, int i, R& a, R& s) {
     const float2 t = __ldg((const float2*)P.sigf + (size_t)i * P.nch + k);
@@ -833,7 +840,7 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
   // 1/v and 1/(|mu| v) (relativistic: v = c sqrt(x (2 + x)) / (1 + x), x = E / m c^2);
   // both from one reciprocal root, and the time quantum folded into the second
   const double amu = fabs(L.mu);
-  const bool still = L.mu == 0.0;
+  const bool still = dzero(L.mu);
   const R x = mul_rn(e, (R)P.inv_mass[s]);
   R inv_v;
   double inv_szq;                          // Q_T / (|mu| v): time units per metre along z
@@ -956,13 +963,13 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
     if (P.track_time) L.tal += tfl;
     zc = L.z;
   } else {
-    const bool up = L.mu > 0.0;
+    const bool up = dpos(L.mu);
     bool ex;
     if (nrec == 0) {
       // Gas only: the rate is sigma_gas n_j, so the flight ends where the gas
       // column C reaches C(z0) +- D with D = tau |mu| / sigma_gas.
       double tgt = 0.0;
-      if (!(gasd > 0.0)) {
+      if (!dpos(gasd)) {
         ex = true;                          // no channel: straight to an end
       } else {
         double D;
@@ -976,7 +983,7 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
           // largest k with C(k) <= target, in [j0, nz) going up, [0, j0] going down
           int lo = up ? j0 : 0, hi = up ? nz : j0 + 1;
           if (P.nq > 0) {
-            const float q = (float)tgt * P.nq_over_colmax_f;
+            const float q = dtof_hint(tgt) * P.nq_over_colmax_f;
             if (q >= 0.0f && q < (float)P.nq) {
               const int qi = (int)q;
               const int a = max(lo, P.ginv[qi] - 1), bb = min(hi, P.ginv[qi + 1] + 1);
@@ -997,7 +1004,7 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
           zc = up ? dmax_nn(zc, L.z) : dmin_nn(zc, L.z);
         }
       }
-    } else if (gasd > 0.0) {
+    } else if (dpos(gasd)) {
       // Gas and field channels, in gas-column units: the column of the whole
       // rate over sigma_gas is G(k) = C(k) + rho0 F0(k) + rho1 F1(k), and the
       // flight ends where G reaches G(z0) +- tau |mu| / sigma_gas.  As G >= C,
@@ -1031,7 +1038,7 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
         const long long tb = dbits(tgt);
         int lo = up ? j0 : 0, hi = up ? nz : j0 + 1;
         if (P.nq > 0) {
-          const float q = (float)tgt * P.nq_over_colmax_f;
+          const float q = dtof_hint(tgt) * P.nq_over_colmax_f;
           if (q >= 0.0f && q < (float)P.nq) {
             const int qi = (int)q;
             const int a = max(lo, P.ginv[qi] - 1), bb = min(hi, P.ginv[qi + 1] + 1);
@@ -1215,12 +1222,13 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
     // CM polar angle (isotropic or tabulated at the lab energy, which is the
     // impact energy for a target at rest): lab polar angle and energy transfer
     const R g = (R)P.gam[s];
+    const R g2 = (R)P.gam2[s];                 // 2 g
     const R cchi = elastic_cchi<F32>(P, ch, e, T::u(w[2]));
-    const R a = fma_rn(mul_rn((R)2, g), cchi, fma_rn(g, g, (R)1));
+    const R a = fma_rn(g2, cchi, fma_rn(g, g, (R)1));
     const R ra = T::rsq(a);
     const R ct = mul_rn(cchi + g, ra);
     // energy given to the target, E - E' = E 2g(1 - cos chi)/(1+g)^2
-    const R de = mul_rn(mul_rn(mul_rn(e, mul_rn((R)2, g)), (R)1 - cchi), (R)P.inv_1pg2[s]);
+    const R de = mul_rn(mul_rn(mul_rn(e, g2), (R)1 - cchi), (R)P.inv_1pg2[s]);
     long long rq = T::quant_de(de);
     if (rq > L.eq) rq = L.eq;
     o.recoil += (unsigned long long)rq;
@@ -1228,9 +1236,9 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
     // sin(theta_lab) sqrt(1 - mu^2) in one root: 1 - ct^2 = (1 - cchi^2) / a
     const R cphi = T::cpi(mul_rn((R)2, T::u(w[3])));
     const R mu = (R)L.mu;
-    const R ss = mul_rn(T::sq(fmax((R)0, mul_rn(fma_rn(-cchi, cchi, (R)1), fma_rn(-mu, mu, (R)1)))),
+    const R ss = mul_rn(T::sq(T::max0(mul_rn(fma_rn(-cchi, cchi, (R)1), fma_rn(-mu, mu, (R)1)))),
                         ra);
-    L.mu = (double)fmin((R)1, fmax((R)-1, fma_rn(mu, ct, mul_rn(ss, cphi))));
+    L.mu = (double)T::clamp1(fma_rn(mu, ct, mul_rn(ss, cphi)));
   } else if (ch.kind == EXCITATION) {
     L.eq -= ch.loss_q;
     o.excit += (unsigned long long)ch.loss_q;

@@ -304,6 +304,7 @@ inline void fill_params(Params& P, const karl_geometry& g, const ModelInfo& m, i
     P.mass[s] = g.species_mass_ev[s];
     P.inv_mass[s] = 1.0 / g.species_mass_ev[s];
     P.gam[s] = g.species_mass_ev[s] / g.target_mass_ev;
+    P.gam2[s] = 2.0 * P.gam[s];
     P.inv_1pg2[s] = 1.0 / ((1.0 + P.gam[s]) * (1.0 + P.gam[s]));
   }
   P.target_mass = g.target_mass_ev;

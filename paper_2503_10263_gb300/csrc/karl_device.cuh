@@ -102,6 +102,7 @@ struct Params {
   double mass[NSP];
   double inv_mass[NSP];
   double gam[NSP];              // m / M_target
+  double gam2[NSP];             // 2 m / M_target
   double inv_1pg2[NSP];         // 1 / (1 + m/M)^2
   double target_mass, eps_ion, inv_eps_ion, kT;
   double drift_c;               // gas drift along +z in units of c (moving targets)
@@ -245,6 +246,28 @@ __device__ __forceinline__ long long trunc_nonneg(double y) {
   return e >= 0 ? (m << e) : (m >> -e);
 }
 
+// Sign tests and clamps of doubles on their bits (integer operations; the
+// same results as the floating-point ones for numbers, zeros included)
+__device__ __forceinline__ bool dpos(double x) { return __double_as_longlong(x) > 0; }  // x > 0
+__device__ __forceinline__ bool dzero(double x) { return (__double_as_longlong(x) << 1) == 0; }
+__device__ __forceinline__ double dmax0(double x) {                                    // max(0, x)
+  return __double_as_longlong(x) < 0 ? 0.0 : x;
+}
+__device__ __forceinline__ double dclamp1(double x) {                                 // to [-1, 1]
+  const long long b = __double_as_longlong(x);
+  return (b & 0x7fffffffffffffffLL) > 0x3ff0000000000000LL
+             ? __longlong_as_double((b & (long long)0x8000000000000000ULL) | 0x3ff0000000000000LL)
+             : x;
+}
+// x (finite, >= 0) truncated to FP32 from its bits: a search hint, not a value
+__device__ __forceinline__ float dtof_hint(double x) {
+  const long long b = __double_as_longlong(x);
+  const long long e = (b >> 52) - 1023 + 127;
+  if (e <= 0) return 0.0f;
+  if (e >= 255) return 3.0e38f;
+  return __int_as_float((int)((e << 23) | ((b >> 29) & 0x7fffff)));
+}
+
 // floor(x) for x < 2^31 as an int, -1 for every negative x (callers clamp
 // below at 0), by the sign bit and trunc_nonneg
 __device__ __forceinline__ int floor_or_m1(double x) {
@@ -252,11 +275,17 @@ __device__ __forceinline__ int floor_or_m1(double x) {
 }
 
 // uniforms from the top bits of a 64-bit word
+// A positive normal double times 2^-k (k < 1023) by lowering its exponent:
+// exact, and an integer operation instead of an FP64 multiply.
+__device__ __forceinline__ double scale_down_pow2(double x, int k) {
+  return __longlong_as_double(__double_as_longlong(x) - ((long long)k << 52));
+}
 __device__ __forceinline__ double u01d(unsigned long long w) {
-  return (double)(w >> 11) * (1.0 / 9007199254740992.0);
+  const unsigned long long m = w >> 11;                  // 53 bits; 0 maps to 0.0
+  return m ? scale_down_pow2((double)m, 53) : 0.0;
 }
 __device__ __forceinline__ double eta01d(unsigned long long w) {
-  return (double)((w >> 11) + 1) * (1.0 / 9007199254740992.0);
+  return scale_down_pow2((double)((w >> 11) + 1), 53);  // in (0, 1]
 }
 __device__ __forceinline__ float u01f(unsigned long long w) {
   return (float)(unsigned)(w >> 40) * (1.0f / 16777216.0f);
