@@ -1033,7 +1033,7 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
       const double tgt = up ? c0 + D : c0 - D;
       // G >= C everywhere (rho and the field columns are non-negative): a
       // target below the gas column's top is below G's top too
-      ex = up ? !(tgt < P.colgas[nz]) && !(tgt < gcol(nz)) : !(tgt > 0.0);
+      ex = up ? !lt_nn(tgt, P.colgas[nz]) && !lt_nn(tgt, gcol(nz)) : !dpos(tgt);
       if (!ex) {
         const long long tb = dbits(tgt);
         int lo = up ? j0 : 0, hi = up ? nz : j0 + 1;
@@ -1054,11 +1054,11 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
         }
         jc = lo;
         double gj = gcol(jc);
-        if (!(gj <= tgt)) {
+        if (lt_nn(tgt, gj)) {
           int l2 = up ? j0 : 0, h2 = jc;
           while (h2 - l2 > 1) {
             const int mid = (l2 + h2) >> 1;
-            if (gcol(mid) <= tgt) l2 = mid; else h2 = mid;
+            if (!lt_nn(tgt, gcol(mid))) l2 = mid; else h2 = mid;
           }
           jc = l2;
           gj = gcol(jc);
@@ -1069,7 +1069,7 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
         rf_end = frate(jc);
         double off;
         const double eps = mul_rn(rf_end, P.invn[jc]);
-        if (nj > 0.0 && fabs(eps) < 1e-6)
+        if (dpos(nj) && dabs_lt(eps, 1e-6))
           // 1 / (n + rf) = (1/n) (1 - eps + eps^2) to eps^3, eps = rf / n
           off = mul_rn(gap, mul_rn(P.invn[jc], fma_rn(-eps, 1.0 - eps, 1.0)));
         else
@@ -1162,7 +1162,7 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
       // units for the cumulative tables), field channel i rho_i f_i(jc)
       const double nj = P.nseg[jc];
       const double tr = mul_rn(u01d(w[1]), nj + rf_end);
-      if (tr < nj) {
+      if (lt_nn(tr, nj)) {
         tg = (R)mul_rn(mul_rn(tr, P.invn[jc]), gasd);
       } else {
         gas_part = false;
@@ -1172,10 +1172,10 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
         for (int c = ncg; c < nsc; ++c) {
           const int kk = P.sc[s][c];
           const double rk = mul_rn(c == ncg ? rho0 : rho1, P.frate[kk][jc]);
-          if (!(rk > 0.0)) continue;
+          if (!dpos(rk)) continue;
           last = c;
           cum += rk;
-          if (tr < cum) { chs = c; break; }
+          if (lt_nn(tr, cum)) { chs = c; break; }
         }
         if (chs < 0) chs = last;
       }
@@ -1183,7 +1183,7 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
       const double nj = P.nseg[jc];
       const double target = mul_rn(u01d(w[1]), segrate(jc));
       const double gasj = mul_rn(gasd, nj);
-      if (target < gasj) {
+      if (lt_nn(target, gasj)) {
         tg = (R)mul_rn(target, P.invn[jc]);
       } else {
         gas_part = false;
@@ -1193,10 +1193,10 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
         for (int c = ncg; c < nsc; ++c) {
           const int kk = P.sc[s][c];
           const double rk = mul_rn(c == ncg ? rc0 : rc1, P.frate[kk][jc]);
-          if (!(rk > 0.0)) continue;
+          if (!dpos(rk)) continue;
           last = c;
           cum += rk;
-          if (target < cum) { chs = c; break; }
+          if (lt_nn(target, cum)) { chs = c; break; }
         }
         if (chs < 0) chs = last;
       }
@@ -1205,7 +1205,7 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
       for (int c = 0; c < ncg; ++c) {
         R a0, sl;
         T::cum2(P, s, row, c, a0, sl);
-        if (tg < fma_rn(tf, sl, a0) + (c >= xslot ? xval : (R)0)) { chs = c; break; }
+        if (lt_nn(tg, fma_rn(tf, sl, a0) + (c >= xslot ? xval : (R)0))) { chs = c; break; }
       }
     }
     if (chs < 0)                        // rounding at the top end

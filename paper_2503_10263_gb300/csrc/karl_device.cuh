@@ -259,6 +259,16 @@ __device__ __forceinline__ double dclamp1(double x) {                           
              ? __longlong_as_double((b & (long long)0x8000000000000000ULL) | 0x3ff0000000000000LL)
              : x;
 }
+// a < b for a, b >= 0 (doubles: on the bits; floats: the FP32 compare)
+__device__ __forceinline__ bool lt_nn(double a, double b) {
+  return __double_as_longlong(a) < __double_as_longlong(b);
+}
+__device__ __forceinline__ bool lt_nn(float a, float b) { return a < b; }
+// |x| < t for t > 0
+__device__ __forceinline__ bool dabs_lt(double x, double t) {
+  return (__double_as_longlong(x) & 0x7fffffffffffffffLL) < __double_as_longlong(t);
+}
+
 // x (finite, >= 0) truncated to FP32 from its bits: a search hint, not a value
 __device__ __forceinline__ float dtof_hint(double x) {
   const long long b = __double_as_longlong(x);

@@ -42,6 +42,19 @@ enum { EV_NONE = 0, EV_WALL = 1, EV_EXIT = 2, EV_CAP = 3, EV_COLL = 4, EV_EBIN =
 constexpr int DOM_REDRAW = 3;          // optical depths drawn anew after an energy-bin stop
 constexpr double INV_C2 = 1.0 / (C_LIGHT * C_LIGHT);
 
+// Comparisons of the step's tests on the bits of the doubles (integer
+// operations, the same outcomes as the floating-point compares for numbers:
+// a <= b for a, b >= 0 is bits(a) <= bits(b); a negative number's bits are
+// negative; -0.0 counts as zero)
+__device__ __forceinline__ long long bits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ bool lt0(double x) {              // x < 0
+  return bits(x) < 0 && (bits(x) << 1) != 0;
+}
+__device__ __forceinline__ double clamp01(double f) {         // to [0, 1]
+  const long long b = bits(f);
+  return b < 0 ? 0.0 : (b > 0x3ff0000000000000LL ? 1.0 : f);
+}
+
 struct OPart {
   double x, y, z, ux, uy, uz, t;
   unsigned long long node, pid;
@@ -80,20 +93,21 @@ __device__ void turn(double d0, double d1, double d2, double ct, double cp, doub
 }
 
 __device__ __forceinline__ int seg_of(const Params& P, const OrbitDev& O, double z) {
-  int j = (int)floor(z * O.inv_dz);
+  const int j = floor_or_m1(z * O.inv_dz);        // floor on the bits (negative: -1)
   return j < 0 ? 0 : (j > P.nz - 1 ? P.nz - 1 : j);
 }
 
-// radial bin of (x, y), searched from the bin b (the particle's bin, or a guess)
+// radial bin of (x, y), searched from the bin b (the particle's bin, or a
+// guess); the squared radii are non-negative, so they compare as integers
 __device__ __forceinline__ int rbin_from(const OrbitDev& O, double x, double y, int b) {
-  const double q = x * x + y * y;
-  while (b > 0 && __ldg(O.edge2 + b) > q) --b;
-  while (b < O.nr - 1 && __ldg(O.edge2 + b + 1) <= q) ++b;
+  const long long q = __double_as_longlong(x * x + y * y);
+  while (b > 0 && __double_as_longlong(__ldg(O.edge2 + b)) > q) --b;
+  while (b < O.nr - 1 && __double_as_longlong(__ldg(O.edge2 + b + 1)) <= q) ++b;
   return b;
 }
 
 __device__ __forceinline__ int rbin_of(const OrbitDev& O, double x, double y) {
-  int b = (int)floor(sqrt(x * x + y * y) * O.r_scale);
+  int b = floor_or_m1(sqrt(x * x + y * y) * O.r_scale);
   b = b < 0 ? 0 : (b > O.nr - 1 ? O.nr - 1 : b);
   return rbin_from(O, x, y, b);
 }
@@ -465,29 +479,31 @@ __global__ void __launch_bounds__(256) orbit_kernel(const Params P, const OrbitD
     double fb = 1.0;
     int event = EV_NONE, end = -1;
     const double xn = Q.x + dx, yn = Q.y + dy, zn = Q.z + dz;
-    if (xn * xn + yn * yn > O.R2) {
+    if (bits(xn * xn + yn * yn) > bits(O.R2)) {
       const double a = dx * dx + dy * dy;
       const double b = Q.x * dx + Q.y * dy;
       const double c = Q.x * Q.x + Q.y * Q.y - O.R2;
       const double disc = sqrt(fmax(0.0, b * b - a * c));
-      double f = b > 0.0 ? -c / (b + disc) : (disc - b) / a;
-      f = fmin(1.0, fmax(0.0, f));
+      double f = dpos(b) ? -c / (b + disc) : (disc - b) / a;
+      f = clamp01(f);
       if (f <= fb) { fb = f; event = EV_WALL; }
     }
-    if (zn < 0.0 || zn > L) {
-      double f = zn < 0.0 ? -Q.z / dz : (L - Q.z) / dz;
-      f = fmin(1.0, fmax(0.0, f));
-      if (event == EV_NONE ? f <= fb : f < fb) { fb = f; event = EV_EXIT; end = zn < 0.0 ? 0 : 1; }
+    const bool below = lt0(zn);
+    if (below || bits(zn) > bits(L)) {
+      double f = below ? -Q.z / dz : (L - Q.z) / dz;
+      f = clamp01(f);
+      if (event == EV_NONE ? f <= fb : f < fb) { fb = f; event = EV_EXIT; end = below ? 0 : 1; }
     }
-    if (Q.t + dt >= P.max_life) {
-      const double f = fmin(1.0, fmax(0.0, (P.max_life - Q.t) / dt));
+    if (bits(Q.t + dt) >= bits(P.max_life)) {
+      const double f = clamp01((P.max_life - Q.t) / dt);
       if (event == EV_NONE ? f <= fb : f < fb) { fb = f; event = EV_CAP; }
     }
-    if (dtau > 0.0 && F.acc + dtau >= F.tau) {
-      const double f = fmin(1.0, fmax(0.0, (F.tau - F.acc) / dtau));
+    if (dpos(dtau) && bits(F.acc + dtau) >= bits(F.tau)) {
+      const double f = clamp01((F.tau - F.acc) / dtau);
       if (event == EV_NONE ? f <= fb : f < fb) { fb = f; event = EV_COLL; }
     }
-    if (event == EV_NONE && (u2n < F.u2lo || u2n >= F.u2hi)) event = EV_EBIN;
+    if (event == EV_NONE && (bits(u2n) < bits(F.u2lo) || bits(u2n) >= bits(F.u2hi)))
+      event = EV_EBIN;
     if (event == EV_NONE || event == EV_EBIN) {
       const int mr = rbin_from(O, Q.x + 0.5 * dx, Q.y + 0.5 * dy, F.rs);
       if (jm == F.cj && mr == F.cr) {
