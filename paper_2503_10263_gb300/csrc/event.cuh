@@ -30,6 +30,14 @@ __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, 
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
+// float <-> double of the FP32 form (the conversions: building them from the
+// bits measured slower there); identities for FP64
+__device__ __forceinline__ double to_d(double x) { return x; }
+__device__ __forceinline__ double to_d(float x) { return (double)x; }
+template <class R> __device__ __forceinline__ R from_d(double x);
+template <> __device__ __forceinline__ double from_d<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from_d<float>(double x) { return (float)x; }
+
 template <bool F32> struct RT;
 template <> struct RT<false> {
   using R = double;
@@ -58,9 +66,10 @@ template <> struct RT<false> {
   }
   static __device__ __forceinline__ R angp(const Params& P, size_t i) { return __ldg(P.ang_pdf + i); }
   static __device__ __forceinline__ R angc(const Params& P, size_t i) { return __ldg(P.ang_cum + i); }
-  // eq 2^-24 (for eq > 0 by lowering the exponent: exact, no FP64 multiply)
+  // eq 2^-24, built from the bits of eq (exact; no FP64 conversion or multiply)
   static __device__ __forceinline__ R energy(long long eq) {
-    return eq > 0 ? scale_down_pow2((double)eq, 24) : (double)eq * (1.0 / 16777216.0);
+    return eq >= 0 && eq < (1LL << 53) ? u53_scaled((unsigned long long)eq, 24)
+                                       : (double)eq * (1.0 / 16777216.0);
   }
   static __device__ __forceinline__ long long quant_de(R de) {   // de >= 0
     return trunc_nonneg(de * 16777216.0 + 0.5);
@@ -835,7 +844,11 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
   int row;                                 // row of the cumulative tables (-1: none)
   if (ti < 0) { ti = 0; tf = (R)0; row = P.n_energy - 1; }          // below the first node
   else if (ti > P.n_energy - 2) { ti = P.n_energy - 2; tf = (R)1; row = -1; }
-  else { tf = lx - (R)ti; row = ti; }
+  else {
+    if constexpr (F32) tf = lx - (R)ti;
+    else tf = lx - i32_to_d(ti);            // the conversion on integer operations
+    row = ti;
+  }
 
   // 1/v and 1/(|mu| v) (relativistic: v = c sqrt(x (2 + x)) / (1 + x), x = E / m c^2);
   // both from one reciprocal root, and the time quantum folded into the second
@@ -894,8 +907,8 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
     for (int c = ncg; c < nsc; ++c) {       // field channels follow the gas channels
       const int k = P.sc[s][c];
       const R cv = channel_coef<F32>(P, k, s, L.eq, ti, tf, inv_v);
-      if (nrec == 0) { rc0 = (double)cv; rcol0 = P.fcol[k]; rrate0 = P.frate[k]; }
-      else { rc1 = (double)cv; rcol1 = P.fcol[k]; rrate1 = P.frate[k]; }
+      if (nrec == 0) { rc0 = to_d(cv); rcol0 = P.fcol[k]; rrate0 = P.frate[k]; }
+      else { rc1 = to_d(cv); rcol1 = P.fcol[k]; rrate1 = P.frate[k]; }
       ++nrec;
     }
   } else {
@@ -906,8 +919,8 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
       if (!field_kind(P.ch[k].kind)) {
         gas += cv;
       } else {
-        if (nrec == 0) { rc0 = (double)cv; rcol0 = P.fcol[k]; rrate0 = P.frate[k]; }
-        else { rc1 = (double)cv; rcol1 = P.fcol[k]; rrate1 = P.frate[k]; }
+        if (nrec == 0) { rc0 = to_d(cv); rcol0 = P.fcol[k]; rrate0 = P.frate[k]; }
+        else { rc1 = to_d(cv); rcol1 = P.fcol[k]; rrate1 = P.frate[k]; }
         ++nrec;
       }
     }
@@ -922,7 +935,7 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
   const size_t trow = (size_t)P.ntb;                         // stride between z rows
   const size_t tbase = (size_t)s * (P.nz + 2) * P.ntb + b;   // (s, row 0, b)
   const size_t xbase = (size_t)s * (P.nz + 2);
-  const double gasd = (double)gas;
+  const double gasd = to_d(gas);
 
   // G(k) = optical-depth column of the whole rate to face k, and the rate in
   // segment j (the column tables may live in shared memory: plain loads)
@@ -974,7 +987,7 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
       } else {
         double D;
         if constexpr (F32) D = (double)mul_rn(mul_rn(tau, (R)amu), __frcp_rn(gas));
-        else D = mul_rn((double)tau, amu) / gasd;
+        else D = mul_rn(to_d(tau), amu) / gasd;
         const double c0 = fma_rn(P.nseg[j0], L.z - P.faces[j0], P.colgas[j0]);
         tgt = up ? c0 + D : c0 - D;
         const long long tb = dbits(tgt);
@@ -1029,7 +1042,7 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
         return r;
       };
       const double c0 = fma_rn(P.nseg[j0] + frate(j0), L.z - P.faces[j0], gcol(j0));
-      const double D = mul_rn(mul_rn((double)tau, amu), ig);
+      const double D = mul_rn(mul_rn(to_d(tau), amu), ig);
       const double tgt = up ? c0 + D : c0 - D;
       // G >= C everywhere (rho and the field columns are non-negative): a
       // target below the gas column's top is below G's top too
@@ -1082,7 +1095,7 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
       // Field channels only (no gas rate): the flight inverts the column of
       // the fields, bracketed from the gas column where there is one.
       const double g0 = fma_rn(segrate(j0), L.z - P.faces[j0], colsum(j0));
-      const double delta = mul_rn((double)tau, amu);
+      const double delta = mul_rn(to_d(tau), amu);
       const double target = up ? g0 + delta : g0 - delta;
       ex = up ? !(target < colsum(nz)) : !(target > 0.0);
       if (!ex) {
@@ -1163,7 +1176,7 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
       const double nj = P.nseg[jc];
       const double tr = mul_rn(u01d(w[1]), nj + rf_end);
       if (lt_nn(tr, nj)) {
-        tg = (R)mul_rn(mul_rn(tr, P.invn[jc]), gasd);
+        tg = from_d<R>(mul_rn(mul_rn(tr, P.invn[jc]), gasd));
       } else {
         gas_part = false;
         tg = (R)0;
@@ -1184,7 +1197,7 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
       const double target = mul_rn(u01d(w[1]), segrate(jc));
       const double gasj = mul_rn(gasd, nj);
       if (lt_nn(target, gasj)) {
-        tg = (R)mul_rn(target, P.invn[jc]);
+        tg = from_d<R>(mul_rn(target, P.invn[jc]));
       } else {
         gas_part = false;
         tg = (R)0;
@@ -1235,10 +1248,10 @@ __device__ void event(const Params& P, unsigned long long* led, Lane& L, EventOu
     L.eq -= rq;
     // sin(theta_lab) sqrt(1 - mu^2) in one root: 1 - ct^2 = (1 - cchi^2) / a
     const R cphi = T::cpi(mul_rn((R)2, T::u(w[3])));
-    const R mu = (R)L.mu;
+    const R mu = from_d<R>(L.mu);
     const R ss = mul_rn(T::sq(T::max0(mul_rn(fma_rn(-cchi, cchi, (R)1), fma_rn(-mu, mu, (R)1)))),
                         ra);
-    L.mu = (double)T::clamp1(fma_rn(mu, ct, mul_rn(ss, cphi)));
+    L.mu = to_d(T::clamp1(fma_rn(mu, ct, mul_rn(ss, cphi))));
   } else if (ch.kind == EXCITATION) {
     L.eq -= ch.loss_q;
     o.excit += (unsigned long long)ch.loss_q;

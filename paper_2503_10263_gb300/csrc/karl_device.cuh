@@ -206,6 +206,22 @@ __device__ __forceinline__ unsigned long long child_node(unsigned long long pare
   return mix64(mix64(parent) ^ (((unsigned long long)ev << 2) | slot));
 }
 
+// Integer-to-double conversions run on GB300's FP64 pipe (16 SM-cycles a
+// warp instruction, like an FP64 fma); these build the same values from the
+// bits with integer operations.
+// m 2^-k for 0 <= m < 2^53 (exact): the leading bit p of m sets the exponent,
+// the bits below it the significand
+__device__ __forceinline__ double u53_scaled(unsigned long long m, int k) {
+  if (m == 0) return 0.0;
+  const int p = 63 - __clzll((long long)m);
+  return __longlong_as_double(((long long)(1023 + p - k) << 52) |
+                              (long long)((m << (52 - p)) & 0x000fffffffffffffULL));
+}
+// (double)k for |k| < 2^31
+__device__ __forceinline__ double i32_to_d(int k) {
+  const double d = u53_scaled((unsigned long long)(k < 0 ? -(long long)k : (long long)k), 0);
+  return k < 0 ? __longlong_as_double(__double_as_longlong(d) | (long long)0x8000000000000000ULL) : d;
+}
 // ln x for positive normal x, table-driven (P. T. P. Tang, "Table-driven
 // implementation of the logarithm function in IEEE floating-point
 // arithmetic", ACM TOMS 16, 1990): x = 2^k m with m in [1, 2) in one of 256
@@ -231,7 +247,7 @@ __device__ __forceinline__ double log_tab(double x) {
   t = __fma_rn(r, t, 1.0 / 3.0);
   t = __fma_rn(r, t, -0.5);
   t = __fma_rn(r, t, 1.0);
-  return __fma_rn((double)k, 0.69314718055994530942, __dadd_rn(c.x, __dmul_rn(r, t)));
+  return __fma_rn(i32_to_d(k), 0.69314718055994530942, __dadd_rn(c.x, __dmul_rn(r, t)));
 }
 
 // Integer part of a double y >= 0 (below 2^63) from its bits: y = m 2^e with
@@ -285,17 +301,11 @@ __device__ __forceinline__ int floor_or_m1(double x) {
 }
 
 // uniforms from the top bits of a 64-bit word
-// A positive normal double times 2^-k (k < 1023) by lowering its exponent:
-// exact, and an integer operation instead of an FP64 multiply.
-__device__ __forceinline__ double scale_down_pow2(double x, int k) {
-  return __longlong_as_double(__double_as_longlong(x) - ((long long)k << 52));
-}
 __device__ __forceinline__ double u01d(unsigned long long w) {
-  const unsigned long long m = w >> 11;                  // 53 bits; 0 maps to 0.0
-  return m ? scale_down_pow2((double)m, 53) : 0.0;
+  return u53_scaled(w >> 11, 53);                        // 53 bits; 0 maps to 0.0
 }
 __device__ __forceinline__ double eta01d(unsigned long long w) {
-  return scale_down_pow2((double)((w >> 11) + 1), 53);  // in (0, 1]
+  return u53_scaled((w >> 11) + 1, 53);                  // in (0, 1]
 }
 __device__ __forceinline__ float u01f(unsigned long long w) {
   return (float)(unsigned)(w >> 40) * (1.0f / 16777216.0f);

@@ -38,3 +38,22 @@ def test_floor_or_m1():
     want = np.where(x < 0, -1, np.floor(x)).astype(np.int64)
     want[x.view(np.int64) < 0] = -1          # -0.0 counts as negative; callers clamp at 0
     np.testing.assert_array_equal(floor_or_m1(x), want)
+
+
+def u53_scaled(m: int, k: int) -> float:
+    """m 2^-k from the bits (0 <= m < 2^53), as the kernels build it."""
+    if m == 0:
+        return 0.0
+    p = m.bit_length() - 1
+    b = ((1023 + p - k) << 52) | ((m << (52 - p)) & 0x000FFFFFFFFFFFFF)
+    return float(np.array([b], np.int64).view(np.float64)[0])
+
+
+def test_integer_to_double_from_bits():
+    rng = np.random.default_rng(3)
+    ms = [0, 1, 2, 3, (1 << 53) - 1, 1 << 52] + [int(x) for x in rng.integers(0, 1 << 53, 20000)]
+    ms += [int(x) >> int(s) for x, s in zip(rng.integers(1, 1 << 53, 2000),
+                                            rng.integers(0, 52, 2000))]
+    for m in ms:
+        for k in (0, 24, 53):
+            assert u53_scaled(m, k) == m * 2.0 ** -k, (m, k)
