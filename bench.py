@@ -51,11 +51,11 @@ BYTES_PER_EVENT_FP32 = 80
 #     which also counts the lanes a divergent warp leaves idle;
 #   DRAM_BYTES: dram__bytes_read.sum + dram__bytes_write.sum, scaled to a launch
 #     by its collisions.
-FP64_OPS_PER_COLLISION = {"fp64": 115.6, "fp32": 26.2}
-FP64_PIPE_CYCLES_PER_COLLISION = {"fp64": 80.2, "fp32": 28.0}
-DRAM_BYTES_PER_COLLISION = {"fp64": 0.149, "fp32": 0.238}
+FP64_OPS_PER_COLLISION = {"fp64": 117.7, "fp32": 26.2}
+FP64_PIPE_CYCLES_PER_COLLISION = {"fp64": 77.0, "fp32": 27.7}
+DRAM_BYTES_PER_COLLISION = {"fp64": 0.157, "fp32": 0.242}
 FP64_OPS_PER_SM_CYCLE = 2
-THREADS_PER_INSTRUCTION = {"fp64": 24.1, "fp32": 22.7}   # smsp__thread_inst_executed_per_inst_executed
+THREADS_PER_INSTRUCTION = {"fp64": 24.2, "fp32": 22.6}   # smsp__thread_inst_executed_per_inst_executed
 WORKLOAD = ("config2: 1e7 decays (1e7 beta e- + 1e7 thermal T2+), parabolic profile with "
             "5e21 m^-2 column, L = 10 m, 1000 z segments, 7 e- channels + T2+ clustering + "
             "e-/ion recombination, two passes")
