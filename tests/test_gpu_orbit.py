@@ -304,3 +304,27 @@ def test_ion_workload_full_size_sampled(karl):
     L = g["ledger"]
     assert L[karl.OB_BIRTHS:karl.OB_BIRTHS + 4].sum() == L[karl.OB_DEATHS:karl.OB_DEATHS + 32].sum()
     assert np.all(g["time_z"].sum(axis=1) == g["time_r"].sum(axis=1))
+
+
+def test_energy_bin_restarts_keep_the_free_path_law_on_the_gpu(karl):
+    """The oracle pin's accelerated electrons through constant-cross-section
+    gas: every energy-bin restart draws a new optical depth, so the
+    uncollided fraction stays exp(-n sigma L); the GPU's flights, restarts
+    and collision counts equal the oracle's."""
+    n_m3, sigma, length = 2e20, 1e-20, 0.5
+    nodes = inputs.energy_nodes(64, 100.0, 2e3)
+    ch = [inputs.Channel("elastic", inputs.ELASTIC, inputs.E, -1, 0.0, np.full_like(nodes, sigma))]
+    prob = inputs.uniform_problem(n_m3, length, 10, ch, n_energy=64, e_min=100.0, e_max=2e3,
+                                  e_cut=0.0, n_tebins=32)
+    prob.target_mass_ev = 1e18
+    orb = _orbit(0.05, frac=0.1, tube_radius_m=1.0, n_rbins=4,
+                 e_z_vm=np.full(prob.n_zbins, -2000.0))
+    n = 6000
+    pr = _prims(np.zeros(n), np.zeros(n), np.zeros(n), np.full(n, 150.0), np.ones(n),
+                np.zeros(n), inputs.E)
+    g = _gpu(karl, prob, orb, pr, seed=8)
+    o = oracle.orbit_run(prob, orb, pr, seed=8, n_threads=THREADS)
+    assert float(np.mean(g["per_primary"] == o["per_primary"])) >= 0.99
+    p = math.exp(-n_m3 * sigma * length)
+    k = int(np.sum(g["per_primary"] == 0))
+    assert abs(k - n * p) < 5 * math.sqrt(n * p * (1 - p))

@@ -282,3 +282,28 @@ def test_flight_restarts_at_each_energy_bin():
     b = [math.floor(math.log(e) / math.log(2e4) * 64) for e in (100.0, 1100.0)]
     assert int(t["ledger"][oracle.OB_N_FLIGHTS]) == b[1] - b[0] + 1 == 17
     assert abs(t["energy"][oracle.OE_EXIT1] - 1100.0) < 0.11
+
+
+def test_energy_bin_restarts_keep_the_free_path_law():
+    """Electrons accelerated along B through uniform gas of constant cross
+    section restart their flight at each energy bin they pass (32 bins over
+    [100 eV, 2 keV] here); a new optical depth is drawn each time, so, the
+    exponential law being memoryless, the fraction crossing the column
+    without a collision is still exp(-n sigma L).  Reusing the first draw
+    would let far more through."""
+    n_m3, sigma, length = 2e20, 1e-20, 0.5
+    nodes = inputs.energy_nodes(64, 100.0, 2e3)
+    ch = [inputs.Channel("elastic", inputs.ELASTIC, inputs.E, -1, 0.0, np.full_like(nodes, sigma))]
+    prob = inputs.uniform_problem(n_m3, length, 10, ch, n_energy=64, e_min=100.0, e_max=2e3,
+                                  e_cut=0.0, n_tebins=32)
+    prob.target_mass_ev = 1e18
+    orb = _orbit(0.05, frac=0.1, tube_radius_m=1.0, n_rbins=4,
+                 e_z_vm=np.full(prob.n_zbins, -2000.0))
+    n = 6000
+    pr = _prims(np.zeros(n), np.zeros(n), np.zeros(n), np.full(n, 150.0), np.ones(n),
+                np.zeros(n), inputs.E)
+    t = oracle.orbit_run(prob, orb, pr, seed=8, n_threads=4)
+    assert t["ledger"][oracle.OB_N_FLIGHTS] > 5 * n           # restarts happened
+    p = math.exp(-n_m3 * sigma * length)
+    k = int(np.sum(t["per_primary"] == 0))
+    assert abs(k - n * p) < 5 * math.sqrt(n * p * (1 - p))
