@@ -84,3 +84,33 @@ def run_cycles_sharded(run_cycle: Callable, prims, seed: int, n_cycles: int, ran
             s = _allreduce_sum(t[k]) if world > 1 else t[k]
             tot[k] = s if k not in tot else tot[k] + s
     return tot
+
+
+ORBIT_RAW_KEYS = ("spectrum", "time_z", "time_r", "cross_pos", "cross_neg", "rcross_out",
+                  "rcross_in", "wall", "ledger", "chan_count")
+
+
+def run_orbit_sharded(run_orbit: Callable, prims, seed: int, rank: int,
+                      world: int) -> Dict[str, np.ndarray]:
+    """The full-orbit run (one pass, no fields fed back) split over `world`
+    ranks by primary-id ranges: histories are independent and their random
+    streams keyed by primary id, so one integer all-reduce of the raw
+    tallies gives the single run's tallies bit for bit; the FP64 energy
+    ledger is summed as well (equal to rounding).  ``run_orbit(prims_slice,
+    seed)`` is the per-rank run (``karl.Context.run_orbit`` on a GPU); the
+    slice carries its primary-id offset."""
+    a, b = shard_range(prims.n, rank, world)
+    mine = type(prims)(*(getattr(prims, k)[a:b].copy() for k in
+                         ("x_m", "y_m", "z_m", "e_ev", "mu", "phi", "species")),
+                       pid_offset=int(prims.pid_offset) + a)
+    t = run_orbit(mine, seed)
+    out = {k: _allreduce_sum(t[k]) if world > 1 else t[k] for k in ORBIT_RAW_KEYS}
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        e = torch.from_numpy(np.ascontiguousarray(t["energy"], np.float64).copy())
+        dist.all_reduce(e, op=dist.ReduceOp.SUM)
+        out["energy"] = e.numpy()
+    else:
+        out["energy"] = t["energy"]
+    return out

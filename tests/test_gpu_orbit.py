@@ -328,3 +328,25 @@ def test_energy_bin_restarts_keep_the_free_path_law_on_the_gpu(karl):
     p = math.exp(-n_m3 * sigma * length)
     k = int(np.sum(g["per_primary"] == 0))
     assert abs(k - n * p) < 5 * math.sqrt(n * p * (1 - p))
+
+
+def test_orbit_shards_add_up_to_the_single_run(karl):
+    """Two primary-id ranges run separately (with their id offsets) give
+    tallies whose sum is the single run's, bit for bit: the per-rank step of
+    shard.run_orbit_sharded on one device."""
+    from paper_2503_10263_gb300 import shard
+    prob, orb, pr = inputs.orbit_config(n_decays=200, seed=6)
+    ctx = karl.Context(prob)
+    try:
+        full = ctx.run_orbit(orb, pr, seed=31)
+        parts = []
+        for rank in range(2):
+            a, b = shard.shard_range(pr.n, rank, 2)
+            sub = inputs.OrbitPrimaries(*(getattr(pr, k)[a:b].copy() for k in
+                                          ("x_m", "y_m", "z_m", "e_ev", "mu", "phi", "species")),
+                                        pid_offset=a)
+            parts.append(ctx.run_orbit(orb, sub, seed=31))
+    finally:
+        ctx.close()
+    for k in shard.ORBIT_RAW_KEYS:
+        np.testing.assert_array_equal(parts[0][k] + parts[1][k], full[k], err_msg=k)

@@ -94,3 +94,35 @@ def test_shard_ranges_cover_all_primaries():
             rs = [shard.shard_range(n, r, world) for r in range(world)]
             assert rs[0][0] == 0 and rs[-1][1] == n
             assert all(rs[i][1] == rs[i + 1][0] for i in range(world - 1))
+
+
+def _orbit_worker(rank, world, port, out_dir):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    prob, orb, pr = inputs.orbit_config(n_decays=40, seed=5)
+
+    def run_orbit(p, seed):
+        return oracle.orbit_run(prob, orb, p, seed=seed)
+
+    t = shard.run_orbit_sharded(run_orbit, pr, seed=21, rank=rank, world=world)
+    np.savez(os.path.join(out_dir, f"orbit{rank}.npz"), **t)
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_equal_single_orbit_run(tmp_path):
+    """The full-orbit form shards the same way: two ranks' summed tallies
+    equal the single run bit for bit (the energy ledger to rounding)."""
+    oracle.build()
+    world = 2
+    mp.start_processes(_orbit_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world,
+                       join=True, start_method="spawn")
+    prob, orb, pr = inputs.orbit_config(n_decays=40, seed=5)
+    full = oracle.orbit_run(prob, orb, pr, seed=21, n_threads=2)
+    r0 = np.load(tmp_path / "orbit0.npz")
+    r1 = np.load(tmp_path / "orbit1.npz")
+    for k in shard.ORBIT_RAW_KEYS:
+        np.testing.assert_array_equal(r0[k], r1[k], err_msg=k)
+        np.testing.assert_array_equal(r0[k], full[k], err_msg=k)
+    np.testing.assert_allclose(r0["energy"], full["energy"], rtol=1e-12, atol=1e-9)
