@@ -183,8 +183,8 @@ def run_reference(args):
             coll += c
             secs += dt
     value = coll / secs
-    sample = (f"first {nd} decays of the workload (both passes) per step, "
-              f"{args.steps} timed steps after {args.warmup} warm-up")
+    sample = (f"first {nd} decays of the workload (both passes) per step; "
+              f"timed steps {args.steps}, warm-up steps {args.warmup}")
     line = {
         "metric": "collision events/s", "value": value, "unit": "collision events/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
